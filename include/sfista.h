@@ -1,0 +1,243 @@
+/*
+ * sfista.h -- C ABI of the GB300 structured-FISTA library (libsfista.so).
+ *
+ * Structured FISTA (sFISTA) for Tikhonov-regularised image deblurring,
+ * Chen, Nagy, Xi, Yu, "Structured FISTA for Image Restoration",
+ * arXiv 1901.00913.  The blur matrix A of b = A x + e (Eq. 1.1) is replaced
+ * by the Kronecker sum A_s = sum_{i=1..r} A_i kron B_i (Eq. Kronecker
+ * structure, Theorem 1), and Alg. 2 minimises
+ *     0.5 || sum_i B_i X A_i^T - B ||_F^2 + 0.5 lambda^2 ||X||_F^2
+ * (Eq. matrix minimization model) with the fixed-step FISTA iteration.
+ *
+ * Paper notation: the paper's left factor H_i is B_i here (m x m, acts on
+ * the row index of the image) and its right factor K_i is A_i (n x n, acts on
+ * the column index); the paper's number of terms s is r here.
+ *
+ * Conventions for every call
+ *   - Images are row-major, img_rows x img_cols (m x n): X[a][b] at
+ *     X[a * n + b], a the row (vertical) index.  The paper's vec() stacks
+ *     columns; the library never relies on that order in memory.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory on the context's device.  The caller owns every buffer
+ *     it passes; the library copies what it keeps.  A context owns its own
+ *     device memory until sfista_destroy().
+ *   - Every call returns an sfista_status; nothing throws across the ABI.
+ *     A failed call writes no output and leaves *out NULL where it has one.
+ *     sfista_last_error() gives a one-line description of the most recent
+ *     failure on the calling thread.
+ *   - A context is used by one host thread at a time; calls on one context
+ *     are ordered on the stream they are given (device calls) or on the
+ *     context's own stream (host calls).
+ */
+#ifndef SFISTA_H
+#define SFISTA_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sfista_ctx sfista_ctx;
+
+typedef enum {
+    SFISTA_OK = 0,
+    SFISTA_EINVAL = 1,    /* bad argument (size, centre, rank, NaN/Inf input, tied singular values) */
+    SFISTA_ENOMEM = 2,    /* host or device allocation failed */
+    SFISTA_ECUDA = 3,     /* a CUDA runtime/driver call failed */
+    SFISTA_ENOTSUP = 4,   /* valid request this build does not implement (e.g. periodic boundary) */
+    SFISTA_ENUMERIC = 5,  /* the iteration produced a non-finite value */
+    SFISTA_ETIMEOUT = 6   /* a device-side wait exceeded its bound; the kernel returned early */
+} sfista_status;
+
+/* Boundary condition (Sec. 2).  Periodic is recognised but not supported:
+ * the paper leaves it out because it rings at the image border. */
+typedef enum {
+    SFISTA_BC_ZERO = 0,       /* A is BTTB; factors are banded Toeplitz             */
+    SFISTA_BC_REFLEXIVE = 1,  /* A is BTHTHB; factors are Toeplitz + Hankel          */
+    SFISTA_BC_PERIODIC = 2    /* -> SFISTA_ENOTSUP                                   */
+} sfista_bc;
+
+/* Arithmetic of the Kronecker operator (the four products of Step 1).
+ * The FISTA state (X_k, X_{k-1}, Y_k) is always carried in FP64. */
+typedef enum {
+    SFISTA_FP32 = 0,     /* FP32 FMA on the CUDA cores                                  */
+    SFISTA_TF32 = 1,     /* one TF32 tensor-core product, FP32 accumulate                */
+    SFISTA_TF32X3 = 2,   /* split TF32: hi*hi + lo*hi + hi*lo, FP32 accumulate           */
+    SFISTA_BF16 = 3,     /* one BF16 tensor-core product, FP32 accumulate                */
+    SFISTA_BF16X3 = 4    /* split BF16: hi*hi + lo*hi + hi*lo, FP32 accumulate           */
+} sfista_prec;
+
+/* How the operator is executed. */
+typedef enum {
+    SFISTA_OP_AUTO = 0,        /* library's choice for (size, r, band, precision)           */
+    SFISTA_OP_BANDED = 1,      /* factors applied from compact band storage (FP32/FP64 FMA)  */
+    SFISTA_OP_GEMM_BAND = 2,   /* dense-factor GEMMs that skip K tiles outside the band       */
+    SFISTA_OP_GEMM_DENSE = 3   /* dense-factor GEMMs over the full K range (Sec. 3.3 O(s(nm^2+mn^2))) */
+} sfista_operator;
+
+typedef struct {
+    int prec;               /* sfista_prec, default SFISTA_FP32                          */
+    int op;                 /* sfista_operator, default SFISTA_OP_AUTO                   */
+    int project_nonneg;     /* 1: X_k <- max(X_k, 0) after the shrink (x >= 0 constraint) */
+    int use_graph;          /* 1 (default): replay the iteration loop as a CUDA graph     */
+    double lipschitz;       /* > 0: use this L; <= 0: estimate lambda_max(A_s^T A_s)      */
+    double lipschitz_tol;   /* relative change that stops the power iteration (1e-10)     */
+    int lipschitz_maxit;    /* power-iteration cap (1000)                                 */
+    int device;             /* CUDA device ordinal (default: current device)              */
+} sfista_opts;
+
+/* Fill *opts with the defaults listed above. */
+void sfista_default_opts(sfista_opts *opts);
+
+/*
+ * sfista_setup -- form the Kronecker approximation of the blur (Sec. 2).
+ *
+ * psf      host, row-major psf_rows x psf_cols PSF P (FP64, finite; used as
+ *          given, not normalised).
+ * center_row, center_col
+ *          0-based pixel of P that images a point source (the paper's
+ *          centre (l, q)); -1 selects the middle pixel.
+ * img_rows, img_cols
+ *          image size m x n; requires psf_rows <= m and psf_cols <= n.
+ * bc       sfista_bc.
+ * r        number of Kronecker terms, 1 <= r <= min(psf_rows, psf_cols).
+ * opts     NULL for defaults.
+ * out      receives the new context.
+ *
+ * In FP64 on the host: the Gram weights of Theorem 1, their Cholesky factors
+ * R (R^T R = G), the SVD of the weighted PSF P_bar = R_r P R_c^T, and the
+ * factor profiles c_k = sqrt(s_k) R_r^{-1} u_k (left) and
+ * d_k = sqrt(s_k) R_c^{-1} v_k (right).  Then, on the device, the banded
+ * factors B_k = toep(c_k) [+ hank(c_k)], A_k = toep(d_k) [+ hank(d_k)] in
+ * the operand formats the precision needs, and (unless opts->lipschitz > 0)
+ * L = lambda_max(A_s^T A_s) by FP64 power iteration.
+ * Errors: EINVAL for bad sizes/centre/rank, non-finite PSF, or
+ * s_r == s_{r+1} > 0 (the truncation is not unique); ENOTSUP for periodic
+ * boundary or a precision/operator pair this build lacks; ENOMEM; ECUDA.
+ */
+sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols,
+                           int center_row, int center_col,
+                           int img_rows, int img_cols, int bc, int r,
+                           const sfista_opts *opts, sfista_ctx **out);
+
+/*
+ * sfista_factorize -- the host half of sfista_setup alone (no device work):
+ * the FP64 Kronecker factorisation of Sec. 2 / Theorem 1 for an m x n image.
+ * sigma      host, min(psf_rows, psf_cols) singular values of P_bar (may be NULL)
+ * C          host, r x psf_rows column profiles c_k (left factors B_k)
+ * D          host, r x psf_cols row profiles d_k (right factors A_k)
+ * approx_err host, sqrt(sum_{k>r} s_k^2) = ||A - A_s||_F (may be NULL)
+ * Same argument checks and errors as sfista_setup.
+ */
+sfista_status sfista_factorize(const double *psf, int psf_rows, int psf_cols,
+                               int center_row, int center_col,
+                               int img_rows, int img_cols, int bc, int r,
+                               double *sigma, double *C, double *D,
+                               double *approx_err);
+
+/* Release every resource of ctx (NULL is ignored). */
+void sfista_destroy(sfista_ctx *ctx);
+
+/*
+ * sfista_solve -- Alg. 2 from X_0 = 0 for `iters` iterations (host buffers).
+ *
+ * b      host, m x n observed image B (FP32).
+ * lambda Tikhonov parameter (>= 0; the penalty is 0.5 lambda^2 ||X||^2).
+ * iters  >= 0; 0 returns X_0 = 0.
+ * x      host, m x n output X_iters (FP32).
+ * Copies b in, runs the loop on the context's stream, copies x out and
+ * synchronises.  ENUMERIC if a non-finite value appeared, ETIMEOUT if a
+ * device wait gave up, EINVAL for non-finite b or bad arguments.
+ */
+sfista_status sfista_solve(sfista_ctx *ctx, const float *b, double lambda,
+                           int iters, float *x);
+
+/*
+ * sfista_solve_device -- as sfista_solve with device buffers d_b, d_x (FP32,
+ * m x n) on the CUDA stream `stream` (cudaStream_t, NULL = legacy default).
+ * Asynchronous: returns after enqueueing; status words are checked on the
+ * next call that synchronises (sfista_sync).
+ */
+sfista_status sfista_solve_device(sfista_ctx *ctx, const float *d_b,
+                                  double lambda, int iters, float *d_x,
+                                  void *stream);
+
+/*
+ * sfista_solve_state -- resumable form of Alg. 2 on FP64 device state.
+ *
+ * d_X, d_Xprev  device, m x n FP64: on entry X_{k0} and X_{k0-1}; on exit
+ *               X_{k0+iters} and X_{k0+iters-1}.  With k0 = 0, d_X is the
+ *               starting point X_0 = Y_1 and d_Xprev is ignored on entry.
+ * k0            number of iterations already done (t_k depends on k only,
+ *               so (X_k, X_{k-1}, k) is the whole state of Alg. 2).
+ */
+sfista_status sfista_solve_state(sfista_ctx *ctx, const float *d_b,
+                                 double lambda, int k0, int iters,
+                                 double *d_X, double *d_Xprev, void *stream);
+
+/* Wait for the context's work on `stream`, then report device-side status
+ * (ENUMERIC / ETIMEOUT) raised since the last sync. */
+sfista_status sfista_sync(sfista_ctx *ctx, void *stream);
+
+/*
+ * sfista_apply -- the Kronecker operator alone, on device FP32 buffers:
+ *   transpose = 0:  d_y = sum_i B_i d_x A_i^T     (A_s, Eq. matrix equation)
+ *   transpose = 1:  d_y = sum_i B_i^T d_x A_i     (A_s^T, Alg. 2 Step 1)
+ * in the context's precision and operator form.  Asynchronous on `stream`.
+ */
+sfista_status sfista_apply(sfista_ctx *ctx, const float *d_x, float *d_y,
+                           int transpose, void *stream);
+
+/*
+ * sfista_info -- scalars of the setup.
+ * lipschitz   L used by Step 1 (estimated or given).
+ * sigma       if non-NULL, min(psf_rows, psf_cols) singular values of P_bar.
+ * approx_err  if non-NULL, sqrt(sum_{k>r} s_k^2) = ||A - A_s||_F (Theorem 1).
+ * config      if non-NULL, int[4]: effective precision, operator form, band
+ *             width of the right factors, band width of the left factors.
+ */
+sfista_status sfista_info(const sfista_ctx *ctx, double *lipschitz,
+                          double *sigma, double *approx_err, int *config);
+
+/* Factor profiles: C (r x psf_rows) column profiles c_k of the left factors,
+ * D (r x psf_cols) row profiles d_k of the right factors (host, FP64). */
+sfista_status sfista_get_profiles(const sfista_ctx *ctx, double *C, double *D);
+
+/* Dense factors on the host, FP64: B (r x m x m), A (r x n x n). */
+sfista_status sfista_get_factors(const sfista_ctx *ctx, double *A, double *B);
+
+/*
+ * sfista_blur -- the exact blur of Eq. (1.1) (not the approximation):
+ *   d_y[a][b] = sum_{i,j} P[i][j] * Xext[a - i + cr][b - j + cc]
+ * with Xext the zero or half-sample-reflected extension of d_x.  Used to
+ * synthesise observations.  psf is host FP64; d_x, d_y device FP32 (m x n,
+ * distinct buffers).  Synchronous.
+ */
+sfista_status sfista_blur(const double *psf, int psf_rows, int psf_cols,
+                          int center_row, int center_col, int bc,
+                          const float *d_x, int img_rows, int img_cols,
+                          float *d_y, void *stream);
+
+/*
+ * sfista_time_stages -- per-kernel timing of one iteration of Alg. 2 on the
+ * context's own stream, for roofline reporting.  Runs `reps` iterations
+ * (k = 1..reps, launched one by one, no graph) on the device observation
+ * d_b, with CUDA events recorded between the four stages of each iteration:
+ *   0: forward right-factor product   (Y A_i^T)
+ *   1: forward left-factor product + residual epilogue
+ *   2: adjoint right-factor product   (R A_i)
+ *   3: adjoint left-factor product + shrink / momentum epilogue
+ * ms (host, float[4]) receives the mean duration of each stage in ms.
+ * Synchronous.  Leaves the solver state undefined (the next solve resets it).
+ */
+sfista_status sfista_time_stages(sfista_ctx *ctx, const float *d_b, double lambda,
+                                 int reps, float *ms);
+
+const char *sfista_strerror(sfista_status s);
+const char *sfista_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFISTA_H */

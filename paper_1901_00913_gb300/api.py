@@ -1,0 +1,276 @@
+"""Python binding of libsfista (ctypes; argument marshalling only).
+
+Every function here forwards to the C entry point of the same name declared
+in ``include/sfista.h``; all arithmetic runs in the library's CUDA kernels and
+host setup.  PyTorch provides device memory and streams.  If the shared
+library is missing or fails to load, ``load()`` raises: there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsfista.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENOTSUP, ENUMERIC, ETIMEOUT = range(7)
+BC = {"zero": 0, "reflexive": 1, "reflective": 1, "periodic": 2}
+PREC = {"fp32": 0, "tf32": 1, "tf32x3": 2, "bf16": 3, "bf16x3": 4}
+OP = {"auto": 0, "banded": 1, "gemm_band": 2, "gemm_dense": 3}
+PREC_NAME = {v: k for k, v in PREC.items()}
+OP_NAME = {v: k for k, v in OP.items()}
+
+_lib = None
+
+
+class SfistaError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("sfista status %d (%s): %s" % (status, _strerror(status), msg))
+        self.status = status
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("op", ctypes.c_int), ("project_nonneg", ctypes.c_int),
+                ("use_graph", ctypes.c_int), ("lipschitz", ctypes.c_double),
+                ("lipschitz_tol", ctypes.c_double), ("lipschitz_maxit", ctypes.c_int),
+                ("device", ctypes.c_int)]
+
+
+def load(path=None):
+    """Load libsfista.so (raises OSError if it is missing: no CPU fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise OSError("libsfista.so not built (%s); run paper_1901_00913_gb300.build.build()" % path)
+    L = ctypes.CDLL(path)
+    vp, i, d, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)
+    L.sfista_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    L.sfista_default_opts.restype = None
+    L.sfista_setup.argtypes = [vp, i, i, i, i, i, i, i, i, ctypes.POINTER(Opts), ctypes.POINTER(vp)]
+    L.sfista_factorize.argtypes = [vp, i, i, i, i, i, i, i, i, vp, vp, vp, D]
+    L.sfista_destroy.argtypes = [vp]
+    L.sfista_destroy.restype = None
+    L.sfista_solve.argtypes = [vp, vp, d, i, vp]
+    L.sfista_solve_device.argtypes = [vp, vp, d, i, vp, vp]
+    L.sfista_solve_state.argtypes = [vp, vp, d, i, i, vp, vp, vp]
+    L.sfista_sync.argtypes = [vp, vp]
+    L.sfista_apply.argtypes = [vp, vp, vp, i, vp]
+    L.sfista_info.argtypes = [vp, D, vp, D, vp]
+    L.sfista_get_profiles.argtypes = [vp, vp, vp]
+    L.sfista_get_factors.argtypes = [vp, vp, vp]
+    L.sfista_blur.argtypes = [vp, i, i, i, i, i, vp, i, i, vp, vp]
+    L.sfista_time_stages.argtypes = [vp, vp, d, i, vp]
+    L.sfista_strerror.argtypes = [i]
+    L.sfista_strerror.restype = ctypes.c_char_p
+    L.sfista_last_error.argtypes = []
+    L.sfista_last_error.restype = ctypes.c_char_p
+    for name in ("sfista_setup", "sfista_factorize", "sfista_solve", "sfista_solve_device", "sfista_solve_state",
+                 "sfista_sync", "sfista_apply", "sfista_info", "sfista_get_profiles",
+                 "sfista_get_factors", "sfista_blur", "sfista_time_stages"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _strerror(s):
+    try:
+        return load().sfista_strerror(s).decode()
+    except OSError:
+        return "?"
+
+
+def _check(status):
+    if status != OK:
+        raise SfistaError(status, load().sfista_last_error().decode())
+
+
+def _ptr(t):
+    """Device pointer of a contiguous CUDA tensor."""
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def default_opts():
+    o = Opts()
+    load().sfista_default_opts(ctypes.byref(o))
+    return o
+
+
+# ------------------------------------------------------------------ C-named calls
+def sfista_setup(psf, img_rows, img_cols, bc, r, center=(-1, -1), opts=None):
+    """Returns an opaque context handle (int).  See include/sfista.h."""
+    P = np.ascontiguousarray(psf, dtype=np.float64)
+    h = ctypes.c_void_p()
+    o = opts if opts is not None else default_opts()
+    _check(load().sfista_setup(P.ctypes.data, P.shape[0], P.shape[1], int(center[0]), int(center[1]),
+                               int(img_rows), int(img_cols), int(bc), int(r), ctypes.byref(o),
+                               ctypes.byref(h)))
+    return h.value
+
+
+def sfista_factorize(psf, img_rows, img_cols, bc, r, center=(-1, -1)):
+    """Host-only FP64 factorisation; returns (sigma, C, D, approx_err)."""
+    P = np.ascontiguousarray(psf, dtype=np.float64)
+    p, q = P.shape
+    sig = np.zeros(min(p, q))
+    C = np.zeros((r, p))
+    D = np.zeros((r, q))
+    err = ctypes.c_double()
+    _check(load().sfista_factorize(P.ctypes.data, p, q, int(center[0]), int(center[1]), int(img_rows),
+                                   int(img_cols), int(bc), int(r), sig.ctypes.data, C.ctypes.data,
+                                   D.ctypes.data, ctypes.byref(err)))
+    return sig, C, D, err.value
+
+
+def sfista_destroy(ctx):
+    load().sfista_destroy(ctypes.c_void_p(ctx))
+
+
+def sfista_solve(ctx, b, lam, iters, x):
+    """Host buffers: b, x float32 contiguous numpy arrays of the image shape."""
+    assert b.dtype == np.float32 and x.dtype == np.float32 and b.flags.c_contiguous and x.flags.c_contiguous
+    _check(load().sfista_solve(ctypes.c_void_p(ctx), b.ctypes.data, float(lam), int(iters), x.ctypes.data))
+
+
+def sfista_solve_device(ctx, d_b, lam, iters, d_x, stream=None):
+    _check(load().sfista_solve_device(ctypes.c_void_p(ctx), _ptr(d_b), float(lam), int(iters), _ptr(d_x),
+                                      _stream_ptr(stream)))
+
+
+def sfista_solve_state(ctx, d_b, lam, k0, iters, d_X, d_Xprev, stream=None):
+    _check(load().sfista_solve_state(ctypes.c_void_p(ctx), _ptr(d_b), float(lam), int(k0), int(iters),
+                                     _ptr(d_X), _ptr(d_Xprev), _stream_ptr(stream)))
+
+
+def sfista_sync(ctx, stream=None):
+    _check(load().sfista_sync(ctypes.c_void_p(ctx), _stream_ptr(stream)))
+
+
+def sfista_apply(ctx, d_x, d_y, transpose=False, stream=None):
+    _check(load().sfista_apply(ctypes.c_void_p(ctx), _ptr(d_x), _ptr(d_y), int(bool(transpose)),
+                               _stream_ptr(stream)))
+
+
+def sfista_info(ctx, kmax):
+    L = ctypes.c_double()
+    err = ctypes.c_double()
+    sig = np.zeros(kmax)
+    cfg = np.zeros(4, dtype=np.int32)
+    _check(load().sfista_info(ctypes.c_void_p(ctx), ctypes.byref(L), sig.ctypes.data, ctypes.byref(err),
+                              cfg.ctypes.data))
+    return {"lipschitz": L.value, "sigma": sig, "approx_err": err.value,
+            "prec": PREC_NAME[int(cfg[0])], "op": OP_NAME[int(cfg[1])],
+            "band_right": int(cfg[2]), "band_left": int(cfg[3])}
+
+
+def sfista_get_profiles(ctx, r, p, q):
+    C = np.zeros((r, p))
+    D = np.zeros((r, q))
+    _check(load().sfista_get_profiles(ctypes.c_void_p(ctx), C.ctypes.data, D.ctypes.data))
+    return C, D
+
+
+def sfista_get_factors(ctx, r, m, n):
+    A = np.zeros((r, n, n))
+    B = np.zeros((r, m, m))
+    _check(load().sfista_get_factors(ctypes.c_void_p(ctx), A.ctypes.data, B.ctypes.data))
+    return A, B
+
+
+def sfista_blur(psf, d_x, bc, center=(-1, -1), d_y=None, stream=None):
+    """Exact blur of Eq. (1.1) of a CUDA float32 image; returns d_y."""
+    import torch
+    P = np.ascontiguousarray(psf, dtype=np.float64)
+    if d_y is None:
+        d_y = torch.empty_like(d_x)
+    m, n = d_x.shape
+    _check(load().sfista_blur(P.ctypes.data, P.shape[0], P.shape[1], int(center[0]), int(center[1]), int(bc),
+                              _ptr(d_x), m, n, _ptr(d_y), _stream_ptr(stream)))
+    return d_y
+
+
+def sfista_time_stages(ctx, d_b, lam, reps):
+    """Mean ms of the four per-iteration stages (see include/sfista.h)."""
+    ms = np.zeros(4, dtype=np.float32)
+    _check(load().sfista_time_stages(ctypes.c_void_p(ctx), _ptr(d_b), float(lam), int(reps), ms.ctypes.data))
+    return ms
+
+
+# ------------------------------------------------------------------ convenience wrapper
+class Sfista:
+    """Owns one context: ``Sfista(psf, (m, n), 'reflexive', r=3, prec='bf16x3')``."""
+
+    def __init__(self, psf, shape, bc, r, center=(-1, -1), prec="fp32", op="auto", project=False,
+                 use_graph=True, lipschitz=None, lipschitz_tol=1e-10, lipschitz_maxit=1000, device=-1):
+        o = default_opts()
+        o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+        o.op = OP[op] if isinstance(op, str) else int(op)
+        o.project_nonneg = int(bool(project))
+        o.use_graph = int(bool(use_graph))
+        o.lipschitz = float(lipschitz) if lipschitz else 0.0
+        o.lipschitz_tol = float(lipschitz_tol)
+        o.lipschitz_maxit = int(lipschitz_maxit)
+        o.device = int(device)
+        bcv = BC[bc] if isinstance(bc, str) else int(bc)
+        self.shape = (int(shape[0]), int(shape[1]))
+        self.psf_shape = np.asarray(psf).shape
+        self.r = int(r)
+        self.ctx = sfista_setup(psf, self.shape[0], self.shape[1], bcv, r, center, o)
+
+    def close(self):
+        if self.ctx:
+            sfista_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        return sfista_info(self.ctx, min(self.psf_shape))
+
+    def profiles(self):
+        return sfista_get_profiles(self.ctx, self.r, *self.psf_shape)
+
+    def factors(self):
+        return sfista_get_factors(self.ctx, self.r, *self.shape)
+
+    def solve(self, b, lam, iters):
+        b = np.ascontiguousarray(b, dtype=np.float32)
+        x = np.empty_like(b)
+        sfista_solve(self.ctx, b, lam, iters, x)
+        return x
+
+    def solve_device(self, d_b, lam, iters, out=None, stream=None, sync=True):
+        import torch
+        out = torch.empty_like(d_b) if out is None else out
+        sfista_solve_device(self.ctx, d_b, lam, iters, out, stream)
+        if sync:
+            sfista_sync(self.ctx, stream)
+        return out
+
+    def solve_state(self, d_b, lam, k0, iters, X, Xprev, stream=None, sync=True):
+        sfista_solve_state(self.ctx, d_b, lam, k0, iters, X, Xprev, stream)
+        if sync:
+            sfista_sync(self.ctx, stream)
+        return X, Xprev
+
+    def apply(self, d_x, transpose=False, out=None, stream=None, sync=True):
+        import torch
+        out = torch.empty_like(d_x) if out is None else out
+        sfista_apply(self.ctx, d_x, out, transpose, stream)
+        if sync:
+            sfista_sync(self.ctx, stream)
+        return out

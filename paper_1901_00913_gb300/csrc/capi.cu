@@ -1,0 +1,636 @@
+// C ABI of libsfista: context, setup, the Alg. 2 loop driver and the
+// operator entry points.  See include/sfista.h for the contract of each call.
+#include <math.h>
+#include <string.h>
+
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "gemm.h"
+#include "internal.h"
+
+namespace sfista {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+sfista_status fail(sfista_status s, const std::string &msg) {
+    g_last_error = msg;
+    return s;
+}
+
+namespace {
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (dev != prev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+__global__ void init_state_kernel(const double *X, const double *Xp, double *Y, float *Yop, void *Yhi,
+                                  void *Ylo, int split_kind, size_t count, double beta) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+         i += (size_t)gridDim.x * blockDim.x) {
+        double y = X[i] + beta * (X[i] - Xp[i]);
+        Y[i] = y;
+        Yop[i] = (float)y;
+        if (split_kind == 1) {
+            __nv_bfloat16 h = __double2bfloat16(y);
+            reinterpret_cast<__nv_bfloat16 *>(Yhi)[i] = h;
+            reinterpret_cast<__nv_bfloat16 *>(Ylo)[i] = __double2bfloat16(y - (double)__bfloat162float(h));
+        } else if (split_kind == 2) {
+            unsigned u;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"((float)y));
+            float h = __uint_as_float(u);
+            reinterpret_cast<float *>(Yhi)[i] = h;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"((float)(y - (double)h)));
+            reinterpret_cast<float *>(Ylo)[i] = __uint_as_float(u);
+        }
+    }
+}
+
+template <typename T>
+cudaError_t upload(T **dst, const T *src, size_t count, cudaStream_t s) {
+    cudaError_t e = cudaMalloc((void **)dst, sizeof(T) * std::max<size_t>(count, 1));
+    if (e) return e;
+    return cudaMemcpyAsync(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice, s);
+}
+
+}  // namespace
+}  // namespace sfista
+
+using namespace sfista;
+
+struct sfista_ctx {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    HostSetup hs;
+    sfista_opts opts;
+    int prec = SFISTA_FP32, op = SFISTA_OP_BANDED;
+    double L = 0.0;
+    int m = 0, n = 0, r = 0;
+    size_t N = 0;
+    // Band storage on the device: FP64 (power iteration) and FP32 (operator).
+    double *dA = nullptr, *dAT = nullptr, *dB = nullptr, *dBT = nullptr;
+    float *fA = nullptr, *fAT = nullptr, *fB = nullptr, *fBT = nullptr;
+    // Iteration state.
+    float *Bd = nullptr, *Yop = nullptr, *Z = nullptr, *R = nullptr, *tmp = nullptr;
+    double *Xb[2] = {nullptr, nullptr}, *Y = nullptr;
+    unsigned *status = nullptr;
+    double *beta = nullptr;
+    int beta_len = 0;
+    std::vector<double> beta_host;
+    // Tensor-core path (operand panels, intermediates, tensor maps).
+    GemmPath *gemm = nullptr;
+    // Cached CUDA graph of the iteration loop.
+    cudaGraphExec_t gexec = nullptr;
+    int g_k0 = -1, g_iters = -1;
+    double g_lam = -1.0;
+};
+
+namespace {
+
+void ctx_free(sfista_ctx *c) {
+    if (!c) return;
+    DeviceGuard g(c->dev);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->gemm) gemm_destroy(c->gemm);
+    void *ptrs[] = {c->dA, c->dAT, c->dB, c->dBT, c->fA, c->fAT, c->fB, c->fBT, c->Bd, c->Yop, c->Z,
+                    c->R, c->tmp, c->Xb[0], c->Xb[1], c->Y, c->status, c->beta};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+sfista_status ensure_beta(sfista_ctx *c, int k_end) {
+    if (k_end <= c->beta_len) return SFISTA_OK;
+    int len = std::max(k_end, 2 * c->beta_len);
+    momentum_table(len, &c->beta_host);
+    SF_CUDA(cudaStreamSynchronize(c->stream));
+    if (c->beta) cudaFree(c->beta);
+    c->beta = nullptr;
+    SF_CUDA(cudaMalloc((void **)&c->beta, sizeof(double) * len));
+    SF_CUDA(cudaMemcpy(c->beta, c->beta_host.data(), sizeof(double) * len, cudaMemcpyHostToDevice));
+    c->beta_len = len;
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    return SFISTA_OK;
+}
+
+// Forward operator with the residual epilogue, then the adjoint with the
+// prox + momentum epilogue: one iteration k of Alg. 2 (Steps 1-3).
+ProxArgs prox_args(sfista_ctx *c, int k, double lam) {
+    ProxArgs pa{};
+    pa.Bd = c->Bd;
+    pa.Xin = c->Xb[(k - 1) & 1];
+    pa.Xout = c->Xb[k & 1];
+    pa.Y = c->Y;
+    pa.Yop = c->Yop;
+    pa.beta = c->beta;
+    pa.k = k;
+    pa.L = c->L;
+    pa.lam2 = lam * lam;
+    pa.project = c->opts.project_nonneg;
+    pa.status = c->status;
+    return pa;
+}
+
+// Stage `st` (0..3) of iteration k; see sfista_time_stages for the numbering.
+void enqueue_stage(sfista_ctx *c, int st, const ProxArgs &pa) {
+    const HostSetup &h = c->hs;
+    if (c->op == SFISTA_OP_BANDED) {
+        switch (st) {
+            case 0: launch_band_rows<float>(c->Yop, c->m, c->n, c->fA, h.A.lo, h.A.w, c->r, c->Z, c->stream); break;
+            case 1: launch_band_cols<float>(c->Z, c->m, c->n, c->fB, h.B.lo, h.B.w, c->r, EPI_RESIDUAL, c->R, pa,
+                                            c->stream); break;
+            case 2: launch_band_rows<float>(c->R, c->m, c->n, c->fAT, h.AT.lo, h.AT.w, c->r, c->Z, c->stream); break;
+            default: launch_band_cols<float>(c->Z, c->m, c->n, c->fBT, h.BT.lo, h.BT.w, c->r, EPI_PROX, nullptr,
+                                             pa, c->stream); break;
+        }
+    } else {
+        gemm_stage(c->gemm, st, pa, c->stream);
+    }
+}
+
+void enqueue_iteration(sfista_ctx *c, int k, double lam) {
+    ProxArgs pa = prox_args(c, k, lam);
+    for (int st = 0; st < 4; ++st) enqueue_stage(c, st, pa);
+}
+
+sfista_status run_loop(sfista_ctx *c, double lam, int k0, int iters) {
+    if (iters <= 0) return SFISTA_OK;
+    if (!c->opts.use_graph) {
+        for (int k = k0 + 1; k <= k0 + iters; ++k) enqueue_iteration(c, k, lam);
+        SF_CUDA(cudaGetLastError());
+        return SFISTA_OK;
+    }
+    if (!(c->gexec && c->g_k0 == k0 && c->g_iters == iters && c->g_lam == lam)) {
+        if (c->gexec) {
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        SF_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        for (int k = k0 + 1; k <= k0 + iters; ++k) enqueue_iteration(c, k, lam);
+        cudaError_t le = cudaGetLastError();
+        cudaError_t ee = cudaStreamEndCapture(c->stream, &graph);
+        if (le != cudaSuccess || ee != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail(SFISTA_ECUDA, std::string("graph capture failed: ") +
+                                          cudaGetErrorString(le != cudaSuccess ? le : ee));
+        }
+        cudaError_t ie = cudaGraphInstantiate(&c->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) {
+            c->gexec = nullptr;
+            return fail(SFISTA_ECUDA, std::string("graph instantiate failed: ") + cudaGetErrorString(ie));
+        }
+        c->g_k0 = k0;
+        c->g_iters = iters;
+        c->g_lam = lam;
+    }
+    SF_CUDA(cudaGraphLaunch(c->gexec, c->stream));
+    return SFISTA_OK;
+}
+
+// FP64 power iteration for lambda_max(A_s^T A_s) with the banded kernels.
+sfista_status power_lipschitz(sfista_ctx *c, double tol, int maxit, double *L_out) {
+    const HostSetup &h = c->hs;
+    size_t N = c->N;
+    double *v = nullptr, *u = nullptr, *w = nullptr, *Zd = nullptr, *partial = nullptr, *dot = nullptr;
+    const int nblk = 256;
+    sfista_status st = SFISTA_OK;
+    double hdot[2] = {0, 0}, mu = 0, prev = 0;
+    ProxArgs pa{};
+    cudaError_t e = cudaSuccess;
+    if ((e = cudaMalloc((void **)&v, N * 8)) || (e = cudaMalloc((void **)&u, N * 8)) ||
+        (e = cudaMalloc((void **)&w, N * 8)) || (e = cudaMalloc((void **)&Zd, N * 8 * c->r)) ||
+        (e = cudaMalloc((void **)&partial, nblk * 2 * 8)) || (e = cudaMalloc((void **)&dot, 2 * 8))) {
+        st = fail(SFISTA_ENOMEM, std::string("power iteration buffers: ") + cudaGetErrorString(e));
+        goto done;
+    }
+    launch_seed_image(v, N, c->stream);
+    launch_dots(v, v, N, partial, nblk, dot, c->stream);
+    launch_scale(v, N, dot, c->stream);
+    for (int it = 1; it <= maxit; ++it) {
+        launch_band_rows<double>(v, c->m, c->n, c->dA, h.A.lo, h.A.w, c->r, Zd, c->stream);
+        launch_band_cols<double>(Zd, c->m, c->n, c->dB, h.B.lo, h.B.w, c->r, EPI_STORE, u, pa, c->stream);
+        launch_band_rows<double>(u, c->m, c->n, c->dAT, h.AT.lo, h.AT.w, c->r, Zd, c->stream);
+        launch_band_cols<double>(Zd, c->m, c->n, c->dBT, h.BT.lo, h.BT.w, c->r, EPI_STORE, w, pa, c->stream);
+        launch_dots(v, w, N, partial, nblk, dot, c->stream);
+        launch_scale(w, N, dot, c->stream);
+        std::swap(v, w);
+        if ((e = cudaMemcpyAsync(hdot, dot, 16, cudaMemcpyDeviceToHost, c->stream)) ||
+            (e = cudaStreamSynchronize(c->stream))) {
+            st = fail(SFISTA_ECUDA, std::string("power iteration: ") + cudaGetErrorString(e));
+            goto done;
+        }
+        mu = hdot[0];
+        if (!isfinite(mu) || !(hdot[1] > 0)) {
+            st = fail(SFISTA_ENUMERIC, "power iteration produced a non-finite or zero vector");
+            goto done;
+        }
+        if (it > 1 && fabs(mu - prev) <= tol * fabs(mu)) break;
+        prev = mu;
+    }
+    *L_out = mu;
+done:
+    cudaFree(v);
+    cudaFree(u);
+    cudaFree(w);
+    cudaFree(Zd);
+    cudaFree(partial);
+    cudaFree(dot);
+    return st;
+}
+
+sfista_status check_ctx(const sfista_ctx *c) {
+    if (!c) return fail(SFISTA_EINVAL, "context is NULL");
+    return SFISTA_OK;
+}
+
+// Reads and clears the device status word (synchronises the context stream).
+sfista_status drain_status(sfista_ctx *c) {
+    unsigned s = 0;
+    SF_CUDA(cudaStreamSynchronize(c->stream));
+    SF_CUDA(cudaMemcpy(&s, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (s) SF_CUDA(cudaMemset(c->status, 0, sizeof(unsigned)));
+    if (s & DEV_TIMEOUT) return fail(SFISTA_ETIMEOUT, "a device-side wait exceeded its bound");
+    if (s & DEV_BADARG) return fail(SFISTA_EINVAL, "a kernel rejected its arguments");
+    if (s & DEV_NONFINITE) return fail(SFISTA_ENUMERIC, "non-finite value in the input or the iterates");
+    return SFISTA_OK;
+}
+
+sfista_status solve_core(sfista_ctx *c, const float *d_b, double lam, int k0, int iters,
+                         const double *X_in, const double *Xprev_in, cudaStream_t user) {
+    if (!d_b) return fail(SFISTA_EINVAL, "b is NULL");
+    if (!(lam >= 0) || !isfinite(lam)) return fail(SFISTA_EINVAL, "lambda must be finite and >= 0");
+    if (iters < 0 || k0 < 0) return fail(SFISTA_EINVAL, "iters and k0 must be >= 0");
+    sfista_status st = ensure_beta(c, k0 + iters + 1);
+    if (st) return st;
+    SF_CUDA(cudaEventRecord(c->ev_in, user));
+    SF_CUDA(cudaStreamWaitEvent(c->stream, c->ev_in, 0));
+    size_t N = c->N;
+    SF_CUDA(cudaMemcpyAsync(c->Bd, d_b, N * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    launch_check_finite(c->Bd, N, c->status, c->stream);
+    double *Xk = c->Xb[k0 & 1], *Xkm = c->Xb[(k0 + 1) & 1];
+    if (X_in) SF_CUDA(cudaMemcpyAsync(Xk, X_in, N * 8, cudaMemcpyDeviceToDevice, c->stream));
+    else SF_CUDA(cudaMemsetAsync(Xk, 0, N * 8, c->stream));
+    if (k0 > 0 && Xprev_in) SF_CUDA(cudaMemcpyAsync(Xkm, Xprev_in, N * 8, cudaMemcpyDeviceToDevice, c->stream));
+    else SF_CUDA(cudaMemcpyAsync(Xkm, Xk, N * 8, cudaMemcpyDeviceToDevice, c->stream));
+    double beta0 = k0 > 0 ? c->beta_host[k0 - 1] : 0.0;
+    void *yhi = nullptr, *ylo = nullptr;
+    int split = 0;
+    if (c->gemm) gemm_state_operands(c->gemm, &yhi, &ylo, &split);
+    init_state_kernel<<<1024, 256, 0, c->stream>>>(Xk, Xkm, c->Y, c->Yop, yhi, ylo, split, N, beta0);
+    if (c->gemm) gemm_prepare_solve(c->gemm, c->Bd, c->stream);
+    SF_CUDA(cudaGetLastError());
+    st = run_loop(c, lam, k0, iters);
+    if (st) return st;
+    SF_CUDA(cudaGetLastError());
+    return SFISTA_OK;
+}
+
+sfista_status finish_on_user(sfista_ctx *c, cudaStream_t user) {
+    SF_CUDA(cudaEventRecord(c->ev_out, c->stream));
+    SF_CUDA(cudaStreamWaitEvent(user, c->ev_out, 0));
+    return SFISTA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sfista_default_opts(sfista_opts *o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->prec = SFISTA_FP32;
+    o->op = SFISTA_OP_AUTO;
+    o->project_nonneg = 0;
+    o->use_graph = 1;
+    o->lipschitz = 0.0;
+    o->lipschitz_tol = 1e-10;
+    o->lipschitz_maxit = 1000;
+    o->device = -1;
+}
+
+sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int center_row,
+                           int center_col, int img_rows, int img_cols, int bc, int r,
+                           const sfista_opts *opts, sfista_ctx **out) {
+    if (!out) return fail(SFISTA_EINVAL, "out is NULL");
+    *out = nullptr;
+    sfista_opts o;
+    sfista_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.prec < SFISTA_FP32 || o.prec > SFISTA_BF16X3) return fail(SFISTA_EINVAL, "unknown precision");
+    if (o.op < SFISTA_OP_AUTO || o.op > SFISTA_OP_GEMM_DENSE) return fail(SFISTA_EINVAL, "unknown operator form");
+    if (!(o.lipschitz <= 0.0 || isfinite(o.lipschitz))) return fail(SFISTA_EINVAL, "lipschitz must be finite");
+    if (center_row == -1 && psf_rows > 0) center_row = (psf_rows - 1) / 2;
+    if (center_col == -1 && psf_cols > 0) center_col = (psf_cols - 1) / 2;
+    sfista_ctx *c = new (std::nothrow) sfista_ctx();
+    if (!c) return fail(SFISTA_ENOMEM, "context allocation failed");
+    sfista_status st = host_setup(psf, psf_rows, psf_cols, center_row, center_col, img_rows, img_cols,
+                                  bc, r, &c->hs);
+    if (st) {
+        delete c;
+        return st;
+    }
+    c->opts = o;
+    c->m = img_rows;
+    c->n = img_cols;
+    c->r = r;
+    c->N = (size_t)img_rows * img_cols;
+    c->prec = o.prec;
+    c->op = o.op;
+    if (c->op == SFISTA_OP_AUTO) c->op = (c->prec == SFISTA_FP32) ? SFISTA_OP_BANDED : SFISTA_OP_GEMM_BAND;
+    if (c->op == SFISTA_OP_BANDED && c->prec != SFISTA_FP32) {
+        delete c;
+        return fail(SFISTA_ENOTSUP, "the banded operator form runs in FP32 only");
+    }
+    if (o.device < 0) {
+        if (cudaGetDevice(&c->dev) != cudaSuccess) {
+            delete c;
+            return fail(SFISTA_ECUDA, "no CUDA device");
+        }
+    } else {
+        c->dev = o.device;
+    }
+    DeviceGuard g(c->dev);
+    auto bail = [&](sfista_status s) {
+        ctx_free(c);
+        return s;
+    };
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) ||
+        (e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming)) ||
+        (e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming)))
+        return bail(fail(SFISTA_ECUDA, std::string("stream/event: ") + cudaGetErrorString(e)));
+    const HostSetup &h = c->hs;
+    int wmax = std::max(std::max(h.A.w, h.AT.w), std::max(h.B.w, h.BT.w));
+    if ((e = band_set_smem_limits(wmax)))
+        return bail(fail(SFISTA_ENOTSUP, std::string("band too wide for shared memory: ") + cudaGetErrorString(e)));
+    std::vector<float> tmpf;
+    auto up_band = [&](const Band &b, double **d64, float **d32) -> cudaError_t {
+        cudaError_t ee = upload(d64, b.band.data(), b.band.size(), c->stream);
+        if (ee) return ee;
+        tmpf.assign(b.band.begin(), b.band.end());
+        ee = upload(d32, tmpf.data(), tmpf.size(), c->stream);
+        if (ee) return ee;
+        return cudaStreamSynchronize(c->stream);
+    };
+    if ((e = up_band(h.A, &c->dA, &c->fA)) || (e = up_band(h.AT, &c->dAT, &c->fAT)) ||
+        (e = up_band(h.B, &c->dB, &c->fB)) || (e = up_band(h.BT, &c->dBT, &c->fBT)))
+        return bail(fail(SFISTA_ENOMEM, std::string("factor upload: ") + cudaGetErrorString(e)));
+    size_t N = c->N;
+    if ((e = cudaMalloc((void **)&c->Bd, N * 4)) || (e = cudaMalloc((void **)&c->Yop, N * 4)) ||
+        (e = cudaMalloc((void **)&c->Z, N * 4 * r)) || (e = cudaMalloc((void **)&c->R, N * 4)) ||
+        (e = cudaMalloc((void **)&c->tmp, N * 4)) || (e = cudaMalloc((void **)&c->Xb[0], N * 8)) ||
+        (e = cudaMalloc((void **)&c->Xb[1], N * 8)) || (e = cudaMalloc((void **)&c->Y, N * 8)) ||
+        (e = cudaMalloc((void **)&c->status, 16)))
+        return bail(fail(SFISTA_ENOMEM, std::string("state buffers: ") + cudaGetErrorString(e)));
+    if ((e = cudaMemset(c->status, 0, 16))) return bail(fail(SFISTA_ECUDA, cudaGetErrorString(e)));
+    if (c->op != SFISTA_OP_BANDED) {
+        st = gemm_create(&c->gemm, h, c->prec, c->op == SFISTA_OP_GEMM_DENSE, c->Yop, c->R, c->stream);
+        if (st) return bail(st);
+    }
+    if (o.lipschitz > 0.0) {
+        c->L = o.lipschitz;
+    } else {
+        double tol = o.lipschitz_tol > 0 ? o.lipschitz_tol : 1e-10;
+        int maxit = o.lipschitz_maxit > 0 ? o.lipschitz_maxit : 1000;
+        st = power_lipschitz(c, tol, maxit, &c->L);
+        if (st) return bail(st);
+    }
+    if ((e = cudaStreamSynchronize(c->stream))) return bail(fail(SFISTA_ECUDA, cudaGetErrorString(e)));
+    *out = c;
+    return SFISTA_OK;
+}
+
+void sfista_destroy(sfista_ctx *ctx) { ctx_free(ctx); }
+
+sfista_status sfista_factorize(const double *psf, int p, int q, int cr, int cc, int m, int n, int bc, int r,
+                               double *sigma, double *C, double *D, double *approx_err) {
+    if (cr == -1 && p > 0) cr = (p - 1) / 2;
+    if (cc == -1 && q > 0) cc = (q - 1) / 2;
+    HostSetup h;
+    sfista_status st = host_setup(psf, p, q, cr, cc, m, n, bc, r, &h);
+    if (st) return st;
+    if (sigma) std::copy(h.sigma.begin(), h.sigma.end(), sigma);
+    if (C) std::copy(h.C.begin(), h.C.end(), C);
+    if (D) std::copy(h.D.begin(), h.D.end(), D);
+    if (approx_err) *approx_err = h.approx_err;
+    return SFISTA_OK;
+}
+
+sfista_status sfista_solve_device(sfista_ctx *c, const float *d_b, double lambda, int iters, float *d_x,
+                                  void *stream) {
+    sfista_status st = check_ctx(c);
+    if (st) return st;
+    if (!d_x) return fail(SFISTA_EINVAL, "x is NULL");
+    DeviceGuard g(c->dev);
+    cudaStream_t user = (cudaStream_t)stream;
+    st = solve_core(c, d_b, lambda, 0, iters, nullptr, nullptr, user);
+    if (st) return st;
+    launch_f64_to_f32(c->Xb[iters & 1], d_x, c->N, c->stream);
+    SF_CUDA(cudaGetLastError());
+    return finish_on_user(c, user);
+}
+
+sfista_status sfista_solve_state(sfista_ctx *c, const float *d_b, double lambda, int k0, int iters,
+                                 double *d_X, double *d_Xprev, void *stream) {
+    sfista_status st = check_ctx(c);
+    if (st) return st;
+    if (!d_X || !d_Xprev) return fail(SFISTA_EINVAL, "state buffers are NULL");
+    DeviceGuard g(c->dev);
+    cudaStream_t user = (cudaStream_t)stream;
+    st = solve_core(c, d_b, lambda, k0, iters, d_X, d_Xprev, user);
+    if (st) return st;
+    int ke = k0 + iters;
+    SF_CUDA(cudaMemcpyAsync(d_X, c->Xb[ke & 1], c->N * 8, cudaMemcpyDeviceToDevice, c->stream));
+    SF_CUDA(cudaMemcpyAsync(d_Xprev, c->Xb[(ke + 1) & 1], c->N * 8, cudaMemcpyDeviceToDevice, c->stream));
+    return finish_on_user(c, user);
+}
+
+sfista_status sfista_sync(sfista_ctx *c, void *stream) {
+    sfista_status st = check_ctx(c);
+    if (st) return st;
+    DeviceGuard g(c->dev);
+    SF_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return drain_status(c);
+}
+
+sfista_status sfista_solve(sfista_ctx *c, const float *b, double lambda, int iters, float *x) {
+    sfista_status st = check_ctx(c);
+    if (st) return st;
+    if (!b || !x) return fail(SFISTA_EINVAL, "b or x is NULL");
+    DeviceGuard g(c->dev);
+    for (size_t i = 0; i < c->N; ++i)
+        if (!isfinite(b[i])) return fail(SFISTA_EINVAL, "b has a non-finite entry");
+    SF_CUDA(cudaMemcpyAsync(c->tmp, b, c->N * 4, cudaMemcpyHostToDevice, c->stream));
+    st = solve_core(c, c->tmp, lambda, 0, iters, nullptr, nullptr, c->stream);
+    if (st) return st;
+    launch_f64_to_f32(c->Xb[iters & 1], c->tmp, c->N, c->stream);
+    SF_CUDA(cudaMemcpyAsync(x, c->tmp, c->N * 4, cudaMemcpyDeviceToHost, c->stream));
+    return drain_status(c);
+}
+
+sfista_status sfista_apply(sfista_ctx *c, const float *d_x, float *d_y, int transpose, void *stream) {
+    sfista_status st = check_ctx(c);
+    if (st) return st;
+    if (!d_x || !d_y) return fail(SFISTA_EINVAL, "x or y is NULL");
+    DeviceGuard g(c->dev);
+    cudaStream_t user = (cudaStream_t)stream;
+    SF_CUDA(cudaEventRecord(c->ev_in, user));
+    SF_CUDA(cudaStreamWaitEvent(c->stream, c->ev_in, 0));
+    const HostSetup &h = c->hs;
+    ProxArgs pa{};
+    if (c->op == SFISTA_OP_BANDED) {
+        const Band &F = transpose ? h.AT : h.A;
+        const Band &G = transpose ? h.BT : h.B;
+        launch_band_rows<float>(d_x, c->m, c->n, transpose ? c->fAT : c->fA, F.lo, F.w, c->r, c->Z, c->stream);
+        launch_band_cols<float>(c->Z, c->m, c->n, transpose ? c->fBT : c->fB, G.lo, G.w, c->r, EPI_STORE, d_y,
+                                pa, c->stream);
+    } else {
+        st = gemm_apply(c->gemm, d_x, d_y, transpose, c->stream);
+        if (st) return st;
+    }
+    SF_CUDA(cudaGetLastError());
+    return finish_on_user(c, user);
+}
+
+sfista_status sfista_info(const sfista_ctx *c, double *lipschitz, double *sigma, double *approx_err,
+                          int *config) {
+    sfista_status st = check_ctx(c);
+    if (st) return st;
+    if (lipschitz) *lipschitz = c->L;
+    if (sigma) std::copy(c->hs.sigma.begin(), c->hs.sigma.end(), sigma);
+    if (approx_err) *approx_err = c->hs.approx_err;
+    if (config) {
+        config[0] = c->prec;
+        config[1] = c->op;
+        config[2] = c->hs.A.w;
+        config[3] = c->hs.B.w;
+    }
+    return SFISTA_OK;
+}
+
+sfista_status sfista_get_profiles(const sfista_ctx *c, double *C, double *D) {
+    sfista_status st = check_ctx(c);
+    if (st) return st;
+    if (C) std::copy(c->hs.C.begin(), c->hs.C.end(), C);
+    if (D) std::copy(c->hs.D.begin(), c->hs.D.end(), D);
+    return SFISTA_OK;
+}
+
+sfista_status sfista_get_factors(const sfista_ctx *c, double *A, double *B) {
+    sfista_status st = check_ctx(c);
+    if (st) return st;
+    auto dense = [](const Band &b, double *out) {
+        size_t len = b.len;
+        std::fill(out, out + (size_t)b.r * len * len, 0.0);
+        for (int i = 0; i < b.r; ++i)
+            for (int k = 0; k < b.w; ++k)
+                for (size_t row = 0; row < len; ++row) {
+                    long col = (long)row + b.lo + k;
+                    if (col >= 0 && col < (long)len)
+                        out[((size_t)i * len + row) * len + col] = b.band[((size_t)i * b.w + k) * len + row];
+                }
+    };
+    if (A) dense(c->hs.A, A);
+    if (B) dense(c->hs.B, B);
+    return SFISTA_OK;
+}
+
+sfista_status sfista_blur(const double *psf, int p, int q, int cr, int cc, int bc, const float *d_x, int m,
+                          int n, float *d_y, void *stream) {
+    if (!psf || !d_x || !d_y) return fail(SFISTA_EINVAL, "NULL pointer");
+    if (p < 1 || q < 1 || m < 1 || n < 1 || p > m || q > n) return fail(SFISTA_EINVAL, "bad sizes");
+    if (bc == SFISTA_BC_PERIODIC) return fail(SFISTA_ENOTSUP, "periodic boundary is not supported");
+    if (bc != SFISTA_BC_ZERO && bc != SFISTA_BC_REFLEXIVE) return fail(SFISTA_EINVAL, "unknown boundary");
+    if (cr == -1) cr = (p - 1) / 2;
+    if (cc == -1) cc = (q - 1) / 2;
+    if (cr < 0 || cr >= p || cc < 0 || cc >= q) return fail(SFISTA_EINVAL, "PSF centre outside the PSF");
+    std::vector<float> pf((size_t)p * q);
+    for (size_t i = 0; i < pf.size(); ++i) {
+        if (!isfinite(psf[i])) return fail(SFISTA_EINVAL, "PSF has a non-finite entry");
+        pf[i] = (float)psf[i];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    float *dP = nullptr;
+    SF_CUDA(cudaMalloc((void **)&dP, pf.size() * 4));
+    cudaError_t e = cudaMemcpyAsync(dP, pf.data(), pf.size() * 4, cudaMemcpyHostToDevice, s);
+    if (!e) {
+        launch_blur_exact(d_x, m, n, dP, p, q, cr, cc, bc, d_y, s);
+        e = cudaGetLastError();
+    }
+    if (!e) e = cudaStreamSynchronize(s);
+    cudaFree(dP);
+    if (e) return fail(SFISTA_ECUDA, std::string("blur: ") + cudaGetErrorString(e));
+    return SFISTA_OK;
+}
+
+sfista_status sfista_time_stages(sfista_ctx *c, const float *d_b, double lambda, int reps, float *ms) {
+    sfista_status st = check_ctx(c);
+    if (st) return st;
+    if (!ms || reps < 1) return fail(SFISTA_EINVAL, "ms is NULL or reps < 1");
+    DeviceGuard g(c->dev);
+    st = solve_core(c, d_b, lambda, 0, 0, nullptr, nullptr, c->stream);
+    if (st) return st;
+    cudaEvent_t ev[5];
+    for (int i = 0; i < 5; ++i) SF_CUDA(cudaEventCreate(&ev[i]));
+    double acc[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaSuccess;
+    for (int k = 1; k <= reps && !e; ++k) {
+        ProxArgs pa = prox_args(c, k, lambda);
+        e = cudaEventRecord(ev[0], c->stream);
+        for (int s4 = 0; s4 < 4 && !e; ++s4) {
+            enqueue_stage(c, s4, pa);
+            e = cudaEventRecord(ev[s4 + 1], c->stream);
+        }
+        if (!e) e = cudaEventSynchronize(ev[4]);
+        for (int s4 = 0; s4 < 4 && !e; ++s4) {
+            float t = 0;
+            e = cudaEventElapsedTime(&t, ev[s4], ev[s4 + 1]);
+            acc[s4] += t;
+        }
+    }
+    for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
+    if (e) return fail(SFISTA_ECUDA, std::string("stage timing: ") + cudaGetErrorString(e));
+    for (int s4 = 0; s4 < 4; ++s4) ms[s4] = (float)(acc[s4] / reps);
+    return drain_status(c);
+}
+
+const char *sfista_strerror(sfista_status s) {
+    switch (s) {
+        case SFISTA_OK: return "ok";
+        case SFISTA_EINVAL: return "invalid argument";
+        case SFISTA_ENOMEM: return "out of memory";
+        case SFISTA_ECUDA: return "CUDA error";
+        case SFISTA_ENOTSUP: return "not supported";
+        case SFISTA_ENUMERIC: return "non-finite value";
+        case SFISTA_ETIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+const char *sfista_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,28 @@
+// Tensor-core (tcgen05 / TMEM / TMA) execution of the Kronecker operator as
+// four GEMMs per iteration with fused epilogues.  Library-internal.
+#pragma once
+
+#include "internal.h"
+
+namespace sfista {
+
+struct GemmPath;
+
+// Builds operand panels and intermediates for precision `prec` from the
+// host setup.  dense = true uses the full K range, otherwise K tiles outside
+// the factor band are skipped.  Yop / R are the FP32 state buffers of the
+// context (used by the FP32 SIMT GEMM variant).
+sfista_status gemm_create(GemmPath **out, const HostSetup &h, int prec, bool dense, float *Yop,
+                          float *R, cudaStream_t s);
+void gemm_destroy(GemmPath *g);
+// Split-operand copies of Y that the prox epilogue must write.
+void gemm_state_operands(GemmPath *g, void **yhi, void **ylo, int *split_kind);
+// Called once per solve after B has been copied in (binds its pointer).
+void gemm_prepare_solve(GemmPath *g, const float *Bd, cudaStream_t s);
+// Stage st (0..3) of one iteration of Alg. 2: the four GEMMs with the
+// residual (stage 1) and prox / momentum (stage 3) epilogues.
+void gemm_stage(GemmPath *g, int st, const ProxArgs &pa, cudaStream_t s);
+// The operator alone (transpose = 0: A_s, 1: A_s^T) on FP32 device buffers.
+sfista_status gemm_apply(GemmPath *g, const float *x, float *y, int transpose, cudaStream_t s);
+
+}  // namespace sfista

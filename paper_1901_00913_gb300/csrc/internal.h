@@ -1,0 +1,110 @@
+// Library-internal declarations shared by the host setup, the kernels and the
+// C ABI of libsfista.  Nothing here is part of the public interface.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sfista.h"
+
+namespace sfista {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string &msg);
+sfista_status fail(sfista_status s, const std::string &msg);
+#define SF_CUDA(call)                                                          \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess)                                                 \
+            return ::sfista::fail(SFISTA_ECUDA, std::string(#call) + ": " +    \
+                                                    cudaGetErrorString(e_));   \
+    } while (0)
+
+// Device status word bits (OR-reduced by kernels, read by sfista_sync).
+enum : unsigned {
+    DEV_NONFINITE = 1u,
+    DEV_TIMEOUT = 2u,
+    DEV_BADARG = 4u,
+};
+
+// ------------------------------------------------------------------ host setup (FP64)
+// Band storage of one family of r banded n x n factors F_i:
+//   F_i[row][row + lo + k] = band[(i * w + k) * len + row],  k in [0, w)
+// (transposed so that consecutive rows are contiguous).  Entries whose column
+// falls outside [0, len) are stored as zero.
+struct Band {
+    int len = 0, r = 0, lo = 0, w = 0;
+    std::vector<double> band;   // r * w * len
+};
+
+struct HostSetup {
+    int m = 0, n = 0, p = 0, q = 0, cr = 0, cc = 0, bc = 0, r = 0;
+    std::vector<double> sigma;  // min(p, q) singular values of P_bar
+    double approx_err = 0.0;    // sqrt(sum_{k > r} sigma_k^2)
+    std::vector<double> C;      // r x p column profiles (left factors B_k)
+    std::vector<double> D;      // r x q row profiles (right factors A_k)
+    Band A, AT, B, BT;          // right factor, its transpose, left factor, its transpose
+};
+
+// Sec. 2 / Theorem 1 in FP64; returns SFISTA_OK or an error (message set).
+sfista_status host_setup(const double *psf, int p, int q, int cr, int cc, int m,
+                         int n, int bc, int r, HostSetup *out);
+
+// beta_k = (t_k - 1) / t_{k+1} for k = 1..iters (index k-1), t_1 = 1 (Alg. 2, Step 2).
+void momentum_table(int k_end, std::vector<double> *beta);
+
+// ------------------------------------------------------------------ device kernels
+// Banded operator passes (compact band storage), T = float or double.
+// rows:  Z[i][a][c] = sum_k In[a][c + lo + k] * Fb[i][k][c]        (i < r)
+// cols:  acc[a][c]  = sum_i sum_k Gb[i][k][a] * Z[i][a + lo + k][c]
+enum EpiKind : int { EPI_STORE = 0, EPI_RESIDUAL = 1, EPI_PROX = 2 };
+
+struct ProxArgs {
+    const float *Bd;     // EPI_RESIDUAL: observed image
+    const double *Xin;   // EPI_PROX: X_{k-1} (FP64)
+    double *Xout;        // EPI_PROX: X_k (FP64; a different buffer, ping-pong)
+    double *Y;           // EPI_PROX: Y_k in, Y_{k+1} out (FP64, in place)
+    float *Yop;          // EPI_PROX: FP32 copy of Y_{k+1} (operand of the next GEMM/pass)
+    void *Yhi, *Ylo;     // EPI_PROX: optional split copies (bf16 or tf32-in-fp32), may be NULL
+    int split_kind;      // 0 none, 1 bf16 hi/lo, 2 tf32 hi/lo (fp32 storage)
+    const double *beta;  // momentum table, beta[k-1] for iteration k
+    int k;               // iteration index (1-based)
+    double L, lam2;      // Lipschitz constant and lambda^2
+    int project;         // max(X, 0) after the shrink
+    unsigned *status;    // device status word
+};
+
+template <typename T>
+void launch_band_rows(const T *In, int m, int n, const T *Fb, int lo, int w, int r, T *Z,
+                      cudaStream_t s);
+template <typename T>
+void launch_band_cols(const T *Z, int m, int n, const T *Gb, int lo, int w, int r,
+                      EpiKind epi, T *Out, const ProxArgs &pa, cudaStream_t s);
+
+size_t band_rows_smem(int w, size_t elem);
+size_t band_cols_smem(int w, size_t elem);
+cudaError_t band_set_smem_limits(int w);
+
+// Small helpers.
+void launch_fill_f64(double *p, size_t count, double v, cudaStream_t s);
+void launch_f64_to_f32(const double *in, float *out, size_t count, cudaStream_t s);
+void launch_f32_to_f64(const float *in, double *out, size_t count, cudaStream_t s);
+void launch_split(const float *in, void *hi, void *lo, size_t count, int kind,
+                  cudaStream_t s);
+void launch_check_finite(const float *in, size_t count, unsigned *status, cudaStream_t s);
+void launch_seed_image(double *v, size_t count, cudaStream_t s);
+// dot[0] = <u, v>, dot[1] = <v, v>  (FP64, deterministic two-pass reduction)
+void launch_dots(const double *u, const double *v, size_t count, double *partial,
+                 int nblk, double *dot, cudaStream_t s);
+void launch_scale(double *v, size_t count, const double *dot, cudaStream_t s);
+void launch_blur_exact(const float *X, int m, int n, const float *P, int p, int q,
+                       int cr, int cc, int bc, float *Y, cudaStream_t s);
+// Dense factor panels from band storage: F[i][row][col] for col in [0, cols).
+// kind: 0 fp32, 1 bf16 hi/lo, 2 tf32 hi/lo (fp32 storage), 3 fp64.
+void launch_densify(const double *band, int r, int len, int lo, int w, int cols,
+                    int kind, void *hi, void *lo_out, size_t ld, cudaStream_t s);
+
+}  // namespace sfista

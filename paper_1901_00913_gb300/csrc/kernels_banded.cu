@@ -1,0 +1,373 @@
+// Banded Kronecker operator on the CUDA cores, plus the fused FISTA epilogue.
+//
+// The factors of Sec. 2 are banded (Toeplitz, plus Hankel corners for the
+// reflective boundary), so each product of Alg. 2, Step 1 is a 1-D banded
+// matrix applied along one image axis:
+//   rows pass:  Z_i[a][c] = sum_k In[a][c + lo + k] * F_i[c][c + lo + k]
+//               (In A_i^T with F = A, or In A_i with F = A^T)
+//   cols pass:  Out[a][c] = sum_i sum_k G_i[a][a + lo + k] * Z_i[a + lo + k][c]
+//               (B_i Z_i with G = B, or B_i^T Z_i with G = B^T)
+// Band entries come from compact storage band[(i*w + k)*len + row], so the
+// zero and reflective boundaries (and any PSF centre) run the same code.
+// The cols pass ends in the fused epilogue: the residual B_s(Y) - B of the
+// forward product, or Step 1's shrink + optional projection + Step 3's
+// momentum for the adjoint, with the FISTA state in FP64.
+#include <cuda_bf16.h>
+
+#include "internal.h"
+
+namespace sfista {
+
+namespace {
+
+constexpr int RT_C = 64;    // rows pass: output columns per block
+constexpr int RT_A = 16;    // rows pass: output rows per block
+constexpr int CT_C = 64;    // cols pass: output columns per block
+constexpr int CT_A = 32;    // cols pass: output rows per block
+constexpr int NTHR = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(NTHR) band_rows_kernel(const T *__restrict__ In, int m, int n,
+                                                         const T *__restrict__ Fb, int lo, int w,
+                                                         int r, T *__restrict__ Z) {
+    extern __shared__ unsigned char smem_raw[];
+    T *Ins = reinterpret_cast<T *>(smem_raw);        // RT_A x (RT_C + w - 1)
+    const int span = RT_C + w - 1;
+    T *Fs = Ins + RT_A * span;                        // w x RT_C
+    const int c0 = blockIdx.x * RT_C, a0 = blockIdx.y * RT_A;
+    const int tid = threadIdx.x, tc = tid % RT_C, tg = tid / RT_C;   // tg in [0, 4)
+    for (int idx = tid; idx < RT_A * span; idx += NTHR) {
+        int row = idx / span, col = idx - row * span;
+        int ga = a0 + row, gc = c0 + lo + col;
+        Ins[idx] = (ga < m && gc >= 0 && gc < n) ? In[(size_t)ga * n + gc] : T(0);
+    }
+    for (int i = 0; i < r; ++i) {
+        __syncthreads();
+        for (int idx = tid; idx < w * RT_C; idx += NTHR) {
+            int k = idx / RT_C, cc = idx - k * RT_C;
+            int gc = c0 + cc;
+            Fs[idx] = (gc < n) ? Fb[((size_t)i * w + k) * n + gc] : T(0);
+        }
+        __syncthreads();
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+        const T *x0 = Ins + (tg * 4) * span + tc;
+        for (int k = 0; k < w; ++k) {
+            T f = Fs[k * RT_C + tc];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[j] = fma(x0[j * span + k], f, acc[j]);
+        }
+        int gc = c0 + tc;
+        if (gc < n) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                int ga = a0 + tg * 4 + j;
+                if (ga < m) Z[((size_t)i * m + ga) * n + gc] = acc[j];
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ float tf32_round(float x) {
+    unsigned u;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+    return __uint_as_float(u);
+}
+
+// Step 1 shrink (+ projection) and Step 3 momentum for one pixel, FP64 state.
+__device__ __forceinline__ void prox_momentum(const ProxArgs &pa, size_t idx, double g) {
+    double y = pa.Y[idx];
+    double xprev = pa.Xin[idx];
+    double x = (pa.L * y - g) / (pa.L + pa.lam2);
+    if (pa.project && x < 0.0) x = 0.0;
+    if (!isfinite(x)) atomicOr(pa.status, DEV_NONFINITE);
+    double beta = pa.beta[pa.k - 1];
+    double yn = x + beta * (x - xprev);
+    pa.Xout[idx] = x;
+    pa.Y[idx] = yn;
+    if (pa.Yop) pa.Yop[idx] = (float)yn;
+    if (pa.split_kind == 1) {
+        __nv_bfloat16 hi = __double2bfloat16(yn);
+        __nv_bfloat16 lo = __double2bfloat16(yn - (double)__bfloat162float(hi));
+        reinterpret_cast<__nv_bfloat16 *>(pa.Yhi)[idx] = hi;
+        reinterpret_cast<__nv_bfloat16 *>(pa.Ylo)[idx] = lo;
+    } else if (pa.split_kind == 2) {
+        float hi = tf32_round((float)yn);
+        float lo = tf32_round((float)(yn - (double)hi));
+        reinterpret_cast<float *>(pa.Yhi)[idx] = hi;
+        reinterpret_cast<float *>(pa.Ylo)[idx] = lo;
+    }
+}
+
+template <typename T, int EPI>
+__global__ void __launch_bounds__(NTHR) band_cols_kernel(const T *__restrict__ Z, int m, int n,
+                                                         const T *__restrict__ Gb, int lo, int w,
+                                                         int r, T *__restrict__ Out, ProxArgs pa) {
+    extern __shared__ unsigned char smem_raw[];
+    T *Zs = reinterpret_cast<T *>(smem_raw);   // (CT_A + w - 1) x CT_C
+    const int span = CT_A + w - 1;
+    T *Gs = Zs + span * CT_C;                   // w x CT_A
+    const int c0 = blockIdx.x * CT_C, a0 = blockIdx.y * CT_A;
+    const int tid = threadIdx.x, tc = tid % CT_C, tg = tid / CT_C;   // rows tg*8 .. tg*8+7
+    T acc[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j] = T(0);
+    for (int i = 0; i < r; ++i) {
+        __syncthreads();
+        for (int idx = tid; idx < span * CT_C; idx += NTHR) {
+            int row = idx / CT_C, col = idx - row * CT_C;
+            int ge = a0 + lo + row, gc = c0 + col;
+            Zs[idx] = (ge >= 0 && ge < m && gc < n) ? Z[((size_t)i * m + ge) * n + gc] : T(0);
+        }
+        for (int idx = tid; idx < w * CT_A; idx += NTHR) {
+            int k = idx / CT_A, ra = idx - k * CT_A;
+            int ga = a0 + ra;
+            Gs[idx] = (ga < m) ? Gb[((size_t)i * w + k) * m + ga] : T(0);
+        }
+        __syncthreads();
+        const T *z0 = Zs + (tg * 8) * CT_C + tc;
+        const T *g0 = Gs + tg * 8;
+        for (int k = 0; k < w; ++k) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[j] = fma(g0[k * CT_A + j], z0[(j + k) * CT_C], acc[j]);
+        }
+    }
+    const int gc = c0 + tc;
+    if (gc >= n) return;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        int ga = a0 + tg * 8 + j;
+        if (ga >= m) break;
+        size_t idx = (size_t)ga * n + gc;
+        if (EPI == EPI_STORE) {
+            Out[idx] = acc[j];
+        } else if (EPI == EPI_RESIDUAL) {
+            Out[idx] = acc[j] - (T)pa.Bd[idx];
+        } else {
+            prox_momentum(pa, idx, (double)acc[j]);
+        }
+    }
+}
+
+}  // namespace
+
+template <typename T>
+void launch_band_rows(const T *In, int m, int n, const T *Fb, int lo, int w, int r, T *Z,
+                      cudaStream_t s) {
+    dim3 grid((n + RT_C - 1) / RT_C, (m + RT_A - 1) / RT_A);
+    size_t sm = sizeof(T) * ((size_t)RT_A * (RT_C + w - 1) + (size_t)w * RT_C);
+    band_rows_kernel<T><<<grid, NTHR, sm, s>>>(In, m, n, Fb, lo, w, r, Z);
+}
+
+template <typename T>
+void launch_band_cols(const T *Z, int m, int n, const T *Gb, int lo, int w, int r, EpiKind epi,
+                      T *Out, const ProxArgs &pa, cudaStream_t s) {
+    dim3 grid((n + CT_C - 1) / CT_C, (m + CT_A - 1) / CT_A);
+    size_t sm = sizeof(T) * ((size_t)(CT_A + w - 1) * CT_C + (size_t)w * CT_A);
+    if (epi == EPI_STORE)
+        band_cols_kernel<T, EPI_STORE><<<grid, NTHR, sm, s>>>(Z, m, n, Gb, lo, w, r, Out, pa);
+    else if (epi == EPI_RESIDUAL)
+        band_cols_kernel<T, EPI_RESIDUAL><<<grid, NTHR, sm, s>>>(Z, m, n, Gb, lo, w, r, Out, pa);
+    else
+        band_cols_kernel<T, EPI_PROX><<<grid, NTHR, sm, s>>>(Z, m, n, Gb, lo, w, r, Out, pa);
+}
+
+size_t band_rows_smem(int w, size_t elem) { return elem * ((size_t)RT_A * (RT_C + w - 1) + (size_t)w * RT_C); }
+size_t band_cols_smem(int w, size_t elem) { return elem * ((size_t)(CT_A + w - 1) * CT_C + (size_t)w * CT_A); }
+
+cudaError_t band_set_smem_limits(int w) {
+    cudaError_t e;
+    int f = (int)band_rows_smem(w, 8), g = (int)band_cols_smem(w, 8);
+    if ((e = cudaFuncSetAttribute(band_rows_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, f))) return e;
+    if ((e = cudaFuncSetAttribute(band_rows_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, f))) return e;
+    if ((e = cudaFuncSetAttribute(band_cols_kernel<float, EPI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, g))) return e;
+    if ((e = cudaFuncSetAttribute(band_cols_kernel<float, EPI_RESIDUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, g))) return e;
+    if ((e = cudaFuncSetAttribute(band_cols_kernel<float, EPI_PROX>, cudaFuncAttributeMaxDynamicSharedMemorySize, g))) return e;
+    if ((e = cudaFuncSetAttribute(band_cols_kernel<double, EPI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, g))) return e;
+    return cudaSuccess;
+}
+
+template void launch_band_rows<float>(const float *, int, int, const float *, int, int, int, float *, cudaStream_t);
+template void launch_band_rows<double>(const double *, int, int, const double *, int, int, int, double *, cudaStream_t);
+template void launch_band_cols<float>(const float *, int, int, const float *, int, int, int, EpiKind, float *, const ProxArgs &, cudaStream_t);
+template void launch_band_cols<double>(const double *, int, int, const double *, int, int, int, EpiKind, double *, const ProxArgs &, cudaStream_t);
+
+// ------------------------------------------------------------------ helpers
+namespace {
+
+__global__ void fill_f64_kernel(double *p, size_t count, double v) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+__global__ void f64_to_f32_kernel(const double *in, float *out, size_t count) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+__global__ void f32_to_f64_kernel(const float *in, double *out, size_t count) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = (double)in[i];
+}
+__global__ void check_finite_kernel(const float *in, size_t count, unsigned *status) {
+    bool bad = false;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        bad |= !isfinite(in[i]);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, DEV_NONFINITE);
+}
+// Deterministic positive start vector for the power iteration: a 64-bit
+// integer hash of the pixel index mapped to [0.5, 1.5).
+__global__ void seed_image_kernel(double *v, size_t count) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        unsigned long long z = (unsigned long long)i + 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        v[i] = 0.5 + (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    }
+}
+// partial[b*2 + {0,1}] = block sums of u.v and v.v; fixed grid => deterministic.
+__global__ void dots_kernel(const double *u, const double *v, size_t count, double *partial) {
+    __shared__ double s0[256], s1[256];
+    double a = 0, b = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        a += u[i] * v[i];
+        b += v[i] * v[i];
+    }
+    s0[threadIdx.x] = a;
+    s1[threadIdx.x] = b;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            s0[threadIdx.x] += s0[threadIdx.x + h];
+            s1[threadIdx.x] += s1[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = s0[0];
+        partial[2 * blockIdx.x + 1] = s1[0];
+    }
+}
+__global__ void dots_final_kernel(const double *partial, int nblk, double *dot) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double a = 0, b = 0;
+        for (int i = 0; i < nblk; ++i) {
+            a += partial[2 * i];
+            b += partial[2 * i + 1];
+        }
+        dot[0] = a;
+        dot[1] = b;
+    }
+}
+// v *= 1 / sqrt(dot[1])
+__global__ void scale_kernel(double *v, size_t count, const double *dot) {
+    double s = 1.0 / sqrt(dot[1]);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        v[i] *= s;
+}
+__device__ __forceinline__ int ext_index_dev(int t, int len, int bc) {
+    if (t >= 0 && t < len) return t;
+    if (bc == 0) return -1;
+    t = (t < 0) ? -1 - t : 2 * len - 1 - t;
+    return (t >= 0 && t < len) ? t : -1;
+}
+// Exact blur of Eq. (1.1), one output pixel per thread, FP64 accumulation.
+__global__ void blur_exact_kernel(const float *X, int m, int n, const float *P, int p, int q,
+                                  int cr, int cc, int bc, float *Y) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x, a = blockIdx.y;
+    if (b >= n || a >= m) return;
+    double s = 0.0;
+    for (int i = 0; i < p; ++i) {
+        int ra = ext_index_dev(a - i + cr, m, bc);
+        if (ra < 0) continue;
+        const float *xr = X + (size_t)ra * n;
+        for (int j = 0; j < q; ++j) {
+            int cb = ext_index_dev(b - j + cc, n, bc);
+            if (cb >= 0) s += (double)P[i * q + j] * (double)xr[cb];
+        }
+    }
+    Y[(size_t)a * n + b] = (float)s;
+}
+// Dense factor panel F[i][row][col] (row < len, col < cols, leading dim ld)
+// from band storage, in the operand format `kind`.
+__global__ void densify_kernel(const double *band, int r, int len, int lo, int w, int cols, int kind,
+                               void *hi, void *lo_out, size_t ld) {
+    size_t total = (size_t)r * len * ld;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        size_t col = t % ld, rest = t / ld;
+        int row = (int)(rest % len), i = (int)(rest / len);
+        long k = (long)col - row - lo;
+        double v = 0.0;
+        if ((int)col < cols && k >= 0 && k < w) v = band[((size_t)i * w + k) * len + row];
+        if (kind == 0) {
+            reinterpret_cast<float *>(hi)[t] = (float)v;
+        } else if (kind == 1) {
+            __nv_bfloat16 h = __double2bfloat16(v);
+            reinterpret_cast<__nv_bfloat16 *>(hi)[t] = h;
+            if (lo_out) reinterpret_cast<__nv_bfloat16 *>(lo_out)[t] = __double2bfloat16(v - (double)__bfloat162float(h));
+        } else if (kind == 2) {
+            float h = tf32_round((float)v);
+            reinterpret_cast<float *>(hi)[t] = h;
+            if (lo_out) reinterpret_cast<float *>(lo_out)[t] = tf32_round((float)(v - (double)h));
+        } else {
+            reinterpret_cast<double *>(hi)[t] = v;
+        }
+    }
+}
+__global__ void split_kernel(const float *in, void *hi, void *lo, size_t count, int kind) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        float v = in[i];
+        if (kind == 1) {
+            __nv_bfloat16 h = __float2bfloat16_rn(v);
+            reinterpret_cast<__nv_bfloat16 *>(hi)[i] = h;
+            reinterpret_cast<__nv_bfloat16 *>(lo)[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+        } else {
+            float h = tf32_round(v);
+            reinterpret_cast<float *>(hi)[i] = h;
+            reinterpret_cast<float *>(lo)[i] = tf32_round(v - h);
+        }
+    }
+}
+
+int grid_for(size_t count) {
+    size_t g = (count + 255) / 256;
+    return (int)(g < 4096 ? (g ? g : 1) : 4096);
+}
+
+}  // namespace
+
+void launch_fill_f64(double *p, size_t count, double v, cudaStream_t s) {
+    fill_f64_kernel<<<grid_for(count), 256, 0, s>>>(p, count, v);
+}
+void launch_f64_to_f32(const double *in, float *out, size_t count, cudaStream_t s) {
+    f64_to_f32_kernel<<<grid_for(count), 256, 0, s>>>(in, out, count);
+}
+void launch_f32_to_f64(const float *in, double *out, size_t count, cudaStream_t s) {
+    f32_to_f64_kernel<<<grid_for(count), 256, 0, s>>>(in, out, count);
+}
+void launch_check_finite(const float *in, size_t count, unsigned *status, cudaStream_t s) {
+    check_finite_kernel<<<grid_for(count), 256, 0, s>>>(in, count, status);
+}
+void launch_seed_image(double *v, size_t count, cudaStream_t s) {
+    seed_image_kernel<<<grid_for(count), 256, 0, s>>>(v, count);
+}
+void launch_dots(const double *u, const double *v, size_t count, double *partial, int nblk, double *dot,
+                 cudaStream_t s) {
+    dots_kernel<<<nblk, 256, 0, s>>>(u, v, count, partial);
+    dots_final_kernel<<<1, 32, 0, s>>>(partial, nblk, dot);
+}
+void launch_scale(double *v, size_t count, const double *dot, cudaStream_t s) {
+    scale_kernel<<<grid_for(count), 256, 0, s>>>(v, count, dot);
+}
+void launch_blur_exact(const float *X, int m, int n, const float *P, int p, int q, int cr, int cc, int bc,
+                       float *Y, cudaStream_t s) {
+    dim3 grid((n + 127) / 128, m);
+    blur_exact_kernel<<<grid, 128, 0, s>>>(X, m, n, P, p, q, cr, cc, bc, Y);
+}
+void launch_densify(const double *band, int r, int len, int lo, int w, int cols, int kind, void *hi,
+                    void *lo_out, size_t ld, cudaStream_t s) {
+    densify_kernel<<<grid_for((size_t)r * len * ld), 256, 0, s>>>(band, r, len, lo, w, cols, kind, hi, lo_out, ld);
+}
+void launch_split(const float *in, void *hi, void *lo, size_t count, int kind, cudaStream_t s) {
+    split_kernel<<<grid_for(count), 256, 0, s>>>(in, hi, lo, count, kind);
+}
+
+}  // namespace sfista

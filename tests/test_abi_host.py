@@ -1,0 +1,109 @@
+"""C-ABI library: loads, exports what include/sfista.h declares, host setup
+matches the oracle, argument errors come back as status codes (no GPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import kron
+from paper_1901_00913_gb300 import api, build, workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return api.load()
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(sfista_\w+)\s*\(", src))
+    return sorted(names)
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("case", [((15, 15), (7, 7), (64, 60), 3),
+                                  ((9, 13), (2, 9), (40, 33), 4),
+                                  ((31, 31), (15, 15), (128, 128), 5)])
+def test_factorize_matches_oracle(lib, bc, case):
+    """The library's own FP64 Jacobi SVD / Cholesky / Gram setup == the oracle's (Theorem 1)."""
+    (p, q), (cr, cc), (m, n), r = case
+    g = W.rng(p * 100 + q + bc)
+    P = W.rotated_gaussian_psf(max(p, q), 3.0, 1.2, 0.6)[:p, :q] + 0.05 * g.uniform(size=(p, q))
+    sig, C, D, err = api.sfista_factorize(P, m, n, bc, r, center=(cr, cc))
+    ka = kron.kron_approx(P, cr, cc, m, n, bc, r)
+    np.testing.assert_allclose(sig, ka.sigma, rtol=0, atol=1e-13 * ka.sigma[0])
+    assert abs(err - ka.approx_err) <= 1e-12 * ka.sigma[0]
+    for k in range(r):
+        np.testing.assert_allclose(np.outer(C[k], D[k]), np.outer(ka.C[k], ka.D[k]), rtol=0,
+                                   atol=1e-12 * np.abs(np.outer(ka.C[0], ka.D[0])).max())
+
+
+def test_factorize_sign_rule(lib):
+    """Largest-|u| entry positive: with distinct singular values the profiles themselves agree."""
+    P = W.rotated_gaussian_psf(15, 3.0, 1.0, np.deg2rad(30))
+    sig, C, D, err = api.sfista_factorize(P, 64, 64, 1, 3)
+    ka = kron.kron_approx(P, 7, 7, 64, 64, 1, 3)
+    np.testing.assert_allclose(C, ka.C, atol=1e-12)
+    np.testing.assert_allclose(D, ka.D, atol=1e-12)
+
+
+@pytest.mark.parametrize("args,status", [
+    (dict(m=10, n=10, bc=1, r=3), api.EINVAL),        # PSF larger than the image
+    (dict(m=64, n=64, bc=2, r=3), api.ENOTSUP),       # periodic boundary
+    (dict(m=64, n=64, bc=7, r=3), api.EINVAL),        # unknown boundary
+    (dict(m=64, n=64, bc=1, r=0), api.EINVAL),        # rank too small
+    (dict(m=64, n=64, bc=1, r=16), api.EINVAL),       # rank > min(p, q)
+    (dict(m=64, n=64, bc=1, r=3, center=(15, 0)), api.EINVAL),   # centre outside
+])
+def test_argument_errors(lib, args, status):
+    P = W.gaussian_psf(15, 2.0)
+    with pytest.raises(api.SfistaError) as ei:
+        api.sfista_factorize(P, args["m"], args["n"], args["bc"], args["r"], center=args.get("center", (-1, -1)))
+    assert ei.value.status == status
+    o = api.default_opts()
+    with pytest.raises(api.SfistaError) as ei:
+        api.sfista_setup(P, args["m"], args["n"], args["bc"], args["r"], args.get("center", (-1, -1)), o)
+    assert ei.value.status == status
+
+
+def test_nonfinite_psf_rejected(lib):
+    P = W.gaussian_psf(9, 2.0)
+    P[3, 4] = np.nan
+    with pytest.raises(api.SfistaError) as ei:
+        api.sfista_factorize(P, 32, 32, 0, 1)
+    assert ei.value.status == api.EINVAL
+
+
+def test_tied_singular_values_rejected(lib):
+    """A PSF whose weighted singular values tie at the truncation point has no unique rank-r sum."""
+    P = np.zeros((5, 5))
+    P[1, 1] = P[3, 3] = 1.0       # two equal separable bumps -> sigma_1 == sigma_2 (zero BC weights equal)
+    P[1, 3] = P[3, 1] = 0.0
+    sig, C, D, err = api.sfista_factorize(P, 32, 32, 0, 2, center=(2, 2))
+    assert err < 1e-14
+    with pytest.raises(api.SfistaError) as ei:
+        api.sfista_factorize(P, 32, 32, 0, 1, center=(2, 2))
+    assert ei.value.status == api.EINVAL
+
+
+def test_default_opts(lib):
+    o = api.default_opts()
+    assert o.prec == 0 and o.op == 0 and o.use_graph == 1 and o.device == -1
+    assert o.lipschitz == 0.0 and o.lipschitz_maxit > 0

@@ -1,0 +1,253 @@
+"""GPU path vs the FP64 oracle, through the C ABI (needs a GB300).
+
+Inputs are seeded and synthetic; the oracle computes its own factorisation,
+operator and iterations in FP64, and both sides take the same FP32 b and the
+same L (an input of Alg. 2, computed by the oracle).  Tolerances are relative
+Frobenius errors: 1e-5 for the FP32 operator, 1e-4 (and 0.01 dB PSNR) for the
+split-precision tensor-core operators.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import kron
+from paper_1901_00913_gb300 import api, workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "tf32x3": 1e-4, "bf16x3": 1e-4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+    assert torch.cuda.is_available()
+
+
+def _problem(m, n, psf, bc, seed, noise=0.01, centre=None):
+    g = W.rng(seed)
+    x = W.shapes_image(g, m, n, rects=6, ellipses=6)
+    cr, cc = centre if centre else ((psf.shape[0] - 1) // 2, (psf.shape[1] - 1) // 2)
+    bx = oracle.blur(x, psf, cr, cc, bc)
+    b = (bx + W.noise_scale(bx, g.standard_normal((m, n)), noise)).astype(np.float32)
+    return x, b, (cr, cc)
+
+
+def _oracle_L(ka, maxit=300):
+    L, _ = oracle.lipschitz(ka, np.ones((ka.m, ka.n)), tol=1e-9, maxit=maxit)
+    return L
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+# ------------------------------------------------------------------ exact blur
+@pytest.mark.parametrize("bc", [0, 1])
+def test_blur_exact_matches_oracle(bc):
+    g = W.rng(101)
+    P = W.random_psf(g, 7, 5)
+    X = g.uniform(size=(200, 176))
+    Y = api.sfista_blur(P, _cuda(X), bc, center=(2, 3)).cpu().numpy()
+    Yo = oracle.blur(X.astype(np.float32).astype(np.float64), P.astype(np.float32).astype(np.float64), 2, 3, bc)
+    assert oracle.rel_fro(Y, Yo) < 1e-6
+
+
+# ------------------------------------------------------------------ operator
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("transpose", [False, True])
+@pytest.mark.parametrize("shape", [(200, 176), (64, 64), (37, 45)])
+def test_apply_matches_oracle(bc, transpose, shape):
+    """A_s X and A_s^T X on ragged sizes with a non-centred, non-square PSF."""
+    m, n = shape
+    g = W.rng(102 + m)
+    P = W.random_psf(g, 13, 11)
+    ka = kron.kron_approx(P, 4, 7, m, n, bc, 3)
+    s = api.Sfista(P, (m, n), bc, 3, center=(4, 7), prec="fp32", op="banded", lipschitz=1.0)
+    X = g.standard_normal((m, n)).astype(np.float32)
+    Y = s.apply(_cuda(X), transpose=transpose).cpu().numpy()
+    Yo = (oracle.kron_apply_T if transpose else oracle.kron_apply)(X.astype(np.float64), ka)
+    assert oracle.rel_fro(Y, Yo) < 1e-6
+    s.close()
+
+
+def test_adjoint_identity_gpu():
+    g = W.rng(103)
+    P = W.rotated_gaussian_psf(31, 3.0, 1.0, np.deg2rad(30))
+    s = api.Sfista(P, (256, 240), 1, 3, prec="fp32", op="banded", lipschitz=1.0)
+    X = _cuda(g.standard_normal((256, 240)))
+    Y = _cuda(g.standard_normal((256, 240)))
+    lhs = torch.sum(s.apply(X).double() * Y.double()).item()
+    rhs = torch.sum(X.double() * s.apply(Y, transpose=True).double()).item()
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+    s.close()
+
+
+def test_factors_match_oracle_dense():
+    P = W.rotated_gaussian_psf(15, 3.0, 1.0, 0.4)
+    s = api.Sfista(P, (48, 40), 1, 3, lipschitz=1.0)
+    A, B = s.factors()
+    ka = kron.kron_approx(P, 7, 7, 48, 40, 1, 3)
+    Bo, Ao = kron.dense_factors(ka)
+    np.testing.assert_allclose(A, Ao, atol=1e-12)
+    np.testing.assert_allclose(B, Bo, atol=1e-12)
+    s.close()
+
+
+# ------------------------------------------------------------------ Lipschitz constant
+@pytest.mark.parametrize("bc,r", [(0, 1), (1, 2), (1, 3)])
+def test_lipschitz_matches_oracle(bc, r):
+    P = W.rotated_gaussian_psf(9, 2.0, 1.0, 0.3)
+    ka = kron.kron_approx(P, 4, 4, 24, 20, bc, r)
+    As = kron.explicit_kron_matrix(ka)
+    Lx = float(np.linalg.eigvalsh(As.T @ As).max())
+    s = api.Sfista(P, (24, 20), bc, r, lipschitz_tol=1e-14, lipschitz_maxit=20000)
+    L = s.info()["lipschitz"]
+    assert abs(L - Lx) <= 1e-9 * Lx
+    s.close()
+
+
+# ------------------------------------------------------------------ Alg. 2
+def test_solve_config1_fp32():
+    """64^2, separable Gaussian (r=1 exact), zero boundary, 100 iterations."""
+    pr = W.config1()
+    cr, cc = pr.centre
+    bx = oracle.blur(pr.x_true, pr.psf, cr, cc, pr.bc)
+    b = (bx + W.noise_scale(bx, pr.noise, pr.noise_level)).astype(np.float32)
+    ka = kron.kron_approx(pr.psf, cr, cc, 64, 64, pr.bc, pr.r)
+    L = _oracle_L(ka, maxit=3000)
+    Xo = oracle.sfista(b.astype(np.float64), ka, L, pr.lam, pr.iters)
+    s = api.Sfista(pr.psf, (64, 64), pr.bc, pr.r, prec="fp32", lipschitz=L)
+    Xd = s.solve_device(_cuda(b), pr.lam, pr.iters).cpu().numpy()
+    Xh = s.solve(b, pr.lam, pr.iters)
+    assert oracle.rel_fro(Xd, Xo) <= TOL["fp32"]
+    np.testing.assert_array_equal(Xd, Xh)
+    s.close()
+
+
+@pytest.fixture(scope="module")
+def cfg2():
+    pr = W.config2()
+    cr, cc = pr.centre
+    bx = oracle.blur(pr.x_true, pr.psf, cr, cc, pr.bc)
+    b = (bx + W.noise_scale(bx, pr.noise, pr.noise_level)).astype(np.float32)
+    ka = kron.kron_approx(pr.psf, cr, cc, 512, 512, pr.bc, pr.r)
+    L = _oracle_L(ka)
+    Xo = oracle.sfista(b.astype(np.float64), ka, L, pr.lam, pr.iters)
+    return pr, b, ka, L, Xo
+
+
+def test_solve_config2_fp32(cfg2):
+    """512^2, rotated Gaussian, reflexive, r=3, 200 iterations: rel err <= 1e-5."""
+    pr, b, ka, L, Xo = cfg2
+    s = api.Sfista(pr.psf, (512, 512), pr.bc, pr.r, prec="fp32", lipschitz=L)
+    X = s.solve_device(_cuda(b), pr.lam, pr.iters).cpu().numpy()
+    assert oracle.rel_fro(X, Xo) <= TOL["fp32"]
+    assert abs(oracle.psnr(X, pr.x_true) - oracle.psnr(Xo, pr.x_true)) <= 0.01
+    s.close()
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+def test_solve_ragged(bc):
+    m, n = 200, 176
+    g = W.rng(104)
+    P = W.random_psf(g, 11, 9)
+    x, b, (cr, cc) = _problem(m, n, P, bc, 105, centre=(3, 5))
+    ka = kron.kron_approx(P, cr, cc, m, n, bc, 3)
+    L = _oracle_L(ka)
+    Xo = oracle.sfista(b.astype(np.float64), ka, L, 0.01, 60)
+    s = api.Sfista(P, (m, n), bc, 3, center=(cr, cc), prec="fp32", lipschitz=L)
+    X = s.solve_device(_cuda(b), 0.01, 60).cpu().numpy()
+    assert oracle.rel_fro(X, Xo) <= TOL["fp32"]
+    s.close()
+
+
+def test_graph_and_direct_launch_agree():
+    P = W.rotated_gaussian_psf(15, 2.0, 1.0, 0.3)
+    x, b, _ = _problem(96, 80, P, 1, 106)
+    outs = []
+    for graph in (True, False):
+        s = api.Sfista(P, (96, 80), 1, 2, lipschitz=1.0, use_graph=graph)
+        outs.append(s.solve_device(_cuda(b), 0.01, 40).cpu().numpy())
+        s.close()
+    np.testing.assert_array_equal(outs[0], outs[1])
+
+
+def test_resume_state_matches_uninterrupted():
+    P = W.rotated_gaussian_psf(15, 2.0, 1.0, 0.3)
+    x, b, _ = _problem(96, 80, P, 1, 107)
+    s = api.Sfista(P, (96, 80), 1, 2, lipschitz=1.0)
+    db = _cuda(b)
+    X = torch.zeros(96, 80, dtype=torch.float64, device="cuda")
+    Xp = torch.zeros_like(X)
+    s.solve_state(db, 0.01, 0, 30, X, Xp)
+    ref = X.clone()
+    X.zero_()
+    Xp.zero_()
+    s.solve_state(db, 0.01, 0, 20, X, Xp)
+    s.solve_state(db, 0.01, 20, 10, X, Xp)
+    assert torch.max(torch.abs(X - ref)).item() <= 1e-12
+    ka = kron.kron_approx(P, 7, 7, 96, 80, 1, 2)
+    Xo = oracle.sfista(b.astype(np.float64), ka, 1.0, 0.01, 30)
+    assert oracle.rel_fro(ref.cpu().numpy(), Xo) <= 1e-6
+    s.close()
+
+
+def test_projection_matches_oracle():
+    P = W.rotated_gaussian_psf(15, 2.0, 1.0, 0.3)
+    x, b, _ = _problem(96, 80, P, 1, 108)
+    b = b - 0.1
+    ka = kron.kron_approx(P, 7, 7, 96, 80, 1, 2)
+    Xo = oracle.sfista(b.astype(np.float64), ka, 1.0, 0.01, 40, project=True)
+    s = api.Sfista(P, (96, 80), 1, 2, lipschitz=1.0, project=True)
+    X = s.solve_device(_cuda(b), 0.01, 40).cpu().numpy()
+    assert X.min() >= 0.0
+    assert oracle.rel_fro(X, Xo) <= 1e-5
+    s.close()
+
+
+def test_zero_iterations_returns_zero():
+    P = W.gaussian_psf(9, 2.0)
+    s = api.Sfista(P, (40, 40), 0, 1, lipschitz=1.0)
+    X = s.solve_device(_cuda(np.ones((40, 40))), 0.01, 0)
+    assert torch.count_nonzero(X).item() == 0
+    s.close()
+
+
+def test_nonfinite_input_reported():
+    P = W.gaussian_psf(9, 2.0)
+    s = api.Sfista(P, (40, 40), 0, 1, lipschitz=1.0)
+    b = np.ones((40, 40), dtype=np.float32)
+    b[3, 3] = np.inf
+    with pytest.raises(api.SfistaError) as ei:
+        s.solve(b, 0.01, 5)
+    assert ei.value.status == api.EINVAL
+    with pytest.raises(api.SfistaError) as ei:
+        s.solve_device(_cuda(b), 0.01, 5)
+    assert ei.value.status == api.ENUMERIC
+    X = s.solve_device(_cuda(np.ones((40, 40))), 0.01, 5)     # context still usable
+    assert torch.isfinite(X).all().item()
+    s.close()
+
+
+# ------------------------------------------------------------------ full size
+def test_config3_full_size_operator_and_steps():
+    """2048^2, r=5, 63x63 mixture PSF: the operator, its adjoint and 2 iterations vs the oracle."""
+    pr = W.config3()
+    cr, cc = pr.centre
+    n = 2048
+    ka = kron.kron_approx(pr.psf, cr, cc, n, n, pr.bc, pr.r)
+    s = api.Sfista(pr.psf, (n, n), pr.bc, pr.r, prec="fp32", lipschitz=1.0)
+    X = pr.x_true.astype(np.float32)
+    for tr in (False, True):
+        Y = s.apply(_cuda(X), transpose=tr).cpu().numpy()
+        Yo = (oracle.kron_apply_T if tr else oracle.kron_apply)(X.astype(np.float64), ka)
+        assert oracle.rel_fro(Y, Yo) < 1e-6
+    bx = oracle.blur(pr.x_true, pr.psf, cr, cc, pr.bc)
+    b = (bx + W.noise_scale(bx, pr.noise, pr.noise_level)).astype(np.float32)
+    Xo = oracle.sfista(b.astype(np.float64), ka, 1.0, pr.lam, 2)
+    Xg = s.solve_device(_cuda(b), pr.lam, 2).cpu().numpy()
+    assert oracle.rel_fro(Xg, Xo) <= TOL["fp32"]
+    s.close()
