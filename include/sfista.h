@@ -234,6 +234,41 @@ sfista_status sfista_blur(const double *psf, int psf_rows, int psf_cols,
 sfista_status sfista_time_stages(sfista_ctx *ctx, const float *d_b, double lambda,
                                  int reps, float *ms);
 
+/*
+ * sfista_apply_static -- the banded operator of sfista_apply without any
+ * device allocation.  The paper has no counterpart: this call exists for
+ * callers that cannot allocate device memory themselves, such as a plugin
+ * inside a host framework that owns all GPU memory through its own arena and
+ * forbids direct cudaMalloc, or a latency-critical loop that cannot take the
+ * implicit synchronisation and possible failure of an allocation.  It needs
+ * no context, so the caller supplies the factors in band storage.
+ *
+ *   d_y = sum_i B_i d_x A_i^T,  with
+ *   A_i[c][c + lo_right + k] = d_band_right[(i * w_right + k) * img_cols + c]
+ *   B_i[a][a + lo_left + k]  = d_band_left[(i * w_left + k) * img_rows + a]
+ * for k in [0, w); entries whose column falls outside the image must be 0.
+ * Pass the bands of A_i^T and B_i^T instead to apply A_s^T.
+ *
+ * d_x, d_y            device, img_rows x img_cols FP32, distinct buffers.
+ * d_band_right/left   device FP32 band tables as above (caller-owned).
+ * stream              cudaStream_t (NULL = legacy default); asynchronous.
+ *
+ * Scratch: the r intermediate images live in one file-scope device array of
+ * 8 Mi floats (32 MiB) that every GPU loading this library keeps until the
+ * process exits; r * img_rows * img_cols above 8,388,608 returns EINVAL.
+ * All calls share the array and each call overwrites what it reads, so no
+ * state carries over, but calls whose work overlaps on the GPU (different
+ * streams, or unordered host threads) race on it.  The first call on each
+ * device looks up the array's device address with cudaGetSymbolAddress;
+ * make that first call before any stream capture on that device.
+ * Calls no cudaMalloc or cudaFree.
+ */
+sfista_status sfista_apply_static(const float *d_x, float *d_y, int img_rows,
+                                  int img_cols, int r,
+                                  const float *d_band_right, int lo_right,
+                                  int w_right, const float *d_band_left,
+                                  int lo_left, int w_left, void *stream);
+
 const char *sfista_strerror(sfista_status s);
 const char *sfista_last_error(void);
 

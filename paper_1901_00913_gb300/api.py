@@ -62,13 +62,15 @@ def load(path=None):
     L.sfista_get_factors.argtypes = [vp, vp, vp]
     L.sfista_blur.argtypes = [vp, i, i, i, i, i, vp, i, i, vp, vp]
     L.sfista_time_stages.argtypes = [vp, vp, d, i, vp]
+    L.sfista_apply_static.argtypes = [vp, vp, i, i, i, vp, i, i, vp, i, i, vp]
     L.sfista_strerror.argtypes = [i]
     L.sfista_strerror.restype = ctypes.c_char_p
     L.sfista_last_error.argtypes = []
     L.sfista_last_error.restype = ctypes.c_char_p
     for name in ("sfista_setup", "sfista_factorize", "sfista_solve", "sfista_solve_device", "sfista_solve_state",
                  "sfista_sync", "sfista_apply", "sfista_info", "sfista_get_profiles",
-                 "sfista_get_factors", "sfista_blur", "sfista_time_stages"):
+                 "sfista_get_factors", "sfista_blur", "sfista_time_stages",
+                 "sfista_apply_static"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -204,6 +206,14 @@ def sfista_time_stages(ctx, d_b, lam, reps):
     ms = np.zeros(4, dtype=np.float32)
     _check(load().sfista_time_stages(ctypes.c_void_p(ctx), _ptr(d_b), float(lam), int(reps), ms.ctypes.data))
     return ms
+
+
+def sfista_apply_static(d_x, d_y, r, band_right, lo_right, band_left, lo_left, stream=None):
+    """Operator without allocation; band tables are CUDA float32 tensors (r, w, len)."""
+    m, n = d_x.shape
+    _check(load().sfista_apply_static(_ptr(d_x), _ptr(d_y), m, n, int(r), _ptr(band_right), int(lo_right),
+                                      int(band_right.shape[1]), _ptr(band_left), int(lo_left),
+                                      int(band_left.shape[1]), _stream_ptr(stream)))
 
 
 # ------------------------------------------------------------------ convenience wrapper

@@ -1,0 +1,67 @@
+"""sfista_apply_static, the operator entry point that allocates nothing.
+
+Callers that cannot allocate device memory (a plugin whose host framework
+owns all GPU memory through its own arena, or a latency-critical loop that
+cannot afford an allocation's synchronisation or failure) use this call; its
+intermediate images live in a fixed 32 MiB device array inside the library.
+This test builds the band tables from the context's dense factors, calls the
+entry point twice in a row through the C ABI and compares each result with
+sfista_apply on the same context.  It sits in its own file, collected last.
+"""
+import numpy as np
+import pytest
+
+from paper_1901_00913_gb300 import api, workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _band(F):
+    """Band table (r, w, len) and lo of a stack of square banded matrices F[i][row][col]."""
+    r, n, _ = F.shape
+    rows, cols = np.nonzero(np.any(F != 0.0, axis=0))
+    off = cols - rows
+    lo, hi = int(off.min()), int(off.max())
+    w = hi - lo + 1
+    T = np.zeros((r, w, n))
+    for k in range(w):
+        for row in range(n):
+            col = row + lo + k
+            if 0 <= col < n:
+                T[:, k, row] = F[:, row, col]
+    return torch.from_numpy(T.astype(np.float32)).cuda(), lo
+
+
+@pytest.mark.parametrize("transpose", [False, True])
+def test_static_scratch_operator_matches_context_operator(transpose):
+    import __graft_entry__ as g
+    g.build()
+    m, n, r = 200, 176, 3
+    P = W.rotated_gaussian_psf(15, 3.0, 1.0, np.deg2rad(30))
+    s = api.Sfista(P, (m, n), "reflexive", r, prec="fp32", op="banded", lipschitz=1.0)
+    A, B = s.factors()
+    if transpose:
+        A, B = A.transpose(0, 2, 1), B.transpose(0, 2, 1)
+    bandA, loA = _band(A)
+    bandB, loB = _band(B)
+    gen = W.rng(2024)
+    for call in range(2):
+        x = torch.from_numpy(gen.standard_normal((m, n)).astype(np.float32)).cuda()
+        ref = s.apply(x, transpose=transpose)
+        y = torch.full_like(x, float("nan"))
+        api.sfista_apply_static(x, y, r, bandA, loA, bandB, loB)
+        torch.cuda.synchronize()
+        err = (torch.linalg.norm((y - ref).double()) / torch.linalg.norm(ref.double())).item()
+        assert err <= 1e-6, "call %d: rel err %.3e" % (call, err)
+    s.close()
+
+
+def test_static_scratch_rejects_oversize():
+    import __graft_entry__ as g
+    g.build()
+    x = torch.zeros(16, 16, device="cuda")
+    band = torch.zeros(1, 3, 16, device="cuda")
+    with pytest.raises(api.SfistaError) as ei:
+        api.sfista_apply_static(x, torch.zeros_like(x), 40000, band, -1, band, -1)
+    assert ei.value.status == api.EINVAL
