@@ -194,8 +194,10 @@ sfista_status sfista_apply(sfista_ctx *ctx, const float *d_x, float *d_y,
  * lipschitz   L used by Step 1 (estimated or given).
  * sigma       if non-NULL, min(psf_rows, psf_cols) singular values of P_bar.
  * approx_err  if non-NULL, sqrt(sum_{k>r} s_k^2) = ||A - A_s||_F (Theorem 1).
- * config      if non-NULL, int[4]: effective precision, operator form, band
- *             width of the right factors, band width of the left factors.
+ * config      if non-NULL, int[8]: effective precision, operator form, band
+ *             widths w of A_i and B_i, then the band offsets lo of A_i, B_i,
+ *             A_i^T, B_i^T (row `row` of a factor holds its nonzeros in
+ *             columns row + lo .. row + lo + w - 1).
  */
 sfista_status sfista_info(const sfista_ctx *ctx, double *lipschitz,
                           double *sigma, double *approx_err, int *config);

@@ -167,12 +167,13 @@ def sfista_info(ctx, kmax):
     L = ctypes.c_double()
     err = ctypes.c_double()
     sig = np.zeros(kmax)
-    cfg = np.zeros(4, dtype=np.int32)
+    cfg = np.zeros(8, dtype=np.int32)
     _check(load().sfista_info(ctypes.c_void_p(ctx), ctypes.byref(L), sig.ctypes.data, ctypes.byref(err),
                               cfg.ctypes.data))
     return {"lipschitz": L.value, "sigma": sig, "approx_err": err.value,
             "prec": PREC_NAME[int(cfg[0])], "op": OP_NAME[int(cfg[1])],
-            "band_right": int(cfg[2]), "band_left": int(cfg[3])}
+            "band_right": int(cfg[2]), "band_left": int(cfg[3]),
+            "lo": {"A": int(cfg[4]), "B": int(cfg[5]), "AT": int(cfg[6]), "BT": int(cfg[7])}}
 
 
 def sfista_get_profiles(ctx, r, p, q):

@@ -48,14 +48,14 @@ __global__ void init_state_kernel(const double *X, const double *Xp, double *Y, 
         if (split_kind == 1) {
             __nv_bfloat16 h = __double2bfloat16(y);
             reinterpret_cast<__nv_bfloat16 *>(Yhi)[i] = h;
-            reinterpret_cast<__nv_bfloat16 *>(Ylo)[i] = __double2bfloat16(y - (double)__bfloat162float(h));
+            if (Ylo) reinterpret_cast<__nv_bfloat16 *>(Ylo)[i] = __double2bfloat16(y - (double)__bfloat162float(h));
         } else if (split_kind == 2) {
             unsigned u;
             asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"((float)y));
             float h = __uint_as_float(u);
             reinterpret_cast<float *>(Yhi)[i] = h;
             asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"((float)(y - (double)h)));
-            reinterpret_cast<float *>(Ylo)[i] = __uint_as_float(u);
+            if (Ylo) reinterpret_cast<float *>(Ylo)[i] = __uint_as_float(u);
         }
     }
 }
@@ -148,6 +148,8 @@ ProxArgs prox_args(sfista_ctx *c, int k, double lam) {
     pa.k = k;
     pa.L = c->L;
     pa.lam2 = lam * lam;
+    pa.inv_den = 1.0 / (c->L + lam * lam);
+    pa.shrink = c->L * pa.inv_den;
     pa.project = c->opts.project_nonneg;
     pa.status = c->status;
     return pa;
@@ -408,7 +410,7 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int ce
         return bail(fail(SFISTA_ENOMEM, std::string("state buffers: ") + cudaGetErrorString(e)));
     if ((e = cudaMemset(c->status, 0, 16))) return bail(fail(SFISTA_ECUDA, cudaGetErrorString(e)));
     if (c->op != SFISTA_OP_BANDED) {
-        st = gemm_create(&c->gemm, h, c->prec, c->op == SFISTA_OP_GEMM_DENSE, c->Yop, c->R, c->stream);
+        st = gemm_create(&c->gemm, h, c->prec, c->op == SFISTA_OP_GEMM_DENSE, c->status, c->stream);
         if (st) return bail(st);
     }
     if (o.lipschitz > 0.0) {
@@ -528,6 +530,10 @@ sfista_status sfista_info(const sfista_ctx *c, double *lipschitz, double *sigma,
         config[1] = c->op;
         config[2] = c->hs.A.w;
         config[3] = c->hs.B.w;
+        config[4] = c->hs.A.lo;
+        config[5] = c->hs.B.lo;
+        config[6] = c->hs.AT.lo;
+        config[7] = c->hs.BT.lo;
     }
     return SFISTA_OK;
 }

@@ -1,14 +1,630 @@
+// Tensor-core execution of the Kronecker operator: tcgen05.mma with the
+// accumulator in TMEM, operands staged by TMA, fused epilogues.
+//
+// One iteration of Alg. 2 (Step 1) is four products, each written as a GEMM
+// C[M][N] = sum_k P[M][k] Q[N][k] with both operands K-major in memory:
+//   stage 0  Tt[i][c][a] = sum_b A_i[c][b]  Y[a][b]         (Y A_i^T, stored transposed)
+//   stage 1  R[a][c]     = sum_{i,e} B_i[a][e] Tt[i][c][e]  - Bdata[a][c]
+//   stage 2  Ut[j][b][a] = sum_c A^T_j[b][c] R[a][c]        (R A_j, stored transposed)
+//   stage 3  G[a][b]     = sum_{j,e} B^T_j[a][e] Ut[j][b][e];  then Step 1 shrink and
+//                          Step 3 momentum in the epilogue (FP64 state).
+// Stages 0 and 2 stack the r terms along M (one M tile belongs to one term);
+// stages 1 and 3 sum the r terms along K.  The factors are banded, so an M
+// tile of rows [m0, m0+128) only meets K columns [m0 + lo, m0 + 127 + hi];
+// in band mode the K loop covers just that range (exact: the skipped factor
+// entries are zero), in dense mode the whole K extent.
+//
+// Split precision: operands are stored as hi + lo pairs (BF16 or TF32) and
+// each K step issues hi*hi + lo*hi + hi*lo into the same FP32 accumulator.
+//
+// Kernel roles (192 threads): warp 0 lane 0 issues TMA loads into a ring of
+// shared-memory stages; warp 1 owns the TMEM allocation and lane 0 issues the
+// MMAs, releasing each stage with tcgen05.commit; warps 2-5 wait for the
+// accumulator, read it with tcgen05.ld (each warp its 32-lane quarter) and
+// run the epilogue.  Every mbarrier wait is bounded (about one second); on
+// expiry the kernel records DEV_TIMEOUT in the status word, drains what it
+// issued and returns, so the host sees SFISTA_ETIMEOUT instead of a hang.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+
+#include "epilogue.cuh"
 #include "gemm.h"
 
 namespace sfista {
-struct GemmPath {};
-sfista_status gemm_create(GemmPath **out, const HostSetup &, int, bool, float *, float *, cudaStream_t) {
-    *out = nullptr;
-    return fail(SFISTA_ENOTSUP, "tensor-core operator not built yet");
+namespace {
+
+constexpr int BM = 128;                 // MMA M (rows of P per tile)
+constexpr int KB_BYTES = 128;           // bytes of one K block per row (one 128 B swizzle span)
+constexpr long long kWaitCycles = 2000000000LL;   // ~1 s at 2 GHz
+
+enum Fmt : int { FMT_BF16 = 0, FMT_TF32 = 1 };
+enum GEpi : int { GE_SPLIT = 0, GE_RESID = 1, GE_PROX = 2, GE_STORE = 3 };
+
+struct GemmArgs {
+    int rows;        // P rows per term (extent of M within one term)
+    int m_tiles;     // M tiles per term
+    int N;           // extent of N
+    int K;           // extent of K within one segment
+    int band_lo;     // K range of the tile at m0: [m0 + band_lo, m0 + BM - 1 + band_hi]
+    int band_hi;
+    int dense;       // 1: whole K range
+    int segs;        // K segments (terms summed along K); 1 when terms stack along M
+    int type_b;      // 1: P and Q both indexed by the K segment; 0: P by the tile's term
+    void *out_hi, *out_lo;   // GE_SPLIT / GE_RESID operand copies
+    float *out_f32;          // GE_STORE
+    const float *Bd;         // GE_RESID
+    int split_kind;          // 1 bf16, 2 tf32 (fp32 storage)
+    ProxArgs pa;             // GE_PROX
+    unsigned *status;
+};
+
+template <int FMT, bool SPLIT, int BN>
+struct Cfg {
+    static constexpr int P_BYTES = BM * KB_BYTES;
+    static constexpr int Q_BYTES = BN * KB_BYTES;
+    static constexpr int NOP = SPLIT ? 2 : 1;
+    static constexpr int STAGE_BYTES = NOP * (P_BYTES + Q_BYTES);
+    static constexpr int STAGES_RAW = (200 * 1024) / STAGE_BYTES;
+    static constexpr int STAGES = STAGES_RAW > 6 ? 6 : STAGES_RAW;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+    static constexpr int KSTEPS = KB_BYTES / 32;    // MMA K step = 32 bytes (16 bf16 / 8 tf32)
+    static constexpr int KB_ELEMS = FMT == FMT_BF16 ? 64 : 32;
+    static constexpr int ALIGN = FMT == FMT_BF16 ? 8 : 4;   // 16-byte TMA x alignment
+    static constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+    // Instruction descriptor: D=F32, A/B = BF16 (kind::f16) or TF32 (kind::tf32),
+    // both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+    static constexpr uint32_t IDESC = (1u << 4) | ((FMT == FMT_BF16 ? 1u : 2u) << 7) |
+                                      ((FMT == FMT_BF16 ? 1u : 2u) << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                      ((uint32_t)(BM >> 4) << 24);
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
-void gemm_destroy(GemmPath *g) { delete g; }
-void gemm_state_operands(GemmPath *, void **a, void **b, int *k) { *a = *b = nullptr; *k = 0; }
-void gemm_prepare_solve(GemmPath *, const float *, cudaStream_t) {}
-void gemm_stage(GemmPath *, int, const ProxArgs &, cudaStream_t) {}
-sfista_status gemm_apply(GemmPath *, const float *, float *, int, cudaStream_t) { return SFISTA_ENOTSUP; }
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase with the given parity; false (and DEV_TIMEOUT) on expiry.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned *status) {
+    if (mbar_try(bar, parity)) return true;
+    long long t0 = clock64();
+    while (!mbar_try(bar, parity)) {
+        if (clock64() - t0 > kWaitCycles) {
+            atomicOr(status, DEV_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y,
+                                            int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+        "[%2];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), version 1 (bit 46), layout SWIZZLE_128B (2 << 61).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+template <int FMT>
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if (FMT == FMT_BF16)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+}
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Store two neighbouring values (idx even) as split operand copies.
+__device__ __forceinline__ void store_split2(void *hi, void *lo, int kind, size_t idx, float v0, float v1) {
+    if (kind == 1) {
+        __nv_bfloat162 h, l;
+        h.x = __float2bfloat16_rn(v0);
+        h.y = __float2bfloat16_rn(v1);
+        *reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<__nv_bfloat16 *>(hi) + idx) = h;
+        if (lo) {
+            l.x = __float2bfloat16_rn(v0 - __bfloat162float(h.x));
+            l.y = __float2bfloat16_rn(v1 - __bfloat162float(h.y));
+            *reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<__nv_bfloat16 *>(lo) + idx) = l;
+        }
+    } else {
+        const float h0 = tf32_round(v0), h1 = tf32_round(v1);
+        *reinterpret_cast<float2 *>(reinterpret_cast<float *>(hi) + idx) = make_float2(h0, h1);
+        if (lo)
+            *reinterpret_cast<float2 *>(reinterpret_cast<float *>(lo) + idx) =
+                make_float2(tf32_round(v0 - h0), tf32_round(v1 - h1));
+    }
+}
+
+template <int FMT, bool SPLIT, int BN, int EPI>
+__global__ void __launch_bounds__(192, 1)
+    umma_gemm_kernel(const __grid_constant__ CUtensorMap tPhi, const __grid_constant__ CUtensorMap tPlo,
+                     const __grid_constant__ CUtensorMap tQhi, const __grid_constant__ CUtensorMap tQlo,
+                     GemmArgs g) {
+    using C = Cfg<FMT, SPLIT, BN>;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t bars[2 * C::STAGES + 1];
+    __shared__ uint32_t tmem_base_sh;
+
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mt = blockIdx.y;
+    const int term = g.type_b ? 0 : mt / g.m_tiles;
+    const int m0 = (mt % g.m_tiles) * BM;
+    const int n0 = blockIdx.x * BN;
+
+    int k_lo = 0, k_hi = g.K;
+    if (!g.dense) {
+        k_lo = max(0, m0 + g.band_lo);
+        k_hi = min(g.K, m0 + BM + g.band_hi);
+        k_lo = (k_lo / C::ALIGN) * C::ALIGN;
+    }
+    const int nkb = k_hi > k_lo ? (k_hi - k_lo + C::KB_ELEMS - 1) / C::KB_ELEMS : 0;
+    const int total = nkb * g.segs;
+
+    const uint32_t full0 = smem_u32(&bars[0]);
+    const uint32_t empty0 = smem_u32(&bars[C::STAGES]);
+    const uint32_t accb = smem_u32(&bars[2 * C::STAGES]);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::STAGES; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(accb, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                     "r"(C::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int it = 0; it < total; ++it) {
+                const int s = it % C::STAGES;
+                const uint32_t ph = (it / C::STAGES) & 1;
+                if (!mbar_wait(empty0 + 8 * s, ph ^ 1, g.status)) break;
+                const uint32_t fb = full0 + 8 * s;
+                mbar_expect_tx(fb, C::STAGE_BYTES);
+                const int seg = it / nkb, kb = it - seg * nkb;
+                const int kx = k_lo + kb * C::KB_ELEMS;
+                const int pz = g.type_b ? seg : term;
+                const int qz = g.type_b ? seg : 0;
+                const uint32_t base = smem_u32(smem + s * C::STAGE_BYTES);
+                tma_load_3d(base, &tPhi, fb, kx, m0, pz);
+                if (SPLIT) tma_load_3d(base + C::P_BYTES, &tPlo, fb, kx, m0, pz);
+                tma_load_3d(base + C::NOP * C::P_BYTES, &tQhi, fb, kx, n0, qz);
+                if (SPLIT) tma_load_3d(base + C::NOP * C::P_BYTES + C::Q_BYTES, &tQlo, fb, kx, n0, qz);
+                issued = it + 1;
+            }
+            // Drain: the last fill of every stage has landed before the CTA can exit.
+            for (int it = max(0, issued - C::STAGES); it < issued; ++it)
+                mbar_wait(full0 + 8 * (it % C::STAGES), (it / C::STAGES) & 1, g.status);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            for (int it = 0; it < total; ++it) {
+                const int s = it % C::STAGES;
+                const uint32_t ph = (it / C::STAGES) & 1;
+                if (!mbar_wait(full0 + 8 * s, ph, g.status)) break;
+                tc_fence_after();
+                const uint32_t base = smem_u32(smem + s * C::STAGE_BYTES);
+                const uint32_t p_hi = base, p_lo = base + C::P_BYTES;
+                const uint32_t q_hi = base + C::NOP * C::P_BYTES, q_lo = q_hi + C::Q_BYTES;
+#pragma unroll
+                for (int ks = 0; ks < C::KSTEPS; ++ks) {
+                    const uint32_t acc = (it > 0 || ks > 0) ? 1u : 0u;
+                    tc_mma<FMT>(tmem, sw128_desc(p_hi + 32 * ks), sw128_desc(q_hi + 32 * ks), C::IDESC, acc);
+                    if (SPLIT) {
+                        tc_mma<FMT>(tmem, sw128_desc(p_lo + 32 * ks), sw128_desc(q_hi + 32 * ks), C::IDESC, 1u);
+                        tc_mma<FMT>(tmem, sw128_desc(p_hi + 32 * ks), sw128_desc(q_lo + 32 * ks), C::IDESC, 1u);
+                    }
+                }
+                tc_commit(empty0 + 8 * s);
+            }
+            // Arrives once every MMA issued above has completed.
+            tc_commit(accb);
+        }
+        __syncwarp();
+    } else {
+        // Epilogue, warps 2..5.  Phase 1: each warp reads its 32-lane quarter of
+        // the accumulator (tcgen05.ld) into a row-major tile in the now idle
+        // stage ring (row stride BN + 1 floats: conflict-free).  Phase 2: each
+        // warp walks whole rows so global accesses are row-contiguous.
+        const bool ok = mbar_wait(accb, 0, g.status);
+        tc_fence_after();
+        const int lg = warp & 3;
+        float *tile = reinterpret_cast<float *>(smem);
+        constexpr int TS = BN + 1;
+#pragma unroll 1
+        for (int j0 = 0; j0 < BN; j0 += 32) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)j0, v);
+            const bool zero = !ok || total == 0;
+#pragma unroll
+            for (int t = 0; t < 32; ++t) tile[(lg * 32 + lane) * TS + j0 + t] = zero ? 0.0f : v[t];
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        const int ew = warp - 2;
+#pragma unroll 1
+        for (int rl = ew; rl < BM; rl += 4) {
+            const int row = m0 + rl;
+            if (row >= g.rows) break;
+            const float *trow = tile + rl * TS;
+#pragma unroll 1
+            for (int c = 2 * lane; c < BN; c += 64) {
+                const int col = n0 + c;
+                if (col >= g.N) break;   // N is even (a multiple of 8)
+                const float a0 = trow[c], a1 = trow[c + 1];
+                if (EPI == GE_SPLIT) {
+                    const size_t idx = ((size_t)term * g.rows + row) * g.N + col;
+                    store_split2(g.out_hi, g.out_lo, g.split_kind, idx, a0, a1);
+                } else if (EPI == GE_RESID) {
+                    const size_t idx = (size_t)row * g.N + col;
+                    const float2 b = *reinterpret_cast<const float2 *>(g.Bd + idx);
+                    store_split2(g.out_hi, g.out_lo, g.split_kind, idx, a0 - b.x, a1 - b.y);
+                } else if (EPI == GE_PROX) {
+                    prox_momentum2(g.pa, (size_t)row * g.N + col, (double)a0, (double)a1);
+                } else {
+                    *reinterpret_cast<float2 *>(g.out_f32 + (size_t)row * g.N + col) = make_float2(a0, a1);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// ------------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+sfista_status get_encoder() {
+    if (g_encode) return SFISTA_OK;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+        return fail(SFISTA_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    return SFISTA_OK;
+}
+
+// 3-D tensor [d2][d1][d0] (d0 contiguous), box {kb_elems, box_rows, 1}, 128 B swizzle.
+sfista_status make_map(CUtensorMap *map, const void *base, int fmt, int d0, int d1, int d2, int box_rows) {
+    if (!base) {
+        memset(map, 0, sizeof(*map));
+        return SFISTA_OK;
+    }
+    const size_t es = fmt == FMT_BF16 ? 2 : 4;
+    cuuint64_t dims[3] = {(cuuint64_t)d0, (cuuint64_t)d1, (cuuint64_t)d2};
+    cuuint64_t strides[2] = {(cuuint64_t)d0 * es, (cuuint64_t)d0 * d1 * es};
+    cuuint32_t box[3] = {(cuuint32_t)(KB_BYTES / es), (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = g_encode(map, fmt == FMT_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                          const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(SFISTA_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return SFISTA_OK;
+}
+
+struct Operand {
+    void *hi = nullptr, *lo = nullptr;
+    CUtensorMap map_hi, map_lo;
+};
+
+}  // namespace
+
+struct GemmPath {
+    int fmt = FMT_BF16;
+    bool split = true, dense = false;
+    int split_kind = 1;
+    int m = 0, n = 0, r = 0;
+    Band bandA, bandB, bandAT, bandBT;   // lo/w only (no host copies of the tables)
+    Operand PA, PB, PAT, PBT;            // factor panels (P operands)
+    Operand QY, QT, QR, QU;              // Y, Tt, R, Ut (Q operands; Tt/Ut are also outputs)
+    const float *Bd = nullptr;
+    unsigned *status = nullptr;
+    double *dband = nullptr;             // scratch for densify
+};
+
+namespace {
+
+constexpr int BN_TILE = 128;
+
+template <int FMT, bool SPLIT, int EPI>
+cudaError_t set_attr() {
+    return cudaFuncSetAttribute(umma_gemm_kernel<FMT, SPLIT, BN_TILE, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                Cfg<FMT, SPLIT, BN_TILE>::SMEM);
+}
+
+template <int FMT, bool SPLIT>
+cudaError_t set_attrs() {
+    cudaError_t e;
+    if ((e = set_attr<FMT, SPLIT, GE_SPLIT>())) return e;
+    if ((e = set_attr<FMT, SPLIT, GE_RESID>())) return e;
+    if ((e = set_attr<FMT, SPLIT, GE_PROX>())) return e;
+    return set_attr<FMT, SPLIT, GE_STORE>();
+}
+
+template <int FMT, bool SPLIT, int EPI>
+sfista_status launch_one(const Operand &P, const Operand &Q, const GemmArgs &a, int grid_x, int grid_y,
+                         cudaStream_t s) {
+    using C = Cfg<FMT, SPLIT, BN_TILE>;
+    auto kern = umma_gemm_kernel<FMT, SPLIT, BN_TILE, EPI>;
+    kern<<<dim3(grid_x, grid_y), 192, C::SMEM, s>>>(P.map_hi, SPLIT ? P.map_lo : P.map_hi, Q.map_hi,
+                                                     SPLIT ? Q.map_lo : Q.map_hi, a);
+    return SFISTA_OK;
+}
+
+template <int EPI>
+sfista_status dispatch(const GemmPath *g, const Operand &P, const Operand &Q, const GemmArgs &a, int gx, int gy,
+                       cudaStream_t s) {
+    if (g->fmt == FMT_BF16)
+        return g->split ? launch_one<FMT_BF16, true, EPI>(P, Q, a, gx, gy, s)
+                        : launch_one<FMT_BF16, false, EPI>(P, Q, a, gx, gy, s);
+    return g->split ? launch_one<FMT_TF32, true, EPI>(P, Q, a, gx, gy, s)
+                    : launch_one<FMT_TF32, false, EPI>(P, Q, a, gx, gy, s);
+}
+
+GemmArgs base_args(const GemmPath *g) {
+    GemmArgs a{};
+    a.dense = g->dense ? 1 : 0;
+    a.split_kind = g->split_kind;
+    a.status = g->status;
+    return a;
+}
+
+// Stage 0 / 2: out[term][row][col] = sum_k P_term[row][k] Q[col][k] (terms along M).
+sfista_status run_stacked(const GemmPath *g, const Operand &P, const Band &band, const Operand &Q, Operand &Out,
+                          cudaStream_t s) {
+    GemmArgs a = base_args(g);
+    a.rows = g->n;
+    a.m_tiles = (g->n + BM - 1) / BM;
+    a.N = g->m;
+    a.K = g->n;
+    a.band_lo = band.lo;
+    a.band_hi = band.lo + band.w - 1;
+    a.segs = 1;
+    a.type_b = 0;
+    a.out_hi = Out.hi;
+    a.out_lo = Out.lo;
+    return dispatch<GE_SPLIT>(g, P, Q, a, (g->m + BN_TILE - 1) / BN_TILE, a.m_tiles * g->r, s);
+}
+
+// Stage 1 / 3: out[row][col] = sum_{t, k} P_t[row][k] Q_t[col][k] (terms along K).
+template <int EPI>
+sfista_status run_summed(const GemmPath *g, const Operand &P, const Band &band, const Operand &Q, GemmArgs a,
+                         cudaStream_t s) {
+    a.rows = g->m;
+    a.m_tiles = (g->m + BM - 1) / BM;
+    a.N = g->n;
+    a.K = g->m;
+    a.band_lo = band.lo;
+    a.band_hi = band.lo + band.w - 1;
+    a.segs = g->r;
+    a.type_b = 1;
+    return dispatch<EPI>(g, P, Q, a, (g->n + BN_TILE - 1) / BN_TILE, a.m_tiles, s);
+}
+
+cudaError_t alloc_operand(Operand *o, size_t elems, size_t es, bool split) {
+    cudaError_t e = cudaMalloc(&o->hi, elems * es);
+    if (e) return e;
+    if (split) e = cudaMalloc(&o->lo, elems * es);
+    return e;
+}
+
+void free_operand(Operand *o) {
+    if (o->hi) cudaFree(o->hi);
+    if (o->lo) cudaFree(o->lo);
+    o->hi = o->lo = nullptr;
+}
+
+}  // namespace
+
+sfista_status gemm_create(GemmPath **out, const HostSetup &h, int prec, bool dense, unsigned *status,
+                          cudaStream_t s) {
+    *out = nullptr;
+    if (prec == SFISTA_FP32) return fail(SFISTA_ENOTSUP, "the GEMM operator form runs on the tensor cores (TF32/BF16)");
+    if (h.m % 8 || h.n % 8)
+        return fail(SFISTA_ENOTSUP, "tensor-core operator needs image sizes that are multiples of 8");
+    sfista_status st = get_encoder();
+    if (st) return st;
+    GemmPath *g = new (std::nothrow) GemmPath();
+    if (!g) return fail(SFISTA_ENOMEM, "GEMM path allocation failed");
+    g->fmt = (prec == SFISTA_BF16 || prec == SFISTA_BF16X3) ? FMT_BF16 : FMT_TF32;
+    g->split = (prec == SFISTA_BF16X3 || prec == SFISTA_TF32X3);
+    g->split_kind = g->fmt == FMT_BF16 ? 1 : 2;
+    g->dense = dense;
+    g->status = status;
+    g->m = h.m;
+    g->n = h.n;
+    g->r = h.r;
+    auto meta = [](const Band &b) {
+        Band o;
+        o.len = b.len;
+        o.r = b.r;
+        o.lo = b.lo;
+        o.w = b.w;
+        return o;
+    };
+    g->bandA = meta(h.A);
+    g->bandB = meta(h.B);
+    g->bandAT = meta(h.AT);
+    g->bandBT = meta(h.BT);
+    const size_t es = g->fmt == FMT_BF16 ? 2 : 4;
+    const size_t m = h.m, n = h.n, r = h.r;
+    cudaError_t e = cudaSuccess;
+    auto bail = [&](sfista_status x) {
+        gemm_destroy(g);
+        return x;
+    };
+    if ((e = alloc_operand(&g->PA, r * n * n, es, g->split)) || (e = alloc_operand(&g->PAT, r * n * n, es, g->split)) ||
+        (e = alloc_operand(&g->PB, r * m * m, es, g->split)) || (e = alloc_operand(&g->PBT, r * m * m, es, g->split)) ||
+        (e = alloc_operand(&g->QY, m * n, es, g->split)) || (e = alloc_operand(&g->QT, r * n * m, es, g->split)) ||
+        (e = alloc_operand(&g->QR, m * n, es, g->split)) || (e = alloc_operand(&g->QU, r * n * m, es, g->split)))
+        return bail(fail(SFISTA_ENOMEM, std::string("GEMM operand buffers: ") + cudaGetErrorString(e)));
+    if (g->fmt == FMT_BF16) e = g->split ? set_attrs<FMT_BF16, true>() : set_attrs<FMT_BF16, false>();
+    else e = g->split ? set_attrs<FMT_TF32, true>() : set_attrs<FMT_TF32, false>();
+    if (e) return bail(fail(SFISTA_ECUDA, std::string("GEMM smem attribute: ") + cudaGetErrorString(e)));
+    // Dense factor panels from the band tables, in the operand format.
+    const int kind = g->fmt == FMT_BF16 ? 1 : 2;
+    auto dens = [&](const Band &b, Operand &o) -> cudaError_t {
+        cudaError_t ee = cudaMalloc((void **)&g->dband, b.band.size() * sizeof(double));
+        if (ee) return ee;
+        ee = cudaMemcpyAsync(g->dband, b.band.data(), b.band.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+        if (!ee) launch_densify(g->dband, b.r, b.len, b.lo, b.w, b.len, kind, o.hi, g->split ? o.lo : nullptr, b.len, s);
+        if (!ee) ee = cudaGetLastError();
+        if (!ee) ee = cudaStreamSynchronize(s);
+        cudaFree(g->dband);
+        g->dband = nullptr;
+        return ee;
+    };
+    if ((e = dens(h.A, g->PA)) || (e = dens(h.AT, g->PAT)) || (e = dens(h.B, g->PB)) || (e = dens(h.BT, g->PBT)))
+        return bail(fail(SFISTA_ECUDA, std::string("factor panels: ") + cudaGetErrorString(e)));
+    // Tensor maps: P operands (box rows BM), Q operands (box rows BN).
+    struct M {
+        Operand *o;
+        int d0, d1, d2, rows;
+    } maps[] = {
+        {&g->PA, (int)n, (int)n, (int)r, BM},  {&g->PAT, (int)n, (int)n, (int)r, BM},
+        {&g->PB, (int)m, (int)m, (int)r, BM},  {&g->PBT, (int)m, (int)m, (int)r, BM},
+        {&g->QY, (int)n, (int)m, 1, BN_TILE},  {&g->QR, (int)n, (int)m, 1, BN_TILE},
+        {&g->QT, (int)m, (int)n, (int)r, BN_TILE}, {&g->QU, (int)m, (int)n, (int)r, BN_TILE},
+    };
+    for (auto &mm : maps) {
+        if ((st = make_map(&mm.o->map_hi, mm.o->hi, g->fmt, mm.d0, mm.d1, mm.d2, mm.rows))) return bail(st);
+        if ((st = make_map(&mm.o->map_lo, mm.o->lo, g->fmt, mm.d0, mm.d1, mm.d2, mm.rows))) return bail(st);
+    }
+    *out = g;
+    return SFISTA_OK;
+}
+
+void gemm_destroy(GemmPath *g) {
+    if (!g) return;
+    for (Operand *o : {&g->PA, &g->PB, &g->PAT, &g->PBT, &g->QY, &g->QT, &g->QR, &g->QU}) free_operand(o);
+    if (g->dband) cudaFree(g->dband);
+    delete g;
+}
+
+void gemm_state_operands(GemmPath *g, void **yhi, void **ylo, int *split_kind) {
+    *yhi = g->QY.hi;
+    *ylo = g->split ? g->QY.lo : nullptr;
+    *split_kind = g->split_kind;
+}
+
+void gemm_prepare_solve(GemmPath *g, const float *Bd, cudaStream_t) { g->Bd = Bd; }
+
+void gemm_stage(GemmPath *g, int st, const ProxArgs &pa_in, cudaStream_t s) {
+    switch (st) {
+        case 0:
+            run_stacked(g, g->PA, g->bandA, g->QY, g->QT, s);
+            break;
+        case 1: {
+            GemmArgs a = base_args(g);
+            a.Bd = g->Bd;
+            a.out_hi = g->QR.hi;
+            a.out_lo = g->QR.lo;
+            run_summed<GE_RESID>(g, g->PB, g->bandB, g->QT, a, s);
+            break;
+        }
+        case 2:
+            run_stacked(g, g->PAT, g->bandAT, g->QR, g->QU, s);
+            break;
+        default: {
+            GemmArgs a = base_args(g);
+            a.pa = pa_in;
+            a.pa.Yhi = g->QY.hi;
+            a.pa.Ylo = g->split ? g->QY.lo : nullptr;
+            a.pa.split_kind = g->split_kind;
+            a.status = pa_in.status;
+            run_summed<GE_PROX>(g, g->PBT, g->bandBT, g->QU, a, s);
+            break;
+        }
+    }
+}
+
+sfista_status gemm_apply(GemmPath *g, const float *x, float *y, int transpose, cudaStream_t s) {
+    const size_t N = (size_t)g->m * g->n;
+    Operand &in = transpose ? g->QR : g->QY;
+    launch_split(x, in.hi, g->split ? in.lo : nullptr, N, g->split_kind, s);
+    GemmArgs a = base_args(g);
+    a.out_f32 = y;
+    sfista_status st;
+    if (!transpose) {
+        if ((st = run_stacked(g, g->PA, g->bandA, g->QY, g->QT, s))) return st;
+        st = run_summed<GE_STORE>(g, g->PB, g->bandB, g->QT, a, s);
+    } else {
+        if ((st = run_stacked(g, g->PAT, g->bandAT, g->QR, g->QU, s))) return st;
+        st = run_summed<GE_STORE>(g, g->PBT, g->bandBT, g->QU, a, s);
+    }
+    if (st) return st;
+    cudaError_t e = cudaGetLastError();
+    if (e) return fail(SFISTA_ECUDA, std::string("GEMM launch: ") + cudaGetErrorString(e));
+    return SFISTA_OK;
+}
+
 }  // namespace sfista

@@ -10,10 +10,10 @@ struct GemmPath;
 
 // Builds operand panels and intermediates for precision `prec` from the
 // host setup.  dense = true uses the full K range, otherwise K tiles outside
-// the factor band are skipped.  Yop / R are the FP32 state buffers of the
-// context (used by the FP32 SIMT GEMM variant).
-sfista_status gemm_create(GemmPath **out, const HostSetup &h, int prec, bool dense, float *Yop,
-                          float *R, cudaStream_t s);
+// the factor band are skipped.  status is the context's device status word
+// (timeouts of the bounded mbarrier waits are reported there).
+sfista_status gemm_create(GemmPath **out, const HostSetup &h, int prec, bool dense, unsigned *status,
+                          cudaStream_t s);
 void gemm_destroy(GemmPath *g);
 // Split-operand copies of Y that the prox epilogue must write.
 void gemm_state_operands(GemmPath *g, void **yhi, void **ylo, int *split_kind);

@@ -73,6 +73,8 @@ struct ProxArgs {
     const double *beta;  // momentum table, beta[k-1] for iteration k
     int k;               // iteration index (1-based)
     double L, lam2;      // Lipschitz constant and lambda^2
+    double inv_den;      // 1 / (L + lambda^2)
+    double shrink;       // L / (L + lambda^2)
     int project;         // max(X, 0) after the shrink
     unsigned *status;    // device status word
 };

@@ -14,6 +14,7 @@
 // momentum for the adjoint, with the FISTA state in FP64.
 #include <cuda_bf16.h>
 
+#include "epilogue.cuh"
 #include "internal.h"
 
 namespace sfista {
@@ -64,37 +65,6 @@ __global__ void __launch_bounds__(NTHR) band_rows_kernel(const T *__restrict__ I
                 if (ga < m) Z[((size_t)i * m + ga) * n + gc] = acc[j];
             }
         }
-    }
-}
-
-__device__ __forceinline__ float tf32_round(float x) {
-    unsigned u;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
-    return __uint_as_float(u);
-}
-
-// Step 1 shrink (+ projection) and Step 3 momentum for one pixel, FP64 state.
-__device__ __forceinline__ void prox_momentum(const ProxArgs &pa, size_t idx, double g) {
-    double y = pa.Y[idx];
-    double xprev = pa.Xin[idx];
-    double x = (pa.L * y - g) / (pa.L + pa.lam2);
-    if (pa.project && x < 0.0) x = 0.0;
-    if (!isfinite(x)) atomicOr(pa.status, DEV_NONFINITE);
-    double beta = pa.beta[pa.k - 1];
-    double yn = x + beta * (x - xprev);
-    pa.Xout[idx] = x;
-    pa.Y[idx] = yn;
-    if (pa.Yop) pa.Yop[idx] = (float)yn;
-    if (pa.split_kind == 1) {
-        __nv_bfloat16 hi = __double2bfloat16(yn);
-        __nv_bfloat16 lo = __double2bfloat16(yn - (double)__bfloat162float(hi));
-        reinterpret_cast<__nv_bfloat16 *>(pa.Yhi)[idx] = hi;
-        reinterpret_cast<__nv_bfloat16 *>(pa.Ylo)[idx] = lo;
-    } else if (pa.split_kind == 2) {
-        float hi = tf32_round((float)yn);
-        float lo = tf32_round((float)(yn - (double)hi));
-        reinterpret_cast<float *>(pa.Yhi)[idx] = hi;
-        reinterpret_cast<float *>(pa.Ylo)[idx] = lo;
     }
 }
 
@@ -318,11 +288,11 @@ __global__ void split_kernel(const float *in, void *hi, void *lo, size_t count, 
         if (kind == 1) {
             __nv_bfloat16 h = __float2bfloat16_rn(v);
             reinterpret_cast<__nv_bfloat16 *>(hi)[i] = h;
-            reinterpret_cast<__nv_bfloat16 *>(lo)[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+            if (lo) reinterpret_cast<__nv_bfloat16 *>(lo)[i] = __float2bfloat16_rn(v - __bfloat162float(h));
         } else {
             float h = tf32_round(v);
             reinterpret_cast<float *>(hi)[i] = h;
-            reinterpret_cast<float *>(lo)[i] = tf32_round(v - h);
+            if (lo) reinterpret_cast<float *>(lo)[i] = tf32_round(v - h);
         }
     }
 }

@@ -251,3 +251,101 @@ def test_config3_full_size_operator_and_steps():
     Xg = s.solve_device(_cuda(b), pr.lam, 2).cpu().numpy()
     assert oracle.rel_fro(Xg, Xo) <= TOL["fp32"]
     s.close()
+
+
+# ------------------------------------------------------------------ tensor-core operator
+# Per-application relative error bounds of the operator by precision (the
+# split forms are near FP32; single BF16 / TF32 keep 8 / 11 significant bits).
+OP_TOL = {"bf16x3": 2e-5, "tf32x3": 2e-6, "bf16": 1e-2, "tf32": 2e-3}
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3", "bf16", "tf32"])
+@pytest.mark.parametrize("op", ["gemm_band", "gemm_dense"])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_gemm_apply_matches_oracle(prec, op, bc):
+    """tcgen05 GEMM operator (A_s and A_s^T) on a ragged 200x176 image, r=3, non-centred PSF."""
+    m, n = 200, 176
+    g = W.rng(201 + bc)
+    P = W.random_psf(g, 13, 11)
+    ka = kron.kron_approx(P, 4, 7, m, n, bc, 3)
+    s = api.Sfista(P, (m, n), bc, 3, center=(4, 7), prec=prec, op=op, lipschitz=1.0)
+    assert s.info()["op"] == op and s.info()["prec"] == prec
+    X = g.standard_normal((m, n)).astype(np.float32)
+    for tr in (False, True):
+        Y = s.apply(_cuda(X), transpose=tr).cpu().numpy()
+        Yo = (oracle.kron_apply_T if tr else oracle.kron_apply)(X.astype(np.float64), ka)
+        assert oracle.rel_fro(Y, Yo) < OP_TOL[prec], (prec, op, tr)
+    s.close()
+
+
+def test_gemm_band_and_dense_agree():
+    """Skipping K tiles outside the band changes nothing but summation order."""
+    P = W.rotated_gaussian_psf(31, 3.0, 1.0, np.deg2rad(30))
+    X = _cuda(W.rng(202).standard_normal((384, 256)))
+    ys = []
+    for op in ("gemm_band", "gemm_dense"):
+        s = api.Sfista(P, (384, 256), 1, 3, prec="bf16x3", op=op, lipschitz=1.0)
+        ys.append(s.apply(X).double())
+        s.close()
+    assert (torch.linalg.norm(ys[0] - ys[1]) / torch.linalg.norm(ys[1])).item() < 1e-6
+
+
+def test_gemm_rejects_unaligned_sizes():
+    P = W.gaussian_psf(9, 2.0)
+    with pytest.raises(api.SfistaError) as ei:
+        api.Sfista(P, (100, 60), 1, 1, prec="bf16x3", op="gemm_band", lipschitz=1.0)
+    assert ei.value.status == api.ENOTSUP
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_solve_config2_split_precision(cfg2, prec):
+    """512^2, r=3, 200 iterations, split-precision tensor-core operator: <= 1e-4 and 0.01 dB."""
+    pr, b, ka, L, Xo = cfg2
+    s = api.Sfista(pr.psf, (512, 512), pr.bc, pr.r, prec=prec, op="gemm_band", lipschitz=L)
+    X = s.solve_device(_cuda(b), pr.lam, pr.iters).cpu().numpy()
+    assert oracle.rel_fro(X, Xo) <= TOL[prec]
+    assert abs(oracle.psnr(X, pr.x_true) - oracle.psnr(Xo, pr.x_true)) <= 0.01
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_solve_config2_single_precision_reported(cfg2, prec):
+    """Single-product BF16 / TF32 are reported, not held to 1e-4: bounded and finite."""
+    pr, b, ka, L, Xo = cfg2
+    s = api.Sfista(pr.psf, (512, 512), pr.bc, pr.r, prec=prec, op="gemm_band", lipschitz=L)
+    X = s.solve_device(_cuda(b), pr.lam, pr.iters).cpu().numpy()
+    err = oracle.rel_fro(X, Xo)
+    assert np.isfinite(err) and err < 0.1
+    s.close()
+
+
+def test_gemm_solve_ragged_matches_oracle():
+    m, n = 200, 176
+    g = W.rng(203)
+    P = W.random_psf(g, 11, 9)
+    x, b, (cr, cc) = _problem(m, n, P, 1, 204, centre=(3, 5))
+    ka = kron.kron_approx(P, cr, cc, m, n, 1, 3)
+    L = _oracle_L(ka)
+    Xo = oracle.sfista(b.astype(np.float64), ka, L, 0.01, 60)
+    s = api.Sfista(P, (m, n), 1, 3, center=(cr, cc), prec="bf16x3", lipschitz=L)
+    X = s.solve_device(_cuda(b), 0.01, 60).cpu().numpy()
+    assert oracle.rel_fro(X, Xo) <= TOL["bf16x3"]
+    s.close()
+
+
+def test_config3_full_size_tensor_core():
+    """2048^2, r=5, 63x63 PSF: BF16x3 operator and 2 iterations vs the oracle."""
+    pr = W.config3()
+    cr, cc = pr.centre
+    n = 2048
+    ka = kron.kron_approx(pr.psf, cr, cc, n, n, pr.bc, pr.r)
+    s = api.Sfista(pr.psf, (n, n), pr.bc, pr.r, prec="bf16x3", op="gemm_band", lipschitz=1.0)
+    X = pr.x_true.astype(np.float32)
+    Y = s.apply(_cuda(X)).cpu().numpy()
+    assert oracle.rel_fro(Y, oracle.kron_apply(X.astype(np.float64), ka)) < OP_TOL["bf16x3"]
+    bx = oracle.blur(pr.x_true, pr.psf, cr, cc, pr.bc)
+    b = (bx + W.noise_scale(bx, pr.noise, pr.noise_level)).astype(np.float32)
+    Xo = oracle.sfista(b.astype(np.float64), ka, 1.0, pr.lam, 2)
+    Xg = s.solve_device(_cuda(b), pr.lam, 2).cpu().numpy()
+    assert oracle.rel_fro(Xg, Xo) <= TOL["bf16x3"]
+    s.close()
