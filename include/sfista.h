@@ -73,7 +73,9 @@ typedef enum {
     SFISTA_OP_AUTO = 0,        /* library's choice for (size, r, band, precision)           */
     SFISTA_OP_BANDED = 1,      /* factors applied from compact band storage (FP32/FP64 FMA)  */
     SFISTA_OP_GEMM_BAND = 2,   /* dense-factor GEMMs that skip K tiles outside the band       */
-    SFISTA_OP_GEMM_DENSE = 3   /* dense-factor GEMMs over the full K range (Sec. 3.3 O(s(nm^2+mn^2))) */
+    SFISTA_OP_GEMM_DENSE = 3,  /* dense-factor GEMMs over the full K range (Sec. 3.3 O(s(nm^2+mn^2))) */
+    SFISTA_OP_BANDED_FUSED = 4 /* banded FP32 operator, the whole iteration loop in one persistent
+                                  cooperative launch (grid barrier between the four phases) */
 } sfista_operator;
 
 typedef struct {
@@ -175,6 +177,36 @@ sfista_status sfista_solve_device(sfista_ctx *ctx, const float *d_b,
 sfista_status sfista_solve_state(sfista_ctx *ctx, const float *d_b,
                                  double lambda, int k0, int iters,
                                  double *d_X, double *d_Xprev, void *stream);
+
+/*
+ * Batched solves: many independent problems (any image sizes, PSFs, ranks,
+ * one precision and operator family) advance together, one launch per stage
+ * of Alg. 2 covering the tiles of every problem, the iteration loop replayed
+ * as one CUDA graph.
+ *
+ * sfista_batch_create -- group nprob contexts made by sfista_setup (same
+ *   device, same precision; all tensor-core forms or all banded forms).  The
+ *   batch uses each context's state buffers: do not solve with a grouped
+ *   context on its own while a batch solve of it is in flight.
+ * sfista_batch_solve -- Alg. 2 from X_0 = 0 for every problem.
+ *   d_b, d_x  host arrays of nprob device pointers (FP32, problem p is
+ *             m_p x n_p); lambdas host array of nprob values.
+ *   Asynchronous on `stream`; sfista_batch_sync reports device status of
+ *   every problem (the first error found).
+ * sfista_solve_batched -- create, solve, sync and destroy in one call.
+ */
+typedef struct sfista_batch sfista_batch;
+sfista_status sfista_batch_create(sfista_ctx *const *ctxs, int nprob,
+                                  sfista_batch **out);
+sfista_status sfista_batch_solve(sfista_batch *batch, const float *const *d_b,
+                                 const double *lambdas, int iters,
+                                 float *const *d_x, void *stream);
+sfista_status sfista_batch_sync(sfista_batch *batch, void *stream);
+void sfista_batch_destroy(sfista_batch *batch);
+sfista_status sfista_solve_batched(sfista_ctx *const *ctxs,
+                                   const float *const *d_b,
+                                   const double *lambdas, int nprob, int iters,
+                                   float *const *d_x, void *stream);
 
 /* Wait for the context's work on `stream`, then report device-side status
  * (ENUMERIC / ETIMEOUT) raised since the last sync. */

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libsfista.so")
 OK, EINVAL, ENOMEM, ECUDA, ENOTSUP, ENUMERIC, ETIMEOUT = range(7)
 BC = {"zero": 0, "reflexive": 1, "reflective": 1, "periodic": 2}
 PREC = {"fp32": 0, "tf32": 1, "tf32x3": 2, "bf16": 3, "bf16x3": 4}
-OP = {"auto": 0, "banded": 1, "gemm_band": 2, "gemm_dense": 3}
+OP = {"auto": 0, "banded": 1, "gemm_band": 2, "gemm_dense": 3, "banded_fused": 4}
 PREC_NAME = {v: k for k, v in PREC.items()}
 OP_NAME = {v: k for k, v in OP.items()}
 
@@ -63,6 +63,12 @@ def load(path=None):
     L.sfista_blur.argtypes = [vp, i, i, i, i, i, vp, i, i, vp, vp]
     L.sfista_time_stages.argtypes = [vp, vp, d, i, vp]
     L.sfista_apply_static.argtypes = [vp, vp, i, i, i, vp, i, i, vp, i, i, vp]
+    L.sfista_batch_create.argtypes = [vp, i, ctypes.POINTER(vp)]
+    L.sfista_batch_solve.argtypes = [vp, vp, vp, i, vp, vp]
+    L.sfista_batch_sync.argtypes = [vp, vp]
+    L.sfista_batch_destroy.argtypes = [vp]
+    L.sfista_batch_destroy.restype = None
+    L.sfista_solve_batched.argtypes = [vp, vp, vp, i, i, vp, vp]
     L.sfista_strerror.argtypes = [i]
     L.sfista_strerror.restype = ctypes.c_char_p
     L.sfista_last_error.argtypes = []
@@ -70,7 +76,8 @@ def load(path=None):
     for name in ("sfista_setup", "sfista_factorize", "sfista_solve", "sfista_solve_device", "sfista_solve_state",
                  "sfista_sync", "sfista_apply", "sfista_info", "sfista_get_profiles",
                  "sfista_get_factors", "sfista_blur", "sfista_time_stages",
-                 "sfista_apply_static"):
+                 "sfista_apply_static", "sfista_batch_create", "sfista_batch_solve", "sfista_batch_sync",
+                 "sfista_solve_batched"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -215,6 +222,68 @@ def sfista_apply_static(d_x, d_y, r, band_right, lo_right, band_left, lo_left, s
     _check(load().sfista_apply_static(_ptr(d_x), _ptr(d_y), m, n, int(r), _ptr(band_right), int(lo_right),
                                       int(band_right.shape[1]), _ptr(band_left), int(lo_left),
                                       int(band_left.shape[1]), _stream_ptr(stream)))
+
+
+def _ptr_array(ts):
+    arr = (ctypes.c_void_p * len(ts))()
+    for i, t in enumerate(ts):
+        arr[i] = _ptr(t).value
+    return arr
+
+
+def sfista_batch_create(ctxs):
+    arr = (ctypes.c_void_p * len(ctxs))(*ctxs)
+    h = ctypes.c_void_p()
+    _check(load().sfista_batch_create(arr, len(ctxs), ctypes.byref(h)))
+    return h.value
+
+
+def sfista_batch_solve(batch, d_bs, lambdas, iters, d_xs, stream=None):
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    _check(load().sfista_batch_solve(ctypes.c_void_p(batch), _ptr_array(d_bs), lam.ctypes.data, int(iters),
+                                     _ptr_array(d_xs), _stream_ptr(stream)))
+
+
+def sfista_batch_sync(batch, stream=None):
+    _check(load().sfista_batch_sync(ctypes.c_void_p(batch), _stream_ptr(stream)))
+
+
+def sfista_batch_destroy(batch):
+    load().sfista_batch_destroy(ctypes.c_void_p(batch))
+
+
+def sfista_solve_batched(ctxs, d_bs, lambdas, iters, d_xs, stream=None):
+    arr = (ctypes.c_void_p * len(ctxs))(*ctxs)
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    _check(load().sfista_solve_batched(arr, _ptr_array(d_bs), lam.ctypes.data, len(ctxs), int(iters),
+                                       _ptr_array(d_xs), _stream_ptr(stream)))
+
+
+class Batch:
+    """Groups Sfista objects: ``Batch([s1, s2, ...]).solve([b1, b2, ...], [lam1, ...], iters)``."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        self.handle = sfista_batch_create([s.ctx for s in self.solvers])
+
+    def solve(self, d_bs, lambdas, iters, outs=None, stream=None, sync=True):
+        import torch
+        outs = [torch.empty_like(b) for b in d_bs] if outs is None else outs
+        sfista_batch_solve(self.handle, d_bs, lambdas, iters, outs, stream)
+        if sync:
+            sfista_batch_sync(self.handle, stream)
+        return outs
+
+    def close(self):
+        if self.handle:
+            sfista_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------------------ convenience wrapper

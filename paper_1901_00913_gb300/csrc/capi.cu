@@ -94,6 +94,10 @@ struct sfista_ctx {
     std::vector<double> beta_host;
     // Tensor-core path (operand panels, intermediates, tensor maps).
     GemmPath *gemm = nullptr;
+    // Persistent solver launch shape and its grid-barrier words.
+    int pgrid = 0, prows_chunk = 1, pcols_chunk = 1;
+    size_t psmem = 0;
+    unsigned *bar = nullptr;
     // Cached CUDA graph of the iteration loop.
     cudaGraphExec_t gexec = nullptr;
     int g_k0 = -1, g_iters = -1;
@@ -109,7 +113,7 @@ void ctx_free(sfista_ctx *c) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->gemm) gemm_destroy(c->gemm);
     void *ptrs[] = {c->dA, c->dAT, c->dB, c->dBT, c->fA, c->fAT, c->fB, c->fBT, c->Bd, c->Yop, c->Z,
-                    c->R, c->tmp, c->Xb[0], c->Xb[1], c->Y, c->status, c->beta};
+                    c->R, c->tmp, c->Xb[0], c->Xb[1], c->Y, c->status, c->beta, c->bar};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
@@ -158,7 +162,7 @@ ProxArgs prox_args(sfista_ctx *c, int k, double lam) {
 // Stage `st` (0..3) of iteration k; see sfista_time_stages for the numbering.
 void enqueue_stage(sfista_ctx *c, int st, const ProxArgs &pa) {
     const HostSetup &h = c->hs;
-    if (c->op == SFISTA_OP_BANDED) {
+    if (c->op == SFISTA_OP_BANDED || c->op == SFISTA_OP_BANDED_FUSED) {
         switch (st) {
             case 0: launch_band_rows<float>(c->Yop, c->m, c->n, c->fA, h.A.lo, h.A.w, c->r, c->Z, c->stream); break;
             case 1: launch_band_cols<float>(c->Z, c->m, c->n, c->fB, h.B.lo, h.B.w, c->r, EPI_RESIDUAL, c->R, pa,
@@ -179,6 +183,13 @@ void enqueue_iteration(sfista_ctx *c, int k, double lam) {
 
 sfista_status run_loop(sfista_ctx *c, double lam, int k0, int iters) {
     if (iters <= 0) return SFISTA_OK;
+    if (c->op == SFISTA_OP_BANDED_FUSED) {
+        const HostSetup &h = c->hs;
+        ProxArgs pa = prox_args(c, k0 + 1, lam);
+        SF_CUDA(launch_persistent(c->pgrid, c->psmem, c->prows_chunk, c->pcols_chunk, c->m, c->n, c->r, c->fA, h.A, c->fB, h.B, c->fAT, h.AT, c->fBT,
+                                  h.BT, c->Z, c->R, c->Xb[0], c->Xb[1], pa, k0, iters, c->bar, c->stream));
+        return SFISTA_OK;
+    }
     if (!c->opts.use_graph) {
         for (int k = k0 + 1; k <= k0 + iters; ++k) enqueue_iteration(c, k, lam);
         SF_CUDA(cudaGetLastError());
@@ -319,6 +330,48 @@ sfista_status finish_on_user(sfista_ctx *c, cudaStream_t user) {
 
 }  // namespace
 
+
+struct sfista_batch {
+    std::vector<sfista_ctx *> ctxs;
+    int dev = 0;
+    bool gemm = false;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    GemmBatch *gb = nullptr;
+    BandProb *d_probs = nullptr;
+    std::vector<BandProb> h_probs;
+    BandItem *d_items[4] = {nullptr, nullptr, nullptr, nullptr};
+    int nitems[4] = {0, 0, 0, 0};
+    size_t smem = 0;
+    cudaGraphExec_t gexec = nullptr;
+    int g_iters = -1;
+    std::vector<double> g_lams;
+};
+
+namespace {
+
+void batch_free(sfista_batch *b) {
+    if (!b) return;
+    DeviceGuard g(b->dev);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->gb) gemm_batch_destroy(b->gb);
+    if (b->d_probs) cudaFree(b->d_probs);
+    for (int st = 0; st < 4; ++st)
+        if (b->d_items[st]) cudaFree(b->d_items[st]);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+void batch_stage(sfista_batch *b, int st, int k) {
+    if (b->gemm) gemm_batch_stage(b->gb, st, k, b->stream);
+    else launch_band_grouped_stage(st, b->d_probs, b->d_items[st], b->nitems[st], k, b->smem, b->stream);
+}
+
+}  // namespace
+
 extern "C" {
 
 void sfista_default_opts(sfista_opts *o) {
@@ -343,7 +396,7 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int ce
     sfista_default_opts(&o);
     if (opts) o = *opts;
     if (o.prec < SFISTA_FP32 || o.prec > SFISTA_BF16X3) return fail(SFISTA_EINVAL, "unknown precision");
-    if (o.op < SFISTA_OP_AUTO || o.op > SFISTA_OP_GEMM_DENSE) return fail(SFISTA_EINVAL, "unknown operator form");
+    if (o.op < SFISTA_OP_AUTO || o.op > SFISTA_OP_BANDED_FUSED) return fail(SFISTA_EINVAL, "unknown operator form");
     if (!(o.lipschitz <= 0.0 || isfinite(o.lipschitz))) return fail(SFISTA_EINVAL, "lipschitz must be finite");
     if (center_row == -1 && psf_rows > 0) center_row = (psf_rows - 1) / 2;
     if (center_col == -1 && psf_cols > 0) center_col = (psf_cols - 1) / 2;
@@ -363,7 +416,7 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int ce
     c->prec = o.prec;
     c->op = o.op;
     if (c->op == SFISTA_OP_AUTO) c->op = (c->prec == SFISTA_FP32) ? SFISTA_OP_BANDED : SFISTA_OP_GEMM_BAND;
-    if (c->op == SFISTA_OP_BANDED && c->prec != SFISTA_FP32) {
+    if ((c->op == SFISTA_OP_BANDED || c->op == SFISTA_OP_BANDED_FUSED) && c->prec != SFISTA_FP32) {
         delete c;
         return fail(SFISTA_ENOTSUP, "the banded operator form runs in FP32 only");
     }
@@ -409,7 +462,14 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int ce
         (e = cudaMalloc((void **)&c->status, 16)))
         return bail(fail(SFISTA_ENOMEM, std::string("state buffers: ") + cudaGetErrorString(e)));
     if ((e = cudaMemset(c->status, 0, 16))) return bail(fail(SFISTA_ECUDA, cudaGetErrorString(e)));
-    if (c->op != SFISTA_OP_BANDED) {
+    if (c->op == SFISTA_OP_BANDED_FUSED) {
+        if ((e = cudaMalloc((void **)&c->bar, 16)) || (e = cudaMemset(c->bar, 0, 16)))
+            return bail(fail(SFISTA_ENOMEM, std::string("barrier words: ") + cudaGetErrorString(e)));
+        st = persistent_config(c->m, c->n, c->r, wmax, c->dev, &c->pgrid, &c->psmem, &c->prows_chunk,
+                               &c->pcols_chunk);
+        if (st) return bail(st);
+    }
+    if (c->op == SFISTA_OP_GEMM_BAND || c->op == SFISTA_OP_GEMM_DENSE) {
         st = gemm_create(&c->gemm, h, c->prec, c->op == SFISTA_OP_GEMM_DENSE, c->status, c->stream);
         if (st) return bail(st);
     }
@@ -504,7 +564,7 @@ sfista_status sfista_apply(sfista_ctx *c, const float *d_x, float *d_y, int tran
     SF_CUDA(cudaStreamWaitEvent(c->stream, c->ev_in, 0));
     const HostSetup &h = c->hs;
     ProxArgs pa{};
-    if (c->op == SFISTA_OP_BANDED) {
+    if (c->op == SFISTA_OP_BANDED || c->op == SFISTA_OP_BANDED_FUSED) {
         const Band &F = transpose ? h.AT : h.A;
         const Band &G = transpose ? h.BT : h.B;
         launch_band_rows<float>(d_x, c->m, c->n, transpose ? c->fAT : c->fA, F.lo, F.w, c->r, c->Z, c->stream);
@@ -593,17 +653,249 @@ sfista_status sfista_blur(const double *psf, int p, int q, int cr, int cc, int b
     return SFISTA_OK;
 }
 
+
+sfista_status sfista_batch_create(sfista_ctx *const *ctxs, int nprob, sfista_batch **out) {
+    if (!out) return fail(SFISTA_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!ctxs || nprob < 1) return fail(SFISTA_EINVAL, "no problems");
+    for (int p = 0; p < nprob; ++p)
+        if (!ctxs[p]) return fail(SFISTA_EINVAL, "a context is NULL");
+    const bool gemm = ctxs[0]->op == SFISTA_OP_GEMM_BAND || ctxs[0]->op == SFISTA_OP_GEMM_DENSE;
+    for (int p = 0; p < nprob; ++p) {
+        const bool gp = ctxs[p]->op == SFISTA_OP_GEMM_BAND || ctxs[p]->op == SFISTA_OP_GEMM_DENSE;
+        if (gp != gemm || ctxs[p]->prec != ctxs[0]->prec || ctxs[p]->dev != ctxs[0]->dev)
+            return fail(SFISTA_EINVAL, "batched problems need one device, one precision and one operator family");
+        for (int q = 0; q < p; ++q)
+            if (ctxs[q] == ctxs[p]) return fail(SFISTA_EINVAL, "a context appears twice in the batch");
+    }
+    sfista_batch *b = new (std::nothrow) sfista_batch();
+    if (!b) return fail(SFISTA_ENOMEM, "batch allocation failed");
+    b->ctxs.assign(ctxs, ctxs + nprob);
+    b->dev = ctxs[0]->dev;
+    b->gemm = gemm;
+    DeviceGuard g(b->dev);
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking)) ||
+        (e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming)) ||
+        (e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming))) {
+        batch_free(b);
+        return fail(SFISTA_ECUDA, std::string("batch stream: ") + cudaGetErrorString(e));
+    }
+    if (gemm) {
+        std::vector<GemmPath *> paths(nprob);
+        for (int p = 0; p < nprob; ++p) paths[p] = ctxs[p]->gemm;
+        sfista_status st = gemm_batch_create(&b->gb, paths.data(), nprob, b->stream);
+        if (st) {
+            batch_free(b);
+            return st;
+        }
+    } else {
+        b->h_probs.resize(nprob);
+        std::vector<BandItem> items[4];
+        std::vector<int> order(nprob);
+        for (int p = 0; p < nprob; ++p) order[p] = p;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            return (double)ctxs[x]->N * ctxs[x]->r > (double)ctxs[y]->N * ctxs[y]->r;
+        });
+        for (int p = 0; p < nprob; ++p) {
+            sfista_ctx *c = ctxs[p];
+            const HostSetup &h = c->hs;
+            BandProb &P = b->h_probs[p];
+            P = BandProb{};
+            P.m = c->m;
+            P.n = c->n;
+            P.r = c->r;
+            int wmax = std::max(std::max(h.A.w, h.AT.w), std::max(h.B.w, h.BT.w));
+            size_t sm = 0;
+            persistent_chunks(c->r, wmax, &P.rows_chunk, &P.cols_chunk, &sm);
+            b->smem = std::max(b->smem, sm);
+            P.fA = c->fA;
+            P.fB = c->fB;
+            P.fAT = c->fAT;
+            P.fBT = c->fBT;
+            P.loA = h.A.lo;
+            P.wA = h.A.w;
+            P.loB = h.B.lo;
+            P.wB = h.B.w;
+            P.loAT = h.AT.lo;
+            P.wAT = h.AT.w;
+            P.loBT = h.BT.lo;
+            P.wBT = h.BT.w;
+            P.Z = c->Z;
+            P.R = c->R;
+        }
+        for (int p : order) {
+            const BandProb &P = b->h_probs[p];
+            const int nq = (P.r + P.rows_chunk - 1) / P.rows_chunk;
+            for (int q = 0; q < nq; ++q)
+                for (int t = 0; t < band_rows_tiles(P.m, P.n); ++t) items[0].push_back(BandItem{p, q, t, 0});
+            for (int t = 0; t < band_cols_tiles(P.m, P.n); ++t) items[1].push_back(BandItem{p, 0, t, 0});
+        }
+        items[2] = items[0];
+        items[3] = items[1];
+        if ((e = band_grouped_prepare(b->smem)) ||
+            (e = cudaMalloc((void **)&b->d_probs, nprob * sizeof(BandProb)))) {
+            batch_free(b);
+            return fail(SFISTA_ENOTSUP, std::string("grouped banded tables: ") + cudaGetErrorString(e));
+        }
+        for (int st = 0; st < 4; ++st) {
+            b->nitems[st] = (int)items[st].size();
+            if ((e = cudaMalloc((void **)&b->d_items[st], items[st].size() * sizeof(BandItem))) ||
+                (e = cudaMemcpy(b->d_items[st], items[st].data(), items[st].size() * sizeof(BandItem),
+                                cudaMemcpyHostToDevice))) {
+                batch_free(b);
+                return fail(SFISTA_ENOMEM, std::string("grouped work lists: ") + cudaGetErrorString(e));
+            }
+        }
+    }
+    *out = b;
+    return SFISTA_OK;
+}
+
+void sfista_batch_destroy(sfista_batch *b) { batch_free(b); }
+
+sfista_status sfista_batch_solve(sfista_batch *b, const float *const *d_b, const double *lambdas, int iters,
+                                 float *const *d_x, void *stream) {
+    if (!b) return fail(SFISTA_EINVAL, "batch is NULL");
+    if (!d_b || !lambdas || !d_x) return fail(SFISTA_EINVAL, "NULL argument array");
+    if (iters < 0) return fail(SFISTA_EINVAL, "iters must be >= 0");
+    const int np = (int)b->ctxs.size();
+    for (int p = 0; p < np; ++p) {
+        if (!d_b[p] || !d_x[p]) return fail(SFISTA_EINVAL, "NULL observation or output pointer");
+        if (!(lambdas[p] >= 0) || !isfinite(lambdas[p])) return fail(SFISTA_EINVAL, "lambda must be finite and >= 0");
+    }
+    DeviceGuard g(b->dev);
+    cudaStream_t user = (cudaStream_t)stream;
+    for (int p = 0; p < np; ++p) {
+        sfista_ctx *c = b->ctxs[p];
+        sfista_status st = ensure_beta(c, iters + 1);
+        if (st) return st;
+    }
+    SF_CUDA(cudaEventRecord(b->ev_in, user));
+    SF_CUDA(cudaStreamWaitEvent(b->stream, b->ev_in, 0));
+    std::vector<ProxArgs> pas(np);
+    std::vector<const float *> bds(np);
+    for (int p = 0; p < np; ++p) {
+        sfista_ctx *c = b->ctxs[p];
+        SF_CUDA(cudaMemcpyAsync(c->Bd, d_b[p], c->N * sizeof(float), cudaMemcpyDeviceToDevice, b->stream));
+        launch_check_finite(c->Bd, c->N, c->status, b->stream);
+        SF_CUDA(cudaMemsetAsync(c->Xb[0], 0, c->N * 8, b->stream));
+        SF_CUDA(cudaMemsetAsync(c->Xb[1], 0, c->N * 8, b->stream));
+        void *yhi = nullptr, *ylo = nullptr;
+        int split = 0;
+        if (c->gemm) gemm_state_operands(c->gemm, &yhi, &ylo, &split);
+        init_state_kernel<<<256, 256, 0, b->stream>>>(c->Xb[0], c->Xb[1], c->Y, c->Yop, yhi, ylo, split, c->N, 0.0);
+        ProxArgs pa = prox_args(c, 1, lambdas[p]);
+        pa.Xin = c->Xb[0];
+        pa.Xout = c->Xb[1];
+        pas[p] = pa;
+        bds[p] = c->Bd;
+    }
+    if (b->gemm) {
+        sfista_status st = gemm_batch_bind(b->gb, bds.data(), pas.data(), b->stream);
+        if (st) return st;
+    } else {
+        for (int p = 0; p < np; ++p) b->h_probs[p].pa = pas[p];
+        SF_CUDA(cudaMemcpyAsync(b->d_probs, b->h_probs.data(), np * sizeof(BandProb), cudaMemcpyHostToDevice,
+                                b->stream));
+        SF_CUDA(cudaStreamSynchronize(b->stream));   // host staging array is reused on the next solve
+    }
+    if (iters > 0) {
+        std::vector<double> lams(lambdas, lambdas + np);
+        if (!(b->gexec && b->g_iters == iters && b->g_lams == lams)) {
+            if (b->gexec) {
+                cudaGraphExecDestroy(b->gexec);
+                b->gexec = nullptr;
+            }
+            cudaGraph_t graph = nullptr;
+            SF_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            for (int k = 1; k <= iters; ++k)
+                for (int st = 0; st < 4; ++st) batch_stage(b, st, k);
+            cudaError_t le = cudaGetLastError();
+            cudaError_t ee = cudaStreamEndCapture(b->stream, &graph);
+            if (le || ee) {
+                if (graph) cudaGraphDestroy(graph);
+                return fail(SFISTA_ECUDA, std::string("batch graph capture: ") + cudaGetErrorString(le ? le : ee));
+            }
+            cudaError_t ie = cudaGraphInstantiate(&b->gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie) {
+                b->gexec = nullptr;
+                return fail(SFISTA_ECUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(ie));
+            }
+            b->g_iters = iters;
+            b->g_lams = lams;
+        }
+        SF_CUDA(cudaGraphLaunch(b->gexec, b->stream));
+    }
+    for (int p = 0; p < np; ++p) {
+        sfista_ctx *c = b->ctxs[p];
+        launch_f64_to_f32(c->Xb[iters & 1], d_x[p], c->N, b->stream);
+    }
+    SF_CUDA(cudaGetLastError());
+    SF_CUDA(cudaEventRecord(b->ev_out, b->stream));
+    SF_CUDA(cudaStreamWaitEvent(user, b->ev_out, 0));
+    return SFISTA_OK;
+}
+
+sfista_status sfista_batch_sync(sfista_batch *b, void *stream) {
+    if (!b) return fail(SFISTA_EINVAL, "batch is NULL");
+    DeviceGuard g(b->dev);
+    SF_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    SF_CUDA(cudaStreamSynchronize(b->stream));
+    sfista_status worst = SFISTA_OK;
+    for (sfista_ctx *c : b->ctxs) {
+        sfista_status st = drain_status(c);
+        if (st && !worst) worst = st;
+    }
+    return worst;
+}
+
+sfista_status sfista_solve_batched(sfista_ctx *const *ctxs, const float *const *d_b, const double *lambdas,
+                                   int nprob, int iters, float *const *d_x, void *stream) {
+    sfista_batch *b = nullptr;
+    sfista_status st = sfista_batch_create(ctxs, nprob, &b);
+    if (st) return st;
+    st = sfista_batch_solve(b, d_b, lambdas, iters, d_x, stream);
+    if (!st) st = sfista_batch_sync(b, stream);
+    batch_free(b);
+    return st;
+}
+
 sfista_status sfista_time_stages(sfista_ctx *c, const float *d_b, double lambda, int reps, float *ms) {
     sfista_status st = check_ctx(c);
     if (st) return st;
     if (!ms || reps < 1) return fail(SFISTA_EINVAL, "ms is NULL or reps < 1");
     DeviceGuard g(c->dev);
+    st = ensure_beta(c, reps + 1);
+    if (st) return st;
     st = solve_core(c, d_b, lambda, 0, 0, nullptr, nullptr, c->stream);
     if (st) return st;
     cudaEvent_t ev[5];
     for (int i = 0; i < 5; ++i) SF_CUDA(cudaEventCreate(&ev[i]));
     double acc[4] = {0, 0, 0, 0};
     cudaError_t e = cudaSuccess;
+    if (c->op == SFISTA_OP_BANDED_FUSED) {
+        // One persistent launch covers all four stages: report its mean time
+        // per iteration in slot 0.
+        e = cudaEventRecord(ev[0], c->stream);
+        if (!e) {
+            sfista_status rs = run_loop(c, lambda, 0, reps);
+            if (rs) {
+                for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
+                return rs;
+            }
+            e = cudaEventRecord(ev[1], c->stream);
+        }
+        if (!e) e = cudaEventSynchronize(ev[1]);
+        float t = 0;
+        if (!e) e = cudaEventElapsedTime(&t, ev[0], ev[1]);
+        for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
+        if (e) return fail(SFISTA_ECUDA, std::string("stage timing: ") + cudaGetErrorString(e));
+        ms[0] = t / reps;
+        ms[1] = ms[2] = ms[3] = 0.0f;
+        return drain_status(c);
+    }
     for (int k = 1; k <= reps && !e; ++k) {
         ProxArgs pa = prox_args(c, k, lambda);
         e = cudaEventRecord(ev[0], c->stream);

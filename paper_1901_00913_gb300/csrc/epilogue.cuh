@@ -16,8 +16,8 @@ static __device__ __forceinline__ float tf32_round(float x) {
 
 // Step 1 shrink (+ projection) and Step 3 momentum for one pixel, FP64 state.
 static __device__ __forceinline__ void prox_momentum(const ProxArgs &pa, size_t idx, double g) {
-    double y = pa.Y[idx];
-    double xprev = pa.Xin[idx];
+    double y = __ldcg(pa.Y + idx);
+    double xprev = __ldcg(pa.Xin + idx);
     // (L y - g) / (L + lambda^2) with the two constants folded on the host
     double x = fma(pa.shrink, y, -pa.inv_den * g);
     if (pa.project && x < 0.0) x = 0.0;
@@ -42,8 +42,8 @@ static __device__ __forceinline__ void prox_momentum(const ProxArgs &pa, size_t 
 
 // Two neighbouring pixels idx, idx + 1 (idx even): vector loads and stores.
 static __device__ __forceinline__ void prox_momentum2(const ProxArgs &pa, size_t idx, double g0, double g1) {
-    const double2 y = *reinterpret_cast<const double2 *>(pa.Y + idx);
-    const double2 xp = *reinterpret_cast<const double2 *>(pa.Xin + idx);
+    const double2 y = __ldcg(reinterpret_cast<const double2 *>(pa.Y + idx));
+    const double2 xp = __ldcg(reinterpret_cast<const double2 *>(pa.Xin + idx));
     double x0 = fma(pa.shrink, y.x, -pa.inv_den * g0);
     double x1 = fma(pa.shrink, y.y, -pa.inv_den * g1);
     if (pa.project) {

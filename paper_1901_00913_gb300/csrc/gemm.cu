@@ -32,6 +32,7 @@
 
 #include <algorithm>
 #include <string>
+#include <vector>
 
 #include "epilogue.cuh"
 #include "gemm.h"
@@ -187,11 +188,13 @@ __device__ __forceinline__ void store_split2(void *hi, void *lo, int kind, size_
     }
 }
 
+// One output tile (M tile index mt counting terms for stacked stages, N tile
+// index nt) of one GEMM stage.  The tensor maps may live in kernel parameter
+// space (single problem) or in global memory (grouped launch).
 template <int FMT, bool SPLIT, int BN, int EPI>
-__global__ void __launch_bounds__(192, 1)
-    umma_gemm_kernel(const __grid_constant__ CUtensorMap tPhi, const __grid_constant__ CUtensorMap tPlo,
-                     const __grid_constant__ CUtensorMap tQhi, const __grid_constant__ CUtensorMap tQlo,
-                     GemmArgs g) {
+__device__ __forceinline__ void umma_gemm_tile(const CUtensorMap *pPhi, const CUtensorMap *pPlo,
+                                               const CUtensorMap *pQhi, const CUtensorMap *pQlo, const GemmArgs &g,
+                                               int mt, int ntile) {
     using C = Cfg<FMT, SPLIT, BN>;
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bars[2 * C::STAGES + 1];
@@ -199,10 +202,9 @@ __global__ void __launch_bounds__(192, 1)
 
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int mt = blockIdx.y;
     const int term = g.type_b ? 0 : mt / g.m_tiles;
     const int m0 = (mt % g.m_tiles) * BM;
-    const int n0 = blockIdx.x * BN;
+    const int n0 = ntile * BN;
 
     int k_lo = 0, k_hi = g.K;
     if (!g.dense) {
@@ -249,10 +251,10 @@ __global__ void __launch_bounds__(192, 1)
                 const int pz = g.type_b ? seg : term;
                 const int qz = g.type_b ? seg : 0;
                 const uint32_t base = smem_u32(smem + s * C::STAGE_BYTES);
-                tma_load_3d(base, &tPhi, fb, kx, m0, pz);
-                if (SPLIT) tma_load_3d(base + C::P_BYTES, &tPlo, fb, kx, m0, pz);
-                tma_load_3d(base + C::NOP * C::P_BYTES, &tQhi, fb, kx, n0, qz);
-                if (SPLIT) tma_load_3d(base + C::NOP * C::P_BYTES + C::Q_BYTES, &tQlo, fb, kx, n0, qz);
+                tma_load_3d(base, pPhi, fb, kx, m0, pz);
+                if (SPLIT) tma_load_3d(base + C::P_BYTES, pPlo, fb, kx, m0, pz);
+                tma_load_3d(base + C::NOP * C::P_BYTES, pQhi, fb, kx, n0, qz);
+                if (SPLIT) tma_load_3d(base + C::NOP * C::P_BYTES + C::Q_BYTES, pQlo, fb, kx, n0, qz);
                 issued = it + 1;
             }
             // Drain: the last fill of every stage has landed before the CTA can exit.
@@ -338,6 +340,37 @@ __global__ void __launch_bounds__(192, 1)
     }
 }
 
+template <int FMT, bool SPLIT, int BN, int EPI>
+__global__ void __launch_bounds__(192, 1)
+    umma_gemm_kernel(const __grid_constant__ CUtensorMap tPhi, const __grid_constant__ CUtensorMap tPlo,
+                     const __grid_constant__ CUtensorMap tQhi, const __grid_constant__ CUtensorMap tQlo,
+                     GemmArgs g) {
+    umma_gemm_tile<FMT, SPLIT, BN, EPI>(&tPhi, &tPlo, &tQhi, &tQlo, g, blockIdx.y, blockIdx.x);
+}
+
+// Grouped launch: block b runs tile work[b] of problem work[b].prob, whose
+// four tensor maps (P hi, P lo, Q hi, Q lo) and arguments live in global
+// memory.  For the prox epilogue, k selects X_{k-1} / X_k among the
+// problem's two state buffers (stored in pa.Xin / pa.Xout as buffers 0 / 1).
+struct WorkItem {
+    int prob, mt, nt, pad;
+};
+
+template <int FMT, bool SPLIT, int BN, int EPI>
+__global__ void __launch_bounds__(192, 1)
+    umma_gemm_grouped(const CUtensorMap *maps, const GemmArgs *args, const WorkItem *work, int k) {
+    const WorkItem w = work[blockIdx.x];
+    GemmArgs g = args[w.prob];
+    if (EPI == GE_PROX) {
+        double *b0 = const_cast<double *>(g.pa.Xin), *b1 = g.pa.Xout;
+        g.pa.k = k;
+        g.pa.Xin = (k - 1) & 1 ? b1 : b0;
+        g.pa.Xout = k & 1 ? b1 : b0;
+    }
+    const CUtensorMap *m4 = maps + 4 * w.prob;
+    umma_gemm_tile<FMT, SPLIT, BN, EPI>(m4, m4 + 1, m4 + 2, m4 + 3, g, w.mt, w.nt);
+}
+
 // ------------------------------------------------------------------ host side
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
@@ -397,8 +430,11 @@ constexpr int BN_TILE = 128;
 
 template <int FMT, bool SPLIT, int EPI>
 cudaError_t set_attr() {
-    return cudaFuncSetAttribute(umma_gemm_kernel<FMT, SPLIT, BN_TILE, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                Cfg<FMT, SPLIT, BN_TILE>::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(umma_gemm_kernel<FMT, SPLIT, BN_TILE, EPI>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<FMT, SPLIT, BN_TILE>::SMEM);
+    if (e) return e;
+    return cudaFuncSetAttribute(umma_gemm_grouped<FMT, SPLIT, BN_TILE, EPI>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<FMT, SPLIT, BN_TILE>::SMEM);
 }
 
 template <int FMT, bool SPLIT>
@@ -439,8 +475,7 @@ GemmArgs base_args(const GemmPath *g) {
 }
 
 // Stage 0 / 2: out[term][row][col] = sum_k P_term[row][k] Q[col][k] (terms along M).
-sfista_status run_stacked(const GemmPath *g, const Operand &P, const Band &band, const Operand &Q, Operand &Out,
-                          cudaStream_t s) {
+GemmArgs stacked_args(const GemmPath *g, const Band &band, Operand &Out, int *gx, int *gy) {
     GemmArgs a = base_args(g);
     a.rows = g->n;
     a.m_tiles = (g->n + BM - 1) / BM;
@@ -452,22 +487,38 @@ sfista_status run_stacked(const GemmPath *g, const Operand &P, const Band &band,
     a.type_b = 0;
     a.out_hi = Out.hi;
     a.out_lo = Out.lo;
-    return dispatch<GE_SPLIT>(g, P, Q, a, (g->m + BN_TILE - 1) / BN_TILE, a.m_tiles * g->r, s);
+    *gx = (g->m + BN_TILE - 1) / BN_TILE;
+    *gy = a.m_tiles * g->r;
+    return a;
 }
 
 // Stage 1 / 3: out[row][col] = sum_{t, k} P_t[row][k] Q_t[col][k] (terms along K).
+void summed_args(const GemmPath *g, const Band &band, GemmArgs *a, int *gx, int *gy) {
+    a->rows = g->m;
+    a->m_tiles = (g->m + BM - 1) / BM;
+    a->N = g->n;
+    a->K = g->m;
+    a->band_lo = band.lo;
+    a->band_hi = band.lo + band.w - 1;
+    a->segs = g->r;
+    a->type_b = 1;
+    *gx = (g->n + BN_TILE - 1) / BN_TILE;
+    *gy = a->m_tiles;
+}
+
+sfista_status run_stacked(const GemmPath *g, const Operand &P, const Band &band, const Operand &Q, Operand &Out,
+                          cudaStream_t s) {
+    int gx, gy;
+    GemmArgs a = stacked_args(g, band, Out, &gx, &gy);
+    return dispatch<GE_SPLIT>(g, P, Q, a, gx, gy, s);
+}
+
 template <int EPI>
 sfista_status run_summed(const GemmPath *g, const Operand &P, const Band &band, const Operand &Q, GemmArgs a,
                          cudaStream_t s) {
-    a.rows = g->m;
-    a.m_tiles = (g->m + BM - 1) / BM;
-    a.N = g->n;
-    a.K = g->m;
-    a.band_lo = band.lo;
-    a.band_hi = band.lo + band.w - 1;
-    a.segs = g->r;
-    a.type_b = 1;
-    return dispatch<EPI>(g, P, Q, a, (g->n + BN_TILE - 1) / BN_TILE, a.m_tiles, s);
+    int gx, gy;
+    summed_args(g, band, &a, &gx, &gy);
+    return dispatch<EPI>(g, P, Q, a, gx, gy, s);
 }
 
 cudaError_t alloc_operand(Operand *o, size_t elems, size_t es, bool split) {
@@ -606,6 +657,163 @@ void gemm_stage(GemmPath *g, int st, const ProxArgs &pa_in, cudaStream_t s) {
         }
     }
 }
+
+// ------------------------------------------------------------------ grouped (batched) launches
+struct GemmBatch {
+    int nprob = 0, fmt = FMT_BF16;
+    bool split = true;
+    std::vector<GemmPath *> paths;
+    CUtensorMap *d_maps[4] = {nullptr, nullptr, nullptr, nullptr};   // per stage: nprob x 4
+    GemmArgs *d_args[4] = {nullptr, nullptr, nullptr, nullptr};
+    std::vector<GemmArgs> h_args[4];
+    WorkItem *d_work[4] = {nullptr, nullptr, nullptr, nullptr};
+    int nwork[4] = {0, 0, 0, 0};
+};
+
+void gemm_batch_destroy(GemmBatch *b) {
+    if (!b) return;
+    for (int st = 0; st < 4; ++st) {
+        if (b->d_maps[st]) cudaFree(b->d_maps[st]);
+        if (b->d_args[st]) cudaFree(b->d_args[st]);
+        if (b->d_work[st]) cudaFree(b->d_work[st]);
+    }
+    delete b;
+}
+
+sfista_status gemm_batch_create(GemmBatch **out, GemmPath *const *paths, int nprob, cudaStream_t s) {
+    *out = nullptr;
+    if (nprob < 1) return fail(SFISTA_EINVAL, "empty batch");
+    GemmBatch *b = new (std::nothrow) GemmBatch();
+    if (!b) return fail(SFISTA_ENOMEM, "batch allocation failed");
+    b->nprob = nprob;
+    b->fmt = paths[0]->fmt;
+    b->split = paths[0]->split;
+    b->paths.assign(paths, paths + nprob);
+    for (int p = 0; p < nprob; ++p)
+        if (paths[p]->fmt != b->fmt || paths[p]->split != b->split) {
+            gemm_batch_destroy(b);
+            return fail(SFISTA_EINVAL, "all problems of a batch need the same precision");
+        }
+    // Problems in decreasing order of work so the largest tiles start first.
+    std::vector<int> order(nprob);
+    for (int p = 0; p < nprob; ++p) order[p] = p;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const GemmPath *a = paths[x], *c = paths[y];
+        return (double)a->m * a->n * a->r > (double)c->m * c->n * c->r;
+    });
+    cudaError_t e = cudaSuccess;
+    for (int st = 0; st < 4 && !e; ++st) {
+        std::vector<CUtensorMap> maps(4 * (size_t)nprob);
+        std::vector<WorkItem> work;
+        b->h_args[st].resize(nprob);
+        for (int p = 0; p < nprob; ++p) {
+            GemmPath *g = paths[p];
+            const Operand *P = nullptr, *Q = nullptr;
+            int gx = 0, gy = 0;
+            GemmArgs a{};
+            if (st == 0) {
+                a = stacked_args(g, g->bandA, g->QT, &gx, &gy);
+                P = &g->PA;
+                Q = &g->QY;
+            } else if (st == 1) {
+                a = base_args(g);
+                a.out_hi = g->QR.hi;
+                a.out_lo = g->QR.lo;
+                summed_args(g, g->bandB, &a, &gx, &gy);
+                P = &g->PB;
+                Q = &g->QT;
+            } else if (st == 2) {
+                a = stacked_args(g, g->bandAT, g->QU, &gx, &gy);
+                P = &g->PAT;
+                Q = &g->QR;
+            } else {
+                a = base_args(g);
+                summed_args(g, g->bandBT, &a, &gx, &gy);
+                P = &g->PBT;
+                Q = &g->QU;
+            }
+            b->h_args[st][p] = a;
+            maps[4 * p + 0] = P->map_hi;
+            maps[4 * p + 1] = b->split ? P->map_lo : P->map_hi;
+            maps[4 * p + 2] = Q->map_hi;
+            maps[4 * p + 3] = b->split ? Q->map_lo : Q->map_hi;
+        }
+        for (int p : order) {
+            GemmPath *g = paths[p];
+            int gx = 0, gy = 0;
+            if (st == 0 || st == 2) {
+                gx = (g->m + BN_TILE - 1) / BN_TILE;
+                gy = ((g->n + BM - 1) / BM) * g->r;
+            } else {
+                gx = (g->n + BN_TILE - 1) / BN_TILE;
+                gy = (g->m + BM - 1) / BM;
+            }
+            for (int mt = 0; mt < gy; ++mt)
+                for (int nt = 0; nt < gx; ++nt) work.push_back(WorkItem{p, mt, nt, 0});
+        }
+        b->nwork[st] = (int)work.size();
+        if ((e = cudaMalloc((void **)&b->d_maps[st], maps.size() * sizeof(CUtensorMap)))) break;
+        if ((e = cudaMalloc((void **)&b->d_args[st], nprob * sizeof(GemmArgs)))) break;
+        if ((e = cudaMalloc((void **)&b->d_work[st], work.size() * sizeof(WorkItem)))) break;
+        if ((e = cudaMemcpyAsync(b->d_maps[st], maps.data(), maps.size() * sizeof(CUtensorMap),
+                                 cudaMemcpyHostToDevice, s)))
+            break;
+        if ((e = cudaMemcpyAsync(b->d_work[st], work.data(), work.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
+                                 s)))
+            break;
+        e = cudaStreamSynchronize(s);
+    }
+    if (e) {
+        gemm_batch_destroy(b);
+        return fail(SFISTA_ENOMEM, std::string("batch tables: ") + cudaGetErrorString(e));
+    }
+    *out = b;
+    return SFISTA_OK;
+}
+
+// Per solve: observation pointers and the prox arguments of every problem
+// (pa.Xin / pa.Xout hold the problem's state buffers 0 / 1).
+sfista_status gemm_batch_bind(GemmBatch *b, const float *const *Bds, const ProxArgs *pas, cudaStream_t s) {
+    for (int p = 0; p < b->nprob; ++p) {
+        GemmPath *g = b->paths[p];
+        b->h_args[1][p].Bd = Bds[p];
+        GemmArgs &a = b->h_args[3][p];
+        a.pa = pas[p];
+        a.pa.Yhi = g->QY.hi;
+        a.pa.Ylo = g->split ? g->QY.lo : nullptr;
+        a.pa.split_kind = g->split_kind;
+        a.status = pas[p].status;
+        for (int st = 0; st < 4; ++st) b->h_args[st][p].status = pas[p].status;
+    }
+    for (int st = 0; st < 4; ++st) {
+        cudaError_t e = cudaMemcpyAsync(b->d_args[st], b->h_args[st].data(), b->nprob * sizeof(GemmArgs),
+                                        cudaMemcpyHostToDevice, s);
+        if (e) return fail(SFISTA_ECUDA, std::string("batch args: ") + cudaGetErrorString(e));
+    }
+    return SFISTA_OK;
+}
+
+namespace {
+template <int FMT, bool SPLIT, int EPI>
+void launch_grouped(const GemmBatch *b, int st, int k, cudaStream_t s) {
+    using C = Cfg<FMT, SPLIT, BN_TILE>;
+    umma_gemm_grouped<FMT, SPLIT, BN_TILE, EPI><<<b->nwork[st], 192, C::SMEM, s>>>(b->d_maps[st], b->d_args[st],
+                                                                                   b->d_work[st], k);
+}
+template <int FMT, bool SPLIT>
+void grouped_stage(const GemmBatch *b, int st, int k, cudaStream_t s) {
+    if (st == 0 || st == 2) launch_grouped<FMT, SPLIT, GE_SPLIT>(b, st, k, s);
+    else if (st == 1) launch_grouped<FMT, SPLIT, GE_RESID>(b, st, k, s);
+    else launch_grouped<FMT, SPLIT, GE_PROX>(b, st, k, s);
+}
+}  // namespace
+
+void gemm_batch_stage(GemmBatch *b, int st, int k, cudaStream_t s) {
+    if (b->fmt == FMT_BF16) b->split ? grouped_stage<FMT_BF16, true>(b, st, k, s) : grouped_stage<FMT_BF16, false>(b, st, k, s);
+    else b->split ? grouped_stage<FMT_TF32, true>(b, st, k, s) : grouped_stage<FMT_TF32, false>(b, st, k, s);
+}
+
+int gemm_batch_launches_per_iteration(const GemmBatch *) { return 4; }
 
 sfista_status gemm_apply(GemmPath *g, const float *x, float *y, int transpose, cudaStream_t s) {
     const size_t N = (size_t)g->m * g->n;

@@ -25,4 +25,13 @@ void gemm_stage(GemmPath *g, int st, const ProxArgs &pa, cudaStream_t s);
 // The operator alone (transpose = 0: A_s, 1: A_s^T) on FP32 device buffers.
 sfista_status gemm_apply(GemmPath *g, const float *x, float *y, int transpose, cudaStream_t s);
 
+// Grouped execution of many problems (same precision, any sizes, ranks and
+// bands): one launch per stage covers every problem's tiles.
+struct GemmBatch;
+sfista_status gemm_batch_create(GemmBatch **out, GemmPath *const *paths, int nprob, cudaStream_t s);
+// Per solve: B pointers and prox arguments (pa.Xin / pa.Xout = state buffers 0 / 1).
+sfista_status gemm_batch_bind(GemmBatch *b, const float *const *Bds, const ProxArgs *pas, cudaStream_t s);
+void gemm_batch_stage(GemmBatch *b, int st, int k, cudaStream_t s);
+void gemm_batch_destroy(GemmBatch *b);
+
 }  // namespace sfista

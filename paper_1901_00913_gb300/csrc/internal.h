@@ -90,6 +90,33 @@ size_t band_rows_smem(int w, size_t elem);
 size_t band_cols_smem(int w, size_t elem);
 cudaError_t band_set_smem_limits(int w);
 
+// Persistent cooperative solver (kernels_persistent.cu).
+sfista_status persistent_config(int m, int n, int r, int wmax, int dev, int *grid, size_t *smem, int *rows_chunk,
+                                int *cols_chunk);
+cudaError_t launch_persistent(int grid, size_t smem, int rows_chunk, int cols_chunk, int m, int n, int r, const float *fA, const Band &A,
+                              const float *fB, const Band &B, const float *fAT, const Band &AT, const float *fBT,
+                              const Band &BT, float *Z, float *R, double *Xb0, double *Xb1, const ProxArgs &pa,
+                              int k0, int iters, unsigned *bar, cudaStream_t s);
+
+// Grouped (batched) banded FP32 execution: one launch per stage over the
+// tiles of many problems of any size, rank and band.
+struct BandProb {
+    int m, n, r, rows_chunk, cols_chunk;
+    const float *fA, *fB, *fAT, *fBT;
+    int loA, wA, loB, wB, loAT, wAT, loBT, wBT;
+    float *Z, *R;
+    ProxArgs pa;   // Bd, Y, Yop, beta, constants, status; Xin / Xout = state buffers 0 / 1
+};
+struct BandItem {
+    int prob, q, tile, pad;   // rows pass: q = term chunk; cols pass: q = 0
+};
+void persistent_chunks(int r, int wmax, int *rows_chunk, int *cols_chunk, size_t *smem);
+cudaError_t band_grouped_prepare(size_t smem);
+void launch_band_grouped_stage(int st, const BandProb *probs, const BandItem *items, int nitems, int k, size_t smem,
+                               cudaStream_t s);
+int band_rows_tiles(int m, int n);
+int band_cols_tiles(int m, int n);
+
 // Small helpers.
 void launch_fill_f64(double *p, size_t count, double v, cudaStream_t s);
 void launch_f64_to_f32(const double *in, float *out, size_t count, cudaStream_t s);

@@ -1,0 +1,324 @@
+// The whole Alg. 2 loop in one persistent, cooperatively launched kernel
+// (banded FP32 operator, FP64 FISTA state).
+//
+// For small and medium images one iteration is only a few hundred MFLOP, so
+// four dependent launches per iteration spend most of their time in launch
+// latency and ramp-up.  Here every block stays resident for the whole solve
+// and walks the four phases of each iteration,
+//   phase 0  Z_i = Y A_i^T          (rows pass, work item = term x tile)
+//   phase 1  R   = sum_i B_i Z_i - B (cols pass + residual)
+//   phase 2  Z_i = R A_i            (rows pass with the band of A^T)
+//   phase 3  G   = sum_i B_i^T Z_i; shrink, optional projection, momentum
+// separated by a grid-wide barrier.  The barrier is a counter plus a
+// generation word in global memory; its spin is bounded (about one second),
+// after which the block records DEV_TIMEOUT and the kernel returns.  The
+// cooperative launch guarantees that all blocks are co-resident.  Data that
+// another block wrote earlier in the same launch is read with ld.global.cg
+// (L2, not the non-coherent L1).
+#include <algorithm>
+
+#include "epilogue.cuh"
+#include "internal.h"
+
+namespace sfista {
+namespace {
+
+constexpr int PT = 256;          // threads per block
+constexpr int PR_A = 16;         // rows-pass tile: 16 rows x 64 columns
+constexpr int PR_C = 64;
+constexpr int PC_A = 16;         // cols-pass tile: 16 rows x 64 columns
+constexpr int PC_C = 64;
+constexpr long long kBarrierCycles = 2000000000LL;
+
+struct PersistArgs {
+    int m, n, r;
+    const float *fA, *fB, *fAT, *fBT;
+    int loA, wA, loB, wB, loAT, wAT, loBT, wBT;
+    float *Z, *R;
+    ProxArgs pa;             // Bd, Y, Yop, beta, constants, status (Xin/Xout set per iteration)
+    double *Xb0, *Xb1;
+    int k0, iters;
+    unsigned *bar_count, *bar_gen;
+    int rows_chunk, cols_chunk;   // terms staged per load phase
+};
+
+// Grid-wide barrier with a bounded spin.  Returns false if it gave up.
+__device__ bool grid_barrier(unsigned *count, unsigned *gen, unsigned nblocks, unsigned *status, int *abort_sh) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = gen;
+        const unsigned g = *vgen;
+        __threadfence();
+        if (atomicAdd(count, 1u) == nblocks - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*vgen == g) {
+                if (clock64() - t0 > kBarrierCycles) {
+                    atomicOr(status, DEV_TIMEOUT);
+                    *abort_sh = 1;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *abort_sh == 0;
+}
+
+// One tile of a rows pass for terms [t0, t0 + nt): the input tile and all nt
+// band tiles are staged in one load phase, then
+//   Z_i[a][c] = sum_k In[a][c + lo + k] F_i[c][k].
+__device__ void rows_item(const float *In, int m, int n, const float *Fb, int lo, int w, int t0, int nt, int a0,
+                          int c0, float *Z, float *sm) {
+    const int span = PR_C + w - 1;
+    float *Ins = sm;                 // PR_A x span
+    float *Fs = sm + PR_A * span;    // nt x w x PR_C
+    const int tid = threadIdx.x, tc = tid % PR_C, tg = tid / PR_C;
+    for (int idx = tid; idx < PR_A * span; idx += PT) {
+        const int row = idx / span, col = idx - row * span;
+        const int ga = a0 + row, gc = c0 + lo + col;
+        Ins[idx] = (ga < m && gc >= 0 && gc < n) ? __ldcg(In + (size_t)ga * n + gc) : 0.0f;
+    }
+    for (int idx = tid; idx < nt * w * PR_C; idx += PT) {
+        const int tk = idx / PR_C, cc = idx - tk * PR_C;   // tk = t * w + k
+        Fs[idx] = (c0 + cc < n) ? Fb[((size_t)t0 * w + tk) * n + c0 + cc] : 0.0f;
+    }
+    __syncthreads();
+    const float *x0 = Ins + (tg * 4) * span + tc;
+    const int gc = c0 + tc;
+    for (int t = 0; t < nt; ++t) {
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        const float *f0 = Fs + t * w * PR_C + tc;
+        for (int k = 0; k < w; ++k) {
+            const float f = f0[k * PR_C];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[j] = fmaf(x0[j * span + k], f, acc[j]);
+        }
+        if (gc < n) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int ga = a0 + tg * 4 + j;
+                if (ga < m) Z[((size_t)(t0 + t) * m + ga) * n + gc] = acc[j];
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// One tile of a cols pass summed over the r terms (staged `chunk` terms per
+// load phase), then the epilogue.
+template <int EPI>
+__device__ void cols_item(const float *Z, int m, int n, int r, int chunk, const float *Gb, int lo, int w, int a0,
+                          int c0, float *Out, const ProxArgs &pa, float *sm) {
+    const int span = PC_A + w - 1;
+    const int tid = threadIdx.x, tc = tid % PC_C, tg = tid / PC_C;   // rows tg*4 .. tg*4+3
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int t0 = 0; t0 < r; t0 += chunk) {
+        const int nt = min(chunk, r - t0);
+        float *Zs = sm;                        // nt x span x PC_C
+        float *Gs = sm + nt * span * PC_C;     // nt x w x PC_A
+        for (int idx = tid; idx < nt * span * PC_C; idx += PT) {
+            const int tr = idx / PC_C, col = idx - tr * PC_C;   // tr = t * span + row
+            const int t = tr / span, row = tr - t * span;
+            const int ge = a0 + lo + row, gc = c0 + col;
+            Zs[idx] = (ge >= 0 && ge < m && gc < n) ? __ldcg(Z + ((size_t)(t0 + t) * m + ge) * n + gc) : 0.0f;
+        }
+        for (int idx = tid; idx < nt * w * PC_A; idx += PT) {
+            const int tk = idx / PC_A, ra = idx - tk * PC_A;
+            Gs[idx] = (a0 + ra < m) ? Gb[((size_t)t0 * w + tk) * m + a0 + ra] : 0.0f;
+        }
+        __syncthreads();
+        for (int t = 0; t < nt; ++t) {
+            const float *z0 = Zs + (t * span + tg * 4) * PC_C + tc;
+            const float *g0 = Gs + t * w * PC_A + tg * 4;
+            for (int k = 0; k < w; ++k) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[j] = fmaf(g0[k * PC_A + j], z0[(j + k) * PC_C], acc[j]);
+            }
+        }
+        __syncthreads();
+    }
+    const int gc = c0 + tc;
+    if (gc >= n) return;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int ga = a0 + tg * 4 + j;
+        if (ga >= m) break;
+        const size_t idx = (size_t)ga * n + gc;
+        if (EPI == EPI_RESIDUAL) Out[idx] = acc[j] - pa.Bd[idx];
+        else prox_momentum(pa, idx, (double)acc[j]);
+    }
+}
+
+__global__ void __launch_bounds__(PT) band_solve_persistent(PersistArgs a) {
+    extern __shared__ float sm[];
+    __shared__ int abort_sh;
+    if (threadIdx.x == 0) abort_sh = 0;
+    __syncthreads();
+    const int m = a.m, n = a.n, r = a.r;
+    const int rt_c = (n + PR_C - 1) / PR_C, rt_a = (m + PR_A - 1) / PR_A;
+    const int ct_c = (n + PC_C - 1) / PC_C, ct_a = (m + PC_A - 1) / PC_A;
+    const int rch = a.rows_chunk, nrch = (r + rch - 1) / rch;
+    const int rows_items = nrch * rt_a * rt_c, cols_items = ct_a * ct_c;
+    const unsigned nb = gridDim.x;
+    ProxArgs pa = a.pa;
+    for (int k = a.k0 + 1; k <= a.k0 + a.iters; ++k) {
+        pa.k = k;
+        pa.Xin = (k - 1) & 1 ? a.Xb1 : a.Xb0;
+        pa.Xout = k & 1 ? a.Xb1 : a.Xb0;
+        for (int it = blockIdx.x; it < rows_items; it += nb) {
+            const int q = it / (rt_a * rt_c), t = it - q * rt_a * rt_c;
+            rows_item(pa.Yop, m, n, a.fA, a.loA, a.wA, q * rch, min(rch, r - q * rch), (t / rt_c) * PR_A,
+                      (t % rt_c) * PR_C, a.Z, sm);
+        }
+        if (!grid_barrier(a.bar_count, a.bar_gen, nb, pa.status, &abort_sh)) return;
+        for (int it = blockIdx.x; it < cols_items; it += nb)
+            cols_item<EPI_RESIDUAL>(a.Z, m, n, r, a.cols_chunk, a.fB, a.loB, a.wB, (it / ct_c) * PC_A, (it % ct_c) * PC_C, a.R, pa,
+                                    sm);
+        if (!grid_barrier(a.bar_count, a.bar_gen, nb, pa.status, &abort_sh)) return;
+        for (int it = blockIdx.x; it < rows_items; it += nb) {
+            const int q = it / (rt_a * rt_c), t = it - q * rt_a * rt_c;
+            rows_item(a.R, m, n, a.fAT, a.loAT, a.wAT, q * rch, min(rch, r - q * rch), (t / rt_c) * PR_A,
+                      (t % rt_c) * PR_C, a.Z, sm);
+        }
+        if (!grid_barrier(a.bar_count, a.bar_gen, nb, pa.status, &abort_sh)) return;
+        for (int it = blockIdx.x; it < cols_items; it += nb)
+            cols_item<EPI_PROX>(a.Z, m, n, r, a.cols_chunk, a.fBT, a.loBT, a.wBT, (it / ct_c) * PC_A, (it % ct_c) * PC_C, nullptr,
+                                pa, sm);
+        if (!grid_barrier(a.bar_count, a.bar_gen, nb, pa.status, &abort_sh)) return;
+    }
+}
+
+}  // namespace
+
+constexpr size_t kPersistSmemBudget = 100 * 1024;   // two blocks per SM
+
+// Terms staged per load phase so that one item fits the shared-memory budget.
+void persistent_chunks(int r, int wmax, int *rows_chunk, int *cols_chunk, size_t *smem) {
+    const size_t f = sizeof(float);
+    const size_t rows_fixed = (size_t)PR_A * (PR_C + wmax - 1) * f, rows_term = (size_t)wmax * PR_C * f;
+    const size_t cols_term = ((size_t)(PC_A + wmax - 1) * PC_C + (size_t)wmax * PC_A) * f;
+    int rc = rows_fixed < kPersistSmemBudget ? (int)((kPersistSmemBudget - rows_fixed) / rows_term) : 1;
+    int cc = (int)(kPersistSmemBudget / cols_term);
+    rc = std::max(1, std::min(r, rc));
+    cc = std::max(1, std::min(r, cc));
+    *rows_chunk = rc;
+    *cols_chunk = cc;
+    *smem = std::max(rows_fixed + rc * rows_term, cc * cols_term);
+}
+
+namespace {
+
+// Grouped stages: block b runs work item items[b] of problem items[b].prob.
+__global__ void __launch_bounds__(PT) band_rows_grouped(const BandProb *probs, const BandItem *items, int phase) {
+    extern __shared__ float sm[];
+    const BandItem it = items[blockIdx.x];
+    const BandProb &P = probs[it.prob];
+    const int rt_c = (P.n + PR_C - 1) / PR_C;
+    const int t0 = it.q * P.rows_chunk, nt = min(P.rows_chunk, P.r - t0);
+    const float *In = phase == 0 ? P.pa.Yop : P.R;
+    const float *F = phase == 0 ? P.fA : P.fAT;
+    const int lo = phase == 0 ? P.loA : P.loAT, w = phase == 0 ? P.wA : P.wAT;
+    rows_item(In, P.m, P.n, F, lo, w, t0, nt, (it.tile / rt_c) * PR_A, (it.tile % rt_c) * PR_C, P.Z, sm);
+}
+
+__global__ void __launch_bounds__(PT) band_cols_grouped(const BandProb *probs, const BandItem *items, int phase,
+                                                        int k) {
+    extern __shared__ float sm[];
+    const BandItem it = items[blockIdx.x];
+    const BandProb &P = probs[it.prob];
+    const int ct_c = (P.n + PC_C - 1) / PC_C;
+    const int a0 = (it.tile / ct_c) * PC_A, c0 = (it.tile % ct_c) * PC_C;
+    ProxArgs pa = P.pa;
+    if (phase == 1) {
+        cols_item<EPI_RESIDUAL>(P.Z, P.m, P.n, P.r, P.cols_chunk, P.fB, P.loB, P.wB, a0, c0, P.R, pa, sm);
+    } else {
+        double *b0 = const_cast<double *>(pa.Xin), *b1 = pa.Xout;
+        pa.k = k;
+        pa.Xin = (k - 1) & 1 ? b1 : b0;
+        pa.Xout = k & 1 ? b1 : b0;
+        cols_item<EPI_PROX>(P.Z, P.m, P.n, P.r, P.cols_chunk, P.fBT, P.loBT, P.wBT, a0, c0, nullptr, pa, sm);
+    }
+}
+
+}  // namespace
+
+int band_rows_tiles(int m, int n) { return ((m + PR_A - 1) / PR_A) * ((n + PR_C - 1) / PR_C); }
+int band_cols_tiles(int m, int n) { return ((m + PC_A - 1) / PC_A) * ((n + PC_C - 1) / PC_C); }
+
+cudaError_t band_grouped_prepare(size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(band_rows_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e) return e;
+    return cudaFuncSetAttribute(band_cols_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+void launch_band_grouped_stage(int st, const BandProb *probs, const BandItem *items, int nitems, int k, size_t smem,
+                               cudaStream_t s) {
+    if (st == 0 || st == 2) band_rows_grouped<<<nitems, PT, smem, s>>>(probs, items, st);
+    else band_cols_grouped<<<nitems, PT, smem, s>>>(probs, items, st, k);
+}
+
+
+// Grid size for the persistent solver: all co-resident blocks, capped by the work.
+sfista_status persistent_config(int m, int n, int r, int wmax, int dev, int *grid, size_t *smem, int *rows_chunk,
+                                int *cols_chunk) {
+    persistent_chunks(r, wmax, rows_chunk, cols_chunk, smem);
+    cudaError_t e = cudaFuncSetAttribute(band_solve_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)*smem);
+    if (e != cudaSuccess) return fail(SFISTA_ENOTSUP, std::string("persistent smem: ") + cudaGetErrorString(e));
+    int per_sm = 0, sms = 0, coop = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, band_solve_persistent, PT, *smem)) ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) ||
+        (e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev)))
+        return fail(SFISTA_ECUDA, std::string("occupancy query: ") + cudaGetErrorString(e));
+    if (!coop || per_sm < 1) return fail(SFISTA_ENOTSUP, "cooperative launch unavailable for the persistent solver");
+    const long nrch = (r + *rows_chunk - 1) / *rows_chunk;
+    const long work = std::max<long>(nrch * ((m + PR_A - 1) / PR_A) * ((n + PR_C - 1) / PR_C),
+                                     (long)((m + PC_A - 1) / PC_A) * ((n + PC_C - 1) / PC_C));
+    *grid = (int)std::min<long>((long)std::min(per_sm, 2) * sms, work);
+    return SFISTA_OK;
+}
+
+cudaError_t launch_persistent(int grid, size_t smem, int rows_chunk, int cols_chunk, int m, int n, int r, const float *fA, const Band &A,
+                              const float *fB, const Band &B, const float *fAT, const Band &AT, const float *fBT,
+                              const Band &BT, float *Z, float *R, double *Xb0, double *Xb1, const ProxArgs &pa,
+                              int k0, int iters, unsigned *bar, cudaStream_t s) {
+    PersistArgs a{};
+    a.m = m;
+    a.n = n;
+    a.r = r;
+    a.fA = fA;
+    a.fB = fB;
+    a.fAT = fAT;
+    a.fBT = fBT;
+    a.loA = A.lo;
+    a.wA = A.w;
+    a.loB = B.lo;
+    a.wB = B.w;
+    a.loAT = AT.lo;
+    a.wAT = AT.w;
+    a.loBT = BT.lo;
+    a.wBT = BT.w;
+    a.Z = Z;
+    a.R = R;
+    a.pa = pa;
+    a.Xb0 = Xb0;
+    a.Xb1 = Xb1;
+    a.k0 = k0;
+    a.iters = iters;
+    a.bar_count = bar;
+    a.bar_gen = bar + 1;
+    a.rows_chunk = rows_chunk;
+    a.cols_chunk = cols_chunk;
+    cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
+    if (e) return e;
+    void *args[] = {&a};
+    return cudaLaunchCooperativeKernel((const void *)band_solve_persistent, dim3(grid), dim3(PT), args, smem, s);
+}
+
+}  // namespace sfista

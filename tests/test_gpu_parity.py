@@ -139,18 +139,20 @@ def cfg2():
     return pr, b, ka, L, Xo
 
 
-def test_solve_config2_fp32(cfg2):
+@pytest.mark.parametrize("op", ["banded", "banded_fused"])
+def test_solve_config2_fp32(cfg2, op):
     """512^2, rotated Gaussian, reflexive, r=3, 200 iterations: rel err <= 1e-5."""
     pr, b, ka, L, Xo = cfg2
-    s = api.Sfista(pr.psf, (512, 512), pr.bc, pr.r, prec="fp32", lipschitz=L)
+    s = api.Sfista(pr.psf, (512, 512), pr.bc, pr.r, prec="fp32", op=op, lipschitz=L)
     X = s.solve_device(_cuda(b), pr.lam, pr.iters).cpu().numpy()
     assert oracle.rel_fro(X, Xo) <= TOL["fp32"]
     assert abs(oracle.psnr(X, pr.x_true) - oracle.psnr(Xo, pr.x_true)) <= 0.01
     s.close()
 
 
+@pytest.mark.parametrize("op", ["banded", "banded_fused"])
 @pytest.mark.parametrize("bc", [0, 1])
-def test_solve_ragged(bc):
+def test_solve_ragged(bc, op):
     m, n = 200, 176
     g = W.rng(104)
     P = W.random_psf(g, 11, 9)
@@ -158,7 +160,7 @@ def test_solve_ragged(bc):
     ka = kron.kron_approx(P, cr, cc, m, n, bc, 3)
     L = _oracle_L(ka)
     Xo = oracle.sfista(b.astype(np.float64), ka, L, 0.01, 60)
-    s = api.Sfista(P, (m, n), bc, 3, center=(cr, cc), prec="fp32", lipschitz=L)
+    s = api.Sfista(P, (m, n), bc, 3, center=(cr, cc), prec="fp32", op=op, lipschitz=L)
     X = s.solve_device(_cuda(b), 0.01, 60).cpu().numpy()
     assert oracle.rel_fro(X, Xo) <= TOL["fp32"]
     s.close()
@@ -175,10 +177,12 @@ def test_graph_and_direct_launch_agree():
     np.testing.assert_array_equal(outs[0], outs[1])
 
 
-def test_resume_state_matches_uninterrupted():
+@pytest.mark.parametrize("op", ["banded", "banded_fused", "gemm_band"])
+def test_resume_state_matches_uninterrupted(op):
     P = W.rotated_gaussian_psf(15, 2.0, 1.0, 0.3)
     x, b, _ = _problem(96, 80, P, 1, 107)
-    s = api.Sfista(P, (96, 80), 1, 2, lipschitz=1.0)
+    prec = "tf32x3" if op == "gemm_band" else "fp32"
+    s = api.Sfista(P, (96, 80), 1, 2, lipschitz=1.0, op=op, prec=prec)
     db = _cuda(b)
     X = torch.zeros(96, 80, dtype=torch.float64, device="cuda")
     Xp = torch.zeros_like(X)
@@ -195,16 +199,18 @@ def test_resume_state_matches_uninterrupted():
     s.close()
 
 
-def test_projection_matches_oracle():
+@pytest.mark.parametrize("op,prec,tol", [("banded", "fp32", 1e-5), ("banded_fused", "fp32", 1e-5),
+                                          ("gemm_band", "bf16x3", 1e-4)])
+def test_projection_matches_oracle(op, prec, tol):
     P = W.rotated_gaussian_psf(15, 2.0, 1.0, 0.3)
     x, b, _ = _problem(96, 80, P, 1, 108)
     b = b - 0.1
     ka = kron.kron_approx(P, 7, 7, 96, 80, 1, 2)
     Xo = oracle.sfista(b.astype(np.float64), ka, 1.0, 0.01, 40, project=True)
-    s = api.Sfista(P, (96, 80), 1, 2, lipschitz=1.0, project=True)
+    s = api.Sfista(P, (96, 80), 1, 2, lipschitz=1.0, project=True, op=op, prec=prec)
     X = s.solve_device(_cuda(b), 0.01, 40).cpu().numpy()
     assert X.min() >= 0.0
-    assert oracle.rel_fro(X, Xo) <= 1e-5
+    assert oracle.rel_fro(X, Xo) <= tol
     s.close()
 
 
