@@ -208,6 +208,34 @@ sfista_status sfista_solve_batched(sfista_ctx *const *ctxs,
                                    const double *lambdas, int nprob, int iters,
                                    float *const *d_x, void *stream);
 
+/*
+ * Differentiating the unrolled solve (Alg. 2 for a fixed number of
+ * iterations, no projection, L held fixed).  Both calls need a context with
+ * the banded operator form (SFISTA_FP32 with SFISTA_OP_BANDED or
+ * SFISTA_OP_BANDED_FUSED); otherwise ENOTSUP.
+ *
+ * sfista_unrolled_fwd -- X_iters from X_0 = 0 into d_x (device FP32, m x n),
+ *   saving (X_k, X_{k-1}) at k = 0, ckpt_every, 2 ckpt_every, ... into d_ckpt
+ *   (device FP64, caller-owned, 2 * ceil(iters / ckpt_every) * m * n values).
+ *
+ * sfista_unrolled_bwd -- given d_gX = dl/dX_iters (device FP32, m x n) and the
+ *   checkpoints of the forward with the same b, lambda, iters, ckpt_every:
+ *     d_gb      device FP32 m x n: dl/db
+ *     g_lambda  host FP64 scalar:  dl/dlambda
+ *     d_gA      device FP32 r x n x n (or NULL): dl/dA_i, the dense right factors
+ *     d_gB      device FP32 r x m x m (or NULL): dl/dB_i, the dense left factors
+ *   The adjoint of each step is the step's own symmetric operator
+ *   M = (L I - A_s^T A_s) / (L + lambda^2); segments between checkpoints are
+ *   recomputed from their checkpoint.  Synchronous.
+ */
+sfista_status sfista_unrolled_fwd(sfista_ctx *ctx, const float *d_b, double lambda,
+                                  int iters, int ckpt_every, double *d_ckpt,
+                                  float *d_x, void *stream);
+sfista_status sfista_unrolled_bwd(sfista_ctx *ctx, const float *d_b, double lambda,
+                                  int iters, int ckpt_every, const double *d_ckpt,
+                                  const float *d_gX, float *d_gb, double *g_lambda,
+                                  float *d_gA, float *d_gB, void *stream);
+
 /* Wait for the context's work on `stream`, then report device-side status
  * (ENUMERIC / ETIMEOUT) raised since the last sync. */
 sfista_status sfista_sync(sfista_ctx *ctx, void *stream);

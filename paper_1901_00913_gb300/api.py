@@ -69,6 +69,8 @@ def load(path=None):
     L.sfista_batch_destroy.argtypes = [vp]
     L.sfista_batch_destroy.restype = None
     L.sfista_solve_batched.argtypes = [vp, vp, vp, i, i, vp, vp]
+    L.sfista_unrolled_fwd.argtypes = [vp, vp, d, i, i, vp, vp, vp]
+    L.sfista_unrolled_bwd.argtypes = [vp, vp, d, i, i, vp, vp, vp, ctypes.POINTER(ctypes.c_double), vp, vp, vp]
     L.sfista_strerror.argtypes = [i]
     L.sfista_strerror.restype = ctypes.c_char_p
     L.sfista_last_error.argtypes = []
@@ -77,7 +79,7 @@ def load(path=None):
                  "sfista_sync", "sfista_apply", "sfista_info", "sfista_get_profiles",
                  "sfista_get_factors", "sfista_blur", "sfista_time_stages",
                  "sfista_apply_static", "sfista_batch_create", "sfista_batch_solve", "sfista_batch_sync",
-                 "sfista_solve_batched"):
+                 "sfista_solve_batched", "sfista_unrolled_fwd", "sfista_unrolled_bwd"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -284,6 +286,74 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def sfista_unrolled_fwd(ctx, d_b, lam, iters, ckpt_every, d_ckpt, d_x, stream=None):
+    _check(load().sfista_unrolled_fwd(ctypes.c_void_p(ctx), _ptr(d_b), float(lam), int(iters), int(ckpt_every),
+                                      _ptr(d_ckpt), _ptr(d_x), _stream_ptr(stream)))
+
+
+def sfista_unrolled_bwd(ctx, d_b, lam, iters, ckpt_every, d_ckpt, d_gX, d_gb, d_gA=None, d_gB=None, stream=None):
+    gl = ctypes.c_double()
+    _check(load().sfista_unrolled_bwd(ctypes.c_void_p(ctx), _ptr(d_b), float(lam), int(iters), int(ckpt_every),
+                                      _ptr(d_ckpt), _ptr(d_gX), _ptr(d_gb), ctypes.byref(gl),
+                                      _ptr(d_gA) if d_gA is not None else None,
+                                      _ptr(d_gB) if d_gB is not None else None, _stream_ptr(stream)))
+    return gl.value
+
+
+def _unrolled_function():
+    import torch
+
+    class SfistaUnrolled(torch.autograd.Function):
+        """X_iters of Alg. 2 as a differentiable function of (b, lambda, A, B).
+
+        A (r x n x n) and B (r x m x m) must hold the context's dense factors
+        (``Sfista.factors()``); they are inputs only so that autograd can return
+        dl/dA_i and dl/dB_i.  L is held fixed.
+        """
+
+        @staticmethod
+        def forward(fctx, solver, b, lam, A, B, iters, ckpt_every):
+            m, n = b.shape
+            nseg = (iters + ckpt_every - 1) // ckpt_every
+            ck = torch.empty(2 * nseg, m, n, dtype=torch.float64, device=b.device)
+            x = torch.empty_like(b)
+            lam_v = float(lam)
+            sfista_unrolled_fwd(solver.ctx, b.contiguous(), lam_v, iters, ckpt_every, ck, x)
+            sfista_sync(solver.ctx)
+            fctx.solver, fctx.iters, fctx.ckpt, fctx.lam = solver, iters, ckpt_every, lam_v
+            fctx.save_for_backward(b.contiguous(), ck, lam)
+            fctx.want = (A.requires_grad if A is not None else False, B.requires_grad if B is not None else False)
+            fctx.shapes = (None if A is None else A.shape, None if B is None else B.shape)
+            return x
+
+        @staticmethod
+        def backward(fctx, gX):
+            b, ck, lam = fctx.saved_tensors
+            gb = torch.empty_like(b)
+            gA = torch.empty(fctx.shapes[0], dtype=torch.float32, device=b.device) if fctx.want[0] else None
+            gB = torch.empty(fctx.shapes[1], dtype=torch.float32, device=b.device) if fctx.want[1] else None
+            gl = sfista_unrolled_bwd(fctx.solver.ctx, b, fctx.lam, fctx.iters, fctx.ckpt, ck,
+                                     gX.contiguous().float(), gb, gA, gB)
+            glam = torch.tensor(gl, dtype=lam.dtype, device=lam.device).reshape(lam.shape)
+            return None, gb, glam, gA, gB, None, None
+
+    return SfistaUnrolled
+
+
+_UNROLLED = None
+
+
+def unrolled_solve(solver, b, lam, iters, ckpt_every=10, A=None, B=None):
+    """Differentiable X_iters = sFISTA(b, lambda; A, B) for ``solver`` (banded FP32 form)."""
+    global _UNROLLED
+    import torch
+    if _UNROLLED is None:
+        _UNROLLED = _unrolled_function()
+    if not torch.is_tensor(lam):
+        lam = torch.tensor(float(lam), dtype=torch.float64, device=b.device)
+    return _UNROLLED.apply(solver, b, lam, A, B, iters, ckpt_every)
 
 
 # ------------------------------------------------------------------ convenience wrapper

@@ -9,8 +9,7 @@
 #include <string>
 #include <vector>
 
-#include "gemm.h"
-#include "internal.h"
+#include "ctx.h"
 
 namespace sfista {
 
@@ -24,19 +23,6 @@ sfista_status fail(sfista_status s, const std::string &msg) {
 
 namespace {
 
-// Restores the caller's current device on scope exit.
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        cudaGetDevice(&prev);
-        if (dev != prev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        cudaGetDevice(&cur);
-        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-    }
-};
 
 __global__ void init_state_kernel(const double *X, const double *Xp, double *Y, float *Yop, void *Yhi,
                                   void *Ylo, int split_kind, size_t count, double beta) {
@@ -60,6 +46,15 @@ __global__ void init_state_kernel(const double *X, const double *Xp, double *Y, 
     }
 }
 
+}  // namespace
+
+void launch_init_state(const double *X, const double *Xp, double *Y, float *Yop, void *Yhi, void *Ylo, int split_kind,
+                       size_t count, double beta, cudaStream_t s) {
+    init_state_kernel<<<1024, 256, 0, s>>>(X, Xp, Y, Yop, Yhi, Ylo, split_kind, count, beta);
+}
+
+namespace {
+
 template <typename T>
 cudaError_t upload(T **dst, const T *src, size_t count, cudaStream_t s) {
     cudaError_t e = cudaMalloc((void **)dst, sizeof(T) * std::max<size_t>(count, 1));
@@ -72,37 +67,6 @@ cudaError_t upload(T **dst, const T *src, size_t count, cudaStream_t s) {
 
 using namespace sfista;
 
-struct sfista_ctx {
-    int dev = 0;
-    cudaStream_t stream = nullptr;
-    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-    HostSetup hs;
-    sfista_opts opts;
-    int prec = SFISTA_FP32, op = SFISTA_OP_BANDED;
-    double L = 0.0;
-    int m = 0, n = 0, r = 0;
-    size_t N = 0;
-    // Band storage on the device: FP64 (power iteration) and FP32 (operator).
-    double *dA = nullptr, *dAT = nullptr, *dB = nullptr, *dBT = nullptr;
-    float *fA = nullptr, *fAT = nullptr, *fB = nullptr, *fBT = nullptr;
-    // Iteration state.
-    float *Bd = nullptr, *Yop = nullptr, *Z = nullptr, *R = nullptr, *tmp = nullptr;
-    double *Xb[2] = {nullptr, nullptr}, *Y = nullptr;
-    unsigned *status = nullptr;
-    double *beta = nullptr;
-    int beta_len = 0;
-    std::vector<double> beta_host;
-    // Tensor-core path (operand panels, intermediates, tensor maps).
-    GemmPath *gemm = nullptr;
-    // Persistent solver launch shape and its grid-barrier words.
-    int pgrid = 0, prows_chunk = 1, pcols_chunk = 1;
-    size_t psmem = 0;
-    unsigned *bar = nullptr;
-    // Cached CUDA graph of the iteration loop.
-    cudaGraphExec_t gexec = nullptr;
-    int g_k0 = -1, g_iters = -1;
-    double g_lam = -1.0;
-};
 
 namespace {
 
@@ -122,7 +86,8 @@ void ctx_free(sfista_ctx *c) {
     delete c;
 }
 
-sfista_status ensure_beta(sfista_ctx *c, int k_end) {
+}  // namespace
+sfista_status sfista::ensure_beta(sfista_ctx *c, int k_end) {
     if (k_end <= c->beta_len) return SFISTA_OK;
     int len = std::max(k_end, 2 * c->beta_len);
     momentum_table(len, &c->beta_host);
@@ -138,10 +103,12 @@ sfista_status ensure_beta(sfista_ctx *c, int k_end) {
     }
     return SFISTA_OK;
 }
+namespace {
 
 // Forward operator with the residual epilogue, then the adjoint with the
 // prox + momentum epilogue: one iteration k of Alg. 2 (Steps 1-3).
-ProxArgs prox_args(sfista_ctx *c, int k, double lam) {
+}  // namespace
+ProxArgs sfista::prox_args(sfista_ctx *c, int k, double lam) {
     ProxArgs pa{};
     pa.Bd = c->Bd;
     pa.Xin = c->Xb[(k - 1) & 1];
@@ -158,6 +125,7 @@ ProxArgs prox_args(sfista_ctx *c, int k, double lam) {
     pa.status = c->status;
     return pa;
 }
+namespace {
 
 // Stage `st` (0..3) of iteration k; see sfista_time_stages for the numbering.
 void enqueue_stage(sfista_ctx *c, int st, const ProxArgs &pa) {
@@ -176,10 +144,12 @@ void enqueue_stage(sfista_ctx *c, int st, const ProxArgs &pa) {
     }
 }
 
-void enqueue_iteration(sfista_ctx *c, int k, double lam) {
+}  // namespace
+void sfista::enqueue_iteration(sfista_ctx *c, int k, double lam) {
     ProxArgs pa = prox_args(c, k, lam);
     for (int st = 0; st < 4; ++st) enqueue_stage(c, st, pa);
 }
+namespace {
 
 sfista_status run_loop(sfista_ctx *c, double lam, int k0, int iters) {
     if (iters <= 0) return SFISTA_OK;
@@ -281,7 +251,8 @@ sfista_status check_ctx(const sfista_ctx *c) {
 }
 
 // Reads and clears the device status word (synchronises the context stream).
-sfista_status drain_status(sfista_ctx *c) {
+}  // namespace
+sfista_status sfista::drain_status(sfista_ctx *c) {
     unsigned s = 0;
     SF_CUDA(cudaStreamSynchronize(c->stream));
     SF_CUDA(cudaMemcpy(&s, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
@@ -291,8 +262,10 @@ sfista_status drain_status(sfista_ctx *c) {
     if (s & DEV_NONFINITE) return fail(SFISTA_ENUMERIC, "non-finite value in the input or the iterates");
     return SFISTA_OK;
 }
+namespace {
 
-sfista_status solve_core(sfista_ctx *c, const float *d_b, double lam, int k0, int iters,
+}  // namespace
+sfista_status sfista::solve_core(sfista_ctx *c, const float *d_b, double lam, int k0, int iters,
                          const double *X_in, const double *Xprev_in, cudaStream_t user) {
     if (!d_b) return fail(SFISTA_EINVAL, "b is NULL");
     if (!(lam >= 0) || !isfinite(lam)) return fail(SFISTA_EINVAL, "lambda must be finite and >= 0");
@@ -321,12 +294,15 @@ sfista_status solve_core(sfista_ctx *c, const float *d_b, double lam, int k0, in
     SF_CUDA(cudaGetLastError());
     return SFISTA_OK;
 }
+namespace {
 
-sfista_status finish_on_user(sfista_ctx *c, cudaStream_t user) {
+}  // namespace
+sfista_status sfista::finish_on_user(sfista_ctx *c, cudaStream_t user) {
     SF_CUDA(cudaEventRecord(c->ev_out, c->stream));
     SF_CUDA(cudaStreamWaitEvent(user, c->ev_out, 0));
     return SFISTA_OK;
 }
+namespace {
 
 }  // namespace
 

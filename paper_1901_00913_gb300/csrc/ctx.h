@@ -1,0 +1,75 @@
+// Library-internal definition of the solver context (shared by the C ABI
+// translation units).  Not part of the public interface.
+#pragma once
+
+#include <vector>
+
+#include "gemm.h"
+#include "internal.h"
+
+namespace sfista {
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (dev != prev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace sfista
+
+struct sfista_ctx {
+    using HostSetup = sfista::HostSetup;
+    using GemmPath = sfista::GemmPath;
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    HostSetup hs;
+    sfista_opts opts;
+    int prec = SFISTA_FP32, op = SFISTA_OP_BANDED;
+    double L = 0.0;
+    int m = 0, n = 0, r = 0;
+    size_t N = 0;
+    // Band storage on the device: FP64 (power iteration) and FP32 (operator).
+    double *dA = nullptr, *dAT = nullptr, *dB = nullptr, *dBT = nullptr;
+    float *fA = nullptr, *fAT = nullptr, *fB = nullptr, *fBT = nullptr;
+    // Iteration state.
+    float *Bd = nullptr, *Yop = nullptr, *Z = nullptr, *R = nullptr, *tmp = nullptr;
+    double *Xb[2] = {nullptr, nullptr}, *Y = nullptr;
+    unsigned *status = nullptr;
+    double *beta = nullptr;
+    int beta_len = 0;
+    std::vector<double> beta_host;
+    // Tensor-core path (operand panels, intermediates, tensor maps).
+    GemmPath *gemm = nullptr;
+    // Persistent solver launch shape and its grid-barrier words.
+    int pgrid = 0, prows_chunk = 1, pcols_chunk = 1;
+    size_t psmem = 0;
+    unsigned *bar = nullptr;
+    // Cached CUDA graph of the iteration loop.
+    cudaGraphExec_t gexec = nullptr;
+    int g_k0 = -1, g_iters = -1;
+    double g_lam = -1.0;
+};
+
+namespace sfista {
+
+// Helpers of capi.cu used by the other C-ABI translation units.
+ProxArgs prox_args(sfista_ctx *c, int k, double lam);
+sfista_status ensure_beta(sfista_ctx *c, int k_end);
+void enqueue_iteration(sfista_ctx *c, int k, double lam);
+sfista_status solve_core(sfista_ctx *c, const float *d_b, double lam, int k0, int iters, const double *X_in,
+                         const double *Xprev_in, cudaStream_t user);
+sfista_status drain_status(sfista_ctx *c);
+sfista_status finish_on_user(sfista_ctx *c, cudaStream_t user);
+void launch_init_state(const double *X, const double *Xp, double *Y, float *Yop, void *Yhi, void *Ylo, int split_kind,
+                       size_t count, double beta, cudaStream_t s);
+
+}  // namespace sfista
