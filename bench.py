@@ -60,6 +60,20 @@ def mma_flops_per_stage(info, m, n, r, prec, op):
     return [st0, st1, st2, st3]
 
 
+def replica_throughput(local_ms, iters, steps, world, device="cpu"):
+    """Replicas, no data-path collective: every rank solved `steps` problems of `iters`
+    iterations in local_ms.  Returns (whole-job iterations/s, slowest rank's ms) using a
+    MAX all-reduce of the times (the only collective, outside the timed region)."""
+    ms = float(local_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * iters * steps / (ms / 1e3), ms
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -182,6 +196,153 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_large(args, torch):
+    """--workload cfg3: 2048^2, r=5, 63x63 PSF, 300 iterations per step; every form is
+    checked against the FP64 oracle on the first `--check-iters` iterations."""
+    from paper_1901_00913_gb300 import api, build, workloads as W
+    import oracle
+    from oracle import kron
+    build.build()
+    pr = W.config3()
+    n, iters, r = pr.x_true.shape[0], pr.iters, pr.r
+    db = _observation_gpu(pr, torch)
+    b_host = db.cpu().numpy()
+    s0 = api.Sfista(pr.psf, (n, n), pr.bc, r, prec="fp32", op="banded", lipschitz_tol=1e-8, lipschitz_maxit=300)
+    L = s0.info()["lipschitz"]
+    s0.close()
+    cr, cc = pr.centre
+    ka = kron.kron_approx(pr.psf, cr, cc, n, n, pr.bc, r)
+    t0 = time.perf_counter()
+    Xref = oracle.sfista(b_host.astype(np.float64), ka, L, pr.lam, args.check_iters)
+    cpu_s = time.perf_counter() - t0
+    peaks, peak_src_name = _peaks()
+    forms = {}
+    for f in args.forms.split(","):
+        prec, op = f.split(":")
+        s = api.Sfista(pr.psf, (n, n), pr.bc, r, prec=prec, op=op, lipschitz=L)
+        Xc = s.solve_device(db, pr.lam, args.check_iters).cpu().numpy()
+        err = oracle.rel_fro(Xc, Xref)
+        out = torch.empty_like(db)
+        for _ in range(args.warmup):
+            s.solve_device(db, pr.lam, iters, out=out)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ms = 0.0
+        with Clocks(0) as clk:
+            for _ in range(args.steps):
+                ev0.record()
+                s.solve_device(db, pr.lam, iters, out=out, sync=False)
+                ev1.record()
+                torch.cuda.synchronize()
+                ms += ev0.elapsed_time(ev1)
+        api.sfista_sync(s.ctx)
+        info = s.info()
+        sm = [float(x) for x in api.sfista_time_stages(s.ctx, db, pr.lam, 5)]
+        v = iters * args.steps / (ms / 1e3)
+        wA, wB = info["band_right"], info["band_left"]
+        alg = [2.0 * wA * r * n * n, 2.0 * wB * r * n * n] * 2
+        if op.startswith("gemm"):
+            work = mma_flops_per_stage(info, n, n, r, prec, op)
+            bf16 = peaks.get("bf16_tflops", 1900.0)
+            peak = bf16 if prec.startswith("bf16") else bf16 * (1.1 / 2.25)
+            bound = "tensor"
+        else:
+            work = alg if op == "banded" else [sum(alg), 0, 0, 0]
+            peak, bound = FP32_PEAK_TFLOPS, "alu"
+        dom = int(np.argmax(sm))
+        ach = work[dom] / (sm[dom] / 1e3) / 1e12
+        forms[prec + ":" + op] = {
+            "iters_per_s": v, "rel_err_vs_oracle_first_%d_its" % args.check_iters: err, "stage_ms": sm,
+            "dominant_stage": STAGES[dom], "roofline": {"bound": bound, "achieved_tflops": ach, "peak": peak,
+                                                        "frac": ach / peak},
+            "op_tflops_executed": sum(work) * v / 1e12, "op_tflops_algorithmic": sum(alg) * v / 1e12,
+            "dense_equiv_tflops": 8.0 * r * n ** 3 * v / 1e12, "clocks": clk.summary()}
+        s.close()
+    line = {"metric": METRIC, "workload": "2048x2048 reflexive, 63x63 mixture+Moffat PSF, r=5, lambda=0.002, "
+            "0.5% noise, 300 its", "unit": "iters/s", "steps": args.steps, "warmup": args.warmup,
+            "forms": forms, "cpu_baseline": {"value": args.check_iters / cpu_s, "unit": "iters/s",
+                                             "kind": "oracle", "sample": "%d iterations" % args.check_iters},
+            "peaks": {"source": peak_src_name, "bf16_tflops": peaks.get("bf16_tflops")}}
+    print(json.dumps(line), flush=True)
+
+
+def run_batched(args, torch):
+    """--workload cfg4: 64 problems of uneven size / PSF / rank, 150 iterations, grouped launches."""
+    from paper_1901_00913_gb300 import api, build, workloads as W
+    import oracle
+    from oracle import kron
+    build.build()
+    probs = W.config4()
+    iters = probs[0].iters
+    d_bs, Ls = [], []
+    for pr in probs:
+        db = _observation_gpu(pr, torch)
+        d_bs.append(db)
+        s0 = api.Sfista(pr.psf, pr.x_true.shape, pr.bc, pr.r, prec="fp32", op="banded", lipschitz_tol=1e-7,
+                        lipschitz_maxit=200)
+        Ls.append(s0.info()["lipschitz"])
+        s0.close()
+    lams = [pr.lam for pr in probs]
+    # oracle on a sample: the three smallest problems and the largest
+    order = sorted(range(len(probs)), key=lambda k: probs[k].x_true.size * probs[k].r)
+    sample = order[:3] + order[-1:]
+    refs = {}
+    t0 = time.perf_counter()
+    for k in sample:
+        pr = probs[k]
+        cr, cc = pr.centre
+        ka = kron.kron_approx(pr.psf, cr, cc, pr.x_true.shape[0], pr.x_true.shape[1], pr.bc, pr.r)
+        refs[k] = oracle.sfista(d_bs[k].double().cpu().numpy(), ka, Ls[k], lams[k], iters)
+    cpu_s = time.perf_counter() - t0
+    total_px = sum(pr.x_true.size for pr in probs)
+    forms = {}
+    for f in args.forms.split(","):
+        prec, op = f.split(":")
+        solvers = [api.Sfista(pr.psf, pr.x_true.shape, pr.bc, pr.r, prec=prec, op=op, lipschitz=L)
+                   for pr, L in zip(probs, Ls)]
+        batch = api.Batch(solvers)
+        outs = [torch.empty_like(d) for d in d_bs]
+        for _ in range(args.warmup):
+            batch.solve(d_bs, lams, iters, outs=outs)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ms = 0.0
+        with Clocks(0) as clk:
+            for _ in range(args.steps):
+                ev0.record()
+                batch.solve(d_bs, lams, iters, outs=outs, sync=False)
+                ev1.record()
+                torch.cuda.synchronize()
+                ms += ev0.elapsed_time(ev1)
+        api.sfista_batch_sync(batch.handle)
+        errs = {probs[k].name: oracle.rel_fro(outs[k].cpu().numpy(), refs[k]) for k in sample}
+        # the same problems one at a time (no grouping), for comparison
+        t_single = 0.0
+        for sv, db, lam in zip(solvers, d_bs, lams):
+            sv.solve_device(db, lam, iters)
+        ev0.record()
+        for sv, db, lam in zip(solvers, d_bs, lams):
+            sv.solve_device(db, lam, iters, sync=False)
+        ev1.record()
+        torch.cuda.synchronize()
+        t_single = ev0.elapsed_time(ev1)
+        v = len(probs) * iters * args.steps / (ms / 1e3)
+        forms[prec + ":" + op] = {"problem_iters_per_s": v, "batch_iters_per_s": v / len(probs),
+                                  "megapixel_iters_per_s": total_px * iters * args.steps / (ms / 1e3) / 1e6,
+                                  "sequential_problem_iters_per_s": len(probs) * iters / (t_single / 1e3),
+                                  "max_rel_err_sample": max(errs.values()), "rel_err_sample": errs,
+                                  "clocks": clk.summary()}
+        batch.close()
+        for sv in solvers:
+            sv.close()
+    line = {"metric": METRIC, "workload": "64 problems, n in {256..1024}, PSF 15-41 px mixtures, r in 1..4, "
+            "reflexive, lambda 0.005, 1% noise, 150 its, grouped launches + CUDA graph", "unit": "problem-iters/s",
+            "steps": args.steps, "warmup": args.warmup, "forms": forms,
+            "cpu_baseline": {"value": len(sample) * iters / cpu_s, "unit": "problem-iters/s", "kind": "oracle",
+                             "sample": "4 problems (3 smallest, largest), full 150 its"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -191,10 +352,18 @@ def main():
     ap.add_argument("--forms", default="fp32:banded_fused,fp32:banded,bf16x3:gemm_band,tf32x3:gemm_band,bf16:gemm_band,tf32:gemm_band",
                     help="comma list of prec:op forms to measure")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "cfg4"])
+    ap.add_argument("--check-iters", type=int, default=10)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "cfg2":
+        import torch
+        if args.forms.startswith("fp32:banded_fused,fp32:banded,bf16x3"):
+            args.forms = ("fp32:banded,bf16x3:gemm_band,tf32x3:gemm_band,bf16x3:gemm_dense" if args.workload == "cfg3"
+                          else "fp32:banded,bf16x3:gemm_band,tf32x3:gemm_band")
+        return run_large(args, torch) if args.workload == "cfg3" else run_batched(args, torch)
 
     import torch
     from paper_1901_00913_gb300 import api, build
@@ -248,10 +417,7 @@ def main():
             torch.cuda.synchronize()
         api.sfista_sync(s.ctx)
         ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = t.item()
+        _, ms = replica_throughput(ms, iters, args.steps, world, "cuda")
         X = out.cpu().numpy()
         stage_ms = api.sfista_time_stages(s.ctx, db, pr.lam, 50)
         info = s.info()

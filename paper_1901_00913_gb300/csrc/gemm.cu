@@ -17,11 +17,11 @@
 // Split precision: operands are stored as hi + lo pairs (BF16 or TF32) and
 // each K step issues hi*hi + lo*hi + hi*lo into the same FP32 accumulator.
 //
-// Kernel roles (192 threads): warp 0 lane 0 issues TMA loads into a ring of
+// Kernel roles (320 threads): warp 0 lane 0 issues TMA loads into a ring of
 // shared-memory stages; warp 1 owns the TMEM allocation and lane 0 issues the
-// MMAs, releasing each stage with tcgen05.commit; warps 2-5 wait for the
-// accumulator, read it with tcgen05.ld (each warp its 32-lane quarter) and
-// run the epilogue.  Every mbarrier wait is bounded (about one second); on
+// MMAs, releasing each stage with tcgen05.commit; warps 2-9 wait for the
+// accumulator, read it with tcgen05.ld (two warps per 32-lane quarter, one
+// per column half) and run the epilogue.  Every mbarrier wait is bounded (about one second); on
 // expiry the kernel records DEV_TIMEOUT in the status word, drains what it
 // issued and returns, so the host sees SFISTA_ETIMEOUT instead of a hang.
 #include <cuda.h>
@@ -287,27 +287,29 @@ __device__ __forceinline__ void umma_gemm_tile(const CUtensorMap *pPhi, const CU
         }
         __syncwarp();
     } else {
-        // Epilogue, warps 2..5.  Phase 1: each warp reads its 32-lane quarter of
-        // the accumulator (tcgen05.ld) into a row-major tile in the now idle
-        // stage ring (row stride BN + 1 floats: conflict-free).  Phase 2: each
-        // warp walks whole rows so global accesses are row-contiguous.
+        // Epilogue, warps 2..9.  Phase 1: warp w reads TMEM lane quarter w % 4
+        // (the only quarter it may access), column half (w - 2) / 4, into a
+        // row-major tile in the now idle stage ring (row stride BN + 1 floats:
+        // conflict-free).  Phase 2: the eight warps walk whole rows so global
+        // accesses are row-contiguous.
         const bool ok = mbar_wait(accb, 0, g.status);
         tc_fence_after();
         const int lg = warp & 3;
+        const int half = (warp - 2) >> 2;
         float *tile = reinterpret_cast<float *>(smem);
         constexpr int TS = BN + 1;
 #pragma unroll 1
-        for (int j0 = 0; j0 < BN; j0 += 32) {
+        for (int j0 = half * (BN / 2); j0 < (half + 1) * (BN / 2); j0 += 32) {
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)j0, v);
             const bool zero = !ok || total == 0;
 #pragma unroll
             for (int t = 0; t < 32; ++t) tile[(lg * 32 + lane) * TS + j0 + t] = zero ? 0.0f : v[t];
         }
-        asm volatile("bar.sync 1, 128;" ::: "memory");
+        asm volatile("bar.sync 1, 256;" ::: "memory");
         const int ew = warp - 2;
 #pragma unroll 1
-        for (int rl = ew; rl < BM; rl += 4) {
+        for (int rl = ew; rl < BM; rl += 8) {
             const int row = m0 + rl;
             if (row >= g.rows) break;
             const float *trow = tile + rl * TS;
@@ -341,7 +343,7 @@ __device__ __forceinline__ void umma_gemm_tile(const CUtensorMap *pPhi, const CU
 }
 
 template <int FMT, bool SPLIT, int BN, int EPI>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(320, 1)
     umma_gemm_kernel(const __grid_constant__ CUtensorMap tPhi, const __grid_constant__ CUtensorMap tPlo,
                      const __grid_constant__ CUtensorMap tQhi, const __grid_constant__ CUtensorMap tQlo,
                      GemmArgs g) {
@@ -357,7 +359,7 @@ struct WorkItem {
 };
 
 template <int FMT, bool SPLIT, int BN, int EPI>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(320, 1)
     umma_gemm_grouped(const CUtensorMap *maps, const GemmArgs *args, const WorkItem *work, int k) {
     const WorkItem w = work[blockIdx.x];
     GemmArgs g = args[w.prob];
@@ -451,7 +453,7 @@ sfista_status launch_one(const Operand &P, const Operand &Q, const GemmArgs &a, 
                          cudaStream_t s) {
     using C = Cfg<FMT, SPLIT, BN_TILE>;
     auto kern = umma_gemm_kernel<FMT, SPLIT, BN_TILE, EPI>;
-    kern<<<dim3(grid_x, grid_y), 192, C::SMEM, s>>>(P.map_hi, SPLIT ? P.map_lo : P.map_hi, Q.map_hi,
+    kern<<<dim3(grid_x, grid_y), 320, C::SMEM, s>>>(P.map_hi, SPLIT ? P.map_lo : P.map_hi, Q.map_hi,
                                                      SPLIT ? Q.map_lo : Q.map_hi, a);
     return SFISTA_OK;
 }
@@ -648,6 +650,7 @@ void gemm_stage(GemmPath *g, int st, const ProxArgs &pa_in, cudaStream_t s) {
         default: {
             GemmArgs a = base_args(g);
             a.pa = pa_in;
+            a.pa.Yop = nullptr;   // the tensor-core operands are the split copies
             a.pa.Yhi = g->QY.hi;
             a.pa.Ylo = g->split ? g->QY.lo : nullptr;
             a.pa.split_kind = g->split_kind;
@@ -779,6 +782,7 @@ sfista_status gemm_batch_bind(GemmBatch *b, const float *const *Bds, const ProxA
         b->h_args[1][p].Bd = Bds[p];
         GemmArgs &a = b->h_args[3][p];
         a.pa = pas[p];
+        a.pa.Yop = nullptr;
         a.pa.Yhi = g->QY.hi;
         a.pa.Ylo = g->split ? g->QY.lo : nullptr;
         a.pa.split_kind = g->split_kind;
@@ -797,7 +801,7 @@ namespace {
 template <int FMT, bool SPLIT, int EPI>
 void launch_grouped(const GemmBatch *b, int st, int k, cudaStream_t s) {
     using C = Cfg<FMT, SPLIT, BN_TILE>;
-    umma_gemm_grouped<FMT, SPLIT, BN_TILE, EPI><<<b->nwork[st], 192, C::SMEM, s>>>(b->d_maps[st], b->d_args[st],
+    umma_gemm_grouped<FMT, SPLIT, BN_TILE, EPI><<<b->nwork[st], 320, C::SMEM, s>>>(b->d_maps[st], b->d_args[st],
                                                                                    b->d_work[st], k);
 }
 template <int FMT, bool SPLIT>
