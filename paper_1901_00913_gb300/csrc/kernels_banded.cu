@@ -14,6 +14,7 @@
 // momentum for the adjoint, with the FISTA state in FP64.
 #include <cuda_bf16.h>
 
+#include "band_items.cuh"
 #include "epilogue.cuh"
 #include "internal.h"
 
@@ -21,138 +22,85 @@ namespace sfista {
 
 namespace {
 
-constexpr int RT_C = 64;    // rows pass: output columns per block
-constexpr int RT_A = 16;    // rows pass: output rows per block
-constexpr int CT_C = 64;    // cols pass: output columns per block
-constexpr int CT_A = 32;    // cols pass: output rows per block
-constexpr int NTHR = 256;
-
 template <typename T>
-__global__ void __launch_bounds__(NTHR) band_rows_kernel(const T *__restrict__ In, int m, int n,
-                                                         const T *__restrict__ Fb, int lo, int w,
-                                                         int r, T *__restrict__ Z) {
-    extern __shared__ unsigned char smem_raw[];
-    T *Ins = reinterpret_cast<T *>(smem_raw);        // RT_A x (RT_C + w - 1)
-    const int span = RT_C + w - 1;
-    T *Fs = Ins + RT_A * span;                        // w x RT_C
-    const int c0 = blockIdx.x * RT_C, a0 = blockIdx.y * RT_A;
-    const int tid = threadIdx.x, tc = tid % RT_C, tg = tid / RT_C;   // tg in [0, 4)
-    for (int idx = tid; idx < RT_A * span; idx += NTHR) {
-        int row = idx / span, col = idx - row * span;
-        int ga = a0 + row, gc = c0 + lo + col;
-        Ins[idx] = (ga < m && gc >= 0 && gc < n) ? In[(size_t)ga * n + gc] : T(0);
-    }
-    for (int i = 0; i < r; ++i) {
-        __syncthreads();
-        for (int idx = tid; idx < w * RT_C; idx += NTHR) {
-            int k = idx / RT_C, cc = idx - k * RT_C;
-            int gc = c0 + cc;
-            Fs[idx] = (gc < n) ? Fb[((size_t)i * w + k) * n + gc] : T(0);
-        }
-        __syncthreads();
-        T acc[4] = {T(0), T(0), T(0), T(0)};
-        const T *x0 = Ins + (tg * 4) * span + tc;
-        for (int k = 0; k < w; ++k) {
-            T f = Fs[k * RT_C + tc];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[j] = fma(x0[j * span + k], f, acc[j]);
-        }
-        int gc = c0 + tc;
-        if (gc < n) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                int ga = a0 + tg * 4 + j;
-                if (ga < m) Z[((size_t)i * m + ga) * n + gc] = acc[j];
-            }
-        }
-    }
+__global__ void __launch_bounds__(band::NT) band_rows_kernel(const T *__restrict__ In, int m, int n,
+                                                            const T *__restrict__ Fb, int lo, int w, int r, int chunk,
+                                                            T *__restrict__ Z) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    const int t0 = blockIdx.z * chunk;
+    band::rows_item<T, false>(In, m, n, Fb, lo, w, t0, min(chunk, r - t0), blockIdx.y * band::TA,
+                              blockIdx.x * band::TC, Z, sm);
 }
 
 template <typename T, int EPI>
-__global__ void __launch_bounds__(NTHR) band_cols_kernel(const T *__restrict__ Z, int m, int n,
-                                                         const T *__restrict__ Gb, int lo, int w,
-                                                         int r, T *__restrict__ Out, ProxArgs pa) {
-    extern __shared__ unsigned char smem_raw[];
-    T *Zs = reinterpret_cast<T *>(smem_raw);   // (CT_A + w - 1) x CT_C
-    const int span = CT_A + w - 1;
-    T *Gs = Zs + span * CT_C;                   // w x CT_A
-    const int c0 = blockIdx.x * CT_C, a0 = blockIdx.y * CT_A;
-    const int tid = threadIdx.x, tc = tid % CT_C, tg = tid / CT_C;   // rows tg*8 .. tg*8+7
-    T acc[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j] = T(0);
-    for (int i = 0; i < r; ++i) {
-        __syncthreads();
-        for (int idx = tid; idx < span * CT_C; idx += NTHR) {
-            int row = idx / CT_C, col = idx - row * CT_C;
-            int ge = a0 + lo + row, gc = c0 + col;
-            Zs[idx] = (ge >= 0 && ge < m && gc < n) ? Z[((size_t)i * m + ge) * n + gc] : T(0);
-        }
-        for (int idx = tid; idx < w * CT_A; idx += NTHR) {
-            int k = idx / CT_A, ra = idx - k * CT_A;
-            int ga = a0 + ra;
-            Gs[idx] = (ga < m) ? Gb[((size_t)i * w + k) * m + ga] : T(0);
-        }
-        __syncthreads();
-        const T *z0 = Zs + (tg * 8) * CT_C + tc;
-        const T *g0 = Gs + tg * 8;
-        for (int k = 0; k < w; ++k) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) acc[j] = fma(g0[k * CT_A + j], z0[(j + k) * CT_C], acc[j]);
-        }
-    }
-    const int gc = c0 + tc;
-    if (gc >= n) return;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        int ga = a0 + tg * 8 + j;
-        if (ga >= m) break;
-        size_t idx = (size_t)ga * n + gc;
-        if (EPI == EPI_STORE) {
-            Out[idx] = acc[j];
-        } else if (EPI == EPI_RESIDUAL) {
-            Out[idx] = acc[j] - (T)pa.Bd[idx];
-        } else {
-            prox_momentum(pa, idx, (double)acc[j]);
-        }
-    }
+__global__ void __launch_bounds__(band::NT) band_cols_kernel(const T *__restrict__ Z, int m, int n,
+                                                            const T *__restrict__ Gb, int lo, int w, int r, int chunk,
+                                                            T *__restrict__ Out, ProxArgs pa) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    band::cols_item<T, EPI, false>(Z, m, n, r, chunk, Gb, lo, w, blockIdx.y * band::TA, blockIdx.x * band::TC, Out,
+                                   pa, sm);
+}
+
+constexpr size_t kBandSmemBudget = 96 * 1024;
+constexpr size_t kBandSmemMax = 227 * 1024;
+
+// Terms staged per load phase so that a block stays within the budget.
+template <typename T>
+int rows_chunk(int r, int w) {
+    const size_t fixed = band::rows_smem<T>(w, 0), per = band::rows_smem<T>(w, 1) - fixed;
+    int c = fixed < kBandSmemBudget ? (int)((kBandSmemBudget - fixed) / per) : 1;
+    return c < 1 ? 1 : (c > r ? r : c);
+}
+template <typename T>
+int cols_chunk(int r, int w) {
+    int c = (int)(kBandSmemBudget / band::cols_smem<T>(w, 1));
+    return c < 1 ? 1 : (c > r ? r : c);
 }
 
 }  // namespace
 
 template <typename T>
-void launch_band_rows(const T *In, int m, int n, const T *Fb, int lo, int w, int r, T *Z,
-                      cudaStream_t s) {
-    dim3 grid((n + RT_C - 1) / RT_C, (m + RT_A - 1) / RT_A);
-    size_t sm = sizeof(T) * ((size_t)RT_A * (RT_C + w - 1) + (size_t)w * RT_C);
-    band_rows_kernel<T><<<grid, NTHR, sm, s>>>(In, m, n, Fb, lo, w, r, Z);
+void launch_band_rows(const T *In, int m, int n, const T *Fb, int lo, int w, int r, T *Z, cudaStream_t s) {
+    const int chunk = rows_chunk<T>(r, w);
+    dim3 grid((n + band::TC - 1) / band::TC, (m + band::TA - 1) / band::TA, (r + chunk - 1) / chunk);
+    band_rows_kernel<T><<<grid, band::NT, band::rows_smem<T>(w, chunk), s>>>(In, m, n, Fb, lo, w, r, chunk, Z);
 }
 
 template <typename T>
-void launch_band_cols(const T *Z, int m, int n, const T *Gb, int lo, int w, int r, EpiKind epi,
-                      T *Out, const ProxArgs &pa, cudaStream_t s) {
-    dim3 grid((n + CT_C - 1) / CT_C, (m + CT_A - 1) / CT_A);
-    size_t sm = sizeof(T) * ((size_t)(CT_A + w - 1) * CT_C + (size_t)w * CT_A);
+void launch_band_cols(const T *Z, int m, int n, const T *Gb, int lo, int w, int r, EpiKind epi, T *Out,
+                      const ProxArgs &pa, cudaStream_t s) {
+    const int chunk = cols_chunk<T>(r, w);
+    dim3 grid((n + band::TC - 1) / band::TC, (m + band::TA - 1) / band::TA);
+    const size_t sm = band::cols_smem<T>(w, chunk);
     if (epi == EPI_STORE)
-        band_cols_kernel<T, EPI_STORE><<<grid, NTHR, sm, s>>>(Z, m, n, Gb, lo, w, r, Out, pa);
+        band_cols_kernel<T, EPI_STORE><<<grid, band::NT, sm, s>>>(Z, m, n, Gb, lo, w, r, chunk, Out, pa);
     else if (epi == EPI_RESIDUAL)
-        band_cols_kernel<T, EPI_RESIDUAL><<<grid, NTHR, sm, s>>>(Z, m, n, Gb, lo, w, r, Out, pa);
+        band_cols_kernel<T, EPI_RESIDUAL><<<grid, band::NT, sm, s>>>(Z, m, n, Gb, lo, w, r, chunk, Out, pa);
     else
-        band_cols_kernel<T, EPI_PROX><<<grid, NTHR, sm, s>>>(Z, m, n, Gb, lo, w, r, Out, pa);
+        band_cols_kernel<T, EPI_PROX><<<grid, band::NT, sm, s>>>(Z, m, n, Gb, lo, w, r, chunk, Out, pa);
 }
 
-size_t band_rows_smem(int w, size_t elem) { return elem * ((size_t)RT_A * (RT_C + w - 1) + (size_t)w * RT_C); }
-size_t band_cols_smem(int w, size_t elem) { return elem * ((size_t)(CT_A + w - 1) * CT_C + (size_t)w * CT_A); }
+size_t band_rows_smem(int w, size_t elem) {
+    return elem == 8 ? band::rows_smem<double>(w, 1) : band::rows_smem<float>(w, 1);
+}
+size_t band_cols_smem(int w, size_t elem) {
+    return elem == 8 ? band::cols_smem<double>(w, 1) : band::cols_smem<float>(w, 1);
+}
 
+// Allows the banded kernels the largest dynamic shared memory a block may
+// use; fails if even one term of width w does not fit.
 cudaError_t band_set_smem_limits(int w) {
+    if (band_rows_smem(w, 8) > kBandSmemMax || band_cols_smem(w, 8) > kBandSmemMax) return cudaErrorInvalidValue;
+    const int lim = (int)kBandSmemMax;
     cudaError_t e;
-    int f = (int)band_rows_smem(w, 8), g = (int)band_cols_smem(w, 8);
-    if ((e = cudaFuncSetAttribute(band_rows_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, f))) return e;
-    if ((e = cudaFuncSetAttribute(band_rows_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, f))) return e;
-    if ((e = cudaFuncSetAttribute(band_cols_kernel<float, EPI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, g))) return e;
-    if ((e = cudaFuncSetAttribute(band_cols_kernel<float, EPI_RESIDUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, g))) return e;
-    if ((e = cudaFuncSetAttribute(band_cols_kernel<float, EPI_PROX>, cudaFuncAttributeMaxDynamicSharedMemorySize, g))) return e;
-    if ((e = cudaFuncSetAttribute(band_cols_kernel<double, EPI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, g))) return e;
+    if ((e = cudaFuncSetAttribute(band_rows_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if ((e = cudaFuncSetAttribute(band_rows_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if ((e = cudaFuncSetAttribute(band_cols_kernel<float, EPI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if ((e = cudaFuncSetAttribute(band_cols_kernel<float, EPI_RESIDUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if ((e = cudaFuncSetAttribute(band_cols_kernel<float, EPI_PROX>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if ((e = cudaFuncSetAttribute(band_cols_kernel<double, EPI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
     return cudaSuccess;
 }
 

@@ -17,6 +17,7 @@
 // (L2, not the non-coherent L1).
 #include <algorithm>
 
+#include "band_items.cuh"
 #include "epilogue.cuh"
 #include "internal.h"
 
@@ -24,10 +25,10 @@ namespace sfista {
 namespace {
 
 constexpr int PT = 256;          // threads per block
-constexpr int PR_A = 16;         // rows-pass tile: 16 rows x 64 columns
-constexpr int PR_C = 64;
-constexpr int PC_A = 16;         // cols-pass tile: 16 rows x 64 columns
-constexpr int PC_C = 64;
+constexpr int PR_A = band::TA;     // rows-pass tile: 16 rows x 64 columns
+constexpr int PR_C = band::TC;
+constexpr int PC_A = band::TA;     // cols-pass tile: 16 rows x 64 columns
+constexpr int PC_C = band::TC;
 constexpr long long kBarrierCycles = 2000000000LL;
 
 struct PersistArgs {
@@ -70,89 +71,15 @@ __device__ bool grid_barrier(unsigned *count, unsigned *gen, unsigned nblocks, u
     return *abort_sh == 0;
 }
 
-// One tile of a rows pass for terms [t0, t0 + nt): the input tile and all nt
-// band tiles are staged in one load phase, then
-//   Z_i[a][c] = sum_k In[a][c + lo + k] F_i[c][k].
-__device__ void rows_item(const float *In, int m, int n, const float *Fb, int lo, int w, int t0, int nt, int a0,
-                          int c0, float *Z, float *sm) {
-    const int span = PR_C + w - 1;
-    float *Ins = sm;                 // PR_A x span
-    float *Fs = sm + PR_A * span;    // nt x w x PR_C
-    const int tid = threadIdx.x, tc = tid % PR_C, tg = tid / PR_C;
-    for (int idx = tid; idx < PR_A * span; idx += PT) {
-        const int row = idx / span, col = idx - row * span;
-        const int ga = a0 + row, gc = c0 + lo + col;
-        Ins[idx] = (ga < m && gc >= 0 && gc < n) ? __ldcg(In + (size_t)ga * n + gc) : 0.0f;
-    }
-    for (int idx = tid; idx < nt * w * PR_C; idx += PT) {
-        const int tk = idx / PR_C, cc = idx - tk * PR_C;   // tk = t * w + k
-        Fs[idx] = (c0 + cc < n) ? Fb[((size_t)t0 * w + tk) * n + c0 + cc] : 0.0f;
-    }
-    __syncthreads();
-    const float *x0 = Ins + (tg * 4) * span + tc;
-    const int gc = c0 + tc;
-    for (int t = 0; t < nt; ++t) {
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-        const float *f0 = Fs + t * w * PR_C + tc;
-        for (int k = 0; k < w; ++k) {
-            const float f = f0[k * PR_C];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[j] = fmaf(x0[j * span + k], f, acc[j]);
-        }
-        if (gc < n) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int ga = a0 + tg * 4 + j;
-                if (ga < m) Z[((size_t)(t0 + t) * m + ga) * n + gc] = acc[j];
-            }
-        }
-    }
-    __syncthreads();
+__device__ __forceinline__ void rows_item(const float *In, int m, int n, const float *Fb, int lo, int w, int t0,
+                                          int nt, int a0, int c0, float *Z, float *sm) {
+    band::rows_item<float, true>(In, m, n, Fb, lo, w, t0, nt, a0, c0, Z, sm);
 }
 
-// One tile of a cols pass summed over the r terms (staged `chunk` terms per
-// load phase), then the epilogue.
 template <int EPI>
-__device__ void cols_item(const float *Z, int m, int n, int r, int chunk, const float *Gb, int lo, int w, int a0,
-                          int c0, float *Out, const ProxArgs &pa, float *sm) {
-    const int span = PC_A + w - 1;
-    const int tid = threadIdx.x, tc = tid % PC_C, tg = tid / PC_C;   // rows tg*4 .. tg*4+3
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int t0 = 0; t0 < r; t0 += chunk) {
-        const int nt = min(chunk, r - t0);
-        float *Zs = sm;                        // nt x span x PC_C
-        float *Gs = sm + nt * span * PC_C;     // nt x w x PC_A
-        for (int idx = tid; idx < nt * span * PC_C; idx += PT) {
-            const int tr = idx / PC_C, col = idx - tr * PC_C;   // tr = t * span + row
-            const int t = tr / span, row = tr - t * span;
-            const int ge = a0 + lo + row, gc = c0 + col;
-            Zs[idx] = (ge >= 0 && ge < m && gc < n) ? __ldcg(Z + ((size_t)(t0 + t) * m + ge) * n + gc) : 0.0f;
-        }
-        for (int idx = tid; idx < nt * w * PC_A; idx += PT) {
-            const int tk = idx / PC_A, ra = idx - tk * PC_A;
-            Gs[idx] = (a0 + ra < m) ? Gb[((size_t)t0 * w + tk) * m + a0 + ra] : 0.0f;
-        }
-        __syncthreads();
-        for (int t = 0; t < nt; ++t) {
-            const float *z0 = Zs + (t * span + tg * 4) * PC_C + tc;
-            const float *g0 = Gs + t * w * PC_A + tg * 4;
-            for (int k = 0; k < w; ++k) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[j] = fmaf(g0[k * PC_A + j], z0[(j + k) * PC_C], acc[j]);
-            }
-        }
-        __syncthreads();
-    }
-    const int gc = c0 + tc;
-    if (gc >= n) return;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int ga = a0 + tg * 4 + j;
-        if (ga >= m) break;
-        const size_t idx = (size_t)ga * n + gc;
-        if (EPI == EPI_RESIDUAL) Out[idx] = acc[j] - pa.Bd[idx];
-        else prox_momentum(pa, idx, (double)acc[j]);
-    }
+__device__ __forceinline__ void cols_item(const float *Z, int m, int n, int r, int chunk, const float *Gb, int lo,
+                                          int w, int a0, int c0, float *Out, const ProxArgs &pa, float *sm) {
+    band::cols_item<float, EPI, true>(Z, m, n, r, chunk, Gb, lo, w, a0, c0, Out, pa, sm);
 }
 
 __global__ void __launch_bounds__(PT) band_solve_persistent(PersistArgs a) {
@@ -200,9 +127,9 @@ constexpr size_t kPersistSmemBudget = 100 * 1024;   // two blocks per SM
 
 // Terms staged per load phase so that one item fits the shared-memory budget.
 void persistent_chunks(int r, int wmax, int *rows_chunk, int *cols_chunk, size_t *smem) {
-    const size_t f = sizeof(float);
-    const size_t rows_fixed = (size_t)PR_A * (PR_C + wmax - 1) * f, rows_term = (size_t)wmax * PR_C * f;
-    const size_t cols_term = ((size_t)(PC_A + wmax - 1) * PC_C + (size_t)wmax * PC_A) * f;
+    const size_t rows_fixed = band::rows_smem<float>(wmax, 0);
+    const size_t rows_term = band::rows_smem<float>(wmax, 1) - rows_fixed;
+    const size_t cols_term = band::cols_smem<float>(wmax, 1);
     int rc = rows_fixed < kPersistSmemBudget ? (int)((kPersistSmemBudget - rows_fixed) / rows_term) : 1;
     int cc = (int)(kPersistSmemBudget / cols_term);
     rc = std::max(1, std::min(r, rc));
