@@ -57,6 +57,12 @@ __device__ __forceinline__ void stage(T *dst, const T *src, bool pred, const T *
                      : "memory");
     }
 }
+// Programmatic dependent launch: wait for the preceding kernel in the stream
+// (its writes become visible), and let the next one start its prologue.
+// Both are no-ops when the kernel was not launched with the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 template <bool CG>
 __device__ __forceinline__ void stage_wait() {
     if (!CG) asm volatile("cp.async.wait_all;" ::: "memory");
@@ -123,6 +129,10 @@ __device__ __forceinline__ void rows_item(const T *__restrict__ In, int m, int n
     T *Ins = sm;                 // TA x sp (columns >= span are zero)
     T *Fs = sm + TA * sp;        // nt x w x TC
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool cin = c0 + lane < n;
+    for (int tk = warp; tk < nt * w; tk += NT / 32)   // band tables: constant, staged before the wait
+        stage<T, false>(Fs + tk * TC + lane, Fb + ((size_t)t0 * w + tk) * n + c0 + lane, cin, Fb);
+    if (!CG) pdl_wait();
     {
         const int row = tid >> 3, j0 = tid & 7;          // 32 rows x 8 threads
         const int ga = a0 + row;
@@ -132,9 +142,6 @@ __device__ __forceinline__ void rows_item(const T *__restrict__ In, int m, int n
                          In);
         }
     }
-    const bool cin = c0 + lane < n;
-    for (int tk = warp; tk < nt * w; tk += NT / 32)
-        stage<T, false>(Fs + tk * TC + lane, Fb + ((size_t)t0 * w + tk) * n + c0 + lane, cin, Fb);
     stage_wait<false>();
     __syncthreads();
     const int cb = warp * 4;
@@ -149,6 +156,7 @@ __device__ __forceinline__ void rows_item(const T *__restrict__ In, int m, int n
         }
     }
     __syncthreads();
+    if (!CG) pdl_trigger();
 }
 
 // K terms at once, each with its own Z window and accumulator chain; the
@@ -204,6 +212,10 @@ __device__ __forceinline__ void cols_item(const T *__restrict__ Z, int m, int n,
         const int nt = min(chunk, r - t0);
         T *Zs = sm;                        // nt x zs x TC
         T *Gs = sm + nt * zs * TC;         // nt x w x TA
+        const bool rin = a0 + lane < m;
+        for (int tk = warp; tk < nt * w; tk += NT / 32)   // band tables: constant, staged before the wait
+            stage<T, false>(Gs + tk * TA + lane, Gb + ((size_t)t0 * w + tk) * m + a0 + lane, rin, Gb);
+        if (!CG) pdl_wait();
         for (int t = 0; t < nt; ++t) {
             const T *zt = Z + (size_t)(t0 + t) * m * n;
             for (int row = warp; row < zs; row += NT / 32) {
@@ -212,9 +224,6 @@ __device__ __forceinline__ void cols_item(const T *__restrict__ Z, int m, int n,
                              row < span && cin && ge >= 0 && ge < m, Z);
             }
         }
-        const bool rin = a0 + lane < m;
-        for (int tk = warp; tk < nt * w; tk += NT / 32)
-            stage<T, false>(Gs + tk * TA + lane, Gb + ((size_t)t0 * w + tk) * m + a0 + lane, rin, Gb);
         stage_wait<false>();
         __syncthreads();
         for (int tb = 0; tb < nt; tb += 4) {
@@ -229,16 +238,18 @@ __device__ __forceinline__ void cols_item(const T *__restrict__ Z, int m, int n,
         }
         __syncthreads();
     }
-    if (!cin) return;
+    if (cin) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int ga = a0 + rb + j;
-        if (ga >= m) break;
-        const size_t idx = (size_t)ga * n + gc;
-        if (EPI == EPI_STORE) Out[idx] = acc[j];
-        else if (EPI == EPI_RESIDUAL) Out[idx] = acc[j] - (T)pa.Bd[idx];
-        else prox_momentum(pa, idx, (double)acc[j]);
+        for (int j = 0; j < 4; ++j) {
+            const int ga = a0 + rb + j;
+            if (ga >= m) break;
+            const size_t idx = (size_t)ga * n + gc;
+            if (EPI == EPI_STORE) Out[idx] = acc[j];
+            else if (EPI == EPI_RESIDUAL) Out[idx] = acc[j] - (T)pa.Bd[idx];
+            else prox_momentum(pa, idx, (double)acc[j]);
+        }
     }
+    if (!CG) pdl_trigger();
 }
 
 }  // namespace band

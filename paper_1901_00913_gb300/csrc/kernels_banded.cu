@@ -61,11 +61,29 @@ int cols_chunk(int r, int w) {
 
 }  // namespace
 
+// Launch with programmatic stream serialisation: the kernel may start (and
+// stage its constant band tables) while the previous kernel in the stream
+// finishes; it waits (griddepcontrol.wait) before reading that kernel's output.
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kern)(KArgs...), dim3 grid, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(band::NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 template <typename T>
 void launch_band_rows(const T *In, int m, int n, const T *Fb, int lo, int w, int r, T *Z, cudaStream_t s) {
     const int chunk = rows_chunk<T>(r, w);
     dim3 grid((n + band::TC - 1) / band::TC, (m + band::TA - 1) / band::TA, (r + chunk - 1) / chunk);
-    band_rows_kernel<T><<<grid, band::NT, band::rows_smem<T>(w, chunk), s>>>(In, m, n, Fb, lo, w, r, chunk, Z);
+    launch_pdl(band_rows_kernel<T>, grid, band::rows_smem<T>(w, chunk), s, In, m, n, Fb, lo, w, r, chunk, Z);
 }
 
 template <typename T>
@@ -75,11 +93,11 @@ void launch_band_cols(const T *Z, int m, int n, const T *Gb, int lo, int w, int 
     dim3 grid((n + band::TC - 1) / band::TC, (m + band::TA - 1) / band::TA);
     const size_t sm = band::cols_smem<T>(w, chunk);
     if (epi == EPI_STORE)
-        band_cols_kernel<T, EPI_STORE><<<grid, band::NT, sm, s>>>(Z, m, n, Gb, lo, w, r, chunk, Out, pa);
+        launch_pdl(band_cols_kernel<T, EPI_STORE>, grid, sm, s, Z, m, n, Gb, lo, w, r, chunk, Out, pa);
     else if (epi == EPI_RESIDUAL)
-        band_cols_kernel<T, EPI_RESIDUAL><<<grid, band::NT, sm, s>>>(Z, m, n, Gb, lo, w, r, chunk, Out, pa);
+        launch_pdl(band_cols_kernel<T, EPI_RESIDUAL>, grid, sm, s, Z, m, n, Gb, lo, w, r, chunk, Out, pa);
     else
-        band_cols_kernel<T, EPI_PROX><<<grid, band::NT, sm, s>>>(Z, m, n, Gb, lo, w, r, chunk, Out, pa);
+        launch_pdl(band_cols_kernel<T, EPI_PROX>, grid, sm, s, Z, m, n, Gb, lo, w, r, chunk, Out, pa);
 }
 
 size_t band_rows_smem(int w, size_t elem) {
