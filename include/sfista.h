@@ -331,6 +331,15 @@ sfista_status sfista_apply_static(const float *d_x, float *d_y, int img_rows,
                                   int w_right, const float *d_band_left,
                                   int lo_left, int w_left, void *stream);
 
+/*
+ * sfista_selftest_wait_timeout -- exercises the failure path of the bounded
+ * device-side waits: launches a kernel that waits on an mbarrier nothing
+ * arrives at.  The wait gives up after about one second, the kernel records
+ * the timeout and returns, and this call reports SFISTA_ETIMEOUT (any other
+ * status means the guard did not work).  The context stays usable.
+ */
+sfista_status sfista_selftest_wait_timeout(sfista_ctx *ctx);
+
 const char *sfista_strerror(sfista_status s);
 const char *sfista_last_error(void);
 

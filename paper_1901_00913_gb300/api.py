@@ -69,6 +69,7 @@ def load(path=None):
     L.sfista_batch_destroy.argtypes = [vp]
     L.sfista_batch_destroy.restype = None
     L.sfista_solve_batched.argtypes = [vp, vp, vp, i, i, vp, vp]
+    L.sfista_selftest_wait_timeout.argtypes = [vp]
     L.sfista_unrolled_fwd.argtypes = [vp, vp, d, i, i, vp, vp, vp]
     L.sfista_unrolled_bwd.argtypes = [vp, vp, d, i, i, vp, vp, vp, ctypes.POINTER(ctypes.c_double), vp, vp, vp]
     L.sfista_strerror.argtypes = [i]
@@ -79,7 +80,7 @@ def load(path=None):
                  "sfista_sync", "sfista_apply", "sfista_info", "sfista_get_profiles",
                  "sfista_get_factors", "sfista_blur", "sfista_time_stages",
                  "sfista_apply_static", "sfista_batch_create", "sfista_batch_solve", "sfista_batch_sync",
-                 "sfista_solve_batched", "sfista_unrolled_fwd", "sfista_unrolled_bwd"):
+                 "sfista_solve_batched", "sfista_unrolled_fwd", "sfista_unrolled_bwd", "sfista_selftest_wait_timeout"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -286,6 +287,11 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def sfista_selftest_wait_timeout(ctx):
+    """Returns the status of the bounded-wait self-test (SFISTA_ETIMEOUT when the guard works)."""
+    return load().sfista_selftest_wait_timeout(ctypes.c_void_p(ctx))
 
 
 def sfista_unrolled_fwd(ctx, d_b, lam, iters, ckpt_every, d_ckpt, d_x, stream=None):

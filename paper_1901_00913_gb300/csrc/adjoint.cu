@@ -155,12 +155,11 @@ extern "C" sfista_status sfista_unrolled_fwd(sfista_ctx *c, const float *d_b, do
     const int nseg = (iters + ckpt_every - 1) / ckpt_every;
     for (int j = 0; j < nseg; ++j) {
         const int k0 = j * ckpt_every, k1 = std::min(iters, k0 + ckpt_every);
-        SF_CUDA(cudaMemcpyAsync(d_ckpt + (size_t)2 * j * N, c->Xb[k0 & 1], N * 8, cudaMemcpyDeviceToDevice, c->stream));
-        SF_CUDA(cudaMemcpyAsync(d_ckpt + (size_t)(2 * j + 1) * N, c->Xb[(k0 + 1) & 1], N * 8,
-                                cudaMemcpyDeviceToDevice, c->stream));
+        launch_df_to_f64(c->Xb[k0 & 1], d_ckpt + (size_t)2 * j * N, N, c->stream);
+        launch_df_to_f64(c->Xb[(k0 + 1) & 1], d_ckpt + (size_t)(2 * j + 1) * N, N, c->stream);
         for (int k = k0 + 1; k <= k1; ++k) enqueue_iteration(c, k, lambda);
     }
-    launch_f64_to_f32(c->Xb[iters & 1], d_x, N, c->stream);
+    launch_df_to_f32(c->Xb[iters & 1], d_x, N, c->stream);
     SF_CUDA(cudaGetLastError());
     return finish_on_user(c, user);
 }
@@ -205,15 +204,14 @@ extern "C" sfista_status sfista_unrolled_bwd(sfista_ctx *c, const float *d_b, do
     for (int j = nseg - 1; j >= 0; --j) {
         const int k0 = j * ce, k1 = std::min(iters, k0 + ce);
         // Re-run the segment from its checkpoint, keeping X_k and Y_k.
-        SF_CUDA(cudaMemcpyAsync(c->Xb[k0 & 1], d_ckpt + (size_t)2 * j * N, N * 8, cudaMemcpyDeviceToDevice, s));
-        SF_CUDA(cudaMemcpyAsync(c->Xb[(k0 + 1) & 1], d_ckpt + (size_t)(2 * j + 1) * N, N * 8,
-                                cudaMemcpyDeviceToDevice, s));
+        launch_f64_to_df(d_ckpt + (size_t)2 * j * N, c->Xb[k0 & 1], N, s);
+        launch_f64_to_df(d_ckpt + (size_t)(2 * j + 1) * N, c->Xb[(k0 + 1) & 1], N, s);
         launch_init_state(c->Xb[k0 & 1], c->Xb[(k0 + 1) & 1], c->Y, c->Yop, nullptr, nullptr, 0, N,
                           k0 > 0 ? c->beta_host[k0 - 1] : 0.0, s);
         for (int k = k0 + 1; k <= k1; ++k) {
-            SF_CUDA(cudaMemcpyAsync(segY + (size_t)(k - k0 - 1) * N, c->Y, N * 8, cudaMemcpyDeviceToDevice, s));
+            launch_df_to_f64(c->Y, segY + (size_t)(k - k0 - 1) * N, N, s);
             enqueue_iteration(c, k, lambda);
-            SF_CUDA(cudaMemcpyAsync(segX + (size_t)(k - k0 - 1) * N, c->Xb[k & 1], N * 8, cudaMemcpyDeviceToDevice, s));
+            launch_df_to_f64(c->Xb[k & 1], segX + (size_t)(k - k0 - 1) * N, N, s);
         }
         // Reverse sweep over the segment.
         for (int k = k1; k > k0; --k) {

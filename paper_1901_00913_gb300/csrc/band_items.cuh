@@ -239,14 +239,26 @@ __device__ __forceinline__ void cols_item(const T *__restrict__ Z, int m, int n,
         __syncthreads();
     }
     if (cin) {
+        if (EPI == EPI_PROX) {
+            size_t idx[4];
+            float g[4];
+            bool ok[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int ga = a0 + rb + j;
-            if (ga >= m) break;
-            const size_t idx = (size_t)ga * n + gc;
-            if (EPI == EPI_STORE) Out[idx] = acc[j];
-            else if (EPI == EPI_RESIDUAL) Out[idx] = acc[j] - (T)pa.Bd[idx];
-            else prox_momentum(pa, idx, (double)acc[j]);
+            for (int j = 0; j < 4; ++j) {
+                ok[j] = a0 + rb + j < m;
+                idx[j] = (size_t)(a0 + rb + j) * n + gc;
+                g[j] = (float)acc[j];
+            }
+            prox_momentum_n<4>(pa, idx, g, ok);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int ga = a0 + rb + j;
+                if (ga >= m) break;
+                const size_t idx = (size_t)ga * n + gc;
+                if (EPI == EPI_STORE) Out[idx] = acc[j];
+                else Out[idx] = acc[j] - (T)pa.Bd[idx];
+            }
         }
     }
     if (!CG) pdl_trigger();

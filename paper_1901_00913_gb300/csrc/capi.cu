@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "epilogue.cuh"
 
 namespace sfista {
 
@@ -24,36 +25,21 @@ sfista_status fail(sfista_status s, const std::string &msg) {
 namespace {
 
 
-__global__ void init_state_kernel(const double *X, const double *Xp, double *Y, float *Yop, void *Yhi,
-                                  void *Ylo, int split_kind, size_t count, double beta) {
+// Y_{k0+1} = X + beta (X - Xp) in double-float, plus its operand copies.
+__global__ void init_state_kernel(const float2 *X, const float2 *Xp, float2 *Y, float *Yop, void *Yhi, void *Ylo,
+                                  int split_kind, size_t count, float2 beta) {
+    ProxArgs pa{};
+    pa.Yop = Yop;
+    pa.Yhi = Yhi;
+    pa.Ylo = Ylo;
+    pa.split_kind = split_kind;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
          i += (size_t)gridDim.x * blockDim.x) {
-        double y = X[i] + beta * (X[i] - Xp[i]);
+        const float2 y = dfp::add(X[i], dfp::mul(beta, dfp::sub(X[i], Xp[i])));
         Y[i] = y;
-        Yop[i] = (float)y;
-        if (split_kind == 1) {
-            __nv_bfloat16 h = __double2bfloat16(y);
-            reinterpret_cast<__nv_bfloat16 *>(Yhi)[i] = h;
-            if (Ylo) reinterpret_cast<__nv_bfloat16 *>(Ylo)[i] = __double2bfloat16(y - (double)__bfloat162float(h));
-        } else if (split_kind == 2) {
-            unsigned u;
-            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"((float)y));
-            float h = __uint_as_float(u);
-            reinterpret_cast<float *>(Yhi)[i] = h;
-            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"((float)(y - (double)h)));
-            if (Ylo) reinterpret_cast<float *>(Ylo)[i] = __uint_as_float(u);
-        }
+        store_operands(pa, i, y);
     }
 }
-
-}  // namespace
-
-void launch_init_state(const double *X, const double *Xp, double *Y, float *Yop, void *Yhi, void *Ylo, int split_kind,
-                       size_t count, double beta, cudaStream_t s) {
-    init_state_kernel<<<1024, 256, 0, s>>>(X, Xp, Y, Yop, Yhi, Ylo, split_kind, count, beta);
-}
-
-namespace {
 
 template <typename T>
 cudaError_t upload(T **dst, const T *src, size_t count, cudaStream_t s) {
@@ -61,6 +47,15 @@ cudaError_t upload(T **dst, const T *src, size_t count, cudaStream_t s) {
     if (e) return e;
     return cudaMemcpyAsync(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice, s);
 }
+
+}  // namespace
+
+void launch_init_state(const float2 *X, const float2 *Xp, float2 *Y, float *Yop, void *Yhi, void *Ylo, int split_kind,
+                       size_t count, double beta, cudaStream_t s) {
+    init_state_kernel<<<1024, 256, 0, s>>>(X, Xp, Y, Yop, Yhi, Ylo, split_kind, count, dfp::from_double(beta));
+}
+
+namespace {
 
 }  // namespace
 }  // namespace sfista
@@ -94,8 +89,10 @@ sfista_status sfista::ensure_beta(sfista_ctx *c, int k_end) {
     SF_CUDA(cudaStreamSynchronize(c->stream));
     if (c->beta) cudaFree(c->beta);
     c->beta = nullptr;
-    SF_CUDA(cudaMalloc((void **)&c->beta, sizeof(double) * len));
-    SF_CUDA(cudaMemcpy(c->beta, c->beta_host.data(), sizeof(double) * len, cudaMemcpyHostToDevice));
+    std::vector<float2> bdf(len);
+    for (int i = 0; i < len; ++i) bdf[i] = dfp::from_double(c->beta_host[i]);
+    SF_CUDA(cudaMalloc((void **)&c->beta, sizeof(float2) * len));
+    SF_CUDA(cudaMemcpy(c->beta, bdf.data(), sizeof(float2) * len, cudaMemcpyHostToDevice));
     c->beta_len = len;
     if (c->gexec) {
         cudaGraphExecDestroy(c->gexec);
@@ -119,8 +116,8 @@ ProxArgs sfista::prox_args(sfista_ctx *c, int k, double lam) {
     pa.k = k;
     pa.L = c->L;
     pa.lam2 = lam * lam;
-    pa.inv_den = 1.0 / (c->L + lam * lam);
-    pa.shrink = c->L * pa.inv_den;
+    pa.inv_den = dfp::from_double(1.0 / (c->L + lam * lam));
+    pa.shrink = dfp::from_double(c->L / (c->L + lam * lam));
     pa.project = c->opts.project_nonneg;
     pa.status = c->status;
     return pa;
@@ -277,16 +274,16 @@ sfista_status sfista::solve_core(sfista_ctx *c, const float *d_b, double lam, in
     size_t N = c->N;
     SF_CUDA(cudaMemcpyAsync(c->Bd, d_b, N * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
     launch_check_finite(c->Bd, N, c->status, c->stream);
-    double *Xk = c->Xb[k0 & 1], *Xkm = c->Xb[(k0 + 1) & 1];
-    if (X_in) SF_CUDA(cudaMemcpyAsync(Xk, X_in, N * 8, cudaMemcpyDeviceToDevice, c->stream));
+    float2 *Xk = c->Xb[k0 & 1], *Xkm = c->Xb[(k0 + 1) & 1];
+    if (X_in) launch_f64_to_df(X_in, Xk, N, c->stream);
     else SF_CUDA(cudaMemsetAsync(Xk, 0, N * 8, c->stream));
-    if (k0 > 0 && Xprev_in) SF_CUDA(cudaMemcpyAsync(Xkm, Xprev_in, N * 8, cudaMemcpyDeviceToDevice, c->stream));
+    if (k0 > 0 && Xprev_in) launch_f64_to_df(Xprev_in, Xkm, N, c->stream);
     else SF_CUDA(cudaMemcpyAsync(Xkm, Xk, N * 8, cudaMemcpyDeviceToDevice, c->stream));
     double beta0 = k0 > 0 ? c->beta_host[k0 - 1] : 0.0;
     void *yhi = nullptr, *ylo = nullptr;
     int split = 0;
     if (c->gemm) gemm_state_operands(c->gemm, &yhi, &ylo, &split);
-    init_state_kernel<<<1024, 256, 0, c->stream>>>(Xk, Xkm, c->Y, c->Yop, yhi, ylo, split, N, beta0);
+    launch_init_state(Xk, Xkm, c->Y, c->Yop, yhi, ylo, split, N, beta0, c->stream);
     if (c->gemm) gemm_prepare_solve(c->gemm, c->Bd, c->stream);
     SF_CUDA(cudaGetLastError());
     st = run_loop(c, lam, k0, iters);
@@ -487,7 +484,7 @@ sfista_status sfista_solve_device(sfista_ctx *c, const float *d_b, double lambda
     cudaStream_t user = (cudaStream_t)stream;
     st = solve_core(c, d_b, lambda, 0, iters, nullptr, nullptr, user);
     if (st) return st;
-    launch_f64_to_f32(c->Xb[iters & 1], d_x, c->N, c->stream);
+    launch_df_to_f32(c->Xb[iters & 1], d_x, c->N, c->stream);
     SF_CUDA(cudaGetLastError());
     return finish_on_user(c, user);
 }
@@ -502,8 +499,8 @@ sfista_status sfista_solve_state(sfista_ctx *c, const float *d_b, double lambda,
     st = solve_core(c, d_b, lambda, k0, iters, d_X, d_Xprev, user);
     if (st) return st;
     int ke = k0 + iters;
-    SF_CUDA(cudaMemcpyAsync(d_X, c->Xb[ke & 1], c->N * 8, cudaMemcpyDeviceToDevice, c->stream));
-    SF_CUDA(cudaMemcpyAsync(d_Xprev, c->Xb[(ke + 1) & 1], c->N * 8, cudaMemcpyDeviceToDevice, c->stream));
+    launch_df_to_f64(c->Xb[ke & 1], d_X, c->N, c->stream);
+    launch_df_to_f64(c->Xb[(ke + 1) & 1], d_Xprev, c->N, c->stream);
     return finish_on_user(c, user);
 }
 
@@ -525,7 +522,7 @@ sfista_status sfista_solve(sfista_ctx *c, const float *b, double lambda, int ite
     SF_CUDA(cudaMemcpyAsync(c->tmp, b, c->N * 4, cudaMemcpyHostToDevice, c->stream));
     st = solve_core(c, c->tmp, lambda, 0, iters, nullptr, nullptr, c->stream);
     if (st) return st;
-    launch_f64_to_f32(c->Xb[iters & 1], c->tmp, c->N, c->stream);
+    launch_df_to_f32(c->Xb[iters & 1], c->tmp, c->N, c->stream);
     SF_CUDA(cudaMemcpyAsync(x, c->tmp, c->N * 4, cudaMemcpyDeviceToHost, c->stream));
     return drain_status(c);
 }
@@ -760,7 +757,7 @@ sfista_status sfista_batch_solve(sfista_batch *b, const float *const *d_b, const
         void *yhi = nullptr, *ylo = nullptr;
         int split = 0;
         if (c->gemm) gemm_state_operands(c->gemm, &yhi, &ylo, &split);
-        init_state_kernel<<<256, 256, 0, b->stream>>>(c->Xb[0], c->Xb[1], c->Y, c->Yop, yhi, ylo, split, c->N, 0.0);
+        launch_init_state(c->Xb[0], c->Xb[1], c->Y, c->Yop, yhi, ylo, split, c->N, 0.0, b->stream);
         ProxArgs pa = prox_args(c, 1, lambdas[p]);
         pa.Xin = c->Xb[0];
         pa.Xout = c->Xb[1];
@@ -806,7 +803,7 @@ sfista_status sfista_batch_solve(sfista_batch *b, const float *const *d_b, const
     }
     for (int p = 0; p < np; ++p) {
         sfista_ctx *c = b->ctxs[p];
-        launch_f64_to_f32(c->Xb[iters & 1], d_x[p], c->N, b->stream);
+        launch_df_to_f32(c->Xb[iters & 1], d_x[p], c->N, b->stream);
     }
     SF_CUDA(cudaGetLastError());
     SF_CUDA(cudaEventRecord(b->ev_out, b->stream));
@@ -889,6 +886,18 @@ sfista_status sfista_time_stages(sfista_ctx *c, const float *d_b, double lambda,
     for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
     if (e) return fail(SFISTA_ECUDA, std::string("stage timing: ") + cudaGetErrorString(e));
     for (int s4 = 0; s4 < 4; ++s4) ms[s4] = (float)(acc[s4] / reps);
+    return drain_status(c);
+}
+
+sfista_status sfista_selftest_wait_timeout(sfista_ctx *c) {
+    sfista_status st = check_ctx(c);
+    if (st) return st;
+    DeviceGuard g(c->dev);
+    SF_CUDA(cudaStreamSynchronize(c->stream));
+    st = drain_status(c);   // start from a clean status word
+    if (st) return st;
+    launch_wait_timeout_selftest(c->status, c->stream);
+    SF_CUDA(cudaGetLastError());
     return drain_status(c);
 }
 

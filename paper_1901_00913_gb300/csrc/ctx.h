@@ -42,9 +42,9 @@ struct sfista_ctx {
     float *fA = nullptr, *fAT = nullptr, *fB = nullptr, *fBT = nullptr;
     // Iteration state.
     float *Bd = nullptr, *Yop = nullptr, *Z = nullptr, *R = nullptr, *tmp = nullptr;
-    double *Xb[2] = {nullptr, nullptr}, *Y = nullptr;
+    float2 *Xb[2] = {nullptr, nullptr}, *Y = nullptr;   // double-float FISTA state
     unsigned *status = nullptr;
-    double *beta = nullptr;
+    float2 *beta = nullptr;        // double-float momentum table
     int beta_len = 0;
     std::vector<double> beta_host;
     // Tensor-core path (operand panels, intermediates, tensor maps).
@@ -69,7 +69,7 @@ sfista_status solve_core(sfista_ctx *c, const float *d_b, double lam, int k0, in
                          const double *Xprev_in, cudaStream_t user);
 sfista_status drain_status(sfista_ctx *c);
 sfista_status finish_on_user(sfista_ctx *c, cudaStream_t user);
-void launch_init_state(const double *X, const double *Xp, double *Y, float *Yop, void *Yhi, void *Ylo, int split_kind,
+void launch_init_state(const float2 *X, const float2 *Xp, float2 *Y, float *Yop, void *Yhi, void *Ylo, int split_kind,
                        size_t count, double beta, cudaStream_t s);
 
 }  // namespace sfista

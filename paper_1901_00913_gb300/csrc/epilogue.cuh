@@ -4,6 +4,7 @@
 
 #include <cuda_bf16.h>
 
+#include "dfloat.cuh"
 #include "internal.h"
 
 namespace sfista {
@@ -14,67 +15,98 @@ static __device__ __forceinline__ float tf32_round(float x) {
     return __uint_as_float(u);
 }
 
-// Step 1 shrink (+ projection) and Step 3 momentum for one pixel, FP64 state.
-static __device__ __forceinline__ void prox_momentum(const ProxArgs &pa, size_t idx, double g) {
-    double y = __ldcg(pa.Y + idx);
-    double xprev = __ldcg(pa.Xin + idx);
-    // (L y - g) / (L + lambda^2) with the two constants folded on the host
-    double x = fma(pa.shrink, y, -pa.inv_den * g);
-    if (pa.project && x < 0.0) x = 0.0;
-    if (!isfinite(x)) atomicOr(pa.status, DEV_NONFINITE);
-    double beta = pa.beta[pa.k - 1];
-    double yn = x + beta * (x - xprev);
-    pa.Xout[idx] = x;
-    pa.Y[idx] = yn;
-    if (pa.Yop) pa.Yop[idx] = (float)yn;
+// Step 1 shrink (+ projection) and Step 3 momentum for one pixel, with the
+// state in double-float:  X_k = s Y_k - d G  (s = L/(L+lambda^2),
+// d = 1/(L+lambda^2)),  Y_{k+1} = X_k + beta_k (X_k - X_{k-1}).
+// Also writes the operand copies of Y_{k+1}: FP32 (banded operator) and/or a
+// hi/lo split (BF16 or TF32) for the tensor-core operator.
+static __device__ __forceinline__ float2 prox_step(const ProxArgs &pa, float2 y, float2 xp, float g, float2 beta,
+                                                   float2 *xout, bool *bad) {
+    float2 x = dfp::sub(dfp::mul(pa.shrink, y), dfp::mul_f(pa.inv_den, g));
+    if (pa.project && x.x < 0.0f) x = make_float2(0.0f, 0.0f);
+    *bad |= !isfinite(x.x);
+    *xout = x;
+    return dfp::add(x, dfp::mul(beta, dfp::sub(x, xp)));
+}
+
+static __device__ __forceinline__ void store_operands(const ProxArgs &pa, size_t idx, float2 yn) {
+    const float yf = dfp::to_float(yn);
+    if (pa.Yop) pa.Yop[idx] = yf;
     if (pa.split_kind == 1) {
-        __nv_bfloat16 hi = __double2bfloat16(yn);
-        __nv_bfloat16 lo = __double2bfloat16(yn - (double)__bfloat162float(hi));
-        reinterpret_cast<__nv_bfloat16 *>(pa.Yhi)[idx] = hi;
-        if (pa.Ylo) reinterpret_cast<__nv_bfloat16 *>(pa.Ylo)[idx] = lo;
+        const __nv_bfloat16 h = __float2bfloat16_rn(yf);
+        reinterpret_cast<__nv_bfloat16 *>(pa.Yhi)[idx] = h;
+        if (pa.Ylo)
+            reinterpret_cast<__nv_bfloat16 *>(pa.Ylo)[idx] =
+                __float2bfloat16_rn(__fadd_rn(__fsub_rn(yn.x, __bfloat162float(h)), yn.y));
     } else if (pa.split_kind == 2) {
-        float hi = tf32_round((float)yn);
-        float lo = tf32_round((float)(yn - (double)hi));
-        reinterpret_cast<float *>(pa.Yhi)[idx] = hi;
-        if (pa.Ylo) reinterpret_cast<float *>(pa.Ylo)[idx] = lo;
+        const float h = tf32_round(yf);
+        reinterpret_cast<float *>(pa.Yhi)[idx] = h;
+        if (pa.Ylo) reinterpret_cast<float *>(pa.Ylo)[idx] = tf32_round(__fadd_rn(__fsub_rn(yn.x, h), yn.y));
     }
 }
 
-// Two neighbouring pixels idx, idx + 1 (idx even): vector loads and stores.
-static __device__ __forceinline__ void prox_momentum2(const ProxArgs &pa, size_t idx, double g0, double g1) {
-    const double2 y = __ldcg(reinterpret_cast<const double2 *>(pa.Y + idx));
-    const double2 xp = __ldcg(reinterpret_cast<const double2 *>(pa.Xin + idx));
-    double x0 = fma(pa.shrink, y.x, -pa.inv_den * g0);
-    double x1 = fma(pa.shrink, y.y, -pa.inv_den * g1);
-    if (pa.project) {
-        x0 = x0 < 0.0 ? 0.0 : x0;
-        x1 = x1 < 0.0 ? 0.0 : x1;
+static __device__ __forceinline__ void prox_momentum(const ProxArgs &pa, size_t idx, float g) {
+    const float2 y = __ldcg(pa.Y + idx), xp = __ldcg(pa.Xin + idx);
+    bool bad = false;
+    float2 x;
+    const float2 yn = prox_step(pa, y, xp, g, pa.beta[pa.k - 1], &x, &bad);
+    if (bad) atomicOr(pa.status, DEV_NONFINITE);
+    pa.Xout[idx] = x;
+    pa.Y[idx] = yn;
+    store_operands(pa, idx, yn);
+}
+
+// N pixels at once: every state load is issued before any arithmetic or
+// store, so a thread keeps 2N loads in flight.
+template <int N>
+static __device__ __forceinline__ void prox_momentum_n(const ProxArgs &pa, const size_t *idx, const float *g,
+                                                       const bool *valid) {
+    float2 y[N], xp[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        y[q] = valid[q] ? __ldcg(pa.Y + idx[q]) : make_float2(0.f, 0.f);
+        xp[q] = valid[q] ? __ldcg(pa.Xin + idx[q]) : make_float2(0.f, 0.f);
     }
-    if (!isfinite(x0) || !isfinite(x1)) atomicOr(pa.status, DEV_NONFINITE);
-    const double beta = pa.beta[pa.k - 1];
-    const double y0 = x0 + beta * (x0 - xp.x), y1 = x1 + beta * (x1 - xp.y);
-    *reinterpret_cast<double2 *>(pa.Xout + idx) = make_double2(x0, x1);
-    *reinterpret_cast<double2 *>(pa.Y + idx) = make_double2(y0, y1);
-    if (pa.Yop) *reinterpret_cast<float2 *>(pa.Yop + idx) = make_float2((float)y0, (float)y1);
-    if (pa.split_kind == 1) {
-        __nv_bfloat16 h0 = __double2bfloat16(y0), h1 = __double2bfloat16(y1);
-        __nv_bfloat162 h;
-        h.x = h0;
-        h.y = h1;
-        *reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<__nv_bfloat16 *>(pa.Yhi) + idx) = h;
-        if (pa.Ylo) {
-            __nv_bfloat162 l;
-            l.x = __double2bfloat16(y0 - (double)__bfloat162float(h0));
-            l.y = __double2bfloat16(y1 - (double)__bfloat162float(h1));
-            *reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<__nv_bfloat16 *>(pa.Ylo) + idx) = l;
-        }
-    } else if (pa.split_kind == 2) {
-        const float h0 = tf32_round((float)y0), h1 = tf32_round((float)y1);
-        *reinterpret_cast<float2 *>(reinterpret_cast<float *>(pa.Yhi) + idx) = make_float2(h0, h1);
-        if (pa.Ylo)
-            *reinterpret_cast<float2 *>(reinterpret_cast<float *>(pa.Ylo) + idx) =
-                make_float2(tf32_round((float)(y0 - (double)h0)), tf32_round((float)(y1 - (double)h1)));
+    const float2 beta = pa.beta[pa.k - 1];
+    bool bad = false;
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        if (!valid[q]) continue;
+        float2 x;
+        const float2 yn = prox_step(pa, y[q], xp[q], g[q], beta, &x, &bad);
+        pa.Xout[idx[q]] = x;
+        pa.Y[idx[q]] = yn;
+        store_operands(pa, idx[q], yn);
     }
+    if (bad) atomicOr(pa.status, DEV_NONFINITE);
+}
+
+// Pairs of neighbouring pixels (idx[q] even) for N rows at once.
+template <int N>
+static __device__ __forceinline__ void prox_momentum2_n(const ProxArgs &pa, const size_t *idx, const float *g0,
+                                                        const float *g1, const bool *valid) {
+    float4 y[N], xp[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        y[q] = valid[q] ? __ldcg(reinterpret_cast<const float4 *>(pa.Y + idx[q])) : make_float4(0.f, 0.f, 0.f, 0.f);
+        xp[q] = valid[q] ? __ldcg(reinterpret_cast<const float4 *>(pa.Xin + idx[q])) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const float2 beta = pa.beta[pa.k - 1];
+    bool bad = false;
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        if (!valid[q]) continue;
+        float2 x0, x1;
+        const float2 y0 = prox_step(pa, make_float2(y[q].x, y[q].y), make_float2(xp[q].x, xp[q].y), g0[q], beta, &x0,
+                                    &bad);
+        const float2 y1 = prox_step(pa, make_float2(y[q].z, y[q].w), make_float2(xp[q].z, xp[q].w), g1[q], beta, &x1,
+                                    &bad);
+        *reinterpret_cast<float4 *>(pa.Xout + idx[q]) = make_float4(x0.x, x0.y, x1.x, x1.y);
+        *reinterpret_cast<float4 *>(pa.Y + idx[q]) = make_float4(y0.x, y0.y, y1.x, y1.y);
+        store_operands(pa, idx[q], y0);
+        store_operands(pa, idx[q] + 1, y1);
+    }
+    if (bad) atomicOr(pa.status, DEV_NONFINITE);
 }
 
 }  // namespace sfista

@@ -308,27 +308,50 @@ __device__ __forceinline__ void umma_gemm_tile(const CUtensorMap *pPhi, const CU
         }
         asm volatile("bar.sync 1, 256;" ::: "memory");
         const int ew = warp - 2;
+        if (EPI == GE_PROX) {
+            // Four rows per step (rl, rl + 8, rl + 16, rl + 24): all FP64 state
+            // loads of the step are in flight before any arithmetic.
 #pragma unroll 1
-        for (int rl = ew; rl < BM; rl += 8) {
-            const int row = m0 + rl;
-            if (row >= g.rows) break;
-            const float *trow = tile + rl * TS;
+            for (int rl = ew; rl < BM; rl += 32) {
 #pragma unroll 1
-            for (int c = 2 * lane; c < BN; c += 64) {
-                const int col = n0 + c;
-                if (col >= g.N) break;   // N is even (a multiple of 8)
-                const float a0 = trow[c], a1 = trow[c + 1];
-                if (EPI == GE_SPLIT) {
-                    const size_t idx = ((size_t)term * g.rows + row) * g.N + col;
-                    store_split2(g.out_hi, g.out_lo, g.split_kind, idx, a0, a1);
-                } else if (EPI == GE_RESID) {
-                    const size_t idx = (size_t)row * g.N + col;
-                    const float2 b = *reinterpret_cast<const float2 *>(g.Bd + idx);
-                    store_split2(g.out_hi, g.out_lo, g.split_kind, idx, a0 - b.x, a1 - b.y);
-                } else if (EPI == GE_PROX) {
-                    prox_momentum2(g.pa, (size_t)row * g.N + col, (double)a0, (double)a1);
-                } else {
-                    *reinterpret_cast<float2 *>(g.out_f32 + (size_t)row * g.N + col) = make_float2(a0, a1);
+                for (int c = 2 * lane; c < BN; c += 64) {
+                    const int col = n0 + c;
+                    if (col >= g.N) break;   // N is even (a multiple of 8)
+                    size_t idx[4];
+                    float g0[4], g1[4];
+                    bool ok[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int rr = rl + 8 * q, row = m0 + rr;
+                        ok[q] = rr < BM && row < g.rows;
+                        idx[q] = (size_t)row * g.N + col;
+                        g0[q] = ok[q] ? tile[rr * TS + c] : 0.0f;
+                        g1[q] = ok[q] ? tile[rr * TS + c + 1] : 0.0f;
+                    }
+                    prox_momentum2_n<4>(g.pa, idx, g0, g1, ok);
+                }
+            }
+        } else {
+#pragma unroll 1
+            for (int rl = ew; rl < BM; rl += 8) {
+                const int row = m0 + rl;
+                if (row >= g.rows) break;
+                const float *trow = tile + rl * TS;
+#pragma unroll 1
+                for (int c = 2 * lane; c < BN; c += 64) {
+                    const int col = n0 + c;
+                    if (col >= g.N) break;   // N is even (a multiple of 8)
+                    const float a0 = trow[c], a1 = trow[c + 1];
+                    if (EPI == GE_SPLIT) {
+                        const size_t idx = ((size_t)term * g.rows + row) * g.N + col;
+                        store_split2(g.out_hi, g.out_lo, g.split_kind, idx, a0, a1);
+                    } else if (EPI == GE_RESID) {
+                        const size_t idx = (size_t)row * g.N + col;
+                        const float2 b = *reinterpret_cast<const float2 *>(g.Bd + idx);
+                        store_split2(g.out_hi, g.out_lo, g.split_kind, idx, a0 - b.x, a1 - b.y);
+                    } else {
+                        *reinterpret_cast<float2 *>(g.out_f32 + (size_t)row * g.N + col) = make_float2(a0, a1);
+                    }
                 }
             }
         }
@@ -364,13 +387,24 @@ __global__ void __launch_bounds__(320, 1)
     const WorkItem w = work[blockIdx.x];
     GemmArgs g = args[w.prob];
     if (EPI == GE_PROX) {
-        double *b0 = const_cast<double *>(g.pa.Xin), *b1 = g.pa.Xout;
+        float2 *b0 = const_cast<float2 *>(g.pa.Xin), *b1 = g.pa.Xout;
         g.pa.k = k;
         g.pa.Xin = (k - 1) & 1 ? b1 : b0;
         g.pa.Xout = k & 1 ? b1 : b0;
     }
     const CUtensorMap *m4 = maps + 4 * w.prob;
     umma_gemm_tile<FMT, SPLIT, BN, EPI>(m4, m4 + 1, m4 + 2, m4 + 3, g, w.mt, w.nt);
+}
+
+// Self-test of the bounded wait: one thread waits on an mbarrier that nothing
+// arrives at, so the wait runs out after ~1 s and records DEV_TIMEOUT.
+__global__ void wait_timeout_selftest(unsigned *status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_wait(smem_u32(&bar), 0, status);
+    }
 }
 
 // ------------------------------------------------------------------ host side
@@ -614,6 +648,10 @@ sfista_status gemm_create(GemmPath **out, const HostSetup &h, int prec, bool den
     }
     *out = g;
     return SFISTA_OK;
+}
+
+void launch_wait_timeout_selftest(unsigned *status, cudaStream_t s) {
+    wait_timeout_selftest<<<1, 32, 0, s>>>(status);
 }
 
 void gemm_destroy(GemmPath *g) {

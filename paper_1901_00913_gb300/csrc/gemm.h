@@ -25,6 +25,10 @@ void gemm_stage(GemmPath *g, int st, const ProxArgs &pa, cudaStream_t s);
 // The operator alone (transpose = 0: A_s, 1: A_s^T) on FP32 device buffers.
 sfista_status gemm_apply(GemmPath *g, const float *x, float *y, int transpose, cudaStream_t s);
 
+// Launches a kernel whose bounded mbarrier wait expires (nothing arrives);
+// it records DEV_TIMEOUT in *status and returns after about one second.
+void launch_wait_timeout_selftest(unsigned *status, cudaStream_t s);
+
 // Grouped execution of many problems (same precision, any sizes, ranks and
 // bands): one launch per stage covers every problem's tiles.
 struct GemmBatch;

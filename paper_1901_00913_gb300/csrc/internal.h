@@ -64,17 +64,18 @@ enum EpiKind : int { EPI_STORE = 0, EPI_RESIDUAL = 1, EPI_PROX = 2 };
 
 struct ProxArgs {
     const float *Bd;     // EPI_RESIDUAL: observed image
-    const double *Xin;   // EPI_PROX: X_{k-1} (FP64)
-    double *Xout;        // EPI_PROX: X_k (FP64; a different buffer, ping-pong)
-    double *Y;           // EPI_PROX: Y_k in, Y_{k+1} out (FP64, in place)
+    // FISTA state as double-float pairs (hi, lo), 8 bytes per pixel.
+    const float2 *Xin;   // EPI_PROX: X_{k-1}
+    float2 *Xout;        // EPI_PROX: X_k (a different buffer, ping-pong)
+    float2 *Y;           // EPI_PROX: Y_k in, Y_{k+1} out (in place)
     float *Yop;          // EPI_PROX: FP32 copy of Y_{k+1} (operand of the next GEMM/pass)
     void *Yhi, *Ylo;     // EPI_PROX: optional split copies (bf16 or tf32-in-fp32), may be NULL
     int split_kind;      // 0 none, 1 bf16 hi/lo, 2 tf32 hi/lo (fp32 storage)
-    const double *beta;  // momentum table, beta[k-1] for iteration k
+    const float2 *beta;  // momentum table (double-float), beta[k-1] for iteration k
     int k;               // iteration index (1-based)
     double L, lam2;      // Lipschitz constant and lambda^2
-    double inv_den;      // 1 / (L + lambda^2)
-    double shrink;       // L / (L + lambda^2)
+    float2 inv_den;      // 1 / (L + lambda^2), double-float
+    float2 shrink;       // L / (L + lambda^2), double-float
     int project;         // max(X, 0) after the shrink
     unsigned *status;    // device status word
 };
@@ -95,7 +96,7 @@ sfista_status persistent_config(int m, int n, int r, int wmax, int dev, int *gri
                                 int *cols_chunk);
 cudaError_t launch_persistent(int grid, size_t smem, int rows_chunk, int cols_chunk, int m, int n, int r, const float *fA, const Band &A,
                               const float *fB, const Band &B, const float *fAT, const Band &AT, const float *fBT,
-                              const Band &BT, float *Z, float *R, double *Xb0, double *Xb1, const ProxArgs &pa,
+                              const Band &BT, float *Z, float *R, float2 *Xb0, float2 *Xb1, const ProxArgs &pa,
                               int k0, int iters, unsigned *bar, cudaStream_t s);
 
 // Grouped (batched) banded FP32 execution: one launch per stage over the
@@ -120,6 +121,10 @@ int band_cols_tiles(int m, int n);
 // Small helpers.
 void launch_fill_f64(double *p, size_t count, double v, cudaStream_t s);
 void launch_f64_to_f32(const double *in, float *out, size_t count, cudaStream_t s);
+// Double-float state conversions.
+void launch_df_to_f32(const float2 *in, float *out, size_t count, cudaStream_t s);
+void launch_df_to_f64(const float2 *in, double *out, size_t count, cudaStream_t s);
+void launch_f64_to_df(const double *in, float2 *out, size_t count, cudaStream_t s);
 void launch_f32_to_f64(const float *in, double *out, size_t count, cudaStream_t s);
 void launch_split(const float *in, void *hi, void *lo, size_t count, int kind,
                   cudaStream_t s);

@@ -138,6 +138,18 @@ __global__ void f64_to_f32_kernel(const double *in, float *out, size_t count) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
         out[i] = (float)in[i];
 }
+__global__ void df_to_f32_kernel(const float2 *in, float *out, size_t count) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = dfp::to_float(in[i]);
+}
+__global__ void df_to_f64_kernel(const float2 *in, double *out, size_t count) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = dfp::to_double(in[i]);
+}
+__global__ void f64_to_df_kernel(const double *in, float2 *out, size_t count) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = dfp::from_double(in[i]);
+}
 __global__ void f32_to_f64_kernel(const float *in, double *out, size_t count) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
         out[i] = (double)in[i];
@@ -275,6 +287,15 @@ void launch_fill_f64(double *p, size_t count, double v, cudaStream_t s) {
 }
 void launch_f64_to_f32(const double *in, float *out, size_t count, cudaStream_t s) {
     f64_to_f32_kernel<<<grid_for(count), 256, 0, s>>>(in, out, count);
+}
+void launch_df_to_f32(const float2 *in, float *out, size_t count, cudaStream_t s) {
+    df_to_f32_kernel<<<grid_for(count), 256, 0, s>>>(in, out, count);
+}
+void launch_df_to_f64(const float2 *in, double *out, size_t count, cudaStream_t s) {
+    df_to_f64_kernel<<<grid_for(count), 256, 0, s>>>(in, out, count);
+}
+void launch_f64_to_df(const double *in, float2 *out, size_t count, cudaStream_t s) {
+    f64_to_df_kernel<<<grid_for(count), 256, 0, s>>>(in, out, count);
 }
 void launch_f32_to_f64(const float *in, double *out, size_t count, cudaStream_t s) {
     f32_to_f64_kernel<<<grid_for(count), 256, 0, s>>>(in, out, count);

@@ -37,7 +37,7 @@ struct PersistArgs {
     int loA, wA, loB, wB, loAT, wAT, loBT, wBT;
     float *Z, *R;
     ProxArgs pa;             // Bd, Y, Yop, beta, constants, status (Xin/Xout set per iteration)
-    double *Xb0, *Xb1;
+    float2 *Xb0, *Xb1;
     int k0, iters;
     unsigned *bar_count, *bar_gen;
     int rows_chunk, cols_chunk;   // terms staged per load phase
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(PT) band_cols_grouped(const BandProb *probs, c
     if (phase == 1) {
         cols_item<EPI_RESIDUAL>(P.Z, P.m, P.n, P.r, P.cols_chunk, P.fB, P.loB, P.wB, a0, c0, P.R, pa, sm);
     } else {
-        double *b0 = const_cast<double *>(pa.Xin), *b1 = pa.Xout;
+        float2 *b0 = const_cast<float2 *>(pa.Xin), *b1 = pa.Xout;
         pa.k = k;
         pa.Xin = (k - 1) & 1 ? b1 : b0;
         pa.Xout = k & 1 ? b1 : b0;
@@ -213,7 +213,7 @@ sfista_status persistent_config(int m, int n, int r, int wmax, int dev, int *gri
 
 cudaError_t launch_persistent(int grid, size_t smem, int rows_chunk, int cols_chunk, int m, int n, int r, const float *fA, const Band &A,
                               const float *fB, const Band &B, const float *fAT, const Band &AT, const float *fBT,
-                              const Band &BT, float *Z, float *R, double *Xb0, double *Xb1, const ProxArgs &pa,
+                              const Band &BT, float *Z, float *R, float2 *Xb0, float2 *Xb1, const ProxArgs &pa,
                               int k0, int iters, unsigned *bar, cudaStream_t s) {
     PersistArgs a{};
     a.m = m;

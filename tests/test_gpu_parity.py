@@ -355,3 +355,18 @@ def test_config3_full_size_tensor_core():
     Xg = s.solve_device(_cuda(b), pr.lam, 2).cpu().numpy()
     assert oracle.rel_fro(Xg, Xo) <= TOL["bf16x3"]
     s.close()
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """A device wait that nothing satisfies gives up after ~1 s: ETIMEOUT, then the context still solves."""
+    import time
+    P = W.gaussian_psf(9, 2.0)
+    s = api.Sfista(P, (40, 40), 0, 1, prec="bf16x3", lipschitz=1.0)
+    t0 = time.perf_counter()
+    st = api.sfista_selftest_wait_timeout(s.ctx)
+    dt = time.perf_counter() - t0
+    assert st == api.ETIMEOUT
+    assert 0.2 < dt < 30.0
+    X = s.solve_device(_cuda(np.ones((40, 40))), 0.01, 5)
+    assert torch.isfinite(X).all().item()
+    s.close()
