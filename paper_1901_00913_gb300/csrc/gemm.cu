@@ -188,47 +188,86 @@ __device__ __forceinline__ void store_split2(void *hi, void *lo, int kind, size_
     }
 }
 
-// One output tile (M tile index mt counting terms for stacked stages, N tile
-// index nt) of one GEMM stage.  The tensor maps may live in kernel parameter
-// space (single problem) or in global memory (grouped launch).
-template <int FMT, bool SPLIT, int BN, int EPI>
-__device__ __forceinline__ void umma_gemm_tile(const CUtensorMap *pPhi, const CUtensorMap *pPlo,
-                                               const CUtensorMap *pQhi, const CUtensorMap *pQlo, const GemmArgs &g,
-                                               int mt, int ntile) {
+struct WorkItem {
+    int prob, mt, nt, pad;
+};
+
+template <int FMT, bool SPLIT, int BN>
+struct PCfg {
     using C = Cfg<FMT, SPLIT, BN>;
+    static constexpr int STAGING = BM * (BN / 2 + 1) * 4;   // epilogue half tile, row stride BN/2 + 1 floats
+    static constexpr int RING_MAX = 225 * 1024 - STAGING;
+    static constexpr int STAGES_RAW = RING_MAX / C::STAGE_BYTES;
+    static constexpr int STAGES = STAGES_RAW > 6 ? 6 : (STAGES_RAW < 2 ? 2 : STAGES_RAW);
+    static constexpr int SMEM = STAGES * C::STAGE_BYTES + STAGING + 1024;
+    static constexpr uint32_t TMEM_COLS = 2 * BN;   // two accumulators
+};
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// K range of the M tile starting at m0 (band mode) and the number of K blocks.
+template <int FMT, bool SPLIT, int BN>
+__device__ __forceinline__ void tile_k_range(const GemmArgs &g, int m0, int *k_lo, int *nkb) {
+    using C = Cfg<FMT, SPLIT, BN>;
+    int lo = 0, hi = g.K;
+    if (!g.dense) {
+        lo = max(0, m0 + g.band_lo);
+        hi = min(g.K, m0 + BM + g.band_hi);
+        lo = (lo / C::ALIGN) * C::ALIGN;
+    }
+    *k_lo = lo;
+    *nkb = hi > lo ? (hi - lo + C::KB_ELEMS - 1) / C::KB_ELEMS : 0;
+}
+
+// Persistent GEMM stage.  CTA c walks tiles c, c + gridDim.x, ...; the TMA
+// producer and the MMA issuer run ahead through a ring of shared-memory
+// stages while the eight epilogue warps drain the previous tile from the
+// other of two TMEM accumulators.  Tiles come from (mt, nt) = (t / ntn, t % ntn)
+// of one problem, or from a work list over many problems (GROUPED), whose
+// tensor maps and arguments then live in global memory; for the grouped prox
+// epilogue, k selects X_{k-1} / X_k among each problem's two state buffers
+// (stored in pa.Xin / pa.Xout as buffers 0 / 1).
+template <int FMT, bool SPLIT, int BN, int EPI, bool GROUPED>
+__global__ void __launch_bounds__(320, 1)
+    umma_gemm_persistent(const __grid_constant__ CUtensorMap tPhi, const __grid_constant__ CUtensorMap tPlo,
+                         const __grid_constant__ CUtensorMap tQhi, const __grid_constant__ CUtensorMap tQlo,
+                         const __grid_constant__ GemmArgs g1, int ntn, int ntiles, const CUtensorMap *maps,
+                         const GemmArgs *args, const WorkItem *work, int kswap) {
+    using C = Cfg<FMT, SPLIT, BN>;
+    using PC = PCfg<FMT, SPLIT, BN>;
+    constexpr int S = PC::STAGES;
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t bars[2 * C::STAGES + 1];
+    __shared__ __align__(8) uint64_t bars[2 * S + 5];
     __shared__ uint32_t tmem_base_sh;
+    __shared__ int ep_abort;   // epilogue warps leave the tile loop together
 
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    float *tile = reinterpret_cast<float *>(smem + S * C::STAGE_BYTES);
+    constexpr int HB = BN / 2;     // columns per staged half
+    static_assert(HB == 64, "the epilogue maps one column pair per lane");
+    constexpr int TS = HB + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int term = g.type_b ? 0 : mt / g.m_tiles;
-    const int m0 = (mt % g.m_tiles) * BM;
-    const int n0 = ntile * BN;
-
-    int k_lo = 0, k_hi = g.K;
-    if (!g.dense) {
-        k_lo = max(0, m0 + g.band_lo);
-        k_hi = min(g.K, m0 + BM + g.band_hi);
-        k_lo = (k_lo / C::ALIGN) * C::ALIGN;
-    }
-    const int nkb = k_hi > k_lo ? (k_hi - k_lo + C::KB_ELEMS - 1) / C::KB_ELEMS : 0;
-    const int total = nkb * g.segs;
-
-    const uint32_t full0 = smem_u32(&bars[0]);
-    const uint32_t empty0 = smem_u32(&bars[C::STAGES]);
-    const uint32_t accb = smem_u32(&bars[2 * C::STAGES]);
+    const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[S]);
+    const uint32_t tfull0 = smem_u32(&bars[2 * S]), tempty0 = smem_u32(&bars[2 * S + 2]);
+    const uint32_t drainb = smem_u32(&bars[2 * S + 4]);
     if (threadIdx.x == 0) {
-        for (int s = 0; s < C::STAGES; ++s) {
-            mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, 1);
+        for (int q = 0; q < S; ++q) {
+            mbar_init(full0 + 8 * q, 1);
+            mbar_init(empty0 + 8 * q, 1);
         }
-        mbar_init(accb, 1);
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(tfull0 + 8 * q, 1);
+            mbar_init(tempty0 + 8 * q, 8);
+        }
+        mbar_init(drainb, 1);
+        ep_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
-                     "r"(C::TMEM_COLS)
+                     "r"(PC::TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -237,163 +276,204 @@ __device__ __forceinline__ void umma_gemm_tile(const CUtensorMap *pPhi, const CU
     tc_fence_after();
     const uint32_t tmem = tmem_base_sh;
 
+    // Tile t -> its tensor maps, arguments and (mt, nt).
+    auto fetch = [&](int t, const CUtensorMap *&m4, const GemmArgs *&ga, int &mt, int &nt) {
+        if (GROUPED) {
+            const WorkItem w = work[t];
+            m4 = maps + 4 * w.prob;
+            ga = args + w.prob;
+            mt = w.mt;
+            nt = w.nt;
+        } else {
+            m4 = nullptr;
+            ga = &g1;
+            mt = t / ntn;
+            nt = t - mt * ntn;
+        }
+    };
+
     if (warp == 0) {
         if (lane == 0) {
-            int issued = 0;
-            for (int it = 0; it < total; ++it) {
-                const int s = it % C::STAGES;
-                const uint32_t ph = (it / C::STAGES) & 1;
-                if (!mbar_wait(empty0 + 8 * s, ph ^ 1, g.status)) break;
-                const uint32_t fb = full0 + 8 * s;
-                mbar_expect_tx(fb, C::STAGE_BYTES);
-                const int seg = it / nkb, kb = it - seg * nkb;
-                const int kx = k_lo + kb * C::KB_ELEMS;
-                const int pz = g.type_b ? seg : term;
-                const int qz = g.type_b ? seg : 0;
-                const uint32_t base = smem_u32(smem + s * C::STAGE_BYTES);
-                tma_load_3d(base, pPhi, fb, kx, m0, pz);
-                if (SPLIT) tma_load_3d(base + C::P_BYTES, pPlo, fb, kx, m0, pz);
-                tma_load_3d(base + C::NOP * C::P_BYTES, pQhi, fb, kx, n0, qz);
-                if (SPLIT) tma_load_3d(base + C::NOP * C::P_BYTES + C::Q_BYTES, pQlo, fb, kx, n0, qz);
-                issued = it + 1;
+            int it = 0;
+            bool abort = false;
+            for (int t = blockIdx.x; t < ntiles && !abort; t += gridDim.x) {
+                const CUtensorMap *m4;
+                const GemmArgs *ga;
+                int mt, nt;
+                fetch(t, m4, ga, mt, nt);
+                const int term = ga->type_b ? 0 : mt / ga->m_tiles;
+                const int m0 = (mt % ga->m_tiles) * BM, n0 = nt * BN;
+                int k_lo, nkb;
+                tile_k_range<FMT, SPLIT, BN>(*ga, m0, &k_lo, &nkb);
+                const int total = nkb * ga->segs;
+                const CUtensorMap *pPhi = GROUPED ? m4 : &tPhi, *pPlo = GROUPED ? m4 + 1 : &tPlo;
+                const CUtensorMap *pQhi = GROUPED ? m4 + 2 : &tQhi, *pQlo = GROUPED ? m4 + 3 : &tQlo;
+                for (int q = 0; q < total; ++q, ++it) {
+                    const int s = it % S;
+                    const uint32_t ph = (it / S) & 1;
+                    if (!mbar_wait(empty0 + 8 * s, ph ^ 1, ga->status)) {
+                        abort = true;
+                        break;
+                    }
+                    const uint32_t fb = full0 + 8 * s;
+                    mbar_expect_tx(fb, C::STAGE_BYTES);
+                    const int seg = q / nkb, kb = q - seg * nkb;
+                    const int kx = k_lo + kb * C::KB_ELEMS;
+                    const int pz = ga->type_b ? seg : term, qz = ga->type_b ? seg : 0;
+                    const uint32_t base = smem_u32(smem + s * C::STAGE_BYTES);
+                    tma_load_3d(base, pPhi, fb, kx, m0, pz);
+                    if (SPLIT) tma_load_3d(base + C::P_BYTES, pPlo, fb, kx, m0, pz);
+                    tma_load_3d(base + C::NOP * C::P_BYTES, pQhi, fb, kx, n0, qz);
+                    if (SPLIT) tma_load_3d(base + C::NOP * C::P_BYTES + C::Q_BYTES, pQlo, fb, kx, n0, qz);
+                }
             }
             // Drain: the last fill of every stage has landed before the CTA can exit.
-            for (int it = max(0, issued - C::STAGES); it < issued; ++it)
-                mbar_wait(full0 + 8 * (it % C::STAGES), (it / C::STAGES) & 1, g.status);
+            for (int x = max(0, it - S); x < it; ++x)
+                mbar_wait(full0 + 8 * (x % S), (x / S) & 1, GROUPED ? args[0].status : g1.status);
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            for (int it = 0; it < total; ++it) {
-                const int s = it % C::STAGES;
-                const uint32_t ph = (it / C::STAGES) & 1;
-                if (!mbar_wait(full0 + 8 * s, ph, g.status)) break;
+            int it = 0, j = 0;
+            bool abort = false;
+            unsigned *st = GROUPED ? args[0].status : g1.status;
+            for (int t = blockIdx.x; t < ntiles && !abort; t += gridDim.x, ++j) {
+                const CUtensorMap *m4;
+                const GemmArgs *ga;
+                int mt, nt;
+                fetch(t, m4, ga, mt, nt);
+                const int m0 = (mt % ga->m_tiles) * BM;
+                int k_lo, nkb;
+                tile_k_range<FMT, SPLIT, BN>(*ga, m0, &k_lo, &nkb);
+                const int total = nkb * ga->segs;
+                const int b = j & 1;
+                if (!mbar_wait(tempty0 + 8 * b, ((j >> 1) & 1) ^ 1, st)) break;
                 tc_fence_after();
-                const uint32_t base = smem_u32(smem + s * C::STAGE_BYTES);
-                const uint32_t p_hi = base, p_lo = base + C::P_BYTES;
-                const uint32_t q_hi = base + C::NOP * C::P_BYTES, q_lo = q_hi + C::Q_BYTES;
-#pragma unroll
-                for (int ks = 0; ks < C::KSTEPS; ++ks) {
-                    const uint32_t acc = (it > 0 || ks > 0) ? 1u : 0u;
-                    tc_mma<FMT>(tmem, sw128_desc(p_hi + 32 * ks), sw128_desc(q_hi + 32 * ks), C::IDESC, acc);
-                    if (SPLIT) {
-                        tc_mma<FMT>(tmem, sw128_desc(p_lo + 32 * ks), sw128_desc(q_hi + 32 * ks), C::IDESC, 1u);
-                        tc_mma<FMT>(tmem, sw128_desc(p_hi + 32 * ks), sw128_desc(q_lo + 32 * ks), C::IDESC, 1u);
+                const uint32_t d = tmem + (uint32_t)(b * BN);
+                for (int q = 0; q < total; ++q, ++it) {
+                    const int s = it % S;
+                    const uint32_t ph = (it / S) & 1;
+                    if (!mbar_wait(full0 + 8 * s, ph, st)) {
+                        abort = true;
+                        break;
                     }
+                    tc_fence_after();
+                    const uint32_t base = smem_u32(smem + s * C::STAGE_BYTES);
+                    const uint32_t p_hi = base, p_lo = base + C::P_BYTES;
+                    const uint32_t q_hi = base + C::NOP * C::P_BYTES, q_lo = q_hi + C::Q_BYTES;
+#pragma unroll
+                    for (int ks = 0; ks < C::KSTEPS; ++ks) {
+                        const uint32_t acc = (q > 0 || ks > 0) ? 1u : 0u;
+                        tc_mma<FMT>(d, sw128_desc(p_hi + 32 * ks), sw128_desc(q_hi + 32 * ks), C::IDESC, acc);
+                        if (SPLIT) {
+                            tc_mma<FMT>(d, sw128_desc(p_lo + 32 * ks), sw128_desc(q_hi + 32 * ks), C::IDESC, 1u);
+                            tc_mma<FMT>(d, sw128_desc(p_hi + 32 * ks), sw128_desc(q_lo + 32 * ks), C::IDESC, 1u);
+                        }
+                    }
+                    tc_commit(empty0 + 8 * s);
                 }
-                tc_commit(empty0 + 8 * s);
+                tc_commit(tfull0 + 8 * b);   // arrives once this tile's MMAs complete
             }
-            // Arrives once every MMA issued above has completed.
-            tc_commit(accb);
+            // Every MMA issued above has completed before TMEM is released.
+            tc_commit(drainb);
+            mbar_wait(drainb, 0, st);
         }
         __syncwarp();
     } else {
-        // Epilogue, warps 2..9.  Phase 1: warp w reads TMEM lane quarter w % 4
-        // (the only quarter it may access), column half (w - 2) / 4, into a
-        // row-major tile in the now idle stage ring (row stride BN + 1 floats:
-        // conflict-free).  Phase 2: the eight warps walk whole rows so global
-        // accesses are row-contiguous.
-        const bool ok = mbar_wait(accb, 0, g.status);
-        tc_fence_after();
-        const int lg = warp & 3;
-        const int half = (warp - 2) >> 2;
-        float *tile = reinterpret_cast<float *>(smem);
-        constexpr int TS = BN + 1;
-#pragma unroll 1
-        for (int j0 = half * (BN / 2); j0 < (half + 1) * (BN / 2); j0 += 32) {
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)j0, v);
-            const bool zero = !ok || total == 0;
-#pragma unroll
-            for (int t = 0; t < 32; ++t) tile[(lg * 32 + lane) * TS + j0 + t] = zero ? 0.0f : v[t];
-        }
-        asm volatile("bar.sync 1, 256;" ::: "memory");
-        const int ew = warp - 2;
-        if (EPI == GE_PROX) {
-            // Four rows per step (rl, rl + 8, rl + 16, rl + 24): all FP64 state
-            // loads of the step are in flight before any arithmetic.
-#pragma unroll 1
-            for (int rl = ew; rl < BM; rl += 32) {
-#pragma unroll 1
-                for (int c = 2 * lane; c < BN; c += 64) {
-                    const int col = n0 + c;
-                    if (col >= g.N) break;   // N is even (a multiple of 8)
-                    size_t idx[4];
-                    float g0[4], g1[4];
-                    bool ok[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int rr = rl + 8 * q, row = m0 + rr;
-                        ok[q] = rr < BM && row < g.rows;
-                        idx[q] = (size_t)row * g.N + col;
-                        g0[q] = ok[q] ? tile[rr * TS + c] : 0.0f;
-                        g1[q] = ok[q] ? tile[rr * TS + c + 1] : 0.0f;
-                    }
-                    prox_momentum2_n<4>(g.pa, idx, g0, g1, ok);
-                }
+        // Epilogue, warps 2..9, one column half of the tile at a time.  Phase 1:
+        // warp w reads TMEM lane quarter w % 4 (the only quarter it may access),
+        // 32 of the half's columns, into the staging tile; after the second half
+        // the accumulator is released to the MMA warp.  Phase 2: the eight warps
+        // walk whole rows of the half so global accesses are row-contiguous.
+        const int lg = warp & 3, sub = (warp - 2) >> 2, ew = warp - 2;
+        int j = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+            const CUtensorMap *m4;
+            const GemmArgs *ga;
+            int mt, nt;
+            fetch(t, m4, ga, mt, nt);
+            const int term = ga->type_b ? 0 : mt / ga->m_tiles;
+            const int m0 = (mt % ga->m_tiles) * BM;
+            int k_lo, nkb;
+            tile_k_range<FMT, SPLIT, BN>(*ga, m0, &k_lo, &nkb);
+            const int total = nkb * ga->segs;
+            const int b = j & 1;
+            const bool ok = mbar_wait(tfull0 + 8 * b, (j >> 1) & 1, ga->status);
+            tc_fence_after();
+            if (!ok) ep_abort = 1;
+            ProxArgs pa = ga->pa;
+            if (EPI == GE_PROX && GROUPED) {
+                float2 *b0 = const_cast<float2 *>(pa.Xin), *b1 = pa.Xout;
+                pa.k = kswap;
+                pa.Xin = (kswap - 1) & 1 ? b1 : b0;
+                pa.Xout = kswap & 1 ? b1 : b0;
             }
-        } else {
 #pragma unroll 1
-            for (int rl = ew; rl < BM; rl += 8) {
-                const int row = m0 + rl;
-                if (row >= g.rows) break;
-                const float *trow = tile + rl * TS;
+            for (int h = 0; h < 2; ++h) {
+                {
+                    float v[32];
+                    tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * BN + h * HB + sub * 32), v);
+                    const bool zero = !ok || total == 0;
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) tile[(lg * 32 + lane) * TS + sub * 32 + q] = zero ? 0.0f : v[q];
+                }
+                if (h == 1) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(tempty0 + 8 * b);
+                }
+                asm volatile("bar.sync 1, 256;" ::: "memory");
+                const int n0 = nt * BN + h * HB;
+                const int c = 2 * lane;   // HB == 64: one column pair per lane
+                const int col = n0 + c;
+                if (EPI == GE_PROX) {
+                    if (col < ga->N) {   // N is even (a multiple of 8)
 #pragma unroll 1
-                for (int c = 2 * lane; c < BN; c += 64) {
-                    const int col = n0 + c;
-                    if (col >= g.N) break;   // N is even (a multiple of 8)
-                    const float a0 = trow[c], a1 = trow[c + 1];
-                    if (EPI == GE_SPLIT) {
-                        const size_t idx = ((size_t)term * g.rows + row) * g.N + col;
-                        store_split2(g.out_hi, g.out_lo, g.split_kind, idx, a0, a1);
-                    } else if (EPI == GE_RESID) {
-                        const size_t idx = (size_t)row * g.N + col;
-                        const float2 b = *reinterpret_cast<const float2 *>(g.Bd + idx);
-                        store_split2(g.out_hi, g.out_lo, g.split_kind, idx, a0 - b.x, a1 - b.y);
-                    } else {
-                        *reinterpret_cast<float2 *>(g.out_f32 + (size_t)row * g.N + col) = make_float2(a0, a1);
+                        for (int rl = ew; rl < BM; rl += 32) {
+                            size_t idx[4];
+                            float g0[4], g1v[4];
+                            bool okr[4];
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const int rr = rl + 8 * q, row = m0 + rr;
+                                okr[q] = rr < BM && row < ga->rows;
+                                idx[q] = (size_t)row * ga->N + col;
+                                g0[q] = okr[q] ? tile[rr * TS + c] : 0.0f;
+                                g1v[q] = okr[q] ? tile[rr * TS + c + 1] : 0.0f;
+                            }
+                            prox_momentum2_n<4>(pa, idx, g0, g1v, okr);
+                        }
+                    }
+                } else if (col < ga->N) {
+                    const int rows = ga->rows, N = ga->N, sk = ga->split_kind;
+                    void *ohi = ga->out_hi, *olo = ga->out_lo;
+#pragma unroll 1
+                    for (int rl = ew; rl < BM; rl += 8) {
+                        const int row = m0 + rl;
+                        if (row >= rows) break;
+                        const float a0 = tile[rl * TS + c], a1 = tile[rl * TS + c + 1];
+                        if (EPI == GE_SPLIT) {
+                            store_split2(ohi, olo, sk, ((size_t)term * rows + row) * N + col, a0, a1);
+                        } else if (EPI == GE_RESID) {
+                            const size_t idx = (size_t)row * N + col;
+                            const float2 bb = *reinterpret_cast<const float2 *>(ga->Bd + idx);
+                            store_split2(ohi, olo, sk, idx, a0 - bb.x, a1 - bb.y);
+                        } else {
+                            *reinterpret_cast<float2 *>(ga->out_f32 + (size_t)row * N + col) = make_float2(a0, a1);
+                        }
                     }
                 }
+                asm volatile("bar.sync 1, 256;" ::: "memory");   // staging tile free again
             }
+            if (ep_abort) break;                                  // uniform across the epilogue warps
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(PC::TMEM_COLS)
                      : "memory");
     }
-}
-
-template <int FMT, bool SPLIT, int BN, int EPI>
-__global__ void __launch_bounds__(320, 1)
-    umma_gemm_kernel(const __grid_constant__ CUtensorMap tPhi, const __grid_constant__ CUtensorMap tPlo,
-                     const __grid_constant__ CUtensorMap tQhi, const __grid_constant__ CUtensorMap tQlo,
-                     GemmArgs g) {
-    umma_gemm_tile<FMT, SPLIT, BN, EPI>(&tPhi, &tPlo, &tQhi, &tQlo, g, blockIdx.y, blockIdx.x);
-}
-
-// Grouped launch: block b runs tile work[b] of problem work[b].prob, whose
-// four tensor maps (P hi, P lo, Q hi, Q lo) and arguments live in global
-// memory.  For the prox epilogue, k selects X_{k-1} / X_k among the
-// problem's two state buffers (stored in pa.Xin / pa.Xout as buffers 0 / 1).
-struct WorkItem {
-    int prob, mt, nt, pad;
-};
-
-template <int FMT, bool SPLIT, int BN, int EPI>
-__global__ void __launch_bounds__(320, 1)
-    umma_gemm_grouped(const CUtensorMap *maps, const GemmArgs *args, const WorkItem *work, int k) {
-    const WorkItem w = work[blockIdx.x];
-    GemmArgs g = args[w.prob];
-    if (EPI == GE_PROX) {
-        float2 *b0 = const_cast<float2 *>(g.pa.Xin), *b1 = g.pa.Xout;
-        g.pa.k = k;
-        g.pa.Xin = (k - 1) & 1 ? b1 : b0;
-        g.pa.Xout = k & 1 ? b1 : b0;
-    }
-    const CUtensorMap *m4 = maps + 4 * w.prob;
-    umma_gemm_tile<FMT, SPLIT, BN, EPI>(m4, m4 + 1, m4 + 2, m4 + 3, g, w.mt, w.nt);
 }
 
 // Self-test of the bounded wait: one thread waits on an mbarrier that nothing
@@ -458,6 +538,7 @@ struct GemmPath {
     const float *Bd = nullptr;
     unsigned *status = nullptr;
     double *dband = nullptr;             // scratch for densify
+    int sms = 1;                         // SM count: the persistent grids use one CTA per SM
 };
 
 namespace {
@@ -466,11 +547,12 @@ constexpr int BN_TILE = 128;
 
 template <int FMT, bool SPLIT, int EPI>
 cudaError_t set_attr() {
-    cudaError_t e = cudaFuncSetAttribute(umma_gemm_kernel<FMT, SPLIT, BN_TILE, EPI>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<FMT, SPLIT, BN_TILE>::SMEM);
+    const int sm = PCfg<FMT, SPLIT, BN_TILE>::SMEM;
+    cudaError_t e = cudaFuncSetAttribute(umma_gemm_persistent<FMT, SPLIT, BN_TILE, EPI, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e) return e;
-    return cudaFuncSetAttribute(umma_gemm_grouped<FMT, SPLIT, BN_TILE, EPI>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<FMT, SPLIT, BN_TILE>::SMEM);
+    return cudaFuncSetAttribute(umma_gemm_persistent<FMT, SPLIT, BN_TILE, EPI, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 
 template <int FMT, bool SPLIT>
@@ -482,13 +564,15 @@ cudaError_t set_attrs() {
     return set_attr<FMT, SPLIT, GE_STORE>();
 }
 
+// One persistent launch over the gx * gy tiles of a stage (one CTA per SM).
 template <int FMT, bool SPLIT, int EPI>
-sfista_status launch_one(const Operand &P, const Operand &Q, const GemmArgs &a, int grid_x, int grid_y,
+sfista_status launch_one(const Operand &P, const Operand &Q, const GemmArgs &a, int grid_x, int grid_y, int sms,
                          cudaStream_t s) {
-    using C = Cfg<FMT, SPLIT, BN_TILE>;
-    auto kern = umma_gemm_kernel<FMT, SPLIT, BN_TILE, EPI>;
-    kern<<<dim3(grid_x, grid_y), 320, C::SMEM, s>>>(P.map_hi, SPLIT ? P.map_lo : P.map_hi, Q.map_hi,
-                                                     SPLIT ? Q.map_lo : Q.map_hi, a);
+    const int ntiles = grid_x * grid_y;
+    const int grid = ntiles < sms ? ntiles : sms;
+    umma_gemm_persistent<FMT, SPLIT, BN_TILE, EPI, false><<<grid, 320, PCfg<FMT, SPLIT, BN_TILE>::SMEM, s>>>(
+        P.map_hi, SPLIT ? P.map_lo : P.map_hi, Q.map_hi, SPLIT ? Q.map_lo : Q.map_hi, a, grid_x, ntiles, nullptr,
+        nullptr, nullptr, 0);
     return SFISTA_OK;
 }
 
@@ -496,10 +580,10 @@ template <int EPI>
 sfista_status dispatch(const GemmPath *g, const Operand &P, const Operand &Q, const GemmArgs &a, int gx, int gy,
                        cudaStream_t s) {
     if (g->fmt == FMT_BF16)
-        return g->split ? launch_one<FMT_BF16, true, EPI>(P, Q, a, gx, gy, s)
-                        : launch_one<FMT_BF16, false, EPI>(P, Q, a, gx, gy, s);
-    return g->split ? launch_one<FMT_TF32, true, EPI>(P, Q, a, gx, gy, s)
-                    : launch_one<FMT_TF32, false, EPI>(P, Q, a, gx, gy, s);
+        return g->split ? launch_one<FMT_BF16, true, EPI>(P, Q, a, gx, gy, g->sms, s)
+                        : launch_one<FMT_BF16, false, EPI>(P, Q, a, gx, gy, g->sms, s);
+    return g->split ? launch_one<FMT_TF32, true, EPI>(P, Q, a, gx, gy, g->sms, s)
+                    : launch_one<FMT_TF32, false, EPI>(P, Q, a, gx, gy, g->sms, s);
 }
 
 GemmArgs base_args(const GemmPath *g) {
@@ -587,6 +671,12 @@ sfista_status gemm_create(GemmPath **out, const HostSetup &h, int prec, bool den
     g->split_kind = g->fmt == FMT_BF16 ? 1 : 2;
     g->dense = dense;
     g->status = status;
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || g->sms < 1)
+            g->sms = 1;
+    }
     g->m = h.m;
     g->n = h.n;
     g->r = h.r;
@@ -701,7 +791,7 @@ void gemm_stage(GemmPath *g, int st, const ProxArgs &pa_in, cudaStream_t s) {
 
 // ------------------------------------------------------------------ grouped (batched) launches
 struct GemmBatch {
-    int nprob = 0, fmt = FMT_BF16;
+    int nprob = 0, fmt = FMT_BF16, sms = 1;
     bool split = true;
     std::vector<GemmPath *> paths;
     CUtensorMap *d_maps[4] = {nullptr, nullptr, nullptr, nullptr};   // per stage: nprob x 4
@@ -727,6 +817,7 @@ sfista_status gemm_batch_create(GemmBatch **out, GemmPath *const *paths, int npr
     GemmBatch *b = new (std::nothrow) GemmBatch();
     if (!b) return fail(SFISTA_ENOMEM, "batch allocation failed");
     b->nprob = nprob;
+    b->sms = paths[0]->sms;
     b->fmt = paths[0]->fmt;
     b->split = paths[0]->split;
     b->paths.assign(paths, paths + nprob);
@@ -838,9 +929,12 @@ sfista_status gemm_batch_bind(GemmBatch *b, const float *const *Bds, const ProxA
 namespace {
 template <int FMT, bool SPLIT, int EPI>
 void launch_grouped(const GemmBatch *b, int st, int k, cudaStream_t s) {
-    using C = Cfg<FMT, SPLIT, BN_TILE>;
-    umma_gemm_grouped<FMT, SPLIT, BN_TILE, EPI><<<b->nwork[st], 320, C::SMEM, s>>>(b->d_maps[st], b->d_args[st],
-                                                                                   b->d_work[st], k);
+    const int grid = b->nwork[st] < b->sms ? b->nwork[st] : b->sms;
+    // The parameter-space maps are unused in grouped mode: pass the first problem's.
+    const Operand &P0 = b->paths[0]->PA;
+    umma_gemm_persistent<FMT, SPLIT, BN_TILE, EPI, true><<<grid, 320, PCfg<FMT, SPLIT, BN_TILE>::SMEM, s>>>(
+        P0.map_hi, P0.map_hi, P0.map_hi, P0.map_hi, b->h_args[st][0], 1, b->nwork[st], b->d_maps[st], b->d_args[st],
+        b->d_work[st], k);
 }
 template <int FMT, bool SPLIT>
 void grouped_stage(const GemmBatch *b, int st, int k, cudaStream_t s) {
