@@ -247,7 +247,7 @@ def run_large(args, torch):
             peak = bf16 if prec.startswith("bf16") else bf16 * (1.1 / 2.25)
             bound = "tensor"
         else:
-            work = alg if op == "banded" else [sum(alg), 0, 0, 0]
+            work = {"banded": alg, "banded_fused": [alg[0] + alg[1], 0, alg[2] + alg[3], 0]}.get(op, [sum(alg), 0, 0, 0])
             peak, bound = FP32_PEAK_TFLOPS, "alu"
         dom = int(np.argmax(sm))
         ach = work[dom] / (sm[dom] / 1e3) / 1e12
@@ -349,7 +349,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--forms", default="fp32:banded_fused,fp32:banded,bf16x3:gemm_band,tf32x3:gemm_band,bf16:gemm_band,tf32:gemm_band",
+    ap.add_argument("--forms", default="fp32:banded_fused,fp32:banded,fp32:banded_persistent,bf16x3:gemm_band,tf32x3:gemm_band,bf16:gemm_band,tf32:gemm_band",
                     help="comma list of prec:op forms to measure")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "cfg4"])
@@ -360,9 +360,9 @@ def main():
         return run_reference(args)
     if args.workload != "cfg2":
         import torch
-        if args.forms.startswith("fp32:banded_fused,fp32:banded,bf16x3"):
-            args.forms = ("fp32:banded,bf16x3:gemm_band,tf32x3:gemm_band,bf16x3:gemm_dense" if args.workload == "cfg3"
-                          else "fp32:banded,bf16x3:gemm_band,tf32x3:gemm_band")
+        if args.forms.startswith("fp32:banded_fused,fp32:banded,fp32:banded_persistent"):
+            args.forms = ("fp32:banded_fused,fp32:banded,bf16x3:gemm_band,tf32x3:gemm_band,bf16x3:gemm_dense"
+                          if args.workload == "cfg3" else "fp32:banded,bf16x3:gemm_band,tf32x3:gemm_band")
         return run_large(args, torch) if args.workload == "cfg3" else run_batched(args, torch)
 
     import torch
@@ -455,9 +455,11 @@ def main():
         alg = [2.0 * wA * r * n * n, 2.0 * wB * r * n * n, 2.0 * wA * r * n * n, 2.0 * wB * r * n * n]
         sm = [float(x) for x in res["stage_ms"]]
         dom = int(np.argmax(sm))
-        if op == "banded_fused":
+        if op == "banded_persistent":
             work = [sum(alg), 0.0, 0.0, 0.0]   # one persistent launch: all four stages per iteration
-        if op in ("banded", "banded_fused"):
+        elif op == "banded_fused":
+            work = [alg[0] + alg[1], 0.0, alg[2] + alg[3], 0.0]   # one kernel per operator application
+        if op in ("banded", "banded_fused", "banded_persistent"):
             work = alg
             bound, peak, unit = "alu", FP32_PEAK_TFLOPS, "TFLOP/s"
             peak_src = "152 SM x 128 FP32 lanes x 2 x 2070 MHz (derived)"
@@ -469,7 +471,9 @@ def main():
             peak_src = ("%s bf16 burst" % peak_src_name) + ("" if prec.startswith("bf16") else " x 1.1/2.25 (tf32 nominal ratio)")
         achieved = work[dom] / (sm[dom] / 1e3) / 1e12
         ok = err <= TOL.get(prec, float("inf"))
-        kname = "band_solve_persistent (whole iteration)" if op == "banded_fused" else STAGES[dom]
+        kname = {"banded_persistent": "band_solve_persistent (whole iteration)",
+                 "banded_fused": ["band_op_fused_kernel (forward + residual)", "",
+                                  "band_op_fused_kernel (adjoint + shrink + momentum)", ""][dom]}.get(op, STAGES[dom])
         lines[key] = dict(kernel=kname, value=v, err=err, dpsnr=dpsnr, stage_ms=sm, dom=dom, achieved=achieved, ok=ok,
                           bound=bound, peak=peak, unit=unit, peak_src=peak_src, prec=prec,
                           op_tflops_alg=sum(alg) * v / world / 1e12,

@@ -74,8 +74,11 @@ typedef enum {
     SFISTA_OP_BANDED = 1,      /* factors applied from compact band storage (FP32/FP64 FMA)  */
     SFISTA_OP_GEMM_BAND = 2,   /* dense-factor GEMMs that skip K tiles outside the band       */
     SFISTA_OP_GEMM_DENSE = 3,  /* dense-factor GEMMs over the full K range (Sec. 3.3 O(s(nm^2+mn^2))) */
-    SFISTA_OP_BANDED_FUSED = 4 /* banded FP32 operator, the whole iteration loop in one persistent
-                                  cooperative launch (grid barrier between the four phases) */
+    SFISTA_OP_BANDED_PERSISTENT = 4, /* banded FP32 operator, the whole iteration loop in one
+                                        persistent cooperative launch (grid barrier between phases) */
+    SFISTA_OP_BANDED_FUSED = 5 /* banded FP32 operator, one kernel per operator application: the
+                                  row pass is kept in shared memory for the column pass (the
+                                  automatic FP32 choice up to 1024^2 pixels and band width 48) */
 } sfista_operator;
 
 typedef struct {
@@ -211,8 +214,8 @@ sfista_status sfista_solve_batched(sfista_ctx *const *ctxs,
 /*
  * Differentiating the unrolled solve (Alg. 2 for a fixed number of
  * iterations, no projection, L held fixed).  Both calls need a context with
- * the banded operator form (SFISTA_FP32 with SFISTA_OP_BANDED or
- * SFISTA_OP_BANDED_FUSED); otherwise ENOTSUP.
+ * a banded operator form (SFISTA_FP32 with SFISTA_OP_BANDED,
+ * SFISTA_OP_BANDED_PERSISTENT or SFISTA_OP_BANDED_FUSED); otherwise ENOTSUP.
  *
  * sfista_unrolled_fwd -- X_iters from X_0 = 0 into d_x (device FP32, m x n),
  *   saving (X_k, X_{k-1}) at k = 0, ckpt_every, 2 ckpt_every, ... into d_ckpt

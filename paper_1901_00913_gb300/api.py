@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libsfista.so")
 OK, EINVAL, ENOMEM, ECUDA, ENOTSUP, ENUMERIC, ETIMEOUT = range(7)
 BC = {"zero": 0, "reflexive": 1, "reflective": 1, "periodic": 2}
 PREC = {"fp32": 0, "tf32": 1, "tf32x3": 2, "bf16": 3, "bf16x3": 4}
-OP = {"auto": 0, "banded": 1, "gemm_band": 2, "gemm_dense": 3, "banded_fused": 4}
+OP = {"auto": 0, "banded": 1, "gemm_band": 2, "gemm_dense": 3, "banded_persistent": 4, "banded_fused": 5}
 PREC_NAME = {v: k for k, v in PREC.items()}
 OP_NAME = {v: k for k, v in OP.items()}
 

@@ -114,7 +114,7 @@ struct Scratch {
 
 sfista_status check_unrolled(sfista_ctx *c, int iters, int ckpt) {
     if (!c) return fail(SFISTA_EINVAL, "context is NULL");
-    if (c->op != SFISTA_OP_BANDED && c->op != SFISTA_OP_BANDED_FUSED)
+    if (!is_banded(c->op))
         return fail(SFISTA_ENOTSUP, "the unrolled adjoint runs on the banded FP32 operator form");
     if (c->opts.project_nonneg) return fail(SFISTA_ENOTSUP, "the projection is not differentiable");
     if (iters < 1 || ckpt < 1) return fail(SFISTA_EINVAL, "iters and ckpt_every must be >= 1");

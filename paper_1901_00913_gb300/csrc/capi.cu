@@ -127,7 +127,16 @@ namespace {
 // Stage `st` (0..3) of iteration k; see sfista_time_stages for the numbering.
 void enqueue_stage(sfista_ctx *c, int st, const ProxArgs &pa) {
     const HostSetup &h = c->hs;
-    if (c->op == SFISTA_OP_BANDED || c->op == SFISTA_OP_BANDED_FUSED) {
+    if (c->op == SFISTA_OP_BANDED_FUSED) {
+        // Two launches per iteration: stage 0 = forward operator + residual,
+        // stage 2 = adjoint + shrink / momentum (stages 1 and 3 are empty).
+        if (st == 0)
+            launch_band_op_fused(c->Yop, c->m, c->n, c->r, c->fA, h.A.lo, h.A.w, c->fB, h.B.lo, h.B.w, EPI_RESIDUAL,
+                                 c->R, pa, c->stream);
+        else if (st == 2)
+            launch_band_op_fused(c->R, c->m, c->n, c->r, c->fAT, h.AT.lo, h.AT.w, c->fBT, h.BT.lo, h.BT.w, EPI_PROX,
+                                 nullptr, pa, c->stream);
+    } else if (is_banded(c->op)) {
         switch (st) {
             case 0: launch_band_rows<float>(c->Yop, c->m, c->n, c->fA, h.A.lo, h.A.w, c->r, c->Z, c->stream); break;
             case 1: launch_band_cols<float>(c->Z, c->m, c->n, c->fB, h.B.lo, h.B.w, c->r, EPI_RESIDUAL, c->R, pa,
@@ -150,7 +159,7 @@ namespace {
 
 sfista_status run_loop(sfista_ctx *c, double lam, int k0, int iters) {
     if (iters <= 0) return SFISTA_OK;
-    if (c->op == SFISTA_OP_BANDED_FUSED) {
+    if (c->op == SFISTA_OP_BANDED_PERSISTENT) {
         const HostSetup &h = c->hs;
         ProxArgs pa = prox_args(c, k0 + 1, lam);
         SF_CUDA(launch_persistent(c->pgrid, c->psmem, c->prows_chunk, c->pcols_chunk, c->m, c->n, c->r, c->fA, h.A, c->fB, h.B, c->fAT, h.AT, c->fBT,
@@ -388,8 +397,16 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int ce
     c->N = (size_t)img_rows * img_cols;
     c->prec = o.prec;
     c->op = o.op;
-    if (c->op == SFISTA_OP_AUTO) c->op = (c->prec == SFISTA_FP32) ? SFISTA_OP_BANDED : SFISTA_OP_GEMM_BAND;
-    if ((c->op == SFISTA_OP_BANDED || c->op == SFISTA_OP_BANDED_FUSED) && c->prec != SFISTA_FP32) {
+    if (c->op == SFISTA_OP_AUTO) {
+        // Measured on GB300: one kernel per operator application wins while the
+        // halo rows it recomputes stay below ~1.5x the tile (band <= 48) and the
+        // image is small enough for launch latency to dominate; otherwise the
+        // two-pass form.  Tensor-core forms default to band-aware GEMMs.
+        const int wl = std::max(c->hs.B.w, c->hs.BT.w);
+        const bool small = (size_t)img_rows * img_cols <= ((size_t)1 << 20) && wl <= 48;
+        c->op = (c->prec == SFISTA_FP32) ? (small ? SFISTA_OP_BANDED_FUSED : SFISTA_OP_BANDED) : SFISTA_OP_GEMM_BAND;
+    }
+    if (is_banded(c->op) && c->prec != SFISTA_FP32) {
         delete c;
         return fail(SFISTA_ENOTSUP, "the banded operator form runs in FP32 only");
     }
@@ -435,7 +452,12 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int ce
         (e = cudaMalloc((void **)&c->status, 16)))
         return bail(fail(SFISTA_ENOMEM, std::string("state buffers: ") + cudaGetErrorString(e)));
     if ((e = cudaMemset(c->status, 0, 16))) return bail(fail(SFISTA_ECUDA, cudaGetErrorString(e)));
-    if (c->op == SFISTA_OP_BANDED_FUSED) {
+    if (c->op == SFISTA_OP_BANDED_FUSED &&
+        !band_op_fused_prepare(c->r, std::max(h.A.w, h.AT.w), std::max(h.B.w, h.BT.w))) {
+        if (o.op == SFISTA_OP_BANDED_FUSED) return bail(fail(SFISTA_ENOTSUP, "fused banded tile exceeds shared memory"));
+        c->op = SFISTA_OP_BANDED;   // automatic choice falls back to the two-pass form
+    }
+    if (c->op == SFISTA_OP_BANDED_PERSISTENT) {
         if ((e = cudaMalloc((void **)&c->bar, 16)) || (e = cudaMemset(c->bar, 0, 16)))
             return bail(fail(SFISTA_ENOMEM, std::string("barrier words: ") + cudaGetErrorString(e)));
         st = persistent_config(c->m, c->n, c->r, wmax, c->dev, &c->pgrid, &c->psmem, &c->prows_chunk,
@@ -537,7 +559,12 @@ sfista_status sfista_apply(sfista_ctx *c, const float *d_x, float *d_y, int tran
     SF_CUDA(cudaStreamWaitEvent(c->stream, c->ev_in, 0));
     const HostSetup &h = c->hs;
     ProxArgs pa{};
-    if (c->op == SFISTA_OP_BANDED || c->op == SFISTA_OP_BANDED_FUSED) {
+    if (c->op == SFISTA_OP_BANDED_FUSED) {
+        const Band &F = transpose ? h.AT : h.A;
+        const Band &G = transpose ? h.BT : h.B;
+        launch_band_op_fused(d_x, c->m, c->n, c->r, transpose ? c->fAT : c->fA, F.lo, F.w, transpose ? c->fBT : c->fB,
+                             G.lo, G.w, EPI_STORE, d_y, pa, c->stream);
+    } else if (is_banded(c->op)) {
         const Band &F = transpose ? h.AT : h.A;
         const Band &G = transpose ? h.BT : h.B;
         launch_band_rows<float>(d_x, c->m, c->n, transpose ? c->fAT : c->fA, F.lo, F.w, c->r, c->Z, c->stream);
@@ -848,7 +875,7 @@ sfista_status sfista_time_stages(sfista_ctx *c, const float *d_b, double lambda,
     for (int i = 0; i < 5; ++i) SF_CUDA(cudaEventCreate(&ev[i]));
     double acc[4] = {0, 0, 0, 0};
     cudaError_t e = cudaSuccess;
-    if (c->op == SFISTA_OP_BANDED_FUSED) {
+    if (c->op == SFISTA_OP_BANDED_PERSISTENT) {
         // One persistent launch covers all four stages: report its mean time
         // per iteration in slot 0.
         e = cudaEventRecord(ev[0], c->stream);

@@ -118,6 +118,16 @@ void launch_band_grouped_stage(int st, const BandProb *probs, const BandItem *it
 int band_rows_tiles(int m, int n);
 int band_cols_tiles(int m, int n);
 
+// One kernel per banded operator application (kernels_fused.cu).
+size_t band_op_fused_smem(int r, int wF, int wG);
+bool band_op_fused_prepare(int r, int wF, int wG);
+void launch_band_op_fused(const float *In, int m, int n, int r, const float *Fb, int loF, int wF, const float *Gb,
+                          int loG, int wG, EpiKind epi, float *Out, const ProxArgs &pa, cudaStream_t s);
+
+inline bool is_banded(int op) {
+    return op == SFISTA_OP_BANDED || op == SFISTA_OP_BANDED_PERSISTENT || op == SFISTA_OP_BANDED_FUSED;
+}
+
 // Small helpers.
 void launch_fill_f64(double *p, size_t count, double v, cudaStream_t s);
 void launch_f64_to_f32(const double *in, float *out, size_t count, cudaStream_t s);

@@ -24,7 +24,7 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-@pytest.mark.parametrize("op", ["banded", "banded_fused"])
+@pytest.mark.parametrize("op", ["banded", "banded_fused", "banded_persistent"])
 def test_gradients_match_oracle_reverse_mode(op):
     m, n, r, K, ck = 64, 56, 2, 12, 5
     g = W.rng(401)

@@ -56,16 +56,17 @@ def test_blur_exact_matches_oracle(bc):
 
 
 # ------------------------------------------------------------------ operator
+@pytest.mark.parametrize("op", ["banded", "banded_fused"])
 @pytest.mark.parametrize("bc", [0, 1])
 @pytest.mark.parametrize("transpose", [False, True])
 @pytest.mark.parametrize("shape", [(200, 176), (64, 64), (37, 45)])
-def test_apply_matches_oracle(bc, transpose, shape):
+def test_apply_matches_oracle(bc, transpose, shape, op):
     """A_s X and A_s^T X on ragged sizes with a non-centred, non-square PSF."""
     m, n = shape
     g = W.rng(102 + m)
     P = W.random_psf(g, 13, 11)
     ka = kron.kron_approx(P, 4, 7, m, n, bc, 3)
-    s = api.Sfista(P, (m, n), bc, 3, center=(4, 7), prec="fp32", op="banded", lipschitz=1.0)
+    s = api.Sfista(P, (m, n), bc, 3, center=(4, 7), prec="fp32", op=op, lipschitz=1.0)
     X = g.standard_normal((m, n)).astype(np.float32)
     Y = s.apply(_cuda(X), transpose=transpose).cpu().numpy()
     Yo = (oracle.kron_apply_T if transpose else oracle.kron_apply)(X.astype(np.float64), ka)
@@ -139,7 +140,7 @@ def cfg2():
     return pr, b, ka, L, Xo
 
 
-@pytest.mark.parametrize("op", ["banded", "banded_fused"])
+@pytest.mark.parametrize("op", ["banded", "banded_fused", "banded_persistent"])
 def test_solve_config2_fp32(cfg2, op):
     """512^2, rotated Gaussian, reflexive, r=3, 200 iterations: rel err <= 1e-5."""
     pr, b, ka, L, Xo = cfg2
@@ -150,7 +151,7 @@ def test_solve_config2_fp32(cfg2, op):
     s.close()
 
 
-@pytest.mark.parametrize("op", ["banded", "banded_fused"])
+@pytest.mark.parametrize("op", ["banded", "banded_fused", "banded_persistent"])
 @pytest.mark.parametrize("bc", [0, 1])
 def test_solve_ragged(bc, op):
     m, n = 200, 176
@@ -177,7 +178,7 @@ def test_graph_and_direct_launch_agree():
     np.testing.assert_array_equal(outs[0], outs[1])
 
 
-@pytest.mark.parametrize("op", ["banded", "banded_fused", "gemm_band"])
+@pytest.mark.parametrize("op", ["banded", "banded_fused", "banded_persistent", "gemm_band"])
 def test_resume_state_matches_uninterrupted(op):
     P = W.rotated_gaussian_psf(15, 2.0, 1.0, 0.3)
     x, b, _ = _problem(96, 80, P, 1, 107)
@@ -200,7 +201,7 @@ def test_resume_state_matches_uninterrupted(op):
 
 
 @pytest.mark.parametrize("op,prec,tol", [("banded", "fp32", 1e-5), ("banded_fused", "fp32", 1e-5),
-                                          ("gemm_band", "bf16x3", 1e-4)])
+                                          ("banded_persistent", "fp32", 1e-5), ("gemm_band", "bf16x3", 1e-4)])
 def test_projection_matches_oracle(op, prec, tol):
     P = W.rotated_gaussian_psf(15, 2.0, 1.0, 0.3)
     x, b, _ = _problem(96, 80, P, 1, 108)
@@ -246,6 +247,7 @@ def test_config3_full_size_operator_and_steps():
     n = 2048
     ka = kron.kron_approx(pr.psf, cr, cc, n, n, pr.bc, pr.r)
     s = api.Sfista(pr.psf, (n, n), pr.bc, pr.r, prec="fp32", lipschitz=1.0)
+    assert s.info()["op"] == "banded"          # automatic choice at 2048^2 with a 63-wide band
     X = pr.x_true.astype(np.float32)
     for tr in (False, True):
         Y = s.apply(_cuda(X), transpose=tr).cpu().numpy()
