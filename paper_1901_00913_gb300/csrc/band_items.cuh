@@ -63,6 +63,14 @@ __device__ __forceinline__ void stage(T *dst, const T *src, bool pred, const T *
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// 16-byte global -> shared copy of `bytes` (0..16) bytes, zero-filling the
+// rest; dst and src must be 16-byte aligned (src unused when bytes == 0).
+__device__ __forceinline__ void stage16(float *dst, const float *src, int bytes, const float *safe) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(bytes > 0 ? src : safe), "r"(bytes)
+                 : "memory");
+}
+
 template <bool CG>
 __device__ __forceinline__ void stage_wait() {
     if (!CG) asm volatile("cp.async.wait_all;" ::: "memory");
@@ -160,18 +168,19 @@ __device__ __forceinline__ void rows_item(const T *__restrict__ In, int m, int n
 }
 
 // K terms at once, each with its own Z window and accumulator chain; the
-// chains are summed into acc at the end (term order is kept).
-template <typename T, int K>
+// chains are summed into acc at the end (term order is kept).  ZST is the
+// row stride of the staged Z tile.
+template <typename T, int K, int ZST = TC>
 __device__ __forceinline__ void cols_terms(const T *zc, const T *gr, int w, int zs, T *acc) {
     T a[K][4], z[K][4];
 #pragma unroll
     for (int q = 0; q < K; ++q) {
         a[q][0] = a[q][1] = a[q][2] = a[q][3] = T(0);
-        const T *zq = zc + q * zs * TC;
+        const T *zq = zc + q * zs * ZST;
         z[q][0] = zq[0];
-        z[q][1] = zq[TC];
-        z[q][2] = zq[2 * TC];
-        z[q][3] = zq[3 * TC];
+        z[q][1] = zq[ZST];
+        z[q][2] = zq[2 * ZST];
+        z[q][3] = zq[3 * ZST];
     }
 #pragma unroll 2
     for (int k = 0; k < w; ++k) {
@@ -186,7 +195,7 @@ __device__ __forceinline__ void cols_terms(const T *zc, const T *gr, int w, int 
             z[q][0] = z[q][1];
             z[q][1] = z[q][2];
             z[q][2] = z[q][3];
-            z[q][3] = zc[(q * zs + k + 4) * TC];
+            z[q][3] = zc[(q * zs + k + 4) * ZST];
         }
     }
 #pragma unroll

@@ -23,6 +23,7 @@ namespace {
 using band::NT;
 using band::TA;
 using band::TC;
+constexpr int ZST = TC + 4;   // Z row stride: float4 stores of 32 consecutive rows hit distinct banks
 
 struct FusedGeom {
     int zs;    // staged Z rows per term: TA + wG (last one spare, zero)
@@ -38,7 +39,7 @@ __host__ __device__ inline FusedGeom fused_geom(int r, int wF, int wG) {
     g.off_f = (in + 3) & ~size_t(3);
     g.off_g = g.off_f + (size_t)r * wF * TC;
     g.off_z = g.off_g + (size_t)r * wG * TA;
-    g.total = g.off_z + (size_t)r * g.zs * TC;
+    g.total = g.off_z + (size_t)r * g.zs * ZST;
     return g;
 }
 
@@ -83,11 +84,22 @@ __global__ void __launch_bounds__(NT) band_op_fused_kernel(const float *__restri
     const int e0 = a0 + loG;                 // first staged row
     const int spanc = TC + wF - 1, spanr = TA + wG - 1;
     // Constant band tiles first, then (after the previous kernel) the input tile.
-    const bool cin = c0 + lane < n, rin = a0 + lane < m;
-    for (int tk = warp; tk < r * wF; tk += NT / 32)
-        band::stage<float, false>(Fs + tk * TC + lane, Fb + (size_t)tk * n + c0 + lane, cin, Fb);
-    for (int tk = warp; tk < r * wG; tk += NT / 32)
-        band::stage<float, false>(Gs + tk * TA + lane, Gb + (size_t)tk * m + a0 + lane, rin, Gb);
+    if ((n & 3) == 0 && (m & 3) == 0) {
+        // 16-byte copies: thread (row tk, quad j) copies 4 band entries; the
+        // tail of a ragged tile is zero-filled by the copy's source size.
+        const int j = tid & 7;
+        const int fb = min(16, max(0, (n - (c0 + 4 * j)) * 4)), gb = min(16, max(0, (m - (a0 + 4 * j)) * 4));
+        for (int tk = tid >> 3; tk < r * wF; tk += NT / 8)
+            band::stage16(Fs + tk * TC + 4 * j, Fb + (size_t)tk * n + c0 + 4 * j, fb, Fb);
+        for (int tk = tid >> 3; tk < r * wG; tk += NT / 8)
+            band::stage16(Gs + tk * TA + 4 * j, Gb + (size_t)tk * m + a0 + 4 * j, gb, Gb);
+    } else {
+        const bool cin = c0 + lane < n, rin = a0 + lane < m;
+        for (int tk = warp; tk < r * wF; tk += NT / 32)
+            band::stage<float, false>(Fs + tk * TC + lane, Fb + (size_t)tk * n + c0 + lane, cin, Fb);
+        for (int tk = warp; tk < r * wG; tk += NT / 32)
+            band::stage<float, false>(Gs + tk * TA + lane, Gb + (size_t)tk * m + a0 + lane, rin, Gb);
+    }
     band::pdl_wait();
     for (int row = warp; row < geo.zs; row += NT / 32) {
         const int ge = e0 + row;
@@ -107,13 +119,13 @@ __global__ void __launch_bounds__(NT) band_op_fused_kernel(const float *__restri
         if (row < geo.zs) {
             const float *xr = Ins + row * geo.sp + cb;
             for (int tb = 0; tb < r; tb += 4) {
-                float *zo = Zs + ((size_t)tb * geo.zs + row) * TC + cb;
+                float *zo = Zs + ((size_t)tb * geo.zs + row) * ZST + cb;
                 const float *fr = Fs + tb * wF * TC + cb;
                 switch (min(4, r - tb)) {
-                    case 1: rows_to_smem<1>(xr, fr, wF, zo, geo.zs * TC); break;
-                    case 2: rows_to_smem<2>(xr, fr, wF, zo, geo.zs * TC); break;
-                    case 3: rows_to_smem<3>(xr, fr, wF, zo, geo.zs * TC); break;
-                    default: rows_to_smem<4>(xr, fr, wF, zo, geo.zs * TC); break;
+                    case 1: rows_to_smem<1>(xr, fr, wF, zo, geo.zs * ZST); break;
+                    case 2: rows_to_smem<2>(xr, fr, wF, zo, geo.zs * ZST); break;
+                    case 3: rows_to_smem<3>(xr, fr, wF, zo, geo.zs * ZST); break;
+                    default: rows_to_smem<4>(xr, fr, wF, zo, geo.zs * ZST); break;
                 }
             }
         }
@@ -123,13 +135,13 @@ __global__ void __launch_bounds__(NT) band_op_fused_kernel(const float *__restri
     const int rb = warp * 4, gc = c0 + lane;
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     for (int tb = 0; tb < r; tb += 4) {
-        const float *zc = Zs + ((size_t)tb * geo.zs + rb) * TC + lane;
+        const float *zc = Zs + ((size_t)tb * geo.zs + rb) * ZST + lane;
         const float *gr = Gs + tb * wG * TA + rb;
         switch (min(4, r - tb)) {
-            case 1: band::cols_terms<float, 1>(zc, gr, wG, geo.zs, acc); break;
-            case 2: band::cols_terms<float, 2>(zc, gr, wG, geo.zs, acc); break;
-            case 3: band::cols_terms<float, 3>(zc, gr, wG, geo.zs, acc); break;
-            default: band::cols_terms<float, 4>(zc, gr, wG, geo.zs, acc); break;
+            case 1: band::cols_terms<float, 1, ZST>(zc, gr, wG, geo.zs, acc); break;
+            case 2: band::cols_terms<float, 2, ZST>(zc, gr, wG, geo.zs, acc); break;
+            case 3: band::cols_terms<float, 3, ZST>(zc, gr, wG, geo.zs, acc); break;
+            default: band::cols_terms<float, 4, ZST>(zc, gr, wG, geo.zs, acc); break;
         }
     }
     if (gc < n) {
