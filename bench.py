@@ -455,12 +455,13 @@ def main():
         alg = [2.0 * wA * r * n * n, 2.0 * wB * r * n * n, 2.0 * wA * r * n * n, 2.0 * wB * r * n * n]
         sm = [float(x) for x in res["stage_ms"]]
         dom = int(np.argmax(sm))
-        if op == "banded_persistent":
-            work = [sum(alg), 0.0, 0.0, 0.0]   # one persistent launch: all four stages per iteration
-        elif op == "banded_fused":
-            work = [alg[0] + alg[1], 0.0, alg[2] + alg[3], 0.0]   # one kernel per operator application
         if op in ("banded", "banded_fused", "banded_persistent"):
-            work = alg
+            if op == "banded_persistent":
+                work = [sum(alg), 0.0, 0.0, 0.0]   # one persistent launch: all four stages per iteration
+            elif op == "banded_fused":
+                work = [alg[0] + alg[1], 0.0, alg[2] + alg[3], 0.0]   # one kernel per operator application
+            else:
+                work = alg
             bound, peak, unit = "alu", FP32_PEAK_TFLOPS, "TFLOP/s"
             peak_src = "152 SM x 128 FP32 lanes x 2 x 2070 MHz (derived)"
         else:
