@@ -168,19 +168,18 @@ __device__ __forceinline__ void rows_item(const T *__restrict__ In, int m, int n
 }
 
 // K terms at once, each with its own Z window and accumulator chain; the
-// chains are summed into acc at the end (term order is kept).  ZST is the
-// row stride of the staged Z tile.
-template <typename T, int K, int ZST = TC>
+// chains are summed into acc at the end (term order is kept).
+template <typename T, int K>
 __device__ __forceinline__ void cols_terms(const T *zc, const T *gr, int w, int zs, T *acc) {
     T a[K][4], z[K][4];
 #pragma unroll
     for (int q = 0; q < K; ++q) {
         a[q][0] = a[q][1] = a[q][2] = a[q][3] = T(0);
-        const T *zq = zc + q * zs * ZST;
+        const T *zq = zc + q * zs * TC;
         z[q][0] = zq[0];
-        z[q][1] = zq[ZST];
-        z[q][2] = zq[2 * ZST];
-        z[q][3] = zq[3 * ZST];
+        z[q][1] = zq[TC];
+        z[q][2] = zq[2 * TC];
+        z[q][3] = zq[3 * TC];
     }
 #pragma unroll 2
     for (int k = 0; k < w; ++k) {
@@ -195,7 +194,7 @@ __device__ __forceinline__ void cols_terms(const T *zc, const T *gr, int w, int 
             z[q][0] = z[q][1];
             z[q][1] = z[q][2];
             z[q][2] = z[q][3];
-            z[q][3] = zc[(q * zs + k + 4) * ZST];
+            z[q][3] = zc[(q * zs + k + 4) * TC];
         }
     }
 #pragma unroll

@@ -6,11 +6,35 @@
 // shrink + Step 3 momentum).  A block computes a 32 x 32 output tile: it
 // stages the input tile with its halo in both directions and all band tiles
 // (cp.async, one load phase), computes the intermediate rows Z_i for the
-// 32 + wG - 1 rows the column pass needs into shared memory, then runs the
-// column pass.  Z never goes to global memory and an iteration of Alg. 2 is
-// two launches.  The row pass repeats the halo rows' work ((32 + wG - 1) / 32
-// times the two-pass count); at small and medium sizes the launch and load
-// latency saved outweighs it.
+// rows the column pass needs into shared memory, then runs the column pass.
+// Z never goes to global memory and an iteration of Alg. 2 is two launches.
+//
+// Tap padding.  Both passes step through the taps four at a time with
+// 16-byte shared loads.  The input tile is staged from the 4-aligned column
+// c0 + loF - off (off = loF mod 4), so the row-pass coefficients are placed
+// `off` taps late and the tap count is rounded up to a multiple of 4 with
+// zero coefficients (wF4 taps); the column pass rounds wG up the same way
+// (wG4).  Zero taps add exact zeros, in the same order, so every output is
+// the sum the unpadded loop forms.
+//
+// Shared layout (floats):
+//   In [rows][sp]        staged input, rows = (32 + wG4) rounded up to 32,
+//                        sp = 4 * odd >= 32 + wF4
+//   F  [r][wF4][32]      row-pass coefficients of this column tile
+//   G  [r][wG4][32]      column-pass coefficients of this row tile
+//   Zt [r][32][zsp]      Z transposed (column-major per term), zsp = 4 * odd
+// Odd multiples of four floats make the 16-byte accesses of 8 consecutive
+// lanes (rows of In, columns of Zt) land in distinct banks.
+//
+// Row pass: lane l owns Z rows e and e + 32 of a 64-row group, warp w
+// columns 4w .. 4w+3; one broadcast coefficient load feeds 8 FMAs and the
+// input window advances by one 16-byte load per 4 taps and row.
+// Column pass: lane l owns column l, warp w output rows 4w .. 4w+3; per 4
+// taps one 16-byte Zt load (4 consecutive rows of the lane's column) and
+// four broadcast coefficient loads.
+// The row pass repeats the halo rows' work ((32 + wG4) / 32 times the
+// two-pass count); at small and medium sizes the launch and load latency
+// saved outweighs it.
 #include <algorithm>
 
 #include "band_items.cuh"
@@ -23,110 +47,216 @@ namespace {
 using band::NT;
 using band::TA;
 using band::TC;
-constexpr int ZST = TC + 4;   // Z row stride: float4 stores of 32 consecutive rows hit distinct banks
 
 struct FusedGeom {
-    int zs;    // staged Z rows per term: TA + wG (last one spare, zero)
-    int sp;    // input tile row stride: (TC + wF) | 1
+    int off;         // loF mod 4: leading zero taps of the row pass
+    int wF4, wG4;    // padded tap counts (multiples of 4)
+    int zs;          // Z rows the column pass reads: TA + wG4
+    int rows;        // staged input rows: zs rounded up to 32
+    int sp, zsp;     // row strides of In and Zt
     size_t off_f, off_g, off_z, total;   // float offsets / size
 };
 
-__host__ __device__ inline FusedGeom fused_geom(int r, int wF, int wG) {
+__host__ __device__ inline FusedGeom fused_geom(int r, int loF, int wF, int wG) {
     FusedGeom g;
-    g.zs = TA + wG;
-    g.sp = (TC + wF) | 1;
-    const size_t in = (size_t)g.zs * g.sp;
-    g.off_f = (in + 3) & ~size_t(3);
-    g.off_g = g.off_f + (size_t)r * wF * TC;
-    g.off_z = g.off_g + (size_t)r * wG * TA;
-    g.total = g.off_z + (size_t)r * g.zs * ZST;
+    g.off = ((loF % 4) + 4) % 4;
+    g.wF4 = (wF + g.off + 3) & ~3;
+    g.wG4 = (wG + 3) & ~3;
+    g.zs = TA + g.wG4;
+    g.rows = (g.zs + 31) & ~31;
+    g.sp = 4 * (((TC + g.wF4) / 4) | 1);
+    g.zsp = 4 * ((g.zs / 4) | 1);
+    g.off_f = (size_t)g.rows * g.sp;
+    g.off_g = g.off_f + (size_t)r * g.wF4 * TC;
+    g.off_z = g.off_g + (size_t)r * g.wG4 * TA;
+    g.total = g.off_z + (size_t)r * TC * g.zsp;
     return g;
 }
 
-// Row pass into shared memory for K terms: lane l owns Z rows rbase + l, warp
-// w columns 4w .. 4w+3; the input window is shared by the K terms.
-template <int K>
-__device__ __forceinline__ void rows_to_smem(const float *xr, const float *fr, int wF, float *zs_out, int zs_stride) {
-    float acc[K][4];
+__device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+
+// Row pass for K terms on one (TWO: two) rows per lane.  xa: the lane's first
+// input row at column cb; fr: coefficients at column cb of the first term;
+// zt: Zt entry (first term, column cb, row e).
+template <int K, bool TWO>
+__device__ __forceinline__ void rows_pass(const float *xa, int sp, const float *fr, int wF4, float *zt, int zsp,
+                                          bool sta, bool stb) {
+    float acc[TWO ? 2 : 1][K][4];
 #pragma unroll
-    for (int q = 0; q < K; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
-    float x0 = xr[0], x1 = xr[1], x2 = xr[2], x3 = xr[3];
-#pragma unroll 2
-    for (int k = 0; k < wF; ++k) {
+    for (int h = 0; h < (TWO ? 2 : 1); ++h)
 #pragma unroll
-        for (int q = 0; q < K; ++q) {
-            const float4 f = *reinterpret_cast<const float4 *>(fr + (q * wF + k) * TC);
-            acc[q][0] = fmaf(x0, f.x, acc[q][0]);
-            acc[q][1] = fmaf(x1, f.y, acc[q][1]);
-            acc[q][2] = fmaf(x2, f.z, acc[q][2]);
-            acc[q][3] = fmaf(x3, f.w, acc[q][3]);
+        for (int q = 0; q < K; ++q) acc[h][q][0] = acc[h][q][1] = acc[h][q][2] = acc[h][q][3] = 0.f;
+    const float *xb = xa + 32 * sp;
+    float4 a0 = lds4(xa), b0 = TWO ? lds4(xb) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+    for (int k = 0; k < wF4; k += 4) {
+        const float4 a1 = lds4(xa + k + 4);
+        const float4 b1 = TWO ? lds4(xb + k + 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float xw[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float yw[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+#pragma unroll
+            for (int q = 0; q < K; ++q) {
+                const float4 f = lds4(fr + (q * wF4 + k + t) * TC);
+                acc[0][q][0] = fmaf(xw[t], f.x, acc[0][q][0]);
+                acc[0][q][1] = fmaf(xw[t + 1], f.y, acc[0][q][1]);
+                acc[0][q][2] = fmaf(xw[t + 2], f.z, acc[0][q][2]);
+                acc[0][q][3] = fmaf(xw[t + 3], f.w, acc[0][q][3]);
+                if (TWO) {
+                    acc[TWO ? 1 : 0][q][0] = fmaf(yw[t], f.x, acc[TWO ? 1 : 0][q][0]);
+                    acc[TWO ? 1 : 0][q][1] = fmaf(yw[t + 1], f.y, acc[TWO ? 1 : 0][q][1]);
+                    acc[TWO ? 1 : 0][q][2] = fmaf(yw[t + 2], f.z, acc[TWO ? 1 : 0][q][2]);
+                    acc[TWO ? 1 : 0][q][3] = fmaf(yw[t + 3], f.w, acc[TWO ? 1 : 0][q][3]);
+                }
+            }
         }
-        x0 = x1;
-        x1 = x2;
-        x2 = x3;
-        x3 = xr[k + 4];
+        a0 = a1;
+        b0 = b1;
     }
 #pragma unroll
     for (int q = 0; q < K; ++q)
-        *reinterpret_cast<float4 *>(zs_out + q * zs_stride) = make_float4(acc[q][0], acc[q][1], acc[q][2], acc[q][3]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (sta) zt[(q * TC + j) * zsp] = acc[0][q][j];
+            if (TWO && stb) zt[(q * TC + j) * zsp + 32] = acc[TWO ? 1 : 0][q][j];
+        }
 }
 
-template <int EPI>
+// Column pass for K terms.  zc: Zt entry (first term, the lane's column,
+// row rb); gr: coefficients of rows rb .. rb+3 of the first term.  Each
+// term's chain is summed into acc at the end, terms in order.
+template <int K>
+__device__ __forceinline__ void cols_pass(const float *zc, int zsp, const float *gr, int wG4, float *acc) {
+    float a[K][4];
+    float4 w0[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        a[q][0] = a[q][1] = a[q][2] = a[q][3] = 0.f;
+        w0[q] = lds4(zc + q * TC * zsp);
+    }
+#pragma unroll 1
+    for (int k = 0; k < wG4; k += 4) {
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            const float4 w1 = lds4(zc + q * TC * zsp + k + 4);
+            const float z[8] = {w0[q].x, w0[q].y, w0[q].z, w0[q].w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const float4 g = lds4(gr + (q * wG4 + k + t) * TA);
+                a[q][0] = fmaf(g.x, z[t], a[q][0]);
+                a[q][1] = fmaf(g.y, z[t + 1], a[q][1]);
+                a[q][2] = fmaf(g.z, z[t + 2], a[q][2]);
+                a[q][3] = fmaf(g.w, z[t + 3], a[q][3]);
+            }
+            w0[q] = w1;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        acc[0] += a[q][0];
+        acc[1] += a[q][1];
+        acc[2] += a[q][2];
+        acc[3] += a[q][3];
+    }
+}
+
+// VEC: 16-byte staging (n, m multiples of 4 and In 16-byte aligned);
+// otherwise element-wise copies into the same layout.
+template <int EPI, bool VEC>
 __global__ void __launch_bounds__(NT) band_op_fused_kernel(const float *__restrict__ In, int m, int n, int r,
                                                            const float *__restrict__ Fb, int loF, int wF,
                                                            const float *__restrict__ Gb, int loG, int wG,
                                                            float *__restrict__ Out, ProxArgs pa) {
     extern __shared__ __align__(16) float sm[];
-    const FusedGeom geo = fused_geom(r, wF, wG);
+    const FusedGeom geo = fused_geom(r, loF, wF, wG);
     float *Ins = sm, *Fs = sm + geo.off_f, *Gs = sm + geo.off_g, *Zs = sm + geo.off_z;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int a0 = blockIdx.y * TA, c0 = blockIdx.x * TC;
-    const int e0 = a0 + loG;                 // first staged row
-    const int spanc = TC + wF - 1, spanr = TA + wG - 1;
+    const int e0 = a0 + loG;                   // first staged row
+    const int colbase = c0 + loF - geo.off;    // first staged column (4-aligned)
+    const int width = TC + geo.wF4;            // staged columns
     // Constant band tiles first, then (after the previous kernel) the input tile.
-    if ((n & 3) == 0 && (m & 3) == 0) {
-        // 16-byte copies: thread (row tk, quad j) copies 4 band entries; the
-        // tail of a ragged tile is zero-filled by the copy's source size.
-        const int j = tid & 7;
-        const int fb = min(16, max(0, (n - (c0 + 4 * j)) * 4)), gb = min(16, max(0, (m - (a0 + 4 * j)) * 4));
-        for (int tk = tid >> 3; tk < r * wF; tk += NT / 8)
-            band::stage16(Fs + tk * TC + 4 * j, Fb + (size_t)tk * n + c0 + 4 * j, fb, Fb);
-        for (int tk = tid >> 3; tk < r * wG; tk += NT / 8)
-            band::stage16(Gs + tk * TA + 4 * j, Gb + (size_t)tk * m + a0 + 4 * j, gb, Gb);
+    if (VEC) {
+        const int tr = tid >> 3, j = tid & 7;
+        const int fb = c0 + 4 * j < n ? 16 : 0, gb = a0 + 4 * j < m ? 16 : 0;
+        for (int q = 0; q < r; ++q) {
+            for (int kp = tr; kp < geo.wF4; kp += NT / 8) {
+                const int k = kp - geo.off;
+                const bool ok = k >= 0 && k < wF;
+                band::stage16(Fs + (q * geo.wF4 + kp) * TC + 4 * j,
+                              Fb + (size_t)(q * wF + (ok ? k : 0)) * n + c0 + 4 * j, ok ? fb : 0, Fb);
+            }
+            for (int kp = tr; kp < geo.wG4; kp += NT / 8) {
+                const bool ok = kp < wG;
+                band::stage16(Gs + (q * geo.wG4 + kp) * TA + 4 * j,
+                              Gb + (size_t)(q * wG + (ok ? kp : 0)) * m + a0 + 4 * j, ok ? gb : 0, Gb);
+            }
+        }
     } else {
         const bool cin = c0 + lane < n, rin = a0 + lane < m;
-        for (int tk = warp; tk < r * wF; tk += NT / 32)
-            band::stage<float, false>(Fs + tk * TC + lane, Fb + (size_t)tk * n + c0 + lane, cin, Fb);
-        for (int tk = warp; tk < r * wG; tk += NT / 32)
-            band::stage<float, false>(Gs + tk * TA + lane, Gb + (size_t)tk * m + a0 + lane, rin, Gb);
+        for (int q = 0; q < r; ++q) {
+            for (int kp = warp; kp < geo.wF4; kp += NT / 32) {
+                const int k = kp - geo.off;
+                const bool ok = k >= 0 && k < wF;
+                band::stage<float, false>(Fs + (q * geo.wF4 + kp) * TC + lane,
+                                          Fb + (size_t)(q * wF + (ok ? k : 0)) * n + c0 + lane, ok && cin, Fb);
+            }
+            for (int kp = warp; kp < geo.wG4; kp += NT / 32) {
+                const bool ok = kp < wG;
+                band::stage<float, false>(Gs + (q * geo.wG4 + kp) * TA + lane,
+                                          Gb + (size_t)(q * wG + (ok ? kp : 0)) * m + a0 + lane, ok && rin, Gb);
+            }
+        }
     }
     band::pdl_wait();
-    for (int row = warp; row < geo.zs; row += NT / 32) {
-        const int ge = e0 + row;
-        const bool rok = row < spanr && ge >= 0 && ge < m;
-        for (int col = lane; col < geo.sp; col += 32) {
-            const int gc = c0 + loF + col;
-            band::stage<float, false>(Ins + row * geo.sp + col, In + (size_t)ge * n + gc,
-                                      rok && col < spanc && gc >= 0 && gc < n, In);
+    if (VEC) {
+        const int nch = width >> 2;
+        const int lsh = nch <= 8 ? 3 : (nch <= 16 ? 4 : 5);   // threads per staged row: 1 << lsh
+        const int tr = tid >> lsh, tc = tid & ((1 << lsh) - 1);
+        for (int e = tr; e < geo.rows; e += NT >> lsh) {
+            const int ge = e0 + e;
+            const bool rok = e < geo.zs && ge >= 0 && ge < m;
+            for (int t = tc; t < nch; t += 1 << lsh) {
+                const int gcol = colbase + 4 * t;
+                const bool ok = rok && gcol >= 0 && gcol < n;
+                band::stage16(Ins + e * geo.sp + 4 * t, In + (size_t)(ok ? ge : 0) * n + (ok ? gcol : 0), ok ? 16 : 0,
+                              In);
+            }
+        }
+    } else {
+        for (int e = warp; e < geo.rows; e += NT / 32) {
+            const int ge = e0 + e;
+            const bool rok = e < geo.zs && ge >= 0 && ge < m;
+            for (int s = lane; s < width; s += 32) {
+                const int gcol = colbase + s;
+                const bool ok = rok && gcol >= 0 && gcol < n;
+                band::stage<float, false>(Ins + e * geo.sp + s, In + (size_t)(ok ? ge : 0) * n + (ok ? gcol : 0), ok,
+                                          In);
+            }
         }
     }
     band::stage_wait<false>();
     __syncthreads();
-    // Row pass: Z_i for staged rows [0, zs) (row zs-1 and out-of-image rows come out 0).
+    // Row pass: Z_i for rows [0, zs) into Zt.
     const int cb = warp * 4;
-    for (int rbase = 0; rbase < geo.zs; rbase += 32) {
-        const int row = rbase + lane;
-        if (row < geo.zs) {
-            const float *xr = Ins + row * geo.sp + cb;
-            for (int tb = 0; tb < r; tb += 4) {
-                float *zo = Zs + ((size_t)tb * geo.zs + row) * ZST + cb;
-                const float *fr = Fs + tb * wF * TC + cb;
-                switch (min(4, r - tb)) {
-                    case 1: rows_to_smem<1>(xr, fr, wF, zo, geo.zs * ZST); break;
-                    case 2: rows_to_smem<2>(xr, fr, wF, zo, geo.zs * ZST); break;
-                    case 3: rows_to_smem<3>(xr, fr, wF, zo, geo.zs * ZST); break;
-                    default: rows_to_smem<4>(xr, fr, wF, zo, geo.zs * ZST); break;
-                }
+    for (int rbase = 0; rbase < geo.zs; rbase += 64) {
+        const int e = rbase + lane;
+        const bool two = rbase + 32 < geo.zs;
+        const float *xa = Ins + e * geo.sp + cb;
+        for (int tb = 0; tb < r; tb += 4) {
+            const float *fr = Fs + tb * geo.wF4 * TC + cb;
+            float *zt = Zs + (size_t)(tb * TC + cb) * geo.zsp + e;
+            const bool sta = e < geo.zs, stb = e + 32 < geo.zs;
+            switch (min(4, r - tb) + (two ? 4 : 0)) {
+                case 1: rows_pass<1, false>(xa, geo.sp, fr, geo.wF4, zt, geo.zsp, sta, stb); break;
+                case 2: rows_pass<2, false>(xa, geo.sp, fr, geo.wF4, zt, geo.zsp, sta, stb); break;
+                case 3: rows_pass<3, false>(xa, geo.sp, fr, geo.wF4, zt, geo.zsp, sta, stb); break;
+                case 4: rows_pass<4, false>(xa, geo.sp, fr, geo.wF4, zt, geo.zsp, sta, stb); break;
+                case 5: rows_pass<1, true>(xa, geo.sp, fr, geo.wF4, zt, geo.zsp, sta, stb); break;
+                case 6: rows_pass<2, true>(xa, geo.sp, fr, geo.wF4, zt, geo.zsp, sta, stb); break;
+                case 7: rows_pass<3, true>(xa, geo.sp, fr, geo.wF4, zt, geo.zsp, sta, stb); break;
+                default: rows_pass<4, true>(xa, geo.sp, fr, geo.wF4, zt, geo.zsp, sta, stb); break;
             }
         }
     }
@@ -135,13 +265,13 @@ __global__ void __launch_bounds__(NT) band_op_fused_kernel(const float *__restri
     const int rb = warp * 4, gc = c0 + lane;
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     for (int tb = 0; tb < r; tb += 4) {
-        const float *zc = Zs + ((size_t)tb * geo.zs + rb) * ZST + lane;
-        const float *gr = Gs + tb * wG * TA + rb;
+        const float *zc = Zs + (size_t)(tb * TC + lane) * geo.zsp + rb;
+        const float *gr = Gs + tb * geo.wG4 * TA + rb;
         switch (min(4, r - tb)) {
-            case 1: band::cols_terms<float, 1, ZST>(zc, gr, wG, geo.zs, acc); break;
-            case 2: band::cols_terms<float, 2, ZST>(zc, gr, wG, geo.zs, acc); break;
-            case 3: band::cols_terms<float, 3, ZST>(zc, gr, wG, geo.zs, acc); break;
-            default: band::cols_terms<float, 4, ZST>(zc, gr, wG, geo.zs, acc); break;
+            case 1: cols_pass<1>(zc, geo.zsp, gr, geo.wG4, acc); break;
+            case 2: cols_pass<2>(zc, geo.zsp, gr, geo.wG4, acc); break;
+            case 3: cols_pass<3>(zc, geo.zsp, gr, geo.wG4, acc); break;
+            default: cols_pass<4>(zc, geo.zsp, gr, geo.wG4, acc); break;
         }
     }
     if (gc < n) {
@@ -171,15 +301,27 @@ __global__ void __launch_bounds__(NT) band_op_fused_kernel(const float *__restri
 
 constexpr size_t kFusedSmemMax = 227 * 1024;
 
+template <int EPI>
+void launch_epi(const cudaLaunchConfig_t &cfg, bool vec, const float *In, int m, int n, int r, const float *Fb,
+                int loF, int wF, const float *Gb, int loG, int wG, float *Out, const ProxArgs &pa) {
+    if (vec)
+        cudaLaunchKernelEx(&cfg, band_op_fused_kernel<EPI, true>, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out, pa);
+    else
+        cudaLaunchKernelEx(&cfg, band_op_fused_kernel<EPI, false>, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out, pa);
+}
+
 }  // namespace
 
-size_t band_op_fused_smem(int r, int wF, int wG) { return sizeof(float) * fused_geom(r, wF, wG).total; }
+// Largest shared-memory size over the four possible column offsets.
+size_t band_op_fused_smem(int r, int wF, int wG) { return sizeof(float) * fused_geom(r, 3, wF, wG).total; }
 
 // Sets the kernels' shared-memory limit; false if one tile does not fit.
 bool band_op_fused_prepare(int r, int wF, int wG) {
     const size_t sm = band_op_fused_smem(r, wF, wG);
     if (sm > kFusedSmemMax) return false;
-    for (auto k : {band_op_fused_kernel<EPI_STORE>, band_op_fused_kernel<EPI_RESIDUAL>, band_op_fused_kernel<EPI_PROX>})
+    for (auto k : {band_op_fused_kernel<EPI_STORE, true>, band_op_fused_kernel<EPI_RESIDUAL, true>,
+                   band_op_fused_kernel<EPI_PROX, true>, band_op_fused_kernel<EPI_STORE, false>,
+                   band_op_fused_kernel<EPI_RESIDUAL, false>, band_op_fused_kernel<EPI_PROX, false>})
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemMax) != cudaSuccess)
             return false;
     return true;
@@ -187,10 +329,12 @@ bool band_op_fused_prepare(int r, int wF, int wG) {
 
 void launch_band_op_fused(const float *In, int m, int n, int r, const float *Fb, int loF, int wF, const float *Gb,
                           int loG, int wG, EpiKind epi, float *Out, const ProxArgs &pa, cudaStream_t s) {
+    const bool vec = (n % 4) == 0 && (m % 4) == 0 && ((uintptr_t)In % 16) == 0 && ((uintptr_t)Fb % 16) == 0 &&
+                     ((uintptr_t)Gb % 16) == 0;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((n + TC - 1) / TC, (m + TA - 1) / TA);
     cfg.blockDim = dim3(NT);
-    cfg.dynamicSmemBytes = band_op_fused_smem(r, wF, wG);
+    cfg.dynamicSmemBytes = sizeof(float) * fused_geom(r, loF, wF, wG).total;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -198,11 +342,11 @@ void launch_band_op_fused(const float *In, int m, int n, int r, const float *Fb,
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (epi == EPI_STORE)
-        cudaLaunchKernelEx(&cfg, band_op_fused_kernel<EPI_STORE>, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out, pa);
+        launch_epi<EPI_STORE>(cfg, vec, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out, pa);
     else if (epi == EPI_RESIDUAL)
-        cudaLaunchKernelEx(&cfg, band_op_fused_kernel<EPI_RESIDUAL>, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out, pa);
+        launch_epi<EPI_RESIDUAL>(cfg, vec, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out, pa);
     else
-        cudaLaunchKernelEx(&cfg, band_op_fused_kernel<EPI_PROX>, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out, pa);
+        launch_epi<EPI_PROX>(cfg, vec, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out, pa);
 }
 
 }  // namespace sfista

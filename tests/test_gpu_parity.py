@@ -74,6 +74,27 @@ def test_apply_matches_oracle(bc, transpose, shape, op):
     s.close()
 
 
+@pytest.mark.parametrize("psf_shape,centre,r", [((41, 9), (20, 4), 2), ((9, 10), (2, 6), 3), ((12, 13), (5, 5), 5),
+                                               ((7, 14), (3, 0), 4), ((10, 7), (9, 6), 1), ((6, 11), (0, 10), 6)])
+@pytest.mark.parametrize("shape", [(96, 100), (45, 38)])
+def test_fused_apply_band_offsets(psf_shape, centre, r, shape):
+    """The one-kernel operator over PSF widths and centres that give every
+    column-offset class of the band (mod 4), term counts split 4 + rest, a
+    column band wider than 32 rows, and aligned / unaligned image widths."""
+    m, n = shape
+    g = W.rng(110 + psf_shape[0] * 16 + psf_shape[1])
+    P = W.random_psf(g, *psf_shape)
+    ka = kron.kron_approx(P, centre[0], centre[1], m, n, 1, r)
+    s = api.Sfista(P, (m, n), 1, r, center=centre, prec="fp32", op="banded_fused", lipschitz=1.0)
+    assert s.info()["op"] == "banded_fused"
+    X = g.standard_normal((m, n)).astype(np.float32)
+    for transpose in (False, True):
+        Y = s.apply(_cuda(X), transpose=transpose).cpu().numpy()
+        Yo = (oracle.kron_apply_T if transpose else oracle.kron_apply)(X.astype(np.float64), ka)
+        assert oracle.rel_fro(Y, Yo) < 1e-6
+    s.close()
+
+
 def test_adjoint_identity_gpu():
     g = W.rng(103)
     P = W.rotated_gaussian_psf(31, 3.0, 1.0, np.deg2rad(30))
