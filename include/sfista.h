@@ -59,7 +59,8 @@ typedef enum {
 } sfista_bc;
 
 /* Arithmetic of the Kronecker operator (the four products of Step 1).
- * The FISTA state (X_k, X_{k-1}, Y_k) is always carried in FP64. */
+ * The FISTA state (X_k, X_{k-1}, Y_k) is always carried as double-float pairs
+ * (hi + lo, two FP32 words, about 48 significant bits). */
 typedef enum {
     SFISTA_FP32 = 0,     /* FP32 FMA on the CUDA cores                                  */
     SFISTA_TF32 = 1,     /* one TF32 tensor-core product, FP32 accumulate                */
@@ -169,7 +170,9 @@ sfista_status sfista_solve_device(sfista_ctx *ctx, const float *d_b,
                                   void *stream);
 
 /*
- * sfista_solve_state -- resumable form of Alg. 2 on FP64 device state.
+ * sfista_solve_state -- resumable form of Alg. 2 on FP64 device state
+ * (converted to the internal double-float state on entry and back to FP64
+ * on exit).
  *
  * d_X, d_Xprev  device, m x n FP64: on entry X_{k0} and X_{k0-1}; on exit
  *               X_{k0+iters} and X_{k0+iters-1}.  With k0 = 0, d_X is the

@@ -7,7 +7,7 @@
 //   stage 1  R[a][c]     = sum_{i,e} B_i[a][e] Tt[i][c][e]  - Bdata[a][c]
 //   stage 2  Ut[j][b][a] = sum_c A^T_j[b][c] R[a][c]        (R A_j, stored transposed)
 //   stage 3  G[a][b]     = sum_{j,e} B^T_j[a][e] Ut[j][b][e];  then Step 1 shrink and
-//                          Step 3 momentum in the epilogue (FP64 state).
+//                          Step 3 momentum in the epilogue (double-float state).
 // Stages 0 and 2 stack the r terms along M (one M tile belongs to one term);
 // stages 1 and 3 sum the r terms along K.  The factors are banded, so an M
 // tile of rows [m0, m0+128) only meets K columns [m0 + lo, m0 + 127 + hi];

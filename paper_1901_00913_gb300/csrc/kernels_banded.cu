@@ -11,7 +11,7 @@
 // zero and reflective boundaries (and any PSF centre) run the same code.
 // The cols pass ends in the fused epilogue: the residual B_s(Y) - B of the
 // forward product, or Step 1's shrink + optional projection + Step 3's
-// momentum for the adjoint, with the FISTA state in FP64.
+// momentum for the adjoint, with the FISTA state as double-float pairs.
 #include <cuda_bf16.h>
 
 #include "band_items.cuh"

@@ -1,5 +1,5 @@
 // The whole Alg. 2 loop in one persistent, cooperatively launched kernel
-// (banded FP32 operator, FP64 FISTA state).
+// (banded FP32 operator, double-float FISTA state).
 //
 // For small and medium images one iteration is only a few hundred MFLOP, so
 // four dependent launches per iteration spend most of their time in launch
