@@ -343,6 +343,93 @@ def run_batched(args, torch):
     print(json.dumps(line), flush=True)
 
 
+def run_unrolled(args, torch):
+    """--workload cfg5: reverse mode of the unrolled 50-iteration solve (512^2, r=3, checkpoint every 10).
+
+    One step = sfista_unrolled_fwd (forward with checkpoints) + the loss gradient
+    2 (X_50 - X_true) + sfista_unrolled_bwd (gradients for b, lambda, A_i, B_i).
+    Parity: the GPU backward is fed the oracle's dl/dX_50 and compared with the
+    oracle's FP64 reverse mode (dense factors).
+    """
+    from paper_1901_00913_gb300 import api, build, workloads as W
+    from oracle import adjoint, kron
+    build.build()
+    pr = W.config5()
+    K, ck = pr.iters, pr.extra["ckpt_every"]
+    m, n = pr.x_true.shape
+    r = pr.r
+    db = _observation_gpu(pr, torch)
+    s0 = api.Sfista(pr.psf, (m, n), pr.bc, r, prec="fp32", op="banded")
+    L = s0.info()["lipschitz"]
+    s0.close()
+    xt = torch.from_numpy(pr.x_true.astype(np.float32)).cuda()
+    cr, cc = pr.centre
+    ka = kron.kron_approx(pr.psf, cr, cc, m, n, pr.bc, r)
+    Bf, Af = kron.dense_factors(ka)
+    b64 = db.double().cpu().numpy()
+    t0 = time.perf_counter()
+    Xo = adjoint.unrolled_forward(b64, Af, Bf, L, pr.lam, K)[0]
+    gXo = 2.0 * (Xo - pr.x_true)
+    ob, ol, oA, oB = adjoint.unrolled_grad(b64, Af, Bf, L, pr.lam, K, gXo)
+    cpu_s = time.perf_counter() - t0
+
+    def rel(a, b):
+        return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+    nseg = (K + ck - 1) // ck
+    forms = {}
+    for f in args.forms.split(","):
+        prec, op = f.split(":")
+        s = api.Sfista(pr.psf, (m, n), pr.bc, r, prec=prec, op=op, lipschitz=L)
+        ckpt = torch.empty(2 * nseg, m, n, dtype=torch.float64, device="cuda")
+        X = torch.empty_like(db)
+        gX = torch.empty_like(db)
+        gb = torch.empty_like(db)
+        gA = torch.empty(r, n, n, device="cuda")
+        gB = torch.empty(r, m, m, device="cuda")
+        # parity against the oracle's reverse mode, on the oracle's dl/dX
+        api.sfista_unrolled_fwd(s.ctx, db, pr.lam, K, ck, ckpt, X)
+        gl = api.sfista_unrolled_bwd(s.ctx, db, pr.lam, K, ck, ckpt,
+                                     torch.from_numpy(gXo.astype(np.float32)).cuda(), gb, gA, gB)
+        torch.cuda.synchronize()
+        errs = {"X": rel(X.cpu().numpy(), Xo), "g_b": rel(gb.cpu().numpy(), ob),
+                "g_lambda": abs(gl - ol) / abs(ol), "g_A": rel(gA.cpu().numpy(), oA), "g_B": rel(gB.cpu().numpy(), oB)}
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        fwd_ms = bwd_ms = 0.0
+        for it in range(args.warmup + args.steps):
+            ev[0].record()
+            api.sfista_unrolled_fwd(s.ctx, db, pr.lam, K, ck, ckpt, X)
+            ev[1].record()
+            torch.sub(X, xt, out=gX).mul_(2.0)
+            api.sfista_unrolled_bwd(s.ctx, db, pr.lam, K, ck, ckpt, gX, gb, gA, gB)
+            ev[2].record()
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                fwd_ms += ev[0].elapsed_time(ev[1])
+                bwd_ms += ev[1].elapsed_time(ev[2])
+        with Clocks(0) as clk:
+            for _ in range(2):
+                api.sfista_unrolled_fwd(s.ctx, db, pr.lam, K, ck, ckpt, X)
+                torch.sub(X, xt, out=gX).mul_(2.0)
+                api.sfista_unrolled_bwd(s.ctx, db, pr.lam, K, ck, ckpt, gX, gb, gA, gB)
+            torch.cuda.synchronize()
+        step_ms = (fwd_ms + bwd_ms) / args.steps
+        forms[prec + ":" + op] = {"unrolled_iters_per_s": K / (step_ms / 1e3), "ms_per_step": step_ms,
+                                  "fwd_ms": fwd_ms / args.steps, "bwd_ms": bwd_ms / args.steps,
+                                  "rel_err_vs_oracle_reverse_mode": errs,
+                                  "meets_tol": errs["X"] <= 1e-5 and max(errs[k] for k in errs if k != "X") <= 1e-4,
+                                  "clocks": clk.summary()}
+        s.close()
+    line = {"metric": METRIC, "workload": "512x512 reflexive, 31x31 rotated Gaussian PSF, r=3, lambda=0.005, 50 "
+            "unrolled its, checkpoint every 10; forward + backward for b, lambda, A_i, B_i",
+            "unit": "unrolled iters/s (forward + backward)", "steps": args.steps, "warmup": args.warmup,
+            "forms": forms,
+            "cpu_baseline": {"value": K / cpu_s, "unit": "unrolled iters/s (forward + backward)", "kind": "oracle",
+                             "cores": os.cpu_count(), "sample": "one full 50-iteration FP64 forward + reverse mode "
+                             "(numpy BLAS, dense factors)"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -352,7 +439,7 @@ def main():
     ap.add_argument("--forms", default="fp32:banded_fused,fp32:banded,fp32:banded_persistent,bf16x3:gemm_band,tf32x3:gemm_band,bf16:gemm_band,tf32:gemm_band",
                     help="comma list of prec:op forms to measure")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "cfg4"])
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "cfg4", "cfg5"])
     ap.add_argument("--check-iters", type=int, default=10)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -361,9 +448,11 @@ def main():
     if args.workload != "cfg2":
         import torch
         if args.forms.startswith("fp32:banded_fused,fp32:banded,fp32:banded_persistent"):
-            args.forms = ("fp32:banded_fused,fp32:banded,bf16x3:gemm_band,tf32x3:gemm_band,bf16x3:gemm_dense"
-                          if args.workload == "cfg3" else "fp32:banded,bf16x3:gemm_band,tf32x3:gemm_band")
-        return run_large(args, torch) if args.workload == "cfg3" else run_batched(args, torch)
+            args.forms = {"cfg3": "fp32:banded_fused,fp32:banded,bf16x3:gemm_band,tf32x3:gemm_band,bf16x3:gemm_dense",
+                          "cfg4": "fp32:banded,bf16x3:gemm_band,tf32x3:gemm_band",
+                          "cfg5": "fp32:banded_fused,fp32:banded"}[args.workload]
+        run = {"cfg3": run_large, "cfg4": run_batched, "cfg5": run_unrolled}[args.workload]
+        return run(args, torch)
 
     import torch
     from paper_1901_00913_gb300 import api, build

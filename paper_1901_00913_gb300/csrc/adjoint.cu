@@ -39,64 +39,216 @@ __global__ void scale_f32(float *y, const float *x, float a, size_t n) {
         y[i] = a * x[i];
 }
 
-// C[I][J] += alpha * sum_t P(I, t) Q(J, t), P(I, t) = P[I*psi + t*pst],
-// Q(J, t) = Q[J*qsj + t*qst]; 64 x 64 tiles, 16-deep K slices, 4 x 4 per thread.
-template <bool P_I_CONTIG, bool Q_J_CONTIG>
-__global__ void __launch_bounds__(256) sgemm_acc(float *C, int ldc, int I, int J, int T, const float *P, long psi,
-                                                 long pst, const float *Q, long qsj, long qst, float alpha) {
-    __shared__ float Ps[16][64 + 4], Qs[16][64 + 4];
-    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-    const int I0 = blockIdx.y * 64, J0 = blockIdx.x * 64;
-    float acc[4][4] = {};
-    for (int t0 = 0; t0 < T; t0 += 16) {
-        for (int e = tid; e < 1024; e += 256) {
-            int ii, tt;
-            if (P_I_CONTIG) { ii = e % 64; tt = e / 64; } else { tt = e % 16; ii = e / 16; }
-            const int gi = I0 + ii, gt = t0 + tt;
-            Ps[tt][ii] = (gi < I && gt < T) ? P[gi * psi + gt * pst] : 0.f;
-            int jj, t2;
-            if (Q_J_CONTIG) { jj = e % 64; t2 = e / 64; } else { t2 = e % 16; jj = e / 16; }
-            const int gj = J0 + jj, gt2 = t0 + t2;
-            Qs[t2][jj] = (gj < J && gt2 < T) ? Q[gj * qsj + gt2 * qst] : 0.f;
+// Factor gradients, batched over the buffered steps of a checkpoint segment:
+//   C_i[I][J] += alpha * sum_{part < 2} sum_{s < S} sum_{t < T} P_part(i, s)(I, t) Q_part(i, s)(J, t)
+// with operand (i, s) at base + i * term + s * step.  TN: element (I, t) at
+// [t * ld + I] (I contiguous, contraction over rows); NT: at [I * ld + t]
+// (contraction over columns).  128 x 128 output tiles, 16-deep slices, 8 x 8
+// outputs per thread, the next slice prefetched into registers while the
+// current one is multiplied from shared memory.  The contraction (2 parts x S
+// steps x T rounded up to 16) is split across blockIdx.z for parallelism; each
+// split writes its partial tile and grad_reduce adds the splits in a fixed
+// order (deterministic).
+struct GradOperands {
+    const float *P[2], *Q[2];
+    long p_term, q_term, p_step, q_step, ld;
+    int S, T, I, J, r, splits, slices_per_split;
+};
+
+constexpr int GB = 128, GK = 16, GLD = GB + 4;
+
+// VEC: 16-byte loads (ld, and I, J (TN) or T (NT), multiples of 4, bases
+// 16-byte aligned); otherwise four predicated scalar loads.
+template <bool NT, bool VEC>
+__device__ __forceinline__ void grad_load(const float *base, long ld, int n_idx, int T, int idx0, int t0, int tid,
+                                          float4 *v) {
+    // 512 float4 per 128 x 16 slice, two per thread.
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int f = tid + h * 256;
+        int I, t;
+        if (NT) {
+            I = f & 127;
+            t = (f >> 7) * 4;
+        } else {
+            t = f >> 5;
+            I = (f & 31) * 4;
         }
-        __syncthreads();
+        const int gI = idx0 + I, gt = t0 + t;
+        float x[4] = {0.f, 0.f, 0.f, 0.f};
+        if (VEC) {
+            if (gI < n_idx && gt < T) {
+                const float4 q = __ldg(reinterpret_cast<const float4 *>(NT ? base + (long)gI * ld + gt
+                                                                           : base + (long)gt * ld + gI));
+                x[0] = q.x;
+                x[1] = q.y;
+                x[2] = q.z;
+                x[3] = q.w;
+            }
+        } else {
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            float a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = Ps[k][ty * 4 + i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Qs[k][tx * 4 + j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+            for (int j = 0; j < 4; ++j) {
+                if (NT) {
+                    if (gI < n_idx && gt + j < T) x[j] = __ldg(base + (long)gI * ld + gt + j);
+                } else {
+                    if (gI + j < n_idx && gt < T) x[j] = __ldg(base + (long)gt * ld + gI + j);
+                }
+            }
         }
-        __syncthreads();
+        v[h] = make_float4(x[0], x[1], x[2], x[3]);
     }
+}
+
+template <bool NT>
+__device__ __forceinline__ void grad_store(float (*S)[GLD], int tid, const float4 *v) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int gi = I0 + ty * 4 + i;
-        if (gi >= I) continue;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int gj = J0 + tx * 4 + j;
-            if (gj < J) C[(size_t)gi * ldc + gj] += alpha * acc[i][j];
+    for (int h = 0; h < 2; ++h) {
+        const int f = tid + h * 256;
+        if (NT) {
+            const int I = f & 127, t = (f >> 7) * 4;
+            S[t][I] = v[h].x;
+            S[t + 1][I] = v[h].y;
+            S[t + 2][I] = v[h].z;
+            S[t + 3][I] = v[h].w;
+        } else {
+            *reinterpret_cast<float4 *>(&S[f >> 5][(f & 31) * 4]) = v[h];
         }
+    }
+}
+
+template <bool NT, bool VEC>
+__global__ void __launch_bounds__(256) grad_gemm(GradOperands o, float *partial) {
+    __shared__ __align__(16) float Ps[2][GK][GLD];
+    __shared__ __align__(16) float Qs[2][GK][GLD];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int I0 = blockIdx.y * GB, J0 = blockIdx.x * GB;
+    const int term = blockIdx.z / o.splits, split = blockIdx.z % o.splits;
+    const int Tp = (o.T + GK - 1) / GK;                    // slices per (part, step)
+    const int total = 2 * o.S * Tp;
+    const int u0 = split * o.slices_per_split, u1 = min(total, u0 + o.slices_per_split);
+    float acc[8][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+    auto operands = [&](int u, const float **P, const float **Q, int *t0) {
+        const int part = u / (o.S * Tp), rem = u - part * o.S * Tp, s = rem / Tp;
+        *t0 = (rem - s * Tp) * GK;
+        *P = (part ? o.P[1] : o.P[0]) + term * o.p_term + s * o.p_step;
+        *Q = (part ? o.Q[1] : o.Q[0]) + term * o.q_term + s * o.q_step;
+    };
+    float4 pv[2], qv[2];
+    if (u0 < u1) {
+        const float *P, *Q;
+        int t0;
+        operands(u0, &P, &Q, &t0);
+        grad_load<NT, VEC>(P, o.ld, o.I, o.T, I0, t0, tid, pv);
+        grad_load<NT, VEC>(Q, o.ld, o.J, o.T, J0, t0, tid, qv);
+        grad_store<NT>(Ps[0], tid, pv);
+        grad_store<NT>(Qs[0], tid, qv);
+    }
+    __syncthreads();
+    int cur = 0;
+    for (int u = u0; u < u1; ++u) {
+        const bool next = u + 1 < u1;
+        if (next) {
+            const float *P, *Q;
+            int t0;
+            operands(u + 1, &P, &Q, &t0);
+            grad_load<NT, VEC>(P, o.ld, o.I, o.T, I0, t0, tid, pv);
+            grad_load<NT, VEC>(Q, o.ld, o.J, o.T, J0, t0, tid, qv);
+        }
+#pragma unroll
+        for (int k = 0; k < GK; ++k) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&Ps[cur][k][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&Ps[cur][k][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4 *>(&Qs[cur][k][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4 *>(&Qs[cur][k][64 + tx * 4]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int x = 0; x < 8; ++x)
+#pragma unroll
+                for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+        }
+        if (next) {
+            grad_store<NT>(Ps[cur ^ 1], tid, pv);
+            grad_store<NT>(Qs[cur ^ 1], tid, qv);
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    float *out = partial + ((size_t)term * o.splits + split) * o.I * o.J;
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+        const int gI = I0 + (x < 4 ? ty * 4 + x : 64 + ty * 4 + x - 4);
+        if (gI >= o.I) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int gJ = J0 + h * 64 + tx * 4;
+            float *o4 = out + (size_t)gI * o.J + gJ;
+            if (VEC) {
+                if (gJ < o.J)
+                    *reinterpret_cast<float4 *>(o4) =
+                        make_float4(acc[x][4 * h], acc[x][4 * h + 1], acc[x][4 * h + 2], acc[x][4 * h + 3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (gJ + j < o.J) o4[j] = acc[x][4 * h + j];
+            }
+        }
+    }
+}
+
+// C[i][x] += alpha * sum_split partial[i][split][x], splits in order.
+__global__ void grad_reduce(float *C, const float *partial, int r, int splits, size_t IJ, float alpha) {
+    const size_t total = (size_t)r * IJ;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = e / IJ, x = e - i * IJ;
+        const float *p = partial + i * splits * IJ + x;
+        float sum = 0.f;
+        for (int sp = 0; sp < splits; ++sp) sum += p[(size_t)sp * IJ];
+        C[e] += alpha * sum;
     }
 }
 
 int grid1(size_t n) { return (int)std::min<size_t>(4096, (n + 255) / 256); }
 
-// C (I x J) += alpha * P^T Q  with P (T x I), Q (T x J) row-major: contract rows.
-void gemm_tn(float *C, int I, int J, int T, const float *P, const float *Q, float alpha, cudaStream_t s) {
-    dim3 g((J + 63) / 64, (I + 63) / 64);
-    sgemm_acc<true, true><<<g, 256, 0, s>>>(C, J, I, J, T, P, 1, I, Q, 1, J, alpha);
+constexpr size_t kGradBufferBytes = (size_t)2 << 30;   // factor-gradient step buffers
+
+// Contraction splits: the smallest count (at most 16, at least four slices
+// each) whose blocks fill at least one wave of one block per SM to 90 %.
+int grad_splits(const GradOperands &o, int sms) {
+    const int tiles = ((o.I + GB - 1) / GB) * ((o.J + GB - 1) / GB) * o.r;
+    const int total = 2 * o.S * ((o.T + GK - 1) / GK);
+    const int cap = std::max(1, std::min(16, total / 4));
+    int best = 1;
+    double best_use = 0.0;
+    for (int sp = 1; sp <= cap; ++sp) {
+        const long blocks = (long)tiles * sp;
+        const double use = (double)blocks / ((double)((blocks + sms - 1) / sms) * sms);
+        if (blocks >= sms && use >= 0.9) return sp;
+        if (use > best_use + 1e-9) best_use = use, best = sp;
+    }
+    return best;
 }
-// C (I x J) += alpha * P Q^T  with P (I x T), Q (J x T) row-major: contract columns.
-void gemm_nt(float *C, int I, int J, int T, const float *P, const float *Q, float alpha, cudaStream_t s) {
-    dim3 g((J + 63) / 64, (I + 63) / 64);
-    sgemm_acc<false, false><<<g, 256, 0, s>>>(C, J, I, J, T, P, T, 1, Q, T, 1, alpha);
+
+// vec: every leading dimension, extent and base suits 16-byte access (the
+// caller checks m, n multiples of 4; buffers are cudaMalloc'ed).
+void launch_grad_gemm(bool nt, bool vec, GradOperands o, float *C, float *partial, float alpha, cudaStream_t s) {
+    const int total = 2 * o.S * ((o.T + GK - 1) / GK);
+    o.slices_per_split = (total + o.splits - 1) / o.splits;
+    dim3 g((o.J + GB - 1) / GB, (o.I + GB - 1) / GB, o.r * o.splits);
+    if (nt && vec)
+        grad_gemm<true, true><<<g, 256, 0, s>>>(o, partial);
+    else if (nt)
+        grad_gemm<true, false><<<g, 256, 0, s>>>(o, partial);
+    else if (vec)
+        grad_gemm<false, true><<<g, 256, 0, s>>>(o, partial);
+    else
+        grad_gemm<false, false><<<g, 256, 0, s>>>(o, partial);
+    const size_t IJ = (size_t)o.I * o.J;
+    grad_reduce<<<grid1((size_t)o.r * IJ), 256, 0, s>>>(C, partial, o.r, o.splits, IJ, alpha);
 }
 
 struct Scratch {
@@ -179,16 +331,39 @@ extern "C" sfista_status sfista_unrolled_bwd(sfista_ctx *c, const float *d_b, do
     const HostSetup &h = c->hs;
     const double L = c->L, den = L + lambda * lambda, inv = 1.0 / den;
     const int ce = ckpt_every, nseg = (iters + ce - 1) / ce;
+    const bool factors = d_gA || d_gB;
+    // Factor-gradient operands of up to `scap` steps are buffered and
+    // contracted together (one batched GEMM per family per flush).
+    const size_t step_floats = N * (4 + 4 * (size_t)r);   // R, W, V, Y and U, U2, R A_i, W A_i (r each)
+    const int scap = factors ? (int)std::max<size_t>(1, std::min<size_t>(ce, kGradBufferBytes / (4 * step_floats))) : 0;
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev);
+    const bool vec = m % 4 == 0 && n % 4 == 0;
+    GradOperands oa{}, ob{};
+    oa.S = ob.S = scap;
+    oa.r = ob.r = r;
+    oa.ld = ob.ld = n;
+    oa.T = m, oa.I = n, oa.J = n;   // dl/dA_i = R^T (B_i V) + W^T (B_i Y):  TN over image rows
+    ob.T = n, ob.I = m, ob.J = m;   // dl/dB_i = (R A_i) V^T + (W A_i) Y^T:  NT over image columns
+    oa.splits = factors ? grad_splits(oa, sms) : 1;
+    ob.splits = factors ? grad_splits(ob, sms) : 1;
+    const size_t part_floats = factors ? (size_t)r * std::max((size_t)oa.splits * n * n, (size_t)ob.splits * m * m) : 1;
     Scratch sc;
     double *segX, *segY, *xb, *sumV, *ybar, *dots, *partial, *dot2;
-    float *Vf, *Wf, *Tf, *Yf, *Rf, *U, *U2, *Zs, *Zq;
+    float *Vf, *Wf, *Tf, *Rseg = nullptr, *Wseg = nullptr, *Vseg = nullptr, *Yseg = nullptr, *Useg = nullptr,
+                         *U2seg = nullptr, *Zsseg = nullptr, *Zqseg = nullptr, *gpart = nullptr;
     cudaError_t e;
     if ((e = sc.get(&segX, (size_t)ce * N)) || (e = sc.get(&segY, (size_t)ce * N)) || (e = sc.get(&xb, 3 * N)) ||
         (e = sc.get(&sumV, N)) || (e = sc.get(&ybar, N)) || (e = sc.get(&dots, 2 * (size_t)iters)) ||
         (e = sc.get(&partial, 512)) || (e = sc.get(&dot2, 2)) || (e = sc.get(&Vf, N)) || (e = sc.get(&Wf, N)) ||
-        (e = sc.get(&Tf, N)) || (e = sc.get(&Yf, N)) || (e = sc.get(&Rf, N)) || (e = sc.get(&U, N)) ||
-        (e = sc.get(&U2, N)) || (e = sc.get(&Zs, (size_t)r * N)) || (e = sc.get(&Zq, (size_t)r * N)))
+        (e = sc.get(&Tf, N)))
         return fail(SFISTA_ENOMEM, std::string("adjoint buffers: ") + cudaGetErrorString(e));
+    if (factors &&
+        ((e = sc.get(&Rseg, scap * N)) || (e = sc.get(&Wseg, scap * N)) || (e = sc.get(&Vseg, scap * N)) ||
+         (e = sc.get(&Yseg, scap * N)) || (e = sc.get(&Useg, scap * r * N)) || (e = sc.get(&U2seg, scap * r * N)) ||
+         (e = sc.get(&Zsseg, scap * r * N)) || (e = sc.get(&Zqseg, scap * r * N)) ||
+         (e = sc.get(&gpart, part_floats))))
+        return fail(SFISTA_ENOMEM, std::string("factor-gradient buffers: ") + cudaGetErrorString(e));
     SF_CUDA(cudaEventRecord(c->ev_in, user));
     SF_CUDA(cudaStreamWaitEvent(c->stream, c->ev_in, 0));
     cudaStream_t s = c->stream;
@@ -196,7 +371,6 @@ extern "C" sfista_status sfista_unrolled_bwd(sfista_ctx *c, const float *d_b, do
     SF_CUDA(cudaMemsetAsync(xb, 0, 3 * N * 8, s));
     SF_CUDA(cudaMemsetAsync(sumV, 0, N * 8, s));
     launch_f32_to_f64(d_gX, xb + (size_t)(iters % 3) * N, N, s);
-    const bool factors = d_gA || d_gB;
     if (d_gA) SF_CUDA(cudaMemsetAsync(d_gA, 0, (size_t)r * n * n * 4, s));
     if (d_gB) SF_CUDA(cudaMemsetAsync(d_gB, 0, (size_t)r * m * m * 4, s));
     ProxArgs pz{};
@@ -214,17 +388,20 @@ extern "C" sfista_status sfista_unrolled_bwd(sfista_ctx *c, const float *d_b, do
             launch_df_to_f64(c->Xb[k & 1], segX + (size_t)(k - k0 - 1) * N, N, s);
         }
         // Reverse sweep over the segment.
+        int nb = 0;   // factor-gradient steps buffered
         for (int k = k1; k > k0; --k) {
             double *V = xb + (size_t)(k % 3) * N;
             const double *Xk = segX + (size_t)(k - k0 - 1) * N, *Yk = segY + (size_t)(k - k0 - 1) * N;
-            launch_f64_to_f32(V, Vf, N, s);
-            As_apply(c, Vf, Wf, s);
-            AsT_apply(c, Wf, Tf, s);
+            float *Vk = factors ? Vseg + (size_t)nb * N : Vf, *Wk = factors ? Wseg + (size_t)nb * N : Wf;
+            launch_f64_to_f32(V, Vk, N, s);
+            As_apply(c, Vk, Wk, s);
+            AsT_apply(c, Wk, Tf, s);
             ybar_kernel<<<grid1(N), 256, 0, s>>>(ybar, V, Tf, L, inv, N);
             axpy_f64<<<grid1(N), 256, 0, s>>>(sumV, V, 1.0, N);
             launch_dots(Xk, V, N, partial, 256, dot2, s);
             SF_CUDA(cudaMemcpyAsync(dots + 2 * (size_t)(k - 1), dot2, 16, cudaMemcpyDeviceToDevice, s));
             if (factors) {
+                float *Yf = Yseg + (size_t)nb * N, *Rf = Rseg + (size_t)nb * N;
                 launch_f64_to_f32(Yk, Yf, N, s);
                 ProxArgs pr{};
                 pr.Bd = c->Bd;
@@ -233,21 +410,31 @@ extern "C" sfista_status sfista_unrolled_bwd(sfista_ctx *c, const float *d_b, do
                 if (d_gA) {
                     for (int i = 0; i < r; ++i) {
                         const float *Bi = c->fB + (size_t)i * h.B.w * m;
-                        launch_band_cols<float>(Vf, m, n, Bi, h.B.lo, h.B.w, 1, EPI_STORE, U, pz, s);
-                        launch_band_cols<float>(Yf, m, n, Bi, h.B.lo, h.B.w, 1, EPI_STORE, U2, pz, s);
-                        float *gAi = d_gA + (size_t)i * n * n;
-                        gemm_tn(gAi, n, n, m, Rf, U, minus_inv, s);
-                        gemm_tn(gAi, n, n, m, Wf, U2, minus_inv, s);
+                        float *Ui = Useg + ((size_t)nb * r + i) * N, *U2i = U2seg + ((size_t)nb * r + i) * N;
+                        launch_band_cols<float>(Vk, m, n, Bi, h.B.lo, h.B.w, 1, EPI_STORE, Ui, pz, s);    // B_i V
+                        launch_band_cols<float>(Yf, m, n, Bi, h.B.lo, h.B.w, 1, EPI_STORE, U2i, pz, s);   // B_i Y
                     }
                 }
                 if (d_gB) {
-                    launch_band_rows<float>(Rf, m, n, c->fAT, h.AT.lo, h.AT.w, r, Zs, s);   // R A_i
-                    launch_band_rows<float>(Wf, m, n, c->fAT, h.AT.lo, h.AT.w, r, Zq, s);   // W A_i
-                    for (int i = 0; i < r; ++i) {
-                        float *gBi = d_gB + (size_t)i * m * m;
-                        gemm_nt(gBi, m, m, n, Zs + (size_t)i * N, Vf, minus_inv, s);
-                        gemm_nt(gBi, m, m, n, Zq + (size_t)i * N, Yf, minus_inv, s);
+                    launch_band_rows<float>(Rf, m, n, c->fAT, h.AT.lo, h.AT.w, r, Zsseg + (size_t)nb * r * N, s);
+                    launch_band_rows<float>(Wk, m, n, c->fAT, h.AT.lo, h.AT.w, r, Zqseg + (size_t)nb * r * N, s);
+                }
+                if (++nb == scap || k == k0 + 1) {
+                    if (d_gA) {
+                        GradOperands o = oa;
+                        o.S = nb;
+                        o.P[0] = Rseg, o.P[1] = Wseg, o.Q[0] = Useg, o.Q[1] = U2seg;
+                        o.p_term = 0, o.p_step = (long)N, o.q_term = (long)N, o.q_step = (long)(r * N);
+                        launch_grad_gemm(false, vec, o, d_gA, gpart, minus_inv, s);
                     }
+                    if (d_gB) {
+                        GradOperands o = ob;
+                        o.S = nb;
+                        o.P[0] = Zsseg, o.P[1] = Zqseg, o.Q[0] = Vseg, o.Q[1] = Yseg;
+                        o.p_term = (long)N, o.p_step = (long)(r * N), o.q_term = 0, o.q_step = (long)N;
+                        launch_grad_gemm(true, vec, o, d_gB, gpart, minus_inv, s);
+                    }
+                    nb = 0;
                 }
             }
             if (k >= 2) {
