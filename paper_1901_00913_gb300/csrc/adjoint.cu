@@ -273,16 +273,28 @@ sfista_status check_unrolled(sfista_ctx *c, int iters, int ckpt) {
     return SFISTA_OK;
 }
 
-// Forward operator A_s x (FP32, banded) into out, using the context's Z.
-void As_apply(sfista_ctx *c, const float *x, float *out, cudaStream_t s) {
+// A_s x (FP32, banded) into out: one fused launch when the context uses the
+// fused form, else the two passes through the context's Z.  EPI_RESIDUAL
+// subtracts the context's B (A_s x - B).
+void As_apply(sfista_ctx *c, const float *x, float *out, cudaStream_t s, EpiKind epi = EPI_STORE) {
     const HostSetup &h = c->hs;
     ProxArgs pa{};
+    pa.Bd = c->Bd;
+    if (c->op == SFISTA_OP_BANDED_FUSED) {
+        launch_band_op_fused(x, c->m, c->n, c->r, c->fA, h.A.lo, h.A.w, c->fB, h.B.lo, h.B.w, epi, out, pa, s);
+        return;
+    }
     launch_band_rows<float>(x, c->m, c->n, c->fA, h.A.lo, h.A.w, c->r, c->Z, s);
-    launch_band_cols<float>(c->Z, c->m, c->n, c->fB, h.B.lo, h.B.w, c->r, EPI_STORE, out, pa, s);
+    launch_band_cols<float>(c->Z, c->m, c->n, c->fB, h.B.lo, h.B.w, c->r, epi, out, pa, s);
 }
 void AsT_apply(sfista_ctx *c, const float *x, float *out, cudaStream_t s) {
     const HostSetup &h = c->hs;
     ProxArgs pa{};
+    if (c->op == SFISTA_OP_BANDED_FUSED) {
+        launch_band_op_fused(x, c->m, c->n, c->r, c->fAT, h.AT.lo, h.AT.w, c->fBT, h.BT.lo, h.BT.w, EPI_STORE, out, pa,
+                             s);
+        return;
+    }
     launch_band_rows<float>(x, c->m, c->n, c->fAT, h.AT.lo, h.AT.w, c->r, c->Z, s);
     launch_band_cols<float>(c->Z, c->m, c->n, c->fBT, h.BT.lo, h.BT.w, c->r, EPI_STORE, out, pa, s);
 }
@@ -403,10 +415,7 @@ extern "C" sfista_status sfista_unrolled_bwd(sfista_ctx *c, const float *d_b, do
             if (factors) {
                 float *Yf = Yseg + (size_t)nb * N, *Rf = Rseg + (size_t)nb * N;
                 launch_f64_to_f32(Yk, Yf, N, s);
-                ProxArgs pr{};
-                pr.Bd = c->Bd;
-                launch_band_rows<float>(Yf, m, n, c->fA, h.A.lo, h.A.w, r, c->Z, s);
-                launch_band_cols<float>(c->Z, m, n, c->fB, h.B.lo, h.B.w, r, EPI_RESIDUAL, Rf, pr, s);
+                As_apply(c, Yf, Rf, s, EPI_RESIDUAL);   // R_k = A_s Y_k - B
                 if (d_gA) {
                     for (int i = 0; i < r; ++i) {
                         const float *Bi = c->fB + (size_t)i * h.B.w * m;

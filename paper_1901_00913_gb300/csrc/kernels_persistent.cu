@@ -25,7 +25,7 @@ namespace sfista {
 namespace {
 
 constexpr int PT = 256;          // threads per block
-constexpr int PR_A = band::TA;     // rows-pass tile: 16 rows x 64 columns
+constexpr int PR_A = band::TA;     // rows-pass tile: 32 x 32
 constexpr int PR_C = band::TC;
 constexpr int PC_A = band::TA;     // cols-pass tile: 16 rows x 64 columns
 constexpr int PC_C = band::TC;
@@ -151,7 +151,10 @@ __global__ void __launch_bounds__(PT) band_rows_grouped(const BandProb *probs, c
     const float *In = phase == 0 ? P.pa.Yop : P.R;
     const float *F = phase == 0 ? P.fA : P.fAT;
     const int lo = phase == 0 ? P.loA : P.loAT, w = phase == 0 ? P.wA : P.wAT;
-    rows_item(In, P.m, P.n, F, lo, w, t0, nt, (it.tile / rt_c) * PR_A, (it.tile % rt_c) * PR_C, P.Z, sm);
+    // Separate launches per stage: the input was written by an earlier launch,
+    // so the cp.async (and 16-byte) staging of the plain kernels applies.
+    band::rows_item<float, false>(In, P.m, P.n, F, lo, w, t0, nt, (it.tile / rt_c) * PR_A, (it.tile % rt_c) * PR_C,
+                                  P.Z, sm);
 }
 
 __global__ void __launch_bounds__(PT) band_cols_grouped(const BandProb *probs, const BandItem *items, int phase,
@@ -163,13 +166,15 @@ __global__ void __launch_bounds__(PT) band_cols_grouped(const BandProb *probs, c
     const int a0 = (it.tile / ct_c) * PC_A, c0 = (it.tile % ct_c) * PC_C;
     ProxArgs pa = P.pa;
     if (phase == 1) {
-        cols_item<EPI_RESIDUAL>(P.Z, P.m, P.n, P.r, P.cols_chunk, P.fB, P.loB, P.wB, a0, c0, P.R, pa, sm);
+        band::cols_item<float, EPI_RESIDUAL, false>(P.Z, P.m, P.n, P.r, P.cols_chunk, P.fB, P.loB, P.wB, a0, c0, P.R,
+                                                    pa, sm);
     } else {
         float2 *b0 = const_cast<float2 *>(pa.Xin), *b1 = pa.Xout;
         pa.k = k;
         pa.Xin = (k - 1) & 1 ? b1 : b0;
         pa.Xout = k & 1 ? b1 : b0;
-        cols_item<EPI_PROX>(P.Z, P.m, P.n, P.r, P.cols_chunk, P.fBT, P.loBT, P.wBT, a0, c0, nullptr, pa, sm);
+        band::cols_item<float, EPI_PROX, false>(P.Z, P.m, P.n, P.r, P.cols_chunk, P.fBT, P.loBT, P.wBT, a0, c0,
+                                                nullptr, pa, sm);
     }
 }
 
