@@ -30,6 +30,15 @@ sys.path.insert(0, ROOT)
 METRIC = "sFISTA iters/s and op TFLOP/s, mixed vs FP32 form, at <=1e-4 rel err vs FP64"
 WORKLOAD = "512x512 reflexive, 31x31 rotated Gaussian PSF (3,1,30deg), r=3, lambda=0.005, 1% noise, 200 its"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+# Kernels per sFISTA iteration by operator form (a solve adds an input
+# check, the state initialisation and the output conversion).
+KERNELS_PER_ITER = {"banded": 4, "banded_fused": 2, "banded_persistent": 1, "gemm_band": 4, "gemm_dense": 4}
+# DRAM bytes (read + write) per launch of a form's dominant kernel, from an
+# ncu capture of the current kernel code on this workload (the summary in
+# profiles/ gives the command); forms without one report null.
+TRAFFIC = {"fp32:banded_fused:0": {"bytes": 2.519e6 + 0.0,
+                                   "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, "
+                                             "profiles/banded_fused_fp32_cfg2_512_r3.md"}}
 TOL = {"fp32": 1e-5, "bf16x3": 1e-4, "tf32x3": 1e-4}
 DTYPE = {"fp32": "f32", "bf16x3": "bf16", "tf32x3": "tf32", "bf16": "bf16", "tf32": "tf32"}
 NPROD = {"bf16x3": 3, "tf32x3": 3, "bf16": 1, "tf32": 1}
@@ -250,11 +259,12 @@ def run_large(args, torch):
             work = {"banded": alg, "banded_fused": [alg[0] + alg[1], 0, alg[2] + alg[3], 0]}.get(op, [sum(alg), 0, 0, 0])
             peak, bound = FP32_PEAK_TFLOPS, "alu"
         dom = int(np.argmax(sm))
-        ach = work[dom] / (sm[dom] / 1e3) / 1e12
+        dur_ms = ms / (args.steps * iters) * sm[dom] / sum(sm)   # in-region share, as in the main workload
+        ach = work[dom] / (dur_ms / 1e3) / 1e12
         forms[prec + ":" + op] = {
             "iters_per_s": v, "rel_err_vs_oracle_first_%d_its" % args.check_iters: err, "stage_ms": sm,
             "dominant_stage": STAGES[dom], "roofline": {"bound": bound, "achieved_tflops": ach, "peak": peak,
-                                                        "frac": ach / peak},
+                                                        "frac": ach / peak, "duration_us": dur_ms * 1e3},
             "op_tflops_executed": sum(work) * v / 1e12, "op_tflops_algorithmic": sum(alg) * v / 1e12,
             "dense_equiv_tflops": 8.0 * r * n ** 3 * v / 1e12, "clocks": clk.summary()}
         s.close()
@@ -559,12 +569,19 @@ def main():
             bf16 = peaks.get("bf16_tflops", 1900.0)
             peak = bf16 if prec.startswith("bf16") else bf16 * (1.1 / 2.25)
             peak_src = ("%s bf16 burst" % peak_src_name) + ("" if prec.startswith("bf16") else " x 1.1/2.25 (tf32 nominal ratio)")
-        achieved = work[dom] / (sm[dom] / 1e3) / 1e12
+        # Duration of the dominant kernel inside the timed region: the
+        # per-iteration time of the timed graph runs, split over the stages in
+        # proportion to their standalone event timings.
+        iter_ms = res["ms_total"] / (args.steps * iters)
+        dur_ms = iter_ms * sm[dom] / sum(sm)
+        achieved = work[dom] / (dur_ms / 1e3) / 1e12
         ok = err <= TOL.get(prec, float("inf"))
         kname = {"banded_persistent": "band_solve_persistent (whole iteration)",
                  "banded_fused": ["band_op_fused_kernel (forward + residual)", "",
                                   "band_op_fused_kernel (adjoint + shrink + momentum)", ""][dom]}.get(op, STAGES[dom])
         lines[key] = dict(kernel=kname, value=v, err=err, dpsnr=dpsnr, stage_ms=sm, dom=dom, achieved=achieved, ok=ok,
+                          dur_us=dur_ms * 1e3, launches=KERNELS_PER_ITER.get(op, 4) * iters + 3,
+                          traffic=TRAFFIC.get("%s:%s:%d" % (prec, op, dom)),
                           bound=bound, peak=peak, unit=unit, peak_src=peak_src, prec=prec,
                           op_tflops_alg=sum(alg) * v / world / 1e12,
                           op_tflops_exec=sum(work) * v / world / 1e12,
@@ -584,13 +601,15 @@ def main():
         "op_tflops_algorithmic": L0["op_tflops_alg"], "op_tflops_executed": L0["op_tflops_exec"],
         "roofline": {"bound": L0["bound"], "kernel": L0["kernel"], "achieved": L0["achieved"],
                      "peak": L0["peak"], "unit": L0["unit"], "frac": L0["achieved"] / L0["peak"],
-                     "traffic": None, "peak_source": L0["peak_src"]},
+                     "traffic": L0["traffic"]["bytes"] if L0["traffic"] else None,
+                     "traffic_source": L0["traffic"]["source"] if L0["traffic"] else None,
+                     "duration_us": L0["dur_us"], "peak_source": L0["peak_src"]},
         "stage_ms": dict(zip(STAGES, L0["stage_ms"])),
         "cpu_baseline": {"value": iters / cpu_s, "unit": "iters/s", "cores": cores, "kind": "oracle",
                          "sample": "one full 200-iteration FP64 solve of the same problem"},
         "e2e": {"value": L0["e2e"], "unit": "iters/s", "h2d_bytes_per_step": 4 * n * n,
                 "d2h_bytes_per_step": 4 * n * n},
-        "gpu_launches": (4 * iters + 3) * args.steps,
+        "gpu_launches": L0["launches"] * args.steps,
         "clocks": L0["clocks"],
         "forms": {k: {"iters_per_s": v["value"], "rel_err": v["err"], "dpsnr_db": v["dpsnr"],
                       "meets_tol": v["ok"], "stage_ms": v["stage_ms"], "roofline_frac": v["achieved"] / v["peak"],
