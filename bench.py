@@ -45,6 +45,12 @@ NPROD = {"bf16x3": 3, "tf32x3": 3, "bf16": 1, "tf32": 1}
 STAGES = ["fwd_right", "fwd_left+residual", "adj_right", "adj_left+prox+momentum"]
 
 
+def _form(f):
+    """'prec:op[+tune]' -> (prec, op, tune)."""
+    prec, op = f.split(":") if ":" in f else (f, "auto")
+    return prec, op.replace("+tune", ""), op.endswith("+tune")
+
+
 def mma_flops_per_stage(info, m, n, r, prec, op):
     """Tensor-core flops each GEMM stage issues: 128 x 128 tiles, K blocks of 128 bytes,
     K range per M tile [m0 + lo, m0 + 127 + hi] (band) or [0, K) (dense); x3 for split."""
@@ -227,8 +233,9 @@ def run_large(args, torch):
     peaks, peak_src_name = _peaks()
     forms = {}
     for f in args.forms.split(","):
-        prec, op = f.split(":")
+        prec, op, tune = _form(f)
         s = api.Sfista(pr.psf, (n, n), pr.bc, r, prec=prec, op=op, lipschitz=L)
+        tuned = s.tune(iters=5) if tune else None
         Xc = s.solve_device(db, pr.lam, args.check_iters).cpu().numpy()
         err = oracle.rel_fro(Xc, Xref)
         out = torch.empty_like(db)
@@ -246,6 +253,7 @@ def run_large(args, torch):
                 ms += ev0.elapsed_time(ev1)
         api.sfista_sync(s.ctx)
         info = s.info()
+        op = info["op"]
         sm = [float(x) for x in api.sfista_time_stages(s.ctx, db, pr.lam, 5)]
         v = iters * args.steps / (ms / 1e3)
         wA, wB = info["band_right"], info["band_left"]
@@ -261,7 +269,8 @@ def run_large(args, torch):
         dom = int(np.argmax(sm))
         dur_ms = ms / (args.steps * iters) * sm[dom] / sum(sm)   # in-region share, as in the main workload
         ach = work[dom] / (dur_ms / 1e3) / 1e12
-        forms[prec + ":" + op] = {
+        forms[f] = {
+            "resolved_op": op, "tuned": tuned,
             "iters_per_s": v, "rel_err_vs_oracle_first_%d_its" % args.check_iters: err, "stage_ms": sm,
             "dominant_stage": STAGES[dom], "roofline": {"bound": bound, "achieved_tflops": ach, "peak": peak,
                                                         "frac": ach / peak, "duration_us": dur_ms * 1e3},
@@ -307,9 +316,14 @@ def run_batched(args, torch):
     total_px = sum(pr.x_true.size for pr in probs)
     forms = {}
     for f in args.forms.split(","):
-        prec, op = f.split(":")
+        prec, op, _ = _form(f)
         solvers = [api.Sfista(pr.psf, pr.x_true.shape, pr.bc, pr.r, prec=prec, op=op, lipschitz=L)
                    for pr, L in zip(probs, Ls)]
+        # autotuned tiles: each problem's term chunking (and, for op auto, its form)
+        t_tune = time.perf_counter()
+        for sv in solvers:
+            sv.tune(iters=3)
+        t_tune = time.perf_counter() - t_tune
         batch = api.Batch(solvers)
         outs = [torch.empty_like(d) for d in d_bs]
         for _ in range(args.warmup):
@@ -341,12 +355,14 @@ def run_batched(args, torch):
                                   "megapixel_iters_per_s": total_px * iters * args.steps / (ms / 1e3) / 1e6,
                                   "sequential_problem_iters_per_s": len(probs) * iters / (t_single / 1e3),
                                   "max_rel_err_sample": max(errs.values()), "rel_err_sample": errs,
+                                  "autotune_s": t_tune,
                                   "clocks": clk.summary()}
         batch.close()
         for sv in solvers:
             sv.close()
     line = {"metric": METRIC, "workload": "64 problems, n in {256..1024}, PSF 15-41 px mixtures, r in 1..4, "
-            "reflexive, lambda 0.005, 1% noise, 150 its, grouped launches + CUDA graph", "unit": "problem-iters/s",
+            "reflexive, lambda 0.005, 1% noise, 150 its, grouped launches + CUDA graph, autotuned term chunks",
+            "unit": "problem-iters/s",
             "steps": args.steps, "warmup": args.warmup, "forms": forms,
             "cpu_baseline": {"value": len(sample) * iters / cpu_s, "unit": "problem-iters/s", "kind": "oracle",
                              "sample": "4 problems (3 smallest, largest), full 150 its"}}
@@ -389,7 +405,7 @@ def run_unrolled(args, torch):
     nseg = (K + ck - 1) // ck
     forms = {}
     for f in args.forms.split(","):
-        prec, op = f.split(":")
+        prec, op, _ = _form(f)
         s = api.Sfista(pr.psf, (m, n), pr.bc, r, prec=prec, op=op, lipschitz=L)
         ckpt = torch.empty(2 * nseg, m, n, dtype=torch.float64, device="cuda")
         X = torch.empty_like(db)
@@ -446,7 +462,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--forms", default="fp32:banded_fused,fp32:banded,fp32:banded_persistent,bf16x3:gemm_band,tf32x3:gemm_band,bf16:gemm_band,tf32:gemm_band",
+    ap.add_argument("--forms", default="fp32:auto+tune,fp32:banded_fused,fp32:banded,fp32:banded_persistent,bf16x3:gemm_band,tf32x3:gemm_band,bf16:gemm_band,tf32:gemm_band",
                     help="comma list of prec:op forms to measure")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "cfg4", "cfg5"])
@@ -457,8 +473,9 @@ def main():
         return run_reference(args)
     if args.workload != "cfg2":
         import torch
-        if args.forms.startswith("fp32:banded_fused,fp32:banded,fp32:banded_persistent"):
-            args.forms = {"cfg3": "fp32:banded_fused,fp32:banded,bf16x3:gemm_band,tf32x3:gemm_band,bf16x3:gemm_dense",
+        if args.forms.startswith("fp32:auto+tune,fp32:banded_fused,fp32:banded,fp32:banded_persistent"):
+            args.forms = {"cfg3": "fp32:auto+tune,fp32:banded_fused,fp32:banded,bf16x3:auto+tune,bf16x3:gemm_band,"
+                                  "tf32x3:gemm_band,bf16x3:gemm_dense",
                           "cfg4": "fp32:banded,bf16x3:gemm_band,tf32x3:gemm_band",
                           "cfg5": "fp32:banded_fused,fp32:banded"}[args.workload]
         run = {"cfg3": run_large, "cfg4": run_batched, "cfg5": run_unrolled}[args.workload]
@@ -493,11 +510,12 @@ def main():
     s0.close()
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
-    forms = [f.split(":") if ":" in f else (f, "auto") for f in args.forms.split(",")]
+    forms = [(f,) + _form(f) for f in args.forms.split(",")]
     results = {}
     peaks, peak_src_name = _peaks()
-    for prec, op in forms:
+    for form, prec, op, tune in forms:
         s = api.Sfista(pr.psf, (n, n), pr.bc, pr.r, prec=prec, op=op, lipschitz=L)
+        tuned = s.tune(iters=10) if tune else None
         out = torch.empty_like(db)
         for _ in range(args.warmup):
             s.solve_device(db, pr.lam, iters, out=out)
@@ -530,7 +548,7 @@ def main():
         for _ in range(args.steps):
             api.sfista_solve(s.ctx, bnp, pr.lam, iters, xnp)
         e2e_s = time.perf_counter() - t0
-        results[info["prec"] + ":" + info["op"]] = dict(ms_total=ms, X=X, stage_ms=stage_ms, info=info,
+        results[form] = dict(ms_total=ms, X=X, stage_ms=stage_ms, info=info, tuned=tuned,
                                                  clocks=clk.summary(), e2e_s=e2e_s)
         s.close()
 
@@ -545,8 +563,8 @@ def main():
     r = pr.r
     lines = {}
     for key, res in results.items():
-        prec, op = key.split(":")
         info = res["info"]
+        prec, op = info["prec"], info["op"]
         err = oracle.rel_fro(res["X"], Xref)
         dpsnr = oracle.psnr(res["X"], pr.x_true) - oracle.psnr(Xref, pr.x_true)
         v = world * iters * args.steps / (res["ms_total"] / 1e3)
@@ -586,7 +604,7 @@ def main():
                           op_tflops_alg=sum(alg) * v / world / 1e12,
                           op_tflops_exec=sum(work) * v / world / 1e12,
                           e2e=iters * args.steps / res["e2e_s"], clocks=res["clocks"],
-                          ms_per_step=res["ms_total"] / args.steps)
+                          ms_per_step=res["ms_total"] / args.steps, resolved_op=op, tuned=res["tuned"])
     held = [k for k in lines if lines[k]["ok"] and lines[k]["prec"] in TOL]
     key0 = max(held or list(lines), key=lambda k: lines[k]["value"])
     L0 = lines[key0]
@@ -594,7 +612,8 @@ def main():
         "metric": METRIC, "value": L0["value"], "unit": "iters/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": L0["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[L0["prec"]], "data": "synthetic",
-        "config": {"workload": WORKLOAD, "form": key0, "iters_per_step": iters, "m": n, "n": n, "r": r,
+        "config": {"workload": WORKLOAD, "form": key0, "resolved_op": L0["resolved_op"], "iters_per_step": iters,
+                   "m": n, "n": n, "r": r,
                    "psf": "31x31", "global_batch": 1, "seq_len": 0, "parallelism": "replicas",
                    "l2": "flushed between steps (256 MB write); the solve's working set is L2-resident"},
         "rel_err_vs_fp64_oracle": L0["err"], "dpsnr_db_vs_oracle": L0["dpsnr"],
@@ -613,7 +632,8 @@ def main():
         "clocks": L0["clocks"],
         "forms": {k: {"iters_per_s": v["value"], "rel_err": v["err"], "dpsnr_db": v["dpsnr"],
                       "meets_tol": v["ok"], "stage_ms": v["stage_ms"], "roofline_frac": v["achieved"] / v["peak"],
-                      "bound": v["bound"], "op_tflops_executed": v["op_tflops_exec"]}
+                      "bound": v["bound"], "op_tflops_executed": v["op_tflops_exec"],
+                      "resolved_op": v["resolved_op"], "tuned": v["tuned"]}
                   for k, v in lines.items()},
         "peaks": {"source": peak_src_name, "hbm_gbs": peaks.get("hbm_gbs"), "bf16_tflops": peaks.get("bf16_tflops")},
     }

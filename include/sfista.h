@@ -302,6 +302,39 @@ sfista_status sfista_blur(const double *psf, int psf_rows, int psf_cols,
 sfista_status sfista_time_stages(sfista_ctx *ctx, const float *d_b, double lambda,
                                  int reps, float *ms);
 
+/* One configuration measured by sfista_tune. */
+typedef struct {
+    int op;            /* sfista_operator of the configuration                        */
+    int stage;         /* 0..3: one stage timed alone (see sfista_time_stages);
+                          -1: whole iterations                                         */
+    int chunk;         /* terms staged per block in that stage (two-pass banded form);
+                          0 where it does not apply                                    */
+    float ms;          /* mean time per stage (or per iteration), ms                  */
+} sfista_tune_entry;
+
+/*
+ * sfista_tune -- autotuner for this context's problem shape.  The paper has no
+ * counterpart (its operator runs in serial MATLAB).  Times `iters` repetitions
+ * of each candidate on the context's own stream, on an all-zero observation
+ * (timing does not depend on the data), and keeps the fastest:
+ *   - two-pass banded FP32 form: for each of the four stages, the number of
+ *     terms staged per block (1 .. r, those that fit in shared memory); this
+ *     sets shared memory per block and so the blocks resident per SM;
+ *   - if the operator form was left to SFISTA_OP_AUTO: FP32 contexts also
+ *     compare the tuned two-pass form with the fused form, tensor-core
+ *     contexts the band-limited and full (dense) K ranges.
+ * An explicitly chosen form is kept (only its stages are tuned).  The chosen
+ * configuration applies to later solves, sfista_apply and batches created
+ * afterwards (sfista_info reports the form).
+ * entries      host, caller-owned array of max_entries (may be NULL): every
+ *              measurement, in order.
+ * n_entries    host out (may be NULL): number of measurements made.
+ * Synchronous.  Leaves the solver state undefined (the next solve resets it).
+ * Errors: SFISTA_EINVAL for iters < 1 or max_entries < 0.
+ */
+sfista_status sfista_tune(sfista_ctx *ctx, int iters, sfista_tune_entry *entries, int max_entries,
+                          int *n_entries);
+
 /*
  * sfista_apply_static -- the banded operator of sfista_apply without any
  * device allocation.  The paper has no counterpart: this call exists for

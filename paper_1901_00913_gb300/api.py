@@ -29,6 +29,10 @@ class SfistaError(RuntimeError):
         self.status = status
 
 
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int), ("stage", ctypes.c_int), ("chunk", ctypes.c_int), ("ms", ctypes.c_float)]
+
+
 class Opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("op", ctypes.c_int), ("project_nonneg", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("lipschitz", ctypes.c_double),
@@ -62,6 +66,7 @@ def load(path=None):
     L.sfista_get_factors.argtypes = [vp, vp, vp]
     L.sfista_blur.argtypes = [vp, i, i, i, i, i, vp, i, i, vp, vp]
     L.sfista_time_stages.argtypes = [vp, vp, d, i, vp]
+    L.sfista_tune.argtypes = [vp, i, ctypes.POINTER(TuneEntry), i, ctypes.POINTER(ctypes.c_int)]
     L.sfista_apply_static.argtypes = [vp, vp, i, i, i, vp, i, i, vp, i, i, vp]
     L.sfista_batch_create.argtypes = [vp, i, ctypes.POINTER(vp)]
     L.sfista_batch_solve.argtypes = [vp, vp, vp, i, vp, vp]
@@ -217,6 +222,15 @@ def sfista_time_stages(ctx, d_b, lam, reps):
     ms = np.zeros(4, dtype=np.float32)
     _check(load().sfista_time_stages(ctypes.c_void_p(ctx), _ptr(d_b), float(lam), int(reps), ms.ctypes.data))
     return ms
+
+
+def sfista_tune(ctx, iters=10, max_entries=64):
+    """Autotuner (see include/sfista.h): returns every measurement as dicts."""
+    buf = (TuneEntry * max_entries)()
+    cnt = ctypes.c_int(0)
+    _check(load().sfista_tune(ctypes.c_void_p(ctx), int(iters), buf, int(max_entries), ctypes.byref(cnt)))
+    return [{"op": OP_NAME.get(e.op, e.op), "stage": e.stage, "chunk": e.chunk, "ms": e.ms}
+            for e in buf[:min(cnt.value, max_entries)]]
 
 
 def sfista_apply_static(d_x, d_y, r, band_right, lo_right, band_left, lo_left, stream=None):
@@ -396,6 +410,10 @@ class Sfista:
 
     def info(self):
         return sfista_info(self.ctx, min(self.psf_shape))
+
+    def tune(self, iters=10):
+        """Times the candidate configurations and keeps the fastest; returns the measurements."""
+        return sfista_tune(self.ctx, iters)
 
     def profiles(self):
         return sfista_get_profiles(self.ctx, self.r, *self.psf_shape)

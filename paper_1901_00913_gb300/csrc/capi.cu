@@ -138,12 +138,14 @@ void enqueue_stage(sfista_ctx *c, int st, const ProxArgs &pa) {
                                  nullptr, pa, c->stream);
     } else if (is_banded(c->op)) {
         switch (st) {
-            case 0: launch_band_rows<float>(c->Yop, c->m, c->n, c->fA, h.A.lo, h.A.w, c->r, c->Z, c->stream); break;
+            case 0: launch_band_rows<float>(c->Yop, c->m, c->n, c->fA, h.A.lo, h.A.w, c->r, c->Z, c->stream,
+                                            c->chunk[0]); break;
             case 1: launch_band_cols<float>(c->Z, c->m, c->n, c->fB, h.B.lo, h.B.w, c->r, EPI_RESIDUAL, c->R, pa,
-                                            c->stream); break;
-            case 2: launch_band_rows<float>(c->R, c->m, c->n, c->fAT, h.AT.lo, h.AT.w, c->r, c->Z, c->stream); break;
+                                            c->stream, c->chunk[1]); break;
+            case 2: launch_band_rows<float>(c->R, c->m, c->n, c->fAT, h.AT.lo, h.AT.w, c->r, c->Z, c->stream,
+                                            c->chunk[2]); break;
             default: launch_band_cols<float>(c->Z, c->m, c->n, c->fBT, h.BT.lo, h.BT.w, c->r, EPI_PROX, nullptr,
-                                             pa, c->stream); break;
+                                             pa, c->stream, c->chunk[3]); break;
         }
     } else {
         gemm_stage(c->gemm, st, pa, c->stream);
@@ -707,7 +709,7 @@ sfista_status sfista_batch_create(sfista_ctx *const *ctxs, int nprob, sfista_bat
             P.r = c->r;
             int wmax = std::max(std::max(h.A.w, h.AT.w), std::max(h.B.w, h.BT.w));
             size_t sm = 0;
-            persistent_chunks(c->r, wmax, &P.rows_chunk, &P.cols_chunk, &sm);
+            grouped_chunks(c->r, wmax, c->chunk[0], c->chunk[1], &P.rows_chunk, &P.cols_chunk, &sm);
             b->smem = std::max(b->smem, sm);
             P.fA = c->fA;
             P.fB = c->fB;
@@ -914,6 +916,118 @@ sfista_status sfista_time_stages(sfista_ctx *c, const float *d_b, double lambda,
     if (e) return fail(SFISTA_ECUDA, std::string("stage timing: ") + cudaGetErrorString(e));
     for (int s4 = 0; s4 < 4; ++s4) ms[s4] = (float)(acc[s4] / reps);
     return drain_status(c);
+}
+
+namespace {
+
+// Mean time (ms) of stages [s0, s1] of Alg. 2, repeated `reps` times after two
+// untimed repetitions, launched back to back on the context's stream.
+sfista_status time_stage_range(sfista_ctx *c, int s0, int s1, int reps, float *ms) {
+    cudaEvent_t e0, e1;
+    SF_CUDA(cudaEventCreate(&e0));
+    SF_CUDA(cudaEventCreate(&e1));
+    cudaError_t e = cudaSuccess;
+    for (int k = 1; k <= reps + 2 && !e; ++k) {
+        if (k == 3) e = cudaEventRecord(e0, c->stream);
+        const ProxArgs pa = prox_args(c, k, 0.0);
+        for (int st = s0; st <= s1; ++st) enqueue_stage(c, st, pa);
+    }
+    if (!e) e = cudaEventRecord(e1, c->stream);
+    if (!e) e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (!e) e = cudaEventElapsedTime(&t, e0, e1);
+    if (!e) e = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e) return fail(SFISTA_ECUDA, std::string("tuning: ") + cudaGetErrorString(e));
+    *ms = t / reps;
+    return SFISTA_OK;
+}
+
+}  // namespace
+
+sfista_status sfista_tune(sfista_ctx *c, int iters, sfista_tune_entry *entries, int max_entries, int *n_entries) {
+    sfista_status st = check_ctx(c);
+    if (st) return st;
+    if (n_entries) *n_entries = 0;
+    if (iters < 1 || max_entries < 0) return fail(SFISTA_EINVAL, "iters must be >= 1 and max_entries >= 0");
+    DeviceGuard g(c->dev);
+    st = ensure_beta(c, iters + 3);
+    if (st) return st;
+    // All-zero observation and state (c->tmp is scratch).
+    SF_CUDA(cudaMemsetAsync(c->tmp, 0, c->N * sizeof(float), c->stream));
+    st = solve_core(c, c->tmp, 0.0, 0, 0, nullptr, nullptr, c->stream);
+    if (st) return st;
+    int count = 0;
+    auto log = [&](int op, int stage, int chunk, float ms) {
+        if (entries && count < max_entries) entries[count] = sfista_tune_entry{op, stage, chunk, ms};
+        ++count;
+    };
+    const HostSetup &h = c->hs;
+    const bool auto_op = c->opts.op == SFISTA_OP_AUTO;
+    if (c->prec == SFISTA_FP32 && c->op != SFISTA_OP_BANDED_PERSISTENT) {
+        const int chosen = c->op;
+        if (c->op == SFISTA_OP_BANDED || auto_op) {
+            // Two-pass form: the term chunk of each stage, timed alone.
+            c->op = SFISTA_OP_BANDED;
+            const int widths[4] = {h.A.w, h.B.w, h.AT.w, h.BT.w};
+            for (int s4 = 0; s4 < 4; ++s4) {
+                const bool rows = s4 % 2 == 0;
+                const int lim = rows ? band_rows_chunk_limit(c->r, widths[s4]) : band_cols_chunk_limit(c->r, widths[s4]);
+                float best = 0.f;
+                int best_ch = 0;
+                for (int ch = 1; ch <= lim; ++ch) {
+                    c->chunk[s4] = ch;
+                    float t = 0.f;
+                    st = time_stage_range(c, s4, s4, iters, &t);
+                    if (st) return st;
+                    log(SFISTA_OP_BANDED, s4, ch, t);
+                    if (best_ch == 0 || t < best) best = t, best_ch = ch;
+                }
+                c->chunk[s4] = best_ch;
+            }
+            float t_two = 0.f;
+            st = time_stage_range(c, 0, 3, iters, &t_two);
+            if (st) return st;
+            log(SFISTA_OP_BANDED, -1, 0, t_two);
+            c->op = SFISTA_OP_BANDED;
+            if (auto_op && band_op_fused_prepare(c->r, std::max(h.A.w, h.AT.w), std::max(h.B.w, h.BT.w))) {
+                float t_fused = 0.f;
+                c->op = SFISTA_OP_BANDED_FUSED;
+                st = time_stage_range(c, 0, 3, iters, &t_fused);
+                if (st) return st;
+                log(SFISTA_OP_BANDED_FUSED, -1, 0, t_fused);
+                c->op = t_fused < t_two ? SFISTA_OP_BANDED_FUSED : SFISTA_OP_BANDED;
+            }
+        } else {
+            c->op = chosen;
+        }
+    } else if (c->gemm && auto_op) {
+        float t_band = 0.f, t_dense = 0.f;
+        c->op = SFISTA_OP_GEMM_BAND;
+        gemm_set_dense(c->gemm, false);
+        st = time_stage_range(c, 0, 3, iters, &t_band);
+        if (st) return st;
+        log(SFISTA_OP_GEMM_BAND, -1, 0, t_band);
+        c->op = SFISTA_OP_GEMM_DENSE;
+        gemm_set_dense(c->gemm, true);
+        st = time_stage_range(c, 0, 3, iters, &t_dense);
+        if (st) return st;
+        log(SFISTA_OP_GEMM_DENSE, -1, 0, t_dense);
+        const bool dense = t_dense < t_band;
+        c->op = dense ? SFISTA_OP_GEMM_DENSE : SFISTA_OP_GEMM_BAND;
+        gemm_set_dense(c->gemm, dense);
+    }
+    if (c->gexec) {   // the cached loop graph holds the old configuration
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+        c->g_k0 = c->g_iters = -1;
+    }
+    SF_CUDA(cudaStreamSynchronize(c->stream));
+    st = drain_status(c);
+    SF_CUDA(cudaMemset(c->status, 0, 16));
+    if (n_entries) *n_entries = count;
+    return st;
 }
 
 sfista_status sfista_selftest_wait_timeout(sfista_ctx *c) {

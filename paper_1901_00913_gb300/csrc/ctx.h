@@ -49,6 +49,9 @@ struct sfista_ctx {
     std::vector<double> beta_host;
     // Tensor-core path (operand panels, intermediates, tensor maps).
     GemmPath *gemm = nullptr;
+    // Terms per block of the two-pass banded stages 0..3 (0: default rule);
+    // set by the autotuner.
+    int chunk[4] = {0, 0, 0, 0};
     // Persistent solver launch shape and its grid-barrier words.
     int pgrid = 0, prows_chunk = 1, pcols_chunk = 1;
     size_t psmem = 0;

@@ -71,13 +71,9 @@ struct Cfg {
     static constexpr int Q_BYTES = BN * KB_BYTES;
     static constexpr int NOP = SPLIT ? 2 : 1;
     static constexpr int STAGE_BYTES = NOP * (P_BYTES + Q_BYTES);
-    static constexpr int STAGES_RAW = (200 * 1024) / STAGE_BYTES;
-    static constexpr int STAGES = STAGES_RAW > 6 ? 6 : STAGES_RAW;
-    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
     static constexpr int KSTEPS = KB_BYTES / 32;    // MMA K step = 32 bytes (16 bf16 / 8 tf32)
     static constexpr int KB_ELEMS = FMT == FMT_BF16 ? 64 : 32;
     static constexpr int ALIGN = FMT == FMT_BF16 ? 8 : 4;   // 16-byte TMA x alignment
-    static constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
     // Instruction descriptor: D=F32, A/B = BF16 (kind::f16) or TF32 (kind::tf32),
     // both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
     static constexpr uint32_t IDESC = (1u << 4) | ((FMT == FMT_BF16 ? 1u : 2u) << 7) |
@@ -743,6 +739,8 @@ sfista_status gemm_create(GemmPath **out, const HostSetup &h, int prec, bool den
 void launch_wait_timeout_selftest(unsigned *status, cudaStream_t s) {
     wait_timeout_selftest<<<1, 32, 0, s>>>(status);
 }
+
+void gemm_set_dense(GemmPath *g, bool dense) { g->dense = dense; }
 
 void gemm_destroy(GemmPath *g) {
     if (!g) return;

@@ -15,6 +15,8 @@ struct GemmPath;
 sfista_status gemm_create(GemmPath **out, const HostSetup &h, int prec, bool dense, unsigned *status,
                           cudaStream_t s);
 void gemm_destroy(GemmPath *g);
+// Switches between band-limited and full K ranges (the panels are the same).
+void gemm_set_dense(GemmPath *g, bool dense);
 // Split-operand copies of Y that the prox epilogue must write.
 void gemm_state_operands(GemmPath *g, void **yhi, void **ylo, int *split_kind);
 // Called once per solve after B has been copied in (binds its pointer).

@@ -80,15 +80,21 @@ struct ProxArgs {
     unsigned *status;    // device status word
 };
 
+// chunk: terms staged per block (0: the default rule, a shared-memory budget);
+// a chunk that does not fit falls back to the default.
 template <typename T>
 void launch_band_rows(const T *In, int m, int n, const T *Fb, int lo, int w, int r, T *Z,
-                      cudaStream_t s);
+                      cudaStream_t s, int chunk = 0);
 template <typename T>
 void launch_band_cols(const T *Z, int m, int n, const T *Gb, int lo, int w, int r,
-                      EpiKind epi, T *Out, const ProxArgs &pa, cudaStream_t s);
+                      EpiKind epi, T *Out, const ProxArgs &pa, cudaStream_t s, int chunk = 0);
 
 size_t band_rows_smem(int w, size_t elem);
 size_t band_cols_smem(int w, size_t elem);
+// Largest FP32 term chunk of a rows (cols) block of band width w that fits in
+// shared memory, at most r.
+int band_rows_chunk_limit(int r, int w);
+int band_cols_chunk_limit(int r, int w);
 cudaError_t band_set_smem_limits(int w);
 
 // Persistent cooperative solver (kernels_persistent.cu).
@@ -112,6 +118,9 @@ struct BandItem {
     int prob, q, tile, pad;   // rows pass: q = term chunk; cols pass: q = 0
 };
 void persistent_chunks(int r, int wmax, int *rows_chunk, int *cols_chunk, size_t *smem);
+// Term chunks of the grouped batch kernels: the requested ones (> 0, e.g.
+// from the autotuner) when they fit, else the persistent solver's rule.
+void grouped_chunks(int r, int wmax, int rows_req, int cols_req, int *rows_chunk, int *cols_chunk, size_t *smem);
 cudaError_t band_grouped_prepare(size_t smem);
 void launch_band_grouped_stage(int st, const BandProb *probs, const BandItem *items, int nitems, int k, size_t smem,
                                cudaStream_t s);

@@ -80,16 +80,18 @@ void launch_pdl(void (*kern)(KArgs...), dim3 grid, size_t smem, cudaStream_t s, 
 }
 
 template <typename T>
-void launch_band_rows(const T *In, int m, int n, const T *Fb, int lo, int w, int r, T *Z, cudaStream_t s) {
-    const int chunk = rows_chunk<T>(r, w);
+void launch_band_rows(const T *In, int m, int n, const T *Fb, int lo, int w, int r, T *Z, cudaStream_t s, int req) {
+    int chunk = req > 0 ? std::min(req, r) : rows_chunk<T>(r, w);
+    if (band::rows_smem<T>(w, chunk) > kBandSmemMax) chunk = rows_chunk<T>(r, w);
     dim3 grid((n + band::TC - 1) / band::TC, (m + band::TA - 1) / band::TA, (r + chunk - 1) / chunk);
     launch_pdl(band_rows_kernel<T>, grid, band::rows_smem<T>(w, chunk), s, In, m, n, Fb, lo, w, r, chunk, Z);
 }
 
 template <typename T>
 void launch_band_cols(const T *Z, int m, int n, const T *Gb, int lo, int w, int r, EpiKind epi, T *Out,
-                      const ProxArgs &pa, cudaStream_t s) {
-    const int chunk = cols_chunk<T>(r, w);
+                      const ProxArgs &pa, cudaStream_t s, int req) {
+    int chunk = req > 0 ? std::min(req, r) : cols_chunk<T>(r, w);
+    if (band::cols_smem<T>(w, chunk) > kBandSmemMax) chunk = cols_chunk<T>(r, w);
     dim3 grid((n + band::TC - 1) / band::TC, (m + band::TA - 1) / band::TA);
     const size_t sm = band::cols_smem<T>(w, chunk);
     if (epi == EPI_STORE)
@@ -98,6 +100,17 @@ void launch_band_cols(const T *Z, int m, int n, const T *Gb, int lo, int w, int 
         launch_pdl(band_cols_kernel<T, EPI_RESIDUAL>, grid, sm, s, Z, m, n, Gb, lo, w, r, chunk, Out, pa);
     else
         launch_pdl(band_cols_kernel<T, EPI_PROX>, grid, sm, s, Z, m, n, Gb, lo, w, r, chunk, Out, pa);
+}
+
+int band_rows_chunk_limit(int r, int w) {
+    int c = r;
+    while (c > 1 && band::rows_smem<float>(w, c) > kBandSmemMax) --c;
+    return c;
+}
+int band_cols_chunk_limit(int r, int w) {
+    int c = r;
+    while (c > 1 && band::cols_smem<float>(w, c) > kBandSmemMax) --c;
+    return c;
 }
 
 size_t band_rows_smem(int w, size_t elem) {
@@ -122,10 +135,13 @@ cudaError_t band_set_smem_limits(int w) {
     return cudaSuccess;
 }
 
-template void launch_band_rows<float>(const float *, int, int, const float *, int, int, int, float *, cudaStream_t);
-template void launch_band_rows<double>(const double *, int, int, const double *, int, int, int, double *, cudaStream_t);
-template void launch_band_cols<float>(const float *, int, int, const float *, int, int, int, EpiKind, float *, const ProxArgs &, cudaStream_t);
-template void launch_band_cols<double>(const double *, int, int, const double *, int, int, int, EpiKind, double *, const ProxArgs &, cudaStream_t);
+template void launch_band_rows<float>(const float *, int, int, const float *, int, int, int, float *, cudaStream_t, int);
+template void launch_band_rows<double>(const double *, int, int, const double *, int, int, int, double *, cudaStream_t,
+                                       int);
+template void launch_band_cols<float>(const float *, int, int, const float *, int, int, int, EpiKind, float *,
+                                      const ProxArgs &, cudaStream_t, int);
+template void launch_band_cols<double>(const double *, int, int, const double *, int, int, int, EpiKind, double *,
+                                       const ProxArgs &, cudaStream_t, int);
 
 // ------------------------------------------------------------------ helpers
 namespace {

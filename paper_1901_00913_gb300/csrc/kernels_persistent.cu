@@ -139,6 +139,18 @@ void persistent_chunks(int r, int wmax, int *rows_chunk, int *cols_chunk, size_t
     *smem = std::max(rows_fixed + rc * rows_term, cc * cols_term);
 }
 
+void grouped_chunks(int r, int wmax, int rows_req, int cols_req, int *rows_chunk, int *cols_chunk, size_t *smem) {
+    persistent_chunks(r, wmax, rows_chunk, cols_chunk, smem);
+    const int rc = rows_req > 0 ? std::min(rows_req, r) : *rows_chunk;
+    const int cc = cols_req > 0 ? std::min(cols_req, r) : *cols_chunk;
+    const size_t sm = std::max(band::rows_smem<float>(wmax, rc), band::cols_smem<float>(wmax, cc));
+    if (sm <= 227 * 1024) {
+        *rows_chunk = rc;
+        *cols_chunk = cc;
+        *smem = sm;
+    }
+}
+
 namespace {
 
 // Grouped stages: block b runs work item items[b] of problem items[b].prob.
