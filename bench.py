@@ -325,6 +325,9 @@ def run_batched(args, torch):
             sv.tune(iters=3)
         t_tune = time.perf_counter() - t_tune
         batch = api.Batch(solvers)
+        t_bt = time.perf_counter()
+        batch_tuning = batch.tune(iters=5)     # the grouped launches' shared-memory plan
+        t_tune += time.perf_counter() - t_bt
         outs = [torch.empty_like(d) for d in d_bs]
         for _ in range(args.warmup):
             batch.solve(d_bs, lams, iters, outs=outs)
@@ -355,7 +358,7 @@ def run_batched(args, torch):
                                   "megapixel_iters_per_s": total_px * iters * args.steps / (ms / 1e3) / 1e6,
                                   "sequential_problem_iters_per_s": len(probs) * iters / (t_single / 1e3),
                                   "max_rel_err_sample": max(errs.values()), "rel_err_sample": errs,
-                                  "autotune_s": t_tune,
+                                  "autotune_s": t_tune, "batch_tuning": batch_tuning,
                                   "clocks": clk.summary()}
         batch.close()
         for sv in solvers:

@@ -336,6 +336,22 @@ sfista_status sfista_tune(sfista_ctx *ctx, int iters, sfista_tune_entry *entries
                           int *n_entries);
 
 /*
+ * sfista_batch_tune -- autotuner of a banded batch.  The grouped launches of a
+ * batch share one shared-memory size (that of the largest tile of any
+ * problem), which sets the blocks resident per SM for every problem, so the
+ * batch is tuned as a whole: for each shared-memory budget in a fixed list
+ * (and for the problems' own chunks, budget 0) every problem takes the largest
+ * term chunks that fit, the batch solves `iters` iterations of an all-zero
+ * observation twice (the second timed), and the fastest plan is kept.
+ * entries: one per distinct plan, op = SFISTA_OP_BANDED, stage = -1, chunk =
+ * the budget in KB (0: each problem's own chunks), ms = time per iteration.
+ * Tensor-core batches have a single tile shape: no entries, SFISTA_OK.
+ * Synchronous.  Leaves every grouped context's state undefined.
+ */
+sfista_status sfista_batch_tune(sfista_batch *batch, int iters, sfista_tune_entry *entries, int max_entries,
+                                int *n_entries);
+
+/*
  * sfista_apply_static -- the banded operator of sfista_apply without any
  * device allocation.  The paper has no counterpart: this call exists for
  * callers that cannot allocate device memory themselves, such as a plugin

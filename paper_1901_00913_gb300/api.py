@@ -67,6 +67,7 @@ def load(path=None):
     L.sfista_blur.argtypes = [vp, i, i, i, i, i, vp, i, i, vp, vp]
     L.sfista_time_stages.argtypes = [vp, vp, d, i, vp]
     L.sfista_tune.argtypes = [vp, i, ctypes.POINTER(TuneEntry), i, ctypes.POINTER(ctypes.c_int)]
+    L.sfista_batch_tune.argtypes = [vp, i, ctypes.POINTER(TuneEntry), i, ctypes.POINTER(ctypes.c_int)]
     L.sfista_apply_static.argtypes = [vp, vp, i, i, i, vp, i, i, vp, i, i, vp]
     L.sfista_batch_create.argtypes = [vp, i, ctypes.POINTER(vp)]
     L.sfista_batch_solve.argtypes = [vp, vp, vp, i, vp, vp]
@@ -233,6 +234,14 @@ def sfista_tune(ctx, iters=10, max_entries=64):
             for e in buf[:min(cnt.value, max_entries)]]
 
 
+def sfista_batch_tune(handle, iters=5, max_entries=64):
+    """Batch autotuner (see include/sfista.h): one dict per plan, chunk = budget in KB."""
+    buf = (TuneEntry * max_entries)()
+    cnt = ctypes.c_int(0)
+    _check(load().sfista_batch_tune(ctypes.c_void_p(handle), int(iters), buf, int(max_entries), ctypes.byref(cnt)))
+    return [{"budget_kb": e.chunk, "ms": e.ms} for e in buf[:min(cnt.value, max_entries)]]
+
+
 def sfista_apply_static(d_x, d_y, r, band_right, lo_right, band_left, lo_left, stream=None):
     """Operator without allocation; band tables are CUDA float32 tensors (r, w, len)."""
     m, n = d_x.shape
@@ -290,6 +299,10 @@ class Batch:
         if sync:
             sfista_batch_sync(self.handle, stream)
         return outs
+
+    def tune(self, iters=5):
+        """Chooses the grouped launches' shared-memory plan by measurement; returns the measurements."""
+        return sfista_batch_tune(self.handle, iters)
 
     def close(self):
         if self.handle:

@@ -354,6 +354,64 @@ void batch_stage(sfista_batch *b, int st, int k) {
     else launch_band_grouped_stage(st, b->d_probs, b->d_items[st], b->nitems[st], k, b->smem, b->stream);
 }
 
+// Term chunks, work lists and shared-memory size of a banded batch.  budget 0:
+// each problem's own chunks (tuned, else the default rule); otherwise every
+// problem takes the largest chunks whose tiles fit in `budget` bytes, so the
+// one shared-memory size of the grouped launches stays within it.
+sfista_status band_batch_plan(sfista_batch *b, size_t budget) {
+    const int np = (int)b->ctxs.size();
+    std::vector<int> order(np);
+    for (int p = 0; p < np; ++p) order[p] = p;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return (double)b->ctxs[x]->N * b->ctxs[x]->r > (double)b->ctxs[y]->N * b->ctxs[y]->r;
+    });
+    b->smem = 0;
+    for (int p = 0; p < np; ++p) {
+        sfista_ctx *c = b->ctxs[p];
+        const HostSetup &h = c->hs;
+        BandProb &P = b->h_probs[p];
+        const int wmax = std::max(std::max(h.A.w, h.AT.w), std::max(h.B.w, h.BT.w));
+        int rq = c->chunk[0], cq = c->chunk[1];
+        if (budget) {
+            rq = cq = 1;
+            while (rq < c->r && band_smem_f32(true, wmax, rq + 1) <= budget) ++rq;
+            while (cq < c->r && band_smem_f32(false, wmax, cq + 1) <= budget) ++cq;
+        }
+        size_t sm = 0;
+        grouped_chunks(c->r, wmax, rq, cq, &P.rows_chunk, &P.cols_chunk, &sm);
+        b->smem = std::max(b->smem, sm);
+    }
+    std::vector<BandItem> items[4];
+    for (int p : order) {
+        const BandProb &P = b->h_probs[p];
+        const int nq = (P.r + P.rows_chunk - 1) / P.rows_chunk;
+        for (int q = 0; q < nq; ++q)
+            for (int t = 0; t < band_rows_tiles(P.m, P.n); ++t) items[0].push_back(BandItem{p, q, t, 0});
+        for (int t = 0; t < band_cols_tiles(P.m, P.n); ++t) items[1].push_back(BandItem{p, 0, t, 0});
+    }
+    items[2] = items[0];
+    items[3] = items[1];
+    cudaError_t e = band_grouped_prepare(b->smem);
+    if (e) return fail(SFISTA_ENOTSUP, std::string("grouped banded kernels: ") + cudaGetErrorString(e));
+    for (int st = 0; st < 4; ++st) {
+        if (b->d_items[st]) {
+            cudaFree(b->d_items[st]);
+            b->d_items[st] = nullptr;
+        }
+        b->nitems[st] = (int)items[st].size();
+        if ((e = cudaMalloc((void **)&b->d_items[st], items[st].size() * sizeof(BandItem))) ||
+            (e = cudaMemcpy(b->d_items[st], items[st].data(), items[st].size() * sizeof(BandItem),
+                            cudaMemcpyHostToDevice)))
+            return fail(SFISTA_ENOMEM, std::string("grouped work lists: ") + cudaGetErrorString(e));
+    }
+    if (b->gexec) {   // captured with the old work lists
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+        b->g_iters = -1;
+    }
+    return SFISTA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -693,12 +751,6 @@ sfista_status sfista_batch_create(sfista_ctx *const *ctxs, int nprob, sfista_bat
         }
     } else {
         b->h_probs.resize(nprob);
-        std::vector<BandItem> items[4];
-        std::vector<int> order(nprob);
-        for (int p = 0; p < nprob; ++p) order[p] = p;
-        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-            return (double)ctxs[x]->N * ctxs[x]->r > (double)ctxs[y]->N * ctxs[y]->r;
-        });
         for (int p = 0; p < nprob; ++p) {
             sfista_ctx *c = ctxs[p];
             const HostSetup &h = c->hs;
@@ -707,10 +759,6 @@ sfista_status sfista_batch_create(sfista_ctx *const *ctxs, int nprob, sfista_bat
             P.m = c->m;
             P.n = c->n;
             P.r = c->r;
-            int wmax = std::max(std::max(h.A.w, h.AT.w), std::max(h.B.w, h.BT.w));
-            size_t sm = 0;
-            grouped_chunks(c->r, wmax, c->chunk[0], c->chunk[1], &P.rows_chunk, &P.cols_chunk, &sm);
-            b->smem = std::max(b->smem, sm);
             P.fA = c->fA;
             P.fB = c->fB;
             P.fAT = c->fAT;
@@ -726,28 +774,14 @@ sfista_status sfista_batch_create(sfista_ctx *const *ctxs, int nprob, sfista_bat
             P.Z = c->Z;
             P.R = c->R;
         }
-        for (int p : order) {
-            const BandProb &P = b->h_probs[p];
-            const int nq = (P.r + P.rows_chunk - 1) / P.rows_chunk;
-            for (int q = 0; q < nq; ++q)
-                for (int t = 0; t < band_rows_tiles(P.m, P.n); ++t) items[0].push_back(BandItem{p, q, t, 0});
-            for (int t = 0; t < band_cols_tiles(P.m, P.n); ++t) items[1].push_back(BandItem{p, 0, t, 0});
-        }
-        items[2] = items[0];
-        items[3] = items[1];
-        if ((e = band_grouped_prepare(b->smem)) ||
-            (e = cudaMalloc((void **)&b->d_probs, nprob * sizeof(BandProb)))) {
+        if ((e = cudaMalloc((void **)&b->d_probs, nprob * sizeof(BandProb)))) {
             batch_free(b);
-            return fail(SFISTA_ENOTSUP, std::string("grouped banded tables: ") + cudaGetErrorString(e));
+            return fail(SFISTA_ENOMEM, std::string("grouped banded tables: ") + cudaGetErrorString(e));
         }
-        for (int st = 0; st < 4; ++st) {
-            b->nitems[st] = (int)items[st].size();
-            if ((e = cudaMalloc((void **)&b->d_items[st], items[st].size() * sizeof(BandItem))) ||
-                (e = cudaMemcpy(b->d_items[st], items[st].data(), items[st].size() * sizeof(BandItem),
-                                cudaMemcpyHostToDevice))) {
-                batch_free(b);
-                return fail(SFISTA_ENOMEM, std::string("grouped work lists: ") + cudaGetErrorString(e));
-            }
+        sfista_status st = band_batch_plan(b, 0);
+        if (st) {
+            batch_free(b);
+            return st;
         }
     }
     *out = b;
@@ -851,6 +885,65 @@ sfista_status sfista_batch_sync(sfista_batch *b, void *stream) {
         if (st && !worst) worst = st;
     }
     return worst;
+}
+
+sfista_status sfista_batch_tune(sfista_batch *b, int iters, sfista_tune_entry *entries, int max_entries,
+                                int *n_entries) {
+    if (!b) return fail(SFISTA_EINVAL, "batch is NULL");
+    if (n_entries) *n_entries = 0;
+    if (iters < 1 || max_entries < 0) return fail(SFISTA_EINVAL, "iters must be >= 1 and max_entries >= 0");
+    if (b->gemm) return SFISTA_OK;   // one tile shape: nothing to choose
+    DeviceGuard g(b->dev);
+    const int np = (int)b->ctxs.size();
+    std::vector<const float *> d_b(np);
+    std::vector<float *> d_x(np);
+    std::vector<double> lams(np, 0.0);
+    for (int p = 0; p < np; ++p) {   // all-zero observations; the scratch image doubles as output
+        sfista_ctx *c = b->ctxs[p];
+        SF_CUDA(cudaMemsetAsync(c->tmp, 0, c->N * sizeof(float), b->stream));
+        d_b[p] = c->tmp;
+        d_x[p] = c->tmp;
+    }
+    cudaEvent_t e0, e1;
+    SF_CUDA(cudaEventCreate(&e0));
+    SF_CUDA(cudaEventCreate(&e1));
+    const size_t kb = 1024;
+    const size_t budgets[] = {0, 24 * kb, 32 * kb, 48 * kb, 64 * kb, 80 * kb, 96 * kb, 128 * kb, 160 * kb, 227 * kb};
+    std::vector<std::vector<int>> seen;
+    int count = 0;
+    float best = -1.f;
+    size_t best_budget = 0;
+    sfista_status st = SFISTA_OK;
+    for (size_t bud : budgets) {
+        if ((st = band_batch_plan(b, bud))) break;
+        std::vector<int> sig;
+        for (const BandProb &P : b->h_probs) sig.push_back(P.rows_chunk), sig.push_back(P.cols_chunk);
+        if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;
+        seen.push_back(sig);
+        // The first solve captures the graph of this plan; the second is timed.
+        if ((st = sfista_batch_solve(b, d_b.data(), lams.data(), iters, d_x.data(), b->stream))) break;
+        cudaError_t e = cudaEventRecord(e0, b->stream);
+        if (!e && !(st = sfista_batch_solve(b, d_b.data(), lams.data(), iters, d_x.data(), b->stream)))
+            e = cudaEventRecord(e1, b->stream);
+        if (st) break;
+        float ms = 0.f;
+        if (!e) e = cudaEventSynchronize(e1);
+        if (!e) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e) {
+            st = fail(SFISTA_ECUDA, std::string("batch tuning: ") + cudaGetErrorString(e));
+            break;
+        }
+        ms /= iters;
+        if (entries && count < max_entries) entries[count] = sfista_tune_entry{SFISTA_OP_BANDED, -1, (int)(bud / kb), ms};
+        ++count;
+        if (best < 0.f || ms < best) best = ms, best_budget = bud;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    if ((st = band_batch_plan(b, best_budget))) return st;
+    if (n_entries) *n_entries = count;
+    return sfista_batch_sync(b, nullptr);
 }
 
 sfista_status sfista_solve_batched(sfista_ctx *const *ctxs, const float *const *d_b, const double *lambdas,

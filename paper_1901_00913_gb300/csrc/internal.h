@@ -95,6 +95,8 @@ size_t band_cols_smem(int w, size_t elem);
 // shared memory, at most r.
 int band_rows_chunk_limit(int r, int w);
 int band_cols_chunk_limit(int r, int w);
+// Shared memory of an FP32 rows (cols) block staging `chunk` terms of width w.
+size_t band_smem_f32(bool rows, int w, int chunk);
 cudaError_t band_set_smem_limits(int w);
 
 // Persistent cooperative solver (kernels_persistent.cu).

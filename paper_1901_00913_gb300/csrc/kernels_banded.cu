@@ -102,6 +102,10 @@ void launch_band_cols(const T *Z, int m, int n, const T *Gb, int lo, int w, int 
         launch_pdl(band_cols_kernel<T, EPI_PROX>, grid, sm, s, Z, m, n, Gb, lo, w, r, chunk, Out, pa);
 }
 
+size_t band_smem_f32(bool rows, int w, int chunk) {
+    return rows ? band::rows_smem<float>(w, chunk) : band::cols_smem<float>(w, chunk);
+}
+
 int band_rows_chunk_limit(int r, int w) {
     int c = r;
     while (c > 1 && band::rows_smem<float>(w, c) > kBandSmemMax) --c;

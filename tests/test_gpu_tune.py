@@ -88,3 +88,24 @@ def test_batch_uses_tuned_chunks():
     batch.close()
     for s in solvers:
         s.close()
+
+
+def test_batch_tune_keeps_results():
+    specs = [(96, 128, 11, 2, 506), (128, 96, 17, 3, 507), (64, 64, 9, 1, 508), (200, 176, 23, 4, 509)]
+    pr = [_problem(*sp) for sp in specs]
+    lam, iters = 0.005, 30
+    solvers = [api.Sfista(P, b.shape, 1, ka.r, prec="fp32", op="banded", lipschitz=L) for P, b, ka, L in pr]
+    d_bs = [torch.from_numpy(b).cuda() for _, b, _, _ in pr]
+    batch = api.Batch(solvers)
+    before = [X.clone() for X in batch.solve(d_bs, [lam] * len(pr), iters)]
+    log = batch.tune(iters=3)
+    assert log and all(e["ms"] > 0 for e in log)
+    assert len({e["budget_kb"] for e in log}) == len(log)    # distinct plans only
+    after = batch.solve(d_bs, [lam] * len(pr), iters)
+    for X0, X1, (P, b, ka, L) in zip(before, after, pr):
+        assert torch.equal(X0, X1)     # chunking regroups terms, not the arithmetic
+        Xo = oracle.sfista(b.astype(np.float64), ka, L, lam, iters)
+        assert oracle.rel_fro(X1.cpu().numpy(), Xo) <= 1e-5
+    batch.close()
+    for s in solvers:
+        s.close()
