@@ -69,6 +69,6 @@ def _declare(L):
     L.orc_power_lipschitz.restype = d
     L.orc_objective.argtypes = [_D, _D, i, i, i, _D, i, i, _D, i, i, i, d]
     L.orc_objective.restype = d
-    L.orc_sfista.argtypes = [_D, i, i, i, _D, i, i, _D, i, i, i, d, d, i, i, i,
+    L.orc_sfista.argtypes = [_D, i, i, i, _D, i, i, _D, i, i, i, d, d, i, i, d, i,
                              vp, vp, _D, vp]
-    L.orc_fista_dense.argtypes = [_D, _D, i, d, d, i, _D]
+    L.orc_fista_dense.argtypes = [_D, _D, i, d, d, d, i, _D]

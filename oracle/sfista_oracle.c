@@ -251,10 +251,22 @@ double orc_objective(const double *X, const double *Bd, int m, int n, int r,
     return 0.5 * f + 0.5 * lambda * lambda * g;
 }
 
+/* Soft threshold S_mu(v) = sign(v) max(|v| - mu, 0): the prox of mu |x|. */
+static double soft_threshold(double v, double mu)
+{
+    if (v > mu) return v - mu;
+    if (v < -mu) return v + mu;
+    return 0.0;
+}
+
 /* sFISTA, Alg. 2, with X_0 = 0 (so Y_1 = 0) and a fixed iteration count.
  *   Step 1: X_k = (L Y_k - sum_j B_j^T (sum_i B_i Y_k A_i^T - B) A_j) / (L + lambda^2)
  *           (optionally followed by max(X_k, 0): the prox of the
  *            non-negativity constraint the introduction motivates)
+ *           With mu > 0 the regulariser is g(x) = lambda^2/2 |x|^2 + mu |x|_1
+ *           (the l1 term Sec. 1 and Sec. 5 name for future work), and the
+ *           minimiser of Q_L(x, Y_k) of Sec. 3.1 is, element by element,
+ *           S_mu(L Y_k - grad f(Y_k)) / (L + lambda^2).
  *   Step 2: t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2,  t_1 = 1
  *   Step 3: Y_{k+1} = X_k + (t_k - 1)/t_{k+1} (X_k - X_{k-1})
  * If X_start/Xprev_start are non-NULL the loop resumes from (X_{k0},
@@ -262,7 +274,7 @@ double orc_objective(const double *X, const double *Bd, int m, int n, int r,
  * to X_out and, if Xprev_out is non-NULL, X_{iters-1} to Xprev_out. */
 void orc_sfista(const double *Bd, int m, int n, int r, const double *C, int p,
                 int cr, const double *D, int q, int cc, int bc, double L,
-                double lambda, int iters, int project, int k0,
+                double lambda, int iters, int project, double mu, int k0,
                 const double *X_start, const double *Xprev_start,
                 double *X_out, double *Xprev_out)
 {
@@ -292,7 +304,9 @@ void orc_sfista(const double *Bd, int m, int n, int r, const double *C, int p,
         orc_kron_apply_T(R, m, n, r, C, p, cr, D, q, cc, bc, G);
         memcpy(Xp, X, sizeof(double) * N);
         for (size_t s = 0; s < N; ++s) {
-            double x = (L * Y[s] - G[s]) / (L + lam2);
+            double v = L * Y[s] - G[s];
+            if (mu > 0.0) v = soft_threshold(v, mu);
+            double x = v / (L + lam2);
             if (project && x < 0.0) x = 0.0;
             X[s] = x;
         }
@@ -311,9 +325,10 @@ void orc_sfista(const double *Bd, int m, int n, int r, const double *C, int p,
 }
 
 /* Vector FISTA on an explicit N x N matrix A (Alg. 1), x_0 = 0:
- *   x_k = (L y_k - A^T (A y_k - b)) / (L + lambda^2), then Steps 2-3. */
+ *   x_k = S_mu(L y_k - A^T (A y_k - b)) / (L + lambda^2) (mu = 0: no
+ *   threshold), then Steps 2-3. */
 void orc_fista_dense(const double *A, const double *b, int N, double L,
-                     double lambda, int iters, double *x_out)
+                     double lambda, double mu, int iters, double *x_out)
 {
     double *x = (double *)calloc((size_t)N, sizeof(double));
     double *xp = (double *)calloc((size_t)N, sizeof(double));
@@ -330,7 +345,9 @@ void orc_fista_dense(const double *A, const double *b, int N, double L,
         for (int j = 0; j < N; ++j) {
             double g = 0.0;
             for (int i = 0; i < N; ++i) g += A[(size_t)i * N + j] * r[i];
-            x[j] = (L * y[j] - g) / (L + lam2);
+            double v = L * y[j] - g;
+            if (mu > 0.0) v = soft_threshold(v, mu);
+            x[j] = v / (L + lam2);
         }
         double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
         for (int j = 0; j < N; ++j) y[j] = x[j] + (t - 1.0) / tn * (x[j] - xp[j]);

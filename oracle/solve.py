@@ -82,8 +82,11 @@ def objective(X, Bd, ka, lam):
 
 
 def sfista(Bd, ka, L, lam, iters, project=False, k0=0, X_start=None,
-           Xprev_start=None, return_prev=False):
-    """Alg. 2 from X_0 = 0 (or resumed at iteration k0 from (X_k0, X_k0-1))."""
+           Xprev_start=None, return_prev=False, mu=0.0):
+    """Alg. 2 from X_0 = 0 (or resumed at iteration k0 from (X_k0, X_k0-1)).
+
+    mu > 0 adds mu ||X||_1 to the regulariser: Step 1 becomes the minimiser
+    of Q_L (Sec. 3.1), S_mu(L Y - grad f(Y)) / (L + lam^2) element by element."""
     Bd = _f64(Bd)
     m, n = Bd.shape
     C, p, D, q = _prof(ka)
@@ -93,18 +96,18 @@ def sfista(Bd, ka, L, lam, iters, project=False, k0=0, X_start=None,
     xps = _f64(Xprev_start) if Xprev_start is not None else None
     _native.lib().orc_sfista(
         Bd, m, n, ka.r, C, p, ka.cr, D, q, ka.cc, ka.bc, float(L), float(lam),
-        int(iters), int(bool(project)), int(k0),
+        int(iters), int(bool(project)), float(mu), int(k0),
         xs.ctypes.data if xs is not None else None,
         xps.ctypes.data if xps is not None else None,
         X, Xp.ctypes.data)
     return (X, Xp) if return_prev else X
 
 
-def fista_dense(A, b, L, lam, iters):
-    """Alg. 1 (vector FISTA) on an explicit matrix, x_0 = 0."""
+def fista_dense(A, b, L, lam, iters, mu=0.0):
+    """Alg. 1 (vector FISTA) on an explicit matrix, x_0 = 0 (mu: l1 weight)."""
     A, b = _f64(A), _f64(b)
     x = np.empty_like(b)
-    _native.lib().orc_fista_dense(A, b, b.shape[0], float(L), float(lam), int(iters), x)
+    _native.lib().orc_fista_dense(A, b, b.shape[0], float(L), float(lam), float(mu), int(iters), x)
     return x
 
 

@@ -296,3 +296,44 @@ def test_theorem4_error_falls_with_rank():
     assert errs[-1] < 1e-13
     assert etas[-1] <= etas[0]
     assert all(b <= a * 1.02 for a, b in zip(etas, etas[1:]))
+
+
+# ------------------------------------------------------------------ l1 variant of Step 1
+def _soft(v, mu):
+    return np.sign(v) * np.maximum(np.abs(v) - mu, 0.0)
+
+
+def test_l1_step_with_identity_operator_is_closed_form():
+    """A 1x1 unit PSF gives A_s = I; with L = 1 the first step from Y_1 = 0 is already the
+    minimiser of 1/2||X - B||^2 + lam^2/2 ||X||^2 + mu ||X||_1: S_mu(B) / (1 + lam^2)."""
+    g = W.rng(31)
+    B = g.standard_normal((13, 11))
+    ka = kron.kron_approx(np.ones((1, 1)), 0, 0, 13, 11, 0, 1)
+    lam, mu = 0.3, 0.45
+    X1 = oracle.sfista(B, ka, 1.0, lam, 1, mu=mu)
+    np.testing.assert_allclose(X1, _soft(B, mu) / (1.0 + lam * lam), atol=1e-15)
+    assert np.count_nonzero(X1 == 0.0) > 0      # the threshold does set entries to zero
+    X40 = oracle.sfista(B, ka, 1.0, lam, 40, mu=mu)    # and it is a fixed point
+    np.testing.assert_allclose(X40, X1, atol=1e-14)
+
+
+def test_l1_limit_satisfies_optimality_conditions():
+    """At the limit X* of Step 1 with the l1 term: for X*_j != 0,
+    (grad f + lam^2 X*)_j = -mu sign(X*_j); for X*_j = 0, |(grad f + lam^2 X*)_j| <= mu."""
+    ka, Bd, As, L = _tiny_problem(seed=32)
+    lam, mu = 0.1, 0.2
+    X = oracle.sfista(Bd, ka, L, lam, 6000, mu=mu)
+    G = oracle.kron_apply_T(oracle.kron_apply(X, ka) - Bd, ka) + lam * lam * X
+    nz = X != 0.0
+    assert 0 < nz.sum() < X.size                # both cases occur
+    np.testing.assert_allclose(G[nz], -mu * np.sign(X[nz]), atol=1e-9)
+    assert np.abs(G[~nz]).max() <= mu + 1e-9
+
+
+def test_l1_sfista_equals_vector_fista():
+    """Theorem 3 carries over: the element-wise threshold commutes with vec."""
+    ka, Bd, As, L = _tiny_problem(seed=33)
+    for iters in (1, 5, 30):
+        X = oracle.sfista(Bd, ka, L, 0.05, iters, mu=0.01)
+        x = oracle.fista_dense(As, Bd.flatten(order="F"), L, 0.05, iters, mu=0.01)
+        np.testing.assert_allclose(X.flatten(order="F"), x, atol=1e-13)
