@@ -91,6 +91,11 @@ typedef struct {
     double lipschitz_tol;   /* relative change that stops the power iteration (1e-10)     */
     int lipschitz_maxit;    /* power-iteration cap (1000)                                 */
     int device;             /* CUDA device ordinal (default: current device)              */
+    double l1;              /* mu >= 0 (default 0): adds mu ||X||_1 to the regulariser, so
+                               Step 1 becomes S_mu(L Y_k - grad f(Y_k)) / (L + lambda^2)
+                               with S_mu the soft threshold (the minimiser of Q_L of
+                               Sec. 3.1 for that g; Sec. 1 and Sec. 5 name the l1 term
+                               as future work).  Applied before the projection.         */
 } sfista_opts;
 
 /* Fill *opts with the defaults listed above. */

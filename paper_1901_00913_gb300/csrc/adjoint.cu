@@ -269,6 +269,7 @@ sfista_status check_unrolled(sfista_ctx *c, int iters, int ckpt) {
     if (!is_banded(c->op))
         return fail(SFISTA_ENOTSUP, "the unrolled adjoint runs on the banded FP32 operator form");
     if (c->opts.project_nonneg) return fail(SFISTA_ENOTSUP, "the projection is not differentiable");
+    if (c->opts.l1 > 0.0) return fail(SFISTA_ENOTSUP, "the l1 soft threshold is not differentiable");
     if (iters < 1 || ckpt < 1) return fail(SFISTA_EINVAL, "iters and ckpt_every must be >= 1");
     return SFISTA_OK;
 }

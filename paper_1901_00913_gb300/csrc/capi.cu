@@ -119,6 +119,7 @@ ProxArgs sfista::prox_args(sfista_ctx *c, int k, double lam) {
     pa.inv_den = dfp::from_double(1.0 / (c->L + lam * lam));
     pa.shrink = dfp::from_double(c->L / (c->L + lam * lam));
     pa.project = c->opts.project_nonneg;
+    pa.tau = dfp::from_double(c->opts.l1 / (c->L + lam * lam));
     pa.status = c->status;
     return pa;
 }
@@ -427,6 +428,7 @@ void sfista_default_opts(sfista_opts *o) {
     o->lipschitz_tol = 1e-10;
     o->lipschitz_maxit = 1000;
     o->device = -1;
+    o->l1 = 0.0;
 }
 
 sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int center_row,
@@ -440,6 +442,7 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int ce
     if (o.prec < SFISTA_FP32 || o.prec > SFISTA_BF16X3) return fail(SFISTA_EINVAL, "unknown precision");
     if (o.op < SFISTA_OP_AUTO || o.op > SFISTA_OP_BANDED_FUSED) return fail(SFISTA_EINVAL, "unknown operator form");
     if (!(o.lipschitz <= 0.0 || isfinite(o.lipschitz))) return fail(SFISTA_EINVAL, "lipschitz must be finite");
+    if (!(o.l1 >= 0.0) || !isfinite(o.l1)) return fail(SFISTA_EINVAL, "l1 must be finite and >= 0");
     if (center_row == -1 && psf_rows > 0) center_row = (psf_rows - 1) / 2;
     if (center_col == -1 && psf_cols > 0) center_col = (psf_cols - 1) / 2;
     sfista_ctx *c = new (std::nothrow) sfista_ctx();

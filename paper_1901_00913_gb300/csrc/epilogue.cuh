@@ -15,14 +15,24 @@ static __device__ __forceinline__ float tf32_round(float x) {
     return __uint_as_float(u);
 }
 
-// Step 1 shrink (+ projection) and Step 3 momentum for one pixel, with the
+// Step 1 shrink (+ l1 soft threshold, + projection) and Step 3 momentum for one pixel, with the
 // state in double-float:  X_k = s Y_k - d G  (s = L/(L+lambda^2),
 // d = 1/(L+lambda^2)),  Y_{k+1} = X_k + beta_k (X_k - X_{k-1}).
 // Also writes the operand copies of Y_{k+1}: FP32 (banded operator) and/or a
 // hi/lo split (BF16 or TF32) for the tensor-core operator.
+// With the l1 term the shrunk value is soft-thresholded by tau = mu/(L+lambda^2)
+// first (S_mu(v)/(L+lambda^2) = S_tau(v/(L+lambda^2)) since L+lambda^2 > 0).
+static __device__ __forceinline__ float2 soft_threshold(float2 x, float2 tau) {
+    const bool neg = x.x < 0.0f;   // the hi word carries the sign of a normalised pair
+    const float2 d = dfp::sub(neg ? make_float2(-x.x, -x.y) : x, tau);
+    if (!(d.x > 0.0f)) return make_float2(0.0f, 0.0f);
+    return neg ? make_float2(-d.x, -d.y) : d;
+}
+
 static __device__ __forceinline__ float2 prox_step(const ProxArgs &pa, float2 y, float2 xp, float g, float2 beta,
                                                    float2 *xout, bool *bad) {
     float2 x = dfp::sub(dfp::mul(pa.shrink, y), dfp::mul_f(pa.inv_den, g));
+    if (pa.tau.x > 0.0f) x = soft_threshold(x, pa.tau);
     if (pa.project && x.x < 0.0f) x = make_float2(0.0f, 0.0f);
     *bad |= !isfinite(x.x);
     *xout = x;

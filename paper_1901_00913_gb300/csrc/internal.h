@@ -77,6 +77,7 @@ struct ProxArgs {
     float2 inv_den;      // 1 / (L + lambda^2), double-float
     float2 shrink;       // L / (L + lambda^2), double-float
     int project;         // max(X, 0) after the shrink
+    float2 tau;          // mu / (L + lambda^2), double-float: soft threshold of the l1 term (0: none)
     unsigned *status;    // device status word
 };
 

@@ -85,3 +85,22 @@ def test_batch_rejects_mixed_families():
         api.Batch([a, a])
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("prec,op,tol", [("fp32", "banded", 1e-5), ("bf16x3", "gemm_band", 1e-4)])
+def test_batched_l1_per_problem(probs, prec, op, tol):
+    """Each problem keeps its own l1 weight inside the grouped launches."""
+    pr, iters, _ = probs
+    mus = [0.0, 0.02, 0.05, 0.01, 0.03]
+    refs = [oracle.sfista(b.astype(np.float64), ka, L, lam, iters, mu=mu)
+            for (P, b, ka, L, lam), mu in zip(pr, mus)]
+    solvers = [api.Sfista(P, b.shape, 1, ka.r, prec=prec, op=op, lipschitz=L, l1=mu)
+               for (P, b, ka, L, lam), mu in zip(pr, mus)]
+    d_bs = [torch.from_numpy(b).cuda() for P, b, ka, L, lam in pr]
+    batch = api.Batch(solvers)
+    outs = batch.solve(d_bs, [lam for *_, lam in pr], iters)
+    for k, (X, ref) in enumerate(zip(outs, refs)):
+        assert oracle.rel_fro(X.cpu().numpy(), ref) <= tol, (k, mus[k])
+    batch.close()
+    for s in solvers:
+        s.close()

@@ -236,6 +236,40 @@ def test_projection_matches_oracle(op, prec, tol):
     s.close()
 
 
+@pytest.mark.parametrize("op,prec,tol", [("banded", "fp32", 1e-5), ("banded_fused", "fp32", 1e-5),
+                                         ("banded_persistent", "fp32", 1e-5), ("gemm_band", "bf16x3", 1e-4),
+                                         ("gemm_dense", "tf32x3", 1e-4)])
+@pytest.mark.parametrize("project", [False, True])
+def test_l1_threshold_matches_oracle(op, prec, tol, project):
+    """Step 1 with the l1 term (soft threshold tau = mu / (L + lambda^2)), optionally projected."""
+    P = W.rotated_gaussian_psf(15, 2.0, 1.0, 0.3)
+    x, b, _ = _problem(96, 80, P, 1, 109)
+    ka = kron.kron_approx(P, 7, 7, 96, 80, 1, 2)
+    L = _oracle_L(ka)
+    mu = 0.03
+    Xo = oracle.sfista(b.astype(np.float64), ka, L, 0.01, 40, project=project, mu=mu)
+    nz_o = np.count_nonzero(Xo == 0.0)
+    assert 0.02 * Xo.size < nz_o < 0.98 * Xo.size      # the threshold is active
+    s = api.Sfista(P, (96, 80), 1, 2, lipschitz=L, project=project, op=op, prec=prec, l1=mu)
+    X = s.solve_device(_cuda(b), 0.01, 40).cpu().numpy()
+    assert oracle.rel_fro(X, Xo) <= tol
+    assert abs(np.count_nonzero(X == 0.0) - nz_o) <= 0.01 * Xo.size
+    if project:
+        assert X.min() >= 0.0
+    s.close()
+
+
+def test_l1_rejected_by_reverse_mode():
+    P = W.gaussian_psf(7, 1.5)
+    s = api.Sfista(P, (32, 32), 1, 1, lipschitz=1.0, l1=0.01)
+    db = torch.zeros(32, 32, device="cuda")
+    ck = torch.empty(2, 32, 32, dtype=torch.float64, device="cuda")
+    with pytest.raises(api.SfistaError) as e:
+        api.sfista_unrolled_fwd(s.ctx, db, 0.01, 5, 5, ck, torch.empty_like(db))
+    assert e.value.status == 4     # SFISTA_ENOTSUP
+    s.close()
+
+
 def test_zero_iterations_returns_zero():
     P = W.gaussian_psf(9, 2.0)
     s = api.Sfista(P, (40, 40), 0, 1, lipschitz=1.0)
