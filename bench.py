@@ -459,6 +459,79 @@ def run_unrolled(args, torch):
     print(json.dumps(line), flush=True)
 
 
+def run_example2(args, torch):
+    """--workload ex2: the Example 2 stand-in set (defocus and shake blur at three
+    levels, Gaussian / Laplace / multiplicative noise), 18 problems of 256^2,
+    r = 5, 50 iterations each.  Per case and form: iterations/s, the error
+    against the FP64 oracle on the first --check-iters iterations, the
+    restoration error eta = ||X - x|| / ||x|| and residual gamma = ||A X - b|| /
+    ||b|| (exact blur) of Sec. 4, and the singular-value decay of P and P_bar."""
+    from paper_1901_00913_gb300 import api, build, diagnostics as D, workloads as W
+    import oracle
+    from oracle import kron, _native
+    build.build()
+    cases = W.example2_cases()
+    forms = {}
+    cpu_s, cpu_its = 0.0, 0
+    decay = {}
+    for f in args.forms.split(","):
+        prec, op, tune = _form(f)
+        rows = {}
+        rates = []
+        for pr in cases:
+            n = pr.x_true.shape[0]
+            xt = torch.from_numpy(pr.x_true.astype(np.float32)).cuda()
+            bx = api.sfista_blur(pr.psf, xt, pr.bc).double().cpu().numpy()
+            b = (bx + W.noise_of_kind(pr.extra["noise"], bx, pr.noise, pr.noise_level)).astype(np.float32)
+            db = torch.from_numpy(b).cuda()
+            s = api.Sfista(pr.psf, (n, n), pr.bc, pr.r, prec=prec, op=op)
+            if tune:
+                s.tune(iters=5)
+            info = s.info()
+            L = info["lipschitz"]
+            Xc = s.solve_device(db, pr.lam, args.check_iters).cpu().numpy()
+            if pr.name not in decay:
+                cr, cc = pr.centre
+                ka = kron.kron_approx(pr.psf, cr, cc, n, n, pr.bc, pr.r)
+                t0 = time.perf_counter()
+                Xo = oracle.sfista(b.astype(np.float64), ka, L, pr.lam, args.check_iters)
+                cpu_s += time.perf_counter() - t0
+                cpu_its += args.check_iters
+                decay[pr.name] = {"P": D.decay_ratios(D.psf_singular_values(pr.psf)),
+                                  "P_bar": D.decay_ratios(info["sigma"]), "ref": Xo}
+            err = oracle.rel_fro(Xc, decay[pr.name]["ref"])
+            out = torch.empty_like(db)
+            for _ in range(args.warmup):
+                s.solve_device(db, pr.lam, pr.iters, out=out)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            for _ in range(args.steps):
+                s.solve_device(db, pr.lam, pr.iters, out=out, sync=False)
+            ev1.record()
+            torch.cuda.synchronize()
+            v = pr.iters * args.steps / (ev0.elapsed_time(ev1) / 1e3)
+            rates.append(v)
+            res = api.sfista_blur(pr.psf, out, pr.bc) - db
+            eta = float(torch.linalg.norm(out.double() - xt.double()) / torch.linalg.norm(xt.double()))
+            gamma = float(torch.linalg.norm(res.double()) / torch.linalg.norm(db.double()))
+            rows[pr.name] = {"op": info["op"], "iters_per_s": v,
+                             "rel_err_vs_oracle_first_%d_its" % args.check_iters: err,
+                             "eta": eta, "gamma": gamma, "psf": list(pr.psf.shape),
+                             "sigma_decay": {"P": decay[pr.name]["P"], "P_bar": decay[pr.name]["P_bar"]}}
+            s.close()
+        forms[f] = {"mean_iters_per_s": float(np.mean(rates)), "min_iters_per_s": float(np.min(rates)),
+                    "max_rel_err": max(r["rel_err_vs_oracle_first_%d_its" % args.check_iters]
+                                       for r in rows.values()), "cases": rows}
+    line = {"metric": METRIC, "workload": "Example 2 stand-in: 18 problems 256x256, defocus / shake blur x 3 levels "
+            "x gauss / laplace / multiplicative noise (1%), reflexive, r=5, lambda=0.005, 50 its",
+            "unit": "iters/s", "steps": args.steps, "warmup": args.warmup, "forms": forms,
+            "cpu_baseline": {"value": cpu_its / cpu_s, "unit": "iters/s", "kind": "oracle",
+                             "cores": _native.threads(), "sample": "%d iterations of each of the 18 problems"
+                             % args.check_iters}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -468,7 +541,7 @@ def main():
     ap.add_argument("--forms", default="fp32:auto+tune,fp32:banded_fused,fp32:banded,fp32:banded_persistent,bf16x3:gemm_band,tf32x3:gemm_band,bf16:gemm_band,tf32:gemm_band",
                     help="comma list of prec:op forms to measure")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "cfg4", "cfg5"])
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "cfg4", "cfg5", "ex2"])
     ap.add_argument("--check-iters", type=int, default=10)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -480,8 +553,9 @@ def main():
             args.forms = {"cfg3": "fp32:auto+tune,fp32:banded_fused,fp32:banded,bf16x3:auto+tune,bf16x3:gemm_band,"
                                   "tf32x3:gemm_band,bf16x3:gemm_dense",
                           "cfg4": "fp32:banded,bf16x3:gemm_band,tf32x3:gemm_band",
-                          "cfg5": "fp32:banded_fused,fp32:banded"}[args.workload]
-        run = {"cfg3": run_large, "cfg4": run_batched, "cfg5": run_unrolled}[args.workload]
+                          "cfg5": "fp32:banded_fused,fp32:banded",
+                          "ex2": "fp32:auto,bf16x3:auto"}[args.workload]
+        run = {"cfg3": run_large, "cfg4": run_batched, "cfg5": run_unrolled, "ex2": run_example2}[args.workload]
         return run(args, torch)
 
     import torch

@@ -60,6 +60,19 @@ def shapes_image(g, m, n, rects=12, ellipses=12):
     return X
 
 
+def dots_image(g, m, n, count=None, sigma=(1.0, 3.0)):
+    """Small Gaussian-shaped dots of peak U[0.3, 1] at uniform positions (a
+    stand-in for the 'dot' test images of Example 2); count defaults to n/2."""
+    count = max(1, n // 2) if count is None else count
+    X = np.zeros((m, n))
+    aa, bb = np.mgrid[0:m, 0:n].astype(np.float64)
+    for _ in range(count):
+        a0, b0 = g.uniform(0, m), g.uniform(0, n)
+        s = g.uniform(*sigma)
+        X = np.maximum(X, g.uniform(0.3, 1.0) * np.exp(-((aa - a0) ** 2 + (bb - b0) ** 2) / (2.0 * s * s)))
+    return X
+
+
 def smooth_edges_image(g, m, n, sigma=32.0, rects=40):
     """Gaussian-filtered white noise scaled to [0, 0.6] plus rectangles of step U[0.2,0.4], clipped."""
     from scipy.ndimage import gaussian_filter
@@ -126,6 +139,33 @@ def gaussian_mixture_psf(g, p):
     return P / P.sum()
 
 
+def defocus_psf(p, radius):
+    """Out-of-focus blur: a uniform disk of the given radius (pixel centres with
+    x^2 + y^2 <= radius^2), normalised to sum 1 (the defocus family of Example 2)."""
+    x, y = _grid(p)
+    P = (x * x + y * y <= radius * radius).astype(np.float64)
+    return P / P.sum()
+
+
+def shake_psf(g, p, steps):
+    """Camera-shake blur: a seeded random walk from the centre (steps of
+    N(0, 1) px in each axis, kept inside the p x p support), its visits
+    accumulated with bilinear weights and normalised to sum 1 (the shake
+    family of Example 2)."""
+    P = np.zeros((p, p))
+    c = (p - 1) / 2.0
+    pos = np.array([c, c])
+    for _ in range(steps):
+        pos = np.clip(pos + g.standard_normal(2), 0.0, p - 1.0)
+        i0, j0 = int(np.floor(pos[0])), int(np.floor(pos[1]))
+        fi, fj = pos[0] - i0, pos[1] - j0
+        for di, wi in ((0, 1.0 - fi), (1, fi)):
+            for dj, wj in ((0, 1.0 - fj), (1, fj)):
+                if i0 + di < p and j0 + dj < p:
+                    P[i0 + di, j0 + dj] += wi * wj
+    return P / P.sum()
+
+
 def random_psf(g, p, q):
     """Dense non-symmetric positive PSF (small test cases)."""
     P = g.uniform(0.05, 1.0, size=(p, q))
@@ -137,11 +177,25 @@ def noise_draw(g, m, n):
     return g.standard_normal((m, n))
 
 
+def laplace_noise_draw(g, m, n):
+    """Laplace draw of unit variance (scale 1/sqrt(2))."""
+    return g.laplace(0.0, 1.0 / np.sqrt(2.0), size=(m, n))
+
+
 def noise_scale(blurred, draw, level):
     """Scale a noise draw so that ||noise|| / ||blurred|| = level (NoiseLevel of Sec. 4)."""
     nb = float(np.linalg.norm(blurred))
     nd = float(np.linalg.norm(draw))
     return draw * (level * nb / nd)
+
+
+def noise_of_kind(kind, blurred, draw, level):
+    """Noise e with ||e|| / ||blurred|| = level: 'gauss' and 'laplace' add the
+    scaled draw; 'multiplicative' scales it by the blurred image first
+    (e proportional to blurred * draw, zero where the signal is zero)."""
+    if kind == "multiplicative":
+        return noise_scale(blurred, blurred * draw, level)
+    return noise_scale(blurred, draw, level)
 
 
 # ---------------------------------------------------------------- configs
@@ -211,3 +265,39 @@ def config5(seed=SEED_BASE + 2, n=512):
     pr.iters = 50
     pr.extra["ckpt_every"] = 10
     return pr
+
+
+EX2_LEVELS = ("mild", "medium", "severe")
+EX2_NOISES = ("gauss", "laplace", "multiplicative")
+
+
+def example2_cases(seed=SEED_BASE + 6, n=256, r=5, iters=50, level=0.01, lam=0.005):
+    """Example 2 stand-in: two blur families (defocus disk, camera shake) at
+    three blur levels, each with three noise types, on images cycling through
+    the geometric, dots and smooth stand-ins; reflective boundary, r terms,
+    50 iterations (the paper's fixed count).  18 problems; the noise type is
+    in extra['noise'] and the noise draw matches it (Laplace draw for
+    'laplace', standard normal otherwise)."""
+    g = rng(seed)
+    radii = {"mild": 2.0, "medium": 4.0, "severe": 7.0}
+    shake = {"mild": (9, 12), "medium": (15, 30), "severe": (21, 60)}
+    out = []
+    k = 0
+    for fam in ("defocus", "shake"):
+        for lev in EX2_LEVELS:
+            if fam == "defocus":
+                R = radii[lev]
+                P = defocus_psf(2 * int(np.ceil(R)) + 3, R)
+            else:
+                p, steps = shake[lev]
+                P = shake_psf(g, p, steps)
+            for noise in EX2_NOISES:
+                kind = k % 3
+                x = (shapes_image(g, n, n), dots_image(g, n, n), smooth_edges_image(g, n, n, sigma=n / 16.0,
+                                                                                   rects=8))[kind]
+                draw = laplace_noise_draw(g, n, n) if noise == "laplace" else noise_draw(g, n, n)
+                pr = Problem("ex2_%s_%s_%s" % (fam, lev, noise), x, P, 1, min(r, *P.shape), lam, level, iters,
+                             draw, {"noise": noise, "family": fam, "level": lev})
+                out.append(pr)
+                k += 1
+    return out
