@@ -165,8 +165,26 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def oracle_reference(pr, b32, iters, L):
-    """FP64 oracle solve on the host cores; returns (X, seconds, threads)."""
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or None."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def oracle_reference(pr, b32, iters, L, single_thread_iters=10):
+    """FP64 oracle solve on the host cores; returns (X, seconds, threads, one-thread s/iteration)."""
     import oracle
     from oracle import kron, _native
     cr, cc = pr.centre
@@ -174,7 +192,15 @@ def oracle_reference(pr, b32, iters, L):
     t0 = time.perf_counter()
     X = oracle.sfista(b32.astype(np.float64), ka, L, pr.lam, iters)
     dt = time.perf_counter() - t0
-    return X, dt, _native.threads()
+    nthreads = _native.threads()
+    one = None
+    if single_thread_iters > 0:
+        _native.set_threads(1)
+        t0 = time.perf_counter()
+        oracle.sfista(b32.astype(np.float64), ka, L, pr.lam, single_thread_iters)
+        one = (time.perf_counter() - t0) / single_thread_iters
+        _native.set_threads(nthreads)
+    return X, dt, nthreads, one
 
 
 def run_reference(args):
@@ -636,7 +662,7 @@ def main():
         return
 
     # CPU baseline: the FP64 oracle on the same b and L (also the parity reference).
-    Xref, cpu_s, cores = oracle_reference(pr, b_host, iters, L)
+    Xref, cpu_s, cores, one_s = oracle_reference(pr, b_host, iters, L)
     r = pr.r
     lines = {}
     for key, res in results.items():
@@ -702,7 +728,9 @@ def main():
                      "duration_us": L0["dur_us"], "peak_source": L0["peak_src"]},
         "stage_ms": dict(zip(STAGES, L0["stage_ms"])),
         "cpu_baseline": {"value": iters / cpu_s, "unit": "iters/s", "cores": cores, "kind": "oracle",
-                         "sample": "one full 200-iteration FP64 solve of the same problem"},
+                         "sample": "one full 200-iteration FP64 solve of the same problem",
+                         "single_thread_iters_per_s": 1.0 / one_s if one_s else None,
+                         "cpu_model": cpu_model()},
         "e2e": {"value": L0["e2e"], "unit": "iters/s", "h2d_bytes_per_step": 4 * n * n,
                 "d2h_bytes_per_step": 4 * n * n},
         "gpu_launches": L0["launches"] * args.steps,

@@ -58,8 +58,15 @@ def threads():
         return os.cpu_count() or 1
 
 
+def set_threads(n):
+    """OpenMP threads of the following oracle calls (timing only); returns the count in effect."""
+    return int(lib().orc_set_threads(int(n)))
+
+
 def _declare(L):
     i, d, vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+    L.orc_set_threads.argtypes = [i]
+    L.orc_set_threads.restype = i
     L.orc_blur.argtypes = [_D, i, i, _D, i, i, i, i, i, _D]
     L.orc_blur_T.argtypes = [_D, i, i, _D, i, i, i, i, i, _D]
     L.orc_kron_apply.argtypes = [_D, i, i, i, _D, i, i, _D, i, i, i, _D]

@@ -30,6 +30,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* Extended-image index map for one axis of length len.  Returns the source
  * index in [0,len) or -1 when the extended pixel is zero (zero boundary or
@@ -358,4 +361,17 @@ void orc_fista_dense(const double *A, const double *b, int N, double L,
     free(xp);
     free(y);
     free(r);
+}
+
+/* Number of OpenMP threads for the following calls (n <= 0: leave unchanged);
+ * returns the number in effect (1 without OpenMP).  For timing only. */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
