@@ -421,40 +421,55 @@ __global__ void __launch_bounds__(320, 1)
                 const int n0 = nt * BN + h * HB;
                 const int c = 2 * lane;   // HB == 64: one column pair per lane
                 const int col = n0 + c;
+                // Each warp owns rows ew, ew + 8, ..., ew + 120 of the half and
+                // handles them eight at a time, every global load of a batch
+                // issued before its first use (one memory latency per batch,
+                // not per row).
                 if (EPI == GE_PROX) {
                     if (col < ga->N) {   // N is even (a multiple of 8)
 #pragma unroll 1
-                        for (int rl = ew; rl < BM; rl += 32) {
-                            size_t idx[4];
-                            float g0[4], g1v[4];
-                            bool okr[4];
+                        for (int rl = ew; rl < BM; rl += 64) {
+                            size_t idx[8];
+                            float g0[8], g1v[8];
+                            bool okr[8];
 #pragma unroll
-                            for (int q = 0; q < 4; ++q) {
+                            for (int q = 0; q < 8; ++q) {
                                 const int rr = rl + 8 * q, row = m0 + rr;
                                 okr[q] = rr < BM && row < ga->rows;
                                 idx[q] = (size_t)row * ga->N + col;
                                 g0[q] = okr[q] ? tile[rr * TS + c] : 0.0f;
                                 g1v[q] = okr[q] ? tile[rr * TS + c + 1] : 0.0f;
                             }
-                            prox_momentum2_n<4>(pa, idx, g0, g1v, okr);
+                            prox_momentum2_n<8>(pa, idx, g0, g1v, okr);
                         }
                     }
                 } else if (col < ga->N) {
                     const int rows = ga->rows, N = ga->N, sk = ga->split_kind;
                     void *ohi = ga->out_hi, *olo = ga->out_lo;
 #pragma unroll 1
-                    for (int rl = ew; rl < BM; rl += 8) {
-                        const int row = m0 + rl;
-                        if (row >= rows) break;
-                        const float a0 = tile[rl * TS + c], a1 = tile[rl * TS + c + 1];
-                        if (EPI == GE_SPLIT) {
-                            store_split2(ohi, olo, sk, ((size_t)term * rows + row) * N + col, a0, a1);
-                        } else if (EPI == GE_RESID) {
-                            const size_t idx = (size_t)row * N + col;
-                            const float2 bb = *reinterpret_cast<const float2 *>(ga->Bd + idx);
-                            store_split2(ohi, olo, sk, idx, a0 - bb.x, a1 - bb.y);
-                        } else {
-                            *reinterpret_cast<float2 *>(ga->out_f32 + (size_t)row * N + col) = make_float2(a0, a1);
+                    for (int rl0 = ew; rl0 < BM; rl0 += 64) {
+                        float2 bb[8];
+                        if (EPI == GE_RESID) {
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) {
+                                const int rl = rl0 + 8 * q, row = m0 + rl;
+                                bb[q] = rl < BM && row < rows
+                                            ? __ldg(reinterpret_cast<const float2 *>(ga->Bd + (size_t)row * N + col))
+                                            : make_float2(0.f, 0.f);
+                            }
+                        }
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const int rl = rl0 + 8 * q, row = m0 + rl;
+                            if (rl >= BM || row >= rows) break;
+                            const float a0 = tile[rl * TS + c], a1 = tile[rl * TS + c + 1];
+                            if (EPI == GE_SPLIT) {
+                                store_split2(ohi, olo, sk, ((size_t)term * rows + row) * N + col, a0, a1);
+                            } else if (EPI == GE_RESID) {
+                                store_split2(ohi, olo, sk, (size_t)row * N + col, a0 - bb[q].x, a1 - bb[q].y);
+                            } else {
+                                *reinterpret_cast<float2 *>(ga->out_f32 + (size_t)row * N + col) = make_float2(a0, a1);
+                            }
                         }
                     }
                 }
