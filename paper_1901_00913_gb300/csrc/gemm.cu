@@ -120,6 +120,25 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y), "r"(z)
         : "memory");
 }
+// Tensor store of one box from shared memory (bulk-group completion).
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, uint32_t src, int x, int y, int z) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                     (uint64_t)map),
+                 "r"(src), "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// The committed stores have finished reading shared memory (the buffer may be rewritten).
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// The committed stores are complete.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// Generic-proxy shared-memory writes become visible to the async proxy (TMA).
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
@@ -229,6 +248,7 @@ template <int FMT, bool SPLIT, int BN, int EPI, bool GROUPED>
 __global__ void __launch_bounds__(320, 1)
     umma_gemm_persistent(const __grid_constant__ CUtensorMap tPhi, const __grid_constant__ CUtensorMap tPlo,
                          const __grid_constant__ CUtensorMap tQhi, const __grid_constant__ CUtensorMap tQlo,
+                         const __grid_constant__ CUtensorMap tOhi, const __grid_constant__ CUtensorMap tOlo,
                          const __grid_constant__ GemmArgs g1, int ntn, int ntiles, const CUtensorMap *maps,
                          const GemmArgs *args, const WorkItem *work, int kswap) {
     using C = Cfg<FMT, SPLIT, BN>;
@@ -276,7 +296,7 @@ __global__ void __launch_bounds__(320, 1)
     auto fetch = [&](int t, const CUtensorMap *&m4, const GemmArgs *&ga, int &mt, int &nt) {
         if (GROUPED) {
             const WorkItem w = work[t];
-            m4 = maps + 4 * w.prob;
+            m4 = maps + 6 * w.prob;
             ga = args + w.prob;
             mt = w.mt;
             nt = w.nt;
@@ -405,6 +425,74 @@ __global__ void __launch_bounds__(320, 1)
             }
 #pragma unroll 1
             for (int h = 0; h < 2; ++h) {
+                if constexpr (FMT == FMT_BF16 && (EPI == GE_SPLIT || EPI == GE_RESID)) {
+                    // Split outputs: each warp converts its 32 x 32 block to
+                    // BF16 hi/lo straight from TMEM into two 128B-swizzled boxes
+                    // (the next stage's operand layout), and one thread stores
+                    // them with TMA, asynchronously.
+                    uint8_t *box_hi = reinterpret_cast<uint8_t *>(tile), *box_lo = box_hi + BM * 128;
+                    if (ew == 0 && lane == 0) bulk_wait_read();   // the previous boxes have been read out
+                    asm volatile("bar.sync 1, 256;" ::: "memory");
+                    float v[32];
+                    tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * BN + h * HB + sub * 32), v);
+                    const int R = lg * 32 + lane;   // tile row of this lane
+                    if (!ok || total == 0) {
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) v[q] = 0.0f;
+                    } else if (EPI == GE_RESID) {
+                        const int row = m0 + R, col0 = nt * BN + h * HB + sub * 32;
+                        if (row < ga->rows) {
+                            const float *bp = ga->Bd + (size_t)row * ga->N + col0;
+#pragma unroll
+                            for (int g8 = 0; g8 < 4; ++g8) {
+                                if (col0 + 8 * g8 < ga->N) {   // N is a multiple of 8
+                                    const float4 x0 = __ldg(reinterpret_cast<const float4 *>(bp + 8 * g8));
+                                    const float4 x1 = __ldg(reinterpret_cast<const float4 *>(bp + 8 * g8 + 4));
+                                    v[8 * g8 + 0] -= x0.x;
+                                    v[8 * g8 + 1] -= x0.y;
+                                    v[8 * g8 + 2] -= x0.z;
+                                    v[8 * g8 + 3] -= x0.w;
+                                    v[8 * g8 + 4] -= x1.x;
+                                    v[8 * g8 + 5] -= x1.y;
+                                    v[8 * g8 + 6] -= x1.z;
+                                    v[8 * g8 + 7] -= x1.w;
+                                }
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int c8 = 0; c8 < 4; ++c8) {
+                        uint32_t hw[4], lw[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float a0 = v[8 * c8 + 2 * e], a1 = v[8 * c8 + 2 * e + 1];
+                            const __nv_bfloat162 hh = __floats2bfloat162_rn(a0, a1);
+                            hw[e] = *reinterpret_cast<const uint32_t *>(&hh);
+                            lw[e] = pack_bf16x2(a0 - __bfloat162float(hh.x), a1 - __bfloat162float(hh.y));
+                        }
+                        const int pos = ((sub * 4 + c8) ^ (R & 7)) * 16;
+                        *reinterpret_cast<uint4 *>(box_hi + R * 128 + pos) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        if (SPLIT)
+                            *reinterpret_cast<uint4 *>(box_lo + R * 128 + pos) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    }
+                    if (h == 1) {
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(tempty0 + 8 * b);
+                    }
+                    fence_async_smem();
+                    asm volatile("bar.sync 1, 256;" ::: "memory");
+                    if (ew == 0 && lane == 0) {
+                        const CUtensorMap *oh = GROUPED ? m4 + 4 : &tOhi, *ol = GROUPED ? m4 + 5 : &tOlo;
+                        const int x = nt * BN + h * HB;
+                        if (x < ga->N) {   // boxes reaching past N or the last row are clipped by the unit
+                            tma_store_3d(oh, smem_u32(box_hi), x, m0, term);
+                            if (SPLIT) tma_store_3d(ol, smem_u32(box_lo), x, m0, term);
+                        }
+                        bulk_commit();
+                    }
+                    continue;
+                }
                 {
                     float v[32];
                     tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * BN + h * HB + sub * 32), v);
@@ -477,6 +565,8 @@ __global__ void __launch_bounds__(320, 1)
             }
             if (ep_abort) break;                                  // uniform across the epilogue warps
         }
+        if (FMT == FMT_BF16 && (EPI == GE_SPLIT || EPI == GE_RESID) && ew == 0 && lane == 0)
+            bulk_wait_all();   // the tensor stores are complete before the CTA exits
     }
     tc_fence_before();
     __syncthreads();
@@ -576,25 +666,28 @@ cudaError_t set_attrs() {
 }
 
 // One persistent launch over the gx * gy tiles of a stage (one CTA per SM).
+// O: the output operand (its tensor maps serve the epilogue's tensor stores), or
+// NULL for the stages that write plain FP32 or the FISTA state.
 template <int FMT, bool SPLIT, int EPI>
-sfista_status launch_one(const Operand &P, const Operand &Q, const GemmArgs &a, int grid_x, int grid_y, int sms,
-                         cudaStream_t s) {
+sfista_status launch_one(const Operand &P, const Operand &Q, const Operand *O, const GemmArgs &a, int grid_x,
+                         int grid_y, int sms, cudaStream_t s) {
     const int ntiles = grid_x * grid_y;
     const int grid = ntiles < sms ? ntiles : sms;
+    const Operand &Ou = O ? *O : P;
     umma_gemm_persistent<FMT, SPLIT, BN_TILE, EPI, false><<<grid, 320, PCfg<FMT, SPLIT, BN_TILE>::SMEM, s>>>(
-        P.map_hi, SPLIT ? P.map_lo : P.map_hi, Q.map_hi, SPLIT ? Q.map_lo : Q.map_hi, a, grid_x, ntiles, nullptr,
-        nullptr, nullptr, 0);
+        P.map_hi, SPLIT ? P.map_lo : P.map_hi, Q.map_hi, SPLIT ? Q.map_lo : Q.map_hi, Ou.map_hi,
+        SPLIT ? Ou.map_lo : Ou.map_hi, a, grid_x, ntiles, nullptr, nullptr, nullptr, 0);
     return SFISTA_OK;
 }
 
 template <int EPI>
-sfista_status dispatch(const GemmPath *g, const Operand &P, const Operand &Q, const GemmArgs &a, int gx, int gy,
-                       cudaStream_t s) {
+sfista_status dispatch(const GemmPath *g, const Operand &P, const Operand &Q, const Operand *O, const GemmArgs &a,
+                       int gx, int gy, cudaStream_t s) {
     if (g->fmt == FMT_BF16)
-        return g->split ? launch_one<FMT_BF16, true, EPI>(P, Q, a, gx, gy, g->sms, s)
-                        : launch_one<FMT_BF16, false, EPI>(P, Q, a, gx, gy, g->sms, s);
-    return g->split ? launch_one<FMT_TF32, true, EPI>(P, Q, a, gx, gy, g->sms, s)
-                    : launch_one<FMT_TF32, false, EPI>(P, Q, a, gx, gy, g->sms, s);
+        return g->split ? launch_one<FMT_BF16, true, EPI>(P, Q, O, a, gx, gy, g->sms, s)
+                        : launch_one<FMT_BF16, false, EPI>(P, Q, O, a, gx, gy, g->sms, s);
+    return g->split ? launch_one<FMT_TF32, true, EPI>(P, Q, O, a, gx, gy, g->sms, s)
+                    : launch_one<FMT_TF32, false, EPI>(P, Q, O, a, gx, gy, g->sms, s);
 }
 
 GemmArgs base_args(const GemmPath *g) {
@@ -641,15 +734,15 @@ sfista_status run_stacked(const GemmPath *g, const Operand &P, const Band &band,
                           cudaStream_t s) {
     int gx, gy;
     GemmArgs a = stacked_args(g, band, Out, &gx, &gy);
-    return dispatch<GE_SPLIT>(g, P, Q, a, gx, gy, s);
+    return dispatch<GE_SPLIT>(g, P, Q, &Out, a, gx, gy, s);
 }
 
 template <int EPI>
-sfista_status run_summed(const GemmPath *g, const Operand &P, const Band &band, const Operand &Q, GemmArgs a,
-                         cudaStream_t s) {
+sfista_status run_summed(const GemmPath *g, const Operand &P, const Band &band, const Operand &Q, const Operand *O,
+                         GemmArgs a, cudaStream_t s) {
     int gx, gy;
     summed_args(g, band, &a, &gx, &gy);
-    return dispatch<EPI>(g, P, Q, a, gx, gy, s);
+    return dispatch<EPI>(g, P, Q, O, a, gx, gy, s);
 }
 
 cudaError_t alloc_operand(Operand *o, size_t elems, size_t es, bool split) {
@@ -782,7 +875,7 @@ void gemm_stage(GemmPath *g, int st, const ProxArgs &pa_in, cudaStream_t s) {
             a.Bd = g->Bd;
             a.out_hi = g->QR.hi;
             a.out_lo = g->QR.lo;
-            run_summed<GE_RESID>(g, g->PB, g->bandB, g->QT, a, s);
+            run_summed<GE_RESID>(g, g->PB, g->bandB, g->QT, &g->QR, a, s);
             break;
         }
         case 2:
@@ -796,7 +889,7 @@ void gemm_stage(GemmPath *g, int st, const ProxArgs &pa_in, cudaStream_t s) {
             a.pa.Ylo = g->split ? g->QY.lo : nullptr;
             a.pa.split_kind = g->split_kind;
             a.status = pa_in.status;
-            run_summed<GE_PROX>(g, g->PBT, g->bandBT, g->QU, a, s);
+            run_summed<GE_PROX>(g, g->PBT, g->bandBT, g->QU, nullptr, a, s);
             break;
         }
     }
@@ -807,7 +900,7 @@ struct GemmBatch {
     int nprob = 0, fmt = FMT_BF16, sms = 1;
     bool split = true;
     std::vector<GemmPath *> paths;
-    CUtensorMap *d_maps[4] = {nullptr, nullptr, nullptr, nullptr};   // per stage: nprob x 4
+    CUtensorMap *d_maps[4] = {nullptr, nullptr, nullptr, nullptr};   // per stage: nprob x 6 (P, Q, output)
     GemmArgs *d_args[4] = {nullptr, nullptr, nullptr, nullptr};
     std::vector<GemmArgs> h_args[4];
     WorkItem *d_work[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -848,7 +941,7 @@ sfista_status gemm_batch_create(GemmBatch **out, GemmPath *const *paths, int npr
     });
     cudaError_t e = cudaSuccess;
     for (int st = 0; st < 4 && !e; ++st) {
-        std::vector<CUtensorMap> maps(4 * (size_t)nprob);
+        std::vector<CUtensorMap> maps(6 * (size_t)nprob);
         std::vector<WorkItem> work;
         b->h_args[st].resize(nprob);
         for (int p = 0; p < nprob; ++p) {
@@ -878,10 +971,13 @@ sfista_status gemm_batch_create(GemmBatch **out, GemmPath *const *paths, int npr
                 Q = &g->QU;
             }
             b->h_args[st][p] = a;
-            maps[4 * p + 0] = P->map_hi;
-            maps[4 * p + 1] = b->split ? P->map_lo : P->map_hi;
-            maps[4 * p + 2] = Q->map_hi;
-            maps[4 * p + 3] = b->split ? Q->map_lo : Q->map_hi;
+            const Operand *O = st == 0 ? &g->QT : st == 1 ? &g->QR : st == 2 ? &g->QU : P;
+            maps[6 * p + 0] = P->map_hi;
+            maps[6 * p + 1] = b->split ? P->map_lo : P->map_hi;
+            maps[6 * p + 2] = Q->map_hi;
+            maps[6 * p + 3] = b->split ? Q->map_lo : Q->map_hi;
+            maps[6 * p + 4] = O->map_hi;
+            maps[6 * p + 5] = b->split ? O->map_lo : O->map_hi;
         }
         for (int p : order) {
             GemmPath *g = paths[p];
@@ -946,7 +1042,8 @@ void launch_grouped(const GemmBatch *b, int st, int k, cudaStream_t s) {
     // The parameter-space maps are unused in grouped mode: pass the first problem's.
     const Operand &P0 = b->paths[0]->PA;
     umma_gemm_persistent<FMT, SPLIT, BN_TILE, EPI, true><<<grid, 320, PCfg<FMT, SPLIT, BN_TILE>::SMEM, s>>>(
-        P0.map_hi, P0.map_hi, P0.map_hi, P0.map_hi, b->h_args[st][0], 1, b->nwork[st], b->d_maps[st], b->d_args[st],
+        P0.map_hi, P0.map_hi, P0.map_hi, P0.map_hi, P0.map_hi, P0.map_hi, b->h_args[st][0], 1, b->nwork[st],
+        b->d_maps[st], b->d_args[st],
         b->d_work[st], k);
 }
 template <int FMT, bool SPLIT>
@@ -973,10 +1070,10 @@ sfista_status gemm_apply(GemmPath *g, const float *x, float *y, int transpose, c
     sfista_status st;
     if (!transpose) {
         if ((st = run_stacked(g, g->PA, g->bandA, g->QY, g->QT, s))) return st;
-        st = run_summed<GE_STORE>(g, g->PB, g->bandB, g->QT, a, s);
+        st = run_summed<GE_STORE>(g, g->PB, g->bandB, g->QT, nullptr, a, s);
     } else {
         if ((st = run_stacked(g, g->PAT, g->bandAT, g->QR, g->QU, s))) return st;
-        st = run_summed<GE_STORE>(g, g->PBT, g->bandBT, g->QU, a, s);
+        st = run_summed<GE_STORE>(g, g->PBT, g->bandBT, g->QU, nullptr, a, s);
     }
     if (st) return st;
     cudaError_t e = cudaGetLastError();
