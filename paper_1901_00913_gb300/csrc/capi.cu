@@ -379,7 +379,8 @@ sfista_status band_batch_plan(sfista_batch *b, size_t budget) {
             while (cq < c->r && band_smem_f32(false, wmax, cq + 1) <= budget) ++cq;
         }
         size_t sm = 0;
-        grouped_chunks(c->r, wmax, rq, cq, &P.rows_chunk, &P.cols_chunk, &sm);
+        P.vec = c->m % 4 == 0 && c->n % 4 == 0;   // the buffers are cudaMalloc'ed (aligned)
+        grouped_chunks(c->r, wmax, P.vec, rq, cq, &P.rows_chunk, &P.cols_chunk, &sm);
         b->smem = std::max(b->smem, sm);
     }
     std::vector<BandItem> items[4];
@@ -387,8 +388,8 @@ sfista_status band_batch_plan(sfista_batch *b, size_t budget) {
         const BandProb &P = b->h_probs[p];
         const int nq = (P.r + P.rows_chunk - 1) / P.rows_chunk;
         for (int q = 0; q < nq; ++q)
-            for (int t = 0; t < band_rows_tiles(P.m, P.n); ++t) items[0].push_back(BandItem{p, q, t, 0});
-        for (int t = 0; t < band_cols_tiles(P.m, P.n); ++t) items[1].push_back(BandItem{p, 0, t, 0});
+            for (int t = 0; t < band_rows_tiles(P.m, P.n, P.vec); ++t) items[0].push_back(BandItem{p, q, t, 0});
+        for (int t = 0; t < band_cols_tiles(P.m, P.n, P.vec); ++t) items[1].push_back(BandItem{p, 0, t, 0});
     }
     items[2] = items[0];
     items[3] = items[1];

@@ -112,6 +112,7 @@ cudaError_t launch_persistent(int grid, size_t smem, int rows_chunk, int cols_ch
 // tiles of many problems of any size, rank and band.
 struct BandProb {
     int m, n, r, rows_chunk, cols_chunk;
+    int vec;       // 1: the 16-byte FP32 routines with 64-row tiles (m, n multiples of 4), 0: 32-row scalar ones
     const float *fA, *fB, *fAT, *fBT;
     int loA, wA, loB, wB, loAT, wAT, loBT, wBT;
     float *Z, *R;
@@ -123,12 +124,13 @@ struct BandItem {
 void persistent_chunks(int r, int wmax, int *rows_chunk, int *cols_chunk, size_t *smem);
 // Term chunks of the grouped batch kernels: the requested ones (> 0, e.g.
 // from the autotuner) when they fit, else the persistent solver's rule.
-void grouped_chunks(int r, int wmax, int rows_req, int cols_req, int *rows_chunk, int *cols_chunk, size_t *smem);
+void grouped_chunks(int r, int wmax, bool vec, int rows_req, int cols_req, int *rows_chunk, int *cols_chunk,
+                    size_t *smem);
 cudaError_t band_grouped_prepare(size_t smem);
 void launch_band_grouped_stage(int st, const BandProb *probs, const BandItem *items, int nitems, int k, size_t smem,
                                cudaStream_t s);
-int band_rows_tiles(int m, int n);
-int band_cols_tiles(int m, int n);
+int band_rows_tiles(int m, int n, bool vec);
+int band_cols_tiles(int m, int n, bool vec);
 
 // One kernel per banded operator application (kernels_fused.cu).
 size_t band_op_fused_smem(int r, int wF, int wG);

@@ -14,7 +14,10 @@
 // momentum for the adjoint, with the FISTA state as double-float pairs.
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "band_items.cuh"
+#include "band_items4.cuh"
 #include "epilogue.cuh"
 #include "internal.h"
 
@@ -43,21 +46,63 @@ __global__ void __launch_bounds__(band::NT) band_cols_kernel(const T *__restrict
                                    pa, sm);
 }
 
+// FP32 kernels with 16-byte accesses, one RT x 32 tile per block.
+template <int RT>
+__global__ void __launch_bounds__(band::NT) band_rows_kernel4(const float *__restrict__ In, int m, int n,
+                                                             const float *__restrict__ Fb, int lo, int w, int r,
+                                                             int chunk, float *__restrict__ Z) {
+    extern __shared__ __align__(16) float sm4[];
+    const int t0 = blockIdx.z * chunk;
+    band4::rows_item<RT>(In, m, n, Fb, lo, w, t0, min(chunk, r - t0), blockIdx.y * RT, blockIdx.x * band::TC, Z,
+                         sm4);
+}
+
+template <int EPI, int RT>
+__global__ void __launch_bounds__(band::NT) band_cols_kernel4(const float *__restrict__ Z, int m, int n,
+                                                             const float *__restrict__ Gb, int lo, int w, int r,
+                                                             int chunk, float *__restrict__ Out, ProxArgs pa) {
+    extern __shared__ __align__(16) float sm4[];
+    band4::cols_item<EPI, RT>(Z, m, n, r, chunk, Gb, lo, w, blockIdx.y * RT, blockIdx.x * band::TC, Out, pa, sm4);
+}
+
 constexpr size_t kBandSmemBudget = 96 * 1024;
 constexpr size_t kBandSmemMax = 227 * 1024;
 
+// Shared memory of a rows (cols) block with `chunk` terms: the 16-byte FP32
+// layout with rt-row tiles (rt = 32 or 64), or the scalar one (rt = 0).
+template <typename T>
+size_t rows_bytes(int rt, int w, int chunk) {
+    return rt ? band4::rows_smem(rt, w, chunk) : band::rows_smem<T>(w, chunk);
+}
+template <typename T>
+size_t cols_bytes(int rt, int w, int chunk) {
+    return rt ? band4::cols_smem(rt, w, chunk) : band::cols_smem<T>(w, chunk);
+}
+
 // Terms staged per load phase so that a block stays within the budget.
 template <typename T>
-int rows_chunk(int r, int w) {
-    const size_t fixed = band::rows_smem<T>(w, 0), per = band::rows_smem<T>(w, 1) - fixed;
+int rows_chunk(int rt, int r, int w) {
+    const size_t fixed = rows_bytes<T>(rt, w, 0), per = rows_bytes<T>(rt, w, 1) - fixed;
     int c = fixed < kBandSmemBudget ? (int)((kBandSmemBudget - fixed) / per) : 1;
     return c < 1 ? 1 : (c > r ? r : c);
 }
 template <typename T>
-int cols_chunk(int r, int w) {
-    int c = (int)(kBandSmemBudget / band::cols_smem<T>(w, 1));
+int cols_chunk(int rt, int r, int w) {
+    int c = (int)(kBandSmemBudget / cols_bytes<T>(rt, w, 1));
     return c < 1 ? 1 : (c > r ? r : c);
 }
+
+int sm_count() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
+    }
+    return sms;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
 }  // namespace
 
@@ -79,21 +124,55 @@ void launch_pdl(void (*kern)(KArgs...), dim3 grid, size_t smem, cudaStream_t s, 
     cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
+// The 16-byte FP32 path runs when m and n are multiples of 4 and every buffer
+// is 16-byte aligned; its tiles are 64 rows high when that still gives at
+// least two tiles per SM, else 32.  Returns 0 for the scalar path.
+template <typename T>
+int vec_rows(int m, int n, const void *a, const void *b, const void *c) {
+    if (!(std::is_same<T, float>::value && m % 4 == 0 && n % 4 == 0 && aligned16(a) && aligned16(b) && aligned16(c)))
+        return 0;
+    return band4::tiles(64, m, n) >= 2 * sm_count() ? 64 : 32;
+}
+
 template <typename T>
 void launch_band_rows(const T *In, int m, int n, const T *Fb, int lo, int w, int r, T *Z, cudaStream_t s, int req) {
-    int chunk = req > 0 ? std::min(req, r) : rows_chunk<T>(r, w);
-    if (band::rows_smem<T>(w, chunk) > kBandSmemMax) chunk = rows_chunk<T>(r, w);
-    dim3 grid((n + band::TC - 1) / band::TC, (m + band::TA - 1) / band::TA, (r + chunk - 1) / chunk);
-    launch_pdl(band_rows_kernel<T>, grid, band::rows_smem<T>(w, chunk), s, In, m, n, Fb, lo, w, r, chunk, Z);
+    const int rt = vec_rows<T>(m, n, In, Fb, Z);
+    int chunk = req > 0 ? std::min(req, r) : rows_chunk<T>(rt, r, w);
+    if (rows_bytes<T>(rt, w, chunk) > kBandSmemMax) chunk = rows_chunk<T>(rt, r, w);
+    const int ta = rt ? rt : band::TA;
+    dim3 grid((n + band::TC - 1) / band::TC, (m + ta - 1) / ta, (r + chunk - 1) / chunk);
+    const size_t sm = rows_bytes<T>(rt, w, chunk);
+    if constexpr (std::is_same<T, float>::value) {
+        if (rt == 64) return launch_pdl(band_rows_kernel4<64>, grid, sm, s, In, m, n, Fb, lo, w, r, chunk, Z);
+        if (rt == 32) return launch_pdl(band_rows_kernel4<32>, grid, sm, s, In, m, n, Fb, lo, w, r, chunk, Z);
+    }
+    launch_pdl(band_rows_kernel<T>, grid, sm, s, In, m, n, Fb, lo, w, r, chunk, Z);
+}
+
+template <int RT>
+void launch_cols4(dim3 grid, size_t sm, cudaStream_t s, const float *Z, int m, int n, const float *Gb, int lo, int w,
+                  int r, int chunk, EpiKind epi, float *Out, const ProxArgs &pa) {
+    if (epi == EPI_STORE)
+        launch_pdl(band_cols_kernel4<EPI_STORE, RT>, grid, sm, s, Z, m, n, Gb, lo, w, r, chunk, Out, pa);
+    else if (epi == EPI_RESIDUAL)
+        launch_pdl(band_cols_kernel4<EPI_RESIDUAL, RT>, grid, sm, s, Z, m, n, Gb, lo, w, r, chunk, Out, pa);
+    else
+        launch_pdl(band_cols_kernel4<EPI_PROX, RT>, grid, sm, s, Z, m, n, Gb, lo, w, r, chunk, Out, pa);
 }
 
 template <typename T>
 void launch_band_cols(const T *Z, int m, int n, const T *Gb, int lo, int w, int r, EpiKind epi, T *Out,
                       const ProxArgs &pa, cudaStream_t s, int req) {
-    int chunk = req > 0 ? std::min(req, r) : cols_chunk<T>(r, w);
-    if (band::cols_smem<T>(w, chunk) > kBandSmemMax) chunk = cols_chunk<T>(r, w);
-    dim3 grid((n + band::TC - 1) / band::TC, (m + band::TA - 1) / band::TA);
-    const size_t sm = band::cols_smem<T>(w, chunk);
+    const int rt = vec_rows<T>(m, n, Z, Gb, Z);
+    int chunk = req > 0 ? std::min(req, r) : cols_chunk<T>(rt, r, w);
+    if (cols_bytes<T>(rt, w, chunk) > kBandSmemMax) chunk = cols_chunk<T>(rt, r, w);
+    const int ta = rt ? rt : band::TA;
+    dim3 grid((n + band::TC - 1) / band::TC, (m + ta - 1) / ta);
+    const size_t sm = cols_bytes<T>(rt, w, chunk);
+    if constexpr (std::is_same<T, float>::value) {
+        if (rt == 64) return launch_cols4<64>(grid, sm, s, Z, m, n, Gb, lo, w, r, chunk, epi, Out, pa);
+        if (rt == 32) return launch_cols4<32>(grid, sm, s, Z, m, n, Gb, lo, w, r, chunk, epi, Out, pa);
+    }
     if (epi == EPI_STORE)
         launch_pdl(band_cols_kernel<T, EPI_STORE>, grid, sm, s, Z, m, n, Gb, lo, w, r, chunk, Out, pa);
     else if (epi == EPI_RESIDUAL)
@@ -102,18 +181,20 @@ void launch_band_cols(const T *Z, int m, int n, const T *Gb, int lo, int w, int 
         launch_pdl(band_cols_kernel<T, EPI_PROX>, grid, sm, s, Z, m, n, Gb, lo, w, r, chunk, Out, pa);
 }
 
-size_t band_smem_f32(bool rows, int w, int chunk) {
-    return rows ? band::rows_smem<float>(w, chunk) : band::cols_smem<float>(w, chunk);
+size_t band_smem_f32(bool rows, int w, int chunk) {   // the largest of the layouts
+    size_t b = 0;
+    for (int rt : {0, 32, 64}) b = std::max(b, rows ? rows_bytes<float>(rt, w, chunk) : cols_bytes<float>(rt, w, chunk));
+    return b;
 }
 
 int band_rows_chunk_limit(int r, int w) {
     int c = r;
-    while (c > 1 && band::rows_smem<float>(w, c) > kBandSmemMax) --c;
+    while (c > 1 && band_smem_f32(true, w, c) > kBandSmemMax) --c;
     return c;
 }
 int band_cols_chunk_limit(int r, int w) {
     int c = r;
-    while (c > 1 && band::cols_smem<float>(w, c) > kBandSmemMax) --c;
+    while (c > 1 && band_smem_f32(false, w, c) > kBandSmemMax) --c;
     return c;
 }
 
@@ -131,6 +212,11 @@ cudaError_t band_set_smem_limits(int w) {
     const int lim = (int)kBandSmemMax;
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(band_rows_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    for (auto k : {band_rows_kernel4<32>, band_rows_kernel4<64>})
+        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    for (auto k : {band_cols_kernel4<EPI_STORE, 32>, band_cols_kernel4<EPI_RESIDUAL, 32>, band_cols_kernel4<EPI_PROX, 32>,
+                   band_cols_kernel4<EPI_STORE, 64>, band_cols_kernel4<EPI_RESIDUAL, 64>, band_cols_kernel4<EPI_PROX, 64>})
+        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
     if ((e = cudaFuncSetAttribute(band_rows_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
     if ((e = cudaFuncSetAttribute(band_cols_kernel<float, EPI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
     if ((e = cudaFuncSetAttribute(band_cols_kernel<float, EPI_RESIDUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;

@@ -18,6 +18,7 @@
 #include <algorithm>
 
 #include "band_items.cuh"
+#include "band_items4.cuh"
 #include "epilogue.cuh"
 #include "internal.h"
 
@@ -139,16 +140,19 @@ void persistent_chunks(int r, int wmax, int *rows_chunk, int *cols_chunk, size_t
     *smem = std::max(rows_fixed + rc * rows_term, cc * cols_term);
 }
 
-void grouped_chunks(int r, int wmax, int rows_req, int cols_req, int *rows_chunk, int *cols_chunk, size_t *smem) {
-    persistent_chunks(r, wmax, rows_chunk, cols_chunk, smem);
-    const int rc = rows_req > 0 ? std::min(rows_req, r) : *rows_chunk;
-    const int cc = cols_req > 0 ? std::min(cols_req, r) : *cols_chunk;
-    const size_t sm = std::max(band::rows_smem<float>(wmax, rc), band::cols_smem<float>(wmax, cc));
-    if (sm <= 227 * 1024) {
-        *rows_chunk = rc;
-        *cols_chunk = cc;
-        *smem = sm;
-    }
+void grouped_chunks(int r, int wmax, bool vec, int rows_req, int cols_req, int *rows_chunk, int *cols_chunk,
+                    size_t *smem) {
+    auto rows_b = [&](int c) { return vec ? band4::rows_smem(64, wmax, c) : band::rows_smem<float>(wmax, c); };
+    auto cols_b = [&](int c) { return vec ? band4::cols_smem(64, wmax, c) : band::cols_smem<float>(wmax, c); };
+    // Default: as many terms as fit in the persistent solver's budget.
+    int rc = 1, cc = 1;
+    while (rc < r && rows_b(rc + 1) <= kPersistSmemBudget) ++rc;
+    while (cc < r && cols_b(cc + 1) <= kPersistSmemBudget) ++cc;
+    if (rows_req > 0 && rows_b(std::min(rows_req, r)) <= 227 * 1024) rc = std::min(rows_req, r);
+    if (cols_req > 0 && cols_b(std::min(cols_req, r)) <= 227 * 1024) cc = std::min(cols_req, r);
+    *rows_chunk = rc;
+    *cols_chunk = cc;
+    *smem = std::max(rows_b(rc), cols_b(cc));
 }
 
 namespace {
@@ -164,9 +168,12 @@ __global__ void __launch_bounds__(PT) band_rows_grouped(const BandProb *probs, c
     const float *F = phase == 0 ? P.fA : P.fAT;
     const int lo = phase == 0 ? P.loA : P.loAT, w = phase == 0 ? P.wA : P.wAT;
     // Separate launches per stage: the input was written by an earlier launch,
-    // so the cp.async (and 16-byte) staging of the plain kernels applies.
-    band::rows_item<float, false>(In, P.m, P.n, F, lo, w, t0, nt, (it.tile / rt_c) * PR_A, (it.tile % rt_c) * PR_C,
-                                  P.Z, sm);
+    // so the cp.async staging of the plain kernels applies.
+    if (P.vec)
+        band4::rows_item<64>(In, P.m, P.n, F, lo, w, t0, nt, (it.tile / rt_c) * 64, (it.tile % rt_c) * PR_C, P.Z, sm);
+    else
+        band::rows_item<float, false>(In, P.m, P.n, F, lo, w, t0, nt, (it.tile / rt_c) * PR_A,
+                                      (it.tile % rt_c) * PR_C, P.Z, sm);
 }
 
 __global__ void __launch_bounds__(PT) band_cols_grouped(const BandProb *probs, const BandItem *items, int phase,
@@ -175,25 +182,37 @@ __global__ void __launch_bounds__(PT) band_cols_grouped(const BandProb *probs, c
     const BandItem it = items[blockIdx.x];
     const BandProb &P = probs[it.prob];
     const int ct_c = (P.n + PC_C - 1) / PC_C;
-    const int a0 = (it.tile / ct_c) * PC_A, c0 = (it.tile % ct_c) * PC_C;
+    const int a0 = (it.tile / ct_c) * (P.vec ? 64 : PC_A), c0 = (it.tile % ct_c) * PC_C;
     ProxArgs pa = P.pa;
     if (phase == 1) {
-        band::cols_item<float, EPI_RESIDUAL, false>(P.Z, P.m, P.n, P.r, P.cols_chunk, P.fB, P.loB, P.wB, a0, c0, P.R,
-                                                    pa, sm);
+        if (P.vec)
+            band4::cols_item<EPI_RESIDUAL, 64>(P.Z, P.m, P.n, P.r, P.cols_chunk, P.fB, P.loB, P.wB, a0, c0, P.R, pa,
+                                               sm);
+        else
+            band::cols_item<float, EPI_RESIDUAL, false>(P.Z, P.m, P.n, P.r, P.cols_chunk, P.fB, P.loB, P.wB, a0, c0,
+                                                        P.R, pa, sm);
     } else {
         float2 *b0 = const_cast<float2 *>(pa.Xin), *b1 = pa.Xout;
         pa.k = k;
         pa.Xin = (k - 1) & 1 ? b1 : b0;
         pa.Xout = k & 1 ? b1 : b0;
-        band::cols_item<float, EPI_PROX, false>(P.Z, P.m, P.n, P.r, P.cols_chunk, P.fBT, P.loBT, P.wBT, a0, c0,
-                                                nullptr, pa, sm);
+        if (P.vec)
+            band4::cols_item<EPI_PROX, 64>(P.Z, P.m, P.n, P.r, P.cols_chunk, P.fBT, P.loBT, P.wBT, a0, c0, nullptr,
+                                           pa, sm);
+        else
+            band::cols_item<float, EPI_PROX, false>(P.Z, P.m, P.n, P.r, P.cols_chunk, P.fBT, P.loBT, P.wBT, a0, c0,
+                                                    nullptr, pa, sm);
     }
 }
 
 }  // namespace
 
-int band_rows_tiles(int m, int n) { return ((m + PR_A - 1) / PR_A) * ((n + PR_C - 1) / PR_C); }
-int band_cols_tiles(int m, int n) { return ((m + PC_A - 1) / PC_A) * ((n + PC_C - 1) / PC_C); }
+int band_rows_tiles(int m, int n, bool vec) {
+    return vec ? band4::tiles(64, m, n) : ((m + PR_A - 1) / PR_A) * ((n + PR_C - 1) / PR_C);
+}
+int band_cols_tiles(int m, int n, bool vec) {
+    return vec ? band4::tiles(64, m, n) : ((m + PC_A - 1) / PC_A) * ((n + PC_C - 1) / PC_C);
+}
 
 cudaError_t band_grouped_prepare(size_t smem) {
     cudaError_t e = cudaFuncSetAttribute(band_rows_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
