@@ -293,6 +293,17 @@ sfista_status sfista_blur(const double *psf, int psf_rows, int psf_cols,
                           float *d_y, void *stream);
 
 /*
+ * sfista_objective -- Phi_s(X) = 1/2 ||A_s X - B||_F^2 + 1/2 lambda^2 ||X||_F^2,
+ * the function Alg. 2 minimises (the matrix model with the Kronecker
+ * approximation A_s of Sec. 2), for monitoring convergence or divergence.
+ * d_b, d_x  device, m x n FP32 (B and X).  phi: host out (FP64 sums of the
+ * FP32 operator result).  Synchronous.  Errors: SFISTA_EINVAL for NULL
+ * pointers or lambda < 0.
+ */
+sfista_status sfista_objective(sfista_ctx *ctx, const float *d_b, const float *d_x, double lambda,
+                               double *phi, void *stream);
+
+/*
  * sfista_time_stages -- per-kernel timing of one iteration of Alg. 2 on the
  * context's own stream, for roofline reporting.  Runs `reps` iterations
  * (k = 1..reps, launched one by one, no graph) on the device observation

@@ -66,6 +66,7 @@ def load(path=None):
     L.sfista_get_factors.argtypes = [vp, vp, vp]
     L.sfista_blur.argtypes = [vp, i, i, i, i, i, vp, i, i, vp, vp]
     L.sfista_time_stages.argtypes = [vp, vp, d, i, vp]
+    L.sfista_objective.argtypes = [vp, vp, vp, d, ctypes.POINTER(ctypes.c_double), vp]
     L.sfista_tune.argtypes = [vp, i, ctypes.POINTER(TuneEntry), i, ctypes.POINTER(ctypes.c_int)]
     L.sfista_batch_tune.argtypes = [vp, i, ctypes.POINTER(TuneEntry), i, ctypes.POINTER(ctypes.c_int)]
     L.sfista_apply_static.argtypes = [vp, vp, i, i, i, vp, i, i, vp, i, i, vp]
@@ -223,6 +224,14 @@ def sfista_time_stages(ctx, d_b, lam, reps):
     ms = np.zeros(4, dtype=np.float32)
     _check(load().sfista_time_stages(ctypes.c_void_p(ctx), _ptr(d_b), float(lam), int(reps), ms.ctypes.data))
     return ms
+
+
+def sfista_objective(ctx, d_b, d_x, lam, stream=None):
+    """Phi_s(X) = 1/2 ||A_s X - B||^2 + 1/2 lam^2 ||X||^2 on the device (see include/sfista.h)."""
+    phi = ctypes.c_double()
+    _check(load().sfista_objective(ctypes.c_void_p(ctx), _ptr(d_b), _ptr(d_x), float(lam), ctypes.byref(phi),
+                                   _stream_ptr(stream)))
+    return phi.value
 
 
 def sfista_tune(ctx, iters=10, max_entries=64):
@@ -424,6 +433,10 @@ class Sfista:
 
     def info(self):
         return sfista_info(self.ctx, min(self.psf_shape))
+
+    def objective(self, d_b, d_x, lam):
+        """Phi_s(X) for device tensors B and X."""
+        return sfista_objective(self.ctx, d_b, d_x, lam)
 
     def tune(self, iters=10):
         """Times the candidate configurations and keeps the fastest; returns the measurements."""

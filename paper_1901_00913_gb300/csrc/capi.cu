@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "trace.h"
 #include "epilogue.cuh"
 
 namespace sfista {
@@ -161,6 +162,7 @@ void sfista::enqueue_iteration(sfista_ctx *c, int k, double lam) {
 namespace {
 
 sfista_status run_loop(sfista_ctx *c, double lam, int k0, int iters) {
+    TraceRange trace_("sfista iterations");
     if (iters <= 0) return SFISTA_OK;
     if (c->op == SFISTA_OP_BANDED_PERSISTENT) {
         const HostSetup &h = c->hs;
@@ -180,6 +182,7 @@ sfista_status run_loop(sfista_ctx *c, double lam, int k0, int iters) {
             c->gexec = nullptr;
         }
         cudaGraph_t graph = nullptr;
+        TraceRange capture_("sfista graph capture");
         SF_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
         for (int k = k0 + 1; k <= k0 + iters; ++k) enqueue_iteration(c, k, lam);
         cudaError_t le = cudaGetLastError();
@@ -205,6 +208,7 @@ sfista_status run_loop(sfista_ctx *c, double lam, int k0, int iters) {
 
 // FP64 power iteration for lambda_max(A_s^T A_s) with the banded kernels.
 sfista_status power_lipschitz(sfista_ctx *c, double tol, int maxit, double *L_out) {
+    TraceRange trace_("sfista lipschitz");
     const HostSetup &h = c->hs;
     size_t N = c->N;
     double *v = nullptr, *u = nullptr, *w = nullptr, *Zd = nullptr, *partial = nullptr, *dot = nullptr;
@@ -435,6 +439,7 @@ void sfista_default_opts(sfista_opts *o) {
 sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int center_row,
                            int center_col, int img_rows, int img_cols, int bc, int r,
                            const sfista_opts *opts, sfista_ctx **out) {
+    TraceRange trace_("sfista_setup");
     if (!out) return fail(SFISTA_EINVAL, "out is NULL");
     *out = nullptr;
     sfista_opts o;
@@ -563,6 +568,7 @@ sfista_status sfista_factorize(const double *psf, int p, int q, int cr, int cc, 
 
 sfista_status sfista_solve_device(sfista_ctx *c, const float *d_b, double lambda, int iters, float *d_x,
                                   void *stream) {
+    TraceRange trace_("sfista_solve_device");
     sfista_status st = check_ctx(c);
     if (st) return st;
     if (!d_x) return fail(SFISTA_EINVAL, "x is NULL");
@@ -577,6 +583,7 @@ sfista_status sfista_solve_device(sfista_ctx *c, const float *d_b, double lambda
 
 sfista_status sfista_solve_state(sfista_ctx *c, const float *d_b, double lambda, int k0, int iters,
                                  double *d_X, double *d_Xprev, void *stream) {
+    TraceRange trace_("sfista_solve_state");
     sfista_status st = check_ctx(c);
     if (st) return st;
     if (!d_X || !d_Xprev) return fail(SFISTA_EINVAL, "state buffers are NULL");
@@ -599,6 +606,7 @@ sfista_status sfista_sync(sfista_ctx *c, void *stream) {
 }
 
 sfista_status sfista_solve(sfista_ctx *c, const float *b, double lambda, int iters, float *x) {
+    TraceRange trace_("sfista_solve");
     sfista_status st = check_ctx(c);
     if (st) return st;
     if (!b || !x) return fail(SFISTA_EINVAL, "b or x is NULL");
@@ -639,6 +647,45 @@ sfista_status sfista_apply(sfista_ctx *c, const float *d_x, float *d_y, int tran
         if (st) return st;
     }
     SF_CUDA(cudaGetLastError());
+    return finish_on_user(c, user);
+}
+
+sfista_status sfista_objective(sfista_ctx *c, const float *d_b, const float *d_x, double lambda, double *phi,
+                               void *stream) {
+    TraceRange trace_("sfista_objective");
+    sfista_status st = check_ctx(c);
+    if (st) return st;
+    if (!d_b || !d_x || !phi) return fail(SFISTA_EINVAL, "NULL argument");
+    if (!(lambda >= 0) || !isfinite(lambda)) return fail(SFISTA_EINVAL, "lambda must be finite and >= 0");
+    DeviceGuard g(c->dev);
+    cudaStream_t user = (cudaStream_t)stream;
+    SF_CUDA(cudaEventRecord(c->ev_in, user));
+    SF_CUDA(cudaStreamWaitEvent(c->stream, c->ev_in, 0));
+    // A_s x into the scratch image, then the two sums of squares in FP64.
+    const HostSetup &h = c->hs;
+    ProxArgs pa{};
+    if (c->op == SFISTA_OP_BANDED_FUSED) {
+        launch_band_op_fused(d_x, c->m, c->n, c->r, c->fA, h.A.lo, h.A.w, c->fB, h.B.lo, h.B.w, EPI_STORE, c->tmp, pa,
+                             c->stream);
+    } else if (is_banded(c->op)) {
+        launch_band_rows<float>(d_x, c->m, c->n, c->fA, h.A.lo, h.A.w, c->r, c->Z, c->stream);
+        launch_band_cols<float>(c->Z, c->m, c->n, c->fB, h.B.lo, h.B.w, c->r, EPI_STORE, c->tmp, pa, c->stream);
+    } else {
+        st = gemm_apply(c->gemm, d_x, c->tmp, 0, c->stream);
+        if (st) return st;
+    }
+    const int nblk = 256;
+    double *scratch = nullptr;
+    SF_CUDA(cudaMallocAsync((void **)&scratch, (nblk + 2) * sizeof(double), c->stream));
+    launch_sumsq(c->tmp, d_b, c->N, scratch, nblk, scratch + nblk, c->stream);
+    launch_sumsq(d_x, nullptr, c->N, scratch, nblk, scratch + nblk + 1, c->stream);
+    double sums[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(sums, scratch + nblk, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    cudaFreeAsync(scratch, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (!e) e = cudaGetLastError();
+    if (e) return fail(SFISTA_ECUDA, std::string("objective: ") + cudaGetErrorString(e));
+    *phi = 0.5 * sums[0] + 0.5 * lambda * lambda * sums[1];
     return finish_on_user(c, user);
 }
 
@@ -796,6 +843,7 @@ void sfista_batch_destroy(sfista_batch *b) { batch_free(b); }
 
 sfista_status sfista_batch_solve(sfista_batch *b, const float *const *d_b, const double *lambdas, int iters,
                                  float *const *d_x, void *stream) {
+    TraceRange trace_("sfista_batch_solve");
     if (!b) return fail(SFISTA_EINVAL, "batch is NULL");
     if (!d_b || !lambdas || !d_x) return fail(SFISTA_EINVAL, "NULL argument array");
     if (iters < 0) return fail(SFISTA_EINVAL, "iters must be >= 0");
@@ -893,6 +941,7 @@ sfista_status sfista_batch_sync(sfista_batch *b, void *stream) {
 
 sfista_status sfista_batch_tune(sfista_batch *b, int iters, sfista_tune_entry *entries, int max_entries,
                                 int *n_entries) {
+    TraceRange trace_("sfista_batch_tune");
     if (!b) return fail(SFISTA_EINVAL, "batch is NULL");
     if (n_entries) *n_entries = 0;
     if (iters < 1 || max_entries < 0) return fail(SFISTA_EINVAL, "iters must be >= 1 and max_entries >= 0");
@@ -1044,6 +1093,7 @@ sfista_status time_stage_range(sfista_ctx *c, int s0, int s1, int reps, float *m
 }  // namespace
 
 sfista_status sfista_tune(sfista_ctx *c, int iters, sfista_tune_entry *entries, int max_entries, int *n_entries) {
+    TraceRange trace_("sfista_tune");
     sfista_status st = check_ctx(c);
     if (st) return st;
     if (n_entries) *n_entries = 0;

@@ -158,6 +158,9 @@ void launch_seed_image(double *v, size_t count, cudaStream_t s);
 void launch_dots(const double *u, const double *v, size_t count, double *partial,
                  int nblk, double *dot, cudaStream_t s);
 void launch_scale(double *v, size_t count, const double *dot, cudaStream_t s);
+// *out = sum_i (a_i - b_i)^2 (b may be NULL) in FP64; partial holds nblk doubles.
+void launch_sumsq(const float *a, const float *b, size_t count, double *partial, int nblk, double *out,
+                  cudaStream_t s);
 void launch_blur_exact(const float *X, int m, int n, const float *P, int p, int q,
                        int cr, int cc, int bc, float *Y, cudaStream_t s);
 // Dense factor panels from band storage: F[i][row][col] for col in [0, cols).

@@ -300,6 +300,30 @@ __global__ void dots_kernel(const double *u, const double *v, size_t count, doub
         partial[2 * blockIdx.x + 1] = s1[0];
     }
 }
+// sum_i (a_i - b_i)^2 (b may be NULL: sum_i a_i^2) in FP64, per block, then
+// summed in block order by sumsq_final_kernel (deterministic).
+__global__ void sumsq_kernel(const float *a, const float *b, size_t count, double *partial) {
+    __shared__ double s0[256];
+    double acc = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        const double d = (double)a[i] - (b ? (double)b[i] : 0.0);
+        acc += d * d;
+    }
+    s0[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) s0[threadIdx.x] += s0[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = s0[0];
+}
+__global__ void sumsq_final_kernel(const double *partial, int nblk, double *out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double a = 0;
+        for (int i = 0; i < nblk; ++i) a += partial[i];
+        *out = a;
+    }
+}
 __global__ void dots_final_kernel(const double *partial, int nblk, double *dot) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         double a = 0, b = 0;
@@ -416,6 +440,11 @@ void launch_dots(const double *u, const double *v, size_t count, double *partial
                  cudaStream_t s) {
     dots_kernel<<<nblk, 256, 0, s>>>(u, v, count, partial);
     dots_final_kernel<<<1, 32, 0, s>>>(partial, nblk, dot);
+}
+void launch_sumsq(const float *a, const float *b, size_t count, double *partial, int nblk, double *out,
+                  cudaStream_t s) {
+    sumsq_kernel<<<nblk, 256, 0, s>>>(a, b, count, partial);
+    sumsq_final_kernel<<<1, 32, 0, s>>>(partial, nblk, out);
 }
 void launch_scale(double *v, size_t count, const double *dot, cudaStream_t s) {
     scale_kernel<<<grid_for(count), 256, 0, s>>>(v, count, dot);

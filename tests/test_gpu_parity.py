@@ -270,6 +270,39 @@ def test_l1_rejected_by_reverse_mode():
     s.close()
 
 
+@pytest.mark.parametrize("op,prec,tol", [("banded", "fp32", 1e-6), ("banded_fused", "fp32", 1e-6),
+                                         ("gemm_band", "bf16x3", 1e-4)])
+def test_objective_matches_oracle(op, prec, tol):
+    """Phi_s(X) = 1/2 ||A_s X - B||^2 + 1/2 lam^2 ||X||^2 on the device vs the FP64 oracle."""
+    P = W.rotated_gaussian_psf(15, 2.0, 1.0, 0.3)
+    x, b, _ = _problem(96, 80, P, 1, 111)
+    ka = kron.kron_approx(P, 7, 7, 96, 80, 1, 2)
+    s = api.Sfista(P, (96, 80), 1, 2, lipschitz=1.0, op=op, prec=prec)
+    X = W.rng(112).uniform(size=(96, 80)).astype(np.float32)
+    phi = s.objective(_cuda(b), _cuda(X), 0.05)
+    phio = oracle.objective(X.astype(np.float64), b.astype(np.float64), ka, 0.05)
+    assert abs(phi - phio) <= tol * abs(phio)
+    s.close()
+
+
+@pytest.mark.parametrize("op,prec", [("banded", "fp32"), ("banded_fused", "fp32"), ("banded_persistent", "fp32"),
+                                     ("gemm_band", "bf16x3"), ("gemm_dense", "tf32x3")])
+def test_solves_are_bit_reproducible(op, prec):
+    """Two solves of the same input give bit-identical results (no atomics in the reductions)."""
+    P = W.rotated_gaussian_psf(15, 2.0, 1.0, 0.3)
+    x, b, _ = _problem(128, 96, P, 1, 113)
+    db = _cuda(b)
+    s1 = api.Sfista(P, (128, 96), 1, 2, op=op, prec=prec)
+    s2 = api.Sfista(P, (128, 96), 1, 2, op=op, prec=prec)
+    assert s1.info()["lipschitz"] == s2.info()["lipschitz"]
+    X1 = s1.solve_device(db, 0.01, 30)
+    X2 = s1.solve_device(db, 0.01, 30)
+    X3 = s2.solve_device(db, 0.01, 30)
+    assert torch.equal(X1, X2) and torch.equal(X1, X3)
+    s1.close()
+    s2.close()
+
+
 def test_zero_iterations_returns_zero():
     P = W.gaussian_psf(9, 2.0)
     s = api.Sfista(P, (40, 40), 0, 1, lipschitz=1.0)
