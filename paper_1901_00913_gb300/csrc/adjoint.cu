@@ -386,7 +386,6 @@ extern "C" sfista_status sfista_unrolled_bwd(sfista_ctx *c, const float *d_b, do
     launch_f32_to_f64(d_gX, xb + (size_t)(iters % 3) * N, N, s);
     if (d_gA) SF_CUDA(cudaMemsetAsync(d_gA, 0, (size_t)r * n * n * 4, s));
     if (d_gB) SF_CUDA(cudaMemsetAsync(d_gB, 0, (size_t)r * m * m * 4, s));
-    ProxArgs pz{};
     const float minus_inv = (float)(-inv);
     for (int j = nseg - 1; j >= 0; --j) {
         const int k0 = j * ce, k1 = std::min(iters, k0 + ce);
@@ -417,13 +416,9 @@ extern "C" sfista_status sfista_unrolled_bwd(sfista_ctx *c, const float *d_b, do
                 float *Yf = Yseg + (size_t)nb * N, *Rf = Rseg + (size_t)nb * N;
                 launch_f64_to_f32(Yk, Yf, N, s);
                 As_apply(c, Yf, Rf, s, EPI_RESIDUAL);   // R_k = A_s Y_k - B
-                if (d_gA) {
-                    for (int i = 0; i < r; ++i) {
-                        const float *Bi = c->fB + (size_t)i * h.B.w * m;
-                        float *Ui = Useg + ((size_t)nb * r + i) * N, *U2i = U2seg + ((size_t)nb * r + i) * N;
-                        launch_band_cols<float>(Vk, m, n, Bi, h.B.lo, h.B.w, 1, EPI_STORE, Ui, pz, s);    // B_i V
-                        launch_band_cols<float>(Yf, m, n, Bi, h.B.lo, h.B.w, 1, EPI_STORE, U2i, pz, s);   // B_i Y
-                    }
+                if (d_gA) {   // B_i V and B_i Y for every term, one launch each
+                    launch_band_cols_each(Vk, m, n, c->fB, h.B.lo, h.B.w, r, Useg + (size_t)nb * r * N, s);
+                    launch_band_cols_each(Yf, m, n, c->fB, h.B.lo, h.B.w, r, U2seg + (size_t)nb * r * N, s);
                 }
                 if (d_gB) {
                     launch_band_rows<float>(Rf, m, n, c->fAT, h.AT.lo, h.AT.w, r, Zsseg + (size_t)nb * r * N, s);

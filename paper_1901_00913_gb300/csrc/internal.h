@@ -90,6 +90,10 @@ template <typename T>
 void launch_band_cols(const T *Z, int m, int n, const T *Gb, int lo, int w, int r,
                       EpiKind epi, T *Out, const ProxArgs &pa, cudaStream_t s, int chunk = 0);
 
+// Out + i * m * n = G_i In for every term i (FP32, terms not summed).
+void launch_band_cols_each(const float *In, int m, int n, const float *Gb, int lo, int w, int r, float *Out,
+                           cudaStream_t s);
+
 size_t band_rows_smem(int w, size_t elem);
 size_t band_cols_smem(int w, size_t elem);
 // Largest FP32 term chunk of a rows (cols) block of band width w that fits in

@@ -65,6 +65,28 @@ __global__ void __launch_bounds__(band::NT) band_cols_kernel4(const float *__res
     band4::cols_item<EPI, RT>(Z, m, n, r, chunk, Gb, lo, w, blockIdx.y * RT, blockIdx.x * band::TC, Out, pa, sm4);
 }
 
+// Out + i * m * n = G_i In for each term i = blockIdx.z (terms not summed).
+template <int RT>
+__global__ void __launch_bounds__(band::NT) band_cols_each_kernel4(const float *__restrict__ In, int m, int n,
+                                                                  const float *__restrict__ Gb, int lo, int w,
+                                                                  float *__restrict__ Out) {
+    extern __shared__ __align__(16) float sm4[];
+    const size_t t = blockIdx.z;
+    ProxArgs pa{};
+    band4::cols_item<EPI_STORE, RT>(In, m, n, 1, 1, Gb + t * w * m, lo, w, blockIdx.y * RT, blockIdx.x * band::TC,
+                                    Out + t * m * n, pa, sm4);
+}
+__global__ void __launch_bounds__(band::NT) band_cols_each_kernel(const float *__restrict__ In, int m, int n,
+                                                                 const float *__restrict__ Gb, int lo, int w,
+                                                                 float *__restrict__ Out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const size_t t = blockIdx.z;
+    ProxArgs pa{};
+    band::cols_item<float, EPI_STORE, false>(In, m, n, 1, 1, Gb + t * w * m, lo, w, blockIdx.y * band::TA,
+                                             blockIdx.x * band::TC, Out + t * m * n, pa,
+                                             reinterpret_cast<float *>(smem_raw));
+}
+
 constexpr size_t kBandSmemBudget = 96 * 1024;
 constexpr size_t kBandSmemMax = 227 * 1024;
 
@@ -181,6 +203,17 @@ void launch_band_cols(const T *Z, int m, int n, const T *Gb, int lo, int w, int 
         launch_pdl(band_cols_kernel<T, EPI_PROX>, grid, sm, s, Z, m, n, Gb, lo, w, r, chunk, Out, pa);
 }
 
+void launch_band_cols_each(const float *In, int m, int n, const float *Gb, int lo, int w, int r, float *Out,
+                           cudaStream_t s) {
+    const int rt = vec_rows<float>(m, n, In, Gb, Out);
+    const int ta = rt ? rt : band::TA;
+    dim3 grid((n + band::TC - 1) / band::TC, (m + ta - 1) / ta, r);
+    const size_t sm = cols_bytes<float>(rt, w, 1);
+    if (rt == 64) return launch_pdl(band_cols_each_kernel4<64>, grid, sm, s, In, m, n, Gb, lo, w, Out);
+    if (rt == 32) return launch_pdl(band_cols_each_kernel4<32>, grid, sm, s, In, m, n, Gb, lo, w, Out);
+    launch_pdl(band_cols_each_kernel, grid, sm, s, In, m, n, Gb, lo, w, Out);
+}
+
 size_t band_smem_f32(bool rows, int w, int chunk) {   // the largest of the layouts
     size_t b = 0;
     for (int rt : {0, 32, 64}) b = std::max(b, rows ? rows_bytes<float>(rt, w, chunk) : cols_bytes<float>(rt, w, chunk));
@@ -212,6 +245,8 @@ cudaError_t band_set_smem_limits(int w) {
     const int lim = (int)kBandSmemMax;
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(band_rows_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    for (auto k : {band_cols_each_kernel4<32>, band_cols_each_kernel4<64>, band_cols_each_kernel})
+        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
     for (auto k : {band_rows_kernel4<32>, band_rows_kernel4<64>})
         if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
     for (auto k : {band_cols_kernel4<EPI_STORE, 32>, band_cols_kernel4<EPI_RESIDUAL, 32>, band_cols_kernel4<EPI_PROX, 32>,
@@ -317,22 +352,40 @@ __global__ void sumsq_kernel(const float *a, const float *b, size_t count, doubl
     }
     if (threadIdx.x == 0) partial[blockIdx.x] = s0[0];
 }
-__global__ void sumsq_final_kernel(const double *partial, int nblk, double *out) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double a = 0;
-        for (int i = 0; i < nblk; ++i) a += partial[i];
-        *out = a;
+__global__ void __launch_bounds__(256) sumsq_final_kernel(const double *partial, int nblk, double *out) {
+    __shared__ double s0[256];
+    double a = 0;
+    for (int i = threadIdx.x; i < nblk; i += 256) a += partial[i];
+    s0[threadIdx.x] = a;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) s0[threadIdx.x] += s0[threadIdx.x + h];
+        __syncthreads();
     }
+    if (threadIdx.x == 0) *out = s0[0];
 }
-__global__ void dots_final_kernel(const double *partial, int nblk, double *dot) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double a = 0, b = 0;
-        for (int i = 0; i < nblk; ++i) {
-            a += partial[2 * i];
-            b += partial[2 * i + 1];
+// Final sums of the per-block partials: 256 threads, each adding its strided
+// share in order, then a shared-memory tree (a fixed order: deterministic).
+__global__ void __launch_bounds__(256) dots_final_kernel(const double *partial, int nblk, double *dot) {
+    __shared__ double s0[256], s1[256];
+    double a = 0, b = 0;
+    for (int i = threadIdx.x; i < nblk; i += 256) {
+        a += partial[2 * i];
+        b += partial[2 * i + 1];
+    }
+    s0[threadIdx.x] = a;
+    s1[threadIdx.x] = b;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            s0[threadIdx.x] += s0[threadIdx.x + h];
+            s1[threadIdx.x] += s1[threadIdx.x + h];
         }
-        dot[0] = a;
-        dot[1] = b;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        dot[0] = s0[0];
+        dot[1] = s1[0];
     }
 }
 // v *= 1 / sqrt(dot[1])
@@ -439,12 +492,12 @@ void launch_seed_image(double *v, size_t count, cudaStream_t s) {
 void launch_dots(const double *u, const double *v, size_t count, double *partial, int nblk, double *dot,
                  cudaStream_t s) {
     dots_kernel<<<nblk, 256, 0, s>>>(u, v, count, partial);
-    dots_final_kernel<<<1, 32, 0, s>>>(partial, nblk, dot);
+    dots_final_kernel<<<1, 256, 0, s>>>(partial, nblk, dot);
 }
 void launch_sumsq(const float *a, const float *b, size_t count, double *partial, int nblk, double *out,
                   cudaStream_t s) {
     sumsq_kernel<<<nblk, 256, 0, s>>>(a, b, count, partial);
-    sumsq_final_kernel<<<1, 32, 0, s>>>(partial, nblk, out);
+    sumsq_final_kernel<<<1, 256, 0, s>>>(partial, nblk, out);
 }
 void launch_scale(double *v, size_t count, const double *dot, cudaStream_t s) {
     scale_kernel<<<grid_for(count), 256, 0, s>>>(v, count, dot);
