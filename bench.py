@@ -566,7 +566,6 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--forms", default="fp32:auto+tune,fp32:banded_fused,fp32:banded,fp32:banded_persistent,bf16x3:gemm_band,tf32x3:gemm_band,bf16:gemm_band,tf32:gemm_band",
                     help="comma list of prec:op forms to measure")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "cfg4", "cfg5", "ex2"])
     ap.add_argument("--check-iters", type=int, default=10)
     args = ap.parse_args()

@@ -66,18 +66,23 @@ static __device__ __forceinline__ void prox_momentum(const ProxArgs &pa, size_t 
     store_operands(pa, idx, yn);
 }
 
-// N pixels at once: every state load is issued before any arithmetic or
-// store, so a thread keeps 2N loads in flight.
+// State loads of N pixels (Y_k and X_{k-1}), all issued before any use.
 template <int N>
-static __device__ __forceinline__ void prox_momentum_n(const ProxArgs &pa, const size_t *idx, const float *g,
-                                                       const bool *valid) {
-    float2 y[N], xp[N];
+static __device__ __forceinline__ void prox_load_n(const ProxArgs &pa, const size_t *idx, const bool *valid, float2 *y,
+                                                   float2 *xp) {
 #pragma unroll
     for (int q = 0; q < N; ++q) {
         y[q] = valid[q] ? __ldcg(pa.Y + idx[q]) : make_float2(0.f, 0.f);
         xp[q] = valid[q] ? __ldcg(pa.Xin + idx[q]) : make_float2(0.f, 0.f);
     }
-    const float2 beta = pa.beta[pa.k - 1];
+}
+
+// Step 1 + Step 3 for N pixels whose state (y, xp) and momentum weight
+// beta = beta[k-1] are already loaded.
+template <int N>
+static __device__ __forceinline__ void prox_apply_n(const ProxArgs &pa, const size_t *idx, const float *g,
+                                                    const bool *valid, const float2 *y, const float2 *xp,
+                                                    float2 beta) {
     bool bad = false;
 #pragma unroll
     for (int q = 0; q < N; ++q) {
@@ -89,6 +94,16 @@ static __device__ __forceinline__ void prox_momentum_n(const ProxArgs &pa, const
         store_operands(pa, idx[q], yn);
     }
     if (bad) atomicOr(pa.status, DEV_NONFINITE);
+}
+
+// N pixels at once: every state load is issued before any arithmetic or
+// store, so a thread keeps 2N loads in flight.
+template <int N>
+static __device__ __forceinline__ void prox_momentum_n(const ProxArgs &pa, const size_t *idx, const float *g,
+                                                       const bool *valid) {
+    float2 y[N], xp[N];
+    prox_load_n<N>(pa, idx, valid, y, xp);
+    prox_apply_n<N>(pa, idx, g, valid, y, xp, pa.beta[pa.k - 1]);
 }
 
 // Pairs of neighbouring pixels (idx[q] even) for N rows at once.

@@ -75,9 +75,45 @@ __host__ __device__ inline FusedGeom fused_geom(int r, int loF, int wF, int wG) 
 
 __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 
+// Pixels (a + j, c), j = 0..3, of a thread's epilogue: linear index and bounds.
+__device__ __forceinline__ void epi_index(int m, int n, int a, int c, size_t *idx, bool *ok) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        ok[j] = c < n && a + j < m;
+        idx[j] = (size_t)(a + j) * n + c;
+    }
+}
+
+// Four taps (k .. k+3) of the row pass for K terms: (a0, a1) and (b0, b1) are
+// the lanes' input windows of the two rows at columns cb + k .. cb + k + 7.
+template <int K, bool TWO>
+__device__ __forceinline__ void rows_taps4(const float4 &a0, const float4 &a1, const float4 &b0, const float4 &b1,
+                                           const float *fk, int wF4, float (&acc)[TWO ? 2 : 1][K][4]) {
+    const float xw[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float yw[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            const float4 f = lds4(fk + (q * wF4 + t) * TC);
+            acc[0][q][0] = fmaf(xw[t], f.x, acc[0][q][0]);
+            acc[0][q][1] = fmaf(xw[t + 1], f.y, acc[0][q][1]);
+            acc[0][q][2] = fmaf(xw[t + 2], f.z, acc[0][q][2]);
+            acc[0][q][3] = fmaf(xw[t + 3], f.w, acc[0][q][3]);
+            if (TWO) {
+                acc[TWO ? 1 : 0][q][0] = fmaf(yw[t], f.x, acc[TWO ? 1 : 0][q][0]);
+                acc[TWO ? 1 : 0][q][1] = fmaf(yw[t + 1], f.y, acc[TWO ? 1 : 0][q][1]);
+                acc[TWO ? 1 : 0][q][2] = fmaf(yw[t + 2], f.z, acc[TWO ? 1 : 0][q][2]);
+                acc[TWO ? 1 : 0][q][3] = fmaf(yw[t + 3], f.w, acc[TWO ? 1 : 0][q][3]);
+            }
+        }
+    }
+}
+
 // Row pass for K terms on one (TWO: two) rows per lane.  xa: the lane's first
 // input row at column cb; fr: coefficients at column cb of the first term;
-// zt: Zt entry (first term, column cb, row e).
+// zt: Zt entry (first term, column cb, row e).  The tap loop takes two steps
+// of 4 per trip so the windows alternate between two register sets.
 template <int K, bool TWO>
 __device__ __forceinline__ void rows_pass(const float *xa, int sp, const float *fr, int wF4, float *zt, int zsp,
                                           bool sta, bool stb) {
@@ -87,32 +123,20 @@ __device__ __forceinline__ void rows_pass(const float *xa, int sp, const float *
 #pragma unroll
         for (int q = 0; q < K; ++q) acc[h][q][0] = acc[h][q][1] = acc[h][q][2] = acc[h][q][3] = 0.f;
     const float *xb = xa + 32 * sp;
-    float4 a0 = lds4(xa), b0 = TWO ? lds4(xb) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 a0 = lds4(xa), b0 = TWO ? lds4(xb) : zero;
+    int k = 0;
 #pragma unroll 1
-    for (int k = 0; k < wF4; k += 4) {
-        const float4 a1 = lds4(xa + k + 4);
-        const float4 b1 = TWO ? lds4(xb + k + 4) : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float xw[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        const float yw[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-#pragma unroll
-            for (int q = 0; q < K; ++q) {
-                const float4 f = lds4(fr + (q * wF4 + k + t) * TC);
-                acc[0][q][0] = fmaf(xw[t], f.x, acc[0][q][0]);
-                acc[0][q][1] = fmaf(xw[t + 1], f.y, acc[0][q][1]);
-                acc[0][q][2] = fmaf(xw[t + 2], f.z, acc[0][q][2]);
-                acc[0][q][3] = fmaf(xw[t + 3], f.w, acc[0][q][3]);
-                if (TWO) {
-                    acc[TWO ? 1 : 0][q][0] = fmaf(yw[t], f.x, acc[TWO ? 1 : 0][q][0]);
-                    acc[TWO ? 1 : 0][q][1] = fmaf(yw[t + 1], f.y, acc[TWO ? 1 : 0][q][1]);
-                    acc[TWO ? 1 : 0][q][2] = fmaf(yw[t + 2], f.z, acc[TWO ? 1 : 0][q][2]);
-                    acc[TWO ? 1 : 0][q][3] = fmaf(yw[t + 3], f.w, acc[TWO ? 1 : 0][q][3]);
-                }
-            }
-        }
-        a0 = a1;
-        b0 = b1;
+    for (; k + 8 <= wF4; k += 8) {
+        const float4 a1 = lds4(xa + k + 4), b1 = TWO ? lds4(xb + k + 4) : zero;
+        rows_taps4<K, TWO>(a0, a1, b0, b1, fr + k * TC, wF4, acc);
+        a0 = lds4(xa + k + 8);
+        b0 = TWO ? lds4(xb + k + 8) : zero;
+        rows_taps4<K, TWO>(a1, a0, b1, b0, fr + (k + 4) * TC, wF4, acc);
+    }
+    if (k < wF4) {
+        const float4 a1 = lds4(xa + k + 4), b1 = TWO ? lds4(xb + k + 4) : zero;
+        rows_taps4<K, TWO>(a0, a1, b0, b1, fr + k * TC, wF4, acc);
     }
 #pragma unroll
     for (int q = 0; q < K; ++q)
@@ -123,9 +147,24 @@ __device__ __forceinline__ void rows_pass(const float *xa, int sp, const float *
         }
 }
 
+// Four taps (k .. k+3) of one term of the column pass: (w0, w1) is the Z
+// window of rows rb + k .. rb + k + 7 in the lane's column.
+__device__ __forceinline__ void cols_taps4(const float4 &w0, const float4 &w1, const float *gk, float (&a)[4]) {
+    const float z[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const float4 g = lds4(gk + t * TA);
+        a[0] = fmaf(g.x, z[t], a[0]);
+        a[1] = fmaf(g.y, z[t + 1], a[1]);
+        a[2] = fmaf(g.z, z[t + 2], a[2]);
+        a[3] = fmaf(g.w, z[t + 3], a[3]);
+    }
+}
+
 // Column pass for K terms.  zc: Zt entry (first term, the lane's column,
 // row rb); gr: coefficients of rows rb .. rb+3 of the first term.  Each
-// term's chain is summed into acc at the end, terms in order.
+// term's chain is summed into acc at the end, terms in order.  Two steps
+// of 4 taps per trip, as in the row pass.
 template <int K>
 __device__ __forceinline__ void cols_pass(const float *zc, int zsp, const float *gr, int wG4, float *acc) {
     float a[K][4];
@@ -135,21 +174,23 @@ __device__ __forceinline__ void cols_pass(const float *zc, int zsp, const float 
         a[q][0] = a[q][1] = a[q][2] = a[q][3] = 0.f;
         w0[q] = lds4(zc + q * TC * zsp);
     }
+    int k = 0;
 #pragma unroll 1
-    for (int k = 0; k < wG4; k += 4) {
+    for (; k + 8 <= wG4; k += 8) {
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            const float *zq = zc + q * TC * zsp;
+            const float4 w1 = lds4(zq + k + 4);
+            cols_taps4(w0[q], w1, gr + (q * wG4 + k) * TA, a[q]);
+            w0[q] = lds4(zq + k + 8);
+            cols_taps4(w1, w0[q], gr + (q * wG4 + k + 4) * TA, a[q]);
+        }
+    }
+    if (k < wG4) {
 #pragma unroll
         for (int q = 0; q < K; ++q) {
             const float4 w1 = lds4(zc + q * TC * zsp + k + 4);
-            const float z[8] = {w0[q].x, w0[q].y, w0[q].z, w0[q].w, w1.x, w1.y, w1.z, w1.w};
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const float4 g = lds4(gr + (q * wG4 + k + t) * TA);
-                a[q][0] = fmaf(g.x, z[t], a[q][0]);
-                a[q][1] = fmaf(g.y, z[t + 1], a[q][1]);
-                a[q][2] = fmaf(g.z, z[t + 2], a[q][2]);
-                a[q][3] = fmaf(g.w, z[t + 3], a[q][3]);
-            }
-            w0[q] = w1;
+            cols_taps4(w0[q], w1, gr + (q * wG4 + k) * TA, a[q]);
         }
     }
 #pragma unroll
@@ -161,10 +202,33 @@ __device__ __forceinline__ void cols_pass(const float *zc, int zsp, const float 
     }
 }
 
+// Loads of a thread's epilogue operands: the observed image (residual) or
+// the state Y_k, X_{k-1} and beta_{k-1} (Step 1 + Step 3).
+template <int EPI>
+__device__ __forceinline__ void epi_load(const ProxArgs &pa, int m, int n, int a, int c, float *bv, float2 *y,
+                                         float2 *xp, float2 &beta) {
+    size_t idx[4];
+    bool ok[4];
+    epi_index(m, n, a, c, idx, ok);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) bv[j] = EPI == EPI_RESIDUAL && ok[j] ? __ldcg(pa.Bd + idx[j]) : 0.f;
+    if (EPI == EPI_PROX) {
+        prox_load_n<4>(pa, idx, ok, y, xp);
+        beta = pa.beta[pa.k - 1];
+    }
+}
+
 // VEC: 16-byte staging (n, m multiples of 4 and In 16-byte aligned);
 // otherwise element-wise copies into the same layout.
-template <int EPI, bool VEC>
-__global__ void __launch_bounds__(NT) band_op_fused_kernel(const float *__restrict__ In, int m, int n, int r,
+// PRE: the epilogue's operands are loaded at the start of the block, before
+// the programmatic wait, so their latency overlaps the staging and both
+// passes.  None of them is written by the preceding kernel, and every kernel
+// of the chain triggers its successor only after its own wait, so the kernel
+// that wrote them has completed.  It holds about 30-50 more registers (two
+// blocks per SM instead of three); the host takes it when every tile is
+// resident at two blocks per SM.
+template <int EPI, bool VEC, bool PRE>
+__global__ void __launch_bounds__(NT, PRE ? 2 : 0) band_op_fused_kernel(const float *__restrict__ In, int m, int n, int r,
                                                            const float *__restrict__ Fb, int loF, int wF,
                                                            const float *__restrict__ Gb, int loG, int wG,
                                                            float *__restrict__ Out, ProxArgs pa) {
@@ -176,6 +240,10 @@ __global__ void __launch_bounds__(NT) band_op_fused_kernel(const float *__restri
     const int e0 = a0 + loG;                   // first staged row
     const int colbase = c0 + loF - geo.off;    // first staged column (4-aligned)
     const int width = TC + geo.wF4;            // staged columns
+    const int rb = warp * 4, gc = c0 + lane;   // epilogue: rows a0 + rb .. + 3 of column gc
+    float bv[4];
+    float2 yv[4], xv[4], beta = make_float2(0.f, 0.f);
+    if (PRE) epi_load<EPI>(pa, m, n, a0 + rb, gc, bv, yv, xv, beta);
     // Constant band tiles first, then (after the previous kernel) the input tile.
     if (VEC) {
         const int tr = tid >> 3, j = tid & 7;
@@ -262,7 +330,6 @@ __global__ void __launch_bounds__(NT) band_op_fused_kernel(const float *__restri
     }
     __syncthreads();
     // Column pass: lane l column c0 + l, warp w rows a0 + 4w .. a0 + 4w + 3.
-    const int rb = warp * 4, gc = c0 + lane;
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     for (int tb = 0; tb < r; tb += 4) {
         const float *zc = Zs + (size_t)(tb * TC + lane) * geo.zsp + rb;
@@ -274,27 +341,16 @@ __global__ void __launch_bounds__(NT) band_op_fused_kernel(const float *__restri
             default: cols_pass<4>(zc, geo.zsp, gr, geo.wG4, acc); break;
         }
     }
-    if (gc < n) {
-        if (EPI == EPI_PROX) {
-            size_t idx[4];
-            float g[4];
-            bool ok[4];
+    if (!PRE) epi_load<EPI>(pa, m, n, a0 + rb, gc, bv, yv, xv, beta);
+    size_t idx[4];
+    bool ok[4];
+    epi_index(m, n, a0 + rb, gc, idx, ok);
+    if (EPI == EPI_PROX) {
+        prox_apply_n<4>(pa, idx, acc, ok, yv, xv, beta);
+    } else {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                ok[j] = a0 + rb + j < m;
-                idx[j] = (size_t)(a0 + rb + j) * n + gc;
-                g[j] = acc[j];
-            }
-            prox_momentum_n<4>(pa, idx, g, ok);
-        } else {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int ga = a0 + rb + j;
-                if (ga >= m) break;
-                const size_t idx = (size_t)ga * n + gc;
-                Out[idx] = EPI == EPI_STORE ? acc[j] : acc[j] - pa.Bd[idx];
-            }
-        }
+        for (int j = 0; j < 4; ++j)
+            if (ok[j]) Out[idx[j]] = EPI == EPI_STORE ? acc[j] : acc[j] - bv[j];
     }
     band::pdl_trigger();
 }
@@ -302,12 +358,29 @@ __global__ void __launch_bounds__(NT) band_op_fused_kernel(const float *__restri
 constexpr size_t kFusedSmemMax = 227 * 1024;
 
 template <int EPI>
-void launch_epi(const cudaLaunchConfig_t &cfg, bool vec, const float *In, int m, int n, int r, const float *Fb,
-                int loF, int wF, const float *Gb, int loG, int wG, float *Out, const ProxArgs &pa) {
+void launch_epi(const cudaLaunchConfig_t &cfg, bool vec, bool pre, const float *In, int m, int n, int r,
+                const float *Fb, int loF, int wF, const float *Gb, int loG, int wG, float *Out, const ProxArgs &pa) {
+    if constexpr (EPI != EPI_STORE) {
+        if (vec && pre)
+            return (void)cudaLaunchKernelEx(&cfg, band_op_fused_kernel<EPI, true, true>, In, m, n, r, Fb, loF, wF, Gb,
+                                            loG, wG, Out, pa);
+    }
     if (vec)
-        cudaLaunchKernelEx(&cfg, band_op_fused_kernel<EPI, true>, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out, pa);
+        cudaLaunchKernelEx(&cfg, band_op_fused_kernel<EPI, true, false>, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out,
+                           pa);
     else
-        cudaLaunchKernelEx(&cfg, band_op_fused_kernel<EPI, false>, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out, pa);
+        cudaLaunchKernelEx(&cfg, band_op_fused_kernel<EPI, false, false>, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out,
+                           pa);
+}
+
+int fused_sm_count() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
+    }
+    return sms;
 }
 
 }  // namespace
@@ -319,9 +392,10 @@ size_t band_op_fused_smem(int r, int wF, int wG) { return sizeof(float) * fused_
 bool band_op_fused_prepare(int r, int wF, int wG) {
     const size_t sm = band_op_fused_smem(r, wF, wG);
     if (sm > kFusedSmemMax) return false;
-    for (auto k : {band_op_fused_kernel<EPI_STORE, true>, band_op_fused_kernel<EPI_RESIDUAL, true>,
-                   band_op_fused_kernel<EPI_PROX, true>, band_op_fused_kernel<EPI_STORE, false>,
-                   band_op_fused_kernel<EPI_RESIDUAL, false>, band_op_fused_kernel<EPI_PROX, false>})
+    for (auto k : {band_op_fused_kernel<EPI_STORE, true, false>, band_op_fused_kernel<EPI_RESIDUAL, true, false>,
+                   band_op_fused_kernel<EPI_PROX, true, false>, band_op_fused_kernel<EPI_RESIDUAL, true, true>,
+                   band_op_fused_kernel<EPI_PROX, true, true>, band_op_fused_kernel<EPI_STORE, false, false>,
+                   band_op_fused_kernel<EPI_RESIDUAL, false, false>, band_op_fused_kernel<EPI_PROX, false, false>})
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemMax) != cudaSuccess)
             return false;
     return true;
@@ -341,12 +415,13 @@ void launch_band_op_fused(const float *In, int m, int n, int r, const float *Fb,
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    const bool pre = (long)cfg.gridDim.x * cfg.gridDim.y <= 2L * fused_sm_count();
     if (epi == EPI_STORE)
-        launch_epi<EPI_STORE>(cfg, vec, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out, pa);
+        launch_epi<EPI_STORE>(cfg, vec, pre, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out, pa);
     else if (epi == EPI_RESIDUAL)
-        launch_epi<EPI_RESIDUAL>(cfg, vec, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out, pa);
+        launch_epi<EPI_RESIDUAL>(cfg, vec, pre, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out, pa);
     else
-        launch_epi<EPI_PROX>(cfg, vec, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out, pa);
+        launch_epi<EPI_PROX>(cfg, vec, pre, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out, pa);
 }
 
 }  // namespace sfista
