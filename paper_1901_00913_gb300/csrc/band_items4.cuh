@@ -47,8 +47,35 @@ __host__ __device__ inline int tiles(int rt, int m, int n) { return ((m + rt - 1
 
 __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 
+// Four taps (k .. k+3) of K terms for the lane's H rows: (a0, a1), (b0, b1)
+// are the rows' input windows at columns cb + k .. cb + k + 7.
+template <int K, int H>
+__device__ __forceinline__ void rows_taps4(const float4 &a0, const float4 &a1, const float4 &b0, const float4 &b1,
+                                           const float *fk, int w4, float (&acc)[2][K][4]) {
+    const float xw[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float yw[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            const float4 f = lds4(fk + (q * w4 + u) * TC);
+            acc[0][q][0] = fmaf(xw[u], f.x, acc[0][q][0]);
+            acc[0][q][1] = fmaf(xw[u + 1], f.y, acc[0][q][1]);
+            acc[0][q][2] = fmaf(xw[u + 2], f.z, acc[0][q][2]);
+            acc[0][q][3] = fmaf(xw[u + 3], f.w, acc[0][q][3]);
+            if (H == 2) {
+                acc[1][q][0] = fmaf(yw[u], f.x, acc[1][q][0]);
+                acc[1][q][1] = fmaf(yw[u + 1], f.y, acc[1][q][1]);
+                acc[1][q][2] = fmaf(yw[u + 2], f.z, acc[1][q][2]);
+                acc[1][q][3] = fmaf(yw[u + 3], f.w, acc[1][q][3]);
+            }
+        }
+    }
+}
+
 // K terms of the rows pass for the lane's H rows (xa: first row at column
-// cb; the second, for H = 2, 32 rows below).
+// cb; the second, for H = 2, 32 rows below).  Two steps of 4 taps per trip,
+// the windows alternating between two register sets.
 template <int K, int H>
 __device__ __forceinline__ void rows_terms(const float *xa, int sp, const float *fr, int w4, float *__restrict__ Z,
                                            int m, int n, int t, int ga, int c) {
@@ -58,31 +85,20 @@ __device__ __forceinline__ void rows_terms(const float *xa, int sp, const float 
 #pragma unroll
         for (int q = 0; q < K; ++q) acc[h][q][0] = acc[h][q][1] = acc[h][q][2] = acc[h][q][3] = 0.f;
     const float *xb = xa + 32 * sp;
-    float4 a0 = lds4(xa), b0 = H == 2 ? lds4(xb) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 a0 = lds4(xa), b0 = H == 2 ? lds4(xb) : zero;
+    int k = 0;
 #pragma unroll 1
-    for (int k = 0; k < w4; k += 4) {
-        const float4 a1 = lds4(xa + k + 4), b1 = H == 2 ? lds4(xb + k + 4) : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float xw[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        const float yw[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-#pragma unroll
-            for (int q = 0; q < K; ++q) {
-                const float4 f = lds4(fr + (q * w4 + k + u) * TC);
-                acc[0][q][0] = fmaf(xw[u], f.x, acc[0][q][0]);
-                acc[0][q][1] = fmaf(xw[u + 1], f.y, acc[0][q][1]);
-                acc[0][q][2] = fmaf(xw[u + 2], f.z, acc[0][q][2]);
-                acc[0][q][3] = fmaf(xw[u + 3], f.w, acc[0][q][3]);
-                if (H == 2) {
-                    acc[1][q][0] = fmaf(yw[u], f.x, acc[1][q][0]);
-                    acc[1][q][1] = fmaf(yw[u + 1], f.y, acc[1][q][1]);
-                    acc[1][q][2] = fmaf(yw[u + 2], f.z, acc[1][q][2]);
-                    acc[1][q][3] = fmaf(yw[u + 3], f.w, acc[1][q][3]);
-                }
-            }
-        }
-        a0 = a1;
-        b0 = b1;
+    for (; k + 8 <= w4; k += 8) {
+        const float4 a1 = lds4(xa + k + 4), b1 = H == 2 ? lds4(xb + k + 4) : zero;
+        rows_taps4<K, H>(a0, a1, b0, b1, fr + k * TC, w4, acc);
+        a0 = lds4(xa + k + 8);
+        b0 = H == 2 ? lds4(xb + k + 8) : zero;
+        rows_taps4<K, H>(a1, a0, b1, b0, fr + (k + 4) * TC, w4, acc);
+    }
+    if (k < w4) {
+        const float4 a1 = lds4(xa + k + 4), b1 = H == 2 ? lds4(xb + k + 4) : zero;
+        rows_taps4<K, H>(a0, a1, b0, b1, fr + k * TC, w4, acc);
     }
     if (c < n) {   // n is a multiple of 4: the lane's 4 columns are all inside or all outside
 #pragma unroll
@@ -150,9 +166,28 @@ __device__ __forceinline__ void rows_item(const float *__restrict__ In, int m, i
     band::pdl_trigger();
 }
 
+// Four taps (k .. k+3) of one term for the warp's RW rows: z holds the Z
+// values of rows rb + k .. rb + k + RW + 3 in the lane's column.
+template <int RW, int TA>
+__device__ __forceinline__ void cols_taps4(const float (&z)[RW + 4], const float *gk, float (&a)[RW]) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+#pragma unroll
+        for (int h = 0; h < RW / 4; ++h) {
+            const float4 g = lds4(gk + u * TA + 4 * h);
+            a[4 * h + 0] = fmaf(g.x, z[u + 4 * h], a[4 * h + 0]);
+            a[4 * h + 1] = fmaf(g.y, z[u + 4 * h + 1], a[4 * h + 1]);
+            a[4 * h + 2] = fmaf(g.z, z[u + 4 * h + 2], a[4 * h + 2]);
+            a[4 * h + 3] = fmaf(g.w, z[u + 4 * h + 3], a[4 * h + 3]);
+        }
+    }
+}
+
 // One term of the column pass for the warp's RW rows (4 or 8): zc is the
 // staged Z at (row rb, the lane's column), gr the term's coefficients of rows
-// rb .. rb + RW - 1 (row stride TA).
+// rb .. rb + RW - 1 (row stride TA).  Two steps of 4 taps per trip: the
+// second step's window is the first one's shifted by 4 rows plus 4 new
+// values, so only the carry into the next trip moves registers.
 template <int RW, int TA>
 __device__ __forceinline__ void cols_term(const float *zc, const float *gr, int w4, float *acc) {
     float a[RW], w0[RW];
@@ -161,26 +196,30 @@ __device__ __forceinline__ void cols_term(const float *zc, const float *gr, int 
         a[i] = 0.f;
         w0[i] = zc[i * TC];
     }
+    int k = 0;
 #pragma unroll 1
-    for (int k = 0; k < w4; k += 4) {
+    for (; k + 8 <= w4; k += 8) {
+        float n8[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) n8[i] = zc[(k + RW + i) * TC];
+        float za[RW + 4], zb[RW + 4];
+#pragma unroll
+        for (int i = 0; i < RW + 4; ++i) {
+            za[i] = i < RW ? w0[i] : n8[i - RW];
+            zb[i] = i + 4 < RW ? w0[i + 4] : n8[i + 4 - RW];
+        }
+        cols_taps4<RW, TA>(za, gr + k * TA, a);
+        cols_taps4<RW, TA>(zb, gr + (k + 4) * TA, a);
+#pragma unroll
+        for (int i = 0; i < RW; ++i) w0[i] = i + 8 < RW ? w0[i + 8] : n8[i + 8 - RW];
+    }
+    if (k < w4) {
         float z[RW + 4];
 #pragma unroll
         for (int i = 0; i < RW; ++i) z[i] = w0[i];
 #pragma unroll
         for (int i = 0; i < 4; ++i) z[RW + i] = zc[(k + RW + i) * TC];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-#pragma unroll
-            for (int h = 0; h < RW / 4; ++h) {
-                const float4 g = lds4(gr + (k + u) * TA + 4 * h);
-                a[4 * h + 0] = fmaf(g.x, z[u + 4 * h], a[4 * h + 0]);
-                a[4 * h + 1] = fmaf(g.y, z[u + 4 * h + 1], a[4 * h + 1]);
-                a[4 * h + 2] = fmaf(g.z, z[u + 4 * h + 2], a[4 * h + 2]);
-                a[4 * h + 3] = fmaf(g.w, z[u + 4 * h + 3], a[4 * h + 3]);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < RW; ++i) w0[i] = z[4 + i];
+        cols_taps4<RW, TA>(z, gr + k * TA, a);
     }
 #pragma unroll
     for (int i = 0; i < RW; ++i) acc[i] += a[i];
