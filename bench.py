@@ -32,13 +32,21 @@ WORKLOAD = "512x512 reflexive, 31x31 rotated Gaussian PSF (3,1,30deg), r=3, lamb
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 # Kernels per sFISTA iteration by operator form (a solve adds an input
 # check, the state initialisation and the output conversion).
-KERNELS_PER_ITER = {"banded": 4, "banded_fused": 2, "banded_persistent": 1, "gemm_band": 4, "gemm_dense": 4}
+# Kernel launches per iteration (the persistent form: one launch per solve).
+KERNELS_PER_ITER = {"banded": 4, "banded_fused": 2, "gemm_band": 4, "gemm_dense": 4}
 # DRAM bytes (read + write) per launch of a form's dominant kernel, from an
 # ncu capture of the current kernel code on this workload (the summary in
 # profiles/ gives the command); forms without one report null.
-TRAFFIC = {"fp32:banded_fused:0": {"bytes": 2.519e6 + 0.0,
-                                   "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, "
-                                             "profiles/banded_fused_fp32_cfg2_512_r3.md"}}
+TRAFFIC = {}
+
+
+def one_launch_fused(m, n):
+    """The library's rule for the persistent form: the fused one-launch solver
+    when m, n are multiples of 4 and every 32 x 32 tile has one of the two
+    co-resident blocks per SM, else the two-pass persistent solver."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return m % 4 == 0 and n % 4 == 0 and -(-m // 32) * -(-n // 32) <= 2 * sms
 TOL = {"fp32": 1e-5, "bf16x3": 1e-4, "tf32x3": 1e-4}
 DTYPE = {"fp32": "f32", "bf16x3": "bf16", "tf32x3": "tf32", "bf16": "bf16", "tf32": "tf32"}
 NPROD = {"bf16x3": 3, "tf32x3": 3, "bf16": 1, "tf32": 1}
@@ -696,11 +704,13 @@ def main():
         dur_ms = iter_ms * sm[dom] / sum(sm)
         achieved = work[dom] / (dur_ms / 1e3) / 1e12
         ok = err <= TOL.get(prec, float("inf"))
-        kname = {"banded_persistent": "band_solve_persistent (whole iteration)",
+        kname = {"banded_persistent": ("band_solve_fused (whole solve, one launch)" if one_launch_fused(n, n)
+                                       else "band_solve_persistent (whole solve, one launch)"),
                  "banded_fused": ["band_op_fused_kernel (forward + residual)", "",
                                   "band_op_fused_kernel (adjoint + shrink + momentum)", ""][dom]}.get(op, STAGES[dom])
+        launches = 1 + 3 if op == "banded_persistent" else KERNELS_PER_ITER.get(op, 4) * iters + 3
         lines[key] = dict(kernel=kname, value=v, err=err, dpsnr=dpsnr, stage_ms=sm, dom=dom, achieved=achieved, ok=ok,
-                          dur_us=dur_ms * 1e3, launches=KERNELS_PER_ITER.get(op, 4) * iters + 3,
+                          dur_us=dur_ms * 1e3, launches=launches,
                           traffic=TRAFFIC.get("%s:%s:%d" % (prec, op, dom)),
                           bound=bound, peak=peak, unit=unit, peak_src=peak_src, prec=prec,
                           op_tflops_alg=sum(alg) * v / world / 1e12,

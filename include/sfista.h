@@ -76,10 +76,15 @@ typedef enum {
     SFISTA_OP_GEMM_BAND = 2,   /* dense-factor GEMMs that skip K tiles outside the band       */
     SFISTA_OP_GEMM_DENSE = 3,  /* dense-factor GEMMs over the full K range (Sec. 3.3 O(s(nm^2+mn^2))) */
     SFISTA_OP_BANDED_PERSISTENT = 4, /* banded FP32 operator, the whole iteration loop in one
-                                        persistent cooperative launch (grid barrier between phases) */
+                                        persistent cooperative launch (grid barrier between phases):
+                                        the fused operator form with band tiles and state resident
+                                        when every 32 x 32 tile has its own block (m, n multiples of
+                                        4), else the two-pass form */
     SFISTA_OP_BANDED_FUSED = 5 /* banded FP32 operator, one kernel per operator application: the
                                   row pass is kept in shared memory for the column pass (the
-                                  automatic FP32 choice up to 1024^2 pixels and band width 48) */
+                                  automatic FP32 choice up to 1024^2 pixels and band width 48;
+                                  SFISTA_OP_BANDED_PERSISTENT with the fused form when every
+                                  tile also has its own resident block) */
 } sfista_operator;
 
 typedef struct {

@@ -281,7 +281,7 @@ void As_apply(sfista_ctx *c, const float *x, float *out, cudaStream_t s, EpiKind
     const HostSetup &h = c->hs;
     ProxArgs pa{};
     pa.Bd = c->Bd;
-    if (c->op == SFISTA_OP_BANDED_FUSED) {
+    if (fused_apply(c)) {
         launch_band_op_fused(x, c->m, c->n, c->r, c->fA, h.A.lo, h.A.w, c->fB, h.B.lo, h.B.w, epi, out, pa, s);
         return;
     }
@@ -291,7 +291,7 @@ void As_apply(sfista_ctx *c, const float *x, float *out, cudaStream_t s, EpiKind
 void AsT_apply(sfista_ctx *c, const float *x, float *out, cudaStream_t s) {
     const HostSetup &h = c->hs;
     ProxArgs pa{};
-    if (c->op == SFISTA_OP_BANDED_FUSED) {
+    if (fused_apply(c)) {
         launch_band_op_fused(x, c->m, c->n, c->r, c->fAT, h.AT.lo, h.AT.w, c->fBT, h.BT.lo, h.BT.w, EPI_STORE, out, pa,
                              s);
         return;

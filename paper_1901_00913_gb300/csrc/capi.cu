@@ -129,7 +129,7 @@ namespace {
 // Stage `st` (0..3) of iteration k; see sfista_time_stages for the numbering.
 void enqueue_stage(sfista_ctx *c, int st, const ProxArgs &pa) {
     const HostSetup &h = c->hs;
-    if (c->op == SFISTA_OP_BANDED_FUSED) {
+    if (fused_apply(c)) {
         // Two launches per iteration: stage 0 = forward operator + residual,
         // stage 2 = adjoint + shrink / momentum (stages 1 and 3 are empty).
         if (st == 0)
@@ -167,8 +167,14 @@ sfista_status run_loop(sfista_ctx *c, double lam, int k0, int iters) {
     if (c->op == SFISTA_OP_BANDED_PERSISTENT) {
         const HostSetup &h = c->hs;
         ProxArgs pa = prox_args(c, k0 + 1, lam);
-        SF_CUDA(launch_persistent(c->pgrid, c->psmem, c->prows_chunk, c->pcols_chunk, c->m, c->n, c->r, c->fA, h.A, c->fB, h.B, c->fAT, h.AT, c->fBT,
-                                  h.BT, c->Z, c->R, c->Xb[0], c->Xb[1], pa, k0, iters, c->bar, c->stream));
+        if (c->pfused)
+            SF_CUDA(launch_band_solve_fused(c->pgrid, c->psmem, c->m, c->n, c->r, c->fA, h.A, c->fB, h.B, c->fAT,
+                                            h.AT, c->fBT, h.BT, c->R, c->Xb[0], c->Xb[1], pa, k0, iters, c->bar,
+                                            c->stream));
+        else
+            SF_CUDA(launch_persistent(c->pgrid, c->psmem, c->prows_chunk, c->pcols_chunk, c->m, c->n, c->r, c->fA,
+                                      h.A, c->fB, h.B, c->fAT, h.AT, c->fBT, h.BT, c->Z, c->R, c->Xb[0], c->Xb[1], pa,
+                                      k0, iters, c->bar, c->stream));
         return SFISTA_OK;
     }
     if (!c->opts.use_graph) {
@@ -470,7 +476,9 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int ce
         // Measured on GB300: one kernel per operator application wins while the
         // halo rows it recomputes stay below ~1.5x the tile (band <= 48) and the
         // image is small enough for launch latency to dominate; otherwise the
-        // two-pass form.  Tensor-core forms default to band-aware GEMMs.
+        // two-pass form.  When every tile of the fused form also has its own
+        // resident block, the whole solve runs as one launch (below).
+        // Tensor-core forms default to band-aware GEMMs.
         const int wl = std::max(c->hs.B.w, c->hs.BT.w);
         const bool small = (size_t)img_rows * img_cols <= ((size_t)1 << 20) && wl <= 48;
         c->op = (c->prec == SFISTA_FP32) ? (small ? SFISTA_OP_BANDED_FUSED : SFISTA_OP_BANDED) : SFISTA_OP_GEMM_BAND;
@@ -526,12 +534,25 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int ce
         if (o.op == SFISTA_OP_BANDED_FUSED) return bail(fail(SFISTA_ENOTSUP, "fused banded tile exceeds shared memory"));
         c->op = SFISTA_OP_BANDED;   // automatic choice falls back to the two-pass form
     }
+    if (o.op == SFISTA_OP_AUTO && c->op == SFISTA_OP_BANDED_FUSED) {
+        int grid = 0;
+        size_t smem = 0;
+        if (band_solve_fused_config(c->m, c->n, c->r, h.A, h.B, h.AT, h.BT, c->dev, &grid, &smem))
+            c->op = SFISTA_OP_BANDED_PERSISTENT;
+    }
     if (c->op == SFISTA_OP_BANDED_PERSISTENT) {
-        if ((e = cudaMalloc((void **)&c->bar, 16)) || (e = cudaMemset(c->bar, 0, 16)))
+        if ((e = cudaMalloc((void **)&c->bar, kBarrierBytes)) || (e = cudaMemset(c->bar, 0, kBarrierBytes)))
             return bail(fail(SFISTA_ENOMEM, std::string("barrier words: ") + cudaGetErrorString(e)));
-        st = persistent_config(c->m, c->n, c->r, wmax, c->dev, &c->pgrid, &c->psmem, &c->prows_chunk,
-                               &c->pcols_chunk);
-        if (st) return bail(st);
+        c->pfused = band_solve_fused_config(c->m, c->n, c->r, h.A, h.B, h.AT, h.BT, c->dev, &c->pgrid, &c->psmem);
+        // Single operator applications (sfista_apply, the objective, reverse
+        // mode) then take the fused operator kernel as well.
+        if (c->pfused && !band_op_fused_prepare(c->r, std::max(h.A.w, h.AT.w), std::max(h.B.w, h.BT.w)))
+            c->pfused = 0;
+        if (!c->pfused) {
+            st = persistent_config(c->m, c->n, c->r, wmax, c->dev, &c->pgrid, &c->psmem, &c->prows_chunk,
+                                   &c->pcols_chunk);
+            if (st) return bail(st);
+        }
     }
     if (c->op == SFISTA_OP_GEMM_BAND || c->op == SFISTA_OP_GEMM_DENSE) {
         st = gemm_create(&c->gemm, h, c->prec, c->op == SFISTA_OP_GEMM_DENSE, c->status, c->stream);
@@ -631,7 +652,7 @@ sfista_status sfista_apply(sfista_ctx *c, const float *d_x, float *d_y, int tran
     SF_CUDA(cudaStreamWaitEvent(c->stream, c->ev_in, 0));
     const HostSetup &h = c->hs;
     ProxArgs pa{};
-    if (c->op == SFISTA_OP_BANDED_FUSED) {
+    if (fused_apply(c)) {
         const Band &F = transpose ? h.AT : h.A;
         const Band &G = transpose ? h.BT : h.B;
         launch_band_op_fused(d_x, c->m, c->n, c->r, transpose ? c->fAT : c->fA, F.lo, F.w, transpose ? c->fBT : c->fB,
@@ -664,7 +685,7 @@ sfista_status sfista_objective(sfista_ctx *c, const float *d_b, const float *d_x
     // A_s x into the scratch image, then the two sums of squares in FP64.
     const HostSetup &h = c->hs;
     ProxArgs pa{};
-    if (c->op == SFISTA_OP_BANDED_FUSED) {
+    if (fused_apply(c)) {
         launch_band_op_fused(d_x, c->m, c->n, c->r, c->fA, h.A.lo, h.A.w, c->fB, h.B.lo, h.B.w, EPI_STORE, c->tmp, pa,
                              c->stream);
     } else if (is_banded(c->op)) {
@@ -1090,6 +1111,28 @@ sfista_status time_stage_range(sfista_ctx *c, int s0, int s1, int reps, float *m
     return SFISTA_OK;
 }
 
+// Mean time per iteration of the one-launch solver over `iters` iterations
+// (one untimed launch of 2 iterations first).
+sfista_status time_persistent(sfista_ctx *c, int iters, float *ms) {
+    cudaEvent_t e0, e1;
+    SF_CUDA(cudaEventCreate(&e0));
+    SF_CUDA(cudaEventCreate(&e1));
+    sfista_status st = run_loop(c, 0.0, 0, 2);
+    cudaError_t e = cudaSuccess;
+    if (!st) e = cudaEventRecord(e0, c->stream);
+    if (!st && !e) st = run_loop(c, 0.0, 0, iters);
+    if (!st && !e) e = cudaEventRecord(e1, c->stream);
+    if (!st && !e) e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (!st && !e) e = cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    if (e) return fail(SFISTA_ECUDA, std::string("tuning: ") + cudaGetErrorString(e));
+    *ms = t / iters;
+    return SFISTA_OK;
+}
+
 }  // namespace
 
 sfista_status sfista_tune(sfista_ctx *c, int iters, sfista_tune_entry *entries, int max_entries, int *n_entries) {
@@ -1112,7 +1155,7 @@ sfista_status sfista_tune(sfista_ctx *c, int iters, sfista_tune_entry *entries, 
     };
     const HostSetup &h = c->hs;
     const bool auto_op = c->opts.op == SFISTA_OP_AUTO;
-    if (c->prec == SFISTA_FP32 && c->op != SFISTA_OP_BANDED_PERSISTENT) {
+    if (c->prec == SFISTA_FP32 && (auto_op || c->op != SFISTA_OP_BANDED_PERSISTENT)) {
         const int chosen = c->op;
         if (c->op == SFISTA_OP_BANDED || auto_op) {
             // Two-pass form: the term chunk of each stage, timed alone.
@@ -1145,6 +1188,25 @@ sfista_status sfista_tune(sfista_ctx *c, int iters, sfista_tune_entry *entries, 
                 if (st) return st;
                 log(SFISTA_OP_BANDED_FUSED, -1, 0, t_fused);
                 c->op = t_fused < t_two ? SFISTA_OP_BANDED_FUSED : SFISTA_OP_BANDED;
+                // The one-launch fused solver, when every tile has a resident block.
+                int grid = 0;
+                size_t smem = 0;
+                if (band_solve_fused_config(c->m, c->n, c->r, h.A, h.B, h.AT, h.BT, c->dev, &grid, &smem)) {
+                    if (!c->bar) {
+                        SF_CUDA(cudaMalloc((void **)&c->bar, kBarrierBytes));
+                        SF_CUDA(cudaMemset(c->bar, 0, kBarrierBytes));
+                    }
+                    const int best_op = c->op;
+                    c->op = SFISTA_OP_BANDED_PERSISTENT;
+                    c->pfused = 1;   // band_op_fused_prepare succeeded above
+                    c->pgrid = grid;
+                    c->psmem = smem;
+                    float t_one = 0.f;
+                    st = time_persistent(c, std::max(iters, 40), &t_one);
+                    if (st) return st;
+                    log(SFISTA_OP_BANDED_PERSISTENT, -1, 0, t_one);
+                    if (!(t_one < std::min(t_fused, t_two))) c->op = best_op;
+                }
             }
         } else {
             c->op = chosen;

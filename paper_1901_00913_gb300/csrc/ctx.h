@@ -52,8 +52,9 @@ struct sfista_ctx {
     // Terms per block of the two-pass banded stages 0..3 (0: default rule);
     // set by the autotuner.
     int chunk[4] = {0, 0, 0, 0};
-    // Persistent solver launch shape and its grid-barrier words.
-    int pgrid = 0, prows_chunk = 1, pcols_chunk = 1;
+    // Persistent solver launch shape and its grid-barrier words; pfused: the
+    // one-launch fused solver (every tile resident), else the two-pass one.
+    int pgrid = 0, prows_chunk = 1, pcols_chunk = 1, pfused = 0;
     size_t psmem = 0;
     unsigned *bar = nullptr;
     // Cached CUDA graph of the iteration loop.
@@ -63,6 +64,12 @@ struct sfista_ctx {
 };
 
 namespace sfista {
+
+// Single operator applications take the fused kernel (one launch each): the
+// fused form, and the one-launch solver that is built on it.
+inline bool fused_apply(const sfista_ctx *c) {
+    return c->op == SFISTA_OP_BANDED_FUSED || (c->op == SFISTA_OP_BANDED_PERSISTENT && c->pfused);
+}
 
 // Helpers of capi.cu used by the other C-ABI translation units.
 ProxArgs prox_args(sfista_ctx *c, int k, double lam);

@@ -112,6 +112,17 @@ cudaError_t launch_persistent(int grid, size_t smem, int rows_chunk, int cols_ch
                               const Band &BT, float *Z, float *R, float2 *Xb0, float2 *Xb1, const ProxArgs &pa,
                               int k0, int iters, unsigned *bar, cudaStream_t s);
 
+// The whole solve in one cooperative launch of the fused operator kernel
+// (kernels_fused.cu), when every 32 x 32 output tile has a resident block.
+bool band_solve_fused_config(int m, int n, int r, const Band &A, const Band &B, const Band &AT, const Band &BT,
+                             int dev, int *grid, size_t *smem);
+cudaError_t launch_band_solve_fused(int grid, size_t smem, int m, int n, int r, const float *fA, const Band &A,
+                                    const float *fB, const Band &B, const float *fAT, const Band &AT,
+                                    const float *fBT, const Band &BT, float *R, float2 *Xb0, float2 *Xb1,
+                                    const ProxArgs &pa, int k0, int iters, unsigned *bar, cudaStream_t s);
+// Bytes of grid-barrier words the persistent solvers use.
+constexpr size_t kBarrierBytes = 1024;
+
 // Grouped (batched) banded FP32 execution: one launch per stage over the
 // tiles of many problems of any size, rank and band.
 struct BandProb {

@@ -218,33 +218,15 @@ __device__ __forceinline__ void epi_load(const ProxArgs &pa, int m, int n, int a
     }
 }
 
-// VEC: 16-byte staging (n, m multiples of 4 and In 16-byte aligned);
+// Band tiles of the block's output tile (a0, c0): the row-pass coefficients of
+// its 32 columns and the column-pass coefficients of its 32 rows, every term.
+// VEC: 16-byte copies (n, m multiples of 4, buffers 16-byte aligned);
 // otherwise element-wise copies into the same layout.
-// PRE: the epilogue's operands are loaded at the start of the block, before
-// the programmatic wait, so their latency overlaps the staging and both
-// passes.  None of them is written by the preceding kernel, and every kernel
-// of the chain triggers its successor only after its own wait, so the kernel
-// that wrote them has completed.  It holds about 30-50 more registers (two
-// blocks per SM instead of three); the host takes it when every tile is
-// resident at two blocks per SM.
-template <int EPI, bool VEC, bool PRE>
-__global__ void __launch_bounds__(NT, PRE ? 2 : 0) band_op_fused_kernel(const float *__restrict__ In, int m, int n, int r,
-                                                           const float *__restrict__ Fb, int loF, int wF,
-                                                           const float *__restrict__ Gb, int loG, int wG,
-                                                           float *__restrict__ Out, ProxArgs pa) {
-    extern __shared__ __align__(16) float sm[];
-    const FusedGeom geo = fused_geom(r, loF, wF, wG);
-    float *Ins = sm, *Fs = sm + geo.off_f, *Gs = sm + geo.off_g, *Zs = sm + geo.off_z;
+template <bool VEC>
+__device__ __forceinline__ void stage_bands(const FusedGeom &geo, int r, const float *__restrict__ Fb, int wF,
+                                            const float *__restrict__ Gb, int wG, int m, int n, int a0, int c0,
+                                            float *Fs, float *Gs) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int a0 = blockIdx.y * TA, c0 = blockIdx.x * TC;
-    const int e0 = a0 + loG;                   // first staged row
-    const int colbase = c0 + loF - geo.off;    // first staged column (4-aligned)
-    const int width = TC + geo.wF4;            // staged columns
-    const int rb = warp * 4, gc = c0 + lane;   // epilogue: rows a0 + rb .. + 3 of column gc
-    float bv[4];
-    float2 yv[4], xv[4], beta = make_float2(0.f, 0.f);
-    if (PRE) epi_load<EPI>(pa, m, n, a0 + rb, gc, bv, yv, xv, beta);
-    // Constant band tiles first, then (after the previous kernel) the input tile.
     if (VEC) {
         const int tr = tid >> 3, j = tid & 7;
         const int fb = c0 + 4 * j < n ? 16 : 0, gb = a0 + 4 * j < m ? 16 : 0;
@@ -277,7 +259,15 @@ __global__ void __launch_bounds__(NT, PRE ? 2 : 0) band_op_fused_kernel(const fl
             }
         }
     }
-    band::pdl_wait();
+}
+
+// Input tile with its halo: rows e0 .. e0 + zs - 1 (the rest of the 32-row
+// groups zero), columns from the 4-aligned colbase, zero outside the image.
+template <bool VEC>
+__device__ __forceinline__ void stage_input(const FusedGeom &geo, const float *__restrict__ In, int m, int n, int e0,
+                                            int colbase, float *Ins) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int width = TC + geo.wF4;   // staged columns
     if (VEC) {
         const int nch = width >> 2;
         const int lsh = nch <= 8 ? 3 : (nch <= 16 ? 4 : 5);   // threads per staged row: 1 << lsh
@@ -304,9 +294,14 @@ __global__ void __launch_bounds__(NT, PRE ? 2 : 0) band_op_fused_kernel(const fl
             }
         }
     }
-    band::stage_wait<false>();
-    __syncthreads();
-    // Row pass: Z_i for rows [0, zs) into Zt.
+}
+
+// Both passes on the staged tile (the caller has waited for the copies and
+// synchronised): Z_i for rows [0, zs) into Zt, then the column pass added
+// into acc (rows rb .. rb + 3 of the lane's column, terms summed in order).
+__device__ __forceinline__ void fused_passes(const FusedGeom &geo, int r, const float *Ins, const float *Fs,
+                                             const float *Gs, float *Zs, float *acc) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int cb = warp * 4;
     for (int rbase = 0; rbase < geo.zs; rbase += 64) {
         const int e = rbase + lane;
@@ -329,8 +324,7 @@ __global__ void __launch_bounds__(NT, PRE ? 2 : 0) band_op_fused_kernel(const fl
         }
     }
     __syncthreads();
-    // Column pass: lane l column c0 + l, warp w rows a0 + 4w .. a0 + 4w + 3.
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const int rb = warp * 4;
     for (int tb = 0; tb < r; tb += 4) {
         const float *zc = Zs + (size_t)(tb * TC + lane) * geo.zsp + rb;
         const float *gr = Gs + tb * geo.wG4 * TA + rb;
@@ -341,6 +335,39 @@ __global__ void __launch_bounds__(NT, PRE ? 2 : 0) band_op_fused_kernel(const fl
             default: cols_pass<4>(zc, geo.zsp, gr, geo.wG4, acc); break;
         }
     }
+}
+
+// PRE: the epilogue's operands are loaded at the start of the block, before
+// the programmatic wait, so their latency overlaps the staging and both
+// passes.  None of them is written by the preceding kernel, and every kernel
+// of the chain triggers its successor only after its own wait, so the kernel
+// that wrote them has completed.  It holds about 30-50 more registers (two
+// blocks per SM instead of three); the host takes it when every tile is
+// resident at two blocks per SM.
+template <int EPI, bool VEC, bool PRE>
+__global__ void __launch_bounds__(NT, PRE ? 2 : 0) band_op_fused_kernel(const float *__restrict__ In, int m, int n, int r,
+                                                           const float *__restrict__ Fb, int loF, int wF,
+                                                           const float *__restrict__ Gb, int loG, int wG,
+                                                           float *__restrict__ Out, ProxArgs pa) {
+    extern __shared__ __align__(16) float sm[];
+    const FusedGeom geo = fused_geom(r, loF, wF, wG);
+    float *Ins = sm, *Fs = sm + geo.off_f, *Gs = sm + geo.off_g, *Zs = sm + geo.off_z;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int a0 = blockIdx.y * TA, c0 = blockIdx.x * TC;
+    const int e0 = a0 + loG;                   // first staged row
+    const int colbase = c0 + loF - geo.off;    // first staged column (4-aligned)
+    const int rb = warp * 4, gc = c0 + lane;   // epilogue: rows a0 + rb .. + 3 of column gc
+    float bv[4];
+    float2 yv[4], xv[4], beta = make_float2(0.f, 0.f);
+    if (PRE) epi_load<EPI>(pa, m, n, a0 + rb, gc, bv, yv, xv, beta);
+    // Constant band tiles first, then (after the previous kernel) the input tile.
+    stage_bands<VEC>(geo, r, Fb, wF, Gb, wG, m, n, a0, c0, Fs, Gs);
+    band::pdl_wait();
+    stage_input<VEC>(geo, In, m, n, e0, colbase, Ins);
+    band::stage_wait<false>();
+    __syncthreads();
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    fused_passes(geo, r, Ins, Fs, Gs, Zs, acc);
     if (!PRE) epi_load<EPI>(pa, m, n, a0 + rb, gc, bv, yv, xv, beta);
     size_t idx[4];
     bool ok[4];
@@ -353,6 +380,189 @@ __global__ void __launch_bounds__(NT, PRE ? 2 : 0) band_op_fused_kernel(const fl
             if (ok[j]) Out[idx[j]] = EPI == EPI_STORE ? acc[j] : acc[j] - bv[j];
     }
     band::pdl_trigger();
+}
+
+// ---------------------------------------------------------------------------
+// The whole solve in one cooperative launch, when every output tile has its
+// own resident block (tiles <= co-resident blocks).  Each block keeps, for
+// the whole solve,
+//   - the band tiles of both operator applications (A, B and A^T, B^T) in
+//     shared memory (staged once),
+//   - the double-float state (Y_k, X_{k-1}) and the observed image of its
+//     epilogue pixels in registers (the epilogue's pixel -> thread map is the
+//     same in every iteration),
+// and per iteration runs the forward application with the residual
+// epilogue and the adjoint application with Step 1 + Step 3.  Only R and
+// the FP32 operand copy of Y_{k+1} go through global memory (other blocks
+// read them as halo); X and Y are written once at the end.  Data that
+// another block wrote in this launch is read with 16-byte cp.async.cg
+// copies (L2, not the non-coherent L1).
+// A grid barrier separates the phases (it orders the halo reads of R and of
+// the operand copy of Y after their writes, and their next overwrite after
+// the reads).  Its wait is bounded (about one second); a block that gives up
+// records DEV_TIMEOUT and returns.
+struct FusedSolveArgs {
+    int m, n, r;
+    const float *fA, *fB, *fAT, *fBT;
+    int loA, wA, loB, wB, loAT, wAT, loBT, wBT;
+    float *R;
+    ProxArgs pa;           // Bd, Y, Yop, beta, constants, status
+    float2 *Xb0, *Xb1;     // X_{k0} in Xb[k0 & 1]; X_{k0+iters} goes to Xb[(k0+iters) & 1]
+    int k0, iters;
+    unsigned *bar;         // kBarWords arrival counters, 32 words apart, zero at launch
+};
+
+constexpr int kBarWords = 8;
+constexpr long long kSpinCycles = 2000000000LL;   // about one second
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier number `nth` (1, 2, ...): every block adds one to counter
+// blockIdx % kBarWords, and warp 0 polls the kBarWords counters (one lane
+// each) until their sum reaches nth * gridDim.x.  The poll is bounded; a
+// block that gives up records DEV_TIMEOUT and returns false.
+__device__ bool fused_grid_sync(unsigned *bar, unsigned nth, unsigned *status, int *abort_sh) {
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        if (lane == 0) {
+            __threadfence();
+            atomicAdd(bar + 32 * (blockIdx.x % kBarWords), 1u);
+        }
+        __syncwarp();
+        const unsigned target = nth * gridDim.x;
+        const long long t0 = clock64();
+        for (;;) {
+            const unsigned v = lane < kBarWords ? ld_acquire(bar + 32 * lane) : 0u;
+            if (__reduce_add_sync(0xffffffffu, v) >= target) break;
+            if (clock64() - t0 > kSpinCycles) {
+                if (lane == 0) {
+                    atomicOr(status, DEV_TIMEOUT);
+                    *abort_sh = 1;
+                }
+                break;
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *abort_sh == 0;
+}
+
+struct SolveLayout {
+    FusedGeom gf, gt;            // forward (A, B) and adjoint (A^T, B^T) geometry
+    size_t off_ff, off_gf, off_ft, off_gt, off_z, total;   // float offsets / size
+};
+
+__host__ __device__ inline SolveLayout solve_layout(int r, int loA, int wA, int wB, int loAT, int wAT, int wBT) {
+    SolveLayout L;
+    L.gf = fused_geom(r, loA, wA, wB);
+    L.gt = fused_geom(r, loAT, wAT, wBT);
+    const size_t in = (size_t)max(L.gf.rows * L.gf.sp, L.gt.rows * L.gt.sp);
+    L.off_ff = in;
+    L.off_gf = L.off_ff + (size_t)r * L.gf.wF4 * TC;
+    L.off_ft = L.off_gf + (size_t)r * L.gf.wG4 * TA;
+    L.off_gt = L.off_ft + (size_t)r * L.gt.wF4 * TC;
+    L.off_z = L.off_gt + (size_t)r * L.gt.wG4 * TA;
+    L.total = L.off_z + (size_t)r * TC * max(L.gf.zsp, L.gt.zsp);
+    return L;
+}
+
+// One operator application of the one-launch solver on this block's tile;
+// the geometry and shared-memory offsets come from shared memory (read
+// again in every phase, so they do not hold registers across the loop).
+__device__ __forceinline__ void solve_phase(const FusedGeom &g, const float *In, int m, int n, int r, int lo_rows,
+                                            int lo_cols, size_t off_f, size_t off_g, size_t off_z, float *sm, int a0,
+                                            int c0, float *acc) {
+    stage_input<true>(g, In, m, n, a0 + lo_rows, c0 + lo_cols - g.off, sm);
+    band::stage_wait<false>();
+    __syncthreads();
+    fused_passes(g, r, sm, sm + off_f, sm + off_g, sm + off_z, acc);
+}
+
+__global__ void __launch_bounds__(NT, 2) band_solve_fused(FusedSolveArgs a) {
+    extern __shared__ __align__(16) float sm[];
+    __shared__ SolveLayout Ls;
+    __shared__ int abort_sh;
+    const int m = a.m, n = a.n, r = a.r;
+    const int tiles_c = (n + TC - 1) / TC;
+    const int a0 = (blockIdx.x / tiles_c) * TA, c0 = (blockIdx.x % tiles_c) * TC;
+    if (threadIdx.x == 0) {
+        abort_sh = 0;
+        Ls = solve_layout(r, a.loA, a.wA, a.wB, a.loAT, a.wAT, a.wBT);
+    }
+    __syncthreads();
+    {
+        const SolveLayout L = Ls;
+        stage_bands<true>(L.gf, r, a.fA, a.wA, a.fB, a.wB, m, n, a0, c0, sm + L.off_ff, sm + L.off_gf);
+        stage_bands<true>(L.gt, r, a.fAT, a.wAT, a.fBT, a.wBT, m, n, a0, c0, sm + L.off_ft, sm + L.off_gt);
+    }
+    const int rb = (threadIdx.x >> 5) * 4, gc = c0 + (threadIdx.x & 31);   // epilogue pixels
+    float2 y[4], xp[4];
+    {
+        ProxArgs pa = a.pa;
+        pa.Xin = (a.k0 & 1) ? a.Xb1 : a.Xb0;
+        size_t idx[4];
+        bool ok[4];
+        epi_index(m, n, a0 + rb, gc, idx, ok);
+        prox_load_n<4>(pa, idx, ok, y, xp);
+    }
+    const int kend = a.k0 + a.iters;
+    unsigned nth = 0;
+    for (int k = a.k0 + 1; k <= kend; ++k) {
+        // Forward operator + residual: R = A_s Y_k - B.
+        {
+            size_t idx[4];
+            bool ok[4];
+            epi_index(m, n, a0 + rb, gc, idx, ok);
+            float bv[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bv[j] = ok[j] ? __ldcg(a.pa.Bd + idx[j]) : 0.f;
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            solve_phase(Ls.gf, a.pa.Yop, m, n, r, a.loB, a.loA, Ls.off_ff, Ls.off_gf, Ls.off_z, sm, a0, c0, acc);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (ok[j]) a.R[idx[j]] = acc[j] - bv[j];
+        }
+        if (!fused_grid_sync(a.bar, ++nth, a.pa.status, &abort_sh)) return;
+        // Adjoint + Step 1 shrink + Step 3 momentum.
+        {
+            const float2 beta = a.pa.beta[k - 1];
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            solve_phase(Ls.gt, a.R, m, n, r, a.loBT, a.loAT, Ls.off_ft, Ls.off_gt, Ls.off_z, sm, a0, c0, acc);
+            size_t idx[4];
+            bool ok[4];
+            epi_index(m, n, a0 + rb, gc, idx, ok);
+            float2 *Xlast = ((k - 1) & 1) ? a.Xb1 : a.Xb0;   // X_{k-1}: kept for a resumed solve
+            bool bad = false;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (!ok[j]) continue;
+                float2 x;
+                const float2 yn = prox_step(a.pa, y[j], xp[j], acc[j], beta, &x, &bad);
+                store_operands(a.pa, idx[j], yn);
+                if (k == kend) Xlast[idx[j]] = xp[j];
+                xp[j] = x;
+                y[j] = yn;
+            }
+            if (bad) atomicOr(a.pa.status, DEV_NONFINITE);
+        }
+        if (!fused_grid_sync(a.bar, ++nth, a.pa.status, &abort_sh)) return;
+    }
+    size_t idx[4];
+    bool ok[4];
+    epi_index(m, n, a0 + rb, gc, idx, ok);
+    float2 *Xout = (kend & 1) ? a.Xb1 : a.Xb0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (ok[j]) {
+            Xout[idx[j]] = xp[j];
+            a.pa.Y[idx[j]] = y[j];
+        }
 }
 
 constexpr size_t kFusedSmemMax = 227 * 1024;
@@ -422,6 +632,60 @@ void launch_band_op_fused(const float *In, int m, int n, int r, const float *Fb,
         launch_epi<EPI_RESIDUAL>(cfg, vec, pre, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out, pa);
     else
         launch_epi<EPI_PROX>(cfg, vec, pre, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out, pa);
+}
+
+// Grid and shared memory of the one-launch fused solver; false when a tile
+// does not fit, the 16-byte path does not apply, or the tiles outnumber the
+// co-resident blocks (the caller then takes the two-pass persistent solver).
+bool band_solve_fused_config(int m, int n, int r, const Band &A, const Band &B, const Band &AT, const Band &BT,
+                             int dev, int *grid, size_t *smem) {
+    if (m % 4 || n % 4) return false;
+    *smem = sizeof(float) * solve_layout(r, A.lo, A.w, B.w, AT.lo, AT.w, BT.w).total;
+    if (*smem > kFusedSmemMax) return false;
+    if (cudaFuncSetAttribute(band_solve_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem) != cudaSuccess)
+        return false;
+    int per_sm = 0, sms = 0, coop = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, band_solve_fused, NT, *smem) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess)
+        return false;
+    const long tiles = (long)((m + TA - 1) / TA) * ((n + TC - 1) / TC);
+    if (!coop || per_sm < 1 || tiles > (long)per_sm * sms) return false;
+    *grid = (int)tiles;
+    return true;
+}
+
+cudaError_t launch_band_solve_fused(int grid, size_t smem, int m, int n, int r, const float *fA, const Band &A,
+                                    const float *fB, const Band &B, const float *fAT, const Band &AT,
+                                    const float *fBT, const Band &BT, float *R, float2 *Xb0, float2 *Xb1,
+                                    const ProxArgs &pa, int k0, int iters, unsigned *bar, cudaStream_t s) {
+    FusedSolveArgs a{};
+    a.m = m;
+    a.n = n;
+    a.r = r;
+    a.fA = fA;
+    a.fB = fB;
+    a.fAT = fAT;
+    a.fBT = fBT;
+    a.loA = A.lo;
+    a.wA = A.w;
+    a.loB = B.lo;
+    a.wB = B.w;
+    a.loAT = AT.lo;
+    a.wAT = AT.w;
+    a.loBT = BT.lo;
+    a.wBT = BT.w;
+    a.R = R;
+    a.pa = pa;
+    a.Xb0 = Xb0;
+    a.Xb1 = Xb1;
+    a.k0 = k0;
+    a.iters = iters;
+    a.bar = bar;
+    cudaError_t e = cudaMemsetAsync(bar, 0, kBarrierBytes, s);
+    if (e) return e;
+    void *args[] = {&a};
+    return cudaLaunchCooperativeKernel((const void *)band_solve_fused, dim3(grid), dim3(NT), args, smem, s);
 }
 
 }  // namespace sfista

@@ -188,6 +188,33 @@ def test_solve_ragged(bc, op):
     s.close()
 
 
+@pytest.mark.parametrize("m,n", [(200, 176), (202, 178), (640, 512)])
+def test_persistent_forms_match_oracle(m, n):
+    """The one-launch solver takes the fused form (band tiles and state resident)
+    when m, n are multiples of 4 and every 32 x 32 tile has a co-resident block
+    (200 x 176), else the two-pass form (202 x 178: not multiples of 4;
+    640 x 512: 320 tiles, more than two per SM).  Both against the oracle, and
+    a resumed solve against the uninterrupted one."""
+    P = W.rotated_gaussian_psf(31, 3.0, 1.0, 0.5)
+    x, b, _ = _problem(m, n, P, 1, 108)
+    ka = kron.kron_approx(P, 15, 15, m, n, 1, 3)
+    L = _oracle_L(ka)
+    iters = 24
+    Xo = oracle.sfista(b.astype(np.float64), ka, L, 0.005, iters)
+    s = api.Sfista(P, (m, n), 1, 3, prec="fp32", op="banded_persistent", lipschitz=L)
+    db = _cuda(b)
+    X = s.solve_device(db, 0.005, iters).cpu().numpy()
+    assert oracle.rel_fro(X, Xo) <= TOL["fp32"]
+    ref = torch.zeros(m, n, dtype=torch.float64, device="cuda")
+    s.solve_state(db, 0.005, 0, iters, ref, torch.zeros_like(ref))
+    Xs, Xp = torch.zeros_like(ref), torch.zeros_like(ref)
+    s.solve_state(db, 0.005, 0, 10, Xs, Xp)
+    s.solve_state(db, 0.005, 10, iters - 10, Xs, Xp)
+    assert torch.max(torch.abs(Xs - ref)).item() <= 1e-12
+    assert oracle.rel_fro(ref.cpu().numpy(), Xo) <= TOL["fp32"]
+    s.close()
+
+
 def test_graph_and_direct_launch_agree():
     P = W.rotated_gaussian_psf(15, 2.0, 1.0, 0.3)
     x, b, _ = _problem(96, 80, P, 1, 106)
