@@ -37,7 +37,18 @@ KERNELS_PER_ITER = {"banded": 4, "banded_fused": 2, "gemm_band": 4, "gemm_dense"
 # DRAM bytes (read + write) per launch of a form's dominant kernel, from an
 # ncu capture of the current kernel code on this workload (the summary in
 # profiles/ gives the command); forms without one report null.
-TRAFFIC = {}
+TRAFFIC = {
+    "fp32:banded_persistent:0": {
+        "bytes": 7.421952e6 / 20,
+        "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 20-iteration band_solve_fused "
+                  "launch / 20 (per iteration, the unit of achieved), profiles/solve_fused_fp32_cfg2_512_r3.md"},
+    "fp32:banded_fused:0": {
+        "bytes": 2.542336e6,
+        "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, profiles/banded_fused_fp32_cfg2_512_r3.md"},
+    "fp32:banded_fused:2": {
+        "bytes": 5.697024e6,
+        "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, profiles/banded_fused_fp32_cfg2_512_r3.md"},
+}
 
 
 def one_launch_fused(m, n):
