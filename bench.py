@@ -577,6 +577,131 @@ def run_example2(args, torch):
     print(json.dumps(line), flush=True)
 
 
+def _fft_len(L):
+    """Smallest 2^a 3^b 5^c >= L (sizes cuFFT handles with its fast radices)."""
+    best = 1 << (L - 1).bit_length()
+    a = 1
+    while a < 2 * L:
+        b = a
+        while b < 2 * L:
+            c = b
+            while c < best:
+                if c >= L:
+                    best = c
+                c *= 5
+            b *= 3
+        a *= 2
+    return best
+
+
+def _corr_lines(torch, X, T, lo, bc, summed):
+    """1-D factor applications along the last axis of X (lines of length n):
+    out_k[.., c] = sum_j T[k, j] * ext(X)[.., c + lo + j], ext the zero (bc 0) or
+    half-sample reflected (bc 1) extension, as circular correlations of length
+    N >= n + w - 1 (so no wrap-around) by real FFTs.  summed: the sum over k,
+    else one output per k."""
+    n, (r, w) = X.shape[-1], T.shape
+    L = n + w - 1
+    N = _fft_len(L)
+    t = torch.arange(L, device=X.device) + lo
+    if bc == 1:
+        t = torch.where(t < 0, -1 - t, torch.where(t >= n, 2 * n - 1 - t, t))
+    ok = (t >= 0) & (t < n)
+    E = torch.index_select(X, -1, t.clamp(0, n - 1)) * ok.to(X.dtype)
+    Tf = torch.fft.rfft(T.to(X.dtype), n=N).conj()
+    shape = (r,) + (1,) * (X.dim() - (2 if summed else 1)) + (Tf.shape[-1],)
+    prod = torch.fft.rfft(E, n=N) * Tf.reshape(shape)
+    if summed:
+        prod = prod.sum(0)
+    return torch.fft.irfft(prod, n=N)[..., :n]
+
+
+def fft_kron_apply(torch, Y, C, cr, D, cc, bc):
+    """sum_k B_k Y A_k^T (Sec. 2's matrix form of the Kronecker sum) with every
+    1-D factor applied as the paper's structured product: toep (bc 0) or
+    toep + hank (bc 1) of the profile, i.e. a correlation of the extended line
+    with the reversed profile, computed by FFT.  Y (m, n); C (r, p) column
+    profiles (left factors B_k, centre cr); D (r, q) row profiles (right
+    factors A_k, centre cc)."""
+    p, q = C.shape[1], D.shape[1]
+    Z = _corr_lines(torch, Y, D.flip(-1), cc - (q - 1), bc, False)               # (r, m, n): Y A_k^T
+    out = _corr_lines(torch, Z.transpose(-1, -2), C.flip(-1), cr - (p - 1), bc, True)   # (n, m)
+    return out.transpose(-1, -2)
+
+
+def run_fft(args, torch):
+    """The operator A_s applied once, three ways: the library's banded FP32 form
+    (the automatic FP32 choice), its BF16x3 tensor-core form, and the FFT
+    structured product (cuFFT through torch.fft, FP32, unfused, replayed as a
+    CUDA graph).  Timed with CUDA events over back-to-back applications; error
+    of each against the FP64 oracle's operator on the same input."""
+    from paper_1901_00913_gb300 import api, build, workloads as W
+    import oracle
+    from oracle import kron
+    build.build()
+    api.load()
+    res = {}
+    for name, cfg in (("cfg2", W.config2), ("cfg3", W.config3)):
+        pr = cfg()
+        n = pr.x_true.shape[0]
+        cr, cc = pr.centre
+        X = torch.from_numpy(pr.x_true.astype(np.float32)).cuda()
+        ka = kron.kron_approx(pr.psf, cr, cc, n, n, pr.bc, pr.r)
+        t0 = time.perf_counter()
+        Yo = oracle.kron_apply(pr.x_true, ka)
+        cpu_s = time.perf_counter() - t0
+        forms = {}
+        s32 = api.Sfista(pr.psf, (n, n), pr.bc, pr.r, prec="fp32", op="auto", lipschitz=1.0)
+        C, D = s32.profiles()
+        Cd, Dd = torch.from_numpy(C).float().cuda(), torch.from_numpy(D).float().cuda()
+
+        # The FFT form's ~14 torch operations replayed as one CUDA graph, so
+        # its time is device time (no per-operation host dispatch).
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(3):
+                fft_kron_apply(torch, X, Cd, cr, Dd, cc, pr.bc)
+        torch.cuda.current_stream().wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            Yfft = fft_kron_apply(torch, X, Cd, cr, Dd, cc, pr.bc)
+
+        def fft_form():
+            graph.replay()
+            return Yfft
+
+        sbf = api.Sfista(pr.psf, (n, n), pr.bc, pr.r, prec="bf16x3", op="gemm_band", lipschitz=1.0)
+        out = torch.empty_like(X)
+        cands = [("fp32 banded (%s)" % s32.info()["op"], lambda: s32.apply(X, out=out, sync=False)),
+                 ("bf16x3 tcgen05 gemm_band", lambda: sbf.apply(X, out=out, sync=False)),
+                 ("fp32 FFT structured product (cuFFT, one CUDA graph)", fft_form)]
+        for label, fn in cands:
+            for _ in range(3):
+                Yg = fn()
+            torch.cuda.synchronize()
+            reps = 50 if n <= 512 else 10
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                Yg = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            Yg = fn()
+            torch.cuda.synchronize()
+            forms[label] = {"us_per_application": 1e3 * ms, "applications_per_s": 1e3 / ms,
+                            "rel_err_vs_fp64_oracle": oracle.rel_fro(Yg.double().cpu().numpy(), Yo)}
+        s32.close()
+        sbf.close()
+        res[name] = {"workload": "%s: %dx%d, %dx%d PSF, r=%d, reflexive" % (pr.name, n, n, pr.psf.shape[0],
+                                                                              pr.psf.shape[1], pr.r),
+                     "forms": forms, "oracle_cpu_s": cpu_s}
+    print(json.dumps({"metric": "operator applications/s (A_s once) by form", "workload": "fft",
+                      "unit": "applications/s", "data": "synthetic", "timing": "CUDA events, back-to-back, warm L2",
+                      "configs": res}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -585,7 +710,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--forms", default="fp32:auto+tune,fp32:banded_fused,fp32:banded,fp32:banded_persistent,bf16x3:gemm_band,tf32x3:gemm_band,bf16:gemm_band,tf32:gemm_band",
                     help="comma list of prec:op forms to measure")
-    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "cfg4", "cfg5", "ex2"])
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "cfg4", "cfg5", "ex2", "fft"])
     ap.add_argument("--check-iters", type=int, default=10)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -593,6 +718,8 @@ def main():
         return run_reference(args)
     if args.workload != "cfg2":
         import torch
+        if args.workload == "fft":
+            return run_fft(args, torch)
         if args.forms.startswith("fp32:auto+tune,fp32:banded_fused,fp32:banded,fp32:banded_persistent"):
             args.forms = {"cfg3": "fp32:auto+tune,fp32:banded_fused,fp32:banded,bf16x3:auto+tune,bf16x3:gemm_band,"
                                   "tf32x3:gemm_band,bf16x3:gemm_dense",
