@@ -1,9 +1,11 @@
 // FP32 tile routines of the two-pass banded operator with 16-byte accesses, on
 // RT x 32 output tiles with RT = 64 (large images) or 32 (small ones, where
-// 64-row tiles would leave SMs idle).  The standalone and grouped kernels take
-// them when m and n are multiples of 4 and the buffers 16-byte aligned
-// (decided on the host, which also sizes the grid); otherwise the 32-row
-// scalar routines of band_items.cuh run.  One block has 256 threads (8 warps).
+// 64-row tiles would leave SMs idle); the standalone columns pass also has a
+// 128-row form with two columns per thread (end of this file).  The
+// standalone and grouped kernels take them when m and n are multiples of 4
+// and the buffers 16-byte aligned (decided on the host, which also sizes the
+// grid); otherwise the 32-row scalar routines of band_items.cuh run.  One
+// block has 256 threads (8 warps).
 //
 // Tap padding.  Both passes step through the taps four at a time.  The rows
 // pass stages its input tile from the 4-aligned column c0 + lo - off
@@ -269,6 +271,155 @@ __device__ __forceinline__ void cols_item(const float *__restrict__ Z, int m, in
     }
 #pragma unroll
     for (int h = 0; h < RW / 4; ++h) band::cols_epilogue<float, EPI>(acc + 4 * h, m, n, a0, rb + 4 * h, c0 + lane, Out, pa);
+    band::pdl_trigger();
+}
+
+// ---------------------------------------------------------------------------
+// Columns pass on 128 x 32 tiles (large images): each thread owns two
+// adjacent columns and 8 rows, so one broadcast 16-byte coefficient load
+// feeds 8 FMAs and one 8-byte Z load (two columns of one row) feeds the
+// window of both columns.  Lane l: column pair l % 16, row group l / 16;
+// warp w: rows 16 w + 8 (l / 16) .. + 7.  Taps and terms are summed in the
+// same order as the 64-row routine, so both give the same result bit for bit.
+
+__device__ __forceinline__ float2 lds2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+
+// Four taps for the thread's 8 rows x 2 columns: z holds rows rb + k ..
+// rb + k + 11 of its two columns, gk the coefficients of tap k (row stride TA).
+template <int TA>
+__device__ __forceinline__ void cols_taps4_2(const float2 (&z)[12], const float *gk, float (&a)[8][2]) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float4 g = lds4(gk + u * TA + 4 * h);
+            const float gv[4] = {g.x, g.y, g.z, g.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                a[4 * h + i][0] = fmaf(gv[i], z[u + 4 * h + i].x, a[4 * h + i][0]);
+                a[4 * h + i][1] = fmaf(gv[i], z[u + 4 * h + i].y, a[4 * h + i][1]);
+            }
+        }
+    }
+}
+
+// One term: zc is the staged Z at (row rb, the thread's first column), gr the
+// term's coefficients of rows rb .. rb + 7 (row stride TA).
+template <int TA>
+__device__ __forceinline__ void cols_term2(const float *zc, const float *gr, int w4, float (&acc)[8][2]) {
+    float a[8][2];
+    float2 w0[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        a[i][0] = a[i][1] = 0.f;
+        w0[i] = lds2(zc + i * TC);
+    }
+    int k = 0;
+#pragma unroll 1
+    for (; k + 8 <= w4; k += 8) {
+        float2 n8[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) n8[i] = lds2(zc + (k + 8 + i) * TC);
+        float2 za[12], zb[12];
+#pragma unroll
+        for (int i = 0; i < 12; ++i) {
+            za[i] = i < 8 ? w0[i] : n8[i - 8];
+            zb[i] = i < 4 ? w0[i + 4] : n8[i - 4];
+        }
+        cols_taps4_2<TA>(za, gr + k * TA, a);
+        cols_taps4_2<TA>(zb, gr + (k + 4) * TA, a);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) w0[i] = n8[i];
+    }
+    if (k < w4) {
+        float2 z[12];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) z[i] = w0[i];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) z[8 + i] = lds2(zc + (k + 8 + i) * TC);
+        cols_taps4_2<TA>(z, gr + k * TA, a);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        acc[i][0] += a[i][0];
+        acc[i][1] += a[i][1];
+    }
+}
+
+// sum_i G_i Z_i over all r terms (`chunk` staged per load phase) for the
+// 128 x 32 tile at (a0, c0), then the epilogue on pixel pairs.
+template <int EPI>
+__device__ __forceinline__ void cols_item128(const float *__restrict__ Z, int m, int n, int r, int chunk,
+                                             const float *__restrict__ Gb, int lo, int w, int a0, int c0,
+                                             float *__restrict__ Out, const ProxArgs &pa, float *sm) {
+    constexpr int TA = 128;
+    const int w4 = cols_taps(w), zs = TA + w4;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cp = lane & 15, rb = warp * 16 + (lane >> 4) * 8;
+    const int jz = tid & 7, trz = tid >> 3;     // Z rows: 8 chunks of 4 columns, 32 rows per pass
+    const int jg = tid & 31, trg = tid >> 5;    // coefficient rows: 32 chunks of 4 rows, 8 taps per pass
+    const bool cok = c0 + 4 * jz < n, rok = a0 + 4 * jg < m;
+    float acc[8][2];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i][0] = acc[i][1] = 0.f;
+    for (int t0 = 0; t0 < r; t0 += chunk) {
+        const int nt = min(chunk, r - t0);
+        float *Zs = sm;                    // nt x zs x TC
+        float *Gs = sm + nt * zs * TC;     // nt x w4 x TA
+        for (int q = 0; q < nt; ++q)
+            for (int kp = trg; kp < w4; kp += NT / 32) {
+                const bool ok = kp < w && rok;
+                band::stage16(Gs + (q * w4 + kp) * TA + 4 * jg,
+                              Gb + ((size_t)(t0 + q) * w + (kp < w ? kp : 0)) * m + a0 + 4 * jg, ok ? 16 : 0, Gb);
+            }
+        band::pdl_wait();
+        for (int q = 0; q < nt; ++q) {
+            const float *zt = Z + (size_t)(t0 + q) * m * n;
+            for (int e = trz; e < zs; e += NT / 8) {
+                const int ge = a0 + lo + e;
+                const bool ok = cok && ge >= 0 && ge < m;
+                band::stage16(Zs + (q * zs + e) * TC + 4 * jz, zt + (size_t)(ok ? ge : 0) * n + c0 + 4 * jz,
+                              ok ? 16 : 0, Z);
+            }
+        }
+        band::stage_wait<false>();
+        __syncthreads();
+        for (int q = 0; q < nt; ++q)
+            cols_term2<TA>(Zs + (q * zs + rb) * TC + 2 * cp, Gs + q * w4 * TA + rb, w4, acc);
+        __syncthreads();
+    }
+    const int c = c0 + 2 * cp;
+    if (c < n) {   // n is a multiple of 4: the pair is all inside or all outside
+        if (EPI == EPI_PROX) {
+            size_t idx[8];
+            float g0[8], g1[8];
+            bool ok[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                ok[i] = a0 + rb + i < m;
+                idx[i] = (size_t)(a0 + rb + i) * n + c;
+                g0[i] = acc[i][0];
+                g1[i] = acc[i][1];
+            }
+            prox_momentum2_n<8>(pa, idx, g0, g1, ok);
+        } else {
+            float2 bv[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const size_t idx = (size_t)(a0 + rb + i) * n + c;
+                bv[i] = EPI == EPI_RESIDUAL && a0 + rb + i < m ? __ldcg(reinterpret_cast<const float2 *>(pa.Bd + idx))
+                                                               : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (a0 + rb + i >= m) break;
+                const size_t idx = (size_t)(a0 + rb + i) * n + c;
+                *reinterpret_cast<float2 *>(Out + idx) =
+                    EPI == EPI_STORE ? make_float2(acc[i][0], acc[i][1])
+                                     : make_float2(acc[i][0] - bv[i].x, acc[i][1] - bv[i].y);
+            }
+        }
+    }
     band::pdl_trigger();
 }
 

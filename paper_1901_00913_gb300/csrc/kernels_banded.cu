@@ -65,6 +65,15 @@ __global__ void __launch_bounds__(band::NT) band_cols_kernel4(const float *__res
     band4::cols_item<EPI, RT>(Z, m, n, r, chunk, Gb, lo, w, blockIdx.y * RT, blockIdx.x * band::TC, Out, pa, sm4);
 }
 
+// Columns pass on 128 x 32 tiles, two columns per thread.
+template <int EPI>
+__global__ void __launch_bounds__(band::NT) band_cols_kernel128(const float *__restrict__ Z, int m, int n,
+                                                               const float *__restrict__ Gb, int lo, int w, int r,
+                                                               int chunk, float *__restrict__ Out, ProxArgs pa) {
+    extern __shared__ __align__(16) float sm4[];
+    band4::cols_item128<EPI>(Z, m, n, r, chunk, Gb, lo, w, blockIdx.y * 128, blockIdx.x * band::TC, Out, pa, sm4);
+}
+
 // Out + i * m * n = G_i In for each term i = blockIdx.z (terms not summed).
 template <int RT>
 __global__ void __launch_bounds__(band::NT) band_cols_each_kernel4(const float *__restrict__ In, int m, int n,
@@ -182,16 +191,32 @@ void launch_cols4(dim3 grid, size_t sm, cudaStream_t s, const float *Z, int m, i
         launch_pdl(band_cols_kernel4<EPI_PROX, RT>, grid, sm, s, Z, m, n, Gb, lo, w, r, chunk, Out, pa);
 }
 
+// Row height of the columns pass: 128 when the 16-byte path has 64-row tiles
+// and 128-row tiles still give two per SM, else that of the rows pass.
+template <typename T>
+int cols_rows(int m, int n, const void *a, const void *b, const void *c) {
+    const int rt = vec_rows<T>(m, n, a, b, c);
+    return rt == 64 && band4::tiles(128, m, n) >= 2 * sm_count() ? 128 : rt;
+}
+
 template <typename T>
 void launch_band_cols(const T *Z, int m, int n, const T *Gb, int lo, int w, int r, EpiKind epi, T *Out,
                       const ProxArgs &pa, cudaStream_t s, int req) {
-    const int rt = vec_rows<T>(m, n, Z, Gb, Z);
+    const int rt = cols_rows<T>(m, n, Z, Gb, Out ? (const void *)Out : (const void *)Z);
     int chunk = req > 0 ? std::min(req, r) : cols_chunk<T>(rt, r, w);
     if (cols_bytes<T>(rt, w, chunk) > kBandSmemMax) chunk = cols_chunk<T>(rt, r, w);
     const int ta = rt ? rt : band::TA;
     dim3 grid((n + band::TC - 1) / band::TC, (m + ta - 1) / ta);
     const size_t sm = cols_bytes<T>(rt, w, chunk);
     if constexpr (std::is_same<T, float>::value) {
+        if (rt == 128) {
+            if (epi == EPI_STORE)
+                return launch_pdl(band_cols_kernel128<EPI_STORE>, grid, sm, s, Z, m, n, Gb, lo, w, r, chunk, Out, pa);
+            if (epi == EPI_RESIDUAL)
+                return launch_pdl(band_cols_kernel128<EPI_RESIDUAL>, grid, sm, s, Z, m, n, Gb, lo, w, r, chunk, Out,
+                                  pa);
+            return launch_pdl(band_cols_kernel128<EPI_PROX>, grid, sm, s, Z, m, n, Gb, lo, w, r, chunk, Out, pa);
+        }
         if (rt == 64) return launch_cols4<64>(grid, sm, s, Z, m, n, Gb, lo, w, r, chunk, epi, Out, pa);
         if (rt == 32) return launch_cols4<32>(grid, sm, s, Z, m, n, Gb, lo, w, r, chunk, epi, Out, pa);
     }
@@ -216,7 +241,8 @@ void launch_band_cols_each(const float *In, int m, int n, const float *Gb, int l
 
 size_t band_smem_f32(bool rows, int w, int chunk) {   // the largest of the layouts
     size_t b = 0;
-    for (int rt : {0, 32, 64}) b = std::max(b, rows ? rows_bytes<float>(rt, w, chunk) : cols_bytes<float>(rt, w, chunk));
+    for (int rt : {0, 32, 64, 128})
+        if (rt < 128 || !rows) b = std::max(b, rows ? rows_bytes<float>(rt, w, chunk) : cols_bytes<float>(rt, w, chunk));
     return b;
 }
 
@@ -250,7 +276,8 @@ cudaError_t band_set_smem_limits(int w) {
     for (auto k : {band_rows_kernel4<32>, band_rows_kernel4<64>})
         if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
     for (auto k : {band_cols_kernel4<EPI_STORE, 32>, band_cols_kernel4<EPI_RESIDUAL, 32>, band_cols_kernel4<EPI_PROX, 32>,
-                   band_cols_kernel4<EPI_STORE, 64>, band_cols_kernel4<EPI_RESIDUAL, 64>, band_cols_kernel4<EPI_PROX, 64>})
+                   band_cols_kernel4<EPI_STORE, 64>, band_cols_kernel4<EPI_RESIDUAL, 64>, band_cols_kernel4<EPI_PROX, 64>,
+                   band_cols_kernel128<EPI_STORE>, band_cols_kernel128<EPI_RESIDUAL>, band_cols_kernel128<EPI_PROX>})
         if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
     if ((e = cudaFuncSetAttribute(band_rows_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
     if ((e = cudaFuncSetAttribute(band_cols_kernel<float, EPI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;

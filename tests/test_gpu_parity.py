@@ -215,6 +215,31 @@ def test_persistent_forms_match_oracle(m, n):
     s.close()
 
 
+@pytest.mark.parametrize("psf_shape,centre,r", [((9, 9), (4, 4), 3), ((7, 14), (3, 0), 4), ((10, 7), (9, 6), 1),
+                                               ((41, 37), (20, 18), 2), ((6, 11), (0, 10), 5)])
+def test_one_launch_solver_band_offsets(psf_shape, centre, r):
+    """The one-launch fused solver over PSF widths and centres that give every
+    column-offset class of both operators' bands (mod 4), term counts split
+    4 + rest, and bands wider than 32 rows (two row groups in the row pass),
+    against the oracle and the two-launch fused form."""
+    m, n = 96, 100
+    g = W.rng(140 + psf_shape[0] * 16 + psf_shape[1])
+    P = W.random_psf(g, *psf_shape)
+    x, b, _ = _problem(m, n, P, 1, 141, centre=centre)
+    ka = kron.kron_approx(P, centre[0], centre[1], m, n, 1, r)
+    L = _oracle_L(ka)
+    Xo = oracle.sfista(b.astype(np.float64), ka, L, 0.01, 20)
+    db = _cuda(b)
+    outs = {}
+    for op in ("banded_persistent", "banded_fused"):
+        s = api.Sfista(P, (m, n), 1, r, center=centre, prec="fp32", op=op, lipschitz=L)
+        outs[op] = s.solve_device(db, 0.01, 20).cpu().numpy()
+        s.close()
+    assert oracle.rel_fro(outs["banded_persistent"], Xo) <= TOL["fp32"]
+    # the same arithmetic in the same order: the two forms agree bit for bit
+    assert np.array_equal(outs["banded_persistent"], outs["banded_fused"])
+
+
 def test_graph_and_direct_launch_agree():
     P = W.rotated_gaussian_psf(15, 2.0, 1.0, 0.3)
     x, b, _ = _problem(96, 80, P, 1, 106)
