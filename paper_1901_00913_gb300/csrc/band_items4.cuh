@@ -391,17 +391,20 @@ __device__ __forceinline__ void cols_item128(const float *__restrict__ Z, int m,
     const int c = c0 + 2 * cp;
     if (c < n) {   // n is a multiple of 4: the pair is all inside or all outside
         if (EPI == EPI_PROX) {
-            size_t idx[8];
-            float g0[8], g1[8];
-            bool ok[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                ok[i] = a0 + rb + i < m;
-                idx[i] = (size_t)(a0 + rb + i) * n + c;
-                g0[i] = acc[i][0];
-                g1[i] = acc[i][1];
+            for (int h = 0; h < 2; ++h) {   // four rows at a time: fewer live registers
+                size_t idx[4];
+                float g0[4], g1[4];
+                bool ok[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    ok[i] = a0 + rb + 4 * h + i < m;
+                    idx[i] = (size_t)(a0 + rb + 4 * h + i) * n + c;
+                    g0[i] = acc[4 * h + i][0];
+                    g1[i] = acc[4 * h + i][1];
+                }
+                prox_momentum2_n<4>(pa, idx, g0, g1, ok);
             }
-            prox_momentum2_n<8>(pa, idx, g0, g1, ok);
         } else {
             float2 bv[8];
 #pragma unroll

@@ -65,9 +65,11 @@ __global__ void __launch_bounds__(band::NT) band_cols_kernel4(const float *__res
     band4::cols_item<EPI, RT>(Z, m, n, r, chunk, Gb, lo, w, blockIdx.y * RT, blockIdx.x * band::TC, Out, pa, sm4);
 }
 
-// Columns pass on 128 x 32 tiles, two columns per thread.
+// Columns pass on 128 x 32 tiles, two columns per thread.  The prox
+// instantiation is held to three blocks per SM (80 registers, a few spilled
+// around the epilogue): measured faster than two blocks without spills.
 template <int EPI>
-__global__ void __launch_bounds__(band::NT) band_cols_kernel128(const float *__restrict__ Z, int m, int n,
+__global__ void __launch_bounds__(band::NT, EPI == EPI_PROX ? 3 : 0) band_cols_kernel128(const float *__restrict__ Z, int m, int n,
                                                                const float *__restrict__ Gb, int lo, int w, int r,
                                                                int chunk, float *__restrict__ Out, ProxArgs pa) {
     extern __shared__ __align__(16) float sm4[];
