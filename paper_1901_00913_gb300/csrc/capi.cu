@@ -42,6 +42,26 @@ __global__ void init_state_kernel(const float2 *X, const float2 *Xp, float2 *Y, 
     }
 }
 
+// The FP32 state of a tensor-core form at the start of a solve: X_k0 rounded
+// to FP32 and Y_{k0+1} = X + beta (X - Xp) formed in FP32 exactly as the
+// prox epilogue forms it, so a resumed solve continues bit for bit; then
+// the operand copies of that Y.
+__global__ void init_state32_kernel(const float2 *X, const float2 *Xp, float *X32, float *Y32, void *Yhi, void *Ylo,
+                                    int split_kind, size_t count, float beta) {
+    ProxArgs pa{};
+    pa.Yhi = Yhi;
+    pa.Ylo = Ylo;
+    pa.split_kind = split_kind;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float x = dfp::to_float(X[i]), xp = dfp::to_float(Xp[i]);
+        const float y = fmaf(beta, x - xp, x);
+        X32[i] = x;
+        Y32[i] = y;
+        store_operands32(pa, i, y);
+    }
+}
+
 template <typename T>
 cudaError_t upload(T **dst, const T *src, size_t count, cudaStream_t s) {
     cudaError_t e = cudaMalloc((void **)dst, sizeof(T) * std::max<size_t>(count, 1));
@@ -73,7 +93,8 @@ void ctx_free(sfista_ctx *c) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->gemm) gemm_destroy(c->gemm);
     void *ptrs[] = {c->dA, c->dAT, c->dB, c->dBT, c->fA, c->fAT, c->fB, c->fBT, c->Bd, c->Yop, c->Z,
-                    c->R, c->tmp, c->Xb[0], c->Xb[1], c->Y, c->status, c->beta, c->bar};
+                    c->R, c->tmp, c->Xb[0], c->Xb[1], c->Y, c->status, c->beta, c->bar,
+                    c->Xf[0], c->Xf[1], c->Yf};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
@@ -112,6 +133,11 @@ ProxArgs sfista::prox_args(sfista_ctx *c, int k, double lam) {
     pa.Xin = c->Xb[(k - 1) & 1];
     pa.Xout = c->Xb[k & 1];
     pa.Y = c->Y;
+    if (c->Xf[0]) {
+        pa.Xin32 = c->Xf[(k - 1) & 1];
+        pa.Xout32 = c->Xf[k & 1];
+        pa.Y32 = c->Yf;
+    }
     pa.Yop = c->Yop;
     pa.beta = c->beta;
     pa.k = k;
@@ -306,10 +332,19 @@ sfista_status sfista::solve_core(sfista_ctx *c, const float *d_b, double lam, in
     int split = 0;
     if (c->gemm) gemm_state_operands(c->gemm, &yhi, &ylo, &split);
     launch_init_state(Xk, Xkm, c->Y, c->Yop, yhi, ylo, split, N, beta0, c->stream);
+    if (c->Xf[0])   // the FP32 state the tensor-core prox epilogue iterates on
+        init_state32_kernel<<<1024, 256, 0, c->stream>>>(Xk, Xkm, c->Xf[k0 & 1], c->Yf, yhi, ylo, split, N,
+                                                        (float)beta0);
     if (c->gemm) gemm_prepare_solve(c->gemm, c->Bd, c->stream);
     SF_CUDA(cudaGetLastError());
     st = run_loop(c, lam, k0, iters);
     if (st) return st;
+    if (c->Xf[0] && iters > 0) {   // back into the double-float buffers: X_ke, X_{ke-1}, Y_{ke+1}
+        const int ke = k0 + iters;
+        launch_f32_to_df(c->Xf[ke & 1], c->Xb[ke & 1], N, c->stream);
+        launch_f32_to_df(c->Xf[(ke + 1) & 1], c->Xb[(ke + 1) & 1], N, c->stream);
+        launch_f32_to_df(c->Yf, c->Y, N, c->stream);
+    }
     SF_CUDA(cudaGetLastError());
     return SFISTA_OK;
 }
@@ -557,6 +592,13 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int ce
     if (c->op == SFISTA_OP_GEMM_BAND || c->op == SFISTA_OP_GEMM_DENSE) {
         st = gemm_create(&c->gemm, h, c->prec, c->op == SFISTA_OP_GEMM_DENSE, c->status, c->stream);
         if (st) return bail(st);
+        // FP32 state for the forms whose products are far coarser than FP32
+        // (BF16, BF16x3, TF32); TF32x3 keeps the double-float state, which its
+        // products are accurate enough to use (1.9e-6 vs 1.7e-5 at 512^2).
+        if (c->prec != SFISTA_TF32X3 &&
+            ((e = cudaMalloc((void **)&c->Xf[0], N * 4)) || (e = cudaMalloc((void **)&c->Xf[1], N * 4)) ||
+             (e = cudaMalloc((void **)&c->Yf, N * 4))))
+            return bail(fail(SFISTA_ENOMEM, std::string("FP32 state: ") + cudaGetErrorString(e)));
     }
     if (o.lipschitz > 0.0) {
         c->L = o.lipschitz;
@@ -894,6 +936,11 @@ sfista_status sfista_batch_solve(sfista_batch *b, const float *const *d_b, const
         int split = 0;
         if (c->gemm) gemm_state_operands(c->gemm, &yhi, &ylo, &split);
         launch_init_state(c->Xb[0], c->Xb[1], c->Y, c->Yop, yhi, ylo, split, c->N, 0.0, b->stream);
+        if (c->Xf[0]) {   // X_0 = X_{-1} = Y_1 = 0 in the FP32 state too
+            SF_CUDA(cudaMemsetAsync(c->Xf[0], 0, c->N * 4, b->stream));
+            SF_CUDA(cudaMemsetAsync(c->Xf[1], 0, c->N * 4, b->stream));
+            SF_CUDA(cudaMemsetAsync(c->Yf, 0, c->N * 4, b->stream));
+        }
         ProxArgs pa = prox_args(c, 1, lambdas[p]);
         pa.Xin = c->Xb[0];
         pa.Xout = c->Xb[1];
@@ -939,7 +986,10 @@ sfista_status sfista_batch_solve(sfista_batch *b, const float *const *d_b, const
     }
     for (int p = 0; p < np; ++p) {
         sfista_ctx *c = b->ctxs[p];
-        launch_df_to_f32(c->Xb[iters & 1], d_x[p], c->N, b->stream);
+        if (c->Xf[0])
+            SF_CUDA(cudaMemcpyAsync(d_x[p], c->Xf[iters & 1], c->N * 4, cudaMemcpyDeviceToDevice, b->stream));
+        else
+            launch_df_to_f32(c->Xb[iters & 1], d_x[p], c->N, b->stream);
     }
     SF_CUDA(cudaGetLastError());
     SF_CUDA(cudaEventRecord(b->ev_out, b->stream));

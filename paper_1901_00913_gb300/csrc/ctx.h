@@ -43,6 +43,9 @@ struct sfista_ctx {
     // Iteration state.
     float *Bd = nullptr, *Yop = nullptr, *Z = nullptr, *R = nullptr, *tmp = nullptr;
     float2 *Xb[2] = {nullptr, nullptr}, *Y = nullptr;   // double-float FISTA state
+    // Tensor-core forms: the FP32 state their prox epilogue iterates on,
+    // converted from / to Xb and Y at the start / end of each solve.
+    float *Xf[2] = {nullptr, nullptr}, *Yf = nullptr;
     unsigned *status = nullptr;
     float2 *beta = nullptr;        // double-float momentum table
     int beta_len = 0;

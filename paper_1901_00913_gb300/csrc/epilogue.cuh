@@ -106,6 +106,59 @@ static __device__ __forceinline__ void prox_momentum_n(const ProxArgs &pa, const
     prox_apply_n<N>(pa, idx, g, valid, y, xp, pa.beta[pa.k - 1]);
 }
 
+// FP32 state (tensor-core forms, whose operator error is far above FP32
+// rounding): Step 1 (+ l1 threshold, + projection) and Step 3 in FP32 with
+// the constants rounded to FP32; the operand copies of Y_{k+1} as in
+// store_operands.
+static __device__ __forceinline__ float prox_step32(const ProxArgs &pa, float y, float xp, float g, float beta,
+                                                    float *xout, bool *bad) {
+    float x = fmaf(-pa.inv_den.x, g, pa.shrink.x * y);
+    if (pa.tau.x > 0.0f) x = x > 0.0f ? fmaxf(x - pa.tau.x, 0.0f) : fminf(x + pa.tau.x, 0.0f);
+    if (pa.project && x < 0.0f) x = 0.0f;
+    *bad |= !isfinite(x);
+    *xout = x;
+    return fmaf(beta, x - xp, x);
+}
+
+static __device__ __forceinline__ void store_operands32(const ProxArgs &pa, size_t idx, float yn) {
+    if (pa.Yop) pa.Yop[idx] = yn;
+    if (pa.split_kind == 1) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(yn);
+        reinterpret_cast<__nv_bfloat16 *>(pa.Yhi)[idx] = h;
+        if (pa.Ylo) reinterpret_cast<__nv_bfloat16 *>(pa.Ylo)[idx] = __float2bfloat16_rn(__fsub_rn(yn, __bfloat162float(h)));
+    } else if (pa.split_kind == 2) {
+        const float h = tf32_round(yn);
+        reinterpret_cast<float *>(pa.Yhi)[idx] = h;
+        if (pa.Ylo) reinterpret_cast<float *>(pa.Ylo)[idx] = tf32_round(__fsub_rn(yn, h));
+    }
+}
+
+// Pairs of neighbouring pixels (idx[q] even) for N rows at once, FP32 state.
+template <int N>
+static __device__ __forceinline__ void prox_momentum2_n32(const ProxArgs &pa, const size_t *idx, const float *g0,
+                                                          const float *g1, const bool *valid) {
+    float2 y[N], xp[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        y[q] = valid[q] ? __ldcg(reinterpret_cast<const float2 *>(pa.Y32 + idx[q])) : make_float2(0.f, 0.f);
+        xp[q] = valid[q] ? __ldcg(reinterpret_cast<const float2 *>(pa.Xin32 + idx[q])) : make_float2(0.f, 0.f);
+    }
+    const float beta = pa.beta[pa.k - 1].x;
+    bool bad = false;
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        if (!valid[q]) continue;
+        float x0, x1;
+        const float y0 = prox_step32(pa, y[q].x, xp[q].x, g0[q], beta, &x0, &bad);
+        const float y1 = prox_step32(pa, y[q].y, xp[q].y, g1[q], beta, &x1, &bad);
+        *reinterpret_cast<float2 *>(pa.Xout32 + idx[q]) = make_float2(x0, x1);
+        *reinterpret_cast<float2 *>(pa.Y32 + idx[q]) = make_float2(y0, y1);
+        store_operands32(pa, idx[q], y0);
+        store_operands32(pa, idx[q] + 1, y1);
+    }
+    if (bad) atomicOr(pa.status, DEV_NONFINITE);
+}
+
 // Pairs of neighbouring pixels (idx[q] even) for N rows at once.
 template <int N>
 static __device__ __forceinline__ void prox_momentum2_n(const ProxArgs &pa, const size_t *idx, const float *g0,

@@ -419,9 +419,12 @@ __global__ void __launch_bounds__(320, 1)
             ProxArgs pa = ga->pa;
             if (EPI == GE_PROX && GROUPED) {
                 float2 *b0 = const_cast<float2 *>(pa.Xin), *b1 = pa.Xout;
+                float *f0 = const_cast<float *>(pa.Xin32), *f1 = pa.Xout32;
                 pa.k = kswap;
                 pa.Xin = (kswap - 1) & 1 ? b1 : b0;
                 pa.Xout = kswap & 1 ? b1 : b0;
+                pa.Xin32 = (kswap - 1) & 1 ? f1 : f0;
+                pa.Xout32 = kswap & 1 ? f1 : f0;
             }
 #pragma unroll 1
             for (int h = 0; h < 2; ++h) {
@@ -528,7 +531,8 @@ __global__ void __launch_bounds__(320, 1)
                                 g0[q] = okr[q] ? tile[rr * TS + c] : 0.0f;
                                 g1v[q] = okr[q] ? tile[rr * TS + c + 1] : 0.0f;
                             }
-                            prox_momentum2_n<8>(pa, idx, g0, g1v, okr);
+                            if (pa.Y32) prox_momentum2_n32<8>(pa, idx, g0, g1v, okr);
+                            else prox_momentum2_n<8>(pa, idx, g0, g1v, okr);
                         }
                     }
                 } else if (col < ga->N) {

@@ -79,6 +79,10 @@ struct ProxArgs {
     int project;         // max(X, 0) after the shrink
     float2 tau;          // mu / (L + lambda^2), double-float: soft threshold of the l1 term (0: none)
     unsigned *status;    // device status word
+    // Tensor-core forms: FP32 state (X_{k-1} in, X_k out, Y in place) that
+    // their EPI_PROX epilogue uses instead of Xin / Xout / Y; NULL otherwise.
+    const float *Xin32;
+    float *Xout32, *Y32;
 };
 
 // chunk: terms staged per block (0: the default rule, a shared-memory budget);
@@ -162,6 +166,7 @@ void launch_fill_f64(double *p, size_t count, double v, cudaStream_t s);
 void launch_f64_to_f32(const double *in, float *out, size_t count, cudaStream_t s);
 // Double-float state conversions.
 void launch_df_to_f32(const float2 *in, float *out, size_t count, cudaStream_t s);
+void launch_f32_to_df(const float *in, float2 *out, size_t count, cudaStream_t s);
 void launch_df_to_f64(const float2 *in, double *out, size_t count, cudaStream_t s);
 void launch_f64_to_df(const double *in, float2 *out, size_t count, cudaStream_t s);
 void launch_f32_to_f64(const float *in, double *out, size_t count, cudaStream_t s);

@@ -312,6 +312,10 @@ __global__ void df_to_f32_kernel(const float2 *in, float *out, size_t count) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
         out[i] = dfp::to_float(in[i]);
 }
+__global__ void f32_to_df_kernel(const float *in, float2 *out, size_t count) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = make_float2(in[i], 0.0f);
+}
 __global__ void df_to_f64_kernel(const float2 *in, double *out, size_t count) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
         out[i] = dfp::to_double(in[i]);
@@ -502,6 +506,9 @@ void launch_f64_to_f32(const double *in, float *out, size_t count, cudaStream_t 
 }
 void launch_df_to_f32(const float2 *in, float *out, size_t count, cudaStream_t s) {
     df_to_f32_kernel<<<grid_for(count), 256, 0, s>>>(in, out, count);
+}
+void launch_f32_to_df(const float *in, float2 *out, size_t count, cudaStream_t s) {
+    f32_to_df_kernel<<<grid_for(count), 256, 0, s>>>(in, out, count);
 }
 void launch_df_to_f64(const float2 *in, double *out, size_t count, cudaStream_t s) {
     df_to_f64_kernel<<<grid_for(count), 256, 0, s>>>(in, out, count);

@@ -251,11 +251,14 @@ def test_graph_and_direct_launch_agree():
     np.testing.assert_array_equal(outs[0], outs[1])
 
 
-@pytest.mark.parametrize("op", ["banded", "banded_fused", "banded_persistent", "gemm_band"])
-def test_resume_state_matches_uninterrupted(op):
+@pytest.mark.parametrize("op,prec,tol", [("banded", "fp32", 1e-6), ("banded_fused", "fp32", 1e-6),
+                                         ("banded_persistent", "fp32", 1e-6), ("gemm_band", "tf32x3", 1e-6),
+                                         ("gemm_band", "bf16x3", 1e-4)])
+def test_resume_state_matches_uninterrupted(op, prec, tol):
+    """A solve split at k = 20 continues bit for bit; TF32x3 keeps the
+    double-float state, BF16x3 iterates on an FP32 state."""
     P = W.rotated_gaussian_psf(15, 2.0, 1.0, 0.3)
     x, b, _ = _problem(96, 80, P, 1, 107)
-    prec = "tf32x3" if op == "gemm_band" else "fp32"
     s = api.Sfista(P, (96, 80), 1, 2, lipschitz=1.0, op=op, prec=prec)
     db = _cuda(b)
     X = torch.zeros(96, 80, dtype=torch.float64, device="cuda")
@@ -269,7 +272,7 @@ def test_resume_state_matches_uninterrupted(op):
     assert torch.max(torch.abs(X - ref)).item() <= 1e-12
     ka = kron.kron_approx(P, 7, 7, 96, 80, 1, 2)
     Xo = oracle.sfista(b.astype(np.float64), ka, 1.0, 0.01, 30)
-    assert oracle.rel_fro(ref.cpu().numpy(), Xo) <= 1e-6
+    assert oracle.rel_fro(ref.cpu().numpy(), Xo) <= tol
     s.close()
 
 
