@@ -42,9 +42,12 @@ def probs():
     return pr, iters, refs
 
 
-@pytest.mark.parametrize("prec,op,tol", [("fp32", "banded", 1e-5), ("bf16x3", "gemm_band", 1e-4),
-                                         ("tf32x3", "gemm_band", 1e-4)])
+@pytest.mark.parametrize("prec,op,tol", [("fp32", "banded", 1e-5), ("fp32", "auto", 1e-5),
+                                         ("bf16x3", "gemm_band", 1e-4), ("tf32x3", "gemm_band", 1e-4)])
 def test_batched_matches_oracle_and_single(probs, prec, op, tol):
+    """A batch runs the grouped kernels whatever form its contexts chose (FP32
+    auto: the one-launch fused solver for the single solves here), with the
+    same arithmetic in the same order."""
     pr, iters, refs = probs
     solvers = [api.Sfista(P, b.shape, 1, ka.r, prec=prec, op=op, lipschitz=L) for P, b, ka, L, lam in pr]
     d_bs = [torch.from_numpy(b).cuda() for P, b, ka, L, lam in pr]
