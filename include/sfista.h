@@ -342,8 +342,11 @@ typedef struct {
  *     terms staged per block (1 .. r, those that fit in shared memory); this
  *     sets shared memory per block and so the blocks resident per SM;
  *   - if the operator form was left to SFISTA_OP_AUTO: FP32 contexts also
- *     compare the tuned two-pass form with the fused form, tensor-core
- *     contexts the band-limited and full (dense) K ranges.
+ *     compare the tuned two-pass form with the fused form and, when every
+ *     32 x 32 tile can have its own resident block, with the one-launch
+ *     solver (SFISTA_OP_BANDED_PERSISTENT, timed per iteration over
+ *     max(iters, 40) iterations of one launch); tensor-core contexts compare
+ *     the band-limited and full (dense) K ranges.
  * An explicitly chosen form is kept (only its stages are tuned).  The chosen
  * configuration applies to later solves, sfista_apply and batches created
  * afterwards (sfista_info reports the form).
