@@ -568,6 +568,56 @@ def run_example2(args, torch):
         forms[f] = {"mean_iters_per_s": float(np.mean(rates)), "min_iters_per_s": float(np.min(rates)),
                     "max_rel_err": max(r["rel_err_vs_oracle_first_%d_its" % args.check_iters]
                                        for r in rows.values()), "cases": rows}
+    # The same 18 problems as FP32 batches, two ways: all 18 in one batch (its
+    # tiles outnumber the co-resident blocks: grouped launches), and groups
+    # whose tiles fit as co-resident blocks (one launch of the fused solver
+    # each); plus the batch tuner's own comparison of the two plans on one
+    # such group.
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    solvers, dbs, lams, tiles = [], [], [], []
+    for pr in cases:
+        n = pr.x_true.shape[0]
+        xt = torch.from_numpy(pr.x_true.astype(np.float32)).cuda()
+        bx = api.sfista_blur(pr.psf, xt, pr.bc).double().cpu().numpy()
+        b = (bx + W.noise_of_kind(pr.extra["noise"], bx, pr.noise, pr.noise_level)).astype(np.float32)
+        dbs.append(torch.from_numpy(b).cuda())
+        solvers.append(api.Sfista(pr.psf, (n, n), pr.bc, pr.r, prec="fp32", op="banded"))
+        lams.append(pr.lam)
+        tiles.append((-(-n // 32)) ** 2)
+    fit_groups, cur, used = [], [], 0
+    for i, t in enumerate(tiles):
+        if cur and used + t > 2 * sms:
+            fit_groups.append(cur)
+            cur, used = [], 0
+        cur.append(i)
+        used += t
+    fit_groups.append(cur)
+    iters = cases[0].iters
+    singles = [sv.solve_device(db, lam, iters) for sv, db, lam in zip(solvers, dbs, lams)]
+    for name, groups in (("fp32:batched_all", [list(range(len(cases)))]), ("fp32:batched_one_launch", fit_groups)):
+        batches = [api.Batch([solvers[i] for i in g]) for g in groups]
+        outs = []
+        for _ in range(args.warmup):
+            outs = [bt.solve([dbs[i] for i in g], [lams[i] for i in g], iters) for bt, g in zip(batches, groups)]
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(args.steps):
+            for bt, g, og in zip(batches, groups, outs):
+                bt.solve([dbs[i] for i in g], [lams[i] for i in g], iters, outs=og, sync=False)
+        ev1.record()
+        torch.cuda.synchronize()
+        diff = max(float(torch.max(torch.abs(X - singles[i]))) for g, og in zip(groups, outs) for i, X in zip(g, og))
+        forms[name] = {"problem_iters_per_s": len(cases) * iters * args.steps / (ev0.elapsed_time(ev1) / 1e3),
+                       "groups": [len(g) for g in groups],
+                       "one_launch": all(sum(tiles[i] for i in g) <= 2 * sms for g in groups),
+                       "max_abs_diff_vs_single_solves": diff}
+        if name == "fp32:batched_one_launch":
+            forms[name]["batch_tune_first_group"] = batches[0].tune(iters=10)
+        for bt in batches:
+            bt.close()
+    for sv in solvers:
+        sv.close()
     line = {"metric": METRIC, "workload": "Example 2 stand-in: 18 problems 256x256, defocus / shake blur x 3 levels "
             "x gauss / laplace / multiplicative noise (1%), reflexive, r=5, lambda=0.005, 50 its",
             "unit": "iters/s", "steps": args.steps, "warmup": args.warmup, "forms": forms,

@@ -198,7 +198,10 @@ sfista_status sfista_solve_state(sfista_ctx *ctx, const float *d_b,
  * Batched solves: many independent problems (any image sizes, PSFs, ranks,
  * one precision and operator family) advance together, one launch per stage
  * of Alg. 2 covering the tiles of every problem, the iteration loop replayed
- * as one CUDA graph.
+ * as one CUDA graph.  A banded FP32 batch whose images all have m, n
+ * multiples of 4 and whose 32 x 32 tiles all fit as co-resident blocks (one
+ * block per tile of every problem) runs instead as one cooperative launch of
+ * the fused solver for all iterations; sfista_batch_tune compares the two.
  *
  * sfista_batch_create -- group nprob contexts made by sfista_setup (same
  *   device, same precision; all tensor-core forms or all banded forms).  The
@@ -366,9 +369,14 @@ sfista_status sfista_tune(sfista_ctx *ctx, int iters, sfista_tune_entry *entries
  * batch is tuned as a whole: for each shared-memory budget in a fixed list
  * (and for the problems' own chunks, budget 0) every problem takes the largest
  * term chunks that fit, the batch solves `iters` iterations of an all-zero
- * observation twice (the second timed), and the fastest plan is kept.
- * entries: one per distinct plan, op = SFISTA_OP_BANDED, stage = -1, chunk =
- * the budget in KB (0: each problem's own chunks), ms = time per iteration.
+ * observation twice (the second timed), and the fastest plan is kept.  When
+ * every 32 x 32 tile of every problem can have its own resident block (and
+ * m, n are multiples of 4), the whole batch solve as one cooperative launch
+ * of the fused solver is a further plan (the default for such batches).
+ * entries: one per distinct plan, stage = -1, ms = time per iteration;
+ * op = SFISTA_OP_BANDED with chunk = the budget in KB (0: each problem's own
+ * chunks), or op = SFISTA_OP_BANDED_PERSISTENT (chunk 0) for the one-launch
+ * plan.
  * Tensor-core batches have a single tile shape: no entries, SFISTA_OK.
  * Synchronous.  Leaves every grouped context's state undefined.
  */

@@ -244,11 +244,13 @@ def sfista_tune(ctx, iters=10, max_entries=64):
 
 
 def sfista_batch_tune(handle, iters=5, max_entries=64):
-    """Batch autotuner (see include/sfista.h): one dict per plan, chunk = budget in KB."""
+    """Batch autotuner (see include/sfista.h): one dict per plan; "op" names the
+    plan's form (banded: grouped launches with a shared-memory budget of
+    budget_kb KB; banded_persistent: the whole batch in one launch)."""
     buf = (TuneEntry * max_entries)()
     cnt = ctypes.c_int(0)
     _check(load().sfista_batch_tune(ctypes.c_void_p(handle), int(iters), buf, int(max_entries), ctypes.byref(cnt)))
-    return [{"budget_kb": e.chunk, "ms": e.ms} for e in buf[:min(cnt.value, max_entries)]]
+    return [{"op": OP_NAME.get(e.op, e.op), "budget_kb": e.chunk, "ms": e.ms} for e in buf[:min(cnt.value, max_entries)]]
 
 
 def sfista_apply_static(d_x, d_y, r, band_right, lo_right, band_left, lo_left, stream=None):
@@ -310,7 +312,8 @@ class Batch:
         return outs
 
     def tune(self, iters=5):
-        """Chooses the grouped launches' shared-memory plan by measurement; returns the measurements."""
+        """Chooses the batch plan by measurement (grouped launches and their shared-memory budget, or one
+        launch for the whole batch); returns the measurements."""
         return sfista_batch_tune(self.handle, iters)
 
     def close(self):

@@ -152,6 +152,31 @@ ProxArgs sfista::prox_args(sfista_ctx *c, int k, double lam) {
 }
 namespace {
 
+// The context's problem as a banded descriptor (geometry and buffers; pa
+// left default).
+BandProb ctx_prob(const sfista_ctx *c) {
+    const HostSetup &h = c->hs;
+    BandProb P{};
+    P.m = c->m;
+    P.n = c->n;
+    P.r = c->r;
+    P.fA = c->fA;
+    P.fB = c->fB;
+    P.fAT = c->fAT;
+    P.fBT = c->fBT;
+    P.loA = h.A.lo;
+    P.wA = h.A.w;
+    P.loB = h.B.lo;
+    P.wB = h.B.w;
+    P.loAT = h.AT.lo;
+    P.wAT = h.AT.w;
+    P.loBT = h.BT.lo;
+    P.wBT = h.BT.w;
+    P.Z = c->Z;
+    P.R = c->R;
+    return P;
+}
+
 // Stage `st` (0..3) of iteration k; see sfista_time_stages for the numbering.
 void enqueue_stage(sfista_ctx *c, int st, const ProxArgs &pa) {
     const HostSetup &h = c->hs;
@@ -193,10 +218,13 @@ sfista_status run_loop(sfista_ctx *c, double lam, int k0, int iters) {
     if (c->op == SFISTA_OP_BANDED_PERSISTENT) {
         const HostSetup &h = c->hs;
         ProxArgs pa = prox_args(c, k0 + 1, lam);
-        if (c->pfused)
-            SF_CUDA(launch_band_solve_fused(c->pgrid, c->psmem, c->m, c->n, c->r, c->fA, h.A, c->fB, h.B, c->fAT,
-                                            h.AT, c->fBT, h.BT, c->R, c->Xb[0], c->Xb[1], pa, k0, iters, c->bar,
-                                            c->stream));
+        if (c->pfused) {
+            BandProb P = ctx_prob(c);
+            P.pa = pa;
+            P.pa.Xin = c->Xb[0];
+            P.pa.Xout = c->Xb[1];
+            SF_CUDA(launch_band_solve_fused(c->pgrid, c->psmem, P, k0, iters, c->bar, c->stream));
+        }
         else
             SF_CUDA(launch_persistent(c->pgrid, c->psmem, c->prows_chunk, c->pcols_chunk, c->m, c->n, c->r, c->fA,
                                       h.A, c->fB, h.B, c->fAT, h.AT, c->fBT, h.BT, c->Z, c->R, c->Xb[0], c->Xb[1], pa,
@@ -376,6 +404,13 @@ struct sfista_batch {
     cudaGraphExec_t gexec = nullptr;
     int g_iters = -1;
     std::vector<double> g_lams;
+    // FP32 batches whose tiles all fit as co-resident blocks: the whole batch
+    // solve as one cooperative launch (fused_ok), taken while use_fused.
+    bool fused_ok = false, use_fused = false;
+    int2 *d_fitems = nullptr;
+    int fnitems = 0;
+    size_t fsmem = 0;
+    unsigned *bar = nullptr;
 };
 
 namespace {
@@ -387,6 +422,8 @@ void batch_free(sfista_batch *b) {
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->gb) gemm_batch_destroy(b->gb);
     if (b->d_probs) cudaFree(b->d_probs);
+    if (b->d_fitems) cudaFree(b->d_fitems);
+    if (b->bar) cudaFree(b->bar);
     for (int st = 0; st < 4; ++st)
         if (b->d_items[st]) cudaFree(b->d_items[st]);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
@@ -572,13 +609,12 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int ce
     if (o.op == SFISTA_OP_AUTO && c->op == SFISTA_OP_BANDED_FUSED) {
         int grid = 0;
         size_t smem = 0;
-        if (band_solve_fused_config(c->m, c->n, c->r, h.A, h.B, h.AT, h.BT, c->dev, &grid, &smem))
-            c->op = SFISTA_OP_BANDED_PERSISTENT;
+        if (band_solve_fused_config(ctx_prob(c), c->dev, &grid, &smem)) c->op = SFISTA_OP_BANDED_PERSISTENT;
     }
     if (c->op == SFISTA_OP_BANDED_PERSISTENT) {
         if ((e = cudaMalloc((void **)&c->bar, kBarrierBytes)) || (e = cudaMemset(c->bar, 0, kBarrierBytes)))
             return bail(fail(SFISTA_ENOMEM, std::string("barrier words: ") + cudaGetErrorString(e)));
-        c->pfused = band_solve_fused_config(c->m, c->n, c->r, h.A, h.B, h.AT, h.BT, c->dev, &c->pgrid, &c->psmem);
+        c->pfused = band_solve_fused_config(ctx_prob(c), c->dev, &c->pgrid, &c->psmem);
         // Single operator applications (sfista_apply, the objective, reverse
         // mode) then take the fused operator kernel as well.
         if (c->pfused && !band_op_fused_prepare(c->r, std::max(h.A.w, h.AT.w), std::max(h.B.w, h.BT.w)))
@@ -897,6 +933,17 @@ sfista_status sfista_batch_create(sfista_ctx *const *ctxs, int nprob, sfista_bat
             batch_free(b);
             return st;
         }
+        std::vector<int2> items;
+        if (band_solve_fused_batch_config(b->h_probs.data(), nprob, b->dev, &items, &b->fsmem)) {
+            if ((e = cudaMalloc((void **)&b->d_fitems, items.size() * sizeof(int2))) ||
+                (e = cudaMemcpy(b->d_fitems, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice)) ||
+                (e = cudaMalloc((void **)&b->bar, kBarrierBytes))) {
+                batch_free(b);
+                return fail(SFISTA_ENOMEM, std::string("one-launch batch tables: ") + cudaGetErrorString(e));
+            }
+            b->fnitems = (int)items.size();
+            b->fused_ok = b->use_fused = true;
+        }
     }
     *out = b;
     return SFISTA_OK;
@@ -956,7 +1003,10 @@ sfista_status sfista_batch_solve(sfista_batch *b, const float *const *d_b, const
                                 b->stream));
         SF_CUDA(cudaStreamSynchronize(b->stream));   // host staging array is reused on the next solve
     }
-    if (iters > 0) {
+    if (iters > 0 && b->use_fused) {
+        SF_CUDA(launch_band_solve_fused_batch(b->fnitems, b->fsmem, b->d_probs, b->d_fitems, iters, b->bar,
+                                              b->stream));
+    } else if (iters > 0) {
         std::vector<double> lams(lambdas, lambdas + np);
         if (!(b->gexec && b->g_iters == iters && b->g_lams == lams)) {
             if (b->gexec) {
@@ -1037,8 +1087,31 @@ sfista_status sfista_batch_tune(sfista_batch *b, int iters, sfista_tune_entry *e
     int count = 0;
     float best = -1.f;
     size_t best_budget = 0;
+    bool best_fused = false;
     sfista_status st = SFISTA_OK;
+    if (b->fused_ok) {   // the one-launch solve of the whole batch
+        b->use_fused = true;
+        float ms = 0.f;
+        cudaError_t e = cudaSuccess;
+        if (!(st = sfista_batch_solve(b, d_b.data(), lams.data(), 2, d_x.data(), b->stream))) {
+            e = cudaEventRecord(e0, b->stream);
+            if (!e && !(st = sfista_batch_solve(b, d_b.data(), lams.data(), iters, d_x.data(), b->stream)))
+                e = cudaEventRecord(e1, b->stream);
+            if (!st && !e) e = cudaEventSynchronize(e1);
+            if (!st && !e) e = cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (!st && e) st = fail(SFISTA_ECUDA, std::string("batch tuning: ") + cudaGetErrorString(e));
+        if (!st) {
+            ms /= iters;
+            if (entries && count < max_entries) entries[count] = sfista_tune_entry{SFISTA_OP_BANDED_PERSISTENT, -1, 0, ms};
+            ++count;
+            best = ms;
+            best_fused = true;
+        }
+        b->use_fused = false;
+    }
     for (size_t bud : budgets) {
+        if (st) break;
         if ((st = band_batch_plan(b, bud))) break;
         std::vector<int> sig;
         for (const BandProb &P : b->h_probs) sig.push_back(P.rows_chunk), sig.push_back(P.cols_chunk);
@@ -1060,12 +1133,13 @@ sfista_status sfista_batch_tune(sfista_batch *b, int iters, sfista_tune_entry *e
         ms /= iters;
         if (entries && count < max_entries) entries[count] = sfista_tune_entry{SFISTA_OP_BANDED, -1, (int)(bud / kb), ms};
         ++count;
-        if (best < 0.f || ms < best) best = ms, best_budget = bud;
+        if (best < 0.f || ms < best) best = ms, best_budget = bud, best_fused = false;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st) return st;
-    if ((st = band_batch_plan(b, best_budget))) return st;
+    b->use_fused = best_fused;
+    if (!best_fused && (st = band_batch_plan(b, best_budget))) return st;
     if (n_entries) *n_entries = count;
     return sfista_batch_sync(b, nullptr);
 }
@@ -1241,7 +1315,7 @@ sfista_status sfista_tune(sfista_ctx *c, int iters, sfista_tune_entry *entries, 
                 // The one-launch fused solver, when every tile has a resident block.
                 int grid = 0;
                 size_t smem = 0;
-                if (band_solve_fused_config(c->m, c->n, c->r, h.A, h.B, h.AT, h.BT, c->dev, &grid, &smem)) {
+                if (band_solve_fused_config(ctx_prob(c), c->dev, &grid, &smem)) {
                     if (!c->bar) {
                         SF_CUDA(cudaMalloc((void **)&c->bar, kBarrierBytes));
                         SF_CUDA(cudaMemset(c->bar, 0, kBarrierBytes));

@@ -116,14 +116,6 @@ cudaError_t launch_persistent(int grid, size_t smem, int rows_chunk, int cols_ch
                               const Band &BT, float *Z, float *R, float2 *Xb0, float2 *Xb1, const ProxArgs &pa,
                               int k0, int iters, unsigned *bar, cudaStream_t s);
 
-// The whole solve in one cooperative launch of the fused operator kernel
-// (kernels_fused.cu), when every 32 x 32 output tile has a resident block.
-bool band_solve_fused_config(int m, int n, int r, const Band &A, const Band &B, const Band &AT, const Band &BT,
-                             int dev, int *grid, size_t *smem);
-cudaError_t launch_band_solve_fused(int grid, size_t smem, int m, int n, int r, const float *fA, const Band &A,
-                                    const float *fB, const Band &B, const float *fAT, const Band &AT,
-                                    const float *fBT, const Band &BT, float *R, float2 *Xb0, float2 *Xb1,
-                                    const ProxArgs &pa, int k0, int iters, unsigned *bar, cudaStream_t s);
 // Bytes of grid-barrier words the persistent solvers use.
 constexpr size_t kBarrierBytes = 1024;
 
@@ -140,6 +132,17 @@ struct BandProb {
 struct BandItem {
     int prob, q, tile, pad;   // rows pass: q = term chunk; cols pass: q = 0
 };
+
+// The whole solve in one cooperative launch of the fused operator kernel
+// (kernels_fused.cu), when every 32 x 32 output tile has a resident block:
+// for one problem, or for a batch (one block per tile of every problem).
+// The descriptor's pa.Xin / pa.Xout are the state buffers 0 / 1.
+bool band_solve_fused_config(const BandProb &prob, int dev, int *grid, size_t *smem);
+cudaError_t launch_band_solve_fused(int grid, size_t smem, const BandProb &prob, int k0, int iters, unsigned *bar,
+                                    cudaStream_t s);
+bool band_solve_fused_batch_config(const BandProb *probs, int np, int dev, std::vector<int2> *items, size_t *smem);
+cudaError_t launch_band_solve_fused_batch(int nitems, size_t smem, const BandProb *d_probs, const int2 *d_items,
+                                          int iters, unsigned *bar, cudaStream_t s);
 void persistent_chunks(int r, int wmax, int *rows_chunk, int *cols_chunk, size_t *smem);
 // Term chunks of the grouped batch kernels: the requested ones (> 0, e.g.
 // from the autotuner) when they fit, else the persistent solver's rule.

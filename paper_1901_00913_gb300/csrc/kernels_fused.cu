@@ -36,6 +36,7 @@
 // two-pass count); at small and medium sizes the launch and load latency
 // saved outweighs it.
 #include <algorithm>
+#include <vector>
 
 #include "band_items.cuh"
 #include "epilogue.cuh"
@@ -384,13 +385,15 @@ __global__ void __launch_bounds__(NT, PRE ? 2 : 0) band_op_fused_kernel(const fl
 
 // ---------------------------------------------------------------------------
 // The whole solve in one cooperative launch, when every output tile has its
-// own resident block (tiles <= co-resident blocks).  Each block keeps, for
-// the whole solve,
+// own resident block (tiles <= co-resident blocks), for one problem or for a
+// batch of problems of any size, PSF and rank (one block per tile of every
+// problem; each block copies its problem's descriptor, a BandProb, into
+// shared memory).  Each block keeps, for the whole solve,
 //   - the band tiles of both operator applications (A, B and A^T, B^T) in
 //     shared memory (staged once),
-//   - the double-float state (Y_k, X_{k-1}) and the observed image of its
-//     epilogue pixels in registers (the epilogue's pixel -> thread map is the
-//     same in every iteration),
+//   - the double-float state (Y_k, X_{k-1}) of its epilogue pixels in
+//     registers (the epilogue's pixel -> thread map is the same in every
+//     iteration),
 // and per iteration runs the forward application with the residual
 // epilogue and the adjoint application with Step 1 + Step 3.  Only R and
 // the FP32 operand copy of Y_{k+1} go through global memory (other blocks
@@ -401,16 +404,9 @@ __global__ void __launch_bounds__(NT, PRE ? 2 : 0) band_op_fused_kernel(const fl
 // the operand copy of Y after their writes, and their next overwrite after
 // the reads).  Its wait is bounded (about one second); a block that gives up
 // records DEV_TIMEOUT and returns.
-struct FusedSolveArgs {
-    int m, n, r;
-    const float *fA, *fB, *fAT, *fBT;
-    int loA, wA, loB, wB, loAT, wAT, loBT, wBT;
-    float *R;
-    ProxArgs pa;           // Bd, Y, Yop, beta, constants, status
-    float2 *Xb0, *Xb1;     // X_{k0} in Xb[k0 & 1]; X_{k0+iters} goes to Xb[(k0+iters) & 1]
-    int k0, iters;
-    unsigned *bar;         // kBarWords arrival counters, 32 words apart, zero at launch
-};
+// The descriptor's pa.Xin / pa.Xout are the problem's state buffers 0 / 1:
+// X_{k0} is read from buffer k0 & 1, X_{k0+iters} and X_{k0+iters-1} are
+// written to buffers (k0+iters) & 1 and (k0+iters-1) & 1.
 
 constexpr int kBarWords = 8;
 constexpr long long kSpinCycles = 2000000000LL;   // about one second
@@ -484,84 +480,95 @@ __device__ __forceinline__ void solve_phase(const FusedGeom &g, const float *In,
     fused_passes(g, r, sm, sm + off_f, sm + off_g, sm + off_z, acc);
 }
 
-__global__ void __launch_bounds__(NT, 2) band_solve_fused(FusedSolveArgs a) {
+template <bool BATCH>
+__global__ void __launch_bounds__(NT, 2) band_solve_fused(BandProb one, const BandProb *__restrict__ probs,
+                                                       const int2 *__restrict__ items, int k0, int iters,
+                                                       unsigned *bar) {
     extern __shared__ __align__(16) float sm[];
+    __shared__ BandProb P;
     __shared__ SolveLayout Ls;
-    __shared__ int abort_sh;
-    const int m = a.m, n = a.n, r = a.r;
-    const int tiles_c = (n + TC - 1) / TC;
-    const int a0 = (blockIdx.x / tiles_c) * TA, c0 = (blockIdx.x % tiles_c) * TC;
+    __shared__ int tile_sh, abort_sh;
     if (threadIdx.x == 0) {
         abort_sh = 0;
-        Ls = solve_layout(r, a.loA, a.wA, a.wB, a.loAT, a.wAT, a.wBT);
+        if (BATCH) {
+            const int2 it = items[blockIdx.x];
+            P = probs[it.x];
+            tile_sh = it.y;
+        } else {
+            P = one;
+            tile_sh = blockIdx.x;
+        }
+        Ls = solve_layout(P.r, P.loA, P.wA, P.wB, P.loAT, P.wAT, P.wBT);
     }
     __syncthreads();
+    const int m = P.m, n = P.n, r = P.r;
+    const int tiles_c = (n + TC - 1) / TC;
+    const int a0 = (tile_sh / tiles_c) * TA, c0 = (tile_sh % tiles_c) * TC;
     {
         const SolveLayout L = Ls;
-        stage_bands<true>(L.gf, r, a.fA, a.wA, a.fB, a.wB, m, n, a0, c0, sm + L.off_ff, sm + L.off_gf);
-        stage_bands<true>(L.gt, r, a.fAT, a.wAT, a.fBT, a.wBT, m, n, a0, c0, sm + L.off_ft, sm + L.off_gt);
+        stage_bands<true>(L.gf, r, P.fA, P.wA, P.fB, P.wB, m, n, a0, c0, sm + L.off_ff, sm + L.off_gf);
+        stage_bands<true>(L.gt, r, P.fAT, P.wAT, P.fBT, P.wBT, m, n, a0, c0, sm + L.off_ft, sm + L.off_gt);
     }
     const int rb = (threadIdx.x >> 5) * 4, gc = c0 + (threadIdx.x & 31);   // epilogue pixels
+    float2 *const Xb0 = const_cast<float2 *>(P.pa.Xin), *const Xb1 = P.pa.Xout;
     float2 y[4], xp[4];
     {
-        ProxArgs pa = a.pa;
-        pa.Xin = (a.k0 & 1) ? a.Xb1 : a.Xb0;
+        ProxArgs pa = P.pa;
+        pa.Xin = (k0 & 1) ? Xb1 : Xb0;
         size_t idx[4];
         bool ok[4];
         epi_index(m, n, a0 + rb, gc, idx, ok);
         prox_load_n<4>(pa, idx, ok, y, xp);
     }
-    const int kend = a.k0 + a.iters;
+    const int kend = k0 + iters;
     unsigned nth = 0;
-    for (int k = a.k0 + 1; k <= kend; ++k) {
-        // Forward operator + residual: R = A_s Y_k - B.
-        {
+    for (int k = k0 + 1; k <= kend; ++k) {
+        {   // Forward operator + residual: R = A_s Y_k - B.
             size_t idx[4];
             bool ok[4];
             epi_index(m, n, a0 + rb, gc, idx, ok);
             float bv[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) bv[j] = ok[j] ? __ldcg(a.pa.Bd + idx[j]) : 0.f;
+            for (int j = 0; j < 4; ++j) bv[j] = ok[j] ? __ldcg(P.pa.Bd + idx[j]) : 0.f;
             float acc[4] = {0.f, 0.f, 0.f, 0.f};
-            solve_phase(Ls.gf, a.pa.Yop, m, n, r, a.loB, a.loA, Ls.off_ff, Ls.off_gf, Ls.off_z, sm, a0, c0, acc);
+            solve_phase(Ls.gf, P.pa.Yop, m, n, r, P.loB, P.loA, Ls.off_ff, Ls.off_gf, Ls.off_z, sm, a0, c0, acc);
 #pragma unroll
             for (int j = 0; j < 4; ++j)
-                if (ok[j]) a.R[idx[j]] = acc[j] - bv[j];
+                if (ok[j]) P.R[idx[j]] = acc[j] - bv[j];
         }
-        if (!fused_grid_sync(a.bar, ++nth, a.pa.status, &abort_sh)) return;
-        // Adjoint + Step 1 shrink + Step 3 momentum.
-        {
-            const float2 beta = a.pa.beta[k - 1];
+        if (!fused_grid_sync(bar, ++nth, P.pa.status, &abort_sh)) return;
+        {   // Adjoint + Step 1 shrink + Step 3 momentum.
+            const float2 beta = P.pa.beta[k - 1];
             float acc[4] = {0.f, 0.f, 0.f, 0.f};
-            solve_phase(Ls.gt, a.R, m, n, r, a.loBT, a.loAT, Ls.off_ft, Ls.off_gt, Ls.off_z, sm, a0, c0, acc);
+            solve_phase(Ls.gt, P.R, m, n, r, P.loBT, P.loAT, Ls.off_ft, Ls.off_gt, Ls.off_z, sm, a0, c0, acc);
             size_t idx[4];
             bool ok[4];
             epi_index(m, n, a0 + rb, gc, idx, ok);
-            float2 *Xlast = ((k - 1) & 1) ? a.Xb1 : a.Xb0;   // X_{k-1}: kept for a resumed solve
+            float2 *Xlast = ((k - 1) & 1) ? Xb1 : Xb0;   // X_{k-1}: kept for a resumed solve
             bool bad = false;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 if (!ok[j]) continue;
                 float2 x;
-                const float2 yn = prox_step(a.pa, y[j], xp[j], acc[j], beta, &x, &bad);
-                store_operands(a.pa, idx[j], yn);
+                const float2 yn = prox_step(P.pa, y[j], xp[j], acc[j], beta, &x, &bad);
+                store_operands(P.pa, idx[j], yn);
                 if (k == kend) Xlast[idx[j]] = xp[j];
                 xp[j] = x;
                 y[j] = yn;
             }
-            if (bad) atomicOr(a.pa.status, DEV_NONFINITE);
+            if (bad) atomicOr(P.pa.status, DEV_NONFINITE);
         }
-        if (!fused_grid_sync(a.bar, ++nth, a.pa.status, &abort_sh)) return;
+        if (!fused_grid_sync(bar, ++nth, P.pa.status, &abort_sh)) return;
     }
     size_t idx[4];
     bool ok[4];
     epi_index(m, n, a0 + rb, gc, idx, ok);
-    float2 *Xout = (kend & 1) ? a.Xb1 : a.Xb0;
+    float2 *Xout = (kend & 1) ? Xb1 : Xb0;
 #pragma unroll
     for (int j = 0; j < 4; ++j)
         if (ok[j]) {
             Xout[idx[j]] = xp[j];
-            a.pa.Y[idx[j]] = y[j];
+            P.pa.Y[idx[j]] = y[j];
         }
 }
 
@@ -634,58 +641,86 @@ void launch_band_op_fused(const float *In, int m, int n, int r, const float *Fb,
         launch_epi<EPI_PROX>(cfg, vec, pre, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out, pa);
 }
 
-// Grid and shared memory of the one-launch fused solver; false when a tile
-// does not fit, the 16-byte path does not apply, or the tiles outnumber the
-// co-resident blocks (the caller then takes the two-pass persistent solver).
-bool band_solve_fused_config(int m, int n, int r, const Band &A, const Band &B, const Band &AT, const Band &BT,
-                             int dev, int *grid, size_t *smem) {
-    if (m % 4 || n % 4) return false;
-    *smem = sizeof(float) * solve_layout(r, A.lo, A.w, B.w, AT.lo, AT.w, BT.w).total;
-    if (*smem > kFusedSmemMax) return false;
-    if (cudaFuncSetAttribute(band_solve_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem) != cudaSuccess)
+namespace {
+
+// The most dynamic shared memory a block of `kernel` may take: the device's
+// opt-in maximum less the kernel's static shared memory.
+int max_dynamic_smem(const void *kernel, int dev) {
+    cudaFuncAttributes fa{};
+    int optin = 0;
+    if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return 0;
+    return optin - (int)fa.sharedSizeBytes;
+}
+
+// Shared memory and co-residency of the one-launch solver over `np`
+// problems; false when a tile does not fit, the 16-byte path does not apply
+// or the tiles outnumber the co-resident blocks.
+template <bool BATCH>
+bool solve_fused_fits(const BandProb *probs, int np, int dev, long *tiles, size_t *smem) {
+    *tiles = 0;
+    *smem = 0;
+    for (int p = 0; p < np; ++p) {
+        const BandProb &P = probs[p];
+        if (P.m % 4 || P.n % 4) return false;
+        *smem = std::max(*smem, sizeof(float) * solve_layout(P.r, P.loA, P.wA, P.wB, P.loAT, P.wAT, P.wBT).total);
+        *tiles += (long)((P.m + TA - 1) / TA) * ((P.n + TC - 1) / TC);
+    }
+    // The attribute is per kernel, not per launch: allow the largest size, so
+    // that a later, smaller configuration never lowers an earlier one's limit.
+    const int lim = max_dynamic_smem((const void *)band_solve_fused<BATCH>, dev);
+    if (*smem > (size_t)lim) return false;
+    if (cudaFuncSetAttribute(band_solve_fused<BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) !=
+        cudaSuccess)
         return false;
     int per_sm = 0, sms = 0, coop = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, band_solve_fused, NT, *smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, band_solve_fused<BATCH>, NT, *smem) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess)
         return false;
-    const long tiles = (long)((m + TA - 1) / TA) * ((n + TC - 1) / TC);
-    if (!coop || per_sm < 1 || tiles > (long)per_sm * sms) return false;
+    return coop && per_sm >= 1 && *tiles <= (long)per_sm * sms;
+}
+
+}  // namespace
+
+bool band_solve_fused_config(const BandProb &prob, int dev, int *grid, size_t *smem) {
+    long tiles = 0;
+    if (!solve_fused_fits<false>(&prob, 1, dev, &tiles, smem)) return false;
     *grid = (int)tiles;
     return true;
 }
 
-cudaError_t launch_band_solve_fused(int grid, size_t smem, int m, int n, int r, const float *fA, const Band &A,
-                                    const float *fB, const Band &B, const float *fAT, const Band &AT,
-                                    const float *fBT, const Band &BT, float *R, float2 *Xb0, float2 *Xb1,
-                                    const ProxArgs &pa, int k0, int iters, unsigned *bar, cudaStream_t s) {
-    FusedSolveArgs a{};
-    a.m = m;
-    a.n = n;
-    a.r = r;
-    a.fA = fA;
-    a.fB = fB;
-    a.fAT = fAT;
-    a.fBT = fBT;
-    a.loA = A.lo;
-    a.wA = A.w;
-    a.loB = B.lo;
-    a.wB = B.w;
-    a.loAT = AT.lo;
-    a.wAT = AT.w;
-    a.loBT = BT.lo;
-    a.wBT = BT.w;
-    a.R = R;
-    a.pa = pa;
-    a.Xb0 = Xb0;
-    a.Xb1 = Xb1;
-    a.k0 = k0;
-    a.iters = iters;
-    a.bar = bar;
+cudaError_t launch_band_solve_fused(int grid, size_t smem, const BandProb &prob, int k0, int iters, unsigned *bar,
+                                    cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(bar, 0, kBarrierBytes, s);
     if (e) return e;
-    void *args[] = {&a};
-    return cudaLaunchCooperativeKernel((const void *)band_solve_fused, dim3(grid), dim3(NT), args, smem, s);
+    BandProb one = prob;
+    const BandProb *probs = nullptr;
+    const int2 *items = nullptr;
+    void *args[] = {&one, &probs, &items, &k0, &iters, &bar};
+    return cudaLaunchCooperativeKernel((const void *)band_solve_fused<false>, dim3(grid), dim3(NT), args, smem, s);
+}
+
+bool band_solve_fused_batch_config(const BandProb *probs, int np, int dev, std::vector<int2> *items, size_t *smem) {
+    long tiles = 0;
+    if (!solve_fused_fits<true>(probs, np, dev, &tiles, smem)) return false;
+    items->clear();
+    for (int p = 0; p < np; ++p) {
+        const int t = ((probs[p].m + TA - 1) / TA) * ((probs[p].n + TC - 1) / TC);
+        for (int i = 0; i < t; ++i) items->push_back(make_int2(p, i));
+    }
+    return true;
+}
+
+cudaError_t launch_band_solve_fused_batch(int nitems, size_t smem, const BandProb *d_probs, const int2 *d_items,
+                                          int iters, unsigned *bar, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(bar, 0, kBarrierBytes, s);
+    if (e) return e;
+    BandProb one{};
+    int k0 = 0;
+    void *args[] = {&one, &d_probs, &d_items, &k0, &iters, &bar};
+    return cudaLaunchCooperativeKernel((const void *)band_solve_fused<true>, dim3(nitems), dim3(NT), args, smem, s);
 }
 
 }  // namespace sfista

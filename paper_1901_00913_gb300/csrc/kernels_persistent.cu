@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(PT) band_solve_persistent(PersistArgs a) {
 }  // namespace
 
 constexpr size_t kPersistSmemBudget = 100 * 1024;   // two blocks per SM
+constexpr size_t kPersistSmemMax = 227 * 1024;      // the most one block may use
 
 // Terms staged per load phase so that one item fits the shared-memory budget.
 void persistent_chunks(int r, int wmax, int *rows_chunk, int *cols_chunk, size_t *smem) {
@@ -214,10 +215,14 @@ int band_cols_tiles(int m, int n, bool vec) {
     return vec ? band4::tiles(64, m, n) : ((m + PC_A - 1) / PC_A) * ((n + PC_C - 1) / PC_C);
 }
 
+// The attribute is per kernel, not per batch: allow the largest size, so that
+// a later batch with smaller tiles never lowers an earlier batch's limit.
 cudaError_t band_grouped_prepare(size_t smem) {
-    cudaError_t e = cudaFuncSetAttribute(band_rows_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem > kPersistSmemMax) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(band_rows_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kPersistSmemMax);
     if (e) return e;
-    return cudaFuncSetAttribute(band_cols_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(band_cols_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPersistSmemMax);
 }
 
 void launch_band_grouped_stage(int st, const BandProb *probs, const BandItem *items, int nitems, int k, size_t smem,
@@ -231,8 +236,16 @@ void launch_band_grouped_stage(int st, const BandProb *probs, const BandItem *it
 sfista_status persistent_config(int m, int n, int r, int wmax, int dev, int *grid, size_t *smem, int *rows_chunk,
                                 int *cols_chunk) {
     persistent_chunks(r, wmax, rows_chunk, cols_chunk, smem);
-    cudaError_t e = cudaFuncSetAttribute(band_solve_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)*smem);
+    // The attribute is per kernel: the largest size it may take (the device's
+    // opt-in maximum less its static shared memory), never this one's.
+    cudaFuncAttributes fa{};
+    int optin = 0;
+    cudaError_t e = cudaFuncGetAttributes(&fa, band_solve_persistent);
+    if (!e) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e) return fail(SFISTA_ECUDA, std::string("persistent attributes: ") + cudaGetErrorString(e));
+    const int lim = optin - (int)fa.sharedSizeBytes;
+    if (*smem > (size_t)lim) return fail(SFISTA_ENOTSUP, "persistent solver tile exceeds shared memory");
+    e = cudaFuncSetAttribute(band_solve_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e != cudaSuccess) return fail(SFISTA_ENOTSUP, std::string("persistent smem: ") + cudaGetErrorString(e));
     int per_sm = 0, sms = 0, coop = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, band_solve_persistent, PT, *smem)) ||

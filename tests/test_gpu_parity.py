@@ -240,6 +240,39 @@ def test_one_launch_solver_band_offsets(psf_shape, centre, r):
     assert np.array_equal(outs["banded_persistent"], outs["banded_fused"])
 
 
+def test_earlier_contexts_keep_their_launch_limits():
+    """Kernel attributes are per kernel, not per context or batch: creating a
+    context (and a batch) with a smaller shared-memory layout after a larger
+    one must leave the larger one launchable, for the one-launch solver, the
+    two-launch fused form and the grouped batch."""
+    g = W.rng(150)
+    big = W.rotated_gaussian_psf(31, 3.0, 1.0, 0.5)
+    small = W.random_psf(g, 5, 5)
+    m, n = 96, 128
+    x, b, _ = _problem(m, n, big, 1, 151)
+    ka = kron.kron_approx(big, 15, 15, m, n, 1, 3)
+    L = _oracle_L(ka)
+    Xo = oracle.sfista(b.astype(np.float64), ka, L, 0.005, 15)
+    db = _cuda(b)
+    for op in ("banded_persistent", "banded_fused"):
+        s_big = api.Sfista(big, (m, n), 1, 3, prec="fp32", op=op, lipschitz=L)
+        s_small = api.Sfista(small, (64, 64), 1, 1, prec="fp32", op=op, lipschitz=1.0)
+        X = s_big.solve_device(db, 0.005, 15).cpu().numpy()
+        assert oracle.rel_fro(X, Xo) <= TOL["fp32"], op
+        s_small.close()
+        s_big.close()
+    s_big = api.Sfista(big, (m, n), 1, 3, prec="fp32", op="banded", lipschitz=L)
+    s_small = api.Sfista(small, (64, 64), 1, 1, prec="fp32", op="banded", lipschitz=1.0)
+    batch_big = api.Batch([s_big])
+    batch_small = api.Batch([s_small])
+    X = batch_big.solve([db], [0.005], 15)[0].cpu().numpy()
+    assert oracle.rel_fro(X, Xo) <= TOL["fp32"]
+    batch_small.close()
+    batch_big.close()
+    s_small.close()
+    s_big.close()
+
+
 def test_graph_and_direct_launch_agree():
     P = W.rotated_gaussian_psf(15, 2.0, 1.0, 0.3)
     x, b, _ = _problem(96, 80, P, 1, 106)

@@ -101,7 +101,10 @@ def test_batch_tune_keeps_results():
     before = [X.clone() for X in batch.solve(d_bs, [lam] * len(pr), iters)]
     log = batch.tune(iters=3)
     assert log and all(e["ms"] > 0 for e in log)
-    assert len({e["budget_kb"] for e in log}) == len(log)    # distinct plans only
+    plans = [(e["op"], e["budget_kb"]) for e in log]
+    assert len(set(plans)) == len(plans)    # distinct plans only
+    # 4 + 4x3 + 2x2 + 7x6 tiles of 32 x 32: the one-launch plan is a candidate
+    assert ("banded_persistent", 0) in plans
     after = batch.solve(d_bs, [lam] * len(pr), iters)
     for X0, X1, (P, b, ka, L) in zip(before, after, pr):
         assert torch.equal(X0, X1)     # chunking regroups terms, not the arithmetic
