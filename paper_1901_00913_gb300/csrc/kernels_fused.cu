@@ -421,14 +421,17 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
 // blockIdx % kBarWords, and warp 0 polls the kBarWords counters (one lane
 // each) until their sum reaches nth * gridDim.x.  The poll is bounded; a
 // block that gives up records DEV_TIMEOUT and returns false.
+// Ordering: the block barrier puts every thread's earlier writes before
+// thread 0's release add, a release is cumulative over what precedes it, and
+// a poller's acquire load that reads the count synchronises with the adds it
+// counts; the block barrier after the poll extends that to the whole block.
 __device__ bool fused_grid_sync(unsigned *bar, unsigned nth, unsigned *status, int *abort_sh) {
     __syncthreads();
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
-        if (lane == 0) {
-            __threadfence();
-            atomicAdd(bar + 32 * (blockIdx.x % kBarWords), 1u);
-        }
+        if (lane == 0)
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar + 32 * (blockIdx.x % kBarWords))
+                         : "memory");
         __syncwarp();
         const unsigned target = nth * gridDim.x;
         const long long t0 = clock64();
@@ -443,7 +446,6 @@ __device__ bool fused_grid_sync(unsigned *bar, unsigned nth, unsigned *status, i
                 break;
             }
         }
-        __threadfence();
     }
     __syncthreads();
     return *abort_sh == 0;
