@@ -35,6 +35,10 @@
 // The row pass repeats the halo rows' work ((32 + wG4) / 32 times the
 // two-pass count); at small and medium sizes the launch and load latency
 // saved outweighs it.
+//
+// The same tile routines also run the whole solve in one cooperative launch
+// (band_solve_fused, end of this file) when every tile has its own resident
+// block, for one problem or a batch.
 #include <algorithm>
 #include <vector>
 
