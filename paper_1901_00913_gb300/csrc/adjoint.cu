@@ -48,7 +48,8 @@ __global__ void scale_f32(float *y, const float *x, float a, size_t n) {
 // current one is multiplied from shared memory.  The contraction (2 parts x S
 // steps x T rounded up to 16) is split across blockIdx.z for parallelism; each
 // split writes its partial tile and grad_reduce adds the splits in a fixed
-// order (deterministic).
+// order (deterministic).  Held to two blocks per SM (128 registers, a few
+// spilled): measured faster than one block with 150-160 registers.
 struct GradOperands {
     const float *P[2], *Q[2];
     long p_term, q_term, p_step, q_step, ld;
@@ -117,7 +118,7 @@ __device__ __forceinline__ void grad_store(float (*S)[GLD], int tid, const float
 }
 
 template <bool NT, bool VEC>
-__global__ void __launch_bounds__(256) grad_gemm(GradOperands o, float *partial) {
+__global__ void __launch_bounds__(256, 2) grad_gemm(GradOperands o, float *partial) {
     __shared__ __align__(16) float Ps[2][GK][GLD];
     __shared__ __align__(16) float Qs[2][GK][GLD];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
