@@ -25,14 +25,34 @@
 namespace sfista {
 namespace {
 
-__global__ void axpy_f64(double *y, const double *x, double a, size_t n) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        y[i] += a * x[i];
+// ybar = (L V - T) * inv, and sumV += V (one pass over V).
+__global__ void ybar_kernel(double *ybar, double *sumV, const double *V, const float *T, double L, double inv,
+                            size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double v = V[i];
+        ybar[i] = (L * v - (double)T[i]) * inv;
+        sumV[i] += 1.0 * v;
+    }
 }
-// ybar = (L V - T) * inv
-__global__ void ybar_kernel(double *ybar, const double *V, const float *T, double L, double inv, size_t n) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        ybar[i] = (L * V[i] - (double)T[i]) * inv;
+// End of a reverse step: xa += (1 + beta) ybar, xb += -beta ybar (when
+// `update`), and V = 0 (three distinct buffers).
+__global__ void step_update_kernel(double *xa, double *xb, double *V, const double *ybar, double beta, int update,
+                                   size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        if (update) {
+            const double y = ybar[i];
+            xa[i] += (1.0 + beta) * y;
+            xb[i] += -beta * y;
+        }
+        V[i] = 0.0;
+    }
+}
+// FP32 copies of V and (when Y is not NULL) Y in one pass.
+__global__ void to_f32_pair_kernel(const double *V, float *Vf, const double *Y, float *Yf, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        Vf[i] = (float)V[i];
+        if (Y) Yf[i] = (float)Y[i];
+    }
 }
 __global__ void scale_f32(float *y, const float *x, float a, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -363,13 +383,13 @@ extern "C" sfista_status sfista_unrolled_bwd(sfista_ctx *c, const float *d_b, do
     ob.splits = factors ? grad_splits(ob, sms) : 1;
     const size_t part_floats = factors ? (size_t)r * std::max((size_t)oa.splits * n * n, (size_t)ob.splits * m * m) : 1;
     Scratch sc;
-    double *segX, *segY, *xb, *sumV, *ybar, *dots, *partial, *dot2;
+    double *segX, *segY, *xb, *sumV, *ybar, *dots, *partial;
     float *Vf, *Wf, *Tf, *Rseg = nullptr, *Wseg = nullptr, *Vseg = nullptr, *Yseg = nullptr, *Useg = nullptr,
                          *U2seg = nullptr, *Zsseg = nullptr, *Zqseg = nullptr, *gpart = nullptr;
     cudaError_t e;
     if ((e = sc.get(&segX, (size_t)ce * N)) || (e = sc.get(&segY, (size_t)ce * N)) || (e = sc.get(&xb, 3 * N)) ||
         (e = sc.get(&sumV, N)) || (e = sc.get(&ybar, N)) || (e = sc.get(&dots, 2 * (size_t)iters)) ||
-        (e = sc.get(&partial, 512)) || (e = sc.get(&dot2, 2)) || (e = sc.get(&Vf, N)) || (e = sc.get(&Wf, N)) ||
+        (e = sc.get(&partial, 512)) || (e = sc.get(&Vf, N)) || (e = sc.get(&Wf, N)) ||
         (e = sc.get(&Tf, N)))
         return fail(SFISTA_ENOMEM, std::string("adjoint buffers: ") + cudaGetErrorString(e));
     if (factors &&
@@ -406,16 +426,14 @@ extern "C" sfista_status sfista_unrolled_bwd(sfista_ctx *c, const float *d_b, do
             double *V = xb + (size_t)(k % 3) * N;
             const double *Xk = segX + (size_t)(k - k0 - 1) * N, *Yk = segY + (size_t)(k - k0 - 1) * N;
             float *Vk = factors ? Vseg + (size_t)nb * N : Vf, *Wk = factors ? Wseg + (size_t)nb * N : Wf;
-            launch_f64_to_f32(V, Vk, N, s);
+            float *Yf = factors ? Yseg + (size_t)nb * N : nullptr;
+            to_f32_pair_kernel<<<grid1(N), 256, 0, s>>>(V, Vk, factors ? Yk : nullptr, Yf, N);
             As_apply(c, Vk, Wk, s);
             AsT_apply(c, Wk, Tf, s);
-            ybar_kernel<<<grid1(N), 256, 0, s>>>(ybar, V, Tf, L, inv, N);
-            axpy_f64<<<grid1(N), 256, 0, s>>>(sumV, V, 1.0, N);
-            launch_dots(Xk, V, N, partial, 256, dot2, s);
-            SF_CUDA(cudaMemcpyAsync(dots + 2 * (size_t)(k - 1), dot2, 16, cudaMemcpyDeviceToDevice, s));
+            ybar_kernel<<<grid1(N), 256, 0, s>>>(ybar, sumV, V, Tf, L, inv, N);
+            launch_dots(Xk, V, N, partial, 256, dots + 2 * (size_t)(k - 1), s);
             if (factors) {
-                float *Yf = Yseg + (size_t)nb * N, *Rf = Rseg + (size_t)nb * N;
-                launch_f64_to_f32(Yk, Yf, N, s);
+                float *Rf = Rseg + (size_t)nb * N;
                 As_apply(c, Yf, Rf, s, EPI_RESIDUAL);   // R_k = A_s Y_k - B
                 if (d_gA) {   // B_i V and B_i Y for every term, one launch each
                     launch_band_cols_each(Vk, m, n, c->fB, h.B.lo, h.B.w, r, Useg + (size_t)nb * r * N, s);
@@ -443,12 +461,12 @@ extern "C" sfista_status sfista_unrolled_bwd(sfista_ctx *c, const float *d_b, do
                     nb = 0;
                 }
             }
-            if (k >= 2) {
-                const double beta = c->beta_host[k - 2];   // beta_{k-1}
-                axpy_f64<<<grid1(N), 256, 0, s>>>(xb + (size_t)((k - 1) % 3) * N, ybar, 1.0 + beta, N);
-                axpy_f64<<<grid1(N), 256, 0, s>>>(xb + (size_t)((k - 2) % 3) * N, ybar, -beta, N);
+            {
+                const double beta = k >= 2 ? c->beta_host[k - 2] : 0.0;   // beta_{k-1}
+                step_update_kernel<<<grid1(N), 256, 0, s>>>(xb + (size_t)((k + 2) % 3) * N,
+                                                           xb + (size_t)((k + 1) % 3) * N, V, ybar, beta, k >= 2,
+                                                           N);
             }
-            SF_CUDA(cudaMemsetAsync(V, 0, N * 8, s));
         }
     }
     // dl/dB = A_s (sum_k V) / den
