@@ -210,8 +210,11 @@ sfista_status sfista_solve_state(sfista_ctx *ctx, const float *d_b,
  * sfista_batch_solve -- Alg. 2 from X_0 = 0 for every problem.
  *   d_b, d_x  host arrays of nprob device pointers (FP32, problem p is
  *             m_p x n_p); lambdas host array of nprob values.
- *   Asynchronous on `stream`; sfista_batch_sync reports device status of
- *   every problem (the first error found).
+ *   Asynchronous on `stream`: each d_b[p] is read, and d_x[p] written, in
+ *   stream order (an output may alias an input).  The one-launch form reads
+ *   d_b[p] in place and writes X_iters straight into d_x[p].
+ *   sfista_batch_sync reports device status of every problem (the first
+ *   error found).
  * sfista_solve_batched -- create, solve, sync and destroy in one call.
  */
 typedef struct sfista_batch sfista_batch;

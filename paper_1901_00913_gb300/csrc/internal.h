@@ -128,6 +128,7 @@ struct BandProb {
     int loA, wA, loB, wB, loAT, wAT, loBT, wBT;
     float *Z, *R;
     ProxArgs pa;   // Bd, Y, Yop, beta, constants, status; Xin / Xout = state buffers 0 / 1
+    float *xout;   // one-launch batch: the FP32 result X_iters, written by the solver itself
 };
 struct BandItem {
     int prob, q, tile, pad;   // rows pass: q = term chunk; cols pass: q = 0

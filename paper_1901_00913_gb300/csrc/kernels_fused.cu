@@ -518,7 +518,10 @@ __global__ void __launch_bounds__(NT, 2) band_solve_fused(BandProb one, const Ba
     const int rb = (threadIdx.x >> 5) * 4, gc = c0 + (threadIdx.x & 31);   // epilogue pixels
     float2 *const Xb0 = const_cast<float2 *>(P.pa.Xin), *const Xb1 = P.pa.Xout;
     float2 y[4], xp[4];
-    {
+    if (BATCH) {   // a batch starts from X_0 = X_{-1} = 0, so Y_1 = 0
+#pragma unroll
+        for (int j = 0; j < 4; ++j) y[j] = xp[j] = make_float2(0.f, 0.f);
+    } else {
         ProxArgs pa = P.pa;
         pa.Xin = (k0 & 1) ? Xb1 : Xb0;
         size_t idx[4];
@@ -537,7 +540,18 @@ __global__ void __launch_bounds__(NT, 2) band_solve_fused(BandProb one, const Ba
 #pragma unroll
             for (int j = 0; j < 4; ++j) bv[j] = ok[j] ? __ldcg(P.pa.Bd + idx[j]) : 0.f;
             float acc[4] = {0.f, 0.f, 0.f, 0.f};
-            solve_phase(Ls.gf, P.pa.Yop, m, n, r, P.loB, P.loA, Ls.off_ff, Ls.off_gf, Ls.off_z, sm, a0, c0, acc);
+            // A batch's first iteration applies A_s to Y_1 = 0: every sum is
+            // +0, so R = -B exactly and the passes are skipped (B is checked
+            // for non-finite values here instead of by a separate kernel).
+            if (BATCH && k == 1) {
+                bool bad = false;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) bad |= ok[j] && !isfinite(bv[j]);
+                if (bad) atomicOr(P.pa.status, DEV_NONFINITE);
+            } else {
+                solve_phase(Ls.gf, P.pa.Yop, m, n, r, P.loB, P.loA, Ls.off_ff, Ls.off_gf, Ls.off_z, sm, a0, c0,
+                            acc);
+            }
 #pragma unroll
             for (int j = 0; j < 4; ++j)
                 if (ok[j]) P.R[idx[j]] = acc[j] - bv[j];
@@ -558,7 +572,7 @@ __global__ void __launch_bounds__(NT, 2) band_solve_fused(BandProb one, const Ba
                 float2 x;
                 const float2 yn = prox_step(P.pa, y[j], xp[j], acc[j], beta, &x, &bad);
                 store_operands(P.pa, idx[j], yn);
-                if (k == kend) Xlast[idx[j]] = xp[j];
+                if (!BATCH && k == kend) Xlast[idx[j]] = xp[j];
                 xp[j] = x;
                 y[j] = yn;
             }
@@ -569,6 +583,12 @@ __global__ void __launch_bounds__(NT, 2) band_solve_fused(BandProb one, const Ba
     size_t idx[4];
     bool ok[4];
     epi_index(m, n, a0 + rb, gc, idx, ok);
+    if (BATCH) {   // the FP32 result, straight into the caller's output
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (ok[j]) P.xout[idx[j]] = dfp::to_float(xp[j]);
+        return;
+    }
     float2 *Xout = (kend & 1) ? Xb1 : Xb0;
 #pragma unroll
     for (int j = 0; j < 4; ++j)

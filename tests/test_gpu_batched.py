@@ -107,3 +107,36 @@ def test_batched_l1_per_problem(probs, prec, op, tol):
     batch.close()
     for s in solvers:
         s.close()
+
+
+def test_batch_table_refresh_and_aliasing(probs):
+    """Repeated solves of one batch (FP32 auto: the one-launch form, which
+    reads each B in place and writes each X itself) follow every change of
+    observations, weights and outputs, and an output may be its own input."""
+    pr, iters, _ = probs
+    solvers = [api.Sfista(P, b.shape, 1, ka.r, prec="fp32", lipschitz=L) for P, b, ka, L, lam in pr]
+    d_bs = [torch.from_numpy(b).cuda() for P, b, ka, L, lam in pr]
+    lams = [lam for *_, lam in pr]
+    batch = api.Batch(solvers)
+    outs = [torch.empty_like(d) for d in d_bs]
+
+    def singles(bs, ls):
+        return [s.solve_device(db, lam, iters) for s, db, lam in zip(solvers, bs, ls)]
+
+    for rep in range(2):    # same buffers: the second solve reuses the device table
+        batch.solve(d_bs, lams, iters, outs=outs)
+        for X, Y in zip(outs, singles(d_bs, lams)):
+            assert torch.equal(X, Y)
+    d_bs2 = [0.5 * d + 0.1 for d in d_bs]
+    lams2 = [2.0 * lam for lam in lams]
+    batch.solve(d_bs2, lams2, iters, outs=outs)
+    ref2 = singles(d_bs2, lams2)
+    for X, Y in zip(outs, ref2):
+        assert torch.equal(X, Y)
+    inplace = [d.clone() for d in d_bs2]
+    batch.solve(inplace, lams2, iters, outs=inplace)
+    for X, Y in zip(inplace, ref2):
+        assert torch.equal(X, Y)
+    batch.close()
+    for s in solvers:
+        s.close()
