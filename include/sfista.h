@@ -101,6 +101,15 @@ typedef struct {
                                with S_mu the soft threshold (the minimiser of Q_L of
                                Sec. 3.1 for that g; Sec. 1 and Sec. 5 name the l1 term
                                as future work).  Applied before the projection.         */
+    int refine_every;       /* k_ref >= 0 (default 0: off).  Tensor-core forms: in every
+                               iteration k that is a multiple of k_ref, the residual
+                               R_k = sum_i B_i Y_k A_i^T - B of Alg. 2 (the inner sum of
+                               Step 1) is computed by the FP32 band kernels from the
+                               FP32 factors instead of by the low-precision GEMMs, then
+                               converted to the adjoint GEMMs' operand format.  The
+                               FP32 band forms compute every residual this way already,
+                               so it has no effect there.  Batches reject contexts that
+                               set it on a tensor-core form (SFISTA_ENOTSUP).           */
 } sfista_opts;
 
 /* Fill *opts with the defaults listed above. */

@@ -37,7 +37,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("op", ctypes.c_int), ("project_nonneg", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("lipschitz", ctypes.c_double),
                 ("lipschitz_tol", ctypes.c_double), ("lipschitz_maxit", ctypes.c_int),
-                ("device", ctypes.c_int), ("l1", ctypes.c_double)]
+                ("device", ctypes.c_int), ("l1", ctypes.c_double), ("refine_every", ctypes.c_int)]
 
 
 def load(path=None):
@@ -406,7 +406,8 @@ class Sfista:
     """Owns one context: ``Sfista(psf, (m, n), 'reflexive', r=3, prec='bf16x3')``."""
 
     def __init__(self, psf, shape, bc, r, center=(-1, -1), prec="fp32", op="auto", project=False,
-                 use_graph=True, lipschitz=None, lipschitz_tol=1e-10, lipschitz_maxit=1000, device=-1, l1=0.0):
+                 use_graph=True, lipschitz=None, lipschitz_tol=1e-10, lipschitz_maxit=1000, device=-1, l1=0.0,
+                 refine_every=0):
         o = default_opts()
         o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
         o.op = OP[op] if isinstance(op, str) else int(op)
@@ -417,6 +418,7 @@ class Sfista:
         o.lipschitz_maxit = int(lipschitz_maxit)
         o.device = int(device)
         o.l1 = float(l1)
+        o.refine_every = int(refine_every)
         bcv = BC[bc] if isinstance(bc, str) else int(bc)
         self.shape = (int(shape[0]), int(shape[1]))
         self.psf_shape = np.asarray(psf).shape

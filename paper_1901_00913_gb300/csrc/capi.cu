@@ -208,6 +208,24 @@ void enqueue_stage(sfista_ctx *c, int st, const ProxArgs &pa) {
 }  // namespace
 void sfista::enqueue_iteration(sfista_ctx *c, int k, double lam) {
     ProxArgs pa = prox_args(c, k, lam);
+    if (c->gemm && c->opts.refine_every > 0 && k % c->opts.refine_every == 0) {
+        // Refined residual: R_k = A_s Y_k - B by the FP32 band passes (rows,
+        // then columns with the residual epilogue) on the FP32 value of Y_k,
+        // then split into the operand of the adjoint GEMMs.
+        const HostSetup &h = c->hs;
+        const float *y = c->Yf;   // the FP32 state holds Y_k itself
+        if (!y) {                 // double-float state: its FP32 value
+            launch_df_to_f32(c->Y, c->Yop, c->N, c->stream);
+            y = c->Yop;
+        }
+        launch_band_rows<float>(y, c->m, c->n, c->fA, h.A.lo, h.A.w, c->r, c->Z, c->stream, c->chunk[0]);
+        launch_band_cols<float>(c->Z, c->m, c->n, c->fB, h.B.lo, h.B.w, c->r, EPI_RESIDUAL, c->R, pa, c->stream,
+                                c->chunk[1]);
+        gemm_residual_operand(c->gemm, c->R, c->stream);
+        enqueue_stage(c, 2, pa);
+        enqueue_stage(c, 3, pa);
+        return;
+    }
     for (int st = 0; st < 4; ++st) enqueue_stage(c, st, pa);
 }
 namespace {
@@ -513,6 +531,7 @@ void sfista_default_opts(sfista_opts *o) {
     o->lipschitz_maxit = 1000;
     o->device = -1;
     o->l1 = 0.0;
+    o->refine_every = 0;
 }
 
 sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int center_row,
@@ -528,6 +547,7 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int ce
     if (o.op < SFISTA_OP_AUTO || o.op > SFISTA_OP_BANDED_FUSED) return fail(SFISTA_EINVAL, "unknown operator form");
     if (!(o.lipschitz <= 0.0 || isfinite(o.lipschitz))) return fail(SFISTA_EINVAL, "lipschitz must be finite");
     if (!(o.l1 >= 0.0) || !isfinite(o.l1)) return fail(SFISTA_EINVAL, "l1 must be finite and >= 0");
+    if (o.refine_every < 0) return fail(SFISTA_EINVAL, "refine_every must be >= 0");
     if (center_row == -1 && psf_rows > 0) center_row = (psf_rows - 1) / 2;
     if (center_col == -1 && psf_cols > 0) center_col = (psf_cols - 1) / 2;
     sfista_ctx *c = new (std::nothrow) sfista_ctx();
@@ -878,6 +898,8 @@ sfista_status sfista_batch_create(sfista_ctx *const *ctxs, int nprob, sfista_bat
             return fail(SFISTA_EINVAL, "batched problems need one device, one precision and one operator family");
         for (int q = 0; q < p; ++q)
             if (ctxs[q] == ctxs[p]) return fail(SFISTA_EINVAL, "a context appears twice in the batch");
+        if (gp && ctxs[p]->opts.refine_every > 0)
+            return fail(SFISTA_ENOTSUP, "residual refinement is not available in batched solves");
     }
     sfista_batch *b = new (std::nothrow) sfista_batch();
     if (!b) return fail(SFISTA_ENOMEM, "batch allocation failed");

@@ -1065,6 +1065,10 @@ void gemm_batch_stage(GemmBatch *b, int st, int k, cudaStream_t s) {
 
 int gemm_batch_launches_per_iteration(const GemmBatch *) { return 4; }
 
+void gemm_residual_operand(GemmPath *g, const float *R, cudaStream_t s) {
+    launch_split(R, g->QR.hi, g->split ? g->QR.lo : nullptr, (size_t)g->m * g->n, g->split_kind, s);
+}
+
 sfista_status gemm_apply(GemmPath *g, const float *x, float *y, int transpose, cudaStream_t s) {
     const size_t N = (size_t)g->m * g->n;
     Operand &in = transpose ? g->QR : g->QY;

@@ -24,6 +24,9 @@ void gemm_prepare_solve(GemmPath *g, const float *Bd, cudaStream_t s);
 // Stage st (0..3) of one iteration of Alg. 2: the four GEMMs with the
 // residual (stage 1) and prox / momentum (stage 3) epilogues.
 void gemm_stage(GemmPath *g, int st, const ProxArgs &pa, cudaStream_t s);
+// Converts an FP32 residual R (m x n) into the operand of stages 2 and 3
+// (what stage 1 writes), for residuals computed outside the GEMMs.
+void gemm_residual_operand(GemmPath *g, const float *R, cudaStream_t s);
 // The operator alone (transpose = 0: A_s, 1: A_s^T) on FP32 device buffers.
 sfista_status gemm_apply(GemmPath *g, const float *x, float *y, int transpose, cudaStream_t s);
 

@@ -107,3 +107,13 @@ def test_default_opts(lib):
     o = api.default_opts()
     assert o.prec == 0 and o.op == 0 and o.use_graph == 1 and o.device == -1
     assert o.lipschitz == 0.0 and o.lipschitz_maxit > 0
+    assert o.l1 == 0.0 and o.refine_every == 0
+
+
+@pytest.mark.parametrize("field,value", [("refine_every", -1), ("l1", -0.5), ("prec", 9)])
+def test_option_errors(lib, field, value):
+    o = api.default_opts()
+    setattr(o, field, value)
+    with pytest.raises(api.SfistaError) as ei:
+        api.sfista_setup(W.gaussian_psf(9, 2.0), 64, 64, 1, 2, (-1, -1), o)
+    assert ei.value.status == api.EINVAL
