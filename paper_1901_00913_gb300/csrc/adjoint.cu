@@ -303,7 +303,8 @@ void As_apply(sfista_ctx *c, const float *x, float *out, cudaStream_t s, EpiKind
     ProxArgs pa{};
     pa.Bd = c->Bd;
     if (fused_apply(c)) {
-        launch_band_op_fused(x, c->m, c->n, c->r, c->fA, h.A.lo, h.A.w, c->fB, h.B.lo, h.B.w, epi, out, pa, s);
+        launch_band_op_fused(x, c->m, c->n, c->r, c->fA, h.A.lo, h.A.w, c->fB, h.B.lo, h.B.w, epi, out, pa,
+                             interior_fwd(c), s);
         return;
     }
     launch_band_rows<float>(x, c->m, c->n, c->fA, h.A.lo, h.A.w, c->r, c->Z, s);
@@ -314,7 +315,7 @@ void AsT_apply(sfista_ctx *c, const float *x, float *out, cudaStream_t s) {
     ProxArgs pa{};
     if (fused_apply(c)) {
         launch_band_op_fused(x, c->m, c->n, c->r, c->fAT, h.AT.lo, h.AT.w, c->fBT, h.BT.lo, h.BT.w, EPI_STORE, out, pa,
-                             s);
+                             interior_adj(c), s);
         return;
     }
     launch_band_rows<float>(x, c->m, c->n, c->fAT, h.AT.lo, h.AT.w, c->r, c->Z, s);

@@ -174,6 +174,8 @@ BandProb ctx_prob(const sfista_ctx *c) {
     P.wBT = h.BT.w;
     P.Z = c->Z;
     P.R = c->R;
+    P.tfwd = interior_fwd(c);
+    P.tadj = interior_adj(c);
     return P;
 }
 
@@ -185,10 +187,10 @@ void enqueue_stage(sfista_ctx *c, int st, const ProxArgs &pa) {
         // stage 2 = adjoint + shrink / momentum (stages 1 and 3 are empty).
         if (st == 0)
             launch_band_op_fused(c->Yop, c->m, c->n, c->r, c->fA, h.A.lo, h.A.w, c->fB, h.B.lo, h.B.w, EPI_RESIDUAL,
-                                 c->R, pa, c->stream);
+                                 c->R, pa, interior_fwd(c), c->stream);
         else if (st == 2)
             launch_band_op_fused(c->R, c->m, c->n, c->r, c->fAT, h.AT.lo, h.AT.w, c->fBT, h.BT.lo, h.BT.w, EPI_PROX,
-                                 nullptr, pa, c->stream);
+                                 nullptr, pa, interior_adj(c), c->stream);
     } else if (is_banded(c->op)) {
         switch (st) {
             case 0: launch_band_rows<float>(c->Yop, c->m, c->n, c->fA, h.A.lo, h.A.w, c->r, c->Z, c->stream,
@@ -603,16 +605,30 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int ce
     if ((e = band_set_smem_limits(wmax)))
         return bail(fail(SFISTA_ENOTSUP, std::string("band too wide for shared memory: ") + cudaGetErrorString(e)));
     std::vector<float> tmpf;
-    auto up_band = [&](const Band &b, double **d64, float **d32) -> cudaError_t {
+    // FP32 tables are followed by the row of the middle output index (r x w
+    // values); `interior` is the widest range around it whose rows hold the
+    // same FP32 values bit for bit (the Toeplitz interior of Sec. 2's T + H).
+    auto up_band = [&](const Band &b, double **d64, float **d32, int2 *interior) -> cudaError_t {
         cudaError_t ee = upload(d64, b.band.data(), b.band.size(), c->stream);
         if (ee) return ee;
         tmpf.assign(b.band.begin(), b.band.end());
+        const int len = b.len, ref = len / 2, cnt = b.r * b.w;
+        auto same = [&](int row) {
+            for (int t = 0; t < cnt; ++t)
+                if (memcmp(&tmpf[(size_t)t * len + row], &tmpf[(size_t)t * len + ref], sizeof(float))) return false;
+            return true;
+        };
+        int i0 = ref, i1 = ref + 1;
+        while (i0 > 0 && same(i0 - 1)) --i0;
+        while (i1 < len && same(i1)) ++i1;
+        *interior = make_int2(i0, i1);
+        for (int t = 0; t < cnt; ++t) tmpf.push_back(tmpf[(size_t)t * len + ref]);
         ee = upload(d32, tmpf.data(), tmpf.size(), c->stream);
         if (ee) return ee;
         return cudaStreamSynchronize(c->stream);
     };
-    if ((e = up_band(h.A, &c->dA, &c->fA)) || (e = up_band(h.AT, &c->dAT, &c->fAT)) ||
-        (e = up_band(h.B, &c->dB, &c->fB)) || (e = up_band(h.BT, &c->dBT, &c->fBT)))
+    if ((e = up_band(h.A, &c->dA, &c->fA, &c->interior[0])) || (e = up_band(h.AT, &c->dAT, &c->fAT, &c->interior[1])) ||
+        (e = up_band(h.B, &c->dB, &c->fB, &c->interior[2])) || (e = up_band(h.BT, &c->dBT, &c->fBT, &c->interior[3])))
         return bail(fail(SFISTA_ENOMEM, std::string("factor upload: ") + cudaGetErrorString(e)));
     size_t N = c->N;
     if ((e = cudaMalloc((void **)&c->Bd, N * 4)) || (e = cudaMalloc((void **)&c->Yop, N * 4)) ||
@@ -755,7 +771,7 @@ sfista_status sfista_apply(sfista_ctx *c, const float *d_x, float *d_y, int tran
         const Band &F = transpose ? h.AT : h.A;
         const Band &G = transpose ? h.BT : h.B;
         launch_band_op_fused(d_x, c->m, c->n, c->r, transpose ? c->fAT : c->fA, F.lo, F.w, transpose ? c->fBT : c->fB,
-                             G.lo, G.w, EPI_STORE, d_y, pa, c->stream);
+                             G.lo, G.w, EPI_STORE, d_y, pa, transpose ? interior_adj(c) : interior_fwd(c), c->stream);
     } else if (is_banded(c->op)) {
         const Band &F = transpose ? h.AT : h.A;
         const Band &G = transpose ? h.BT : h.B;
@@ -786,7 +802,7 @@ sfista_status sfista_objective(sfista_ctx *c, const float *d_b, const float *d_x
     ProxArgs pa{};
     if (fused_apply(c)) {
         launch_band_op_fused(d_x, c->m, c->n, c->r, c->fA, h.A.lo, h.A.w, c->fB, h.B.lo, h.B.w, EPI_STORE, c->tmp, pa,
-                             c->stream);
+                             interior_fwd(c), c->stream);
     } else if (is_banded(c->op)) {
         launch_band_rows<float>(d_x, c->m, c->n, c->fA, h.A.lo, h.A.w, c->r, c->Z, c->stream);
         launch_band_cols<float>(c->Z, c->m, c->n, c->fB, h.B.lo, h.B.w, c->r, EPI_STORE, c->tmp, pa, c->stream);
@@ -924,29 +940,7 @@ sfista_status sfista_batch_create(sfista_ctx *const *ctxs, int nprob, sfista_bat
         }
     } else {
         b->h_probs.resize(nprob);
-        for (int p = 0; p < nprob; ++p) {
-            sfista_ctx *c = ctxs[p];
-            const HostSetup &h = c->hs;
-            BandProb &P = b->h_probs[p];
-            P = BandProb{};
-            P.m = c->m;
-            P.n = c->n;
-            P.r = c->r;
-            P.fA = c->fA;
-            P.fB = c->fB;
-            P.fAT = c->fAT;
-            P.fBT = c->fBT;
-            P.loA = h.A.lo;
-            P.wA = h.A.w;
-            P.loB = h.B.lo;
-            P.wB = h.B.w;
-            P.loAT = h.AT.lo;
-            P.wAT = h.AT.w;
-            P.loBT = h.BT.lo;
-            P.wBT = h.BT.w;
-            P.Z = c->Z;
-            P.R = c->R;
-        }
+        for (int p = 0; p < nprob; ++p) b->h_probs[p] = ctx_prob(ctxs[p]);
         if ((e = cudaMalloc((void **)&b->d_probs, nprob * sizeof(BandProb)))) {
             batch_free(b);
             return fail(SFISTA_ENOMEM, std::string("grouped banded tables: ") + cudaGetErrorString(e));

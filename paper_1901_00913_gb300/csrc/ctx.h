@@ -40,6 +40,9 @@ struct sfista_ctx {
     // Band storage on the device: FP64 (power iteration) and FP32 (operator).
     double *dA = nullptr, *dAT = nullptr, *dB = nullptr, *dBT = nullptr;
     float *fA = nullptr, *fAT = nullptr, *fB = nullptr, *fBT = nullptr;
+    // Interior ranges [x, y) of A, A^T, B, B^T: the band rows equal (bit for
+    // bit, FP32) to the Toeplitz row stored after each FP32 table.
+    int2 interior[4] = {};
     // Iteration state.
     float *Bd = nullptr, *Yop = nullptr, *Z = nullptr, *R = nullptr, *tmp = nullptr;
     float2 *Xb[2] = {nullptr, nullptr}, *Y = nullptr;   // double-float FISTA state
@@ -72,6 +75,15 @@ namespace sfista {
 // fused form, and the one-launch solver that is built on it.
 inline bool fused_apply(const sfista_ctx *c) {
     return c->op == SFISTA_OP_BANDED_FUSED || (c->op == SFISTA_OP_BANDED_PERSISTENT && c->pfused);
+}
+
+// Interior ranges (f0, f1, g0, g1) of the forward (A, B) and adjoint
+// (A^T, B^T) band pairs, as the fused kernels take them.
+inline int4 interior_fwd(const sfista_ctx *c) {
+    return make_int4(c->interior[0].x, c->interior[0].y, c->interior[2].x, c->interior[2].y);
+}
+inline int4 interior_adj(const sfista_ctx *c) {
+    return make_int4(c->interior[1].x, c->interior[1].y, c->interior[3].x, c->interior[3].y);
 }
 
 // Helpers of capi.cu used by the other C-ABI translation units.

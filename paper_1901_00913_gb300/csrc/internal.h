@@ -129,6 +129,7 @@ struct BandProb {
     float *Z, *R;
     ProxArgs pa;   // Bd, Y, Yop, beta, constants, status; Xin / Xout = state buffers 0 / 1
     float *xout;   // one-launch batch: the FP32 result X_iters, written by the solver itself
+    int4 tfwd, tadj;   // interior ranges (f0, f1, g0, g1) of (A, B) and (A^T, B^T); see launch_band_op_fused
 };
 struct BandItem {
     int prob, q, tile, pad;   // rows pass: q = term chunk; cols pass: q = 0
@@ -155,11 +156,13 @@ void launch_band_grouped_stage(int st, const BandProb *probs, const BandItem *it
 int band_rows_tiles(int m, int n, bool vec);
 int band_cols_tiles(int m, int n, bool vec);
 
-// One kernel per banded operator application (kernels_fused.cu).
+// One kernel per banded operator application (kernels_fused.cu).  tr =
+// (f0, f1, g0, g1): the output columns of Fb and rows of Gb whose band rows
+// equal the Toeplitz row stored after the table (empty range: none stored).
 size_t band_op_fused_smem(int r, int wF, int wG);
 bool band_op_fused_prepare(int r, int wF, int wG);
 void launch_band_op_fused(const float *In, int m, int n, int r, const float *Fb, int loF, int wF, const float *Gb,
-                          int loG, int wG, EpiKind epi, float *Out, const ProxArgs &pa, cudaStream_t s);
+                          int loG, int wG, EpiKind epi, float *Out, const ProxArgs &pa, int4 tr, cudaStream_t s);
 
 inline bool is_banded(int op) {
     return op == SFISTA_OP_BANDED || op == SFISTA_OP_BANDED_PERSISTENT || op == SFISTA_OP_BANDED_FUSED;

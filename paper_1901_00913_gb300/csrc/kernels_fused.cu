@@ -21,7 +21,9 @@
 //   In [rows][sp]        staged input, rows = (32 + wG4) rounded up to 32,
 //                        sp = 4 * odd >= 32 + wF4
 //   F  [r][wF4][32]      row-pass coefficients of this column tile
+//   tF [r][wF4]          the row that interior columns share (below)
 //   G  [r][wG4][32]      column-pass coefficients of this row tile
+//   tG [r][wG4]          the row that interior rows share
 //   Zt [r][32][zsp]      Z transposed (column-major per term), zsp = 4 * odd
 // Odd multiples of four floats make the 16-byte accesses of 8 consecutive
 // lanes (rows of In, columns of Zt) land in distinct banks.
@@ -35,6 +37,15 @@
 // The row pass repeats the halo rows' work ((32 + wG4) / 32 times the
 // two-pass count); at small and medium sizes the launch and load latency
 // saved outweighs it.
+//
+// Interior rows.  Away from the image edges a factor is Toeplitz (Sec. 2:
+// the Hankel part and the boundary only touch the first and last rows), so
+// every output column of the row pass in [f0, f1), and every output row of
+// the column pass in [g0, g1), has the same coefficients as one reference
+// row (the host checks the FP32 values bit for bit and stores that row after
+// the band table).  A warp whose four columns (rows) are all interior reads
+// one 16-byte Toeplitz load per term and 4 taps instead of one per tap: the
+// same coefficient values in the same order, so the result is unchanged.
 //
 // The same tile routines also run the whole solve in one cooperative launch
 // (band_solve_fused, end of this file) when every tile has its own resident
@@ -72,8 +83,8 @@ __host__ __device__ inline FusedGeom fused_geom(int r, int loF, int wF, int wG) 
     g.sp = 4 * (((TC + g.wF4) / 4) | 1);
     g.zsp = 4 * ((g.zs / 4) | 1);
     g.off_f = (size_t)g.rows * g.sp;
-    g.off_g = g.off_f + (size_t)r * g.wF4 * TC;
-    g.off_z = g.off_g + (size_t)r * g.wG4 * TA;
+    g.off_g = g.off_f + (size_t)r * g.wF4 * (TC + 1);   // F tile, then its Toeplitz row
+    g.off_z = g.off_g + (size_t)r * g.wG4 * (TA + 1);
     g.total = g.off_z + (size_t)r * TC * g.zsp;
     return g;
 }
@@ -91,16 +102,32 @@ __device__ __forceinline__ void epi_index(int m, int n, int a, int c, size_t *id
 
 // Four taps (k .. k+3) of the row pass for K terms: (a0, a1) and (b0, b1) are
 // the lanes' input windows of the two rows at columns cb + k .. cb + k + 7.
-template <int K, bool TWO>
+// TOEP: fk is the Toeplitz row at tap k (one coefficient for all 4 columns).
+__device__ __forceinline__ float comp(const float4 &v, int t) {
+    return t == 0 ? v.x : (t == 1 ? v.y : (t == 2 ? v.z : v.w));
+}
+
+template <int K, bool TWO, bool TOEP>
 __device__ __forceinline__ void rows_taps4(const float4 &a0, const float4 &a1, const float4 &b0, const float4 &b1,
                                            const float *fk, int wF4, float (&acc)[TWO ? 2 : 1][K][4]) {
     const float xw[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
     const float yw[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+    float4 tq[K];
+    if (TOEP) {
+#pragma unroll
+        for (int q = 0; q < K; ++q) tq[q] = lds4(fk + q * wF4);
+    }
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
 #pragma unroll
         for (int q = 0; q < K; ++q) {
-            const float4 f = lds4(fk + (q * wF4 + t) * TC);
+            float4 f;
+            if (TOEP) {
+                const float v = comp(tq[q], t);
+                f = make_float4(v, v, v, v);
+            } else {
+                f = lds4(fk + (q * wF4 + t) * TC);
+            }
             acc[0][q][0] = fmaf(xw[t], f.x, acc[0][q][0]);
             acc[0][q][1] = fmaf(xw[t + 1], f.y, acc[0][q][1]);
             acc[0][q][2] = fmaf(xw[t + 2], f.z, acc[0][q][2]);
@@ -119,9 +146,10 @@ __device__ __forceinline__ void rows_taps4(const float4 &a0, const float4 &a1, c
 // input row at column cb; fr: coefficients at column cb of the first term;
 // zt: Zt entry (first term, column cb, row e).  The tap loop takes two steps
 // of 4 per trip so the windows alternate between two register sets.
-template <int K, bool TWO>
+template <int K, bool TWO, bool TOEP>
 __device__ __forceinline__ void rows_pass(const float *xa, int sp, const float *fr, int wF4, float *zt, int zsp,
                                           bool sta, bool stb) {
+    constexpr int ts = TOEP ? 1 : TC;   // tap stride of the coefficients
     float acc[TWO ? 2 : 1][K][4];
 #pragma unroll
     for (int h = 0; h < (TWO ? 2 : 1); ++h)
@@ -134,14 +162,14 @@ __device__ __forceinline__ void rows_pass(const float *xa, int sp, const float *
 #pragma unroll 1
     for (; k + 8 <= wF4; k += 8) {
         const float4 a1 = lds4(xa + k + 4), b1 = TWO ? lds4(xb + k + 4) : zero;
-        rows_taps4<K, TWO>(a0, a1, b0, b1, fr + k * TC, wF4, acc);
+        rows_taps4<K, TWO, TOEP>(a0, a1, b0, b1, fr + k * ts, wF4, acc);
         a0 = lds4(xa + k + 8);
         b0 = TWO ? lds4(xb + k + 8) : zero;
-        rows_taps4<K, TWO>(a1, a0, b1, b0, fr + (k + 4) * TC, wF4, acc);
+        rows_taps4<K, TWO, TOEP>(a1, a0, b1, b0, fr + (k + 4) * ts, wF4, acc);
     }
     if (k < wF4) {
         const float4 a1 = lds4(xa + k + 4), b1 = TWO ? lds4(xb + k + 4) : zero;
-        rows_taps4<K, TWO>(a0, a1, b0, b1, fr + k * TC, wF4, acc);
+        rows_taps4<K, TWO, TOEP>(a0, a1, b0, b1, fr + k * ts, wF4, acc);
     }
 #pragma unroll
     for (int q = 0; q < K; ++q)
@@ -154,11 +182,21 @@ __device__ __forceinline__ void rows_pass(const float *xa, int sp, const float *
 
 // Four taps (k .. k+3) of one term of the column pass: (w0, w1) is the Z
 // window of rows rb + k .. rb + k + 7 in the lane's column.
+// TOEP: gk is the Toeplitz row at tap k (one coefficient for all 4 rows).
+template <bool TOEP>
 __device__ __forceinline__ void cols_taps4(const float4 &w0, const float4 &w1, const float *gk, float (&a)[4]) {
     const float z[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+    float4 tg;
+    if (TOEP) tg = lds4(gk);
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-        const float4 g = lds4(gk + t * TA);
+        float4 g;
+        if (TOEP) {
+            const float v = comp(tg, t);
+            g = make_float4(v, v, v, v);
+        } else {
+            g = lds4(gk + t * TA);
+        }
         a[0] = fmaf(g.x, z[t], a[0]);
         a[1] = fmaf(g.y, z[t + 1], a[1]);
         a[2] = fmaf(g.z, z[t + 2], a[2]);
@@ -170,8 +208,9 @@ __device__ __forceinline__ void cols_taps4(const float4 &w0, const float4 &w1, c
 // row rb); gr: coefficients of rows rb .. rb+3 of the first term.  Each
 // term's chain is summed into acc at the end, terms in order.  Two steps
 // of 4 taps per trip, as in the row pass.
-template <int K>
+template <int K, bool TOEP>
 __device__ __forceinline__ void cols_pass(const float *zc, int zsp, const float *gr, int wG4, float *acc) {
+    constexpr int ts = TOEP ? 1 : TA;   // tap stride of the coefficients
     float a[K][4];
     float4 w0[K];
 #pragma unroll
@@ -186,16 +225,16 @@ __device__ __forceinline__ void cols_pass(const float *zc, int zsp, const float 
         for (int q = 0; q < K; ++q) {
             const float *zq = zc + q * TC * zsp;
             const float4 w1 = lds4(zq + k + 4);
-            cols_taps4(w0[q], w1, gr + (q * wG4 + k) * TA, a[q]);
+            cols_taps4<TOEP>(w0[q], w1, gr + (q * wG4 + k) * ts, a[q]);
             w0[q] = lds4(zq + k + 8);
-            cols_taps4(w1, w0[q], gr + (q * wG4 + k + 4) * TA, a[q]);
+            cols_taps4<TOEP>(w1, w0[q], gr + (q * wG4 + k + 4) * ts, a[q]);
         }
     }
     if (k < wG4) {
 #pragma unroll
         for (int q = 0; q < K; ++q) {
             const float4 w1 = lds4(zc + q * TC * zsp + k + 4);
-            cols_taps4(w0[q], w1, gr + (q * wG4 + k) * TA, a[q]);
+            cols_taps4<TOEP>(w0[q], w1, gr + (q * wG4 + k) * ts, a[q]);
         }
     }
 #pragma unroll
@@ -227,11 +266,28 @@ __device__ __forceinline__ void epi_load(const ProxArgs &pa, int m, int n, int a
 // its 32 columns and the column-pass coefficients of its 32 rows, every term.
 // VEC: 16-byte copies (n, m multiples of 4, buffers 16-byte aligned);
 // otherwise element-wise copies into the same layout.
+// tr = (f0, f1, g0, g1): the interior ranges; a non-empty range means the
+// band table is followed by its Toeplitz row (r x w values), which is then
+// staged after the tile with the same tap padding.
 template <bool VEC>
 __device__ __forceinline__ void stage_bands(const FusedGeom &geo, int r, const float *__restrict__ Fb, int wF,
                                             const float *__restrict__ Gb, int wG, int m, int n, int a0, int c0,
-                                            float *Fs, float *Gs) {
+                                            float *Fs, float *Gs, int4 tr) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tr.x < tr.y) {
+        const float *tf = Fb + (size_t)r * wF * n;
+        for (int i = tid; i < r * geo.wF4; i += NT) {
+            const int q = i / geo.wF4, k = i % geo.wF4 - geo.off;
+            Fs[(size_t)r * geo.wF4 * TC + i] = k >= 0 && k < wF ? tf[q * wF + k] : 0.f;
+        }
+    }
+    if (tr.z < tr.w) {
+        const float *tg = Gb + (size_t)r * wG * m;
+        for (int i = tid; i < r * geo.wG4; i += NT) {
+            const int q = i / geo.wG4, k = i % geo.wG4;
+            Gs[(size_t)r * geo.wG4 * TA + i] = k < wG ? tg[q * wG + k] : 0.f;
+        }
+    }
     if (VEC) {
         const int tr = tid >> 3, j = tid & 7;
         const int fb = c0 + 4 * j < n ? 16 : 0, gb = a0 + 4 * j < m ? 16 : 0;
@@ -304,42 +360,71 @@ __device__ __forceinline__ void stage_input(const FusedGeom &geo, const float *_
 // Both passes on the staged tile (the caller has waited for the copies and
 // synchronised): Z_i for rows [0, zs) into Zt, then the column pass added
 // into acc (rows rb .. rb + 3 of the lane's column, terms summed in order).
+template <bool TOEP>
+__device__ __forceinline__ void rows_group(const FusedGeom &geo, int r, const float *xa, const float *fbase, int cb,
+                                           float *zcol, int e, bool two) {
+    for (int tb = 0; tb < r; tb += 4) {
+        const float *fr = TOEP ? fbase + tb * geo.wF4 : fbase + tb * geo.wF4 * TC + cb;
+        float *zt = zcol + (size_t)tb * TC * geo.zsp;
+        const bool sta = e < geo.zs, stb = e + 32 < geo.zs;
+        switch (min(4, r - tb) + (two ? 4 : 0)) {
+            case 1: rows_pass<1, false, TOEP>(xa, geo.sp, fr, geo.wF4, zt, geo.zsp, sta, stb); break;
+            case 2: rows_pass<2, false, TOEP>(xa, geo.sp, fr, geo.wF4, zt, geo.zsp, sta, stb); break;
+            case 3: rows_pass<3, false, TOEP>(xa, geo.sp, fr, geo.wF4, zt, geo.zsp, sta, stb); break;
+            case 4: rows_pass<4, false, TOEP>(xa, geo.sp, fr, geo.wF4, zt, geo.zsp, sta, stb); break;
+            case 5: rows_pass<1, true, TOEP>(xa, geo.sp, fr, geo.wF4, zt, geo.zsp, sta, stb); break;
+            case 6: rows_pass<2, true, TOEP>(xa, geo.sp, fr, geo.wF4, zt, geo.zsp, sta, stb); break;
+            case 7: rows_pass<3, true, TOEP>(xa, geo.sp, fr, geo.wF4, zt, geo.zsp, sta, stb); break;
+            default: rows_pass<4, true, TOEP>(xa, geo.sp, fr, geo.wF4, zt, geo.zsp, sta, stb); break;
+        }
+    }
+}
+
+template <bool TOEP>
+__device__ __forceinline__ void cols_group(const FusedGeom &geo, int r, const float *zcol, const float *gbase, int rb,
+                                           float *acc) {
+    for (int tb = 0; tb < r; tb += 4) {
+        const float *zc = zcol + (size_t)tb * TC * geo.zsp;
+        const float *gr = TOEP ? gbase + tb * geo.wG4 : gbase + tb * geo.wG4 * TA + rb;
+        switch (min(4, r - tb)) {
+            case 1: cols_pass<1, TOEP>(zc, geo.zsp, gr, geo.wG4, acc); break;
+            case 2: cols_pass<2, TOEP>(zc, geo.zsp, gr, geo.wG4, acc); break;
+            case 3: cols_pass<3, TOEP>(zc, geo.zsp, gr, geo.wG4, acc); break;
+            default: cols_pass<4, TOEP>(zc, geo.zsp, gr, geo.wG4, acc); break;
+        }
+    }
+}
+
+// rel = the interior ranges relative to the tile origin (columns c - c0 for
+// the row pass, rows a - a0 for the column pass).
 __device__ __forceinline__ void fused_passes(const FusedGeom &geo, int r, const float *Ins, const float *Fs,
-                                             const float *Gs, float *Zs, float *acc) {
+                                             const float *Gs, float *Zs, float *acc, int4 rel) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int cb = warp * 4;
+    const bool toep_f = cb >= rel.x && cb + 4 <= rel.y;   // warp-uniform
+    const float *tF = Fs + (size_t)r * geo.wF4 * TC;
     for (int rbase = 0; rbase < geo.zs; rbase += 64) {
         const int e = rbase + lane;
         const bool two = rbase + 32 < geo.zs;
         const float *xa = Ins + e * geo.sp + cb;
-        for (int tb = 0; tb < r; tb += 4) {
-            const float *fr = Fs + tb * geo.wF4 * TC + cb;
-            float *zt = Zs + (size_t)(tb * TC + cb) * geo.zsp + e;
-            const bool sta = e < geo.zs, stb = e + 32 < geo.zs;
-            switch (min(4, r - tb) + (two ? 4 : 0)) {
-                case 1: rows_pass<1, false>(xa, geo.sp, fr, geo.wF4, zt, geo.zsp, sta, stb); break;
-                case 2: rows_pass<2, false>(xa, geo.sp, fr, geo.wF4, zt, geo.zsp, sta, stb); break;
-                case 3: rows_pass<3, false>(xa, geo.sp, fr, geo.wF4, zt, geo.zsp, sta, stb); break;
-                case 4: rows_pass<4, false>(xa, geo.sp, fr, geo.wF4, zt, geo.zsp, sta, stb); break;
-                case 5: rows_pass<1, true>(xa, geo.sp, fr, geo.wF4, zt, geo.zsp, sta, stb); break;
-                case 6: rows_pass<2, true>(xa, geo.sp, fr, geo.wF4, zt, geo.zsp, sta, stb); break;
-                case 7: rows_pass<3, true>(xa, geo.sp, fr, geo.wF4, zt, geo.zsp, sta, stb); break;
-                default: rows_pass<4, true>(xa, geo.sp, fr, geo.wF4, zt, geo.zsp, sta, stb); break;
-            }
-        }
+        float *zcol = Zs + (size_t)cb * geo.zsp + e;
+        if (toep_f)
+            rows_group<true>(geo, r, xa, tF, cb, zcol, e, two);
+        else
+            rows_group<false>(geo, r, xa, Fs, cb, zcol, e, two);
     }
     __syncthreads();
     const int rb = warp * 4;
-    for (int tb = 0; tb < r; tb += 4) {
-        const float *zc = Zs + (size_t)(tb * TC + lane) * geo.zsp + rb;
-        const float *gr = Gs + tb * geo.wG4 * TA + rb;
-        switch (min(4, r - tb)) {
-            case 1: cols_pass<1>(zc, geo.zsp, gr, geo.wG4, acc); break;
-            case 2: cols_pass<2>(zc, geo.zsp, gr, geo.wG4, acc); break;
-            case 3: cols_pass<3>(zc, geo.zsp, gr, geo.wG4, acc); break;
-            default: cols_pass<4>(zc, geo.zsp, gr, geo.wG4, acc); break;
-        }
-    }
+    const float *zcol = Zs + (size_t)lane * geo.zsp + rb;
+    if (rb >= rel.z && rb + 4 <= rel.w)
+        cols_group<true>(geo, r, zcol, Gs + (size_t)r * geo.wG4 * TA, rb, acc);
+    else
+        cols_group<false>(geo, r, zcol, Gs, rb, acc);
+}
+
+// Interior ranges (global) -> relative to the tile at (a0, c0).
+__device__ __forceinline__ int4 tile_rel(int4 tr, int a0, int c0) {
+    return make_int4(tr.x - c0, tr.y - c0, tr.z - a0, tr.w - a0);
 }
 
 // PRE: the epilogue's operands are loaded at the start of the block, before
@@ -353,7 +438,7 @@ template <int EPI, bool VEC, bool PRE>
 __global__ void __launch_bounds__(NT, PRE ? 2 : 0) band_op_fused_kernel(const float *__restrict__ In, int m, int n, int r,
                                                            const float *__restrict__ Fb, int loF, int wF,
                                                            const float *__restrict__ Gb, int loG, int wG,
-                                                           float *__restrict__ Out, ProxArgs pa) {
+                                                           float *__restrict__ Out, ProxArgs pa, int4 tr) {
     extern __shared__ __align__(16) float sm[];
     const FusedGeom geo = fused_geom(r, loF, wF, wG);
     float *Ins = sm, *Fs = sm + geo.off_f, *Gs = sm + geo.off_g, *Zs = sm + geo.off_z;
@@ -366,13 +451,13 @@ __global__ void __launch_bounds__(NT, PRE ? 2 : 0) band_op_fused_kernel(const fl
     float2 yv[4], xv[4], beta = make_float2(0.f, 0.f);
     if (PRE) epi_load<EPI>(pa, m, n, a0 + rb, gc, bv, yv, xv, beta);
     // Constant band tiles first, then (after the previous kernel) the input tile.
-    stage_bands<VEC>(geo, r, Fb, wF, Gb, wG, m, n, a0, c0, Fs, Gs);
+    stage_bands<VEC>(geo, r, Fb, wF, Gb, wG, m, n, a0, c0, Fs, Gs, tr);
     band::pdl_wait();
     stage_input<VEC>(geo, In, m, n, e0, colbase, Ins);
     band::stage_wait<false>();
     __syncthreads();
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    fused_passes(geo, r, Ins, Fs, Gs, Zs, acc);
+    fused_passes(geo, r, Ins, Fs, Gs, Zs, acc, tile_rel(tr, a0, c0));
     if (!PRE) epi_load<EPI>(pa, m, n, a0 + rb, gc, bv, yv, xv, beta);
     size_t idx[4];
     bool ok[4];
@@ -465,11 +550,11 @@ __host__ __device__ inline SolveLayout solve_layout(int r, int loA, int wA, int 
     L.gf = fused_geom(r, loA, wA, wB);
     L.gt = fused_geom(r, loAT, wAT, wBT);
     const size_t in = (size_t)max(L.gf.rows * L.gf.sp, L.gt.rows * L.gt.sp);
-    L.off_ff = in;
-    L.off_gf = L.off_ff + (size_t)r * L.gf.wF4 * TC;
-    L.off_ft = L.off_gf + (size_t)r * L.gf.wG4 * TA;
-    L.off_gt = L.off_ft + (size_t)r * L.gt.wF4 * TC;
-    L.off_z = L.off_gt + (size_t)r * L.gt.wG4 * TA;
+    L.off_ff = in;   // each table followed by its Toeplitz row
+    L.off_gf = L.off_ff + (size_t)r * L.gf.wF4 * (TC + 1);
+    L.off_ft = L.off_gf + (size_t)r * L.gf.wG4 * (TA + 1);
+    L.off_gt = L.off_ft + (size_t)r * L.gt.wF4 * (TC + 1);
+    L.off_z = L.off_gt + (size_t)r * L.gt.wG4 * (TA + 1);
     L.total = L.off_z + (size_t)r * TC * max(L.gf.zsp, L.gt.zsp);
     return L;
 }
@@ -479,11 +564,11 @@ __host__ __device__ inline SolveLayout solve_layout(int r, int loA, int wA, int 
 // again in every phase, so they do not hold registers across the loop).
 __device__ __forceinline__ void solve_phase(const FusedGeom &g, const float *In, int m, int n, int r, int lo_rows,
                                             int lo_cols, size_t off_f, size_t off_g, size_t off_z, float *sm, int a0,
-                                            int c0, float *acc) {
+                                            int c0, float *acc, int4 tr) {
     stage_input<true>(g, In, m, n, a0 + lo_rows, c0 + lo_cols - g.off, sm);
     band::stage_wait<false>();
     __syncthreads();
-    fused_passes(g, r, sm, sm + off_f, sm + off_g, sm + off_z, acc);
+    fused_passes(g, r, sm, sm + off_f, sm + off_g, sm + off_z, acc, tile_rel(tr, a0, c0));
 }
 
 template <bool BATCH>
@@ -512,8 +597,8 @@ __global__ void __launch_bounds__(NT, 2) band_solve_fused(BandProb one, const Ba
     const int a0 = (tile_sh / tiles_c) * TA, c0 = (tile_sh % tiles_c) * TC;
     {
         const SolveLayout L = Ls;
-        stage_bands<true>(L.gf, r, P.fA, P.wA, P.fB, P.wB, m, n, a0, c0, sm + L.off_ff, sm + L.off_gf);
-        stage_bands<true>(L.gt, r, P.fAT, P.wAT, P.fBT, P.wBT, m, n, a0, c0, sm + L.off_ft, sm + L.off_gt);
+        stage_bands<true>(L.gf, r, P.fA, P.wA, P.fB, P.wB, m, n, a0, c0, sm + L.off_ff, sm + L.off_gf, P.tfwd);
+        stage_bands<true>(L.gt, r, P.fAT, P.wAT, P.fBT, P.wBT, m, n, a0, c0, sm + L.off_ft, sm + L.off_gt, P.tadj);
     }
     const int rb = (threadIdx.x >> 5) * 4, gc = c0 + (threadIdx.x & 31);   // epilogue pixels
     float2 *const Xb0 = const_cast<float2 *>(P.pa.Xin), *const Xb1 = P.pa.Xout;
@@ -550,7 +635,7 @@ __global__ void __launch_bounds__(NT, 2) band_solve_fused(BandProb one, const Ba
                 if (bad) atomicOr(P.pa.status, DEV_NONFINITE);
             } else {
                 solve_phase(Ls.gf, P.pa.Yop, m, n, r, P.loB, P.loA, Ls.off_ff, Ls.off_gf, Ls.off_z, sm, a0, c0,
-                            acc);
+                            acc, P.tfwd);
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j)
@@ -560,7 +645,8 @@ __global__ void __launch_bounds__(NT, 2) band_solve_fused(BandProb one, const Ba
         {   // Adjoint + Step 1 shrink + Step 3 momentum.
             const float2 beta = P.pa.beta[k - 1];
             float acc[4] = {0.f, 0.f, 0.f, 0.f};
-            solve_phase(Ls.gt, P.R, m, n, r, P.loBT, P.loAT, Ls.off_ft, Ls.off_gt, Ls.off_z, sm, a0, c0, acc);
+            solve_phase(Ls.gt, P.R, m, n, r, P.loBT, P.loAT, Ls.off_ft, Ls.off_gt, Ls.off_z, sm, a0, c0, acc,
+                        P.tadj);
             size_t idx[4];
             bool ok[4];
             epi_index(m, n, a0 + rb, gc, idx, ok);
@@ -602,18 +688,19 @@ constexpr size_t kFusedSmemMax = 227 * 1024;
 
 template <int EPI>
 void launch_epi(const cudaLaunchConfig_t &cfg, bool vec, bool pre, const float *In, int m, int n, int r,
-                const float *Fb, int loF, int wF, const float *Gb, int loG, int wG, float *Out, const ProxArgs &pa) {
+                const float *Fb, int loF, int wF, const float *Gb, int loG, int wG, float *Out, const ProxArgs &pa,
+                int4 tr) {
     if constexpr (EPI != EPI_STORE) {
         if (vec && pre)
             return (void)cudaLaunchKernelEx(&cfg, band_op_fused_kernel<EPI, true, true>, In, m, n, r, Fb, loF, wF, Gb,
-                                            loG, wG, Out, pa);
+                                            loG, wG, Out, pa, tr);
     }
     if (vec)
         cudaLaunchKernelEx(&cfg, band_op_fused_kernel<EPI, true, false>, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out,
-                           pa);
+                           pa, tr);
     else
         cudaLaunchKernelEx(&cfg, band_op_fused_kernel<EPI, false, false>, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out,
-                           pa);
+                           pa, tr);
 }
 
 int fused_sm_count() {
@@ -645,7 +732,7 @@ bool band_op_fused_prepare(int r, int wF, int wG) {
 }
 
 void launch_band_op_fused(const float *In, int m, int n, int r, const float *Fb, int loF, int wF, const float *Gb,
-                          int loG, int wG, EpiKind epi, float *Out, const ProxArgs &pa, cudaStream_t s) {
+                          int loG, int wG, EpiKind epi, float *Out, const ProxArgs &pa, int4 tr, cudaStream_t s) {
     const bool vec = (n % 4) == 0 && (m % 4) == 0 && ((uintptr_t)In % 16) == 0 && ((uintptr_t)Fb % 16) == 0 &&
                      ((uintptr_t)Gb % 16) == 0;
     cudaLaunchConfig_t cfg = {};
@@ -660,11 +747,11 @@ void launch_band_op_fused(const float *In, int m, int n, int r, const float *Fb,
     cfg.numAttrs = 1;
     const bool pre = (long)cfg.gridDim.x * cfg.gridDim.y <= 2L * fused_sm_count();
     if (epi == EPI_STORE)
-        launch_epi<EPI_STORE>(cfg, vec, pre, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out, pa);
+        launch_epi<EPI_STORE>(cfg, vec, pre, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out, pa, tr);
     else if (epi == EPI_RESIDUAL)
-        launch_epi<EPI_RESIDUAL>(cfg, vec, pre, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out, pa);
+        launch_epi<EPI_RESIDUAL>(cfg, vec, pre, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out, pa, tr);
     else
-        launch_epi<EPI_PROX>(cfg, vec, pre, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out, pa);
+        launch_epi<EPI_PROX>(cfg, vec, pre, In, m, n, r, Fb, loF, wF, Gb, loG, wG, Out, pa, tr);
 }
 
 namespace {
