@@ -40,15 +40,9 @@ KERNELS_PER_ITER = {"banded": 4, "banded_fused": 2, "gemm_band": 4, "gemm_dense"
 # profiles/ gives the command); forms without one report null.
 TRAFFIC = {
     "fp32:banded_persistent:0": {
-        "bytes": (7.155456e6 + 0.087296e6) / 20,
+        "bytes": (7.192832e6 + 0.101120e6) / 20,
         "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 20-iteration band_solve_fused "
                   "launch / 20 (per iteration, the unit of achieved), profiles/solve_fused_fp32_cfg2_512_r3.md"},
-    "fp32:banded_fused:0": {
-        "bytes": 2.542336e6,
-        "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, profiles/banded_fused_fp32_cfg2_512_r3.md"},
-    "fp32:banded_fused:2": {
-        "bytes": 5.697024e6,
-        "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, profiles/banded_fused_fp32_cfg2_512_r3.md"},
 }
 
 
