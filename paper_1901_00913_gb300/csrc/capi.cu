@@ -176,6 +176,7 @@ BandProb ctx_prob(const sfista_ctx *c) {
     P.R = c->R;
     P.tfwd = interior_fwd(c);
     P.tadj = interior_adj(c);
+    P.th = c->pth;
     return P;
 }
 
@@ -646,12 +647,13 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int ce
     if (o.op == SFISTA_OP_AUTO && c->op == SFISTA_OP_BANDED_FUSED) {
         int grid = 0;
         size_t smem = 0;
-        if (band_solve_fused_config(ctx_prob(c), c->dev, &grid, &smem)) c->op = SFISTA_OP_BANDED_PERSISTENT;
+        int th = 32;
+        if (band_solve_fused_config(ctx_prob(c), c->dev, &grid, &smem, &th)) c->op = SFISTA_OP_BANDED_PERSISTENT;
     }
     if (c->op == SFISTA_OP_BANDED_PERSISTENT) {
         if ((e = cudaMalloc((void **)&c->bar, kBarrierBytes)) || (e = cudaMemset(c->bar, 0, kBarrierBytes)))
             return bail(fail(SFISTA_ENOMEM, std::string("barrier words: ") + cudaGetErrorString(e)));
-        c->pfused = band_solve_fused_config(ctx_prob(c), c->dev, &c->pgrid, &c->psmem);
+        c->pfused = band_solve_fused_config(ctx_prob(c), c->dev, &c->pgrid, &c->psmem, &c->pth);
         // Single operator applications (sfista_apply, the objective, reverse
         // mode) then take the fused operator kernel as well.
         if (c->pfused && !band_op_fused_prepare(c->r, std::max(h.A.w, h.AT.w), std::max(h.B.w, h.BT.w)))
@@ -951,7 +953,9 @@ sfista_status sfista_batch_create(sfista_ctx *const *ctxs, int nprob, sfista_bat
             return st;
         }
         std::vector<int2> items;
-        if (band_solve_fused_batch_config(b->h_probs.data(), nprob, b->dev, &items, &b->fsmem)) {
+        int th = 32;
+        if (band_solve_fused_batch_config(b->h_probs.data(), nprob, b->dev, &items, &b->fsmem, &th)) {
+            for (BandProb &P : b->h_probs) P.th = th;
             if ((e = cudaMalloc((void **)&b->d_fitems, items.size() * sizeof(int2))) ||
                 (e = cudaMemcpy(b->d_fitems, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice)) ||
                 (e = cudaMalloc((void **)&b->bar, kBarrierBytes))) {
@@ -1366,9 +1370,9 @@ sfista_status sfista_tune(sfista_ctx *c, int iters, sfista_tune_entry *entries, 
                 log(SFISTA_OP_BANDED_FUSED, -1, 0, t_fused);
                 c->op = t_fused < t_two ? SFISTA_OP_BANDED_FUSED : SFISTA_OP_BANDED;
                 // The one-launch fused solver, when every tile has a resident block.
-                int grid = 0;
+                int grid = 0, th = 32;
                 size_t smem = 0;
-                if (band_solve_fused_config(ctx_prob(c), c->dev, &grid, &smem)) {
+                if (band_solve_fused_config(ctx_prob(c), c->dev, &grid, &smem, &th)) {
                     if (!c->bar) {
                         SF_CUDA(cudaMalloc((void **)&c->bar, kBarrierBytes));
                         SF_CUDA(cudaMemset(c->bar, 0, kBarrierBytes));
@@ -1378,6 +1382,7 @@ sfista_status sfista_tune(sfista_ctx *c, int iters, sfista_tune_entry *entries, 
                     c->pfused = 1;   // band_op_fused_prepare succeeded above
                     c->pgrid = grid;
                     c->psmem = smem;
+                    c->pth = th;
                     float t_one = 0.f;
                     st = time_persistent(c, std::max(iters, 40), &t_one);
                     if (st) return st;

@@ -60,7 +60,7 @@ struct sfista_ctx {
     int chunk[4] = {0, 0, 0, 0};
     // Persistent solver launch shape and its grid-barrier words; pfused: the
     // one-launch fused solver (every tile resident), else the two-pass one.
-    int pgrid = 0, prows_chunk = 1, pcols_chunk = 1, pfused = 0;
+    int pgrid = 0, prows_chunk = 1, pcols_chunk = 1, pfused = 0, pth = 32;   // pth: one-launch tile height
     size_t psmem = 0;
     unsigned *bar = nullptr;
     // Cached CUDA graph of the iteration loop.

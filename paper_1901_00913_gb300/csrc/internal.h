@@ -130,19 +130,22 @@ struct BandProb {
     ProxArgs pa;   // Bd, Y, Yop, beta, constants, status; Xin / Xout = state buffers 0 / 1
     float *xout;   // one-launch batch: the FP32 result X_iters, written by the solver itself
     int4 tfwd, tadj;   // interior ranges (f0, f1, g0, g1) of (A, B) and (A^T, B^T); see launch_band_op_fused
+    int th;            // one-launch solver: output rows per tile (multiple of 4, <= 32)
 };
 struct BandItem {
     int prob, q, tile, pad;   // rows pass: q = term chunk; cols pass: q = 0
 };
 
 // The whole solve in one cooperative launch of the fused operator kernel
-// (kernels_fused.cu), when every 32 x 32 output tile has a resident block:
+// (kernels_fused.cu), when every th x 32 output tile has a resident block:
 // for one problem, or for a batch (one block per tile of every problem).
+// The configs pick the tile height th (set it in the descriptors' th).
 // The descriptor's pa.Xin / pa.Xout are the state buffers 0 / 1.
-bool band_solve_fused_config(const BandProb &prob, int dev, int *grid, size_t *smem);
+bool band_solve_fused_config(const BandProb &prob, int dev, int *grid, size_t *smem, int *th);
 cudaError_t launch_band_solve_fused(int grid, size_t smem, const BandProb &prob, int k0, int iters, unsigned *bar,
                                     cudaStream_t s);
-bool band_solve_fused_batch_config(const BandProb *probs, int np, int dev, std::vector<int2> *items, size_t *smem);
+bool band_solve_fused_batch_config(const BandProb *probs, int np, int dev, std::vector<int2> *items, size_t *smem,
+                                   int *th);
 cudaError_t launch_band_solve_fused_batch(int nitems, size_t smem, const BandProb *d_probs, const int2 *d_items,
                                           int iters, unsigned *bar, cudaStream_t s);
 void persistent_chunks(int r, int wmax, int *rows_chunk, int *cols_chunk, size_t *smem);

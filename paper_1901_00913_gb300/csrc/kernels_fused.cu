@@ -68,17 +68,19 @@ struct FusedGeom {
     int off;         // loF mod 4: leading zero taps of the row pass
     int wF4, wG4;    // padded tap counts (multiples of 4)
     int zs;          // Z rows the column pass reads: TA + wG4
+    int th;          // output rows of a tile (a multiple of 4, <= 32; the column tile stays 32 wide)
     int rows;        // staged input rows: zs rounded up to 32
     int sp, zsp;     // row strides of In and Zt
     size_t off_f, off_g, off_z, total;   // float offsets / size
 };
 
-__host__ __device__ inline FusedGeom fused_geom(int r, int loF, int wF, int wG) {
+__host__ __device__ inline FusedGeom fused_geom(int r, int loF, int wF, int wG, int th = TA) {
     FusedGeom g;
     g.off = ((loF % 4) + 4) % 4;
     g.wF4 = (wF + g.off + 3) & ~3;
     g.wG4 = (wG + 3) & ~3;
-    g.zs = TA + g.wG4;
+    g.th = th;
+    g.zs = th + g.wG4;
     g.rows = (g.zs + 31) & ~31;
     g.sp = 4 * (((TC + g.wF4) / 4) | 1);
     g.zsp = 4 * ((g.zs / 4) | 1);
@@ -415,6 +417,7 @@ __device__ __forceinline__ void fused_passes(const FusedGeom &geo, int r, const 
     }
     __syncthreads();
     const int rb = warp * 4;
+    if (rb >= geo.th) return;   // rows beyond a shorter tile: nothing to sum
     const float *zcol = Zs + (size_t)lane * geo.zsp + rb;
     if (rb >= rel.z && rb + 4 <= rel.w)
         cols_group<true>(geo, r, zcol, Gs + (size_t)r * geo.wG4 * TA, rb, acc);
@@ -545,10 +548,11 @@ struct SolveLayout {
     size_t off_ff, off_gf, off_ft, off_gt, off_z, total;   // float offsets / size
 };
 
-__host__ __device__ inline SolveLayout solve_layout(int r, int loA, int wA, int wB, int loAT, int wAT, int wBT) {
+__host__ __device__ inline SolveLayout solve_layout(int r, int loA, int wA, int wB, int loAT, int wAT, int wBT,
+                                                    int th) {
     SolveLayout L;
-    L.gf = fused_geom(r, loA, wA, wB);
-    L.gt = fused_geom(r, loAT, wAT, wBT);
+    L.gf = fused_geom(r, loA, wA, wB, th);
+    L.gt = fused_geom(r, loAT, wAT, wBT, th);
     const size_t in = (size_t)max(L.gf.rows * L.gf.sp, L.gt.rows * L.gt.sp);
     L.off_ff = in;   // each table followed by its Toeplitz row
     L.off_gf = L.off_ff + (size_t)r * L.gf.wF4 * (TC + 1);
@@ -589,12 +593,13 @@ __global__ void __launch_bounds__(NT, 2) band_solve_fused(BandProb one, const Ba
             P = one;
             tile_sh = blockIdx.x;
         }
-        Ls = solve_layout(P.r, P.loA, P.wA, P.wB, P.loAT, P.wAT, P.wBT);
+        Ls = solve_layout(P.r, P.loA, P.wA, P.wB, P.loAT, P.wAT, P.wBT, P.th);
     }
     __syncthreads();
     const int m = P.m, n = P.n, r = P.r;
     const int tiles_c = (n + TC - 1) / TC;
-    const int a0 = (tile_sh / tiles_c) * TA, c0 = (tile_sh % tiles_c) * TC;
+    const int a0 = (tile_sh / tiles_c) * P.th, c0 = (tile_sh % tiles_c) * TC;
+    const int mt = min(m, a0 + P.th);   // the tile's rows end here
     {
         const SolveLayout L = Ls;
         stage_bands<true>(L.gf, r, P.fA, P.wA, P.fB, P.wB, m, n, a0, c0, sm + L.off_ff, sm + L.off_gf, P.tfwd);
@@ -611,7 +616,7 @@ __global__ void __launch_bounds__(NT, 2) band_solve_fused(BandProb one, const Ba
         pa.Xin = (k0 & 1) ? Xb1 : Xb0;
         size_t idx[4];
         bool ok[4];
-        epi_index(m, n, a0 + rb, gc, idx, ok);
+        epi_index(mt, n, a0 + rb, gc, idx, ok);
         prox_load_n<4>(pa, idx, ok, y, xp);
     }
     const int kend = k0 + iters;
@@ -620,7 +625,7 @@ __global__ void __launch_bounds__(NT, 2) band_solve_fused(BandProb one, const Ba
         {   // Forward operator + residual: R = A_s Y_k - B.
             size_t idx[4];
             bool ok[4];
-            epi_index(m, n, a0 + rb, gc, idx, ok);
+            epi_index(mt, n, a0 + rb, gc, idx, ok);
             float bv[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) bv[j] = ok[j] ? __ldcg(P.pa.Bd + idx[j]) : 0.f;
@@ -649,7 +654,7 @@ __global__ void __launch_bounds__(NT, 2) band_solve_fused(BandProb one, const Ba
                         P.tadj);
             size_t idx[4];
             bool ok[4];
-            epi_index(m, n, a0 + rb, gc, idx, ok);
+            epi_index(mt, n, a0 + rb, gc, idx, ok);
             float2 *Xlast = ((k - 1) & 1) ? Xb1 : Xb0;   // X_{k-1}: kept for a resumed solve
             bool bad = false;
 #pragma unroll
@@ -668,7 +673,7 @@ __global__ void __launch_bounds__(NT, 2) band_solve_fused(BandProb one, const Ba
     }
     size_t idx[4];
     bool ok[4];
-    epi_index(m, n, a0 + rb, gc, idx, ok);
+    epi_index(mt, n, a0 + rb, gc, idx, ok);
     if (BATCH) {   // the FP32 result, straight into the caller's output
 #pragma unroll
         for (int j = 0; j < 4; ++j)
@@ -768,17 +773,17 @@ int max_dynamic_smem(const void *kernel, int dev) {
 }
 
 // Shared memory and co-residency of the one-launch solver over `np`
-// problems; false when a tile does not fit, the 16-byte path does not apply
-// or the tiles outnumber the co-resident blocks.
+// problems with tiles `th` rows high; false when a tile does not fit, the
+// 16-byte path does not apply or the tiles outnumber the co-resident blocks.
 template <bool BATCH>
-bool solve_fused_fits(const BandProb *probs, int np, int dev, long *tiles, size_t *smem) {
+bool solve_fused_fits(const BandProb *probs, int np, int dev, int th, long *tiles, size_t *smem, int *sms) {
     *tiles = 0;
     *smem = 0;
     for (int p = 0; p < np; ++p) {
         const BandProb &P = probs[p];
         if (P.m % 4 || P.n % 4) return false;
-        *smem = std::max(*smem, sizeof(float) * solve_layout(P.r, P.loA, P.wA, P.wB, P.loAT, P.wAT, P.wBT).total);
-        *tiles += (long)((P.m + TA - 1) / TA) * ((P.n + TC - 1) / TC);
+        *smem = std::max(*smem, sizeof(float) * solve_layout(P.r, P.loA, P.wA, P.wB, P.loAT, P.wAT, P.wBT, th).total);
+        *tiles += (long)((P.m + th - 1) / th) * ((P.n + TC - 1) / TC);
     }
     // The attribute is per kernel, not per launch: allow the largest size, so
     // that a later, smaller configuration never lowers an earlier one's limit.
@@ -787,19 +792,56 @@ bool solve_fused_fits(const BandProb *probs, int np, int dev, long *tiles, size_
     if (cudaFuncSetAttribute(band_solve_fused<BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) !=
         cudaSuccess)
         return false;
-    int per_sm = 0, sms = 0, coop = 0;
+    int per_sm = 0, coop = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, band_solve_fused<BATCH>, NT, *smem) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess)
         return false;
-    return coop && per_sm >= 1 && *tiles <= (long)per_sm * sms;
+    return coop && per_sm >= 1 && *tiles <= (long)per_sm * *sms;
+}
+
+// Tile height of the one-launch solver: the candidate (32, 28, ..., 16 rows)
+// whose busiest SM has the least pass work, counted as
+//   ceil(tiles / SMs) * (lane_rows(th + wG4) * wF4 + th * wG4)
+// where the row pass covers th + wG4 staged rows in groups of 64 (two rows
+// per lane; a last group of at most 32 rows takes one) and the column pass
+// th rows, both 32 columns wide (widest bands of the problems).  Shorter
+// tiles spread a problem over more SMs (at 512^2, 28-row tiles put two
+// blocks on every SM instead of two on 104 and one on 48).  Ties keep the
+// taller tile.  false when no candidate fits.
+template <bool BATCH>
+bool solve_fused_pick(const BandProb *probs, int np, int dev, int *th, long *tiles, size_t *smem) {
+    int wF4 = 0, wG4 = 0;
+    for (int p = 0; p < np; ++p) {
+        const BandProb &P = probs[p];
+        const FusedGeom gf = fused_geom(P.r, P.loA, P.wA, P.wB), gt = fused_geom(P.r, P.loAT, P.wAT, P.wBT);
+        wF4 = std::max(wF4, std::max(gf.wF4, gt.wF4));
+        wG4 = std::max(wG4, std::max(gf.wG4, gt.wG4));
+    }
+    double best = -1.0;
+    for (int t = TA; t >= 16; t -= 4) {
+        long nt = 0;
+        size_t sm = 0;
+        int sms = 1;
+        if (!solve_fused_fits<BATCH>(probs, np, dev, t, &nt, &sm, &sms)) continue;
+        const int zs = t + wG4, rest = zs % 64;
+        const int lane_rows = 64 * (zs / 64) + (rest == 0 ? 0 : (rest <= 32 ? 32 : 64));
+        const double cost = (double)((nt + sms - 1) / sms) * ((double)lane_rows * wF4 + (double)t * wG4);
+        if (best < 0.0 || cost < best) {
+            best = cost;
+            *th = t;
+            *tiles = nt;
+            *smem = sm;
+        }
+    }
+    return best >= 0.0;
 }
 
 }  // namespace
 
-bool band_solve_fused_config(const BandProb &prob, int dev, int *grid, size_t *smem) {
+bool band_solve_fused_config(const BandProb &prob, int dev, int *grid, size_t *smem, int *th) {
     long tiles = 0;
-    if (!solve_fused_fits<false>(&prob, 1, dev, &tiles, smem)) return false;
+    if (!solve_fused_pick<false>(&prob, 1, dev, th, &tiles, smem)) return false;
     *grid = (int)tiles;
     return true;
 }
@@ -815,12 +857,13 @@ cudaError_t launch_band_solve_fused(int grid, size_t smem, const BandProb &prob,
     return cudaLaunchCooperativeKernel((const void *)band_solve_fused<false>, dim3(grid), dim3(NT), args, smem, s);
 }
 
-bool band_solve_fused_batch_config(const BandProb *probs, int np, int dev, std::vector<int2> *items, size_t *smem) {
+bool band_solve_fused_batch_config(const BandProb *probs, int np, int dev, std::vector<int2> *items, size_t *smem,
+                                   int *th) {
     long tiles = 0;
-    if (!solve_fused_fits<true>(probs, np, dev, &tiles, smem)) return false;
+    if (!solve_fused_pick<true>(probs, np, dev, th, &tiles, smem)) return false;
     items->clear();
     for (int p = 0; p < np; ++p) {
-        const int t = ((probs[p].m + TA - 1) / TA) * ((probs[p].n + TC - 1) / TC);
+        const int t = ((probs[p].m + *th - 1) / *th) * ((probs[p].n + TC - 1) / TC);
         for (int i = 0; i < t; ++i) items->push_back(make_int2(p, i));
     }
     return true;
