@@ -37,13 +37,10 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x
 KERNELS_PER_ITER = {"banded": 4, "banded_fused": 2, "gemm_band": 4, "gemm_dense": 4}
 # DRAM bytes (read + write) per launch of a form's dominant kernel, from an
 # ncu capture of the current kernel code on this workload (the summary in
-# profiles/ gives the command); forms without one report null.
-TRAFFIC = {
-    "fp32:banded_persistent:0": {
-        "bytes": (7.192832e6 + 0.101120e6) / 20,
-        "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 20-iteration band_solve_fused "
-                  "launch / 20 (per iteration, the unit of achieved), profiles/solve_fused_fp32_cfg2_512_r3.md"},
-}
+# profiles/ gives the command); forms without one report null.  The last
+# capture of band_solve_fused (0.365 MB per iteration) predates its tile-height
+# choice, so the headline form reports null until it is taken again.
+TRAFFIC = {}
 
 
 def one_launch_fused(m, n):
