@@ -21,6 +21,7 @@ import re
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -138,7 +139,9 @@ class Clocks:
     def __init__(self, dev):
         self.dev = dev
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+        # Raw samples: $SFISTA_CLOCKS_DIR if set, else the temp directory.
+        self.path = os.path.join(os.environ.get("SFISTA_CLOCKS_DIR") or tempfile.gettempdir(),
+                                 "clocks_bench_%d.csv" % os.getpid())
 
     def __enter__(self):
         try:
