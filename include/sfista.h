@@ -161,6 +161,29 @@ sfista_status sfista_factorize(const double *psf, int psf_rows, int psf_cols,
                                double *sigma, double *C, double *D,
                                double *approx_err);
 
+/*
+ * sfista_factor_bands -- the band storage the banded kernels use for one
+ * factor family (host only, no device work), from the same factorisation:
+ *   which 0: A_k (right factors, img_cols x img_cols)   1: A_k^T
+ *         2: B_k (left factors, img_rows x img_rows)    3: B_k^T
+ *   F_k[c][c + lo + t] = band[(k * w + t) * len + c], t in [0, w),
+ *   len = img_cols (which 0, 1) or img_rows (2, 3); entries whose column
+ *   falls outside [0, len) are 0.  In the interior of the axis a factor
+ *   T + H of Sec. 2 is Toeplitz: interior[0..1] = [i0, i1), the widest run
+ *   of rows around len / 2 whose FP32 values equal row len / 2 bit for bit
+ *   (the rows whose kernels take one shared coefficient row).
+ * lo, w      out, the band's first offset and width.
+ * band       host, r * w * len doubles, or NULL to query lo and w first.
+ * interior   host, 2 ints (may be NULL).
+ * Same argument checks and errors as sfista_setup; which outside 0..3 is
+ * SFISTA_EINVAL.
+ */
+sfista_status sfista_factor_bands(const double *psf, int psf_rows, int psf_cols,
+                                  int center_row, int center_col,
+                                  int img_rows, int img_cols, int bc, int r,
+                                  int which, int *lo, int *w, double *band,
+                                  int *interior);
+
 /* Release every resource of ctx (NULL is ignored). */
 void sfista_destroy(sfista_ctx *ctx);
 

@@ -54,6 +54,7 @@ def load(path=None):
     L.sfista_default_opts.restype = None
     L.sfista_setup.argtypes = [vp, i, i, i, i, i, i, i, i, ctypes.POINTER(Opts), ctypes.POINTER(vp)]
     L.sfista_factorize.argtypes = [vp, i, i, i, i, i, i, i, i, vp, vp, vp, D]
+    L.sfista_factor_bands.argtypes = [vp, i, i, i, i, i, i, i, i, i, ctypes.POINTER(i), ctypes.POINTER(i), vp, vp]
     L.sfista_destroy.argtypes = [vp]
     L.sfista_destroy.restype = None
     L.sfista_solve.argtypes = [vp, vp, d, i, vp]
@@ -149,6 +150,22 @@ def sfista_factorize(psf, img_rows, img_cols, bc, r, center=(-1, -1)):
                                    int(img_cols), int(bc), int(r), sig.ctypes.data, C.ctypes.data,
                                    D.ctypes.data, ctypes.byref(err)))
     return sig, C, D, err.value
+
+
+def sfista_factor_bands(psf, img_rows, img_cols, bc, r, which, center=(-1, -1)):
+    """Host-only band storage of one factor family (which: 0 A, 1 A^T, 2 B,
+    3 B^T); returns (band r x w x len, lo, (i0, i1) interior rows)."""
+    P = np.ascontiguousarray(psf, dtype=np.float64)
+    p, q = P.shape
+    lo, w = ctypes.c_int(), ctypes.c_int()
+    args = (P.ctypes.data, p, q, int(center[0]), int(center[1]), int(img_rows), int(img_cols), int(bc), int(r),
+            int(which))
+    _check(load().sfista_factor_bands(*args, ctypes.byref(lo), ctypes.byref(w), None, None))
+    length = int(img_cols) if which in (0, 1) else int(img_rows)
+    band = np.zeros((int(r), w.value, length))
+    inter = (ctypes.c_int * 2)()
+    _check(load().sfista_factor_bands(*args, ctypes.byref(lo), ctypes.byref(w), band.ctypes.data, inter))
+    return band, lo.value, (inter[0], inter[1])
 
 
 def sfista_destroy(ctx):

@@ -614,14 +614,8 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int ce
         if (ee) return ee;
         tmpf.assign(b.band.begin(), b.band.end());
         const int len = b.len, ref = len / 2, cnt = b.r * b.w;
-        auto same = [&](int row) {
-            for (int t = 0; t < cnt; ++t)
-                if (memcmp(&tmpf[(size_t)t * len + row], &tmpf[(size_t)t * len + ref], sizeof(float))) return false;
-            return true;
-        };
-        int i0 = ref, i1 = ref + 1;
-        while (i0 > 0 && same(i0 - 1)) --i0;
-        while (i1 < len && same(i1)) ++i1;
+        int i0 = 0, i1 = 0;
+        band_interior(tmpf.data(), len, cnt, &i0, &i1);
         *interior = make_int2(i0, i1);
         for (int t = 0; t < cnt; ++t) tmpf.push_back(tmpf[(size_t)t * len + ref]);
         ee = upload(d32, tmpf.data(), tmpf.size(), c->stream);
@@ -701,6 +695,26 @@ sfista_status sfista_factorize(const double *psf, int p, int q, int cr, int cc, 
     if (C) std::copy(h.C.begin(), h.C.end(), C);
     if (D) std::copy(h.D.begin(), h.D.end(), D);
     if (approx_err) *approx_err = h.approx_err;
+    return SFISTA_OK;
+}
+
+sfista_status sfista_factor_bands(const double *psf, int p, int q, int cr, int cc, int m, int n, int bc, int r,
+                                  int which, int *lo, int *w, double *band, int *interior) {
+    if (which < 0 || which > 3) return fail(SFISTA_EINVAL, "which must be 0 (A), 1 (A^T), 2 (B) or 3 (B^T)");
+    if (!lo || !w) return fail(SFISTA_EINVAL, "lo or w is NULL");
+    if (cr == -1 && p > 0) cr = (p - 1) / 2;
+    if (cc == -1 && q > 0) cc = (q - 1) / 2;
+    HostSetup h;
+    sfista_status st = host_setup(psf, p, q, cr, cc, m, n, bc, r, &h);
+    if (st) return st;
+    const Band &F = which == 0 ? h.A : which == 1 ? h.AT : which == 2 ? h.B : h.BT;
+    *lo = F.lo;
+    *w = F.w;
+    if (band) std::copy(F.band.begin(), F.band.end(), band);
+    if (interior) {
+        std::vector<float> f(F.band.begin(), F.band.end());
+        band_interior(f.data(), F.len, F.r * F.w, &interior[0], &interior[1]);
+    }
     return SFISTA_OK;
 }
 

@@ -55,6 +55,10 @@ sfista_status host_setup(const double *psf, int p, int q, int cr, int cc, int m,
 
 // beta_k = (t_k - 1) / t_{k+1} for k = 1..iters (index k-1), t_1 = 1 (Alg. 2, Step 2).
 void momentum_table(int k_end, std::vector<double> *beta);
+// Widest run [*i0, *i1) of rows around len / 2 of an FP32 band table
+// (cnt = r * w values per row, stored tbl[t * len + row]) whose values equal
+// row len / 2 bit for bit: the Toeplitz interior of the factor family.
+void band_interior(const float *tbl, int len, int cnt, int *i0, int *i1);
 
 // ------------------------------------------------------------------ device kernels
 // Banded operator passes (compact band storage), T = float or double.

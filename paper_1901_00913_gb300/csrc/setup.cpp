@@ -262,6 +262,20 @@ sfista_status host_setup(const double *psf, int p, int q, int cr, int cc, int m,
     return SFISTA_OK;
 }
 
+void band_interior(const float *tbl, int len, int cnt, int *i0, int *i1) {
+    const int ref = len / 2;
+    auto same = [&](int row) {
+        for (int t = 0; t < cnt; ++t)
+            if (memcmp(&tbl[(size_t)t * len + row], &tbl[(size_t)t * len + ref], sizeof(float))) return false;
+        return true;
+    };
+    int a = ref, b = ref + 1;
+    while (a > 0 && same(a - 1)) --a;
+    while (b < len && same(b)) ++b;
+    *i0 = a;
+    *i1 = b;
+}
+
 void momentum_table(int k_end, std::vector<double> *beta) {
     beta->assign(std::max(k_end, 1), 0.0);
     double t = 1.0;

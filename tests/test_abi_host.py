@@ -117,3 +117,82 @@ def test_option_errors(lib, field, value):
     with pytest.raises(api.SfistaError) as ei:
         api.sfista_setup(W.gaussian_psf(9, 2.0), 64, 64, 1, 2, (-1, -1), o)
     assert ei.value.status == api.EINVAL
+
+
+def _dense_from_band(band, lo):
+    """F_k[c][c + lo + t] = band[k, t, c] (entries outside the axis are 0 by contract)."""
+    r, w, length = band.shape
+    F = np.zeros((r, length, length))
+    for k in range(r):
+        for t in range(w):
+            for c in range(length):
+                j = c + lo + t
+                if 0 <= j < length:
+                    F[k, c, j] = band[k, t, c]
+                else:
+                    assert band[k, t, c] == 0.0
+    return F
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("psf_shape,centre,shape,r", [((9, 7), (4, 3), (40, 36), 2), ((6, 11), (0, 10), (33, 50), 3),
+                                                      ((15, 15), (7, 7), (64, 64), 4)])
+def test_factor_bands_are_the_oracle_factors(lib, bc, psf_shape, centre, shape, r):
+    """The band tables the kernels read hold the factors T + H of Sec. 2 /
+    Theorem 1 (A_k acting on columns, B_k on rows, and their transposes),
+    as the oracle builds them densely."""
+    g = W.rng(900 + psf_shape[0] * 7 + psf_shape[1] + bc)
+    P = W.random_psf(g, *psf_shape)
+    m, n = shape
+    ka = kron.kron_approx(P, centre[0], centre[1], m, n, bc, r)
+    Bo, Ao = kron.dense_factors(ka)
+    ref = {0: Ao, 1: np.transpose(Ao, (0, 2, 1)), 2: Bo, 3: np.transpose(Bo, (0, 2, 1))}
+    for which in range(4):
+        band, lo, _ = api.sfista_factor_bands(P, m, n, bc, r, which, center=centre)
+        F = _dense_from_band(band, lo)
+        scale = np.abs(ref[which]).max()
+        np.testing.assert_allclose(F, ref[which], rtol=0, atol=1e-12 * scale)
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+@pytest.mark.parametrize("psf_shape,centre", [((9, 9), (4, 4)), ((7, 12), (1, 9)), ((13, 5), (12, 0))])
+def test_factor_band_interior_rows(lib, bc, psf_shape, centre):
+    """Interior rows: every row in [i0, i1) holds the middle row's FP32 values
+    bit for bit, the run is maximal, and it covers every row whose taps all
+    land inside the axis (no boundary term), where the factor is Toeplitz."""
+    g = W.rng(950 + psf_shape[0] + 3 * psf_shape[1] + bc)
+    P = W.random_psf(g, *psf_shape)
+    m, n, r = 64, 72, 2
+    for which in range(4):
+        band, lo, (i0, i1) = api.sfista_factor_bands(P, m, n, bc, r, which, center=centre)
+        f = band.astype(np.float32).reshape(-1, band.shape[-1])   # (r * w) x len
+        length = f.shape[1]
+        mid = length // 2
+        assert i0 <= mid < i1
+        for row in range(i0, i1):
+            assert np.array_equal(f[:, row].view(np.uint32), f[:, mid].view(np.uint32))
+        for row in (i0 - 1, i1):
+            if 0 <= row < length:
+                assert not np.array_equal(f[:, row].view(np.uint32), f[:, mid].view(np.uint32))
+        p = psf_shape[1] if which < 2 else psf_shape[0]
+        c = centre[1] if which < 2 else centre[0]
+        # Rows free of the boundary.  Row a of F_k takes taps a - t + c,
+        # t < p: all inside the axis for a in [p-1-c, len-1-c].  Row e of
+        # F_k^T gathers rows a = e + t - c of F_k (all must exist: e in
+        # [c, len-p+c]) and, with reflection, taps of rows near the ends that
+        # reflect onto e (none for e in [p-1-c, len-1-c]).
+        if which % 2 == 0:
+            first, last = p - 1 - c, length - 1 - c
+        else:
+            first, last = max(c, p - 1 - c), min(length - p + c, length - 1 - c)
+        assert i0 <= first and i1 >= last + 1, (which, i0, i1, first, last)
+
+
+def test_factor_bands_argument_errors(lib):
+    P = W.gaussian_psf(9, 2.0)
+    with pytest.raises(api.SfistaError) as ei:
+        api.sfista_factor_bands(P, 32, 32, 1, 2, 4)
+    assert ei.value.status == api.EINVAL
+    with pytest.raises(api.SfistaError) as ei:
+        api.sfista_factor_bands(P, 32, 32, 2, 2, 0)
+    assert ei.value.status == api.ENOTSUP
