@@ -480,7 +480,9 @@ __global__ void __launch_bounds__(NT, PRE ? 2 : 0) band_op_fused_kernel(const fl
 // own resident block (tiles <= co-resident blocks), for one problem or for a
 // batch of problems of any size, PSF and rank (one block per tile of every
 // problem; each block copies its problem's descriptor, a BandProb, into
-// shared memory).  Each block keeps, for the whole solve,
+// shared memory).  Tiles are th x 32 (th = P.th, a multiple of 4 up to 32,
+// picked on the host); warps whose four rows lie past th sit out the column
+// pass and the epilogue.  Each block keeps, for the whole solve,
 //   - the band tiles of both operator applications (A, B and A^T, B^T) in
 //     shared memory (staged once),
 //   - the double-float state (Y_k, X_{k-1}) of its epilogue pixels in
