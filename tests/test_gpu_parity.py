@@ -191,10 +191,11 @@ def test_solve_ragged(bc, op):
 @pytest.mark.parametrize("m,n", [(200, 176), (202, 178), (640, 512)])
 def test_persistent_forms_match_oracle(m, n):
     """The one-launch solver takes the fused form (band tiles and state resident)
-    when m, n are multiples of 4 and every 32 x 32 tile has a co-resident block
-    (200 x 176), else the two-pass form (202 x 178: not multiples of 4;
-    640 x 512: 320 tiles, more than two per SM).  Both against the oracle, and
-    a resumed solve against the uninterrupted one."""
+    when m, n are multiples of 4 and every tile has a co-resident block
+    (200 x 176: 16-row tiles, the last strip ragged), else the two-pass form
+    (202 x 178: not multiples of 4; 640 x 512: 320 tiles of 32 rows, more than
+    two per SM).  Both against the oracle, and a resumed solve against the
+    uninterrupted one."""
     P = W.rotated_gaussian_psf(31, 3.0, 1.0, 0.5)
     x, b, _ = _problem(m, n, P, 1, 108)
     ka = kron.kron_approx(P, 15, 15, m, n, 1, 3)
