@@ -51,7 +51,22 @@ def one_launch_fused(m, n):
     import torch
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     return m % 4 == 0 and n % 4 == 0 and -(-m // 32) * -(-n // 32) <= 2 * sms
+# Stated tolerances against the FP64 oracle: relative Frobenius error, and for
+# the split-precision forms also |PSNR - PSNR_oracle| <= 0.01 dB.  The
+# single-product BF16 / TF32 forms have no stated tolerance: they are reported
+# with their error and meets_tol = None.
 TOL = {"fp32": 1e-5, "bf16x3": 1e-4, "tf32x3": 1e-4}
+DPSNR_TOL = {"bf16x3": 0.01, "tf32x3": 0.01}
+
+
+def meets_tol(prec, err, dpsnr=None):
+    """True / False against the form's stated tolerance, None where it has none."""
+    if prec not in TOL:
+        return None
+    ok = err <= TOL[prec]
+    if prec in DPSNR_TOL:
+        ok = ok and dpsnr is not None and abs(dpsnr) <= DPSNR_TOL[prec]
+    return bool(ok)
 DTYPE = {"fp32": "f32", "bf16x3": "bf16", "tf32x3": "tf32", "bf16": "bf16", "tf32": "tf32"}
 NPROD = {"bf16x3": 3, "tf32x3": 3, "bf16": 1, "tf32": 1}
 STAGES = ["fwd_right", "fwd_left+residual", "adj_right", "adj_left+prox+momentum"]
@@ -892,7 +907,7 @@ def main():
         iter_ms = res["ms_total"] / (args.steps * iters)
         dur_ms = iter_ms * sm[dom] / sum(sm)
         achieved = work[dom] / (dur_ms / 1e3) / 1e12
-        ok = err <= TOL.get(prec, float("inf"))
+        ok = meets_tol(prec, err, dpsnr)
         kname = {"banded_persistent": ("band_solve_fused (whole solve, one launch)" if one_launch_fused(n, n)
                                        else "band_solve_persistent (whole solve, one launch)"),
                  "banded_fused": ["band_op_fused_kernel (forward + residual)", "",
@@ -915,7 +930,7 @@ def main():
                           e2e=iters * args.steps / res["e2e_s"], clocks=res["clocks"],
                           ms_per_step=res["ms_total"] / args.steps, resolved_op=op, tuned=res["tuned"],
                           refine_every=kref)
-    held = [k for k in lines if lines[k]["ok"] and lines[k]["prec"] in TOL and lines[k]["achieved"] is not None]
+    held = [k for k in lines if lines[k]["ok"] is True and lines[k]["achieved"] is not None]
     key0 = max(held or list(lines), key=lambda k: lines[k]["value"])
     L0 = lines[key0]
     line = {

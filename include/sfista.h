@@ -78,8 +78,9 @@ typedef enum {
     SFISTA_OP_BANDED_PERSISTENT = 4, /* banded FP32 operator, the whole iteration loop in one
                                         persistent cooperative launch (grid barrier between phases):
                                         the fused operator form with band tiles and state resident
-                                        when every 32 x 32 tile has its own block (m, n multiples of
-                                        4), else the two-pass form */
+                                        when every th x 32 output tile has its own resident block
+                                        (th, a multiple of 4 from 16 to 32, picked per problem; m, n
+                                        multiples of 4), else the two-pass form */
     SFISTA_OP_BANDED_FUSED = 5 /* banded FP32 operator, one kernel per operator application: the
                                   row pass is kept in shared memory for the column pass (the
                                   automatic FP32 choice up to 1024^2 pixels and band width 48;
@@ -143,7 +144,7 @@ void sfista_default_opts(sfista_opts *opts);
  */
 sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols,
                            int center_row, int center_col,
-                           int img_rows, int img_cols, int bc, int r,
+                           int img_rows, int img_cols, sfista_bc bc, int r,
                            const sfista_opts *opts, sfista_ctx **out);
 
 /*
@@ -157,7 +158,7 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols,
  */
 sfista_status sfista_factorize(const double *psf, int psf_rows, int psf_cols,
                                int center_row, int center_col,
-                               int img_rows, int img_cols, int bc, int r,
+                               int img_rows, int img_cols, sfista_bc bc, int r,
                                double *sigma, double *C, double *D,
                                double *approx_err);
 
@@ -180,7 +181,7 @@ sfista_status sfista_factorize(const double *psf, int psf_rows, int psf_cols,
  */
 sfista_status sfista_factor_bands(const double *psf, int psf_rows, int psf_cols,
                                   int center_row, int center_col,
-                                  int img_rows, int img_cols, int bc, int r,
+                                  int img_rows, int img_cols, sfista_bc bc, int r,
                                   int which, int *lo, int *w, double *band,
                                   int *interior);
 
@@ -331,7 +332,7 @@ sfista_status sfista_get_factors(const sfista_ctx *ctx, double *A, double *B);
  * distinct buffers).  Synchronous.
  */
 sfista_status sfista_blur(const double *psf, int psf_rows, int psf_cols,
-                          int center_row, int center_col, int bc,
+                          int center_row, int center_col, sfista_bc bc,
                           const float *d_x, int img_rows, int img_cols,
                           float *d_y, void *stream);
 
@@ -444,8 +445,13 @@ sfista_status sfista_batch_tune(sfista_batch *batch, int iters, sfista_tune_entr
  * state carries over, but calls whose work overlaps on the GPU (different
  * streams, or unordered host threads) race on it.  The first call on each
  * device looks up the array's device address with cudaGetSymbolAddress;
- * make that first call before any stream capture on that device.
+ * make that first call before any stream capture on that device.  The
+ * address is kept for the life of the process, so do not use this call on a
+ * device after cudaDeviceReset.
  * Calls no cudaMalloc or cudaFree.
+ * Errors: EINVAL for NULL or aliased buffers, sizes or r below 1, band widths
+ * outside [1, 2 * image size], band offsets lo outside
+ * [-2 * image size, image size], or the scratch limit above.
  */
 sfista_status sfista_apply_static(const float *d_x, float *d_y, int img_rows,
                                   int img_cols, int r,

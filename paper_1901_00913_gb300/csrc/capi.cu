@@ -538,7 +538,7 @@ void sfista_default_opts(sfista_opts *o) {
 }
 
 sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int center_row,
-                           int center_col, int img_rows, int img_cols, int bc, int r,
+                           int center_col, int img_rows, int img_cols, sfista_bc bc, int r,
                            const sfista_opts *opts, sfista_ctx **out) {
     TraceRange trace_("sfista_setup");
     if (!out) return fail(SFISTA_EINVAL, "out is NULL");
@@ -684,7 +684,7 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int ce
 
 void sfista_destroy(sfista_ctx *ctx) { ctx_free(ctx); }
 
-sfista_status sfista_factorize(const double *psf, int p, int q, int cr, int cc, int m, int n, int bc, int r,
+sfista_status sfista_factorize(const double *psf, int p, int q, int cr, int cc, int m, int n, sfista_bc bc, int r,
                                double *sigma, double *C, double *D, double *approx_err) {
     if (cr == -1 && p > 0) cr = (p - 1) / 2;
     if (cc == -1 && q > 0) cc = (q - 1) / 2;
@@ -698,7 +698,7 @@ sfista_status sfista_factorize(const double *psf, int p, int q, int cr, int cc, 
     return SFISTA_OK;
 }
 
-sfista_status sfista_factor_bands(const double *psf, int p, int q, int cr, int cc, int m, int n, int bc, int r,
+sfista_status sfista_factor_bands(const double *psf, int p, int q, int cr, int cc, int m, int n, sfista_bc bc, int r,
                                   int which, int *lo, int *w, double *band, int *interior) {
     if (which < 0 || which > 3) return fail(SFISTA_EINVAL, "which must be 0 (A), 1 (A^T), 2 (B) or 3 (B^T)");
     if (!lo || !w) return fail(SFISTA_EINVAL, "lo or w is NULL");
@@ -888,7 +888,7 @@ sfista_status sfista_get_factors(const sfista_ctx *c, double *A, double *B) {
     return SFISTA_OK;
 }
 
-sfista_status sfista_blur(const double *psf, int p, int q, int cr, int cc, int bc, const float *d_x, int m,
+sfista_status sfista_blur(const double *psf, int p, int q, int cr, int cc, sfista_bc bc, const float *d_x, int m,
                           int n, float *d_y, void *stream) {
     if (!psf || !d_x || !d_y) return fail(SFISTA_EINVAL, "NULL pointer");
     if (p < 1 || q < 1 || m < 1 || n < 1 || p > m || q > n) return fail(SFISTA_EINVAL, "bad sizes");

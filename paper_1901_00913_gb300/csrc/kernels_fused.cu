@@ -513,7 +513,7 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
 
 // Grid barrier number `nth` (1, 2, ...): every block adds one to counter
 // blockIdx % kBarWords, and warp 0 polls the kBarWords counters (one lane
-// each) until their sum reaches nth * gridDim.x.  The poll is bounded; a
+// each) until their sum reaches nth * gridDim.x (compared modulo 2^32).  The poll is bounded; a
 // block that gives up records DEV_TIMEOUT and returns false.
 // Ordering: the block barrier puts every thread's earlier writes before
 // thread 0's release add, a release is cumulative over what precedes it, and
@@ -531,7 +531,10 @@ __device__ bool fused_grid_sync(unsigned *bar, unsigned nth, unsigned *status, i
         const long long t0 = clock64();
         for (;;) {
             const unsigned v = lane < kBarWords ? ld_acquire(bar + 32 * lane) : 0u;
-            if (__reduce_add_sync(0xffffffffu, v) >= target) break;
+            // The counters and the target wrap modulo 2^32 on long solves; the
+            // sum never runs more than gridDim.x ahead of or behind the target,
+            // so the signed difference orders them correctly.
+            if ((int)(__reduce_add_sync(0xffffffffu, v) - target) >= 0) break;
             if (clock64() - t0 > kSpinCycles) {
                 if (lane == 0) {
                     atomicOr(status, DEV_TIMEOUT);

@@ -30,7 +30,10 @@ std::mutex g_scratch_mu;
 float *g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of the array on the current device, looked up once per
-// device (in host code the array's name is only a host-side stand-in).
+// device (in host code the array's name is only a host-side stand-in).  The
+// address is kept for the life of the process: after a cudaDeviceReset the
+// module is loaded again and the kept address is stale, so the entry point
+// must not be used across a device reset.
 sfista_status scratch_for_current_device(float **out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
@@ -61,6 +64,13 @@ extern "C" sfista_status sfista_apply_static(const float *d_x, float *d_y, int i
     if (img_rows < 1 || img_cols < 1 || r < 1) return fail(SFISTA_EINVAL, "sizes and r must be positive");
     if (w_right < 1 || w_left < 1 || w_right > 2 * img_cols || w_left > 2 * img_rows)
         return fail(SFISTA_EINVAL, "band widths must be in [1, 2 * image size]");
+    // A band whose offset lies further out than this touches no column of
+    // the image, and the kernels form row + lo (+ tap) in int: bounding lo
+    // keeps that arithmetic far from overflow.
+    if (lo_right < -2 * img_cols || lo_right > img_cols || lo_left < -2 * img_rows || lo_left > img_rows)
+        return fail(SFISTA_EINVAL, "band offsets must be in [-2 * image size, image size]");
+    if (img_rows > (1 << 28) || img_cols > (1 << 28))
+        return fail(SFISTA_EINVAL, "image side above 2^28");
     size_t need = (size_t)r * img_rows * img_cols;
     if (need > kStaticScratchFloats)
         return fail(SFISTA_EINVAL, "r * img_rows * img_cols = " + std::to_string(need) +

@@ -301,3 +301,33 @@ def example2_cases(seed=SEED_BASE + 6, n=256, r=5, iters=50, level=0.01, lam=0.0
                 out.append(pr)
                 k += 1
     return out
+
+
+# ---------------------------------------------------------------- comparison of large results
+# A full 2048^2 result is too large to keep beside the tests, so a long
+# reference run is stored as a summary that any later result can be compared
+# with: the values at a seeded set of pixels, and a CountSketch (each pixel
+# added with a random sign into one of k buckets).  For a difference image d,
+# ||S d||^2 has expectation ||d||_F^2 and relative standard deviation about
+# sqrt(2 / k) (Charikar, Chen, Farach-Colton 2002; a sparse Johnson-
+# Lindenstrauss embedding), so ||S x - S x_ref|| / ||x_ref|| estimates the
+# relative Frobenius error without the reference image.  Only seeded draws
+# and sums: none of the method's arithmetic.
+def sample_pixels(shape, count, seed):
+    """Flat indices of `count` seeded pixels plus the four corners and the
+    middle of every edge (the boundary rows and columns matter for the
+    boundary condition)."""
+    m, n = shape
+    g = rng(seed)
+    idx = g.choice(m * n, size=count, replace=False)
+    edge = [0, n - 1, (m - 1) * n, m * n - 1, n // 2, (m - 1) * n + n // 2, (m // 2) * n, (m // 2) * n + n - 1]
+    return np.unique(np.concatenate([idx, np.asarray(edge)])).astype(np.int64)
+
+
+def count_sketch(X, k, seed):
+    """CountSketch of the flattened image X into k buckets (FP64)."""
+    X = np.asarray(X, dtype=np.float64).ravel()
+    g = rng(seed)
+    bucket = g.integers(0, k, size=X.size)
+    sign = g.integers(0, 2, size=X.size) * 2.0 - 1.0
+    return np.bincount(bucket, weights=sign * X, minlength=k)

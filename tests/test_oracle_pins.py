@@ -206,6 +206,38 @@ def test_theorem2_rate_bound():
         assert Fk - Fs <= c / (k + 1) ** 2 + 1e-14
 
 
+@pytest.mark.parametrize("bc", [0, 1])
+def test_objective_matches_explicit_formula(bc):
+    """Phi_s(X) = 1/2 ||A_s vec X - vec B||^2 + 1/2 lam^2 ||X||^2 (Eq. matrix minimization model),
+    with A_s the explicit sum of Kronecker products acting on the column-stacked vec."""
+    ka, Bd, As, _ = _tiny_problem(bc=bc, seed=27)
+    g = W.rng(28)
+    for lam in (0.0, 0.07, 0.6):
+        X = g.standard_normal(Bd.shape)
+        e = As @ X.flatten(order="F") - Bd.flatten(order="F")
+        want = 0.5 * float(e @ e) + 0.5 * lam * lam * float(np.sum(X * X))
+        assert abs(oracle.objective(X, Bd, ka, lam) - want) <= 1e-13 * want
+
+
+def test_objective_at_and_around_the_minimiser():
+    """At X* = (A_s^T A_s + lam^2 I)^{-1} A_s^T b:  Phi_s(X*) = 1/2 <B - A_s X*, B>, and for any D,
+    Phi_s(X* + D) - Phi_s(X*) = 1/2 ||A_s D||^2 + 1/2 lam^2 ||D||^2 (the quadratic's expansion about its
+    minimiser).  A dropped 1/2, lam in place of lam^2 or a sign error breaks one of the two."""
+    ka, Bd, As, _ = _tiny_problem(seed=29)
+    g = W.rng(30)
+    for lam in (0.05, 0.4):
+        Xs = _tikhonov_minimiser(As, Bd, lam)
+        Fs = oracle.objective(Xs, Bd, ka, lam)
+        r = Bd.flatten(order="F") - As @ Xs.flatten(order="F")
+        assert abs(Fs - 0.5 * float(r @ Bd.flatten(order="F"))) <= 1e-12 * Fs
+        for _ in range(3):
+            D = g.standard_normal(Bd.shape)
+            AD = As @ D.flatten(order="F")
+            want = 0.5 * float(AD @ AD) + 0.5 * lam * lam * float(np.sum(D * D))
+            got = oracle.objective(Xs + D, Bd, ka, lam) - Fs
+            assert abs(got - want) <= 1e-11 * want
+
+
 def test_converges_to_closed_form_tikhonov():
     """With enough iterations X_k -> X* = (A_s^T A_s + lam^2 I)^{-1} A_s^T b, and X* is a fixed point of Step 1."""
     ka, Bd, As, L = _tiny_problem(seed=24)
