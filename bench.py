@@ -38,10 +38,13 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x
 KERNELS_PER_ITER = {"banded": 4, "banded_fused": 2, "gemm_band": 4, "gemm_dense": 4}
 # DRAM bytes (read + write) per launch of a form's dominant kernel, from an
 # ncu capture of the current kernel code on this workload (the summary in
-# profiles/ gives the command); forms without one report null.  The last
-# capture of band_solve_fused (0.365 MB per iteration) predates its tile-height
-# choice, so the headline form reports null until it is taken again.
-TRAFFIC = {}
+# profiles/ gives the command); forms without one report null.
+TRAFFIC = {
+    # one 200-iteration solve (one launch) of band_solve_fused, 28-row tiles, cold L2
+    "fp32:banded_persistent:0": {"bytes": 7267584 + 36864,
+                                 "source": "profiles/solve_fused_fp32_cfg2_512_r3.md (ncu dram__bytes_read.sum + "
+                                           "dram__bytes_write.sum, one 200-iteration launch)"},
+}
 
 
 def one_launch_fused(m, n):
