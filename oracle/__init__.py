@@ -11,8 +11,8 @@ arithmetic.
 Modules
 -------
 ``_native``  builds and loads ``sfista_oracle.c`` (exact blur, the Kronecker
-             operator as 1-D boundary-aware convolutions, Alg. 1 and Alg. 2,
-             power iteration for L).
+             operator as 1-D boundary-aware convolutions, Alg. 1 on an explicit
+             matrix and on the exact blur, Alg. 2, power iteration for L).
 ``kron``     Kronecker approximation of Sec. 2 / Theorem 1 (Gram weights,
              Cholesky, SVD of the weighted PSF, factor profiles, dense
              toep/hank factors for small checks).
@@ -36,6 +36,8 @@ from .solve import (  # noqa: F401
     lipschitz,
     sfista,
     fista_dense,
+    fista_exact,
+    lipschitz_exact,
     objective,
     t_schedule,
     rel_fro,

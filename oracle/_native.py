@@ -79,3 +79,6 @@ def _declare(L):
     L.orc_sfista.argtypes = [_D, i, i, i, _D, i, i, _D, i, i, i, d, d, i, i, d, i,
                              vp, vp, _D, vp]
     L.orc_fista_dense.argtypes = [_D, _D, i, d, d, d, i, _D]
+    L.orc_fista_exact.argtypes = [_D, i, i, _D, i, i, i, i, i, d, d, i, _D]
+    L.orc_power_lipschitz_exact.argtypes = [_D, i, i, _D, i, i, i, i, i, d, i, ctypes.POINTER(ctypes.c_int)]
+    L.orc_power_lipschitz_exact.restype = d

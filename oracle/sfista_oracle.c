@@ -363,6 +363,77 @@ void orc_fista_dense(const double *A, const double *b, int N, double L,
     free(r);
 }
 
+/* Vector FISTA (Alg. 1) on the exact blur A of Eq. (1.1), no Kronecker
+ * approximation, x_0 = 0 and a fixed iteration count.  The vector x is the
+ * image X (any fixed ordering of its pixels gives the same element-wise
+ * steps); A x is orc_blur and A^T r is orc_blur_T:
+ *   Step 1: x_k = (L y_k - A^T (A y_k - b)) / (L + lambda^2)
+ *   Step 2: t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2,  t_1 = 1
+ *   Step 3: y_{k+1} = x_k + (t_k - 1)/t_{k+1} (x_k - x_{k-1})          */
+void orc_fista_exact(const double *Bd, int m, int n, const double *P, int p,
+                     int q, int cr, int cc, int bc, double L, double lambda,
+                     int iters, double *X_out)
+{
+    size_t N = (size_t)m * n;
+    double *x = (double *)calloc(N, sizeof(double));
+    double *xp = (double *)calloc(N, sizeof(double));
+    double *y = (double *)calloc(N, sizeof(double));
+    double *r = (double *)malloc(sizeof(double) * N);
+    double *g = (double *)malloc(sizeof(double) * N);
+    double t = 1.0, lam2 = lambda * lambda;
+    for (int k = 1; k <= iters; ++k) {
+        orc_blur(y, m, n, P, p, q, cr, cc, bc, r);
+        for (size_t s = 0; s < N; ++s) r[s] -= Bd[s];
+        orc_blur_T(r, m, n, P, p, q, cr, cc, bc, g);
+        memcpy(xp, x, sizeof(double) * N);
+        for (size_t s = 0; s < N; ++s) x[s] = (L * y[s] - g[s]) / (L + lam2);
+        double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+        for (size_t s = 0; s < N; ++s) y[s] = x[s] + (t - 1.0) / tn * (x[s] - xp[s]);
+        t = tn;
+    }
+    memcpy(X_out, x, sizeof(double) * N);
+    free(x);
+    free(xp);
+    free(y);
+    free(r);
+    free(g);
+}
+
+/* Largest eigenvalue of A^T A for the exact blur by power iteration from
+ * X0 (overwritten), stopping rule as orc_power_lipschitz. */
+double orc_power_lipschitz_exact(double *X0, int m, int n, const double *P,
+                                 int p, int q, int cr, int cc, int bc,
+                                 double tol, int maxit, int *iters_out)
+{
+    size_t N = (size_t)m * n;
+    double *T = (double *)malloc(sizeof(double) * N);
+    double *U = (double *)malloc(sizeof(double) * N);
+    double nrm = 0.0, mu = 0.0, prev = 0.0;
+    int it = 0;
+    for (size_t t = 0; t < N; ++t) nrm += X0[t] * X0[t];
+    nrm = sqrt(nrm);
+    for (size_t t = 0; t < N; ++t) X0[t] /= nrm;
+    for (it = 1; it <= maxit; ++it) {
+        orc_blur(X0, m, n, P, p, q, cr, cc, bc, T);
+        orc_blur_T(T, m, n, P, p, q, cr, cc, bc, U);
+        mu = 0.0;
+        nrm = 0.0;
+        for (size_t t = 0; t < N; ++t) {
+            mu += X0[t] * U[t];
+            nrm += U[t] * U[t];
+        }
+        nrm = sqrt(nrm);
+        if (nrm == 0.0) break;
+        for (size_t t = 0; t < N; ++t) X0[t] = U[t] / nrm;
+        if (it > 1 && fabs(mu - prev) <= tol * fabs(mu)) break;
+        prev = mu;
+    }
+    if (iters_out) *iters_out = it;
+    free(T);
+    free(U);
+    return mu;
+}
+
 /* Number of OpenMP threads for the following calls (n <= 0: leave unchanged);
  * returns the number in effect (1 without OpenMP).  For timing only. */
 int orc_set_threads(int n)

@@ -111,6 +111,27 @@ def fista_dense(A, b, L, lam, iters, mu=0.0):
     return x
 
 
+def fista_exact(Bd, P, cr, cc, bc, L, lam, iters):
+    """Alg. 1 (vector FISTA) on the exact blur A of Eq. (1.1), x_0 = 0: the
+    comparison system of Sec. 4 (no Kronecker approximation)."""
+    Bd, P = _f64(Bd), _f64(P)
+    m, n = Bd.shape
+    X = np.empty_like(Bd)
+    _native.lib().orc_fista_exact(Bd, m, n, P, P.shape[0], P.shape[1], int(cr), int(cc), int(bc), float(L),
+                                  float(lam), int(iters), X)
+    return X
+
+
+def lipschitz_exact(P, cr, cc, bc, X0, tol=1e-13, maxit=2000):
+    """lambda_max(A^T A) of the exact blur by power iteration from X0; returns (L, iterations)."""
+    X, P = _f64(X0).copy(), _f64(P)
+    m, n = X.shape
+    it = ctypes.c_int(0)
+    L = _native.lib().orc_power_lipschitz_exact(X, m, n, P, P.shape[0], P.shape[1], int(cr), int(cc), int(bc),
+                                                tol, maxit, ctypes.byref(it))
+    return float(L), int(it.value)
+
+
 def t_schedule(iters):
     """t_1 = 1, t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2 (Alg. 2, Step 2); returns t_1..t_{iters+1}."""
     t = [1.0]

@@ -369,3 +369,46 @@ def test_l1_sfista_equals_vector_fista():
         X = oracle.sfista(Bd, ka, L, 0.05, iters, mu=0.01)
         x = oracle.fista_dense(As, Bd.flatten(order="F"), L, 0.05, iters, mu=0.01)
         np.testing.assert_allclose(X.flatten(order="F"), x, atol=1e-13)
+
+
+# ------------------------------------------------------------------ Alg. 1 on the exact blur
+@pytest.mark.parametrize("bc", [0, 1])
+def test_fista_exact_equals_alg1_on_explicit_blur_matrix(bc):
+    """Alg. 1 with A applied by the exact blur == Alg. 1 on the explicit N x N matrix whose columns are
+    point-source images (Sec. 2), iterate for iterate; non-symmetric, non-centred PSF."""
+    g = W.rng(40)
+    P = W.random_psf(g, 5, 4)
+    m, n = 9, 8
+    A = kron.explicit_blur_matrix(P, 1, 3, m, n, bc)
+    x = g.uniform(size=(m, n))
+    Bd = oracle.blur(x, P, 1, 3, bc) + 0.01 * g.standard_normal((m, n))
+    L = float(np.linalg.eigvalsh(A.T @ A).max())
+    for iters in (1, 3, 25):
+        X = oracle.fista_exact(Bd, P, 1, 3, bc, L, 0.05, iters)
+        xd = oracle.fista_dense(A, Bd.flatten(order="F"), L, 0.05, iters)
+        np.testing.assert_allclose(X.flatten(order="F"), xd, atol=1e-13)
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+def test_lipschitz_exact_matches_eig(bc):
+    g = W.rng(41)
+    P = W.random_psf(g, 5, 5)
+    A = kron.explicit_blur_matrix(P, 2, 2, 10, 9, bc)
+    L = float(np.linalg.eigvalsh(A.T @ A).max())
+    Lp, _ = oracle.lipschitz_exact(P, 2, 2, bc, W.rng(1).uniform(size=(10, 9)), tol=1e-15, maxit=20000)
+    assert abs(Lp - L) <= 1e-10 * L
+
+
+def test_fista_exact_is_sfista_for_a_separable_psf():
+    """A separable PSF is its own rank-1 Kronecker approximation (Theorem 1 with sigma_2 = 0), so Alg. 1 on
+    the exact blur and Alg. 2 with r = 1 produce the same iterates."""
+    g = W.rng(42)
+    P = W.gaussian_psf(9, 1.7)
+    x = W.rectangles_image(g, 48, 40)
+    for bc in (0, 1):
+        Bd = oracle.blur(x, P, 4, 4, bc) + 0.01 * g.standard_normal(x.shape)
+        ka = kron.kron_approx(P, 4, 4, 48, 40, bc, 1)
+        assert ka.approx_err < 1e-12
+        X1 = oracle.fista_exact(Bd, P, 4, 4, bc, 1.0, 0.02, 30)
+        X2 = oracle.sfista(Bd, ka, 1.0, 0.02, 30)
+        np.testing.assert_allclose(X1, X2, atol=1e-12)
