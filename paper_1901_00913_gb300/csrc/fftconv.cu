@@ -1,0 +1,599 @@
+// FFT form of the operator: the boundary-extended image convolved with a 2-D
+// kernel through mixed-radix FFTs in shared memory.
+//
+// Why one 2-D convolution.  A right factor A_i = toep(d_i) [+ hank(d_i)]
+// applies the row profile d_i to the zero or reflected extension of each row,
+// and a left factor B_i does the same along columns with c_i (Sec. 2; the
+// Hankel part is exactly the reflection).  The extension acts on each axis
+// separately, so
+//   (sum_i B_i X A_i^T)[a][b] = sum_{k,l} K[k][l] Xext[a - k + cr][b - l + cc],
+//   K = sum_i c_i d_i^T,
+// one 2-D convolution of the extended image with the rank-r kernel K.  The
+// exact blur of Eq. (1.1) has the same form with K = P (the PSF itself), so
+// the same engine applies A for vector FISTA on the unapproximated blur
+// (Alg. 1).  The paper's structured products transform every term's factor
+// separately (1-D FFTs per term); here the r terms are summed in the kernel,
+// so the cost does not grow with r.
+//
+// Index conventions (rows; columns alike with n, q, cc).  offr = p - 1 - cr
+// extension rows lie above row 0; the extended image has m + p - 1 rows,
+// row s holding source row ext(s - offr) (zero or half-sample reflection, as
+// the Hankel part of Sec. 2 encodes).  With N1 >= m + p - 1 (no wrap-around):
+//   forward:  y = h (*) E, h[u mod N1] = K[u + p - 1] for u in [-(p-1), 0],
+//             output rows a in [0, m) are y[a];
+//   adjoint:  u = g (*) R0 with g[s] = K[p - 1 - s] (conj(h^) in frequency),
+//             R0 the input zero-padded, output row a sums u[s] over the s with
+//             ext(s - offr) = a (the transpose of the extension: a fold).
+// (*) is circular convolution of length N1, done as pointwise products of
+// spectra.
+//
+// Three passes per application (Pass A and Pass C along rows, Pass B along
+// columns), each one kernel:
+//   A  two real rows packed as one complex line (real, imaginary part), the
+//      extension gathered on load, a decimation-in-frequency FFT, then the
+//      half spectra of the two rows unpacked (Hermitian symmetry) to S1.
+//   B  per frequency column f of S1: DIF FFT along the rows, product with the
+//      kernel spectrum (conjugated for the adjoint), inverse DIT FFT, the
+//      output rows (forward) or the fold (adjoint) to S2.
+//   C  two rows' half spectra packed into one complex line (Y_a + i Y_{a+1}),
+//      inverse DIT FFT, real and imaginary parts are the two output rows;
+//      column fold for the adjoint; then the epilogue (store, residual, or
+//      Step 1 shrink + Step 3 momentum of Alg. 2 on the double-float state).
+// The DIF FFT leaves its output in digit-reversed order and the inverse DIT
+// FFT with the stages reversed reads exactly that order, so no reordering
+// pass is needed: the kernel spectrum is stored in the same scrambled order
+// (Pass B), and Pass A / C address frequency f at its scrambled position.
+// Twiddles and kernel spectra are computed in FP64 on the host; all device
+// arithmetic is FP32.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <vector>
+
+#include "epilogue.cuh"
+#include "fftconv.h"
+
+namespace sfista {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// -i * a (forward) or +i * a (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 rot(float2 a) {
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// In-register DFT of R points, v[u] = sum_k v[k] w^(u k), w = exp(-+2 pi i / R)
+// (minus: forward, plus: INV; no scaling).
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2 (&v)[R]);
+
+template <>
+__device__ __forceinline__ void dft<2, false>(float2 (&v)[2]) {
+    const float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+}
+template <>
+__device__ __forceinline__ void dft<2, true>(float2 (&v)[2]) {
+    dft<2, false>(v);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2 (&v)[4]) {
+    const float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+    const float2 s13 = cadd(v[1], v[3]), d13 = rot<INV>(csub(v[1], v[3]));
+    v[0] = cadd(s02, s13);
+    v[2] = csub(s02, s13);
+    v[1] = cadd(d02, d13);
+    v[3] = csub(d02, d13);
+}
+template <>
+__device__ __forceinline__ void dft<4, false>(float2 (&v)[4]) {
+    dft4<false>(v);
+}
+template <>
+__device__ __forceinline__ void dft<4, true>(float2 (&v)[4]) {
+    dft4<true>(v);
+}
+
+// R = 3: w = c -+ i s with c = cos(2 pi / 3) = -1/2, s = sin(2 pi / 3) = sqrt(3)/2.
+template <bool INV>
+__device__ __forceinline__ void dft3(float2 (&v)[3]) {
+    const float s3 = 0.86602540378443864676f;
+    const float2 t = cadd(v[1], v[2]);
+    const float2 m = make_float2(v[0].x - 0.5f * t.x, v[0].y - 0.5f * t.y);
+    const float2 d = csub(v[1], v[2]);
+    const float2 j = rot<INV>(make_float2(s3 * d.x, s3 * d.y));   // -+ i s (v1 - v2)
+    v[0] = cadd(v[0], t);
+    v[1] = cadd(m, j);
+    v[2] = csub(m, j);
+}
+template <>
+__device__ __forceinline__ void dft<3, false>(float2 (&v)[3]) {
+    dft3<false>(v);
+}
+template <>
+__device__ __forceinline__ void dft<3, true>(float2 (&v)[3]) {
+    dft3<true>(v);
+}
+
+// R = 5 with c1 = cos(2 pi / 5), c2 = cos(4 pi / 5), s1 = sin(2 pi / 5),
+// s2 = sin(4 pi / 5):  y1,4 = v0 + c1 t1 + c2 t2 -+ i (s1 d1 + s2 d2),
+// y2,3 = v0 + c2 t1 + c1 t2 -+ i (s2 d1 - s1 d2), t = sums, d = differences
+// of the mirrored pairs (1, 4) and (2, 3).
+template <bool INV>
+__device__ __forceinline__ void dft5(float2 (&v)[5]) {
+    const float c1 = 0.30901699437494742410f, c2 = -0.80901699437494742410f;
+    const float s1 = 0.95105651629515357212f, s2 = 0.58778525229247312917f;
+    const float2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+    const float2 d1 = csub(v[1], v[4]), d2 = csub(v[2], v[3]);
+    const float2 a1 = make_float2(v[0].x + c1 * t1.x + c2 * t2.x, v[0].y + c1 * t1.y + c2 * t2.y);
+    const float2 a2 = make_float2(v[0].x + c2 * t1.x + c1 * t2.x, v[0].y + c2 * t1.y + c1 * t2.y);
+    const float2 b1 = rot<INV>(make_float2(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y));
+    const float2 b2 = rot<INV>(make_float2(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y));
+    v[0] = cadd(v[0], cadd(t1, t2));
+    v[1] = cadd(a1, b1);
+    v[4] = csub(a1, b1);
+    v[2] = cadd(a2, b2);
+    v[3] = csub(a2, b2);
+}
+template <>
+__device__ __forceinline__ void dft<5, false>(float2 (&v)[5]) {
+    dft5<false>(v);
+}
+template <>
+__device__ __forceinline__ void dft<5, true>(float2 (&v)[5]) {
+    dft5<true>(v);
+}
+
+// One butterfly of a stage: the R points x[k * M], k < R.
+// DIF (forward): DFT, then twiddles w_L^(u q) on outputs u >= 1.
+// DIT inverse: conjugate twiddles on inputs u >= 1, then the inverse DFT.
+// tw points at this butterfly's twiddle for u = 1; u's is tw[(u - 1) * M].
+template <int R, bool INV>
+__device__ __forceinline__ void bfly(float2 *x, int M, const float2 *__restrict__ tw) {
+    float2 v[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = x[k * M];
+    if (INV) {
+#pragma unroll
+        for (int u = 1; u < R; ++u) v[u] = cmulc(v[u], __ldg(tw + (u - 1) * M));
+        dft<R, true>(v);
+    } else {
+        dft<R, false>(v);
+#pragma unroll
+        for (int u = 1; u < R; ++u) v[u] = cmul(v[u], __ldg(tw + (u - 1) * M));
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) x[k * M] = v[k];
+}
+
+// All stages of `lines` in-place transforms of length P.N held in shared
+// memory at buf + line * ls, the whole block cooperating.  Forward: DIF,
+// natural order in, digit-reversed out.  INV: DIT with the stages in
+// reverse order, digit-reversed in, natural out, unscaled.
+template <bool INV>
+__device__ void fft_lines(float2 *buf, int lines, int ls, const FftLine &P, const float2 *__restrict__ tw) {
+    for (int jj = 0; jj < P.ns; ++jj) {
+        const int j = INV ? P.ns - 1 - jj : jj;
+        const int R = P.R[j], M = P.M[j], L = R * M, per = P.N / R;
+        const float2 *t = tw + P.tw[j];
+        for (int it = threadIdx.x; it < lines * per; it += blockDim.x) {
+            const int line = it / per, bf = it - line * per;
+            const int b = bf / M, q = bf - b * M;
+            float2 *x = buf + (size_t)line * ls + b * L + q;
+            switch (R) {
+                case 2: bfly<2, INV>(x, M, t + q); break;
+                case 3: bfly<3, INV>(x, M, t + q); break;
+                case 4: bfly<4, INV>(x, M, t + q); break;
+                default: bfly<5, INV>(x, M, t + q); break;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Source index of extended index t on an axis of len pixels, or -1 (zero
+// boundary outside, or beyond one reflection).
+__device__ __forceinline__ int ext_src(int t, int len, int bc) {
+    if (t >= 0 && t < len) return t;
+    if (!bc) return -1;
+    t = t < 0 ? -1 - t : 2 * len - 1 - t;
+    return (t >= 0 && t < len) ? t : -1;
+}
+
+// Pass A: rows (extended rows for the forward operator) -> half spectra S1.
+template <bool ADJ>
+__global__ void __launch_bounds__(kThreads) fft_pass_a(FftConvDev P, const float *__restrict__ In, int lpc) {
+    extern __shared__ float2 fbuf[];
+    const int N = P.l2.N, ls = N + 1;
+    const int rows = ADJ ? P.m : P.ext_rows;
+    const int pair0 = blockIdx.x * lpc;
+    for (int it = threadIdx.x; it < lpc * N; it += blockDim.x) {
+        const int j = it / N, t = it - j * N;
+        const int s = 2 * (pair0 + j);
+        float2 v = make_float2(0.f, 0.f);
+        if (ADJ) {
+            if (t < P.n) {
+                if (s < rows) v.x = __ldcg(In + (size_t)s * P.n + t);
+                if (s + 1 < rows) v.y = __ldcg(In + (size_t)(s + 1) * P.n + t);
+            }
+        } else if (t < P.ext_cols) {
+            const int b = ext_src(t - P.offc, P.n, P.bc);
+            if (b >= 0) {
+                const int a0 = s < rows ? ext_src(s - P.offr, P.m, P.bc) : -1;
+                const int a1 = s + 1 < rows ? ext_src(s + 1 - P.offr, P.m, P.bc) : -1;
+                if (a0 >= 0) v.x = __ldcg(In + (size_t)a0 * P.n + b);
+                if (a1 >= 0) v.y = __ldcg(In + (size_t)a1 * P.n + b);
+            }
+        }
+        fbuf[(size_t)j * ls + t] = v;
+    }
+    __syncthreads();
+    fft_lines<false>(fbuf, lpc, ls, P.l2, P.tw2);
+    // Z = FFT(a + i b): A[f] = (Z[f] + conj Z[N-f]) / 2, B[f] = (Z[f] - conj Z[N-f]) / (2i).
+    for (int it = threadIdx.x; it < lpc * P.H2; it += blockDim.x) {
+        const int j = it / P.H2, f = it - j * P.H2;
+        const int s = 2 * (pair0 + j);
+        if (s >= rows) continue;
+        const float2 z1 = fbuf[(size_t)j * ls + __ldg(P.pos2 + f)];
+        const float2 z2 = fbuf[(size_t)j * ls + __ldg(P.pos2 + (f == 0 ? 0 : N - f))];
+        P.S1[(size_t)s * P.H2 + f] = make_float2(0.5f * (z1.x + z2.x), 0.5f * (z1.y - z2.y));
+        if (s + 1 < rows) P.S1[(size_t)(s + 1) * P.H2 + f] = make_float2(0.5f * (z1.y + z2.y), 0.5f * (z2.x - z1.x));
+    }
+}
+
+// Pass B: frequency columns of S1 -> kernel product along the rows -> S2.
+template <bool ADJ>
+__global__ void __launch_bounds__(kThreads) fft_pass_b(FftConvDev P, int lpc) {
+    extern __shared__ float2 fbuf[];
+    const int N = P.l1.N, ls = N + 1;
+    const int rows_in = ADJ ? P.m : P.ext_rows;
+    const int f0 = blockIdx.x * lpc;
+    for (int it = threadIdx.x; it < lpc * N; it += blockDim.x) {
+        const int s = it / lpc, j = it - s * lpc;   // j fastest: neighbouring columns together
+        const int f = f0 + j;
+        fbuf[(size_t)j * ls + s] =
+            (s < rows_in && f < P.H2) ? __ldcg(P.S1 + (size_t)s * P.H2 + f) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    fft_lines<false>(fbuf, lpc, ls, P.l1, P.tw1);
+    for (int it = threadIdx.x; it < lpc * N; it += blockDim.x) {
+        const int pos = it / lpc, j = it - pos * lpc;
+        const int f = f0 + j;
+        if (f >= P.H2) continue;
+        const float2 k = __ldg(P.K + (size_t)pos * P.H2 + f);
+        float2 &x = fbuf[(size_t)j * ls + pos];
+        x = ADJ ? cmulc(x, k) : cmul(x, k);
+    }
+    __syncthreads();
+    fft_lines<true>(fbuf, lpc, ls, P.l1, P.tw1);
+    for (int it = threadIdx.x; it < lpc * P.m; it += blockDim.x) {
+        const int a = it / lpc, j = it - a * lpc;
+        const int f = f0 + j;
+        if (f >= P.H2) continue;
+        const float2 *u = fbuf + (size_t)j * ls;
+        float2 v;
+        if (ADJ) {
+            // extended rows s with ext(s - offr) = a: s = a + offr, and for the
+            // reflective boundary offr - 1 - a and 2m - 1 - a + offr
+            v = u[a + P.offr];
+            if (P.bc) {
+                const int s1 = P.offr - 1 - a, s2 = 2 * P.m - 1 - a + P.offr;
+                if (s1 >= 0) v = cadd(v, u[s1]);
+                if (s2 < P.ext_rows) v = cadd(v, u[s2]);
+            }
+        } else {
+            v = u[a];
+        }
+        P.S2[(size_t)a * P.H2 + f] = v;
+    }
+}
+
+// Pass C: two rows' half spectra -> one inverse FFT -> the two output rows,
+// then the epilogue.
+template <bool ADJ, int EPI>
+__global__ void __launch_bounds__(kThreads) fft_pass_c(FftConvDev P, float *__restrict__ Out, ProxArgs pa, int lpc) {
+    extern __shared__ float2 fbuf[];
+    const int N = P.l2.N, ls = N + 1;
+    const int pair0 = blockIdx.x * lpc;
+    for (int it = threadIdx.x; it < lpc * N; it += blockDim.x) {
+        const int j = it / N, f = it - j * N;
+        const int a = 2 * (pair0 + j);
+        const bool mirror = f >= P.H2;   // Y[f] = conj Y[N - f] for a real row
+        const int g = mirror ? N - f : f;
+        float2 ya = make_float2(0.f, 0.f), yb = make_float2(0.f, 0.f);
+        if (a < P.m) ya = __ldcg(P.S2 + (size_t)a * P.H2 + g);
+        if (a + 1 < P.m) yb = __ldcg(P.S2 + (size_t)(a + 1) * P.H2 + g);
+        if (mirror) {
+            ya.y = -ya.y;
+            yb.y = -yb.y;
+        }
+        fbuf[(size_t)j * ls + __ldg(P.pos2 + f)] = make_float2(ya.x - yb.y, ya.y + yb.x);
+    }
+    __syncthreads();
+    fft_lines<true>(fbuf, lpc, ls, P.l2, P.tw2);
+    const int n = P.n;
+    for (int it = threadIdx.x; it < lpc * 2 * n; it += blockDim.x) {
+        const int j = it / (2 * n), rem = it - j * 2 * n;
+        const int h = rem / n, b = rem - h * n;
+        const int a = 2 * (pair0 + j) + h;
+        if (a >= P.m) continue;
+        const float2 *u = fbuf + (size_t)j * ls;
+        float2 w;
+        if (ADJ) {
+            w = u[b + P.offc];
+            if (P.bc) {
+                const int t1 = P.offc - 1 - b, t2 = 2 * n - 1 - b + P.offc;
+                if (t1 >= 0) w = cadd(w, u[t1]);
+                if (t2 < P.ext_cols) w = cadd(w, u[t2]);
+            }
+        } else {
+            w = u[b];
+        }
+        const float v = h ? w.y : w.x;
+        const size_t idx = (size_t)a * n + b;
+        if (EPI == EPI_STORE)
+            Out[idx] = v;
+        else if (EPI == EPI_RESIDUAL)
+            Out[idx] = v - __ldcg(pa.Bd + idx);
+        else
+            prox_momentum(pa, idx, v);
+    }
+}
+
+// ------------------------------------------------------------------ host plan
+// Smallest even N >= need of the form 2^a 3^b 5^c.
+int smooth_len(int need) {
+    long best = -1;
+    for (long a = 2; a < 4L * need; a *= 2)
+        for (long b = a; b < 4L * need; b *= 3)
+            for (long c = b; c < 4L * need; c *= 5)
+                if (c >= need && (best < 0 || c < best)) best = c;
+    return (int)best;
+}
+
+// DIF stages of length N: radix 4 while possible, then 2, 3, 5.
+bool line_plan(int N, FftLine *P, std::vector<double2> *tw) {
+    std::vector<int> rad;
+    int r = N;
+    while (r % 4 == 0) {
+        rad.push_back(4);
+        r /= 4;
+    }
+    while (r % 2 == 0) {
+        rad.push_back(2);
+        r /= 2;
+    }
+    while (r % 3 == 0) {
+        rad.push_back(3);
+        r /= 3;
+    }
+    while (r % 5 == 0) {
+        rad.push_back(5);
+        r /= 5;
+    }
+    if (r != 1 || (int)rad.size() > kFftMaxStages) return false;
+    P->N = N;
+    P->ns = (int)rad.size();
+    tw->clear();
+    int L = N;
+    for (int j = 0; j < P->ns; ++j) {
+        const int R = rad[j], M = L / R;
+        P->R[j] = R;
+        P->M[j] = M;
+        P->tw[j] = (int)tw->size();
+        for (int u = 1; u < R; ++u)
+            for (int q = 0; q < M; ++q) {
+                const double ang = -2.0 * M_PI * (double)u * q / L;
+                tw->push_back(make_double2(std::cos(ang), std::sin(ang)));
+            }
+        L = M;
+    }
+    return true;
+}
+
+// pos[f]: the position at which the DIF stages leave frequency f.  Position
+// p = sum_j u_j M_j (u_j the butterfly output of stage j) holds frequency
+// f = sum_j u_j R_1 ... R_{j-1}.
+std::vector<int> dif_positions(const FftLine &P) {
+    std::vector<int> pos(P.N);
+    for (int p = 0; p < P.N; ++p) {
+        int rem = p, f = 0, w = 1;
+        for (int j = 0; j < P.ns; ++j) {
+            const int u = rem / P.M[j];
+            rem -= u * P.M[j];
+            f += u * w;
+            w *= P.R[j];
+        }
+        pos[f] = p;
+    }
+    return pos;
+}
+
+template <typename T>
+cudaError_t upload_vec(T **dst, const std::vector<T> &v) {
+    cudaError_t e = cudaMalloc((void **)dst, sizeof(T) * std::max<size_t>(v.size(), 1));
+    if (e) return e;
+    return cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+}
+
+// Lines per block: as many as keep >= 2 blocks per SM over `lines` lines and
+// the buffer under 96 KB.
+int pick_lpc(long lines, int N, int sms) {
+    int lpc = 1;
+    while (lpc < 8 && (size_t)(2 * lpc) * (N + 1) * sizeof(float2) <= 96 * 1024 &&
+           (lines + 2 * lpc - 1) / (2 * lpc) >= 2L * sms)
+        lpc *= 2;
+    return lpc;
+}
+
+// The attribute is per kernel, not per launch: every FFT kernel is allowed
+// the most any plan uses (pick_lpc keeps a block at or under 96 KB, and one
+// line of kFftMaxLen takes 64 KB), so a later, smaller plan never lowers an
+// earlier one's limit.
+constexpr size_t kFftSmemMax = 96 * 1024 + 2 * sizeof(float2) * 8;
+
+template <typename K>
+cudaError_t allow_smem(K kernel, size_t bytes) {
+    if (bytes > kFftSmemMax) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFftSmemMax);
+}
+
+}  // namespace
+
+sfista_status fftconv_create(FftConv **out, const double *K, int p, int q, int cr, int cc, int m, int n, int bc) {
+    *out = nullptr;
+    if (p < 1 || q < 1 || p > m || q > n || cr < 0 || cr >= p || cc < 0 || cc >= q)
+        return fail(SFISTA_EINVAL, "FFT form: kernel larger than the image or centre outside it");
+    FftConv *f = new (std::nothrow) FftConv();
+    if (!f) return fail(SFISTA_ENOMEM, "FFT form: host allocation");
+    FftConvDev &d = f->d;
+    d.m = m;
+    d.n = n;
+    d.bc = bc;
+    d.offr = p - 1 - cr;
+    d.offc = q - 1 - cc;
+    d.ext_rows = m + p - 1;
+    d.ext_cols = n + q - 1;
+    const int N1 = smooth_len(d.ext_rows), N2 = smooth_len(d.ext_cols);
+    if (N1 <= 0 || N2 <= 0 || N1 > kFftMaxLen || N2 > kFftMaxLen) {
+        delete f;
+        return fail(SFISTA_ENOTSUP, "FFT form: image plus kernel exceeds the longest transform (" +
+                                        std::to_string(kFftMaxLen) + ")");
+    }
+    std::vector<double2> tw1, tw2;
+    if (!line_plan(N1, &d.l1, &tw1) || !line_plan(N2, &d.l2, &tw2)) {
+        delete f;
+        return fail(SFISTA_ENOTSUP, "FFT form: no radix plan");
+    }
+    d.H2 = N2 / 2 + 1;
+    const std::vector<int> pos1 = dif_positions(d.l1), pos2 = dif_positions(d.l2);
+    // Kernel spectrum of h[s1][s2] = K[s1' + p - 1][s2' + q - 1] at s = s' mod N,
+    // s' in [-(p-1), 0] x [-(q-1), 0]; scaled by 1 / (N1 N2) and stored with
+    // the row frequency at its DIF position: Kd[pos1[f1]][f2], f2 < H2.
+    std::vector<std::complex<double>> root1(N1), root2(N2);
+    for (int t = 0; t < N1; ++t) root1[t] = std::polar(1.0, -2.0 * M_PI * t / N1);
+    for (int t = 0; t < N2; ++t) root2[t] = std::polar(1.0, -2.0 * M_PI * t / N2);
+    const int H2 = d.H2;
+    std::vector<std::complex<double>> F2((size_t)p * H2);
+    for (int k = 0; k < p; ++k)
+        for (int f2 = 0; f2 < H2; ++f2) {
+            std::complex<double> acc = 0.0;
+            for (int l = 0; l < q; ++l) {
+                const long s2 = ((long)l - (q - 1) + N2) % N2;
+                acc += K[(size_t)k * q + l] * root2[(size_t)((f2 * s2) % N2)];
+            }
+            F2[(size_t)k * H2 + f2] = acc;
+        }
+    std::vector<float2> Kd((size_t)N1 * H2);
+    const double scale = 1.0 / ((double)N1 * N2);
+    std::vector<std::complex<double>> col(p);
+    for (int f1 = 0; f1 < N1; ++f1) {
+        for (int k = 0; k < p; ++k) col[k] = root1[(size_t)((f1 * (((long)k - (p - 1) + N1) % N1)) % N1)];
+        float2 *row = Kd.data() + (size_t)pos1[f1] * H2;
+        for (int f2 = 0; f2 < H2; ++f2) {
+            std::complex<double> acc = 0.0;
+            for (int k = 0; k < p; ++k) acc += F2[(size_t)k * H2 + f2] * col[k];
+            acc *= scale;
+            row[f2] = make_float2((float)acc.real(), (float)acc.imag());
+        }
+    }
+    auto to_f2 = [](const std::vector<double2> &v) {
+        std::vector<float2> o(v.size());
+        for (size_t i = 0; i < v.size(); ++i) o[i] = make_float2((float)v[i].x, (float)v[i].y);
+        return o;
+    };
+    cudaError_t e;
+    if ((e = upload_vec((float2 **)&d.tw1, to_f2(tw1))) || (e = upload_vec((float2 **)&d.tw2, to_f2(tw2))) ||
+        (e = upload_vec((int **)&d.pos2, pos2)) || (e = upload_vec((float2 **)&d.K, Kd)) ||
+        (e = cudaMalloc((void **)&d.S1, sizeof(float2) * (size_t)d.ext_rows * H2)) ||
+        (e = cudaMalloc((void **)&d.S2, sizeof(float2) * (size_t)m * H2))) {
+        fftconv_destroy(f);
+        return fail(SFISTA_ENOMEM, std::string("FFT form buffers: ") + cudaGetErrorString(e));
+    }
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    f->lpc_a = pick_lpc((d.ext_rows + 1) / 2, N2, sms);
+    f->lpc_b = pick_lpc(H2, N1, sms);
+    f->lpc_c = pick_lpc((m + 1) / 2, N2, sms);
+    const size_t sa = sizeof(float2) * f->lpc_a * (N2 + 1), sb = sizeof(float2) * f->lpc_b * (N1 + 1),
+                 sc = sizeof(float2) * f->lpc_c * (N2 + 1);
+    if ((e = allow_smem(fft_pass_a<false>, sa)) || (e = allow_smem(fft_pass_a<true>, sa)) ||
+        (e = allow_smem(fft_pass_b<false>, sb)) || (e = allow_smem(fft_pass_b<true>, sb)) ||
+        (e = allow_smem(fft_pass_c<false, EPI_STORE>, sc)) || (e = allow_smem(fft_pass_c<false, EPI_RESIDUAL>, sc)) ||
+        (e = allow_smem(fft_pass_c<true, EPI_STORE>, sc)) || (e = allow_smem(fft_pass_c<true, EPI_PROX>, sc))) {
+        fftconv_destroy(f);
+        return fail(SFISTA_ENOTSUP, std::string("FFT form shared memory: ") + cudaGetErrorString(e));
+    }
+    *out = f;
+    return SFISTA_OK;
+}
+
+void fftconv_destroy(FftConv *f) {
+    if (!f) return;
+    FftConvDev &d = f->d;
+    for (void *p : {(void *)d.tw1, (void *)d.tw2, (void *)d.pos2, (void *)d.K, (void *)d.S1, (void *)d.S2})
+        if (p) cudaFree(p);
+    delete f;
+}
+
+void fftconv_part(const FftConv *f, int part, bool adj, const float *In, EpiKind epi, float *Out, const ProxArgs &pa,
+                  cudaStream_t s) {
+    const FftConvDev &d = f->d;
+    if (part == 0) {
+        // Pass A reads the input rows (the operator's input), Pass B the spectra.
+        const int rows = adj ? d.m : d.ext_rows;
+        const int ga = (int)(((rows + 1) / 2 + f->lpc_a - 1) / f->lpc_a);
+        const size_t sa = sizeof(float2) * f->lpc_a * (d.l2.N + 1);
+        if (adj)
+            fft_pass_a<true><<<ga, kThreads, sa, s>>>(d, In, f->lpc_a);
+        else
+            fft_pass_a<false><<<ga, kThreads, sa, s>>>(d, In, f->lpc_a);
+        const int gb = (d.H2 + f->lpc_b - 1) / f->lpc_b;
+        const size_t sb = sizeof(float2) * f->lpc_b * (d.l1.N + 1);
+        if (adj)
+            fft_pass_b<true><<<gb, kThreads, sb, s>>>(d, f->lpc_b);
+        else
+            fft_pass_b<false><<<gb, kThreads, sb, s>>>(d, f->lpc_b);
+        return;
+    }
+    const int gc = ((d.m + 1) / 2 + f->lpc_c - 1) / f->lpc_c;
+    const size_t sc = sizeof(float2) * f->lpc_c * (d.l2.N + 1);
+    if (adj) {
+        if (epi == EPI_PROX)
+            fft_pass_c<true, EPI_PROX><<<gc, kThreads, sc, s>>>(d, Out, pa, f->lpc_c);
+        else
+            fft_pass_c<true, EPI_STORE><<<gc, kThreads, sc, s>>>(d, Out, pa, f->lpc_c);
+    } else {
+        if (epi == EPI_RESIDUAL)
+            fft_pass_c<false, EPI_RESIDUAL><<<gc, kThreads, sc, s>>>(d, Out, pa, f->lpc_c);
+        else
+            fft_pass_c<false, EPI_STORE><<<gc, kThreads, sc, s>>>(d, Out, pa, f->lpc_c);
+    }
+}
+
+void fftconv_apply(const FftConv *f, bool adj, const float *In, EpiKind epi, float *Out, const ProxArgs &pa,
+                   cudaStream_t s) {
+    fftconv_part(f, 0, adj, In, epi, Out, pa, s);
+    fftconv_part(f, 1, adj, In, epi, Out, pa, s);
+}
+
+size_t fftconv_bytes(const FftConv *f) {
+    const FftConvDev &d = f->d;
+    return sizeof(float2) * ((size_t)d.ext_rows * d.H2 + (size_t)d.m * d.H2 + (size_t)d.l1.N * d.H2);
+}
+
+}  // namespace sfista

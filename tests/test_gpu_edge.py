@@ -85,42 +85,3 @@ def test_image_larger_than_any_workload():
     X3 = s.solve_device(_cuda(X), 0.01, 3).cpu().numpy()
     assert oracle.rel_fro(X3, oracle.sfista(X.astype(np.float64), ka, 1.0, 0.01, 3)) <= 1e-5
     s.close()
-
-
-@pytest.mark.parametrize("prec,op,tol", [("fp32", "banded", 1e-5), ("bf16x3", "gemm_band", 1e-4)])
-def test_config4_full_batch_sampled(prec, op, tol):
-    """All 64 problems of the batched workload, tuned and grouped as the bench times them, 150
-    iterations; the smallest problem of each size class is checked against the oracle."""
-    probs = W.config4()
-    iters = probs[0].iters
-    d_bs, Ls, solvers = [], [], []
-    for pr in probs:
-        xt = _cuda(pr.x_true)
-        bxg = api.sfista_blur(pr.psf, xt, pr.bc).double().cpu().numpy()
-        b = (bxg + W.noise_scale(bxg, pr.noise, pr.noise_level)).astype(np.float32)
-        d_bs.append(_cuda(b))
-        s0 = api.Sfista(pr.psf, pr.x_true.shape, pr.bc, pr.r, prec="fp32", op="banded", lipschitz_tol=1e-7,
-                        lipschitz_maxit=200)
-        Ls.append(s0.info()["lipschitz"])
-        s0.close()
-        solvers.append(api.Sfista(pr.psf, pr.x_true.shape, pr.bc, pr.r, prec=prec, op=op, lipschitz=Ls[-1]))
-    for sv in solvers:
-        sv.tune(iters=2)
-    batch = api.Batch(solvers)
-    batch.tune(iters=2)
-    outs = batch.solve(d_bs, [pr.lam for pr in probs], iters)
-    sample = {}
-    for k, pr in enumerate(probs):
-        n = pr.x_true.shape[0]
-        if n <= 384 and n not in sample:
-            sample[n] = k
-    assert sample
-    for n, k in sample.items():
-        pr = probs[k]
-        cr, cc = pr.centre
-        ka = kron.kron_approx(pr.psf, cr, cc, n, n, pr.bc, pr.r)
-        Xo = oracle.sfista(d_bs[k].double().cpu().numpy(), ka, Ls[k], pr.lam, iters)
-        assert oracle.rel_fro(outs[k].cpu().numpy(), Xo) <= tol, (pr.name, n)
-    batch.close()
-    for sv in solvers:
-        sv.close()
