@@ -81,11 +81,23 @@ typedef enum {
                                         when every th x 32 output tile has its own resident block
                                         (th, a multiple of 4 from 16 to 32, picked per problem; m, n
                                         multiples of 4), else the two-pass form */
-    SFISTA_OP_BANDED_FUSED = 5 /* banded FP32 operator, one kernel per operator application: the
+    SFISTA_OP_BANDED_FUSED = 5, /* banded FP32 operator, one kernel per operator application: the
                                   row pass is kept in shared memory for the column pass (the
                                   automatic FP32 choice up to 1024^2 pixels and band width 48;
                                   SFISTA_OP_BANDED_PERSISTENT with the fused form when every
                                   tile also has its own resident block) */
+    SFISTA_OP_FFT = 6,         /* FP32 FFT form of the structured product (Sec. 2, fast
+                                  Toeplitz-plus-Hankel products by FFT): the extension of the
+                                  image that toep + hank encode is separable, so
+                                  sum_i B_i X A_i^T is one 2-D convolution of the extended
+                                  image with the rank-r kernel sum_i c_i d_i^T, done by
+                                  mixed-radix (2, 3, 4, 5) FFTs in shared memory; cost
+                                  O(mn log mn) per application, independent of r and of the
+                                  PSF width.  Requires m + psf_rows - 1 and
+                                  n + psf_cols - 1 <= 8192. */
+    SFISTA_OP_EXACT_FFT = 7    /* reported by sfista_info for contexts made by
+                                  sfista_setup_exact (the exact blur A by the same FFT
+                                  engine); not accepted by sfista_setup */
 } sfista_operator;
 
 typedef struct {
@@ -103,14 +115,25 @@ typedef struct {
                                Sec. 3.1 for that g; Sec. 1 and Sec. 5 name the l1 term
                                as future work).  Applied before the projection.         */
     int refine_every;       /* k_ref >= 0 (default 0: off).  Tensor-core forms: in every
-                               iteration k that is a multiple of k_ref, the residual
-                               R_k = sum_i B_i Y_k A_i^T - B of Alg. 2 (the inner sum of
-                               Step 1) is computed by the FP32 band kernels from the
-                               FP32 factors instead of by the low-precision GEMMs, then
-                               converted to the adjoint GEMMs' operand format.  The
-                               FP32 band forms compute every residual this way already,
-                               so it has no effect there.  Batches reject contexts that
-                               set it on a tensor-core form (SFISTA_ENOTSUP).           */
+                               iteration k that is a multiple of k_ref, all of Step 1 of
+                               Alg. 2 -- the residual R_k = sum_i B_i Y_k A_i^T - B and
+                               the adjoint product sum_j B_j^T R_k A_j -- is computed by
+                               the FP32 band kernels from the FP32 factors instead of by
+                               the low-precision GEMMs, with the shrink and momentum on
+                               the form's own state; Y_{k+1} is written in the GEMMs'
+                               operand format.  Such iterations add no product error, so
+                               the error against exact arithmetic falls with k_ref (1:
+                               the FP32 operator's).  The FP32 band forms compute every
+                               iteration this way already, so it has no effect there.
+                               Batches reject contexts that set it on a tensor-core form
+                               (SFISTA_ENOTSUP).                                         */
+    int tile_override;      /* 0 (default): the one-launch solver
+                               (SFISTA_OP_BANDED_PERSISTENT, fused form) picks its tile
+                               height th by a work model at setup, and sfista_tune by
+                               measurement; 16..32 (a multiple of 4): use th x 32 tiles
+                               (SFISTA_EINVAL otherwise; ignored where the one-launch
+                               fused solver is not used, and the two-pass persistent form
+                               is used instead if those tiles do not all fit).          */
 } sfista_opts;
 
 /* Fill *opts with the defaults listed above. */
@@ -146,6 +169,31 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols,
                            int center_row, int center_col,
                            int img_rows, int img_cols, sfista_bc bc, int r,
                            const sfista_opts *opts, sfista_ctx **out);
+
+/*
+ * sfista_setup_exact -- a context whose operator is the exact blur A of
+ * Eq. (1.1) (no Kronecker approximation), for vector FISTA on the
+ * unapproximated problem, Alg. 1: the comparison system of Sec. 4.  Every
+ * solve call (sfista_solve, sfista_solve_device, sfista_solve_state),
+ * sfista_apply (A x and A^T x) and sfista_objective then use A.  Alg. 1's
+ * Step 1 on vec(X) is the same element-wise update as Alg. 2's (Theorem 3
+ * with A in place of A_s), so the iteration, its double-float state and its
+ * epilogue are shared.  A is applied as a 2-D convolution of the zero or
+ * reflected extension of X with the PSF, by the FFT engine of SFISTA_OP_FFT,
+ * in FP32.  L = lambda_max(A^T A) by power iteration with that operator
+ * (FP64 sums) unless opts->lipschitz > 0; opts->prec must be SFISTA_FP32 and
+ * opts->op SFISTA_OP_AUTO (or SFISTA_OP_EXACT_FFT).  Arguments as sfista_setup
+ * without r.  sfista_info reports op = SFISTA_OP_EXACT_FFT, no singular
+ * values (approx_err 0) and band widths 0; sfista_get_profiles,
+ * sfista_get_factors, sfista_tune, the reverse-mode calls and batches return
+ * SFISTA_ENOTSUP for such contexts.
+ * Errors: as sfista_setup; ENOTSUP when m + psf_rows - 1 or n + psf_cols - 1
+ * exceeds 8192.
+ */
+sfista_status sfista_setup_exact(const double *psf, int psf_rows, int psf_cols,
+                                 int center_row, int center_col,
+                                 int img_rows, int img_cols, sfista_bc bc,
+                                 const sfista_opts *opts, sfista_ctx **out);
 
 /*
  * sfista_factorize -- the host half of sfista_setup alone (no device work):
@@ -317,6 +365,23 @@ sfista_status sfista_apply(sfista_ctx *ctx, const float *d_x, float *d_y,
 sfista_status sfista_info(const sfista_ctx *ctx, double *lipschitz,
                           double *sigma, double *approx_err, int *config);
 
+/*
+ * sfista_set_factors -- replace the context's Kronecker factors with given
+ * dense ones (the matrix model of Sec. 1 with any banded A_i, B_i in place of
+ * the factorisation's), e.g. so that the unrolled solve and its gradients
+ * follow factors that an optimiser has changed.
+ * A  host, r x n x n FP64 right factors A_i, or NULL to keep the current ones.
+ * B  host, r x m x m FP64 left factors B_i, or NULL to keep the current ones.
+ * Every entry outside the band of the context's factors (rows a: columns
+ * a + lo .. a + lo + w - 1, as sfista_info reports) must be zero.  L is kept
+ * (held fixed, as in the reverse mode).  Later solves, sfista_apply,
+ * sfista_objective and the reverse-mode calls use the new factors;
+ * sfista_get_factors returns them; sfista_get_profiles then returns ENOTSUP.
+ * Errors: ENOTSUP unless the context has a banded FP32 operator form;
+ * EINVAL for a nonzero entry outside the band.  Synchronous.
+ */
+sfista_status sfista_set_factors(sfista_ctx *ctx, const double *A, const double *B);
+
 /* Factor profiles: C (r x psf_rows) column profiles c_k of the left factors,
  * D (r x psf_cols) row profiles d_k of the right factors (host, FP64). */
 sfista_status sfista_get_profiles(const sfista_ctx *ctx, double *C, double *D);
@@ -368,7 +433,8 @@ typedef struct {
     int stage;         /* 0..3: one stage timed alone (see sfista_time_stages);
                           -1: whole iterations                                         */
     int chunk;         /* terms staged per block in that stage (two-pass banded form);
-                          0 where it does not apply                                    */
+                          for SFISTA_OP_BANDED_PERSISTENT entries the one-launch
+                          solver's tile height th; 0 where neither applies            */
     float ms;          /* mean time per stage (or per iteration), ms                  */
 } sfista_tune_entry;
 
@@ -381,11 +447,13 @@ typedef struct {
  *     terms staged per block (1 .. r, those that fit in shared memory); this
  *     sets shared memory per block and so the blocks resident per SM;
  *   - if the operator form was left to SFISTA_OP_AUTO: FP32 contexts also
- *     compare the tuned two-pass form with the fused form and, when every
- *     32 x 32 tile can have its own resident block, with the one-launch
+ *     compare the tuned two-pass form with the fused form, the FFT form
+ *     (SFISTA_OP_FFT, when its transforms fit) and, when every th x 32 tile
+ *     (th from 32 down to 16) can have its own resident block, the one-launch
  *     solver (SFISTA_OP_BANDED_PERSISTENT, timed per iteration over
- *     max(iters, 40) iterations of one launch); tensor-core contexts compare
- *     the band-limited and full (dense) K ranges.
+ *     max(iters, 40) iterations of one launch, for every tile height th);
+ *     tensor-core contexts compare the band-limited and full (dense) K
+ *     ranges.
  * An explicitly chosen form is kept (only its stages are tuned).  The chosen
  * configuration applies to later solves, sfista_apply and batches created
  * afterwards (sfista_info reports the form).

@@ -16,7 +16,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libsfista.so")
 OK, EINVAL, ENOMEM, ECUDA, ENOTSUP, ENUMERIC, ETIMEOUT = range(7)
 BC = {"zero": 0, "reflexive": 1, "reflective": 1, "periodic": 2}
 PREC = {"fp32": 0, "tf32": 1, "tf32x3": 2, "bf16": 3, "bf16x3": 4}
-OP = {"auto": 0, "banded": 1, "gemm_band": 2, "gemm_dense": 3, "banded_persistent": 4, "banded_fused": 5}
+OP = {"auto": 0, "banded": 1, "gemm_band": 2, "gemm_dense": 3, "banded_persistent": 4, "banded_fused": 5,
+      "fft": 6, "exact_fft": 7}
 PREC_NAME = {v: k for k, v in PREC.items()}
 OP_NAME = {v: k for k, v in OP.items()}
 
@@ -37,7 +38,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("op", ctypes.c_int), ("project_nonneg", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("lipschitz", ctypes.c_double),
                 ("lipschitz_tol", ctypes.c_double), ("lipschitz_maxit", ctypes.c_int),
-                ("device", ctypes.c_int), ("l1", ctypes.c_double), ("refine_every", ctypes.c_int)]
+                ("device", ctypes.c_int), ("l1", ctypes.c_double), ("refine_every", ctypes.c_int),
+                ("tile_override", ctypes.c_int)]
 
 
 def load(path=None):
@@ -53,6 +55,7 @@ def load(path=None):
     L.sfista_default_opts.argtypes = [ctypes.POINTER(Opts)]
     L.sfista_default_opts.restype = None
     L.sfista_setup.argtypes = [vp, i, i, i, i, i, i, i, i, ctypes.POINTER(Opts), ctypes.POINTER(vp)]
+    L.sfista_setup_exact.argtypes = [vp, i, i, i, i, i, i, i, ctypes.POINTER(Opts), ctypes.POINTER(vp)]
     L.sfista_factorize.argtypes = [vp, i, i, i, i, i, i, i, i, vp, vp, vp, D]
     L.sfista_factor_bands.argtypes = [vp, i, i, i, i, i, i, i, i, i, ctypes.POINTER(i), ctypes.POINTER(i), vp, vp]
     L.sfista_destroy.argtypes = [vp]
@@ -65,6 +68,7 @@ def load(path=None):
     L.sfista_info.argtypes = [vp, D, vp, D, vp]
     L.sfista_get_profiles.argtypes = [vp, vp, vp]
     L.sfista_get_factors.argtypes = [vp, vp, vp]
+    L.sfista_set_factors.argtypes = [vp, vp, vp]
     L.sfista_blur.argtypes = [vp, i, i, i, i, i, vp, i, i, vp, vp]
     L.sfista_time_stages.argtypes = [vp, vp, d, i, vp]
     L.sfista_objective.argtypes = [vp, vp, vp, d, ctypes.POINTER(ctypes.c_double), vp]
@@ -84,9 +88,9 @@ def load(path=None):
     L.sfista_strerror.restype = ctypes.c_char_p
     L.sfista_last_error.argtypes = []
     L.sfista_last_error.restype = ctypes.c_char_p
-    for name in ("sfista_setup", "sfista_factorize", "sfista_solve", "sfista_solve_device", "sfista_solve_state",
+    for name in ("sfista_setup", "sfista_setup_exact", "sfista_factorize", "sfista_solve", "sfista_solve_device", "sfista_solve_state",
                  "sfista_sync", "sfista_apply", "sfista_info", "sfista_get_profiles",
-                 "sfista_get_factors", "sfista_blur", "sfista_time_stages",
+                 "sfista_get_factors", "sfista_set_factors", "sfista_blur", "sfista_time_stages",
                  "sfista_apply_static", "sfista_batch_create", "sfista_batch_solve", "sfista_batch_sync",
                  "sfista_solve_batched", "sfista_unrolled_fwd", "sfista_unrolled_bwd", "sfista_selftest_wait_timeout"):
         getattr(L, name).restype = ctypes.c_int
@@ -135,6 +139,16 @@ def sfista_setup(psf, img_rows, img_cols, bc, r, center=(-1, -1), opts=None):
     _check(load().sfista_setup(P.ctypes.data, P.shape[0], P.shape[1], int(center[0]), int(center[1]),
                                int(img_rows), int(img_cols), int(bc), int(r), ctypes.byref(o),
                                ctypes.byref(h)))
+    return h.value
+
+
+def sfista_setup_exact(psf, img_rows, img_cols, bc, center=(-1, -1), opts=None):
+    """Context whose operator is the exact blur A (Alg. 1 on the unapproximated problem); see include/sfista.h."""
+    P = np.ascontiguousarray(psf, dtype=np.float64)
+    h = ctypes.c_void_p()
+    o = opts if opts is not None else default_opts()
+    _check(load().sfista_setup_exact(P.ctypes.data, P.shape[0], P.shape[1], int(center[0]), int(center[1]),
+                                     int(img_rows), int(img_cols), int(bc), ctypes.byref(o), ctypes.byref(h)))
     return h.value
 
 
@@ -222,6 +236,21 @@ def sfista_get_factors(ctx, r, m, n):
     B = np.zeros((r, m, m))
     _check(load().sfista_get_factors(ctypes.c_void_p(ctx), A.ctypes.data, B.ctypes.data))
     return A, B
+
+
+def _host_f64(t):
+    """Host FP64 contiguous copy of a numpy array or torch tensor (marshalling)."""
+    if hasattr(t, "detach"):
+        t = t.detach().double().cpu().numpy()
+    return np.ascontiguousarray(t, dtype=np.float64)
+
+
+def sfista_set_factors(ctx, A=None, B=None):
+    """Replace the dense factors (A: r x n x n, B: r x m x m; None keeps them); see include/sfista.h."""
+    Ah = _host_f64(A) if A is not None else None
+    Bh = _host_f64(B) if B is not None else None
+    _check(load().sfista_set_factors(ctypes.c_void_p(ctx), Ah.ctypes.data if Ah is not None else None,
+                                     Bh.ctypes.data if Bh is not None else None))
 
 
 def sfista_blur(psf, d_x, bc, center=(-1, -1), d_y=None, stream=None):
@@ -370,13 +399,17 @@ def _unrolled_function():
     class SfistaUnrolled(torch.autograd.Function):
         """X_iters of Alg. 2 as a differentiable function of (b, lambda, A, B).
 
-        A (r x n x n) and B (r x m x m) must hold the context's dense factors
-        (``Sfista.factors()``); they are inputs only so that autograd can return
-        dl/dA_i and dl/dB_i.  L is held fixed.
+        A (r x n x n) and B (r x m x m) are the dense factors the solve uses:
+        when given, they are loaded into the context first (sfista_set_factors;
+        they must be zero outside the band of the context's factors), so the
+        forward and the gradients dl/dA_i, dl/dB_i follow the tensors passed.
+        None keeps the context's current factors.  L is held fixed.
         """
 
         @staticmethod
         def forward(fctx, solver, b, lam, A, B, iters, ckpt_every):
+            if A is not None or B is not None:
+                sfista_set_factors(solver.ctx, A, B)
             m, n = b.shape
             nseg = (iters + ckpt_every - 1) // ckpt_every
             ck = torch.empty(2 * nseg, m, n, dtype=torch.float64, device=b.device)
@@ -388,6 +421,7 @@ def _unrolled_function():
             fctx.save_for_backward(b.contiguous(), ck, lam)
             fctx.want = (A.requires_grad if A is not None else False, B.requires_grad if B is not None else False)
             fctx.shapes = (None if A is None else A.shape, None if B is None else B.shape)
+            fctx.dtypes = (None if A is None else A.dtype, None if B is None else B.dtype)
             return x
 
         @staticmethod
@@ -399,6 +433,8 @@ def _unrolled_function():
             gl = sfista_unrolled_bwd(fctx.solver.ctx, b, fctx.lam, fctx.iters, fctx.ckpt, ck,
                                      gX.contiguous().float(), gb, gA, gB)
             glam = torch.tensor(gl, dtype=lam.dtype, device=lam.device).reshape(lam.shape)
+            gA = gA.to(fctx.dtypes[0]) if gA is not None else None
+            gB = gB.to(fctx.dtypes[1]) if gB is not None else None
             return None, gb, glam, gA, gB, None, None
 
     return SfistaUnrolled
@@ -424,7 +460,8 @@ class Sfista:
 
     def __init__(self, psf, shape, bc, r, center=(-1, -1), prec="fp32", op="auto", project=False,
                  use_graph=True, lipschitz=None, lipschitz_tol=1e-10, lipschitz_maxit=1000, device=-1, l1=0.0,
-                 refine_every=0):
+                 refine_every=0, tile_override=0, exact=False):
+        """exact=True: the exact blur A instead of the rank-r approximation (sfista_setup_exact; r unused)."""
         o = default_opts()
         o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
         o.op = OP[op] if isinstance(op, str) else int(op)
@@ -436,11 +473,16 @@ class Sfista:
         o.device = int(device)
         o.l1 = float(l1)
         o.refine_every = int(refine_every)
+        o.tile_override = int(tile_override)
         bcv = BC[bc] if isinstance(bc, str) else int(bc)
         self.shape = (int(shape[0]), int(shape[1]))
         self.psf_shape = np.asarray(psf).shape
         self.r = int(r)
-        self.ctx = sfista_setup(psf, self.shape[0], self.shape[1], bcv, r, center, o)
+        self.exact = bool(exact)
+        if self.exact:
+            self.ctx = sfista_setup_exact(psf, self.shape[0], self.shape[1], bcv, center, o)
+        else:
+            self.ctx = sfista_setup(psf, self.shape[0], self.shape[1], bcv, r, center, o)
 
     def close(self):
         if self.ctx:
@@ -454,14 +496,15 @@ class Sfista:
             pass
 
     def info(self):
-        return sfista_info(self.ctx, min(self.psf_shape))
+        return sfista_info(self.ctx, 0 if self.exact else min(self.psf_shape))
 
     def objective(self, d_b, d_x, lam):
         """Phi_s(X) for device tensors B and X."""
         return sfista_objective(self.ctx, d_b, d_x, lam)
 
     def tune(self, iters=10):
-        """Times the candidate configurations and keeps the fastest; returns the measurements."""
+        """Times the candidate configurations and keeps the fastest; returns the measurements
+        (for one-launch solver entries, ``chunk`` is the tile height)."""
         return sfista_tune(self.ctx, iters)
 
     def profiles(self):
@@ -469,6 +512,10 @@ class Sfista:
 
     def factors(self):
         return sfista_get_factors(self.ctx, self.r, *self.shape)
+
+    def set_factors(self, A=None, B=None):
+        """Use the given dense factors (zero outside the band) from now on; see include/sfista.h."""
+        sfista_set_factors(self.ctx, A, B)
 
     def solve(self, b, lam, iters):
         b = np.ascontiguousarray(b, dtype=np.float32)

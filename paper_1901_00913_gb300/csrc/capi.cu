@@ -36,7 +36,7 @@ __global__ void init_state_kernel(const float2 *X, const float2 *Xp, float2 *Y, 
     pa.split_kind = split_kind;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
          i += (size_t)gridDim.x * blockDim.x) {
-        const float2 y = dfp::add(X[i], dfp::mul(beta, dfp::sub(X[i], Xp[i])));
+        const float2 y = dfp::momentum(X[i], Xp[i], beta);
         Y[i] = y;
         store_operands(pa, i, y);
     }
@@ -92,6 +92,7 @@ void ctx_free(sfista_ctx *c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->gemm) gemm_destroy(c->gemm);
+    if (c->fft) fftconv_destroy(c->fft);
     void *ptrs[] = {c->dA, c->dAT, c->dB, c->dBT, c->fA, c->fAT, c->fB, c->fBT, c->Bd, c->Yop, c->Z,
                     c->R, c->tmp, c->Xb[0], c->Xb[1], c->Y, c->status, c->beta, c->bar,
                     c->Xf[0], c->Xf[1], c->Yf};
@@ -183,7 +184,16 @@ BandProb ctx_prob(const sfista_ctx *c) {
 // Stage `st` (0..3) of iteration k; see sfista_time_stages for the numbering.
 void enqueue_stage(sfista_ctx *c, int st, const ProxArgs &pa) {
     const HostSetup &h = c->hs;
-    if (fused_apply(c)) {
+    if (is_fft(c->op)) {
+        // Stage 0: Passes A and B of A_s Y (or A Y); 1: Pass C + residual;
+        // 2, 3: the same for the adjoint, Pass C with Step 1 + Step 3.
+        switch (st) {
+            case 0: fftconv_part(c->fft, 0, false, c->Yop, EPI_STORE, nullptr, pa, c->stream); break;
+            case 1: fftconv_part(c->fft, 1, false, nullptr, EPI_RESIDUAL, c->R, pa, c->stream); break;
+            case 2: fftconv_part(c->fft, 0, true, c->R, EPI_STORE, nullptr, pa, c->stream); break;
+            default: fftconv_part(c->fft, 1, true, nullptr, EPI_PROX, nullptr, pa, c->stream); break;
+        }
+    } else if (fused_apply(c)) {
         // Two launches per iteration: stage 0 = forward operator + residual,
         // stage 2 = adjoint + shrink / momentum (stages 1 and 3 are empty).
         if (st == 0)
@@ -212,9 +222,11 @@ void enqueue_stage(sfista_ctx *c, int st, const ProxArgs &pa) {
 void sfista::enqueue_iteration(sfista_ctx *c, int k, double lam) {
     ProxArgs pa = prox_args(c, k, lam);
     if (c->gemm && c->opts.refine_every > 0 && k % c->opts.refine_every == 0) {
-        // Refined residual: R_k = A_s Y_k - B by the FP32 band passes (rows,
-        // then columns with the residual epilogue) on the FP32 value of Y_k,
-        // then split into the operand of the adjoint GEMMs.
+        // A refinement iteration runs all of Step 1 in FP32 on the band
+        // kernels: R_k = A_s Y_k - B (rows, then columns with the residual
+        // epilogue) on the FP32 value of Y_k, then G = A_s^T R_k (rows, then
+        // columns with the Step 1 + Step 3 epilogue on the form's own state),
+        // writing Y_{k+1} in the split operand format of the next GEMMs.
         const HostSetup &h = c->hs;
         const float *y = c->Yf;   // the FP32 state holds Y_k itself
         if (!y) {                 // double-float state: its FP32 value
@@ -224,9 +236,12 @@ void sfista::enqueue_iteration(sfista_ctx *c, int k, double lam) {
         launch_band_rows<float>(y, c->m, c->n, c->fA, h.A.lo, h.A.w, c->r, c->Z, c->stream, c->chunk[0]);
         launch_band_cols<float>(c->Z, c->m, c->n, c->fB, h.B.lo, h.B.w, c->r, EPI_RESIDUAL, c->R, pa, c->stream,
                                 c->chunk[1]);
-        gemm_residual_operand(c->gemm, c->R, c->stream);
-        enqueue_stage(c, 2, pa);
-        enqueue_stage(c, 3, pa);
+        ProxArgs pr = pa;
+        gemm_state_operands(c->gemm, &pr.Yhi, &pr.Ylo, &pr.split_kind);
+        pr.Yop = nullptr;
+        launch_band_rows<float>(c->R, c->m, c->n, c->fAT, h.AT.lo, h.AT.w, c->r, c->Z, c->stream, c->chunk[2]);
+        launch_band_cols<float>(c->Z, c->m, c->n, c->fBT, h.BT.lo, h.BT.w, c->r, EPI_PROX, nullptr, pr, c->stream,
+                                c->chunk[3]);
         return;
     }
     for (int st = 0; st < 4; ++st) enqueue_stage(c, st, pa);
@@ -337,6 +352,106 @@ done:
     cudaFree(partial);
     cudaFree(dot);
     return st;
+}
+
+// The FFT engine of a sfista_setup context: kernel K = sum_i c_i d_i^T.
+sfista_status make_fft(sfista_ctx *c) {
+    const HostSetup &h = c->hs;
+    std::vector<double> K((size_t)h.p * h.q, 0.0);
+    for (int i = 0; i < h.r; ++i)
+        for (int k = 0; k < h.p; ++k)
+            for (int l = 0; l < h.q; ++l) K[(size_t)k * h.q + l] += h.C[(size_t)i * h.p + k] * h.D[(size_t)i * h.q + l];
+    return fftconv_create(&c->fft, K.data(), h.p, h.q, h.cr, h.cc, c->m, c->n, h.bc);
+}
+
+// lambda_max(Op^T Op) by power iteration with the context's FFT operator
+// (FP32 applications, FP64 iterate and sums).  The FP32 operator leaves the
+// Rayleigh quotient about 1e-7 noisy, so the stopping tolerance is at least
+// 2e-7.
+sfista_status power_lipschitz_fft(sfista_ctx *c, double tol, int maxit, double *L_out) {
+    TraceRange trace_("sfista lipschitz (FFT operator)");
+    tol = std::max(tol, 2e-7);
+    size_t N = c->N;
+    double *v = nullptr, *w = nullptr, *partial = nullptr, *dot = nullptr;
+    const int nblk = 256;
+    sfista_status st = SFISTA_OK;
+    double hdot[2] = {0, 0}, mu = 0, prev = 0;
+    ProxArgs pa{};
+    cudaError_t e = cudaSuccess;
+    if ((e = cudaMalloc((void **)&v, N * 8)) || (e = cudaMalloc((void **)&w, N * 8)) ||
+        (e = cudaMalloc((void **)&partial, nblk * 2 * 8)) || (e = cudaMalloc((void **)&dot, 2 * 8))) {
+        st = fail(SFISTA_ENOMEM, std::string("power iteration buffers: ") + cudaGetErrorString(e));
+        goto done;
+    }
+    launch_seed_image(v, N, c->stream);
+    launch_dots(v, v, N, partial, nblk, dot, c->stream);
+    launch_scale(v, N, dot, c->stream);
+    for (int it = 1; it <= maxit; ++it) {
+        launch_f64_to_f32(v, c->Yop, N, c->stream);
+        fftconv_apply(c->fft, false, c->Yop, EPI_STORE, c->tmp, pa, c->stream);
+        fftconv_apply(c->fft, true, c->tmp, EPI_STORE, c->R, pa, c->stream);
+        launch_f32_to_f64(c->R, w, N, c->stream);
+        launch_dots(v, w, N, partial, nblk, dot, c->stream);
+        launch_scale(w, N, dot, c->stream);
+        std::swap(v, w);
+        if ((e = cudaMemcpyAsync(hdot, dot, 16, cudaMemcpyDeviceToHost, c->stream)) ||
+            (e = cudaStreamSynchronize(c->stream))) {
+            st = fail(SFISTA_ECUDA, std::string("power iteration: ") + cudaGetErrorString(e));
+            goto done;
+        }
+        mu = hdot[0];
+        if (!isfinite(mu) || !(hdot[1] > 0)) {
+            st = fail(SFISTA_ENUMERIC, "power iteration produced a non-finite or zero vector");
+            goto done;
+        }
+        if (it > 1 && fabs(mu - prev) <= tol * fabs(mu)) break;
+        prev = mu;
+    }
+    *L_out = mu;
+done:
+    cudaFree(v);
+    cudaFree(w);
+    cudaFree(partial);
+    cudaFree(dot);
+    return st;
+}
+
+// Band storage (geometry of `like`: lo, w, len, r) of dense factors F
+// (r x len x len, row-major); transpose = true stores F_i^T.  false if F has
+// a nonzero entry outside that band.
+bool band_from_dense(const double *F, const Band &like, bool transpose, Band *out) {
+    const int r = like.r, len = like.len, lo = like.lo, w = like.w;
+    *out = like;
+    std::fill(out->band.begin(), out->band.end(), 0.0);
+    for (int i = 0; i < r; ++i)
+        for (int row = 0; row < len; ++row)
+            for (int col = 0; col < len; ++col) {
+                // entry (row, col) of the stored matrix G = F_i or F_i^T
+                const double v = transpose ? F[((size_t)i * len + col) * len + row] : F[((size_t)i * len + row) * len + col];
+                const int k = col - row - lo;
+                if (k >= 0 && k < w)
+                    out->band[((size_t)i * w + k) * len + row] = v;
+                else if (v != 0.0)
+                    return false;
+            }
+    return true;
+}
+
+// Rewrites a context's device band tables (FP64, FP32 + its Toeplitz row)
+// from host band storage of unchanged geometry.
+cudaError_t store_band(sfista_ctx *c, const Band &b, double *d64, float *d32, int2 *interior) {
+    cudaError_t e = cudaMemcpyAsync(d64, b.band.data(), sizeof(double) * b.band.size(), cudaMemcpyHostToDevice,
+                                    c->stream);
+    if (e) return e;
+    std::vector<float> f(b.band.begin(), b.band.end());
+    const int len = b.len, ref = len / 2, cnt = b.r * b.w;
+    int i0 = 0, i1 = 0;
+    band_interior(f.data(), len, cnt, &i0, &i1);
+    *interior = make_int2(i0, i1);
+    for (int t = 0; t < cnt; ++t) f.push_back(f[(size_t)t * len + ref]);
+    e = cudaMemcpyAsync(d32, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e) return e;
+    return cudaStreamSynchronize(c->stream);
 }
 
 sfista_status check_ctx(const sfista_ctx *c) {
@@ -535,6 +650,7 @@ void sfista_default_opts(sfista_opts *o) {
     o->device = -1;
     o->l1 = 0.0;
     o->refine_every = 0;
+    o->tile_override = 0;
 }
 
 sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int center_row,
@@ -547,10 +663,12 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int ce
     sfista_default_opts(&o);
     if (opts) o = *opts;
     if (o.prec < SFISTA_FP32 || o.prec > SFISTA_BF16X3) return fail(SFISTA_EINVAL, "unknown precision");
-    if (o.op < SFISTA_OP_AUTO || o.op > SFISTA_OP_BANDED_FUSED) return fail(SFISTA_EINVAL, "unknown operator form");
+    if (o.op < SFISTA_OP_AUTO || o.op > SFISTA_OP_FFT) return fail(SFISTA_EINVAL, "unknown operator form");
     if (!(o.lipschitz <= 0.0 || isfinite(o.lipschitz))) return fail(SFISTA_EINVAL, "lipschitz must be finite");
     if (!(o.l1 >= 0.0) || !isfinite(o.l1)) return fail(SFISTA_EINVAL, "l1 must be finite and >= 0");
     if (o.refine_every < 0) return fail(SFISTA_EINVAL, "refine_every must be >= 0");
+    if (o.tile_override != 0 && (o.tile_override < 16 || o.tile_override > 32 || o.tile_override % 4))
+        return fail(SFISTA_EINVAL, "tile_override must be 0 or a multiple of 4 from 16 to 32");
     if (center_row == -1 && psf_rows > 0) center_row = (psf_rows - 1) / 2;
     if (center_col == -1 && psf_cols > 0) center_col = (psf_cols - 1) / 2;
     sfista_ctx *c = new (std::nothrow) sfista_ctx();
@@ -579,9 +697,9 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int ce
         const bool small = (size_t)img_rows * img_cols <= ((size_t)1 << 20) && wl <= 48;
         c->op = (c->prec == SFISTA_FP32) ? (small ? SFISTA_OP_BANDED_FUSED : SFISTA_OP_BANDED) : SFISTA_OP_GEMM_BAND;
     }
-    if (is_banded(c->op) && c->prec != SFISTA_FP32) {
+    if ((is_banded(c->op) || is_fft(c->op)) && c->prec != SFISTA_FP32) {
         delete c;
-        return fail(SFISTA_ENOTSUP, "the banded operator form runs in FP32 only");
+        return fail(SFISTA_ENOTSUP, "the banded and FFT operator forms run in FP32 only");
     }
     if (o.device < 0) {
         if (cudaGetDevice(&c->dev) != cudaSuccess) {
@@ -642,12 +760,17 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int ce
         int grid = 0;
         size_t smem = 0;
         int th = 32;
-        if (band_solve_fused_config(ctx_prob(c), c->dev, &grid, &smem, &th)) c->op = SFISTA_OP_BANDED_PERSISTENT;
+        if (o.tile_override ? band_solve_fused_config_th(ctx_prob(c), c->dev, o.tile_override, &grid, &smem)
+                            : band_solve_fused_config(ctx_prob(c), c->dev, &grid, &smem, &th))
+            c->op = SFISTA_OP_BANDED_PERSISTENT;
     }
     if (c->op == SFISTA_OP_BANDED_PERSISTENT) {
         if ((e = cudaMalloc((void **)&c->bar, kBarrierBytes)) || (e = cudaMemset(c->bar, 0, kBarrierBytes)))
             return bail(fail(SFISTA_ENOMEM, std::string("barrier words: ") + cudaGetErrorString(e)));
-        c->pfused = band_solve_fused_config(ctx_prob(c), c->dev, &c->pgrid, &c->psmem, &c->pth);
+        c->pfused = o.tile_override
+                        ? band_solve_fused_config_th(ctx_prob(c), c->dev, o.tile_override, &c->pgrid, &c->psmem)
+                        : band_solve_fused_config(ctx_prob(c), c->dev, &c->pgrid, &c->psmem, &c->pth);
+        if (c->pfused && o.tile_override) c->pth = o.tile_override;
         // Single operator applications (sfista_apply, the objective, reverse
         // mode) then take the fused operator kernel as well.
         if (c->pfused && !band_op_fused_prepare(c->r, std::max(h.A.w, h.AT.w), std::max(h.B.w, h.BT.w)))
@@ -657,6 +780,10 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int ce
                                    &c->pcols_chunk);
             if (st) return bail(st);
         }
+    }
+    if (c->op == SFISTA_OP_FFT) {
+        st = make_fft(c);
+        if (st) return bail(st);
     }
     if (c->op == SFISTA_OP_GEMM_BAND || c->op == SFISTA_OP_GEMM_DENSE) {
         st = gemm_create(&c->gemm, h, c->prec, c->op == SFISTA_OP_GEMM_DENSE, c->status, c->stream);
@@ -682,7 +809,126 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int ce
     return SFISTA_OK;
 }
 
+sfista_status sfista_setup_exact(const double *psf, int psf_rows, int psf_cols, int center_row, int center_col,
+                                 int img_rows, int img_cols, sfista_bc bc, const sfista_opts *opts, sfista_ctx **out) {
+    TraceRange trace_("sfista_setup_exact");
+    if (!out) return fail(SFISTA_EINVAL, "out is NULL");
+    *out = nullptr;
+    sfista_opts o;
+    sfista_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.prec != SFISTA_FP32) return fail(SFISTA_ENOTSUP, "the exact blur runs in FP32 only");
+    if (o.op != SFISTA_OP_AUTO && o.op != SFISTA_OP_EXACT_FFT)
+        return fail(SFISTA_EINVAL, "the exact blur has one operator form (SFISTA_OP_EXACT_FFT)");
+    if (!(o.lipschitz <= 0.0 || isfinite(o.lipschitz))) return fail(SFISTA_EINVAL, "lipschitz must be finite");
+    if (!(o.l1 >= 0.0) || !isfinite(o.l1)) return fail(SFISTA_EINVAL, "l1 must be finite and >= 0");
+    if (!psf) return fail(SFISTA_EINVAL, "psf is NULL");
+    if (psf_rows < 1 || psf_cols < 1 || img_rows < 1 || img_cols < 1 || psf_rows > img_rows || psf_cols > img_cols)
+        return fail(SFISTA_EINVAL, "bad sizes (the PSF must fit in the image)");
+    if (bc == SFISTA_BC_PERIODIC) return fail(SFISTA_ENOTSUP, "periodic boundary is not supported");
+    if (bc != SFISTA_BC_ZERO && bc != SFISTA_BC_REFLEXIVE) return fail(SFISTA_EINVAL, "unknown boundary");
+    if (center_row == -1) center_row = (psf_rows - 1) / 2;
+    if (center_col == -1) center_col = (psf_cols - 1) / 2;
+    if (center_row < 0 || center_row >= psf_rows || center_col < 0 || center_col >= psf_cols)
+        return fail(SFISTA_EINVAL, "PSF centre outside the PSF");
+    for (size_t i = 0; i < (size_t)psf_rows * psf_cols; ++i)
+        if (!isfinite(psf[i])) return fail(SFISTA_EINVAL, "non-finite PSF entry");
+    sfista_ctx *c = new (std::nothrow) sfista_ctx();
+    if (!c) return fail(SFISTA_ENOMEM, "context allocation failed");
+    c->opts = o;
+    c->opts.refine_every = 0;
+    c->exact = 1;
+    c->m = img_rows;
+    c->n = img_cols;
+    c->r = 0;
+    c->N = (size_t)img_rows * img_cols;
+    c->prec = SFISTA_FP32;
+    c->op = SFISTA_OP_EXACT_FFT;
+    c->hs.m = img_rows;
+    c->hs.n = img_cols;
+    c->hs.p = psf_rows;
+    c->hs.q = psf_cols;
+    c->hs.cr = center_row;
+    c->hs.cc = center_col;
+    c->hs.bc = bc;
+    if (o.device < 0) {
+        if (cudaGetDevice(&c->dev) != cudaSuccess) {
+            delete c;
+            return fail(SFISTA_ECUDA, "no CUDA device");
+        }
+    } else {
+        c->dev = o.device;
+    }
+    DeviceGuard g(c->dev);
+    auto bail = [&](sfista_status s) {
+        ctx_free(c);
+        return s;
+    };
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) ||
+        (e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming)) ||
+        (e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming)))
+        return bail(fail(SFISTA_ECUDA, std::string("stream/event: ") + cudaGetErrorString(e)));
+    const size_t N = c->N;
+    if ((e = cudaMalloc((void **)&c->Bd, N * 4)) || (e = cudaMalloc((void **)&c->Yop, N * 4)) ||
+        (e = cudaMalloc((void **)&c->R, N * 4)) || (e = cudaMalloc((void **)&c->tmp, N * 4)) ||
+        (e = cudaMalloc((void **)&c->Xb[0], N * 8)) || (e = cudaMalloc((void **)&c->Xb[1], N * 8)) ||
+        (e = cudaMalloc((void **)&c->Y, N * 8)) || (e = cudaMalloc((void **)&c->status, 16)))
+        return bail(fail(SFISTA_ENOMEM, std::string("state buffers: ") + cudaGetErrorString(e)));
+    if ((e = cudaMemset(c->status, 0, 16))) return bail(fail(SFISTA_ECUDA, cudaGetErrorString(e)));
+    sfista_status st = fftconv_create(&c->fft, psf, psf_rows, psf_cols, center_row, center_col, img_rows, img_cols, bc);
+    if (st) return bail(st);
+    if (o.lipschitz > 0.0) {
+        c->L = o.lipschitz;
+    } else {
+        const double tol = o.lipschitz_tol > 0 ? o.lipschitz_tol : 1e-10;
+        const int maxit = o.lipschitz_maxit > 0 ? o.lipschitz_maxit : 1000;
+        st = power_lipschitz_fft(c, tol, maxit, &c->L);
+        if (st) return bail(st);
+    }
+    if ((e = cudaStreamSynchronize(c->stream))) return bail(fail(SFISTA_ECUDA, cudaGetErrorString(e)));
+    *out = c;
+    return SFISTA_OK;
+}
+
 void sfista_destroy(sfista_ctx *ctx) { ctx_free(ctx); }
+
+sfista_status sfista_set_factors(sfista_ctx *c, const double *A, const double *B) {
+    sfista_status st = check_ctx(c);
+    if (st) return st;
+    if (!is_banded(c->op) || c->exact)
+        return fail(SFISTA_ENOTSUP, "factors can be replaced in the banded FP32 forms only");
+    DeviceGuard g(c->dev);
+    HostSetup &h = c->hs;
+    Band nA, nAT, nB, nBT;
+    if (A && !(band_from_dense(A, h.A, false, &nA) && band_from_dense(A, h.AT, true, &nAT)))
+        return fail(SFISTA_EINVAL, "A has a nonzero entry outside the band of the context's right factors");
+    if (B && !(band_from_dense(B, h.B, false, &nB) && band_from_dense(B, h.BT, true, &nBT)))
+        return fail(SFISTA_EINVAL, "B has a nonzero entry outside the band of the context's left factors");
+    SF_CUDA(cudaStreamSynchronize(c->stream));
+    cudaError_t e = cudaSuccess;
+    if (A) {
+        h.A = nA;
+        h.AT = nAT;
+        if ((e = store_band(c, h.A, c->dA, c->fA, &c->interior[0])) ||
+            (e = store_band(c, h.AT, c->dAT, c->fAT, &c->interior[1])))
+            return fail(SFISTA_ECUDA, std::string("factor upload: ") + cudaGetErrorString(e));
+    }
+    if (B) {
+        h.B = nB;
+        h.BT = nBT;
+        if ((e = store_band(c, h.B, c->dB, c->fB, &c->interior[2])) ||
+            (e = store_band(c, h.BT, c->dBT, c->fBT, &c->interior[3])))
+            return fail(SFISTA_ECUDA, std::string("factor upload: ") + cudaGetErrorString(e));
+    }
+    if (A || B) c->custom_factors = 1;
+    if (c->gexec) {   // the captured loop holds the old interior ranges
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+        c->g_k0 = c->g_iters = -1;
+    }
+    return SFISTA_OK;
+}
 
 sfista_status sfista_factorize(const double *psf, int p, int q, int cr, int cc, int m, int n, sfista_bc bc, int r,
                                double *sigma, double *C, double *D, double *approx_err) {
@@ -783,7 +1029,9 @@ sfista_status sfista_apply(sfista_ctx *c, const float *d_x, float *d_y, int tran
     SF_CUDA(cudaStreamWaitEvent(c->stream, c->ev_in, 0));
     const HostSetup &h = c->hs;
     ProxArgs pa{};
-    if (fused_apply(c)) {
+    if (is_fft(c->op)) {
+        fftconv_apply(c->fft, transpose != 0, d_x, EPI_STORE, d_y, pa, c->stream);
+    } else if (fused_apply(c)) {
         const Band &F = transpose ? h.AT : h.A;
         const Band &G = transpose ? h.BT : h.B;
         launch_band_op_fused(d_x, c->m, c->n, c->r, transpose ? c->fAT : c->fA, F.lo, F.w, transpose ? c->fBT : c->fB,
@@ -816,7 +1064,9 @@ sfista_status sfista_objective(sfista_ctx *c, const float *d_b, const float *d_x
     // A_s x into the scratch image, then the two sums of squares in FP64.
     const HostSetup &h = c->hs;
     ProxArgs pa{};
-    if (fused_apply(c)) {
+    if (is_fft(c->op)) {
+        fftconv_apply(c->fft, false, d_x, EPI_STORE, c->tmp, pa, c->stream);
+    } else if (fused_apply(c)) {
         launch_band_op_fused(d_x, c->m, c->n, c->r, c->fA, h.A.lo, h.A.w, c->fB, h.B.lo, h.B.w, EPI_STORE, c->tmp, pa,
                              interior_fwd(c), c->stream);
     } else if (is_banded(c->op)) {
@@ -864,6 +1114,8 @@ sfista_status sfista_info(const sfista_ctx *c, double *lipschitz, double *sigma,
 sfista_status sfista_get_profiles(const sfista_ctx *c, double *C, double *D) {
     sfista_status st = check_ctx(c);
     if (st) return st;
+    if (c->exact) return fail(SFISTA_ENOTSUP, "the exact-blur context has no Kronecker factors");
+    if (c->custom_factors) return fail(SFISTA_ENOTSUP, "the factors were replaced: no profiles describe them");
     if (C) std::copy(c->hs.C.begin(), c->hs.C.end(), C);
     if (D) std::copy(c->hs.D.begin(), c->hs.D.end(), D);
     return SFISTA_OK;
@@ -872,6 +1124,7 @@ sfista_status sfista_get_profiles(const sfista_ctx *c, double *C, double *D) {
 sfista_status sfista_get_factors(const sfista_ctx *c, double *A, double *B) {
     sfista_status st = check_ctx(c);
     if (st) return st;
+    if (c->exact) return fail(SFISTA_ENOTSUP, "the exact-blur context has no Kronecker factors");
     auto dense = [](const Band &b, double *out) {
         size_t len = b.len;
         std::fill(out, out + (size_t)b.r * len * len, 0.0);
@@ -921,8 +1174,10 @@ sfista_status sfista_batch_create(sfista_ctx *const *ctxs, int nprob, sfista_bat
     if (!out) return fail(SFISTA_EINVAL, "out is NULL");
     *out = nullptr;
     if (!ctxs || nprob < 1) return fail(SFISTA_EINVAL, "no problems");
-    for (int p = 0; p < nprob; ++p)
+    for (int p = 0; p < nprob; ++p) {
         if (!ctxs[p]) return fail(SFISTA_EINVAL, "a context is NULL");
+        if (is_fft(ctxs[p]->op)) return fail(SFISTA_ENOTSUP, "batches take banded or tensor-core contexts only");
+    }
     const bool gemm = ctxs[0]->op == SFISTA_OP_GEMM_BAND || ctxs[0]->op == SFISTA_OP_GEMM_DENSE;
     for (int p = 0; p < nprob; ++p) {
         const bool gp = ctxs[p]->op == SFISTA_OP_GEMM_BAND || ctxs[p]->op == SFISTA_OP_GEMM_DENSE;
@@ -1334,6 +1589,7 @@ sfista_status sfista_tune(sfista_ctx *c, int iters, sfista_tune_entry *entries, 
     TraceRange trace_("sfista_tune");
     sfista_status st = check_ctx(c);
     if (st) return st;
+    if (c->exact) return fail(SFISTA_ENOTSUP, "the exact-blur context has a single operator form");
     if (n_entries) *n_entries = 0;
     if (iters < 1 || max_entries < 0) return fail(SFISTA_EINVAL, "iters must be >= 1 and max_entries >= 0");
     DeviceGuard g(c->dev);
@@ -1376,6 +1632,7 @@ sfista_status sfista_tune(sfista_ctx *c, int iters, sfista_tune_entry *entries, 
             if (st) return st;
             log(SFISTA_OP_BANDED, -1, 0, t_two);
             c->op = SFISTA_OP_BANDED;
+            float t_best = t_two;
             if (auto_op && band_op_fused_prepare(c->r, std::max(h.A.w, h.AT.w), std::max(h.B.w, h.BT.w))) {
                 float t_fused = 0.f;
                 c->op = SFISTA_OP_BANDED_FUSED;
@@ -1383,15 +1640,22 @@ sfista_status sfista_tune(sfista_ctx *c, int iters, sfista_tune_entry *entries, 
                 if (st) return st;
                 log(SFISTA_OP_BANDED_FUSED, -1, 0, t_fused);
                 c->op = t_fused < t_two ? SFISTA_OP_BANDED_FUSED : SFISTA_OP_BANDED;
-                // The one-launch fused solver, when every tile has a resident block.
-                int grid = 0, th = 32;
-                size_t smem = 0;
-                if (band_solve_fused_config(ctx_prob(c), c->dev, &grid, &smem, &th)) {
+                t_best = std::min(t_fused, t_two);
+                // The one-launch fused solver, when every tile has a resident
+                // block: every tile height th from 32 down to 16 that fits is
+                // timed (entries report th in `chunk`), or only the requested one.
+                const int best_op = c->op;
+                int best_th = 0, best_grid = 0;
+                size_t best_smem = 0;
+                for (int th = 32; th >= 16; th -= 4) {
+                    if (c->opts.tile_override && th != c->opts.tile_override) continue;
+                    int grid = 0;
+                    size_t smem = 0;
+                    if (!band_solve_fused_config_th(ctx_prob(c), c->dev, th, &grid, &smem)) continue;
                     if (!c->bar) {
                         SF_CUDA(cudaMalloc((void **)&c->bar, kBarrierBytes));
                         SF_CUDA(cudaMemset(c->bar, 0, kBarrierBytes));
                     }
-                    const int best_op = c->op;
                     c->op = SFISTA_OP_BANDED_PERSISTENT;
                     c->pfused = 1;   // band_op_fused_prepare succeeded above
                     c->pgrid = grid;
@@ -1400,8 +1664,40 @@ sfista_status sfista_tune(sfista_ctx *c, int iters, sfista_tune_entry *entries, 
                     float t_one = 0.f;
                     st = time_persistent(c, std::max(iters, 40), &t_one);
                     if (st) return st;
-                    log(SFISTA_OP_BANDED_PERSISTENT, -1, 0, t_one);
-                    if (!(t_one < std::min(t_fused, t_two))) c->op = best_op;
+                    log(SFISTA_OP_BANDED_PERSISTENT, -1, th, t_one);
+                    if (t_one < t_best) {
+                        t_best = t_one;
+                        best_th = th;
+                        best_grid = grid;
+                        best_smem = smem;
+                    }
+                }
+                if (best_th) {
+                    c->op = SFISTA_OP_BANDED_PERSISTENT;
+                    c->pfused = 1;
+                    c->pgrid = best_grid;
+                    c->psmem = best_smem;
+                    c->pth = best_th;
+                } else {
+                    c->op = best_op;
+                }
+            }
+            if (auto_op) {
+                // The FFT form: its cost does not grow with the PSF width or r,
+                // so it wins for wide PSFs.  Skipped when its transforms do not fit.
+                const int best_op = c->op;
+                bool have = c->fft != nullptr;
+                if (!have) {
+                    have = make_fft(c) == SFISTA_OK;
+                    set_error("");
+                }
+                if (have) {
+                    float t_fft = 0.f;
+                    c->op = SFISTA_OP_FFT;
+                    st = time_stage_range(c, 0, 3, iters, &t_fft);
+                    if (st) return st;
+                    log(SFISTA_OP_FFT, -1, 0, t_fft);
+                    if (!(t_fft < t_best)) c->op = best_op;
                 }
             }
         } else {

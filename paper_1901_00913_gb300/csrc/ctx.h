@@ -4,6 +4,7 @@
 
 #include <vector>
 
+#include "fftconv.h"
 #include "gemm.h"
 #include "internal.h"
 
@@ -55,6 +56,11 @@ struct sfista_ctx {
     std::vector<double> beta_host;
     // Tensor-core path (operand panels, intermediates, tensor maps).
     GemmPath *gemm = nullptr;
+    // FFT form (SFISTA_OP_FFT, or the exact blur of a sfista_setup_exact
+    // context: exact = 1, no band storage).
+    sfista::FftConv *fft = nullptr;
+    int exact = 0;
+    int custom_factors = 0;   // sfista_set_factors replaced the setup's factors
     // Terms per block of the two-pass banded stages 0..3 (0: default rule);
     // set by the autotuner.
     int chunk[4] = {0, 0, 0, 0};

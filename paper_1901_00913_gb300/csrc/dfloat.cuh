@@ -42,6 +42,16 @@ __device__ __forceinline__ float2 mul_f(float2 a, float b) {
     e = __fmaf_rn(a.y, b, e);
     return fast_two_sum(p, e);
 }
+// Renormalises a pair: Fast-TwoSum's |a| >= |b| precondition can fail in
+// add() under cancellation (values near zero), leaving |lo| slightly above
+// ulp(hi)/2.  Such a pair converts to FP64 and back as a different pair of
+// the same value, so the state is renormalised where it is stored, and a
+// solve resumed from FP64 continues bit for bit.
+__device__ __forceinline__ float2 normalize(float2 a) { return fast_two_sum(a.x, a.y); }
+// Y = X + beta (X - Xp): Step 3 of Alg. 2, renormalised.
+__device__ __forceinline__ float2 momentum(float2 x, float2 xp, float2 beta) {
+    return normalize(add(x, mul(beta, sub(x, xp))));
+}
 // Conversions (FP64 only at the boundaries of a solve).
 __host__ __device__ __forceinline__ float2 from_double(double v) {
     const float hi = (float)v;

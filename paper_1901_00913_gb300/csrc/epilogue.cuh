@@ -34,9 +34,10 @@ static __device__ __forceinline__ float2 prox_step(const ProxArgs &pa, float2 y,
     float2 x = dfp::sub(dfp::mul(pa.shrink, y), dfp::mul_f(pa.inv_den, g));
     if (pa.tau.x > 0.0f) x = soft_threshold(x, pa.tau);
     if (pa.project && x.x < 0.0f) x = make_float2(0.0f, 0.0f);
+    x = dfp::normalize(x);
     *bad |= !isfinite(x.x);
     *xout = x;
-    return dfp::add(x, dfp::mul(beta, dfp::sub(x, xp)));
+    return dfp::momentum(x, xp, beta);
 }
 
 static __device__ __forceinline__ void store_operands(const ProxArgs &pa, size_t idx, float2 yn) {
@@ -96,11 +97,38 @@ static __device__ __forceinline__ void prox_apply_n(const ProxArgs &pa, const si
     if (bad) atomicOr(pa.status, DEV_NONFINITE);
 }
 
+static __device__ __forceinline__ float prox_step32(const ProxArgs &pa, float y, float xp, float g, float beta,
+                                                    float *xout, bool *bad);
+static __device__ __forceinline__ void store_operands32(const ProxArgs &pa, size_t idx, float yn);
+
 // N pixels at once: every state load is issued before any arithmetic or
-// store, so a thread keeps 2N loads in flight.
+// store, so a thread keeps 2N loads in flight.  With an FP32 state (pa.Y32:
+// the tensor-core forms, when an FP32 iteration of residual refinement runs
+// its adjoint on the band kernels) the step is prox_step32 on that state.
 template <int N>
 static __device__ __forceinline__ void prox_momentum_n(const ProxArgs &pa, const size_t *idx, const float *g,
                                                        const bool *valid) {
+    if (pa.Y32) {
+        float y[N], xp[N];
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            y[q] = valid[q] ? __ldcg(pa.Y32 + idx[q]) : 0.f;
+            xp[q] = valid[q] ? __ldcg(pa.Xin32 + idx[q]) : 0.f;
+        }
+        const float beta = pa.beta[pa.k - 1].x;
+        bool bad = false;
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            if (!valid[q]) continue;
+            float x;
+            const float yn = prox_step32(pa, y[q], xp[q], g[q], beta, &x, &bad);
+            pa.Xout32[idx[q]] = x;
+            pa.Y32[idx[q]] = yn;
+            store_operands32(pa, idx[q], yn);
+        }
+        if (bad) atomicOr(pa.status, DEV_NONFINITE);
+        return;
+    }
     float2 y[N], xp[N];
     prox_load_n<N>(pa, idx, valid, y, xp);
     prox_apply_n<N>(pa, idx, g, valid, y, xp, pa.beta[pa.k - 1]);
@@ -159,10 +187,15 @@ static __device__ __forceinline__ void prox_momentum2_n32(const ProxArgs &pa, co
     if (bad) atomicOr(pa.status, DEV_NONFINITE);
 }
 
-// Pairs of neighbouring pixels (idx[q] even) for N rows at once.
+// Pairs of neighbouring pixels (idx[q] even) for N rows at once (FP32
+// state: prox_momentum2_n32).
 template <int N>
 static __device__ __forceinline__ void prox_momentum2_n(const ProxArgs &pa, const size_t *idx, const float *g0,
                                                         const float *g1, const bool *valid) {
+    if (pa.Y32) {
+        prox_momentum2_n32<N>(pa, idx, g0, g1, valid);
+        return;
+    }
     float4 y[N], xp[N];
 #pragma unroll
     for (int q = 0; q < N; ++q) {

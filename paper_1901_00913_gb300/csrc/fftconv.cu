@@ -157,47 +157,90 @@ __device__ __forceinline__ void dft<5, true>(float2 (&v)[5]) {
     dft5<true>(v);
 }
 
+// R = 8 as two 4-point DFTs of the even and odd points combined with
+// w8^u = exp(-+2 pi i u / 8), u < 4.
+template <bool INV>
+__device__ __forceinline__ void dft8(float2 (&v)[8]) {
+    float2 e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+    dft4<INV>(e);
+    dft4<INV>(o);
+    const float h = 0.70710678118654752440f;
+    const float2 o1 = INV ? make_float2(h * (o[1].x - o[1].y), h * (o[1].x + o[1].y))
+                          : make_float2(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x));
+    const float2 o2 = rot<INV>(o[2]);
+    const float2 o3 = INV ? make_float2(-h * (o[3].x + o[3].y), h * (o[3].x - o[3].y))
+                          : make_float2(h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y));
+    v[0] = cadd(e[0], o[0]);
+    v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], o1);
+    v[5] = csub(e[1], o1);
+    v[2] = cadd(e[2], o2);
+    v[6] = csub(e[2], o2);
+    v[3] = cadd(e[3], o3);
+    v[7] = csub(e[3], o3);
+}
+template <>
+__device__ __forceinline__ void dft<8, false>(float2 (&v)[8]) {
+    dft8<false>(v);
+}
+template <>
+__device__ __forceinline__ void dft<8, true>(float2 (&v)[8]) {
+    dft8<true>(v);
+}
+
 // One butterfly of a stage: the R points x[k * M], k < R.
 // DIF (forward): DFT, then twiddles w_L^(u q) on outputs u >= 1.
 // DIT inverse: conjugate twiddles on inputs u >= 1, then the inverse DFT.
-// tw points at this butterfly's twiddle for u = 1; u's is tw[(u - 1) * M].
+// tw points at this butterfly's twiddle for u = 1 (shared memory); u's is
+// tw[(u - 1) * M].
 template <int R, bool INV>
-__device__ __forceinline__ void bfly(float2 *x, int M, const float2 *__restrict__ tw) {
+__device__ __forceinline__ void bfly(float2 *x, int M, const float2 *tw) {
     float2 v[R];
 #pragma unroll
     for (int k = 0; k < R; ++k) v[k] = x[k * M];
     if (INV) {
 #pragma unroll
-        for (int u = 1; u < R; ++u) v[u] = cmulc(v[u], __ldg(tw + (u - 1) * M));
+        for (int u = 1; u < R; ++u) v[u] = cmulc(v[u], tw[(u - 1) * M]);
         dft<R, true>(v);
     } else {
         dft<R, false>(v);
 #pragma unroll
-        for (int u = 1; u < R; ++u) v[u] = cmul(v[u], __ldg(tw + (u - 1) * M));
+        for (int u = 1; u < R; ++u) v[u] = cmul(v[u], tw[(u - 1) * M]);
     }
 #pragma unroll
     for (int k = 0; k < R; ++k) x[k * M] = v[k];
 }
 
+// x / d for 0 <= x < 2^24 from a float reciprocal, corrected to exact.
+__device__ __forceinline__ int fdiv(int x, int d, float inv) {
+    int q = __float2int_rz((float)x * inv);
+    if (q * d > x) --q;
+    else if ((q + 1) * d <= x) ++q;
+    return q;
+}
+
 // All stages of `lines` in-place transforms of length P.N held in shared
-// memory at buf + line * ls, the whole block cooperating.  Forward: DIF,
-// natural order in, digit-reversed out.  INV: DIT with the stages in
-// reverse order, digit-reversed in, natural out, unscaled.
+// memory at buf + line * ls, the whole block cooperating; tw: the plan's
+// twiddle table in shared memory.  Forward: DIF, natural order in,
+// digit-reversed out.  INV: DIT with the stages in reverse order,
+// digit-reversed in, natural out, unscaled.
 template <bool INV>
-__device__ void fft_lines(float2 *buf, int lines, int ls, const FftLine &P, const float2 *__restrict__ tw) {
+__device__ void fft_lines(float2 *buf, int lines, int ls, const FftLine &P, const float2 *tw) {
     for (int jj = 0; jj < P.ns; ++jj) {
         const int j = INV ? P.ns - 1 - jj : jj;
         const int R = P.R[j], M = P.M[j], L = R * M, per = P.N / R;
+        const float inv_m = 1.0f / (float)M, inv_per = 1.0f / (float)per;
         const float2 *t = tw + P.tw[j];
         for (int it = threadIdx.x; it < lines * per; it += blockDim.x) {
-            const int line = it / per, bf = it - line * per;
-            const int b = bf / M, q = bf - b * M;
+            const int line = fdiv(it, per, inv_per), bf = it - line * per;
+            const int b = fdiv(bf, M, inv_m), q = bf - b * M;
             float2 *x = buf + (size_t)line * ls + b * L + q;
             switch (R) {
                 case 2: bfly<2, INV>(x, M, t + q); break;
                 case 3: bfly<3, INV>(x, M, t + q); break;
                 case 4: bfly<4, INV>(x, M, t + q); break;
-                default: bfly<5, INV>(x, M, t + q); break;
+                case 5: bfly<5, INV>(x, M, t + q); break;
+                default: bfly<8, INV>(x, M, t + q); break;
             }
         }
         __syncthreads();
@@ -213,77 +256,160 @@ __device__ __forceinline__ int ext_src(int t, int len, int bc) {
     return (t >= 0 && t < len) ? t : -1;
 }
 
-// Pass A: rows (extended rows for the forward operator) -> half spectra S1.
-template <bool ADJ>
-__global__ void __launch_bounds__(kThreads) fft_pass_a(FftConvDev P, const float *__restrict__ In, int lpc) {
-    extern __shared__ float2 fbuf[];
-    const int N = P.l2.N, ls = N + 1;
-    const int rows = ADJ ? P.m : P.ext_rows;
-    const int pair0 = blockIdx.x * lpc;
-    for (int it = threadIdx.x; it < lpc * N; it += blockDim.x) {
-        const int j = it / N, t = it - j * N;
-        const int s = 2 * (pair0 + j);
-        float2 v = make_float2(0.f, 0.f);
-        if (ADJ) {
-            if (t < P.n) {
-                if (s < rows) v.x = __ldcg(In + (size_t)s * P.n + t);
-                if (s + 1 < rows) v.y = __ldcg(In + (size_t)(s + 1) * P.n + t);
-            }
-        } else if (t < P.ext_cols) {
-            const int b = ext_src(t - P.offc, P.n, P.bc);
-            if (b >= 0) {
-                const int a0 = s < rows ? ext_src(s - P.offr, P.m, P.bc) : -1;
-                const int a1 = s + 1 < rows ? ext_src(s + 1 - P.offr, P.m, P.bc) : -1;
-                if (a0 >= 0) v.x = __ldcg(In + (size_t)a0 * P.n + b);
-                if (a1 >= 0) v.y = __ldcg(In + (size_t)a1 * P.n + b);
-            }
+// Loop over [0, total) with the block's threads in batches of kBatch items
+// per thread: every item's global loads (load(it)) are issued before any of
+// them is used (use(it, value)), so a thread keeps kBatch loads in flight
+// instead of waiting for each.
+constexpr int kBatch = 8;
+template <typename T, typename Load, typename Use>
+__device__ __forceinline__ void batched(int total, Load load, Use use) {
+    for (int base = threadIdx.x; base < total; base += kBatch * blockDim.x) {
+        T v[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int it = base + u * blockDim.x;
+            if (it < total) v[u] = load(it);
         }
-        fbuf[(size_t)j * ls + t] = v;
-    }
-    __syncthreads();
-    fft_lines<false>(fbuf, lpc, ls, P.l2, P.tw2);
-    // Z = FFT(a + i b): A[f] = (Z[f] + conj Z[N-f]) / 2, B[f] = (Z[f] - conj Z[N-f]) / (2i).
-    for (int it = threadIdx.x; it < lpc * P.H2; it += blockDim.x) {
-        const int j = it / P.H2, f = it - j * P.H2;
-        const int s = 2 * (pair0 + j);
-        if (s >= rows) continue;
-        const float2 z1 = fbuf[(size_t)j * ls + __ldg(P.pos2 + f)];
-        const float2 z2 = fbuf[(size_t)j * ls + __ldg(P.pos2 + (f == 0 ? 0 : N - f))];
-        P.S1[(size_t)s * P.H2 + f] = make_float2(0.5f * (z1.x + z2.x), 0.5f * (z1.y - z2.y));
-        if (s + 1 < rows) P.S1[(size_t)(s + 1) * P.H2 + f] = make_float2(0.5f * (z1.y + z2.y), 0.5f * (z2.x - z1.x));
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int it = base + u * blockDim.x;
+            if (it < total) use(it, v[u]);
+        }
     }
 }
 
-// Pass B: frequency columns of S1 -> kernel product along the rows -> S2.
+// Half spectra are stored in tiles of 8 image rows: element (row s, frequency
+// f) at ((s / 8) * H2 + f) * 8 + s % 8.  A Pass A / Pass C block (up to 8
+// rows) then writes / reads one contiguous run per tile, and a Pass B block
+// (neighbouring frequencies) reads and writes 8 * lines contiguous values
+// per tile.
+__device__ __forceinline__ size_t tile_index(int s, int f, int H2) {
+    return ((size_t)(s >> 3) * H2 + f) * 8 + (s & 7);
+}
+
+// Copies a plan's twiddle table (N - 1 values) and, if pos is non-NULL, the
+// DIF position table (N values) into shared memory.
+__device__ __forceinline__ void stage_tables(const FftLine &P, const float2 *__restrict__ tw_g, float2 *tw,
+                                             const int *__restrict__ pos_g, int *pos) {
+    for (int i = threadIdx.x; i < P.N - 1; i += blockDim.x) tw[i] = __ldg(tw_g + i);
+    if (pos)
+        for (int i = threadIdx.x; i < P.N; i += blockDim.x) pos[i] = __ldg(pos_g + i);
+}
+
+// Shared layout of a pass: `lines` line buffers of N + 1 values (the odd
+// stride spreads the lanes of a stage over the banks), the twiddle table,
+// then (Passes A and C) the position table.
+struct PassSmem {
+    float2 *buf, *tw;
+    int *pos;
+};
+__device__ __forceinline__ PassSmem pass_smem(void *base, int lines, int N, bool with_pos) {
+    PassSmem p;
+    p.buf = reinterpret_cast<float2 *>(base);
+    p.tw = p.buf + (size_t)lines * (N + 1);
+    p.pos = with_pos ? reinterpret_cast<int *>(p.tw + (N - 1)) : nullptr;
+    return p;
+}
+
+// Pass A: rows (extended rows for the forward operator) -> half spectra S1
+// (8-row tiles).
+template <bool ADJ>
+__global__ void __launch_bounds__(kThreads) fft_pass_a(FftConvDev P, const float *__restrict__ In, int lpc) {
+    extern __shared__ __align__(16) unsigned char fsm[];
+    const int N = P.l2.N, ls = N + 1;
+    const PassSmem sm = pass_smem(fsm, lpc, N, true);
+    stage_tables(P.l2, P.tw2, sm.tw, P.pos2, sm.pos);
+    const int rows = ADJ ? P.m : P.ext_rows;
+    const int s0 = 2 * blockIdx.x * lpc;   // first row of the block
+    batched<float2>(
+        lpc * N,
+        [&](int it) {
+            const int j = it / N, t = it - j * N;
+            const int s = s0 + 2 * j;
+            float2 v = make_float2(0.f, 0.f);
+            if (ADJ) {
+                if (t < P.n) {
+                    if (s < rows) v.x = __ldcg(In + (size_t)s * P.n + t);
+                    if (s + 1 < rows) v.y = __ldcg(In + (size_t)(s + 1) * P.n + t);
+                }
+            } else if (t < P.ext_cols) {
+                const int b = ext_src(t - P.offc, P.n, P.bc);
+                if (b >= 0) {
+                    const int a0 = s < rows ? ext_src(s - P.offr, P.m, P.bc) : -1;
+                    const int a1 = s + 1 < rows ? ext_src(s + 1 - P.offr, P.m, P.bc) : -1;
+                    if (a0 >= 0) v.x = __ldcg(In + (size_t)a0 * P.n + b);
+                    if (a1 >= 0) v.y = __ldcg(In + (size_t)a1 * P.n + b);
+                }
+            }
+            return v;
+        },
+        [&](int it, float2 v) {
+            const int j = it / N;
+            sm.buf[(size_t)j * ls + (it - j * N)] = v;
+        });
+    __syncthreads();
+    fft_lines<false>(sm.buf, lpc, ls, P.l2, sm.tw);
+    // Z = FFT(a + i b): A[f] = (Z[f] + conj Z[N-f]) / 2, B[f] = (Z[f] - conj Z[N-f]) / (2i);
+    // the two rows' values at f leave as one 16-byte store, neighbouring
+    // threads taking neighbouring row pairs of the same f.
+    for (int it = threadIdx.x; it < lpc * P.H2; it += blockDim.x) {
+        const int f = it / lpc, j = it - f * lpc;
+        const int s = s0 + 2 * j;
+        if (s >= rows) continue;
+        const float2 z1 = sm.buf[(size_t)j * ls + sm.pos[f]];
+        const float2 z2 = sm.buf[(size_t)j * ls + sm.pos[f == 0 ? 0 : N - f]];
+        const float4 v = make_float4(0.5f * (z1.x + z2.x), 0.5f * (z1.y - z2.y), 0.5f * (z1.y + z2.y),
+                                     0.5f * (z2.x - z1.x));
+        *reinterpret_cast<float4 *>(P.S1 + tile_index(s, f, P.H2)) = v;   // s even: 16-byte aligned
+    }
+}
+
+// Pass B: frequency lines of S1 -> kernel product along the rows -> S2.
 template <bool ADJ>
 __global__ void __launch_bounds__(kThreads) fft_pass_b(FftConvDev P, int lpc) {
-    extern __shared__ float2 fbuf[];
+    extern __shared__ __align__(16) unsigned char fsm[];
     const int N = P.l1.N, ls = N + 1;
+    const PassSmem sm = pass_smem(fsm, lpc, N, false);
+    stage_tables(P.l1, P.tw1, sm.tw, nullptr, nullptr);
     const int rows_in = ADJ ? P.m : P.ext_rows;
     const int f0 = blockIdx.x * lpc;
-    for (int it = threadIdx.x; it < lpc * N; it += blockDim.x) {
-        const int s = it / lpc, j = it - s * lpc;   // j fastest: neighbouring columns together
-        const int f = f0 + j;
-        fbuf[(size_t)j * ls + s] =
-            (s < rows_in && f < P.H2) ? __ldcg(P.S1 + (size_t)s * P.H2 + f) : make_float2(0.f, 0.f);
-    }
+    const int run = 8 * lpc;   // contiguous values per 8-row tile: lpc frequencies x 8 rows
+    const int Nt = (N + 7) & ~7;
+    batched<float2>(
+        lpc * Nt,
+        [&](int it) {
+            const int sb = it / run, rem = it - sb * run;
+            const int j = rem >> 3, s = sb * 8 + (rem & 7);
+            const int f = f0 + j;
+            return (s < rows_in && f < P.H2) ? __ldcg(P.S1 + tile_index(s, f, P.H2)) : make_float2(0.f, 0.f);
+        },
+        [&](int it, float2 v) {
+            const int sb = it / run, rem = it - sb * run;
+            const int s = sb * 8 + (rem & 7);
+            if (s < N) sm.buf[(size_t)(rem >> 3) * ls + s] = v;
+        });
     __syncthreads();
-    fft_lines<false>(fbuf, lpc, ls, P.l1, P.tw1);
-    for (int it = threadIdx.x; it < lpc * N; it += blockDim.x) {
-        const int pos = it / lpc, j = it - pos * lpc;
-        const int f = f0 + j;
-        if (f >= P.H2) continue;
-        const float2 k = __ldg(P.K + (size_t)pos * P.H2 + f);
-        float2 &x = fbuf[(size_t)j * ls + pos];
-        x = ADJ ? cmulc(x, k) : cmul(x, k);
-    }
+    fft_lines<false>(sm.buf, lpc, ls, P.l1, sm.tw);
+    batched<float2>(
+        lpc * N,
+        [&](int it) {
+            const int j = it / N, f = f0 + j;
+            return f < P.H2 ? __ldg(P.K + (size_t)f * N + (it - j * N)) : make_float2(0.f, 0.f);
+        },
+        [&](int it, float2 k) {
+            const int j = it / N;
+            float2 &x = sm.buf[(size_t)j * ls + (it - j * N)];
+            x = ADJ ? cmulc(x, k) : cmul(x, k);
+        });
     __syncthreads();
-    fft_lines<true>(fbuf, lpc, ls, P.l1, P.tw1);
-    for (int it = threadIdx.x; it < lpc * P.m; it += blockDim.x) {
-        const int a = it / lpc, j = it - a * lpc;
+    fft_lines<true>(sm.buf, lpc, ls, P.l1, sm.tw);
+    const int mt = (P.m + 7) & ~7;
+    for (int it = threadIdx.x; it < lpc * mt; it += blockDim.x) {
+        const int ab = it / run, rem = it - ab * run;
+        const int j = rem >> 3, a = ab * 8 + (rem & 7);
         const int f = f0 + j;
-        if (f >= P.H2) continue;
-        const float2 *u = fbuf + (size_t)j * ls;
+        if (f >= P.H2 || a >= P.m) continue;
+        const float2 *u = sm.buf + (size_t)j * ls;
         float2 v;
         if (ADJ) {
             // extended rows s with ext(s - offr) = a: s = a + offr, and for the
@@ -297,7 +423,7 @@ __global__ void __launch_bounds__(kThreads) fft_pass_b(FftConvDev P, int lpc) {
         } else {
             v = u[a];
         }
-        P.S2[(size_t)a * P.H2 + f] = v;
+        P.S2[tile_index(a, f, P.H2)] = v;
     }
 }
 
@@ -305,51 +431,78 @@ __global__ void __launch_bounds__(kThreads) fft_pass_b(FftConvDev P, int lpc) {
 // then the epilogue.
 template <bool ADJ, int EPI>
 __global__ void __launch_bounds__(kThreads) fft_pass_c(FftConvDev P, float *__restrict__ Out, ProxArgs pa, int lpc) {
-    extern __shared__ float2 fbuf[];
+    extern __shared__ __align__(16) unsigned char fsm[];
     const int N = P.l2.N, ls = N + 1;
-    const int pair0 = blockIdx.x * lpc;
-    for (int it = threadIdx.x; it < lpc * N; it += blockDim.x) {
-        const int j = it / N, f = it - j * N;
-        const int a = 2 * (pair0 + j);
-        const bool mirror = f >= P.H2;   // Y[f] = conj Y[N - f] for a real row
-        const int g = mirror ? N - f : f;
-        float2 ya = make_float2(0.f, 0.f), yb = make_float2(0.f, 0.f);
-        if (a < P.m) ya = __ldcg(P.S2 + (size_t)a * P.H2 + g);
-        if (a + 1 < P.m) yb = __ldcg(P.S2 + (size_t)(a + 1) * P.H2 + g);
-        if (mirror) {
-            ya.y = -ya.y;
-            yb.y = -yb.y;
-        }
-        fbuf[(size_t)j * ls + __ldg(P.pos2 + f)] = make_float2(ya.x - yb.y, ya.y + yb.x);
-    }
+    const PassSmem sm = pass_smem(fsm, lpc, N, true);
+    stage_tables(P.l2, P.tw2, sm.tw, P.pos2, sm.pos);
     __syncthreads();
-    fft_lines<true>(fbuf, lpc, ls, P.l2, P.tw2);
-    const int n = P.n;
-    for (int it = threadIdx.x; it < lpc * 2 * n; it += blockDim.x) {
-        const int j = it / (2 * n), rem = it - j * 2 * n;
-        const int h = rem / n, b = rem - h * n;
-        const int a = 2 * (pair0 + j) + h;
-        if (a >= P.m) continue;
-        const float2 *u = fbuf + (size_t)j * ls;
-        float2 w;
-        if (ADJ) {
-            w = u[b + P.offc];
-            if (P.bc) {
-                const int t1 = P.offc - 1 - b, t2 = 2 * n - 1 - b + P.offc;
-                if (t1 >= 0) w = cadd(w, u[t1]);
-                if (t2 < P.ext_cols) w = cadd(w, u[t2]);
+    const int a0 = 2 * blockIdx.x * lpc;
+    batched<float4>(
+        lpc * N,
+        [&](int it) {
+            const int f = it / lpc, j = it - f * lpc;   // neighbouring threads: neighbouring row pairs
+            const int a = a0 + 2 * j;
+            const int g = f >= P.H2 ? N - f : f;
+            return a < P.m ? __ldcg(reinterpret_cast<const float4 *>(P.S2 + tile_index(a, g, P.H2)))
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+        },
+        [&](int it, float4 y) {
+            const int f = it / lpc, j = it - f * lpc;
+            if (f >= P.H2) {   // Y[f] = conj Y[N - f] for a real row
+                y.y = -y.y;
+                y.w = -y.w;
             }
-        } else {
-            w = u[b];
+            // Y_a + i Y_{a+1}; row a + 1 past the image reads the zero padding of S2
+            sm.buf[(size_t)j * ls + sm.pos[f]] = make_float2(y.x - y.w, y.y + y.z);
+        });
+    __syncthreads();
+    fft_lines<true>(sm.buf, lpc, ls, P.l2, sm.tw);
+    // Output pixels, kEpi per thread at a time (their state / observation
+    // loads issued together): pixel `it` of the block is row a0 + it / n.
+    const int n = P.n;
+    constexpr int kEpi = 4;
+    const int total = lpc * 2 * n;
+    for (int base = threadIdx.x; base < total; base += kEpi * blockDim.x) {
+        float g[kEpi];
+        size_t idx[kEpi];
+        bool ok[kEpi];
+#pragma unroll
+        for (int u = 0; u < kEpi; ++u) {
+            const int it = base + u * blockDim.x;
+            const int rr = it / n, b = it - rr * n;   // rr: row within the block
+            const int a = a0 + rr;
+            ok[u] = it < total && a < P.m;
+            idx[u] = (size_t)a * n + b;
+            g[u] = 0.f;
+            if (!ok[u]) continue;
+            const float2 *ub = sm.buf + (size_t)(rr >> 1) * ls;
+            float2 w;
+            if (ADJ) {
+                w = ub[b + P.offc];
+                if (P.bc) {
+                    const int t1 = P.offc - 1 - b, t2 = 2 * n - 1 - b + P.offc;
+                    if (t1 >= 0) w = cadd(w, ub[t1]);
+                    if (t2 < P.ext_cols) w = cadd(w, ub[t2]);
+                }
+            } else {
+                w = ub[b];
+            }
+            g[u] = (rr & 1) ? w.y : w.x;
         }
-        const float v = h ? w.y : w.x;
-        const size_t idx = (size_t)a * n + b;
-        if (EPI == EPI_STORE)
-            Out[idx] = v;
-        else if (EPI == EPI_RESIDUAL)
-            Out[idx] = v - __ldcg(pa.Bd + idx);
-        else
-            prox_momentum(pa, idx, v);
+        if (EPI == EPI_STORE) {
+#pragma unroll
+            for (int u = 0; u < kEpi; ++u)
+                if (ok[u]) Out[idx[u]] = g[u];
+        } else if (EPI == EPI_RESIDUAL) {
+            float bv[kEpi];
+#pragma unroll
+            for (int u = 0; u < kEpi; ++u) bv[u] = ok[u] ? __ldcg(pa.Bd + idx[u]) : 0.f;
+#pragma unroll
+            for (int u = 0; u < kEpi; ++u)
+                if (ok[u]) Out[idx[u]] = g[u] - bv[u];
+        } else {
+            prox_momentum_n<kEpi>(pa, idx, g, ok);
+        }
     }
 }
 
@@ -364,18 +517,24 @@ int smooth_len(int need) {
     return (int)best;
 }
 
-// DIF stages of length N: radix 4 while possible, then 2, 3, 5.
+// DIF stages of length N: the factors 2 as radix 8 and 4 (a single 2 only
+// when the power of two is odd and below 8, or after the 8s), then 3s, 5s.
 bool line_plan(int N, FftLine *P, std::vector<double2> *tw) {
     std::vector<int> rad;
-    int r = N;
-    while (r % 4 == 0) {
-        rad.push_back(4);
-        r /= 4;
-    }
+    int r = N, n2 = 0;
     while (r % 2 == 0) {
-        rad.push_back(2);
         r /= 2;
+        ++n2;
     }
+    while (n2 >= 3 && n2 != 4) {
+        rad.push_back(8);
+        n2 -= 3;
+    }
+    while (n2 >= 2) {
+        rad.push_back(4);
+        n2 -= 2;
+    }
+    if (n2 == 1) rad.push_back(2);
     while (r % 3 == 0) {
         rad.push_back(3);
         r /= 3;
@@ -429,26 +588,32 @@ cudaError_t upload_vec(T **dst, const std::vector<T> &v) {
     return cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
 }
 
-// Lines per block: as many as keep >= 2 blocks per SM over `lines` lines and
-// the buffer under 96 KB.
-int pick_lpc(long lines, int N, int sms) {
-    int lpc = 1;
-    while (lpc < 8 && (size_t)(2 * lpc) * (N + 1) * sizeof(float2) <= 96 * 1024 &&
-           (lines + 2 * lpc - 1) / (2 * lpc) >= 2L * sms)
-        lpc *= 2;
-    return lpc;
+// Shared memory of a pass block: `lines` buffers of N + 1 values, the
+// twiddle table (N - 1 values) and, for Passes A and C, the position table.
+size_t pass_smem_bytes(int lines, int N, bool with_pos) {
+    return sizeof(float2) * ((size_t)lines * (N + 1) + (N - 1)) + (with_pos ? sizeof(int) * N : 0);
+}
+
+// Lines per block (row pairs in Passes A and C, frequencies in Pass B): 4
+// when that still gives a block per SM, so a block's run in each 8-row tile
+// of the spectra is 64 (A, C) or 256 (B) contiguous bytes, else 2, else 1.
+// A block stays within `budget` bytes of shared memory (two blocks per SM).
+int pick_lpc(long lines, int N, int sms, bool with_pos, size_t budget) {
+    const int cand[3] = {4, 2, 1};
+    for (int lpc : cand) {
+        if (lpc > 1 && pass_smem_bytes(lpc, N, with_pos) > budget) continue;
+        if (lpc == 1 || (lines + lpc - 1) / lpc >= (long)sms) return lpc;
+    }
+    return 1;
 }
 
 // The attribute is per kernel, not per launch: every FFT kernel is allowed
-// the most any plan uses (pick_lpc keeps a block at or under 96 KB, and one
-// line of kFftMaxLen takes 64 KB), so a later, smaller plan never lowers an
-// earlier one's limit.
-constexpr size_t kFftSmemMax = 96 * 1024 + 2 * sizeof(float2) * 8;
-
+// the device's per-block maximum once, so a later, smaller plan never lowers
+// an earlier one's limit.
 template <typename K>
-cudaError_t allow_smem(K kernel, size_t bytes) {
-    if (bytes > kFftSmemMax) return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFftSmemMax);
+cudaError_t allow_smem(K kernel, size_t bytes, int limit) {
+    if (bytes > (size_t)limit) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
 }
 
 }  // namespace
@@ -479,10 +644,13 @@ sfista_status fftconv_create(FftConv **out, const double *K, int p, int q, int c
         return fail(SFISTA_ENOTSUP, "FFT form: no radix plan");
     }
     d.H2 = N2 / 2 + 1;
+    d.sr1 = (d.ext_rows + 7) & ~7;   // rows rounded up to whole 8-row tiles
+    d.sr2 = (m + 7) & ~7;
     const std::vector<int> pos1 = dif_positions(d.l1), pos2 = dif_positions(d.l2);
     // Kernel spectrum of h[s1][s2] = K[s1' + p - 1][s2' + q - 1] at s = s' mod N,
-    // s' in [-(p-1), 0] x [-(q-1), 0]; scaled by 1 / (N1 N2) and stored with
-    // the row frequency at its DIF position: Kd[pos1[f1]][f2], f2 < H2.
+    // s' in [-(p-1), 0] x [-(q-1), 0]; scaled by 1 / (N1 N2) and stored
+    // column-frequency-major with the row frequency at its DIF position:
+    // Kd[f2][pos1[f1]], f2 < H2 (Pass B reads one contiguous line per f2).
     std::vector<std::complex<double>> root1(N1), root2(N2);
     for (int t = 0; t < N1; ++t) root1[t] = std::polar(1.0, -2.0 * M_PI * t / N1);
     for (int t = 0; t < N2; ++t) root2[t] = std::polar(1.0, -2.0 * M_PI * t / N2);
@@ -502,12 +670,11 @@ sfista_status fftconv_create(FftConv **out, const double *K, int p, int q, int c
     std::vector<std::complex<double>> col(p);
     for (int f1 = 0; f1 < N1; ++f1) {
         for (int k = 0; k < p; ++k) col[k] = root1[(size_t)((f1 * (((long)k - (p - 1) + N1) % N1)) % N1)];
-        float2 *row = Kd.data() + (size_t)pos1[f1] * H2;
         for (int f2 = 0; f2 < H2; ++f2) {
             std::complex<double> acc = 0.0;
             for (int k = 0; k < p; ++k) acc += F2[(size_t)k * H2 + f2] * col[k];
             acc *= scale;
-            row[f2] = make_float2((float)acc.real(), (float)acc.imag());
+            Kd[(size_t)f2 * N1 + pos1[f1]] = make_float2((float)acc.real(), (float)acc.imag());
         }
     }
     auto to_f2 = [](const std::vector<double2> &v) {
@@ -518,23 +685,29 @@ sfista_status fftconv_create(FftConv **out, const double *K, int p, int q, int c
     cudaError_t e;
     if ((e = upload_vec((float2 **)&d.tw1, to_f2(tw1))) || (e = upload_vec((float2 **)&d.tw2, to_f2(tw2))) ||
         (e = upload_vec((int **)&d.pos2, pos2)) || (e = upload_vec((float2 **)&d.K, Kd)) ||
-        (e = cudaMalloc((void **)&d.S1, sizeof(float2) * (size_t)d.ext_rows * H2)) ||
-        (e = cudaMalloc((void **)&d.S2, sizeof(float2) * (size_t)m * H2))) {
+        (e = cudaMalloc((void **)&d.S1, sizeof(float2) * (size_t)H2 * d.sr1)) ||
+        (e = cudaMalloc((void **)&d.S2, sizeof(float2) * (size_t)H2 * d.sr2)) ||
+        // the padding rows (an odd row count) are read as zeros by Passes B and C
+        (e = cudaMemset(d.S1, 0, sizeof(float2) * (size_t)H2 * d.sr1)) ||
+        (e = cudaMemset(d.S2, 0, sizeof(float2) * (size_t)H2 * d.sr2))) {
         fftconv_destroy(f);
         return fail(SFISTA_ENOMEM, std::string("FFT form buffers: ") + cudaGetErrorString(e));
     }
-    int dev = 0, sms = 152;
+    int dev = 0, sms = 152, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    f->lpc_a = pick_lpc((d.ext_rows + 1) / 2, N2, sms);
-    f->lpc_b = pick_lpc(H2, N1, sms);
-    f->lpc_c = pick_lpc((m + 1) / 2, N2, sms);
-    const size_t sa = sizeof(float2) * f->lpc_a * (N2 + 1), sb = sizeof(float2) * f->lpc_b * (N1 + 1),
-                 sc = sizeof(float2) * f->lpc_c * (N2 + 1);
-    if ((e = allow_smem(fft_pass_a<false>, sa)) || (e = allow_smem(fft_pass_a<true>, sa)) ||
-        (e = allow_smem(fft_pass_b<false>, sb)) || (e = allow_smem(fft_pass_b<true>, sb)) ||
-        (e = allow_smem(fft_pass_c<false, EPI_STORE>, sc)) || (e = allow_smem(fft_pass_c<false, EPI_RESIDUAL>, sc)) ||
-        (e = allow_smem(fft_pass_c<true, EPI_STORE>, sc)) || (e = allow_smem(fft_pass_c<true, EPI_PROX>, sc))) {
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t budget = 110 * 1024;
+    f->lpc_a = pick_lpc((d.ext_rows + 1) / 2, N2, sms, true, budget);
+    f->lpc_b = pick_lpc(H2, N1, sms, false, budget);
+    f->lpc_c = pick_lpc((m + 1) / 2, N2, sms, true, budget);
+    const size_t sa = pass_smem_bytes(f->lpc_a, N2, true), sb = pass_smem_bytes(f->lpc_b, N1, false),
+                 sc = pass_smem_bytes(f->lpc_c, N2, true);
+    if ((e = allow_smem(fft_pass_a<false>, sa, optin)) || (e = allow_smem(fft_pass_a<true>, sa, optin)) ||
+        (e = allow_smem(fft_pass_b<false>, sb, optin)) || (e = allow_smem(fft_pass_b<true>, sb, optin)) ||
+        (e = allow_smem(fft_pass_c<false, EPI_STORE>, sc, optin)) ||
+        (e = allow_smem(fft_pass_c<false, EPI_RESIDUAL>, sc, optin)) ||
+        (e = allow_smem(fft_pass_c<true, EPI_STORE>, sc, optin)) || (e = allow_smem(fft_pass_c<true, EPI_PROX>, sc, optin))) {
         fftconv_destroy(f);
         return fail(SFISTA_ENOTSUP, std::string("FFT form shared memory: ") + cudaGetErrorString(e));
     }
@@ -557,13 +730,13 @@ void fftconv_part(const FftConv *f, int part, bool adj, const float *In, EpiKind
         // Pass A reads the input rows (the operator's input), Pass B the spectra.
         const int rows = adj ? d.m : d.ext_rows;
         const int ga = (int)(((rows + 1) / 2 + f->lpc_a - 1) / f->lpc_a);
-        const size_t sa = sizeof(float2) * f->lpc_a * (d.l2.N + 1);
+        const size_t sa = pass_smem_bytes(f->lpc_a, d.l2.N, true);
         if (adj)
             fft_pass_a<true><<<ga, kThreads, sa, s>>>(d, In, f->lpc_a);
         else
             fft_pass_a<false><<<ga, kThreads, sa, s>>>(d, In, f->lpc_a);
         const int gb = (d.H2 + f->lpc_b - 1) / f->lpc_b;
-        const size_t sb = sizeof(float2) * f->lpc_b * (d.l1.N + 1);
+        const size_t sb = pass_smem_bytes(f->lpc_b, d.l1.N, false);
         if (adj)
             fft_pass_b<true><<<gb, kThreads, sb, s>>>(d, f->lpc_b);
         else
@@ -571,7 +744,7 @@ void fftconv_part(const FftConv *f, int part, bool adj, const float *In, EpiKind
         return;
     }
     const int gc = ((d.m + 1) / 2 + f->lpc_c - 1) / f->lpc_c;
-    const size_t sc = sizeof(float2) * f->lpc_c * (d.l2.N + 1);
+    const size_t sc = pass_smem_bytes(f->lpc_c, d.l2.N, true);
     if (adj) {
         if (epi == EPI_PROX)
             fft_pass_c<true, EPI_PROX><<<gc, kThreads, sc, s>>>(d, Out, pa, f->lpc_c);
@@ -593,7 +766,7 @@ void fftconv_apply(const FftConv *f, bool adj, const float *In, EpiKind epi, flo
 
 size_t fftconv_bytes(const FftConv *f) {
     const FftConvDev &d = f->d;
-    return sizeof(float2) * ((size_t)d.ext_rows * d.H2 + (size_t)d.m * d.H2 + (size_t)d.l1.N * d.H2);
+    return sizeof(float2) * ((size_t)d.sr1 * d.H2 + (size_t)d.sr2 * d.H2 + (size_t)d.l1.N * d.H2);
 }
 
 }  // namespace sfista

@@ -9,7 +9,7 @@
 namespace sfista {
 
 constexpr int kFftMaxStages = 14;
-constexpr int kFftMaxLen = 8192;   // longest line transform (64 KB of shared memory)
+constexpr int kFftMaxLen = 8192;   // longest line transform (one line, its twiddles and positions: 160 KB of shared memory)
 
 // DIF stage plan of one line length N = prod R[j]; stage j has stride M[j]
 // and its twiddles at tw[j] in the plan's table ((R - 1) * M values).
@@ -24,11 +24,12 @@ struct FftConvDev {
     int offr, offc;           // extension rows above / columns left: p - 1 - cr, q - 1 - cc
     int ext_rows, ext_cols;   // m + p - 1, n + q - 1
     int H2;                   // N2 / 2 + 1 stored frequencies along rows
+    int sr1, sr2;             // rows of S1, S2: ext_rows, m rounded up to whole 8-row tiles
     FftLine l1, l2;           // column transforms (length N1 >= ext_rows), row transforms (N2 >= ext_cols)
-    const float2 *tw1, *tw2;  // twiddle tables
+    const float2 *tw1, *tw2;  // twiddle tables (N - 1 values each)
     const int *pos2;          // pos2[f]: DIF position of row frequency f
-    const float2 *K;          // kernel spectrum / (N1 N2): N1 (DIF order) x H2
-    float2 *S1, *S2;          // half spectra: ext_rows x H2, m x H2
+    const float2 *K;          // kernel spectrum / (N1 N2): H2 x N1, the column frequency in DIF order
+    float2 *S1, *S2;          // half spectra in 8-row tiles: (row, f) at ((row / 8) * H2 + f) * 8 + row % 8
 };
 
 struct FftConv {

@@ -146,6 +146,9 @@ struct BandItem {
 // The configs pick the tile height th (set it in the descriptors' th).
 // The descriptor's pa.Xin / pa.Xout are the state buffers 0 / 1.
 bool band_solve_fused_config(const BandProb &prob, int dev, int *grid, size_t *smem, int *th);
+// The same for a given tile height th (a multiple of 4 from 16 to 32); false
+// when those tiles do not all fit as co-resident blocks.
+bool band_solve_fused_config_th(const BandProb &prob, int dev, int th, int *grid, size_t *smem);
 cudaError_t launch_band_solve_fused(int grid, size_t smem, const BandProb &prob, int k0, int iters, unsigned *bar,
                                     cudaStream_t s);
 bool band_solve_fused_batch_config(const BandProb *probs, int np, int dev, std::vector<int2> *items, size_t *smem,
@@ -174,6 +177,8 @@ void launch_band_op_fused(const float *In, int m, int n, int r, const float *Fb,
 inline bool is_banded(int op) {
     return op == SFISTA_OP_BANDED || op == SFISTA_OP_BANDED_PERSISTENT || op == SFISTA_OP_BANDED_FUSED;
 }
+// The FFT engine (fftconv.h): the Kronecker operator, or the exact blur.
+inline bool is_fft(int op) { return op == SFISTA_OP_FFT || op == SFISTA_OP_EXACT_FFT; }
 
 // Small helpers.
 void launch_fill_f64(double *p, size_t count, double v, cudaStream_t s);

@@ -851,6 +851,15 @@ bool band_solve_fused_config(const BandProb &prob, int dev, int *grid, size_t *s
     return true;
 }
 
+bool band_solve_fused_config_th(const BandProb &prob, int dev, int th, int *grid, size_t *smem) {
+    if (th < 16 || th > TA || th % 4) return false;
+    long tiles = 0;
+    int sms = 0;
+    if (!solve_fused_fits<false>(&prob, 1, dev, th, &tiles, smem, &sms)) return false;
+    *grid = (int)tiles;
+    return true;
+}
+
 cudaError_t launch_band_solve_fused(int grid, size_t smem, const BandProb &prob, int k0, int iters, unsigned *bar,
                                     cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(bar, 0, kBarrierBytes, s);

@@ -125,3 +125,54 @@ def test_config5_gradients_vs_central_differences():
     for k, (ad, fd) in enumerate(checks):
         assert abs(ad - fd) <= 1e-3 * abs(fd), (k, ad, fd)
     s.close()
+
+
+def _band_mask(F):
+    """Entries of the stacked factors F that lie inside their band (the band of the setup's factors)."""
+    rows, cols = np.nonzero(np.any(F != 0.0, axis=0))
+    lo, hi = int((cols - rows).min()), int((cols - rows).max())
+    idx = np.arange(F.shape[1])
+    off = idx[None, :] - idx[:, None]
+    return (off >= lo) & (off <= hi)
+
+
+@pytest.mark.parametrize("op", ["banded", "banded_persistent"])
+def test_autograd_follows_the_factors_passed(op):
+    """Perturbed factors (inside the band) passed to the autograd function change the forward, and forward and
+    gradients then match the oracle's reverse mode run with those same factors; a factor with an entry outside
+    the band is refused."""
+    m, n, r, K = 48, 40, 2, 9
+    P = W.rotated_gaussian_psf(9, 2.0, 1.0, 0.3)
+    g = W.rng(403)
+    s = api.Sfista(P, (m, n), 1, r, prec="fp32", op=op, lipschitz=1.0)
+    A0, B0 = s.factors()
+    A = A0 + 0.05 * g.standard_normal(A0.shape) * _band_mask(A0)[None] * (A0 != 0).any(axis=0)[None]
+    B = B0 + 0.05 * g.standard_normal(B0.shape) * _band_mask(B0)[None] * (B0 != 0).any(axis=0)[None]
+    b = torch.from_numpy(g.uniform(size=(m, n)).astype(np.float32)).cuda()
+    xt = torch.from_numpy(g.uniform(size=(m, n)).astype(np.float32)).cuda()
+    lam = torch.tensor(0.03, dtype=torch.float64, device="cuda", requires_grad=True)
+    X0 = api.unrolled_solve(s, b, lam, K, ckpt_every=4).detach()
+    At = torch.from_numpy(A).cuda().requires_grad_(True)
+    Bt = torch.from_numpy(B).cuda().requires_grad_(True)
+    X = api.unrolled_solve(s, b, lam, K, ckpt_every=4, A=At, B=Bt)
+    b64 = b.double().cpu().numpy()
+    Xo = adjoint.unrolled_forward(b64, A, B, 1.0, 0.03, K)[0]
+    assert _rel(X.detach().cpu().numpy(), Xo) < 1e-5
+    assert _rel(X0.cpu().numpy(), Xo) > 1e-3          # the perturbation matters
+    loss = ((X - xt) ** 2).sum()
+    loss.backward()
+    ob, ol, oA, oB = adjoint.unrolled_grad(b64, A, B, 1.0, 0.03, K,
+                                           2.0 * (X.detach().double().cpu().numpy() - xt.double().cpu().numpy()))
+    assert abs(lam.grad.item() - ol) <= 1e-4 * abs(ol)
+    assert _rel(At.grad.cpu().numpy(), oA) < 1e-4
+    assert _rel(Bt.grad.cpu().numpy(), oB) < 1e-4
+    np.testing.assert_allclose(s.factors()[0], A.astype(np.float64), rtol=0, atol=0)
+    bad = A.copy()
+    bad[0, 0, n - 1] = 1.0                              # far outside the band
+    with pytest.raises(api.SfistaError) as ei:
+        s.set_factors(bad, None)
+    assert ei.value.status == api.EINVAL
+    with pytest.raises(api.SfistaError) as ei:
+        s.profiles()
+    assert ei.value.status == api.ENOTSUP
+    s.close()
