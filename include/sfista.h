@@ -79,7 +79,7 @@ typedef enum {
                                         persistent cooperative launch (grid barrier between phases):
                                         the fused operator form with band tiles and state resident
                                         when every th x 32 output tile has its own resident block
-                                        (th, a multiple of 4 from 16 to 32, picked per problem; m, n
+                                        (th, a multiple of 4 from 16 to 64, picked per problem; m, n
                                         multiples of 4), else the two-pass form */
     SFISTA_OP_BANDED_FUSED = 5, /* banded FP32 operator, one kernel per operator application: the
                                   row pass is kept in shared memory for the column pass (the
@@ -130,10 +130,11 @@ typedef struct {
     int tile_override;      /* 0 (default): the one-launch solver
                                (SFISTA_OP_BANDED_PERSISTENT, fused form) picks its tile
                                height th by a work model at setup, and sfista_tune by
-                               measurement; 16..32 (a multiple of 4): use th x 32 tiles
-                               (SFISTA_EINVAL otherwise; ignored where the one-launch
-                               fused solver is not used, and the two-pass persistent form
-                               is used instead if those tiles do not all fit).          */
+                               measurement; 16..64 (a multiple of 4): use th x 32 tiles
+                               (blocks of 256 threads up to 32 rows, 512 above;
+                               SFISTA_EINVAL otherwise; ignored where the one-launch fused
+                               solver is not used, and the two-pass persistent form is
+                               used instead if those tiles do not all fit).             */
 } sfista_opts;
 
 /* Fill *opts with the defaults listed above. */
@@ -449,7 +450,7 @@ typedef struct {
  *   - if the operator form was left to SFISTA_OP_AUTO: FP32 contexts also
  *     compare the tuned two-pass form with the fused form, the FFT form
  *     (SFISTA_OP_FFT, when its transforms fit) and, when every th x 32 tile
- *     (th from 32 down to 16) can have its own resident block, the one-launch
+ *     (th from 64 down to 16) can have its own resident block, the one-launch
  *     solver (SFISTA_OP_BANDED_PERSISTENT, timed per iteration over
  *     max(iters, 40) iterations of one launch, for every tile height th);
  *     tensor-core contexts compare the band-limited and full (dense) K

@@ -667,8 +667,8 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int ce
     if (!(o.lipschitz <= 0.0 || isfinite(o.lipschitz))) return fail(SFISTA_EINVAL, "lipschitz must be finite");
     if (!(o.l1 >= 0.0) || !isfinite(o.l1)) return fail(SFISTA_EINVAL, "l1 must be finite and >= 0");
     if (o.refine_every < 0) return fail(SFISTA_EINVAL, "refine_every must be >= 0");
-    if (o.tile_override != 0 && (o.tile_override < 16 || o.tile_override > 32 || o.tile_override % 4))
-        return fail(SFISTA_EINVAL, "tile_override must be 0 or a multiple of 4 from 16 to 32");
+    if (o.tile_override != 0 && (o.tile_override < 16 || o.tile_override > 64 || o.tile_override % 4))
+        return fail(SFISTA_EINVAL, "tile_override must be 0 or a multiple of 4 from 16 to 64");
     if (center_row == -1 && psf_rows > 0) center_row = (psf_rows - 1) / 2;
     if (center_col == -1 && psf_cols > 0) center_col = (psf_cols - 1) / 2;
     sfista_ctx *c = new (std::nothrow) sfista_ctx();
@@ -1647,7 +1647,7 @@ sfista_status sfista_tune(sfista_ctx *c, int iters, sfista_tune_entry *entries, 
                 const int best_op = c->op;
                 int best_th = 0, best_grid = 0;
                 size_t best_smem = 0;
-                for (int th = 32; th >= 16; th -= 4) {
+                for (int th = 64; th >= 16; th -= 4) {
                     if (c->opts.tile_override && th != c->opts.tile_override) continue;
                     int grid = 0;
                     size_t smem = 0;

@@ -219,6 +219,19 @@ __device__ __forceinline__ int fdiv(int x, int d, float inv) {
     return q;
 }
 
+// One stage of radix R over `lines` transforms: the butterfly loop is
+// specialised on R (no per-butterfly dispatch).
+template <int R, bool INV>
+__device__ __forceinline__ void fft_stage(float2 *buf, int lines, int ls, int N, int M, const float2 *t) {
+    const int L = R * M, per = N / R;
+    const float inv_m = 1.0f / (float)M, inv_per = 1.0f / (float)per;
+    for (int it = threadIdx.x; it < lines * per; it += blockDim.x) {
+        const int line = fdiv(it, per, inv_per), bf = it - line * per;
+        const int b = fdiv(bf, M, inv_m), q = bf - b * M;
+        bfly<R, INV>(buf + (size_t)line * ls + b * L + q, M, t + q);
+    }
+}
+
 // All stages of `lines` in-place transforms of length P.N held in shared
 // memory at buf + line * ls, the whole block cooperating; tw: the plan's
 // twiddle table in shared memory.  Forward: DIF, natural order in,
@@ -228,20 +241,14 @@ template <bool INV>
 __device__ void fft_lines(float2 *buf, int lines, int ls, const FftLine &P, const float2 *tw) {
     for (int jj = 0; jj < P.ns; ++jj) {
         const int j = INV ? P.ns - 1 - jj : jj;
-        const int R = P.R[j], M = P.M[j], L = R * M, per = P.N / R;
-        const float inv_m = 1.0f / (float)M, inv_per = 1.0f / (float)per;
+        const int M = P.M[j];
         const float2 *t = tw + P.tw[j];
-        for (int it = threadIdx.x; it < lines * per; it += blockDim.x) {
-            const int line = fdiv(it, per, inv_per), bf = it - line * per;
-            const int b = fdiv(bf, M, inv_m), q = bf - b * M;
-            float2 *x = buf + (size_t)line * ls + b * L + q;
-            switch (R) {
-                case 2: bfly<2, INV>(x, M, t + q); break;
-                case 3: bfly<3, INV>(x, M, t + q); break;
-                case 4: bfly<4, INV>(x, M, t + q); break;
-                case 5: bfly<5, INV>(x, M, t + q); break;
-                default: bfly<8, INV>(x, M, t + q); break;
-            }
+        switch (P.R[j]) {
+            case 2: fft_stage<2, INV>(buf, lines, ls, P.N, M, t); break;
+            case 3: fft_stage<3, INV>(buf, lines, ls, P.N, M, t); break;
+            case 4: fft_stage<4, INV>(buf, lines, ls, P.N, M, t); break;
+            case 5: fft_stage<5, INV>(buf, lines, ls, P.N, M, t); break;
+            default: fft_stage<8, INV>(buf, lines, ls, P.N, M, t); break;
         }
         __syncthreads();
     }
@@ -594,12 +601,14 @@ size_t pass_smem_bytes(int lines, int N, bool with_pos) {
     return sizeof(float2) * ((size_t)lines * (N + 1) + (N - 1)) + (with_pos ? sizeof(int) * N : 0);
 }
 
-// Lines per block (row pairs in Passes A and C, frequencies in Pass B): 4
+// Lines per block (row pairs in Passes A and C, frequencies in Pass B): 2
 // when that still gives a block per SM, so a block's run in each 8-row tile
-// of the spectra is 64 (A, C) or 256 (B) contiguous bytes, else 2, else 1.
-// A block stays within `budget` bytes of shared memory (two blocks per SM).
+// of the spectra is 32 (A, C) or 128 (B) contiguous bytes, else 1.  A block
+// stays within `budget` bytes of shared memory where it can (three or more
+// blocks per SM hide the latency of the transforms' shared-memory stages
+// better than two blocks of four lines).
 int pick_lpc(long lines, int N, int sms, bool with_pos, size_t budget) {
-    const int cand[3] = {4, 2, 1};
+    const int cand[2] = {2, 1};
     for (int lpc : cand) {
         if (lpc > 1 && pass_smem_bytes(lpc, N, with_pos) > budget) continue;
         if (lpc == 1 || (lines + lpc - 1) / lpc >= (long)sms) return lpc;
@@ -697,7 +706,7 @@ sfista_status fftconv_create(FftConv **out, const double *K, int p, int q, int c
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t budget = 110 * 1024;
+    const size_t budget = 64 * 1024;
     f->lpc_a = pick_lpc((d.ext_rows + 1) / 2, N2, sms, true, budget);
     f->lpc_b = pick_lpc(H2, N1, sms, false, budget);
     f->lpc_c = pick_lpc((m + 1) / 2, N2, sms, true, budget);

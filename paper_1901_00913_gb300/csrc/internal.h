@@ -134,7 +134,7 @@ struct BandProb {
     ProxArgs pa;   // Bd, Y, Yop, beta, constants, status; Xin / Xout = state buffers 0 / 1
     float *xout;   // one-launch batch: the FP32 result X_iters, written by the solver itself
     int4 tfwd, tadj;   // interior ranges (f0, f1, g0, g1) of (A, B) and (A^T, B^T); see launch_band_op_fused
-    int th;            // one-launch solver: output rows per tile (multiple of 4, <= 32)
+    int th;            // one-launch solver: output rows per tile (multiple of 4, <= 64; <= 32 in batches)
 };
 struct BandItem {
     int prob, q, tile, pad;   // rows pass: q = term chunk; cols pass: q = 0
@@ -146,7 +146,7 @@ struct BandItem {
 // The configs pick the tile height th (set it in the descriptors' th).
 // The descriptor's pa.Xin / pa.Xout are the state buffers 0 / 1.
 bool band_solve_fused_config(const BandProb &prob, int dev, int *grid, size_t *smem, int *th);
-// The same for a given tile height th (a multiple of 4 from 16 to 32); false
+// The same for a given tile height th (a multiple of 4 from 16 to 64); false
 // when those tiles do not all fit as co-resident blocks.
 bool band_solve_fused_config_th(const BandProb &prob, int dev, int th, int *grid, size_t *smem);
 cudaError_t launch_band_solve_fused(int grid, size_t smem, const BandProb &prob, int k0, int iters, unsigned *bar,

@@ -68,25 +68,27 @@ struct FusedGeom {
     int off;         // loF mod 4: leading zero taps of the row pass
     int wF4, wG4;    // padded tap counts (multiples of 4)
     int zs;          // Z rows the column pass reads: TA + wG4
-    int th;          // output rows of a tile (a multiple of 4, <= 32; the column tile stays 32 wide)
+    int th;          // output rows of a tile (a multiple of 4, <= gt; the column tile stays 32 wide)
+    int gt;          // rows of the column-pass coefficient tile (32, or 64 for the 512-thread solver)
     int rows;        // staged input rows: zs rounded up to 32
     int sp, zsp;     // row strides of In and Zt
     size_t off_f, off_g, off_z, total;   // float offsets / size
 };
 
-__host__ __device__ inline FusedGeom fused_geom(int r, int loF, int wF, int wG, int th = TA) {
+__host__ __device__ inline FusedGeom fused_geom(int r, int loF, int wF, int wG, int th = TA, int gt = TA) {
     FusedGeom g;
     g.off = ((loF % 4) + 4) % 4;
     g.wF4 = (wF + g.off + 3) & ~3;
     g.wG4 = (wG + 3) & ~3;
     g.th = th;
+    g.gt = gt;
     g.zs = th + g.wG4;
     g.rows = (g.zs + 31) & ~31;
     g.sp = 4 * (((TC + g.wF4) / 4) | 1);
     g.zsp = 4 * ((g.zs / 4) | 1);
     g.off_f = (size_t)g.rows * g.sp;
     g.off_g = g.off_f + (size_t)r * g.wF4 * (TC + 1);   // F tile, then its Toeplitz row
-    g.off_z = g.off_g + (size_t)r * g.wG4 * (TA + 1);
+    g.off_z = g.off_g + (size_t)r * g.wG4 * (gt + 1);
     g.total = g.off_z + (size_t)r * TC * g.zsp;
     return g;
 }
@@ -185,7 +187,7 @@ __device__ __forceinline__ void rows_pass(const float *xa, int sp, const float *
 // Four taps (k .. k+3) of one term of the column pass: (w0, w1) is the Z
 // window of rows rb + k .. rb + k + 7 in the lane's column.
 // TOEP: gk is the Toeplitz row at tap k (one coefficient for all 4 rows).
-template <bool TOEP>
+template <bool TOEP, int GT>
 __device__ __forceinline__ void cols_taps4(const float4 &w0, const float4 &w1, const float *gk, float (&a)[4]) {
     const float z[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
     float4 tg;
@@ -197,7 +199,7 @@ __device__ __forceinline__ void cols_taps4(const float4 &w0, const float4 &w1, c
             const float v = comp(tg, t);
             g = make_float4(v, v, v, v);
         } else {
-            g = lds4(gk + t * TA);
+            g = lds4(gk + t * GT);
         }
         a[0] = fmaf(g.x, z[t], a[0]);
         a[1] = fmaf(g.y, z[t + 1], a[1]);
@@ -210,9 +212,9 @@ __device__ __forceinline__ void cols_taps4(const float4 &w0, const float4 &w1, c
 // row rb); gr: coefficients of rows rb .. rb+3 of the first term.  Each
 // term's chain is summed into acc at the end, terms in order.  Two steps
 // of 4 taps per trip, as in the row pass.
-template <int K, bool TOEP>
+template <int K, bool TOEP, int GT>
 __device__ __forceinline__ void cols_pass(const float *zc, int zsp, const float *gr, int wG4, float *acc) {
-    constexpr int ts = TOEP ? 1 : TA;   // tap stride of the coefficients
+    constexpr int ts = TOEP ? 1 : GT;   // tap stride of the coefficients
     float a[K][4];
     float4 w0[K];
 #pragma unroll
@@ -227,16 +229,16 @@ __device__ __forceinline__ void cols_pass(const float *zc, int zsp, const float 
         for (int q = 0; q < K; ++q) {
             const float *zq = zc + q * TC * zsp;
             const float4 w1 = lds4(zq + k + 4);
-            cols_taps4<TOEP>(w0[q], w1, gr + (q * wG4 + k) * ts, a[q]);
+            cols_taps4<TOEP, GT>(w0[q], w1, gr + (q * wG4 + k) * ts, a[q]);
             w0[q] = lds4(zq + k + 8);
-            cols_taps4<TOEP>(w1, w0[q], gr + (q * wG4 + k + 4) * ts, a[q]);
+            cols_taps4<TOEP, GT>(w1, w0[q], gr + (q * wG4 + k + 4) * ts, a[q]);
         }
     }
     if (k < wG4) {
 #pragma unroll
         for (int q = 0; q < K; ++q) {
             const float4 w1 = lds4(zc + q * TC * zsp + k + 4);
-            cols_taps4<TOEP>(w0[q], w1, gr + (q * wG4 + k) * ts, a[q]);
+            cols_taps4<TOEP, GT>(w0[q], w1, gr + (q * wG4 + k) * ts, a[q]);
         }
     }
 #pragma unroll
@@ -271,53 +273,57 @@ __device__ __forceinline__ void epi_load(const ProxArgs &pa, int m, int n, int a
 // tr = (f0, f1, g0, g1): the interior ranges; a non-empty range means the
 // band table is followed by its Toeplitz row (r x w values), which is then
 // staged after the tile with the same tap padding.
-template <bool VEC>
+template <bool VEC, int NTH = NT, int GT = TA>
 __device__ __forceinline__ void stage_bands(const FusedGeom &geo, int r, const float *__restrict__ Fb, int wF,
                                             const float *__restrict__ Gb, int wG, int m, int n, int a0, int c0,
                                             float *Fs, float *Gs, int4 tr) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tr.x < tr.y) {
         const float *tf = Fb + (size_t)r * wF * n;
-        for (int i = tid; i < r * geo.wF4; i += NT) {
+        for (int i = tid; i < r * geo.wF4; i += NTH) {
             const int q = i / geo.wF4, k = i % geo.wF4 - geo.off;
             Fs[(size_t)r * geo.wF4 * TC + i] = k >= 0 && k < wF ? tf[q * wF + k] : 0.f;
         }
     }
     if (tr.z < tr.w) {
         const float *tg = Gb + (size_t)r * wG * m;
-        for (int i = tid; i < r * geo.wG4; i += NT) {
+        for (int i = tid; i < r * geo.wG4; i += NTH) {
             const int q = i / geo.wG4, k = i % geo.wG4;
-            Gs[(size_t)r * geo.wG4 * TA + i] = k < wG ? tg[q * wG + k] : 0.f;
+            Gs[(size_t)r * geo.wG4 * GT + i] = k < wG ? tg[q * wG + k] : 0.f;
         }
     }
     if (VEC) {
+        // F rows: 32 columns = 8 chunks of 4; G rows: GT rows = GT / 4 chunks.
         const int tr = tid >> 3, j = tid & 7;
-        const int fb = c0 + 4 * j < n ? 16 : 0, gb = a0 + 4 * j < m ? 16 : 0;
+        constexpr int JG = GT / 4;
+        const int trg = tid / JG, jg = tid % JG;
+        const int fb = c0 + 4 * j < n ? 16 : 0, gb = a0 + 4 * jg < m ? 16 : 0;
         for (int q = 0; q < r; ++q) {
-            for (int kp = tr; kp < geo.wF4; kp += NT / 8) {
+            for (int kp = tr; kp < geo.wF4; kp += NTH / 8) {
                 const int k = kp - geo.off;
                 const bool ok = k >= 0 && k < wF;
                 band::stage16(Fs + (q * geo.wF4 + kp) * TC + 4 * j,
                               Fb + (size_t)(q * wF + (ok ? k : 0)) * n + c0 + 4 * j, ok ? fb : 0, Fb);
             }
-            for (int kp = tr; kp < geo.wG4; kp += NT / 8) {
+            for (int kp = trg; kp < geo.wG4; kp += NTH / JG) {
                 const bool ok = kp < wG;
-                band::stage16(Gs + (q * geo.wG4 + kp) * TA + 4 * j,
-                              Gb + (size_t)(q * wG + (ok ? kp : 0)) * m + a0 + 4 * j, ok ? gb : 0, Gb);
+                band::stage16(Gs + (q * geo.wG4 + kp) * GT + 4 * jg,
+                              Gb + (size_t)(q * wG + (ok ? kp : 0)) * m + a0 + 4 * jg, ok ? gb : 0, Gb);
             }
         }
     } else {
+        static_assert(VEC || GT == 32, "the element-wise staging covers 32-row coefficient tiles");
         const bool cin = c0 + lane < n, rin = a0 + lane < m;
         for (int q = 0; q < r; ++q) {
-            for (int kp = warp; kp < geo.wF4; kp += NT / 32) {
+            for (int kp = warp; kp < geo.wF4; kp += NTH / 32) {
                 const int k = kp - geo.off;
                 const bool ok = k >= 0 && k < wF;
                 band::stage<float, false>(Fs + (q * geo.wF4 + kp) * TC + lane,
                                           Fb + (size_t)(q * wF + (ok ? k : 0)) * n + c0 + lane, ok && cin, Fb);
             }
-            for (int kp = warp; kp < geo.wG4; kp += NT / 32) {
+            for (int kp = warp; kp < geo.wG4; kp += NTH / 32) {
                 const bool ok = kp < wG;
-                band::stage<float, false>(Gs + (q * geo.wG4 + kp) * TA + lane,
+                band::stage<float, false>(Gs + (q * geo.wG4 + kp) * GT + lane,
                                           Gb + (size_t)(q * wG + (ok ? kp : 0)) * m + a0 + lane, ok && rin, Gb);
             }
         }
@@ -326,7 +332,7 @@ __device__ __forceinline__ void stage_bands(const FusedGeom &geo, int r, const f
 
 // Input tile with its halo: rows e0 .. e0 + zs - 1 (the rest of the 32-row
 // groups zero), columns from the 4-aligned colbase, zero outside the image.
-template <bool VEC>
+template <bool VEC, int NTH = NT>
 __device__ __forceinline__ void stage_input(const FusedGeom &geo, const float *__restrict__ In, int m, int n, int e0,
                                             int colbase, float *Ins) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -335,7 +341,7 @@ __device__ __forceinline__ void stage_input(const FusedGeom &geo, const float *_
         const int nch = width >> 2;
         const int lsh = nch <= 8 ? 3 : (nch <= 16 ? 4 : 5);   // threads per staged row: 1 << lsh
         const int tr = tid >> lsh, tc = tid & ((1 << lsh) - 1);
-        for (int e = tr; e < geo.rows; e += NT >> lsh) {
+        for (int e = tr; e < geo.rows; e += NTH >> lsh) {
             const int ge = e0 + e;
             const bool rok = e < geo.zs && ge >= 0 && ge < m;
             for (int t = tc; t < nch; t += 1 << lsh) {
@@ -346,7 +352,7 @@ __device__ __forceinline__ void stage_input(const FusedGeom &geo, const float *_
             }
         }
     } else {
-        for (int e = warp; e < geo.rows; e += NT / 32) {
+        for (int e = warp; e < geo.rows; e += NTH / 32) {
             const int ge = e0 + e;
             const bool rok = e < geo.zs && ge >= 0 && ge < m;
             for (int s = lane; s < width; s += 32) {
@@ -382,30 +388,34 @@ __device__ __forceinline__ void rows_group(const FusedGeom &geo, int r, const fl
     }
 }
 
-template <bool TOEP>
+template <bool TOEP, int GT>
 __device__ __forceinline__ void cols_group(const FusedGeom &geo, int r, const float *zcol, const float *gbase, int rb,
                                            float *acc) {
     for (int tb = 0; tb < r; tb += 4) {
         const float *zc = zcol + (size_t)tb * TC * geo.zsp;
-        const float *gr = TOEP ? gbase + tb * geo.wG4 : gbase + tb * geo.wG4 * TA + rb;
+        const float *gr = TOEP ? gbase + tb * geo.wG4 : gbase + tb * geo.wG4 * GT + rb;
         switch (min(4, r - tb)) {
-            case 1: cols_pass<1, TOEP>(zc, geo.zsp, gr, geo.wG4, acc); break;
-            case 2: cols_pass<2, TOEP>(zc, geo.zsp, gr, geo.wG4, acc); break;
-            case 3: cols_pass<3, TOEP>(zc, geo.zsp, gr, geo.wG4, acc); break;
-            default: cols_pass<4, TOEP>(zc, geo.zsp, gr, geo.wG4, acc); break;
+            case 1: cols_pass<1, TOEP, GT>(zc, geo.zsp, gr, geo.wG4, acc); break;
+            case 2: cols_pass<2, TOEP, GT>(zc, geo.zsp, gr, geo.wG4, acc); break;
+            case 3: cols_pass<3, TOEP, GT>(zc, geo.zsp, gr, geo.wG4, acc); break;
+            default: cols_pass<4, TOEP, GT>(zc, geo.zsp, gr, geo.wG4, acc); break;
         }
     }
 }
 
 // rel = the interior ranges relative to the tile origin (columns c - c0 for
 // the row pass, rows a - a0 for the column pass).
+// NTH = 512 (the one-launch solver's 16-warp blocks): warps w and w + 8 take
+// the same four columns in the row pass, alternate 64-row groups each; the
+// column pass gives warp w output rows 4w .. 4w + 3 (up to 64 rows).
+template <int NTH, int GT>
 __device__ __forceinline__ void fused_passes(const FusedGeom &geo, int r, const float *Ins, const float *Fs,
                                              const float *Gs, float *Zs, float *acc, int4 rel) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int cb = warp * 4;
+    const int cb = (warp & 7) * 4, half = NTH == 512 ? warp >> 3 : 0;
     const bool toep_f = cb >= rel.x && cb + 4 <= rel.y;   // warp-uniform
     const float *tF = Fs + (size_t)r * geo.wF4 * TC;
-    for (int rbase = 0; rbase < geo.zs; rbase += 64) {
+    for (int rbase = 64 * half; rbase < geo.zs; rbase += 64 * (NTH / 256)) {
         const int e = rbase + lane;
         const bool two = rbase + 32 < geo.zs;
         const float *xa = Ins + e * geo.sp + cb;
@@ -420,9 +430,9 @@ __device__ __forceinline__ void fused_passes(const FusedGeom &geo, int r, const 
     if (rb >= geo.th) return;   // rows beyond a shorter tile: nothing to sum
     const float *zcol = Zs + (size_t)lane * geo.zsp + rb;
     if (rb >= rel.z && rb + 4 <= rel.w)
-        cols_group<true>(geo, r, zcol, Gs + (size_t)r * geo.wG4 * TA, rb, acc);
+        cols_group<true, GT>(geo, r, zcol, Gs + (size_t)r * geo.wG4 * GT, rb, acc);
     else
-        cols_group<false>(geo, r, zcol, Gs, rb, acc);
+        cols_group<false, GT>(geo, r, zcol, Gs, rb, acc);
 }
 
 // Interior ranges (global) -> relative to the tile at (a0, c0).
@@ -460,7 +470,7 @@ __global__ void __launch_bounds__(NT, PRE ? 2 : 0) band_op_fused_kernel(const fl
     band::stage_wait<false>();
     __syncthreads();
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    fused_passes(geo, r, Ins, Fs, Gs, Zs, acc, tile_rel(tr, a0, c0));
+    fused_passes<NT, TA>(geo, r, Ins, Fs, Gs, Zs, acc, tile_rel(tr, a0, c0));
     if (!PRE) epi_load<EPI>(pa, m, n, a0 + rb, gc, bv, yv, xv, beta);
     size_t idx[4];
     bool ok[4];
@@ -553,17 +563,22 @@ struct SolveLayout {
     size_t off_ff, off_gf, off_ft, off_gt, off_z, total;   // float offsets / size
 };
 
+// th <= 32: 256-thread blocks with 32-row coefficient tiles; th > 32: the
+// 512-thread blocks with 64-row tiles.
+__host__ __device__ inline int solve_gt(int th) { return th > TA ? 2 * TA : TA; }
+
 __host__ __device__ inline SolveLayout solve_layout(int r, int loA, int wA, int wB, int loAT, int wAT, int wBT,
                                                     int th) {
     SolveLayout L;
-    L.gf = fused_geom(r, loA, wA, wB, th);
-    L.gt = fused_geom(r, loAT, wAT, wBT, th);
+    const int gt = solve_gt(th);
+    L.gf = fused_geom(r, loA, wA, wB, th, gt);
+    L.gt = fused_geom(r, loAT, wAT, wBT, th, gt);
     const size_t in = (size_t)max(L.gf.rows * L.gf.sp, L.gt.rows * L.gt.sp);
     L.off_ff = in;   // each table followed by its Toeplitz row
     L.off_gf = L.off_ff + (size_t)r * L.gf.wF4 * (TC + 1);
-    L.off_ft = L.off_gf + (size_t)r * L.gf.wG4 * (TA + 1);
+    L.off_ft = L.off_gf + (size_t)r * L.gf.wG4 * (gt + 1);
     L.off_gt = L.off_ft + (size_t)r * L.gt.wF4 * (TC + 1);
-    L.off_z = L.off_gt + (size_t)r * L.gt.wG4 * (TA + 1);
+    L.off_z = L.off_gt + (size_t)r * L.gt.wG4 * (gt + 1);
     L.total = L.off_z + (size_t)r * TC * max(L.gf.zsp, L.gt.zsp);
     return L;
 }
@@ -571,19 +586,23 @@ __host__ __device__ inline SolveLayout solve_layout(int r, int loA, int wA, int 
 // One operator application of the one-launch solver on this block's tile;
 // the geometry and shared-memory offsets come from shared memory (read
 // again in every phase, so they do not hold registers across the loop).
+template <int NTH, int GT>
 __device__ __forceinline__ void solve_phase(const FusedGeom &g, const float *In, int m, int n, int r, int lo_rows,
                                             int lo_cols, size_t off_f, size_t off_g, size_t off_z, float *sm, int a0,
                                             int c0, float *acc, int4 tr) {
-    stage_input<true>(g, In, m, n, a0 + lo_rows, c0 + lo_cols - g.off, sm);
+    stage_input<true, NTH>(g, In, m, n, a0 + lo_rows, c0 + lo_cols - g.off, sm);
     band::stage_wait<false>();
     __syncthreads();
-    fused_passes(g, r, sm, sm + off_f, sm + off_g, sm + off_z, acc, tile_rel(tr, a0, c0));
+    fused_passes<NTH, GT>(g, r, sm, sm + off_f, sm + off_g, sm + off_z, acc, tile_rel(tr, a0, c0));
 }
 
-template <bool BATCH>
-__global__ void __launch_bounds__(NT, 2) band_solve_fused(BandProb one, const BandProb *__restrict__ probs,
-                                                       const int2 *__restrict__ items, int k0, int iters,
-                                                       unsigned *bar) {
+// NTH = 256 threads (tiles up to 32 rows, two blocks per SM) or 512 (tiles
+// of 36 to 64 rows, one block per SM: fewer halo rows per output row in the
+// row pass); GT = the coefficient tile's rows (32 or 64).
+template <bool BATCH, int NTH, int GT>
+__global__ void __launch_bounds__(NTH, NTH == 256 ? 2 : 1)
+    band_solve_fused(BandProb one, const BandProb *__restrict__ probs, const int2 *__restrict__ items, int k0,
+                     int iters, unsigned *bar) {
     extern __shared__ __align__(16) float sm[];
     __shared__ BandProb P;
     __shared__ SolveLayout Ls;
@@ -607,8 +626,10 @@ __global__ void __launch_bounds__(NT, 2) band_solve_fused(BandProb one, const Ba
     const int mt = min(m, a0 + P.th);   // the tile's rows end here
     {
         const SolveLayout L = Ls;
-        stage_bands<true>(L.gf, r, P.fA, P.wA, P.fB, P.wB, m, n, a0, c0, sm + L.off_ff, sm + L.off_gf, P.tfwd);
-        stage_bands<true>(L.gt, r, P.fAT, P.wAT, P.fBT, P.wBT, m, n, a0, c0, sm + L.off_ft, sm + L.off_gt, P.tadj);
+        stage_bands<true, NTH, GT>(L.gf, r, P.fA, P.wA, P.fB, P.wB, m, n, a0, c0, sm + L.off_ff, sm + L.off_gf,
+                                   P.tfwd);
+        stage_bands<true, NTH, GT>(L.gt, r, P.fAT, P.wAT, P.fBT, P.wBT, m, n, a0, c0, sm + L.off_ft, sm + L.off_gt,
+                                   P.tadj);
     }
     const int rb = (threadIdx.x >> 5) * 4, gc = c0 + (threadIdx.x & 31);   // epilogue pixels
     float2 *const Xb0 = const_cast<float2 *>(P.pa.Xin), *const Xb1 = P.pa.Xout;
@@ -644,7 +665,7 @@ __global__ void __launch_bounds__(NT, 2) band_solve_fused(BandProb one, const Ba
                 for (int j = 0; j < 4; ++j) bad |= ok[j] && !isfinite(bv[j]);
                 if (bad) atomicOr(P.pa.status, DEV_NONFINITE);
             } else {
-                solve_phase(Ls.gf, P.pa.Yop, m, n, r, P.loB, P.loA, Ls.off_ff, Ls.off_gf, Ls.off_z, sm, a0, c0,
+                solve_phase<NTH, GT>(Ls.gf, P.pa.Yop, m, n, r, P.loB, P.loA, Ls.off_ff, Ls.off_gf, Ls.off_z, sm, a0, c0,
                             acc, P.tfwd);
             }
 #pragma unroll
@@ -655,7 +676,7 @@ __global__ void __launch_bounds__(NT, 2) band_solve_fused(BandProb one, const Ba
         {   // Adjoint + Step 1 shrink + Step 3 momentum.
             const float2 beta = P.pa.beta[k - 1];
             float acc[4] = {0.f, 0.f, 0.f, 0.f};
-            solve_phase(Ls.gt, P.R, m, n, r, P.loBT, P.loAT, Ls.off_ft, Ls.off_gt, Ls.off_z, sm, a0, c0, acc,
+            solve_phase<NTH, GT>(Ls.gt, P.R, m, n, r, P.loBT, P.loAT, Ls.off_ft, Ls.off_gt, Ls.off_z, sm, a0, c0, acc,
                         P.tadj);
             size_t idx[4];
             bool ok[4];
@@ -777,11 +798,22 @@ int max_dynamic_smem(const void *kernel, int dev) {
     return optin - (int)fa.sharedSizeBytes;
 }
 
+// The solver instance for tiles th rows high: 256 threads up to 32 rows,
+// 512 threads (single problems) above.
+template <bool BATCH>
+const void *solver_kernel(int th) {
+    if (!BATCH && th > TA) return (const void *)band_solve_fused<false, 512, 2 * TA>;
+    return (const void *)band_solve_fused<BATCH, NT, TA>;
+}
+inline int solver_threads(int th) { return th > TA ? 512 : NT; }
+
 // Shared memory and co-residency of the one-launch solver over `np`
 // problems with tiles `th` rows high; false when a tile does not fit, the
 // 16-byte path does not apply or the tiles outnumber the co-resident blocks.
 template <bool BATCH>
 bool solve_fused_fits(const BandProb *probs, int np, int dev, int th, long *tiles, size_t *smem, int *sms) {
+    if (BATCH && th > TA) return false;
+    const void *kernel = solver_kernel<BATCH>(th);
     *tiles = 0;
     *smem = 0;
     for (int p = 0; p < np; ++p) {
@@ -792,28 +824,29 @@ bool solve_fused_fits(const BandProb *probs, int np, int dev, int th, long *tile
     }
     // The attribute is per kernel, not per launch: allow the largest size, so
     // that a later, smaller configuration never lowers an earlier one's limit.
-    const int lim = max_dynamic_smem((const void *)band_solve_fused<BATCH>, dev);
+    const int lim = max_dynamic_smem(kernel, dev);
     if (*smem > (size_t)lim) return false;
-    if (cudaFuncSetAttribute(band_solve_fused<BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) !=
-        cudaSuccess)
-        return false;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess) return false;
     int per_sm = 0, coop = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, band_solve_fused<BATCH>, NT, *smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, solver_threads(th), *smem) != cudaSuccess ||
         cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess)
         return false;
     return coop && per_sm >= 1 && *tiles <= (long)per_sm * *sms;
 }
 
-// Tile height of the one-launch solver: the candidate (32, 28, ..., 16 rows)
-// whose busiest SM has the least pass work, counted as
-//   ceil(tiles / SMs) * (lane_rows(th + wG4) * wF4 + th * wG4)
+// Tile height of the one-launch solver: the candidate (64, 60, ..., 36 rows
+// on 512-thread blocks for single problems; 32, 28, ..., 16 on 256-thread
+// blocks) whose busiest SM has the least pass work, counted as
+//   ceil(tiles / SMs) * W + 0.01 * W * tiles,  W = lane_rows(th + wG4) * wF4 + th * wG4
 // where the row pass covers th + wG4 staged rows in groups of 64 (two rows
 // per lane; a last group of at most 32 rows takes one) and the column pass
 // th rows, both 32 columns wide (widest bands of the problems).  Shorter
 // tiles spread a problem over more SMs (at 512^2, 28-row tiles put two
 // blocks on every SM instead of two on 104 and one on 48).  Ties keep the
-// taller tile.  false when no candidate fits.
+// taller tile.  Taller tiles repeat fewer halo rows in the row pass (at
+// 512^2, 60-row tiles on 144 blocks: 1.34 executed per algorithmic flop
+// against 1.70 for 28-row tiles).  false when no candidate fits.
 template <bool BATCH>
 bool solve_fused_pick(const BandProb *probs, int np, int dev, int *th, long *tiles, size_t *smem) {
     int wF4 = 0, wG4 = 0;
@@ -824,14 +857,19 @@ bool solve_fused_pick(const BandProb *probs, int np, int dev, int *th, long *til
         wG4 = std::max(wG4, std::max(gf.wG4, gt.wG4));
     }
     double best = -1.0;
-    for (int t = TA; t >= 16; t -= 4) {
+    for (int t = BATCH ? TA : 2 * TA; t >= 16; t -= 4) {
         long nt = 0;
         size_t sm = 0;
         int sms = 1;
         if (!solve_fused_fits<BATCH>(probs, np, dev, t, &nt, &sm, &sms)) continue;
         const int zs = t + wG4, rest = zs % 64;
         const int lane_rows = 64 * (zs / 64) + (rest == 0 ? 0 : (rest <= 32 ? 32 : 64));
-        const double cost = (double)((nt + sms - 1) / sms) * ((double)lane_rows * wF4 + (double)t * wG4);
+        const double work = (double)lane_rows * wF4 + (double)t * wG4;
+        // plus a fixed cost per block (its staging and its arrivals at the grid
+        // barrier) of 1 % of a tile's work: among candidates of nearly equal
+        // work the one with fewer blocks wins (measured at 512^2: 64-row tiles
+        // on 128 blocks 14.4 us per iteration, 60-row tiles on 144 blocks 15.0 us)
+        const double cost = (double)((nt + sms - 1) / sms) * work + 0.01 * work * (double)nt;
         if (best < 0.0 || cost < best) {
             best = cost;
             *th = t;
@@ -852,7 +890,7 @@ bool band_solve_fused_config(const BandProb &prob, int dev, int *grid, size_t *s
 }
 
 bool band_solve_fused_config_th(const BandProb &prob, int dev, int th, int *grid, size_t *smem) {
-    if (th < 16 || th > TA || th % 4) return false;
+    if (th < 16 || th > 2 * TA || th % 4) return false;
     long tiles = 0;
     int sms = 0;
     if (!solve_fused_fits<false>(&prob, 1, dev, th, &tiles, smem, &sms)) return false;
@@ -868,7 +906,8 @@ cudaError_t launch_band_solve_fused(int grid, size_t smem, const BandProb &prob,
     const BandProb *probs = nullptr;
     const int2 *items = nullptr;
     void *args[] = {&one, &probs, &items, &k0, &iters, &bar};
-    return cudaLaunchCooperativeKernel((const void *)band_solve_fused<false>, dim3(grid), dim3(NT), args, smem, s);
+    return cudaLaunchCooperativeKernel(solver_kernel<false>(prob.th), dim3(grid), dim3(solver_threads(prob.th)), args,
+                                       smem, s);
 }
 
 bool band_solve_fused_batch_config(const BandProb *probs, int np, int dev, std::vector<int2> *items, size_t *smem,
@@ -890,7 +929,7 @@ cudaError_t launch_band_solve_fused_batch(int nitems, size_t smem, const BandPro
     BandProb one{};
     int k0 = 0;
     void *args[] = {&one, &d_probs, &d_items, &k0, &iters, &bar};
-    return cudaLaunchCooperativeKernel((const void *)band_solve_fused<true>, dim3(nitems), dim3(NT), args, smem, s);
+    return cudaLaunchCooperativeKernel(solver_kernel<true>(TA), dim3(nitems), dim3(NT), args, smem, s);
 }
 
 }  // namespace sfista

@@ -241,6 +241,29 @@ def test_one_launch_solver_band_offsets(psf_shape, centre, r):
     assert np.array_equal(outs["banded_persistent"], outs["banded_fused"])
 
 
+@pytest.mark.parametrize("shape,th", [((512, 512), 28), ((512, 512), 60), ((512, 512), 64), ((200, 176), 16),
+                                      ((200, 176), 36), ((200, 176), 48), ((200, 176), 64)])
+def test_one_launch_solver_every_tile_height(shape, th):
+    """Tile heights of both block sizes of the one-launch solver (256 threads up to 32 rows, 512 threads
+    above; 200 x 176 leaves a ragged last strip) against the oracle, and bit for bit against the
+    two-launch fused form (every pixel's sums are formed in the same order whatever the tiling)."""
+    m, n = shape
+    P = W.rotated_gaussian_psf(31, 3.0, 1.0, np.deg2rad(30))
+    x, b, _ = _problem(m, n, P, 1, 150 + th)
+    ka = kron.kron_approx(P, 15, 15, m, n, 1, 3)
+    L = _oracle_L(ka)
+    Xo = oracle.sfista(b.astype(np.float64), ka, L, 0.005, 30)
+    db = _cuda(b)
+    s = api.Sfista(P, (m, n), 1, 3, prec="fp32", op="banded_persistent", lipschitz=L, tile_override=th)
+    X = s.solve_device(db, 0.005, 30).cpu().numpy()
+    s.close()
+    f = api.Sfista(P, (m, n), 1, 3, prec="fp32", op="banded_fused", lipschitz=L)
+    Xf = f.solve_device(db, 0.005, 30).cpu().numpy()
+    f.close()
+    assert oracle.rel_fro(X, Xo) <= TOL["fp32"]
+    assert np.array_equal(X, Xf)
+
+
 def test_earlier_contexts_keep_their_launch_limits():
     """Kernel attributes are per kernel, not per context or batch: creating a
     context (and a batch) with a smaller shared-memory layout after a larger
