@@ -40,8 +40,8 @@ KERNELS_PER_ITER = {"banded": 4, "banded_fused": 2, "gemm_band": 4, "gemm_dense"
 # ncu capture of the current kernel code on this workload (the summary in
 # profiles/ gives the command); forms without one report null.
 TRAFFIC = {
-    # one 200-iteration solve (one launch) of band_solve_fused, 28-row tiles, cold L2
-    "fp32:banded_persistent:0": {"bytes": 7267584 + 36864,
+    # one 200-iteration solve (one launch) of band_solve_fused, 64-row tiles on 512-thread blocks, cold L2
+    "fp32:banded_persistent:0": {"bytes": 7209472 + 9216,
                                  "source": "profiles/solve_fused_fp32_cfg2_512_r3.md (ncu dram__bytes_read.sum + "
                                            "dram__bytes_write.sum, one 200-iteration launch)"},
 }
