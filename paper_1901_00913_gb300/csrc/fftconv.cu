@@ -58,6 +58,10 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// The passes' dynamic shared memory, addressed by element offsets (32-bit
+// index arithmetic on a shared-space array).
+extern __shared__ __align__(16) float2 fft_sm[];
+
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -188,47 +192,59 @@ __device__ __forceinline__ void dft<8, true>(float2 (&v)[8]) {
     dft8<true>(v);
 }
 
-// One butterfly of a stage: the R points x[k * M], k < R.
-// DIF (forward): DFT, then twiddles w_L^(u q) on outputs u >= 1.
+// One butterfly of a stage: the R points x[k * M], k < R, with the stage's
+// twiddles w[u - 1] = w_L^(u q), u >= 1, already loaded.
+// DIF (forward): DFT, then the twiddles on outputs u >= 1.
 // DIT inverse: conjugate twiddles on inputs u >= 1, then the inverse DFT.
-// tw points at this butterfly's twiddle for u = 1 (shared memory); u's is
-// tw[(u - 1) * M].
 template <int R, bool INV>
-__device__ __forceinline__ void bfly(float2 *x, int M, const float2 *tw) {
+__device__ __forceinline__ void bfly(int x, int M, const float2 (&w)[R > 1 ? R - 1 : 1]) {
     float2 v[R];
 #pragma unroll
-    for (int k = 0; k < R; ++k) v[k] = x[k * M];
+    for (int k = 0; k < R; ++k) v[k] = fft_sm[x + k * M];
     if (INV) {
 #pragma unroll
-        for (int u = 1; u < R; ++u) v[u] = cmulc(v[u], tw[(u - 1) * M]);
+        for (int u = 1; u < R; ++u) v[u] = cmulc(v[u], w[u - 1]);
         dft<R, true>(v);
     } else {
         dft<R, false>(v);
 #pragma unroll
-        for (int u = 1; u < R; ++u) v[u] = cmul(v[u], tw[(u - 1) * M]);
+        for (int u = 1; u < R; ++u) v[u] = cmul(v[u], w[u - 1]);
     }
 #pragma unroll
-    for (int k = 0; k < R; ++k) x[k * M] = v[k];
+    for (int k = 0; k < R; ++k) fft_sm[x + k * M] = v[k];
 }
 
-// x / d for 0 <= x < 2^24 from a float reciprocal, corrected to exact.
-__device__ __forceinline__ int fdiv(int x, int d, float inv) {
-    int q = __float2int_rz((float)x * inv);
-    if (q * d > x) --q;
-    else if ((q + 1) * d <= x) ++q;
-    return q;
+// One stage of radix R over LINES transforms at buf + line * ls: a thread
+// takes butterfly positions (b, q) of the stage and applies each to every
+// line, so the position arithmetic and the twiddle loads are shared by the
+// lines (and the lines' butterflies are independent work for the pipeline).
+template <int R, bool INV, int LINES>
+__device__ __forceinline__ void fft_stage(int buf, int ls, int N, int M, int t) {
+    const int L = R * M, per = N / R, T = blockDim.x;
+    // position bf = b * M + q of the thread's butterflies bf = tid, tid + T, ...:
+    // divided once, then advanced by (T / M, T % M) with a carry
+    const int db = T / M, dq = T - db * M;
+    int b = threadIdx.x / M, q = threadIdx.x - b * M;
+    for (int bf = threadIdx.x; bf < per; bf += T, b += db, q += dq) {
+        if (q >= M) {
+            q -= M;
+            ++b;
+        }
+        float2 w[R - 1];
+#pragma unroll
+        for (int u = 1; u < R; ++u) w[u - 1] = fft_sm[t + (u - 1) * M + q];
+        const int x = buf + b * L + q;
+#pragma unroll
+        for (int line = 0; line < LINES; ++line) bfly<R, INV>(x + line * ls, M, w);
+    }
 }
 
-// One stage of radix R over `lines` transforms: the butterfly loop is
-// specialised on R (no per-butterfly dispatch).
 template <int R, bool INV>
-__device__ __forceinline__ void fft_stage(float2 *buf, int lines, int ls, int N, int M, const float2 *t) {
-    const int L = R * M, per = N / R;
-    const float inv_m = 1.0f / (float)M, inv_per = 1.0f / (float)per;
-    for (int it = threadIdx.x; it < lines * per; it += blockDim.x) {
-        const int line = fdiv(it, per, inv_per), bf = it - line * per;
-        const int b = fdiv(bf, M, inv_m), q = bf - b * M;
-        bfly<R, INV>(buf + (size_t)line * ls + b * L + q, M, t + q);
+__device__ __forceinline__ void fft_stage_lines(int buf, int lines, int ls, int N, int M, int t) {
+    switch (lines) {
+        case 1: fft_stage<R, INV, 1>(buf, ls, N, M, t); break;
+        case 2: fft_stage<R, INV, 2>(buf, ls, N, M, t); break;
+        default: fft_stage<R, INV, 4>(buf, ls, N, M, t); break;
     }
 }
 
@@ -238,17 +254,17 @@ __device__ __forceinline__ void fft_stage(float2 *buf, int lines, int ls, int N,
 // digit-reversed out.  INV: DIT with the stages in reverse order,
 // digit-reversed in, natural out, unscaled.
 template <bool INV>
-__device__ void fft_lines(float2 *buf, int lines, int ls, const FftLine &P, const float2 *tw) {
+__device__ void fft_lines(int buf, int lines, int ls, const FftLine &P, int tw) {
     for (int jj = 0; jj < P.ns; ++jj) {
         const int j = INV ? P.ns - 1 - jj : jj;
         const int M = P.M[j];
-        const float2 *t = tw + P.tw[j];
+        const int t = tw + P.tw[j];
         switch (P.R[j]) {
-            case 2: fft_stage<2, INV>(buf, lines, ls, P.N, M, t); break;
-            case 3: fft_stage<3, INV>(buf, lines, ls, P.N, M, t); break;
-            case 4: fft_stage<4, INV>(buf, lines, ls, P.N, M, t); break;
-            case 5: fft_stage<5, INV>(buf, lines, ls, P.N, M, t); break;
-            default: fft_stage<8, INV>(buf, lines, ls, P.N, M, t); break;
+            case 2: fft_stage_lines<2, INV>(buf, lines, ls, P.N, M, t); break;
+            case 3: fft_stage_lines<3, INV>(buf, lines, ls, P.N, M, t); break;
+            case 4: fft_stage_lines<4, INV>(buf, lines, ls, P.N, M, t); break;
+            case 5: fft_stage_lines<5, INV>(buf, lines, ls, P.N, M, t); break;
+            default: fft_stage_lines<8, INV>(buf, lines, ls, P.N, M, t); break;
         }
         __syncthreads();
     }
@@ -294,44 +310,65 @@ __device__ __forceinline__ size_t tile_index(int s, int f, int H2) {
     return ((size_t)(s >> 3) * H2 + f) * 8 + (s & 7);
 }
 
-// Copies a plan's twiddle table (N - 1 values) and, if pos is non-NULL, the
-// DIF position table (N values) into shared memory.
-__device__ __forceinline__ void stage_tables(const FftLine &P, const float2 *__restrict__ tw_g, float2 *tw,
-                                             const int *__restrict__ pos_g, int *pos) {
-    for (int i = threadIdx.x; i < P.N - 1; i += blockDim.x) tw[i] = __ldg(tw_g + i);
-    if (pos)
-        for (int i = threadIdx.x; i < P.N; i += blockDim.x) pos[i] = __ldg(pos_g + i);
+// Shared layout of a pass (element offsets into fft_sm): `lines` line
+// buffers of N + 1 values (the odd stride spreads the lanes of a stage over
+// the banks) from 0, the twiddle table (N - 1 values) at tw, then (Passes A
+// and C) the position table (N ints) at int offset pos.
+struct PassSmem {
+    int tw, pos;
+};
+__device__ __forceinline__ PassSmem pass_smem(int lines, int N) {
+    PassSmem p;
+    p.tw = lines * (N + 1);
+    p.pos = 2 * (p.tw + N - 1);
+    return p;
+}
+__device__ __forceinline__ int *fft_pos() { return reinterpret_cast<int *>(fft_sm); }
+
+// Copies a plan's twiddle table and, if pos_g is non-NULL, its DIF position
+// table into shared memory.
+__device__ __forceinline__ void stage_tables(const FftLine &P, const float2 *__restrict__ tw_g,
+                                             const int *__restrict__ pos_g, const PassSmem &sm) {
+    for (int i = threadIdx.x; i < P.N - 1; i += blockDim.x) fft_sm[sm.tw + i] = __ldg(tw_g + i);
+    if (pos_g)
+        for (int i = threadIdx.x; i < P.N; i += blockDim.x) fft_pos()[sm.pos + i] = __ldg(pos_g + i);
 }
 
-// Shared layout of a pass: `lines` line buffers of N + 1 values (the odd
-// stride spreads the lanes of a stage over the banks), the twiddle table,
-// then (Passes A and C) the position table.
-struct PassSmem {
-    float2 *buf, *tw;
-    int *pos;
-};
-__device__ __forceinline__ PassSmem pass_smem(void *base, int lines, int N, bool with_pos) {
-    PassSmem p;
-    p.buf = reinterpret_cast<float2 *>(base);
-    p.tw = p.buf + (size_t)lines * (N + 1);
-    p.pos = with_pos ? reinterpret_cast<int *>(p.tw + (N - 1)) : nullptr;
-    return p;
+// Loop over LPC lines x `cols` columns, columns strided over the block's
+// threads in batches of kBatch per thread: each batch's global loads
+// (load(line, col)) are issued before any is used (use(line, col, value)).
+template <int LPC, typename T, typename Load, typename Use>
+__device__ __forceinline__ void batched_lines(int cols, Load load, Use use) {
+    for (int base = threadIdx.x; base < cols; base += kBatch * blockDim.x) {
+#pragma unroll
+        for (int j = 0; j < LPC; ++j) {
+            T v[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int t = base + u * blockDim.x;
+                if (t < cols) v[u] = load(j, t);
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int t = base + u * blockDim.x;
+                if (t < cols) use(j, t, v[u]);
+            }
+        }
+    }
 }
 
 // Pass A: rows (extended rows for the forward operator) -> half spectra S1
-// (8-row tiles).
-template <bool ADJ>
-__global__ void __launch_bounds__(kThreads) fft_pass_a(FftConvDev P, const float *__restrict__ In, int lpc) {
-    extern __shared__ __align__(16) unsigned char fsm[];
+// (8-row tiles).  LPC: complex lines (row pairs) per block.
+template <bool ADJ, int LPC>
+__global__ void __launch_bounds__(kThreads) fft_pass_a(FftConvDev P, const float *__restrict__ In) {
     const int N = P.l2.N, ls = N + 1;
-    const PassSmem sm = pass_smem(fsm, lpc, N, true);
-    stage_tables(P.l2, P.tw2, sm.tw, P.pos2, sm.pos);
+    const PassSmem sm = pass_smem(LPC, N);
+    stage_tables(P.l2, P.tw2, P.pos2, sm);
     const int rows = ADJ ? P.m : P.ext_rows;
-    const int s0 = 2 * blockIdx.x * lpc;   // first row of the block
-    batched<float2>(
-        lpc * N,
-        [&](int it) {
-            const int j = it / N, t = it - j * N;
+    const int s0 = 2 * blockIdx.x * LPC;   // first row of the block
+    batched_lines<LPC, float2>(
+        N,
+        [&](int j, int t) {
             const int s = s0 + 2 * j;
             float2 v = make_float2(0.f, 0.f);
             if (ADJ) {
@@ -350,21 +387,20 @@ __global__ void __launch_bounds__(kThreads) fft_pass_a(FftConvDev P, const float
             }
             return v;
         },
-        [&](int it, float2 v) {
-            const int j = it / N;
-            sm.buf[(size_t)j * ls + (it - j * N)] = v;
-        });
+        [&](int j, int t, float2 v) { fft_sm[j * ls + t] = v; });
     __syncthreads();
-    fft_lines<false>(sm.buf, lpc, ls, P.l2, sm.tw);
+    fft_lines<false>(0, LPC, ls, P.l2, sm.tw);
     // Z = FFT(a + i b): A[f] = (Z[f] + conj Z[N-f]) / 2, B[f] = (Z[f] - conj Z[N-f]) / (2i);
     // the two rows' values at f leave as one 16-byte store, neighbouring
-    // threads taking neighbouring row pairs of the same f.
-    for (int it = threadIdx.x; it < lpc * P.H2; it += blockDim.x) {
-        const int f = it / lpc, j = it - f * lpc;
+    // threads taking neighbouring row pairs of the same f (one contiguous run
+    // per tile of 8 rows).
+    const int *pos = fft_pos() + sm.pos;
+    for (int it = threadIdx.x; it < LPC * P.H2; it += blockDim.x) {
+        const int f = it / LPC, j = it - f * LPC;
         const int s = s0 + 2 * j;
         if (s >= rows) continue;
-        const float2 z1 = sm.buf[(size_t)j * ls + sm.pos[f]];
-        const float2 z2 = sm.buf[(size_t)j * ls + sm.pos[f == 0 ? 0 : N - f]];
+        const float2 z1 = fft_sm[j * ls + pos[f]];
+        const float2 z2 = fft_sm[j * ls + pos[f == 0 ? 0 : N - f]];
         const float4 v = make_float4(0.5f * (z1.x + z2.x), 0.5f * (z1.y - z2.y), 0.5f * (z1.y + z2.y),
                                      0.5f * (z2.x - z1.x));
         *reinterpret_cast<float4 *>(P.S1 + tile_index(s, f, P.H2)) = v;   // s even: 16-byte aligned
@@ -372,18 +408,18 @@ __global__ void __launch_bounds__(kThreads) fft_pass_a(FftConvDev P, const float
 }
 
 // Pass B: frequency lines of S1 -> kernel product along the rows -> S2.
-template <bool ADJ>
-__global__ void __launch_bounds__(kThreads) fft_pass_b(FftConvDev P, int lpc) {
-    extern __shared__ __align__(16) unsigned char fsm[];
+// LPC: neighbouring frequencies per block.
+template <bool ADJ, int LPC>
+__global__ void __launch_bounds__(kThreads) fft_pass_b(FftConvDev P) {
     const int N = P.l1.N, ls = N + 1;
-    const PassSmem sm = pass_smem(fsm, lpc, N, false);
-    stage_tables(P.l1, P.tw1, sm.tw, nullptr, nullptr);
+    const PassSmem sm = pass_smem(LPC, N);
+    stage_tables(P.l1, P.tw1, nullptr, sm);
     const int rows_in = ADJ ? P.m : P.ext_rows;
-    const int f0 = blockIdx.x * lpc;
-    const int run = 8 * lpc;   // contiguous values per 8-row tile: lpc frequencies x 8 rows
+    const int f0 = blockIdx.x * LPC;
+    constexpr int run = 8 * LPC;   // contiguous values per 8-row tile: LPC frequencies x 8 rows
     const int Nt = (N + 7) & ~7;
     batched<float2>(
-        lpc * Nt,
+        LPC * Nt,
         [&](int it) {
             const int sb = it / run, rem = it - sb * run;
             const int j = rem >> 3, s = sb * 8 + (rem & 7);
@@ -393,30 +429,26 @@ __global__ void __launch_bounds__(kThreads) fft_pass_b(FftConvDev P, int lpc) {
         [&](int it, float2 v) {
             const int sb = it / run, rem = it - sb * run;
             const int s = sb * 8 + (rem & 7);
-            if (s < N) sm.buf[(size_t)(rem >> 3) * ls + s] = v;
+            if (s < N) fft_sm[(rem >> 3) * ls + s] = v;
         });
     __syncthreads();
-    fft_lines<false>(sm.buf, lpc, ls, P.l1, sm.tw);
-    batched<float2>(
-        lpc * N,
-        [&](int it) {
-            const int j = it / N, f = f0 + j;
-            return f < P.H2 ? __ldg(P.K + (size_t)f * N + (it - j * N)) : make_float2(0.f, 0.f);
-        },
-        [&](int it, float2 k) {
-            const int j = it / N;
-            float2 &x = sm.buf[(size_t)j * ls + (it - j * N)];
+    fft_lines<false>(0, LPC, ls, P.l1, sm.tw);
+    batched_lines<LPC, float2>(
+        N,
+        [&](int j, int t) { return f0 + j < P.H2 ? __ldg(P.K + (size_t)(f0 + j) * N + t) : make_float2(0.f, 0.f); },
+        [&](int j, int t, float2 k) {
+            float2 &x = fft_sm[j * ls + t];
             x = ADJ ? cmulc(x, k) : cmul(x, k);
         });
     __syncthreads();
-    fft_lines<true>(sm.buf, lpc, ls, P.l1, sm.tw);
+    fft_lines<true>(0, LPC, ls, P.l1, sm.tw);
     const int mt = (P.m + 7) & ~7;
-    for (int it = threadIdx.x; it < lpc * mt; it += blockDim.x) {
+    for (int it = threadIdx.x; it < LPC * mt; it += blockDim.x) {
         const int ab = it / run, rem = it - ab * run;
         const int j = rem >> 3, a = ab * 8 + (rem & 7);
         const int f = f0 + j;
         if (f >= P.H2 || a >= P.m) continue;
-        const float2 *u = sm.buf + (size_t)j * ls;
+        const float2 *u = fft_sm + j * ls;
         float2 v;
         if (ADJ) {
             // extended rows s with ext(s - offr) = a: s = a + offr, and for the
@@ -435,82 +467,104 @@ __global__ void __launch_bounds__(kThreads) fft_pass_b(FftConvDev P, int lpc) {
 }
 
 // Pass C: two rows' half spectra -> one inverse FFT -> the two output rows,
-// then the epilogue.
-template <bool ADJ, int EPI>
-__global__ void __launch_bounds__(kThreads) fft_pass_c(FftConvDev P, float *__restrict__ Out, ProxArgs pa, int lpc) {
-    extern __shared__ __align__(16) unsigned char fsm[];
+// then the epilogue.  LPC: row pairs per block.
+template <bool ADJ, int EPI, int LPC>
+__global__ void __launch_bounds__(kThreads) fft_pass_c(FftConvDev P, float *__restrict__ Out, ProxArgs pa) {
     const int N = P.l2.N, ls = N + 1;
-    const PassSmem sm = pass_smem(fsm, lpc, N, true);
-    stage_tables(P.l2, P.tw2, sm.tw, P.pos2, sm.pos);
+    const PassSmem sm = pass_smem(LPC, N);
+    stage_tables(P.l2, P.tw2, P.pos2, sm);
     __syncthreads();
-    const int a0 = 2 * blockIdx.x * lpc;
+    const int a0 = 2 * blockIdx.x * LPC;
+    const int *pos = fft_pos() + sm.pos;
     batched<float4>(
-        lpc * N,
+        LPC * N,
         [&](int it) {
-            const int f = it / lpc, j = it - f * lpc;   // neighbouring threads: neighbouring row pairs
+            const int f = it / LPC, j = it - f * LPC;   // neighbouring threads: neighbouring row pairs
             const int a = a0 + 2 * j;
             const int g = f >= P.H2 ? N - f : f;
             return a < P.m ? __ldcg(reinterpret_cast<const float4 *>(P.S2 + tile_index(a, g, P.H2)))
                            : make_float4(0.f, 0.f, 0.f, 0.f);
         },
         [&](int it, float4 y) {
-            const int f = it / lpc, j = it - f * lpc;
+            const int f = it / LPC, j = it - f * LPC;
             if (f >= P.H2) {   // Y[f] = conj Y[N - f] for a real row
                 y.y = -y.y;
                 y.w = -y.w;
             }
             // Y_a + i Y_{a+1}; row a + 1 past the image reads the zero padding of S2
-            sm.buf[(size_t)j * ls + sm.pos[f]] = make_float2(y.x - y.w, y.y + y.z);
+            fft_sm[j * ls + pos[f]] = make_float2(y.x - y.w, y.y + y.z);
         });
     __syncthreads();
-    fft_lines<true>(sm.buf, lpc, ls, P.l2, sm.tw);
-    // Output pixels, kEpi per thread at a time (their state / observation
-    // loads issued together): pixel `it` of the block is row a0 + it / n.
+    fft_lines<true>(0, LPC, ls, P.l2, sm.tw);
+    // Output pixels of each of the block's 2 LPC rows, kEpi per thread at a
+    // time (their state / observation loads issued together).
     const int n = P.n;
     constexpr int kEpi = 4;
-    const int total = lpc * 2 * n;
-    for (int base = threadIdx.x; base < total; base += kEpi * blockDim.x) {
-        float g[kEpi];
-        size_t idx[kEpi];
-        bool ok[kEpi];
+#pragma unroll 1
+    for (int rr = 0; rr < 2 * LPC; ++rr) {
+        const int a = a0 + rr;
+        if (a >= P.m) break;
+        const float2 *ub = fft_sm + (rr >> 1) * ls;
+        for (int base = threadIdx.x; base < n; base += kEpi * blockDim.x) {
+            float g[kEpi];
+            size_t idx[kEpi];
+            bool ok[kEpi];
 #pragma unroll
-        for (int u = 0; u < kEpi; ++u) {
-            const int it = base + u * blockDim.x;
-            const int rr = it / n, b = it - rr * n;   // rr: row within the block
-            const int a = a0 + rr;
-            ok[u] = it < total && a < P.m;
-            idx[u] = (size_t)a * n + b;
-            g[u] = 0.f;
-            if (!ok[u]) continue;
-            const float2 *ub = sm.buf + (size_t)(rr >> 1) * ls;
-            float2 w;
-            if (ADJ) {
-                w = ub[b + P.offc];
-                if (P.bc) {
-                    const int t1 = P.offc - 1 - b, t2 = 2 * n - 1 - b + P.offc;
-                    if (t1 >= 0) w = cadd(w, ub[t1]);
-                    if (t2 < P.ext_cols) w = cadd(w, ub[t2]);
+            for (int u = 0; u < kEpi; ++u) {
+                const int b = base + u * blockDim.x;
+                ok[u] = b < n;
+                idx[u] = (size_t)a * n + b;
+                g[u] = 0.f;
+                if (!ok[u]) continue;
+                float2 w;
+                if (ADJ) {
+                    w = ub[b + P.offc];
+                    if (P.bc) {
+                        const int t1 = P.offc - 1 - b, t2 = 2 * n - 1 - b + P.offc;
+                        if (t1 >= 0) w = cadd(w, ub[t1]);
+                        if (t2 < P.ext_cols) w = cadd(w, ub[t2]);
+                    }
+                } else {
+                    w = ub[b];
                 }
-            } else {
-                w = ub[b];
+                g[u] = (rr & 1) ? w.y : w.x;
             }
-            g[u] = (rr & 1) ? w.y : w.x;
-        }
-        if (EPI == EPI_STORE) {
+            if (EPI == EPI_STORE) {
 #pragma unroll
-            for (int u = 0; u < kEpi; ++u)
-                if (ok[u]) Out[idx[u]] = g[u];
-        } else if (EPI == EPI_RESIDUAL) {
-            float bv[kEpi];
+                for (int u = 0; u < kEpi; ++u)
+                    if (ok[u]) Out[idx[u]] = g[u];
+            } else if (EPI == EPI_RESIDUAL) {
+                float bv[kEpi];
 #pragma unroll
-            for (int u = 0; u < kEpi; ++u) bv[u] = ok[u] ? __ldcg(pa.Bd + idx[u]) : 0.f;
+                for (int u = 0; u < kEpi; ++u) bv[u] = ok[u] ? __ldcg(pa.Bd + idx[u]) : 0.f;
 #pragma unroll
-            for (int u = 0; u < kEpi; ++u)
-                if (ok[u]) Out[idx[u]] = g[u] - bv[u];
-        } else {
-            prox_momentum_n<kEpi>(pa, idx, g, ok);
+                for (int u = 0; u < kEpi; ++u)
+                    if (ok[u]) Out[idx[u]] = g[u] - bv[u];
+            } else {
+                prox_momentum_n<kEpi>(pa, idx, g, ok);
+            }
         }
     }
+}
+
+// Kernel instances by lines per block (1, 2, 4).
+template <bool ADJ>
+void launch_a(int lpc, int grid, size_t smem, cudaStream_t s, const FftConvDev &d, const float *In) {
+    if (lpc == 4) fft_pass_a<ADJ, 4><<<grid, kThreads, smem, s>>>(d, In);
+    else if (lpc == 2) fft_pass_a<ADJ, 2><<<grid, kThreads, smem, s>>>(d, In);
+    else fft_pass_a<ADJ, 1><<<grid, kThreads, smem, s>>>(d, In);
+}
+template <bool ADJ>
+void launch_b(int lpc, int grid, size_t smem, cudaStream_t s, const FftConvDev &d) {
+    if (lpc == 4) fft_pass_b<ADJ, 4><<<grid, kThreads, smem, s>>>(d);
+    else if (lpc == 2) fft_pass_b<ADJ, 2><<<grid, kThreads, smem, s>>>(d);
+    else fft_pass_b<ADJ, 1><<<grid, kThreads, smem, s>>>(d);
+}
+template <bool ADJ, int EPI>
+void launch_c(int lpc, int grid, size_t smem, cudaStream_t s, const FftConvDev &d, float *Out, const ProxArgs &pa) {
+    if (lpc == 4) fft_pass_c<ADJ, EPI, 4><<<grid, kThreads, smem, s>>>(d, Out, pa);
+    else if (lpc == 2) fft_pass_c<ADJ, EPI, 2><<<grid, kThreads, smem, s>>>(d, Out, pa);
+    else fft_pass_c<ADJ, EPI, 1><<<grid, kThreads, smem, s>>>(d, Out, pa);
 }
 
 // ------------------------------------------------------------------ host plan
@@ -601,14 +655,13 @@ size_t pass_smem_bytes(int lines, int N, bool with_pos) {
     return sizeof(float2) * ((size_t)lines * (N + 1) + (N - 1)) + (with_pos ? sizeof(int) * N : 0);
 }
 
-// Lines per block (row pairs in Passes A and C, frequencies in Pass B): 2
-// when that still gives a block per SM, so a block's run in each 8-row tile
-// of the spectra is 32 (A, C) or 128 (B) contiguous bytes, else 1.  A block
-// stays within `budget` bytes of shared memory where it can (three or more
-// blocks per SM hide the latency of the transforms' shared-memory stages
-// better than two blocks of four lines).
+// Lines per block (row pairs in Passes A and C, frequencies in Pass B): 4
+// when that still gives a block per SM, else 2, else 1.  More lines per
+// block share each butterfly's position arithmetic and twiddle loads and
+// make longer contiguous runs in the 8-row tiles of the spectra (64 / 256
+// bytes at 4 lines).  A block stays within `budget` bytes of shared memory.
 int pick_lpc(long lines, int N, int sms, bool with_pos, size_t budget) {
-    const int cand[2] = {2, 1};
+    const int cand[3] = {4, 2, 1};
     for (int lpc : cand) {
         if (lpc > 1 && pass_smem_bytes(lpc, N, with_pos) > budget) continue;
         if (lpc == 1 || (lines + lpc - 1) / lpc >= (long)sms) return lpc;
@@ -620,9 +673,26 @@ int pick_lpc(long lines, int N, int sms, bool with_pos, size_t budget) {
 // the device's per-block maximum once, so a later, smaller plan never lowers
 // an earlier one's limit.
 template <typename K>
-cudaError_t allow_smem(K kernel, size_t bytes, int limit) {
-    if (bytes > (size_t)limit) return cudaErrorInvalidValue;
+cudaError_t allow_smem(K kernel, int limit) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
+}
+template <int LPC>
+cudaError_t allow_smem_lpc(int limit) {
+    cudaError_t e;
+    if ((e = allow_smem(fft_pass_a<false, LPC>, limit)) || (e = allow_smem(fft_pass_a<true, LPC>, limit)) ||
+        (e = allow_smem(fft_pass_b<false, LPC>, limit)) || (e = allow_smem(fft_pass_b<true, LPC>, limit)) ||
+        (e = allow_smem(fft_pass_c<false, EPI_STORE, LPC>, limit)) ||
+        (e = allow_smem(fft_pass_c<false, EPI_RESIDUAL, LPC>, limit)) ||
+        (e = allow_smem(fft_pass_c<true, EPI_STORE, LPC>, limit)) ||
+        (e = allow_smem(fft_pass_c<true, EPI_PROX, LPC>, limit)))
+        return e;
+    return cudaSuccess;
+}
+cudaError_t allow_smem_all(size_t sa, size_t sb, size_t sc, int limit) {
+    if (sa > (size_t)limit || sb > (size_t)limit || sc > (size_t)limit) return cudaErrorInvalidValue;
+    cudaError_t e;
+    if ((e = allow_smem_lpc<1>(limit)) || (e = allow_smem_lpc<2>(limit)) || (e = allow_smem_lpc<4>(limit))) return e;
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -706,17 +776,13 @@ sfista_status fftconv_create(FftConv **out, const double *K, int p, int q, int c
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t budget = 64 * 1024;
+    const size_t budget = 110 * 1024;
     f->lpc_a = pick_lpc((d.ext_rows + 1) / 2, N2, sms, true, budget);
     f->lpc_b = pick_lpc(H2, N1, sms, false, budget);
     f->lpc_c = pick_lpc((m + 1) / 2, N2, sms, true, budget);
     const size_t sa = pass_smem_bytes(f->lpc_a, N2, true), sb = pass_smem_bytes(f->lpc_b, N1, false),
                  sc = pass_smem_bytes(f->lpc_c, N2, true);
-    if ((e = allow_smem(fft_pass_a<false>, sa, optin)) || (e = allow_smem(fft_pass_a<true>, sa, optin)) ||
-        (e = allow_smem(fft_pass_b<false>, sb, optin)) || (e = allow_smem(fft_pass_b<true>, sb, optin)) ||
-        (e = allow_smem(fft_pass_c<false, EPI_STORE>, sc, optin)) ||
-        (e = allow_smem(fft_pass_c<false, EPI_RESIDUAL>, sc, optin)) ||
-        (e = allow_smem(fft_pass_c<true, EPI_STORE>, sc, optin)) || (e = allow_smem(fft_pass_c<true, EPI_PROX>, sc, optin))) {
+    if ((e = allow_smem_all(sa, sb, sc, optin))) {
         fftconv_destroy(f);
         return fail(SFISTA_ENOTSUP, std::string("FFT form shared memory: ") + cudaGetErrorString(e));
     }
@@ -741,29 +807,29 @@ void fftconv_part(const FftConv *f, int part, bool adj, const float *In, EpiKind
         const int ga = (int)(((rows + 1) / 2 + f->lpc_a - 1) / f->lpc_a);
         const size_t sa = pass_smem_bytes(f->lpc_a, d.l2.N, true);
         if (adj)
-            fft_pass_a<true><<<ga, kThreads, sa, s>>>(d, In, f->lpc_a);
+            launch_a<true>(f->lpc_a, ga, sa, s, d, In);
         else
-            fft_pass_a<false><<<ga, kThreads, sa, s>>>(d, In, f->lpc_a);
+            launch_a<false>(f->lpc_a, ga, sa, s, d, In);
         const int gb = (d.H2 + f->lpc_b - 1) / f->lpc_b;
         const size_t sb = pass_smem_bytes(f->lpc_b, d.l1.N, false);
         if (adj)
-            fft_pass_b<true><<<gb, kThreads, sb, s>>>(d, f->lpc_b);
+            launch_b<true>(f->lpc_b, gb, sb, s, d);
         else
-            fft_pass_b<false><<<gb, kThreads, sb, s>>>(d, f->lpc_b);
+            launch_b<false>(f->lpc_b, gb, sb, s, d);
         return;
     }
     const int gc = ((d.m + 1) / 2 + f->lpc_c - 1) / f->lpc_c;
     const size_t sc = pass_smem_bytes(f->lpc_c, d.l2.N, true);
     if (adj) {
         if (epi == EPI_PROX)
-            fft_pass_c<true, EPI_PROX><<<gc, kThreads, sc, s>>>(d, Out, pa, f->lpc_c);
+            launch_c<true, EPI_PROX>(f->lpc_c, gc, sc, s, d, Out, pa);
         else
-            fft_pass_c<true, EPI_STORE><<<gc, kThreads, sc, s>>>(d, Out, pa, f->lpc_c);
+            launch_c<true, EPI_STORE>(f->lpc_c, gc, sc, s, d, Out, pa);
     } else {
         if (epi == EPI_RESIDUAL)
-            fft_pass_c<false, EPI_RESIDUAL><<<gc, kThreads, sc, s>>>(d, Out, pa, f->lpc_c);
+            launch_c<false, EPI_RESIDUAL>(f->lpc_c, gc, sc, s, d, Out, pa);
         else
-            fft_pass_c<false, EPI_STORE><<<gc, kThreads, sc, s>>>(d, Out, pa, f->lpc_c);
+            launch_c<false, EPI_STORE>(f->lpc_c, gc, sc, s, d, Out, pa);
     }
 }
 
