@@ -986,6 +986,45 @@ def config4_section(args, torch):
             "prep_s": prep_s}
 
 
+def wide_section(args, torch, peaks):
+    """512^2 with a 127 x 127 PSF (p about n / 4), r = 3, 200 iterations: the regime where the FFT
+    form's cost (independent of the PSF width) beats the band forms'.  Each form's error against
+    the FP64 oracle on the first 10 iterations; the CPU-baseline leg forms the observation with the
+    oracle's exact blur and runs those 10 oracle iterations."""
+    import oracle
+    from oracle import kron
+    from paper_1901_00913_gb300 import api, workloads as W
+    pr = W.wide_psf()
+    n, r, iters, check = 512, pr.r, pr.iters, 10
+    cr, cc = pr.centre
+    bx = oracle.blur(pr.x_true, pr.psf, cr, cc, pr.bc)
+    b = (bx + W.noise_scale(bx, pr.noise, pr.noise_level)).astype(np.float32)
+    ka = kron.kron_approx(pr.psf, cr, cc, n, n, pr.bc, r)
+    db = torch.from_numpy(b).cuda()
+    s0 = api.Sfista(pr.psf, (n, n), pr.bc, r, prec="fp32", op="banded", lipschitz_tol=1e-8, lipschitz_maxit=300)
+    L = s0.info()["lipschitz"]
+    s0.close()
+    t0 = time.perf_counter()
+    Xo = oracle.sfista(b.astype(np.float64), ka, L, pr.lam, check)
+    cpu_s = time.perf_counter() - t0
+    steps = max(1, min(args.steps, 5))
+    forms = {}
+    for f in ("fp32:auto+tune", "fp32:banded", "fp32:fft", "bf16x3:gemm_band"):
+        prec, op, tune = _form(f)
+        s = api.Sfista(pr.psf, (n, n), pr.bc, r, prec=prec, op=op, lipschitz=L)
+        if tune:
+            s.tune(iters=5)
+        err = oracle.rel_fro(s.solve_device(db, pr.lam, check).cpu().numpy(), Xo)
+        v, _, _ = _solve_rate(s, db, pr.lam, iters, steps, 3, torch)
+        forms[f] = {"resolved_op": s.info()["op"], "iters_per_s": v,
+                    "rel_err_vs_oracle_first_%d_its" % check: err}
+        s.close()
+    return {"workload": "512x512 reflexive, 127x127 mixture+Moffat PSF, r=3, lambda=0.005, 1% noise, 200 its",
+            "unit": "iters/s", "steps": steps, "forms": forms,
+            "cpu_baseline": {"value": check / cpu_s, "unit": "iters/s", "kind": "oracle", "cores": _cores(),
+                             "sample": "%d of the 200 iterations" % check}}
+
+
 def _cores():
     from oracle import _native
     return _native.threads()
@@ -1002,7 +1041,7 @@ def main():
     ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "cfg4", "cfg5", "ex2", "fft"])
     ap.add_argument("--check-iters", type=int, default=10)
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the 2048^2 and batched sections of the default line")
+                    help="skip the 2048^2, batched and wide-PSF sections of the default line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -1196,6 +1235,7 @@ def main():
         # timed region): where the tensor-core and batched targets are stated.
         line["config3"] = config3_section(args, torch, peaks)
         line["config4"] = config4_section(args, torch)
+        line["wide_psf"] = wide_section(args, torch, peaks)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

@@ -258,6 +258,18 @@ def config4(seed=SEED_BASE + 4, count=64, sizes=(256, 384, 512, 768, 1024)):
     return out
 
 
+def wide_psf(seed=SEED_BASE + 7, n=512, p=127):
+    """Config 2's image with a p x p mixture + Moffat PSF (p about n / 4: a PSF wide enough that the
+    band forms' cost per pixel, which grows with p, exceeds the FFT form's), reflective, r=3,
+    lam 0.005, 1 %, 200 its."""
+    pr = config2(n=n)
+    g = rng(seed)
+    pr.name = "wide_%d_p%d_r3" % (n, p)
+    pr.psf = mixture_moffat_psf(g, p)
+    pr.noise = noise_draw(g, n, n)
+    return pr
+
+
 def config5(seed=SEED_BASE + 2, n=512):
     """Config 2's problem (same seed) unrolled for 50 iterations (checkpoint every 10) for gradients."""
     pr = config2(seed=seed, n=n)
