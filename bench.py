@@ -1012,12 +1012,14 @@ def wide_section(args, torch, peaks):
     for f in ("fp32:auto+tune", "fp32:banded", "fp32:fft", "bf16x3:gemm_band"):
         prec, op, tune = _form(f)
         s = api.Sfista(pr.psf, (n, n), pr.bc, r, prec=prec, op=op, lipschitz=L)
-        if tune:
-            s.tune(iters=5)
+        tuned = s.tune(iters=5) if tune else None
         err = oracle.rel_fro(s.solve_device(db, pr.lam, check).cpu().numpy(), Xo)
         v, _, _ = _solve_rate(s, db, pr.lam, iters, steps, 3, torch)
         forms[f] = {"resolved_op": s.info()["op"], "iters_per_s": v,
                     "rel_err_vs_oracle_first_%d_its" % check: err}
+        if tuned is not None:
+            forms[f]["tuned_whole_iteration_ms"] = {e["op"] + ("" if not e["chunk"] else ":%d" % e["chunk"]): e["ms"]
+                                                    for e in tuned if e["stage"] == -1}
         s.close()
     return {"workload": "512x512 reflexive, 127x127 mixture+Moffat PSF, r=3, lambda=0.005, 1% noise, 200 its",
             "unit": "iters/s", "steps": steps, "forms": forms,
