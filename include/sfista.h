@@ -384,7 +384,7 @@ sfista_status sfista_info(const sfista_ctx *ctx, double *lipschitz,
 sfista_status sfista_set_factors(sfista_ctx *ctx, const double *A, const double *B);
 
 /* Factor profiles: C (r x psf_rows) column profiles c_k of the left factors,
- * D (r x psf_cols) row profiles d_k of the right factors (host, FP64). */
+ * D (r x psf_cols) row profiles d_k of the right factors (host, FP64). *
 sfista_status sfista_get_profiles(const sfista_ctx *ctx, double *C, double *D);
 
 /* Dense factors on the host, FP64: B (r x m x m), A (r x n x n). */
