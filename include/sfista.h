@@ -135,6 +135,19 @@ typedef struct {
                                SFISTA_EINVAL otherwise; ignored where the one-launch fused
                                solver is not used, and the two-pass persistent form is
                                used instead if those tiles do not all fit).             */
+    int gemm_bn;            /* tensor-core forms: N tile width of the summed stages 1 and
+                               3 (the left-factor products): 0 (default) = 128; 64, 128
+                               or 256 (SFISTA_EINVAL otherwise).  Wider tiles read each
+                               factor block once for more columns, narrower ones spread
+                               the tiles more evenly over the SMs; sfista_tune measures
+                               all three.                                               */
+    int gemm_stream_panels; /* tensor-core forms, stacked stages 0 and 2 (the right-factor
+                               products): 0 (default) keeps each row tile's factor panel
+                               (all K blocks of its band, hi and lo) resident in shared
+                               memory while the tiles that share it run, where that is
+                               possible (BF16 and BF16x3 band mode, every band within
+                               three K blocks of 64); 1 streams the panel with every
+                               tile.  sfista_tune measures both.                        */
 } sfista_opts;
 
 /* Fill *opts with the defaults listed above. */
@@ -435,7 +448,10 @@ typedef struct {
                           -1: whole iterations                                         */
     int chunk;         /* terms staged per block in that stage (two-pass banded form);
                           for SFISTA_OP_BANDED_PERSISTENT entries the one-launch
-                          solver's tile height th; 0 where neither applies            */
+                          solver's tile height th; for tensor-core stage entries the
+                          N tile width (stages 1, 3) or 1 / 0 for a resident / streamed
+                          factor panel (stages 0, 2; batch entries: stage -1);
+                          0 where none applies                                         */
     float ms;          /* mean time per stage (or per iteration), ms                  */
 } sfista_tune_entry;
 
@@ -454,7 +470,11 @@ typedef struct {
  *     solver (SFISTA_OP_BANDED_PERSISTENT, timed per iteration over
  *     max(iters, 40) iterations of one launch, for every tile height th);
  *     tensor-core contexts compare the band-limited and full (dense) K
- *     ranges.
+ *     ranges;
+ *   - tensor-core forms: for each stage, timed alone in the chosen K range,
+ *     the tile shapes gemm_bn and gemm_stream_panels select between (N tile
+ *     64, 128 or 256 for stages 1 and 3; resident or streamed factor panel
+ *     for stages 0 and 2 where the panel fits).
  * An explicitly chosen form is kept (only its stages are tuned).  The chosen
  * configuration applies to later solves, sfista_apply and batches created
  * afterwards (sfista_info reports the form).
@@ -482,7 +502,11 @@ sfista_status sfista_tune(sfista_ctx *ctx, int iters, sfista_tune_entry *entries
  * op = SFISTA_OP_BANDED with chunk = the budget in KB (0: each problem's own
  * chunks), or op = SFISTA_OP_BANDED_PERSISTENT (chunk 0) for the one-launch
  * plan.
- * Tensor-core batches have a single tile shape: no entries, SFISTA_OK.
+ * Tensor-core batches: when every problem allows resident factor panels in
+ * the grouped stages 0 and 2 (BF16 band mode, bands within three K blocks),
+ * the batch solve is timed with resident and with streamed panels (entries:
+ * op = the problems' form, stage -1, chunk 1 / 0) and the faster is kept;
+ * otherwise there is nothing to choose (no entries, SFISTA_OK).
  * Synchronous.  Leaves every grouped context's state undefined.
  */
 sfista_status sfista_batch_tune(sfista_batch *batch, int iters, sfista_tune_entry *entries, int max_entries,

@@ -39,7 +39,8 @@ class Opts(ctypes.Structure):
                 ("use_graph", ctypes.c_int), ("lipschitz", ctypes.c_double),
                 ("lipschitz_tol", ctypes.c_double), ("lipschitz_maxit", ctypes.c_int),
                 ("device", ctypes.c_int), ("l1", ctypes.c_double), ("refine_every", ctypes.c_int),
-                ("tile_override", ctypes.c_int)]
+                ("tile_override", ctypes.c_int), ("gemm_bn", ctypes.c_int),
+                ("gemm_stream_panels", ctypes.c_int)]
 
 
 def load(path=None):
@@ -292,11 +293,13 @@ def sfista_tune(ctx, iters=10, max_entries=64):
 def sfista_batch_tune(handle, iters=5, max_entries=64):
     """Batch autotuner (see include/sfista.h): one dict per plan; "op" names the
     plan's form (banded: grouped launches with a shared-memory budget of
-    budget_kb KB; banded_persistent: the whole batch in one launch)."""
+    budget_kb KB; banded_persistent: the whole batch in one launch; tensor-core
+    forms: "chunk" 1 / 0 for resident / streamed factor panels)."""
     buf = (TuneEntry * max_entries)()
     cnt = ctypes.c_int(0)
     _check(load().sfista_batch_tune(ctypes.c_void_p(handle), int(iters), buf, int(max_entries), ctypes.byref(cnt)))
-    return [{"op": OP_NAME.get(e.op, e.op), "budget_kb": e.chunk, "ms": e.ms} for e in buf[:min(cnt.value, max_entries)]]
+    return [{"op": OP_NAME.get(e.op, e.op), "budget_kb": e.chunk, "chunk": e.chunk, "ms": e.ms}
+            for e in buf[:min(cnt.value, max_entries)]]
 
 
 def sfista_apply_static(d_x, d_y, r, band_right, lo_right, band_left, lo_left, stream=None):
@@ -460,7 +463,7 @@ class Sfista:
 
     def __init__(self, psf, shape, bc, r, center=(-1, -1), prec="fp32", op="auto", project=False,
                  use_graph=True, lipschitz=None, lipschitz_tol=1e-10, lipschitz_maxit=1000, device=-1, l1=0.0,
-                 refine_every=0, tile_override=0, exact=False):
+                 refine_every=0, tile_override=0, exact=False, gemm_bn=0, gemm_stream_panels=False):
         """exact=True: the exact blur A instead of the rank-r approximation (sfista_setup_exact; r unused)."""
         o = default_opts()
         o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
@@ -474,6 +477,8 @@ class Sfista:
         o.l1 = float(l1)
         o.refine_every = int(refine_every)
         o.tile_override = int(tile_override)
+        o.gemm_bn = int(gemm_bn)
+        o.gemm_stream_panels = int(bool(gemm_stream_panels))
         bcv = BC[bc] if isinstance(bc, str) else int(bc)
         self.shape = (int(shape[0]), int(shape[1]))
         self.psf_shape = np.asarray(psf).shape

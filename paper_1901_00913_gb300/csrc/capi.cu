@@ -651,6 +651,8 @@ void sfista_default_opts(sfista_opts *o) {
     o->l1 = 0.0;
     o->refine_every = 0;
     o->tile_override = 0;
+    o->gemm_bn = 0;
+    o->gemm_stream_panels = 0;
 }
 
 sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int center_row,
@@ -669,6 +671,10 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int ce
     if (o.refine_every < 0) return fail(SFISTA_EINVAL, "refine_every must be >= 0");
     if (o.tile_override != 0 && (o.tile_override < 16 || o.tile_override > 64 || o.tile_override % 4))
         return fail(SFISTA_EINVAL, "tile_override must be 0 or a multiple of 4 from 16 to 64");
+    if (o.gemm_bn != 0 && o.gemm_bn != 64 && o.gemm_bn != 128 && o.gemm_bn != 256)
+        return fail(SFISTA_EINVAL, "gemm_bn must be 0, 64, 128 or 256");
+    if (o.gemm_stream_panels != 0 && o.gemm_stream_panels != 1)
+        return fail(SFISTA_EINVAL, "gemm_stream_panels must be 0 or 1");
     if (center_row == -1 && psf_rows > 0) center_row = (psf_rows - 1) / 2;
     if (center_col == -1 && psf_cols > 0) center_col = (psf_cols - 1) / 2;
     sfista_ctx *c = new (std::nothrow) sfista_ctx();
@@ -788,6 +794,11 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int ce
     if (c->op == SFISTA_OP_GEMM_BAND || c->op == SFISTA_OP_GEMM_DENSE) {
         st = gemm_create(&c->gemm, h, c->prec, c->op == SFISTA_OP_GEMM_DENSE, c->status, c->stream);
         if (st) return bail(st);
+        const int bn = o.gemm_bn ? o.gemm_bn : 128;
+        gemm_set_tile(c->gemm, 1, bn, 0);
+        gemm_set_tile(c->gemm, 3, bn, 0);
+        gemm_set_tile(c->gemm, 0, 128, !o.gemm_stream_panels);
+        gemm_set_tile(c->gemm, 2, 128, !o.gemm_stream_panels);
         // FP32 state for the forms whose products are far coarser than FP32
         // (BF16, BF16x3, TF32); TF32x3 keeps the double-float state, which its
         // products are accurate enough to use (1.9e-6 vs 1.7e-5 at 512^2).
@@ -1392,7 +1403,7 @@ sfista_status sfista_batch_tune(sfista_batch *b, int iters, sfista_tune_entry *e
     if (!b) return fail(SFISTA_EINVAL, "batch is NULL");
     if (n_entries) *n_entries = 0;
     if (iters < 1 || max_entries < 0) return fail(SFISTA_EINVAL, "iters must be >= 1 and max_entries >= 0");
-    if (b->gemm) return SFISTA_OK;   // one tile shape: nothing to choose
+    if (b->gemm && !gemm_batch_res_ok(b->gb)) return SFISTA_OK;   // one tile shape: nothing to choose
     DeviceGuard g(b->dev);
     const int np = (int)b->ctxs.size();
     std::vector<const float *> d_b(np);
@@ -1407,6 +1418,46 @@ sfista_status sfista_batch_tune(sfista_batch *b, int iters, sfista_tune_entry *e
     cudaEvent_t e0, e1;
     SF_CUDA(cudaEventCreate(&e0));
     SF_CUDA(cudaEventCreate(&e1));
+    if (b->gemm) {
+        // Grouped tensor-core stages 0 and 2 with and without resident P
+        // panels (entries: stage -1, chunk 1 = resident, 0 = streamed): the
+        // first batch solve of each plan captures its graph, the second is
+        // timed.
+        int count = 0;
+        float t[2] = {0.f, 0.f};
+        sfista_status st = SFISTA_OK;
+        for (int res = 1; res >= 0 && !st; --res) {
+            gemm_batch_set_res(b->gb, res != 0);
+            if (b->gexec) {   // captured with the other tile shape
+                cudaGraphExecDestroy(b->gexec);
+                b->gexec = nullptr;
+            }
+            if ((st = sfista_batch_solve(b, d_b.data(), lams.data(), iters, d_x.data(), b->stream))) break;
+            cudaError_t e = cudaEventRecord(e0, b->stream);
+            if (!e && !(st = sfista_batch_solve(b, d_b.data(), lams.data(), iters, d_x.data(), b->stream)))
+                e = cudaEventRecord(e1, b->stream);
+            if (st) break;
+            if (!e) e = cudaEventSynchronize(e1);
+            if (!e) e = cudaEventElapsedTime(&t[res], e0, e1);
+            if (e) {
+                st = fail(SFISTA_ECUDA, std::string("batch tuning: ") + cudaGetErrorString(e));
+                break;
+            }
+            t[res] /= iters;
+            if (entries && count < max_entries) entries[count] = sfista_tune_entry{b->ctxs[0]->op, -1, res, t[res]};
+            ++count;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (st) return st;
+        gemm_batch_set_res(b->gb, t[1] <= t[0]);
+        if (b->gexec) {
+            cudaGraphExecDestroy(b->gexec);
+            b->gexec = nullptr;
+        }
+        if (n_entries) *n_entries = count;
+        return sfista_batch_sync(b, nullptr);
+    }
     const size_t kb = 1024;
     const size_t budgets[] = {0, 24 * kb, 32 * kb, 48 * kb, 64 * kb, 80 * kb, 96 * kb, 128 * kb, 160 * kb, 227 * kb};
     std::vector<std::vector<int>> seen;
@@ -1718,6 +1769,28 @@ sfista_status sfista_tune(sfista_ctx *c, int iters, sfista_tune_entry *entries, 
         const bool dense = t_dense < t_band;
         c->op = dense ? SFISTA_OP_GEMM_DENSE : SFISTA_OP_GEMM_BAND;
         gemm_set_dense(c->gemm, dense);
+    }
+    if (c->gemm) {
+        // Tile shape of each tensor-core stage in the chosen K mode, timed
+        // alone: the N tile width of the summed stages 1 and 3 (64, 128 or
+        // 256; entries report it in `chunk`) and the resident P panel of the
+        // stacked stages 0 and 2 (chunk 1; 0 = streamed).
+        for (int s4 = 0; s4 < 4; ++s4) {
+            int bn[3], res[3];
+            const int nopt = gemm_tile_options(c->gemm, s4, bn, res);
+            if (nopt < 2) continue;
+            float best = 0.f;
+            int bi = -1;
+            for (int o = 0; o < nopt; ++o) {
+                gemm_set_tile(c->gemm, s4, bn[o], res[o]);
+                float t = 0.f;
+                st = time_stage_range(c, s4, s4, iters, &t);
+                if (st) return st;
+                log(c->op, s4, s4 % 2 == 0 ? res[o] : bn[o], t);
+                if (bi < 0 || t < best) best = t, bi = o;
+            }
+            gemm_set_tile(c->gemm, s4, bn[bi], res[bi]);
+        }
     }
     if (c->gexec) {   // the cached loop graph holds the old configuration
         cudaGraphExecDestroy(c->gexec);

@@ -220,4 +220,60 @@ static __device__ __forceinline__ void prox_momentum2_n(const ProxArgs &pa, cons
     if (bad) atomicOr(pa.status, DEV_NONFINITE);
 }
 
+// Four neighbouring pixels (idx a multiple of 4, every array 16-byte aligned
+// there): the operand copies of Y_{k+1} as store_operands32 writes them, one
+// 16-byte (FP32 / TF32) or 8-byte (BF16) store per array.
+static __device__ __forceinline__ void store_operands32x4(const ProxArgs &pa, size_t idx, float4 v) {
+    if (pa.Yop) *reinterpret_cast<float4 *>(pa.Yop + idx) = v;
+    if (pa.split_kind == 1) {
+        const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
+        *reinterpret_cast<uint2 *>(reinterpret_cast<__nv_bfloat16 *>(pa.Yhi) + idx) =
+            make_uint2(*reinterpret_cast<const uint32_t *>(&h01), *reinterpret_cast<const uint32_t *>(&h23));
+        if (pa.Ylo) {
+            const __nv_bfloat162 l01 = __floats2bfloat162_rn(__fsub_rn(v.x, __bfloat162float(h01.x)),
+                                                             __fsub_rn(v.y, __bfloat162float(h01.y)));
+            const __nv_bfloat162 l23 = __floats2bfloat162_rn(__fsub_rn(v.z, __bfloat162float(h23.x)),
+                                                             __fsub_rn(v.w, __bfloat162float(h23.y)));
+            *reinterpret_cast<uint2 *>(reinterpret_cast<__nv_bfloat16 *>(pa.Ylo) + idx) =
+                make_uint2(*reinterpret_cast<const uint32_t *>(&l01), *reinterpret_cast<const uint32_t *>(&l23));
+        }
+    } else if (pa.split_kind == 2) {
+        const float4 h = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
+        *reinterpret_cast<float4 *>(reinterpret_cast<float *>(pa.Yhi) + idx) = h;
+        if (pa.Ylo)
+            *reinterpret_cast<float4 *>(reinterpret_cast<float *>(pa.Ylo) + idx) =
+                make_float4(tf32_round(__fsub_rn(v.x, h.x)), tf32_round(__fsub_rn(v.y, h.y)),
+                            tf32_round(__fsub_rn(v.z, h.z)), tf32_round(__fsub_rn(v.w, h.w)));
+    }
+}
+
+// Groups of four neighbouring pixels (idx[q] a multiple of 4) for N rows at
+// once, FP32 state: 16-byte state loads and stores, every load issued before
+// any arithmetic.  Same arithmetic as prox_momentum2_n32.
+template <int N>
+static __device__ __forceinline__ void prox_momentum4_n32(const ProxArgs &pa, const size_t *idx, const float4 *g,
+                                                          const bool *valid) {
+    float4 y[N], xp[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        y[q] = valid[q] ? __ldcg(reinterpret_cast<const float4 *>(pa.Y32 + idx[q])) : make_float4(0.f, 0.f, 0.f, 0.f);
+        xp[q] = valid[q] ? __ldcg(reinterpret_cast<const float4 *>(pa.Xin32 + idx[q])) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const float beta = pa.beta[pa.k - 1].x;
+    bool bad = false;
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        if (!valid[q]) continue;
+        float4 x, yn;
+        yn.x = prox_step32(pa, y[q].x, xp[q].x, g[q].x, beta, &x.x, &bad);
+        yn.y = prox_step32(pa, y[q].y, xp[q].y, g[q].y, beta, &x.y, &bad);
+        yn.z = prox_step32(pa, y[q].z, xp[q].z, g[q].z, beta, &x.z, &bad);
+        yn.w = prox_step32(pa, y[q].w, xp[q].w, g[q].w, beta, &x.w, &bad);
+        *reinterpret_cast<float4 *>(pa.Xout32 + idx[q]) = x;
+        *reinterpret_cast<float4 *>(pa.Y32 + idx[q]) = yn;
+        store_operands32x4(pa, idx[q], yn);
+    }
+    if (bad) atomicOr(pa.status, DEV_NONFINITE);
+}
+
 }  // namespace sfista

@@ -32,6 +32,7 @@
 
 #include <algorithm>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "epilogue.cuh"
@@ -203,18 +204,49 @@ __device__ __forceinline__ void store_split2(void *hi, void *lo, int kind, size_
     }
 }
 
+// Store four neighbouring values (idx a multiple of 4) as split operand
+// copies: one 8-byte (BF16) or 16-byte (TF32) store per copy.
+__device__ __forceinline__ void store_split4(void *hi, void *lo, int kind, size_t idx, float4 v) {
+    if (kind == 1) {
+        const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
+        *reinterpret_cast<uint2 *>(reinterpret_cast<__nv_bfloat16 *>(hi) + idx) =
+            make_uint2(*reinterpret_cast<const uint32_t *>(&h01), *reinterpret_cast<const uint32_t *>(&h23));
+        if (lo)
+            *reinterpret_cast<uint2 *>(reinterpret_cast<__nv_bfloat16 *>(lo) + idx) =
+                make_uint2(pack_bf16x2(v.x - __bfloat162float(h01.x), v.y - __bfloat162float(h01.y)),
+                           pack_bf16x2(v.z - __bfloat162float(h23.x), v.w - __bfloat162float(h23.y)));
+    } else {
+        const float4 h = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
+        *reinterpret_cast<float4 *>(reinterpret_cast<float *>(hi) + idx) = h;
+        if (lo)
+            *reinterpret_cast<float4 *>(reinterpret_cast<float *>(lo) + idx) =
+                make_float4(tf32_round(v.x - h.x), tf32_round(v.y - h.y), tf32_round(v.z - h.z),
+                            tf32_round(v.w - h.w));
+    }
+}
+
 struct WorkItem {
     int prob, mt, nt, pad;
 };
 
-template <int FMT, bool SPLIT, int BN>
+// Shared-memory plan of a kernel instance.  RES: the P panel of a tile (all
+// its K blocks, hi and lo) stays resident in its own region while the tiles
+// that share it run, and the ring carries Q blocks only.
+template <int FMT, bool SPLIT, int BN, bool RES>
 struct PCfg {
     using C = Cfg<FMT, SPLIT, BN>;
-    static constexpr int STAGING = BM * (BN / 2 + 1) * 4;   // epilogue half tile, row stride BN/2 + 1 floats
-    static constexpr int RING_MAX = 225 * 1024 - STAGING;
-    static constexpr int STAGES_RAW = RING_MAX / C::STAGE_BYTES;
+    static_assert(BN % 64 == 0 && BN <= 256, "the epilogue drains 64-column chunks; MMA N <= 256");
+    static_assert(!RES || FMT == FMT_BF16, "a resident panel holds 3 K blocks of 64 BF16 values");
+    static constexpr int CW = 64;                        // accumulator columns per epilogue chunk
+    static constexpr int STAGING = BM * (CW + 1) * 4;    // one chunk, row stride CW + 1 floats
+    static constexpr int RES_KB = RES ? 3 : 0;           // K blocks a resident panel holds
+    static constexpr int P_REGION = RES_KB * C::NOP * C::P_BYTES;
+    static constexpr int STAGE_BYTES = RES ? C::NOP * C::Q_BYTES : C::STAGE_BYTES;
+    static constexpr int RING_MAX = 225 * 1024 - STAGING - P_REGION;
+    static constexpr int STAGES_RAW = RING_MAX / STAGE_BYTES;
     static constexpr int STAGES = STAGES_RAW > 6 ? 6 : (STAGES_RAW < 2 ? 2 : STAGES_RAW);
-    static constexpr int SMEM = STAGES * C::STAGE_BYTES + STAGING + 1024;
+    static constexpr int SMEM = P_REGION + STAGES * STAGE_BYTES + STAGING + 1024;
+    static_assert(SMEM <= 227 * 1024 - 256, "dynamic plus static shared memory of one CTA");
     static constexpr uint32_t TMEM_COLS = 2 * BN;   // two accumulators
 };
 
@@ -236,15 +268,24 @@ __device__ __forceinline__ void tile_k_range(const GemmArgs &g, int m0, int *k_l
     *nkb = hi > lo ? (hi - lo + C::KB_ELEMS - 1) / C::KB_ELEMS : 0;
 }
 
-// Persistent GEMM stage.  CTA c walks tiles c, c + gridDim.x, ...; the TMA
-// producer and the MMA issuer run ahead through a ring of shared-memory
-// stages while the eight epilogue warps drain the previous tile from the
-// other of two TMEM accumulators.  Tiles come from (mt, nt) = (t / ntn, t % ntn)
-// of one problem, or from a work list over many problems (GROUPED), whose
-// tensor maps and arguments then live in global memory; for the grouped prox
-// epilogue, k selects X_{k-1} / X_k among each problem's two state buffers
-// (stored in pa.Xin / pa.Xout as buffers 0 / 1).
-template <int FMT, bool SPLIT, int BN, int EPI, bool GROUPED>
+// Persistent GEMM stage.  CTA c walks tiles c, c + gridDim.x, ... (RES: a
+// contiguous run of tiles, so that consecutive tiles share their P panel);
+// the TMA producer and the MMA issuer run ahead through a ring of
+// shared-memory stages while the eight epilogue warps drain the previous tile
+// from the other of two TMEM accumulators.  Tiles come from (mt, nt) =
+// (t / ntn, t % ntn) of one problem, or from a work list over many problems
+// (GROUPED), whose tensor maps and arguments then live in global memory; for
+// the grouped prox epilogue, k selects X_{k-1} / X_k among each problem's two
+// state buffers (stored in pa.Xin / pa.Xout as buffers 0 / 1).
+//
+// RES (stacked stages, one term per tile): the P operand of a tile depends
+// only on its row tile (term and m0), not on nt.  The producer loads that
+// panel (every K block of the tile's band range, hi and lo) once into a
+// resident region and streams only Q blocks through the ring; before it
+// overwrites the panel for the next row tile it waits until the MMAs that
+// read the old one have completed (the MMA warp commits `pempty` when it
+// moves to a tile of another panel).
+template <int FMT, bool SPLIT, int BN, int EPI, bool GROUPED, bool RES>
 __global__ void __launch_bounds__(320, 1)
     umma_gemm_persistent(const __grid_constant__ CUtensorMap tPhi, const __grid_constant__ CUtensorMap tPlo,
                          const __grid_constant__ CUtensorMap tQhi, const __grid_constant__ CUtensorMap tQlo,
@@ -252,22 +293,23 @@ __global__ void __launch_bounds__(320, 1)
                          const __grid_constant__ GemmArgs g1, int ntn, int ntiles, const CUtensorMap *maps,
                          const GemmArgs *args, const WorkItem *work, int kswap) {
     using C = Cfg<FMT, SPLIT, BN>;
-    using PC = PCfg<FMT, SPLIT, BN>;
+    using PC = PCfg<FMT, SPLIT, BN, RES>;
     constexpr int S = PC::STAGES;
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t bars[2 * S + 5];
+    __shared__ __align__(8) uint64_t bars[2 * S + 7];
     __shared__ uint32_t tmem_base_sh;
     __shared__ int ep_abort;   // epilogue warps leave the tile loop together
 
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    float *tile = reinterpret_cast<float *>(smem + S * C::STAGE_BYTES);
-    constexpr int HB = BN / 2;     // columns per staged half
-    static_assert(HB == 64, "the epilogue maps one column pair per lane");
-    constexpr int TS = HB + 1;
+    uint8_t *ring = smem + PC::P_REGION;   // the resident panel (RES) sits below the ring
+    float *tile = reinterpret_cast<float *>(ring + S * PC::STAGE_BYTES);
+    constexpr int CW = PC::CW;     // columns per epilogue chunk
+    constexpr int TS = CW + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[S]);
     const uint32_t tfull0 = smem_u32(&bars[2 * S]), tempty0 = smem_u32(&bars[2 * S + 2]);
     const uint32_t drainb = smem_u32(&bars[2 * S + 4]);
+    const uint32_t pfull = smem_u32(&bars[2 * S + 5]), pempty = smem_u32(&bars[2 * S + 6]);
     if (threadIdx.x == 0) {
         for (int q = 0; q < S; ++q) {
             mbar_init(full0 + 8 * q, 1);
@@ -278,6 +320,8 @@ __global__ void __launch_bounds__(320, 1)
             mbar_init(tempty0 + 8 * q, 8);
         }
         mbar_init(drainb, 1);
+        mbar_init(pfull, 1);
+        mbar_init(pempty, 1);
         ep_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -291,39 +335,81 @@ __global__ void __launch_bounds__(320, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base_sh;
+    // Programmatic dependent launch: the next stage may launch now (its CTAs
+    // start as ours exit and run their prologue), and this one waits here
+    // until the previous kernel in the stream has completed and its writes
+    // are visible.  Both are no-ops for a plain launch.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 
-    // Tile t -> its tensor maps, arguments and (mt, nt).
-    auto fetch = [&](int t, const CUtensorMap *&m4, const GemmArgs *&ga, int &mt, int &nt) {
+    // This CTA's tiles: t_first, t_first + t_step, ... < t_end.
+    int t_first = blockIdx.x, t_step = gridDim.x, t_end = ntiles;
+    if (RES) {
+        const int per = ntiles / (int)gridDim.x, rem = ntiles - per * (int)gridDim.x;
+        t_first = (int)blockIdx.x * per + min((int)blockIdx.x, rem);
+        t_end = t_first + per + ((int)blockIdx.x < rem ? 1 : 0);
+        t_step = 1;
+    }
+
+    // Tile t -> its tensor maps, arguments, (mt, nt) and the key of its P
+    // panel (problem and row tile).
+    auto fetch = [&](int t, const CUtensorMap *&m4, const GemmArgs *&ga, int &mt, int &nt, int &key) {
         if (GROUPED) {
             const WorkItem w = work[t];
             m4 = maps + 6 * w.prob;
             ga = args + w.prob;
             mt = w.mt;
             nt = w.nt;
+            key = (w.prob << 16) | w.mt;
         } else {
             m4 = nullptr;
             ga = &g1;
             mt = t / ntn;
             nt = t - mt * ntn;
+            key = mt;
         }
+    };
+    // K range of a tile; a band wider than the resident panel (the host does
+    // not choose RES then) leaves the tile empty instead of overrunning it.
+    auto k_range = [&](const GemmArgs &ga, int m0, int &k_lo, int &nkb) {
+        tile_k_range<FMT, SPLIT, BN>(ga, m0, &k_lo, &nkb);
+        if (RES && nkb > PC::RES_KB) nkb = 0;
     };
 
     if (warp == 0) {
         if (lane == 0) {
-            int it = 0;
+            int it = 0, panels = 0, key_prev = -1;
             bool abort = false;
-            for (int t = blockIdx.x; t < ntiles && !abort; t += gridDim.x) {
+            unsigned *st0 = GROUPED ? args[0].status : g1.status;
+            for (int t = t_first; t < t_end && !abort; t += t_step) {
                 const CUtensorMap *m4;
                 const GemmArgs *ga;
-                int mt, nt;
-                fetch(t, m4, ga, mt, nt);
+                int mt, nt, key;
+                fetch(t, m4, ga, mt, nt, key);
                 const int term = ga->type_b ? 0 : mt / ga->m_tiles;
                 const int m0 = (mt % ga->m_tiles) * BM, n0 = nt * BN;
                 int k_lo, nkb;
-                tile_k_range<FMT, SPLIT, BN>(*ga, m0, &k_lo, &nkb);
+                k_range(*ga, m0, k_lo, nkb);
+                if (RES) {
+                    int nkb_full;
+                    tile_k_range<FMT, SPLIT, BN>(*ga, m0, &k_lo, &nkb_full);
+                    if (nkb_full > PC::RES_KB) atomicOr(ga->status, DEV_BADARG);
+                }
                 const int total = nkb * ga->segs;
                 const CUtensorMap *pPhi = GROUPED ? m4 : &tPhi, *pPlo = GROUPED ? m4 + 1 : &tPlo;
                 const CUtensorMap *pQhi = GROUPED ? m4 + 2 : &tQhi, *pQlo = GROUPED ? m4 + 3 : &tQlo;
+                if (RES && key != key_prev) {
+                    // The previous panel is free once the MMAs that read it are done.
+                    if (panels > 0 && !mbar_wait(pempty, (panels - 1) & 1, st0)) break;
+                    mbar_expect_tx(pfull, (uint32_t)(nkb * C::NOP * C::P_BYTES));
+                    for (int kb = 0; kb < nkb; ++kb) {
+                        const uint32_t dst = smem_u32(smem + kb * C::NOP * C::P_BYTES);
+                        tma_load_3d(dst, pPhi, pfull, k_lo + kb * C::KB_ELEMS, m0, term);
+                        if (SPLIT) tma_load_3d(dst + C::P_BYTES, pPlo, pfull, k_lo + kb * C::KB_ELEMS, m0, term);
+                    }
+                    ++panels;
+                    key_prev = key;
+                }
                 for (int q = 0; q < total; ++q, ++it) {
                     const int s = it % S;
                     const uint32_t ph = (it / S) & 1;
@@ -332,38 +418,49 @@ __global__ void __launch_bounds__(320, 1)
                         break;
                     }
                     const uint32_t fb = full0 + 8 * s;
-                    mbar_expect_tx(fb, C::STAGE_BYTES);
+                    mbar_expect_tx(fb, PC::STAGE_BYTES);
                     const int seg = q / nkb, kb = q - seg * nkb;
                     const int kx = k_lo + kb * C::KB_ELEMS;
                     const int pz = ga->type_b ? seg : term, qz = ga->type_b ? seg : 0;
-                    const uint32_t base = smem_u32(smem + s * C::STAGE_BYTES);
-                    tma_load_3d(base, pPhi, fb, kx, m0, pz);
-                    if (SPLIT) tma_load_3d(base + C::P_BYTES, pPlo, fb, kx, m0, pz);
-                    tma_load_3d(base + C::NOP * C::P_BYTES, pQhi, fb, kx, n0, qz);
-                    if (SPLIT) tma_load_3d(base + C::NOP * C::P_BYTES + C::Q_BYTES, pQlo, fb, kx, n0, qz);
+                    const uint32_t base = smem_u32(ring + s * PC::STAGE_BYTES);
+                    const uint32_t qb = RES ? base : base + C::NOP * C::P_BYTES;
+                    if (!RES) {
+                        tma_load_3d(base, pPhi, fb, kx, m0, pz);
+                        if (SPLIT) tma_load_3d(base + C::P_BYTES, pPlo, fb, kx, m0, pz);
+                    }
+                    tma_load_3d(qb, pQhi, fb, kx, n0, qz);
+                    if (SPLIT) tma_load_3d(qb + C::Q_BYTES, pQlo, fb, kx, n0, qz);
                 }
             }
-            // Drain: the last fill of every stage has landed before the CTA can exit.
-            for (int x = max(0, it - S); x < it; ++x)
-                mbar_wait(full0 + 8 * (x % S), (x / S) & 1, GROUPED ? args[0].status : g1.status);
+            // Drain: the last fill of every stage (and of the panel) has landed
+            // before the CTA can exit.
+            for (int x = max(0, it - S); x < it; ++x) mbar_wait(full0 + 8 * (x % S), (x / S) & 1, st0);
+            if (RES && panels > 0) mbar_wait(pfull, (panels - 1) & 1, st0);
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            int it = 0, j = 0;
+            int it = 0, j = 0, panels = 0, key_prev = -1;
             bool abort = false;
             unsigned *st = GROUPED ? args[0].status : g1.status;
-            for (int t = blockIdx.x; t < ntiles && !abort; t += gridDim.x, ++j) {
+            for (int t = t_first; t < t_end && !abort; t += t_step, ++j) {
                 const CUtensorMap *m4;
                 const GemmArgs *ga;
-                int mt, nt;
-                fetch(t, m4, ga, mt, nt);
+                int mt, nt, key;
+                fetch(t, m4, ga, mt, nt, key);
                 const int m0 = (mt % ga->m_tiles) * BM;
                 int k_lo, nkb;
-                tile_k_range<FMT, SPLIT, BN>(*ga, m0, &k_lo, &nkb);
+                k_range(*ga, m0, k_lo, nkb);
                 const int total = nkb * ga->segs;
                 const int b = j & 1;
                 if (!mbar_wait(tempty0 + 8 * b, ((j >> 1) & 1) ^ 1, st)) break;
                 tc_fence_after();
+                if (RES && key != key_prev) {
+                    if (panels > 0) tc_commit(pempty);   // arrives when every MMA issued so far has completed
+                    if (!mbar_wait(pfull, panels & 1, st)) break;
+                    tc_fence_after();
+                    ++panels;
+                    key_prev = key;
+                }
                 const uint32_t d = tmem + (uint32_t)(b * BN);
                 for (int q = 0; q < total; ++q, ++it) {
                     const int s = it % S;
@@ -373,9 +470,10 @@ __global__ void __launch_bounds__(320, 1)
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t base = smem_u32(smem + s * C::STAGE_BYTES);
-                    const uint32_t p_hi = base, p_lo = base + C::P_BYTES;
-                    const uint32_t q_hi = base + C::NOP * C::P_BYTES, q_lo = q_hi + C::Q_BYTES;
+                    const uint32_t base = smem_u32(ring + s * PC::STAGE_BYTES);
+                    const uint32_t p_hi = RES ? smem_u32(smem + q * C::NOP * C::P_BYTES) : base;
+                    const uint32_t p_lo = p_hi + C::P_BYTES;
+                    const uint32_t q_hi = RES ? base : base + C::NOP * C::P_BYTES, q_lo = q_hi + C::Q_BYTES;
 #pragma unroll
                     for (int ks = 0; ks < C::KSTEPS; ++ks) {
                         const uint32_t acc = (q > 0 || ks > 0) ? 1u : 0u;
@@ -395,22 +493,23 @@ __global__ void __launch_bounds__(320, 1)
         }
         __syncwarp();
     } else {
-        // Epilogue, warps 2..9, one column half of the tile at a time.  Phase 1:
-        // warp w reads TMEM lane quarter w % 4 (the only quarter it may access),
-        // 32 of the half's columns, into the staging tile; after the second half
-        // the accumulator is released to the MMA warp.  Phase 2: the eight warps
-        // walk whole rows of the half so global accesses are row-contiguous.
+        // Epilogue, warps 2..9, one chunk of CW = 64 accumulator columns at a
+        // time.  Phase 1: warp w reads TMEM lane quarter w % 4 (the only
+        // quarter it may access), 32 of the chunk's columns, into the staging
+        // tile; after the last chunk the accumulator is released to the MMA
+        // warp.  Phase 2: the eight warps walk whole rows of the chunk so
+        // global accesses are row-contiguous.
         const int lg = warp & 3, sub = (warp - 2) >> 2, ew = warp - 2;
         int j = 0;
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+        for (int t = t_first; t < t_end; t += t_step, ++j) {
             const CUtensorMap *m4;
             const GemmArgs *ga;
-            int mt, nt;
-            fetch(t, m4, ga, mt, nt);
+            int mt, nt, key;
+            fetch(t, m4, ga, mt, nt, key);
             const int term = ga->type_b ? 0 : mt / ga->m_tiles;
             const int m0 = (mt % ga->m_tiles) * BM;
             int k_lo, nkb;
-            tile_k_range<FMT, SPLIT, BN>(*ga, m0, &k_lo, &nkb);
+            k_range(*ga, m0, k_lo, nkb);
             const int total = nkb * ga->segs;
             const int b = j & 1;
             const bool ok = mbar_wait(tfull0 + 8 * b, (j >> 1) & 1, ga->status);
@@ -427,7 +526,8 @@ __global__ void __launch_bounds__(320, 1)
                 pa.Xout32 = kswap & 1 ? f1 : f0;
             }
 #pragma unroll 1
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < BN / CW; ++h) {
+                const bool last = h == BN / CW - 1;
                 if constexpr (FMT == FMT_BF16 && (EPI == GE_SPLIT || EPI == GE_RESID)) {
                     // Split outputs: each warp converts its 32 x 32 block to
                     // BF16 hi/lo straight from TMEM into two 128B-swizzled boxes
@@ -437,13 +537,13 @@ __global__ void __launch_bounds__(320, 1)
                     if (ew == 0 && lane == 0) bulk_wait_read();   // the previous boxes have been read out
                     asm volatile("bar.sync 1, 256;" ::: "memory");
                     float v[32];
-                    tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * BN + h * HB + sub * 32), v);
+                    tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * BN + h * CW + sub * 32), v);
                     const int R = lg * 32 + lane;   // tile row of this lane
                     if (!ok || total == 0) {
 #pragma unroll
                         for (int q = 0; q < 32; ++q) v[q] = 0.0f;
                     } else if (EPI == GE_RESID) {
-                        const int row = m0 + R, col0 = nt * BN + h * HB + sub * 32;
+                        const int row = m0 + R, col0 = nt * BN + h * CW + sub * 32;
                         if (row < ga->rows) {
                             const float *bp = ga->Bd + (size_t)row * ga->N + col0;
 #pragma unroll
@@ -478,7 +578,7 @@ __global__ void __launch_bounds__(320, 1)
                         if (SPLIT)
                             *reinterpret_cast<uint4 *>(box_lo + R * 128 + pos) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                     }
-                    if (h == 1) {
+                    if (last) {
                         tc_fence_before();
                         __syncwarp();
                         if (lane == 0) mbar_arrive(tempty0 + 8 * b);
@@ -487,7 +587,7 @@ __global__ void __launch_bounds__(320, 1)
                     asm volatile("bar.sync 1, 256;" ::: "memory");
                     if (ew == 0 && lane == 0) {
                         const CUtensorMap *oh = GROUPED ? m4 + 4 : &tOhi, *ol = GROUPED ? m4 + 5 : &tOlo;
-                        const int x = nt * BN + h * HB;
+                        const int x = nt * BN + h * CW;
                         if (x < ga->N) {   // boxes reaching past N or the last row are clipped by the unit
                             tma_store_3d(oh, smem_u32(box_hi), x, m0, term);
                             if (SPLIT) tma_store_3d(ol, smem_u32(box_lo), x, m0, term);
@@ -498,26 +598,26 @@ __global__ void __launch_bounds__(320, 1)
                 }
                 {
                     float v[32];
-                    tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * BN + h * HB + sub * 32), v);
+                    tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * BN + h * CW + sub * 32), v);
                     const bool zero = !ok || total == 0;
 #pragma unroll
                     for (int q = 0; q < 32; ++q) tile[(lg * 32 + lane) * TS + sub * 32 + q] = zero ? 0.0f : v[q];
                 }
-                if (h == 1) {
+                if (last) {
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(tempty0 + 8 * b);
                 }
                 asm volatile("bar.sync 1, 256;" ::: "memory");
-                const int n0 = nt * BN + h * HB;
-                const int c = 2 * lane;   // HB == 64: one column pair per lane
-                const int col = n0 + c;
-                // Each warp owns rows ew, ew + 8, ..., ew + 120 of the half and
-                // handles them eight at a time, every global load of a batch
-                // issued before its first use (one memory latency per batch,
-                // not per row).
-                if (EPI == GE_PROX) {
-                    if (col < ga->N) {   // N is even (a multiple of 8)
+                const int n0 = nt * BN + h * CW;
+                if (EPI == GE_PROX && !pa.Y32) {
+                    // Double-float state (8 bytes per pixel): one column pair
+                    // per lane, so that each 16-byte state access of a warp is
+                    // contiguous; warp ew owns rows ew, ew + 8, ..., ew + 120
+                    // and handles them eight at a time, every global load of a
+                    // batch issued before its first use.
+                    const int c2 = 2 * lane, col2 = n0 + c2;
+                    if (col2 < ga->N) {
 #pragma unroll 1
                         for (int rl = ew; rl < BM; rl += 64) {
                             size_t idx[8];
@@ -526,41 +626,60 @@ __global__ void __launch_bounds__(320, 1)
 #pragma unroll
                             for (int q = 0; q < 8; ++q) {
                                 const int rr = rl + 8 * q, row = m0 + rr;
-                                okr[q] = rr < BM && row < ga->rows;
-                                idx[q] = (size_t)row * ga->N + col;
-                                g0[q] = okr[q] ? tile[rr * TS + c] : 0.0f;
-                                g1v[q] = okr[q] ? tile[rr * TS + c + 1] : 0.0f;
+                                okr[q] = row < ga->rows;
+                                idx[q] = (size_t)row * ga->N + col2;
+                                g0[q] = tile[rr * TS + c2];
+                                g1v[q] = tile[rr * TS + c2 + 1];
                             }
-                            if (pa.Y32) prox_momentum2_n32<8>(pa, idx, g0, g1v, okr);
-                            else prox_momentum2_n<8>(pa, idx, g0, g1v, okr);
+                            prox_momentum2_n<8>(pa, idx, g0, g1v, okr);
                         }
                     }
-                } else if (col < ga->N) {
-                    const int rows = ga->rows, N = ga->N, sk = ga->split_kind;
-                    void *ohi = ga->out_hi, *olo = ga->out_lo;
-#pragma unroll 1
-                    for (int rl0 = ew; rl0 < BM; rl0 += 64) {
-                        float2 bb[8];
+                    asm volatile("bar.sync 1, 256;" ::: "memory");   // staging tile free again
+                    continue;
+                }
+                const int c = 4 * (lane & 15);   // CW == 64: four columns per lane, 16 lanes per row
+                const int col = n0 + c;
+                // Warp ew owns rows 2 ew + (lane >> 4) + 16 q (q < 8) of the
+                // chunk and handles all eight in one batch, every global load
+                // issued before its first use (one memory latency per chunk),
+                // with 16-byte loads and stores.
+                const int r0 = 2 * ew + (lane >> 4);
+                if (col < ga->N) {   // N is a multiple of 8 and col of 4: all four columns inside
+                    const int rows = ga->rows, N = ga->N;
+                    size_t idx[8];
+                    float4 gv[8];
+                    bool okr[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int rr = r0 + 16 * q, row = m0 + rr;
+                        okr[q] = row < rows;
+                        idx[q] = (size_t)row * N + col;
+                        const float *tp = tile + rr * TS + c;
+                        gv[q] = make_float4(tp[0], tp[1], tp[2], tp[3]);
+                    }
+                    if (EPI == GE_PROX) {
+                        prox_momentum4_n32<8>(pa, idx, gv, okr);   // FP32 state (the other case is above)
+                    } else {
+                        const int sk = ga->split_kind;
+                        void *ohi = ga->out_hi, *olo = ga->out_lo;
+                        float4 bb[8];
                         if (EPI == GE_RESID) {
 #pragma unroll
-                            for (int q = 0; q < 8; ++q) {
-                                const int rl = rl0 + 8 * q, row = m0 + rl;
-                                bb[q] = rl < BM && row < rows
-                                            ? __ldg(reinterpret_cast<const float2 *>(ga->Bd + (size_t)row * N + col))
-                                            : make_float2(0.f, 0.f);
-                            }
+                            for (int q = 0; q < 8; ++q)
+                                bb[q] = okr[q] ? __ldg(reinterpret_cast<const float4 *>(ga->Bd + idx[q]))
+                                               : make_float4(0.f, 0.f, 0.f, 0.f);
                         }
 #pragma unroll
                         for (int q = 0; q < 8; ++q) {
-                            const int rl = rl0 + 8 * q, row = m0 + rl;
-                            if (rl >= BM || row >= rows) break;
-                            const float a0 = tile[rl * TS + c], a1 = tile[rl * TS + c + 1];
+                            if (!okr[q]) continue;
+                            float4 v = gv[q];
                             if (EPI == GE_SPLIT) {
-                                store_split2(ohi, olo, sk, ((size_t)term * rows + row) * N + col, a0, a1);
+                                store_split4(ohi, olo, sk, (size_t)term * rows * N + idx[q], v);
                             } else if (EPI == GE_RESID) {
-                                store_split2(ohi, olo, sk, (size_t)row * N + col, a0 - bb[q].x, a1 - bb[q].y);
+                                v = make_float4(v.x - bb[q].x, v.y - bb[q].y, v.z - bb[q].z, v.w - bb[q].w);
+                                store_split4(ohi, olo, sk, idx[q], v);
                             } else {
-                                *reinterpret_cast<float2 *>(ga->out_f32 + (size_t)row * N + col) = make_float2(a0, a1);
+                                *reinterpret_cast<float4 *>(ga->out_f32 + idx[q]) = v;
                             }
                         }
                     }
@@ -627,7 +746,9 @@ sfista_status make_map(CUtensorMap *map, const void *base, int fmt, int d0, int 
 
 struct Operand {
     void *hi = nullptr, *lo = nullptr;
-    CUtensorMap map_hi, map_lo;
+    CUtensorMap map_hi, map_lo;         // boxes of 128 rows (P loads, Q loads with BN = 128, tensor stores)
+    CUtensorMap map256_hi, map256_lo;   // Q operands: boxes of 256 rows (BN = 256)
+    CUtensorMap map64_hi, map64_lo;     // Q operands: boxes of 64 rows (BN = 64)
 };
 
 }  // namespace
@@ -644,54 +765,116 @@ struct GemmPath {
     unsigned *status = nullptr;
     double *dband = nullptr;             // scratch for densify
     int sms = 1;                         // SM count: the persistent grids use one CTA per SM
+    // Tile shape of each stage: N tile width (128, or 64 / 256 for the summed
+    // stages 1 and 3) and, for the stacked stages 0 and 2, the resident P
+    // panel (BF16 band mode only, when every row tile's band spans at most
+    // three K blocks: res_ok).
+    int bn[4] = {128, 128, 128, 128};
+    bool res[4] = {false, false, false, false};
+    bool res_ok[4] = {false, false, false, false};
 };
 
 namespace {
 
-constexpr int BN_TILE = 128;
+constexpr int BN_TILE = 128;   // N tile of the grouped launches
 
-template <int FMT, bool SPLIT, int EPI>
-cudaError_t set_attr() {
-    const int sm = PCfg<FMT, SPLIT, BN_TILE>::SMEM;
-    cudaError_t e = cudaFuncSetAttribute(umma_gemm_persistent<FMT, SPLIT, BN_TILE, EPI, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e) return e;
-    return cudaFuncSetAttribute(umma_gemm_persistent<FMT, SPLIT, BN_TILE, EPI, true>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+template <int FMT, bool SPLIT, int BN, int EPI, bool GROUPED, bool RES>
+cudaError_t set_attr1() {
+    return cudaFuncSetAttribute(umma_gemm_persistent<FMT, SPLIT, BN, EPI, GROUPED, RES>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, PCfg<FMT, SPLIT, BN, RES>::SMEM);
 }
 
+// Every kernel instance the launchers below can select: GE_SPLIT with
+// BN = 128 (streamed or, BF16, resident panel), GE_RESID / GE_PROX / GE_STORE
+// with BN = 64, 128 or 256 (single problems), GE_RESID / GE_PROX with 128
+// (grouped).
 template <int FMT, bool SPLIT>
 cudaError_t set_attrs() {
     cudaError_t e;
-    if ((e = set_attr<FMT, SPLIT, GE_SPLIT>())) return e;
-    if ((e = set_attr<FMT, SPLIT, GE_RESID>())) return e;
-    if ((e = set_attr<FMT, SPLIT, GE_PROX>())) return e;
-    return set_attr<FMT, SPLIT, GE_STORE>();
+    if ((e = set_attr1<FMT, SPLIT, 128, GE_SPLIT, false, false>()) ||
+        (e = set_attr1<FMT, SPLIT, 128, GE_SPLIT, true, false>()) ||
+        (e = set_attr1<FMT, SPLIT, 128, GE_RESID, false, false>()) ||
+        (e = set_attr1<FMT, SPLIT, 256, GE_RESID, false, false>()) ||
+        (e = set_attr1<FMT, SPLIT, 64, GE_RESID, false, false>()) ||
+        (e = set_attr1<FMT, SPLIT, 128, GE_RESID, true, false>()) ||
+        (e = set_attr1<FMT, SPLIT, 128, GE_PROX, false, false>()) ||
+        (e = set_attr1<FMT, SPLIT, 256, GE_PROX, false, false>()) ||
+        (e = set_attr1<FMT, SPLIT, 64, GE_PROX, false, false>()) ||
+        (e = set_attr1<FMT, SPLIT, 128, GE_PROX, true, false>()) ||
+        (e = set_attr1<FMT, SPLIT, 128, GE_STORE, false, false>()) ||
+        (e = set_attr1<FMT, SPLIT, 256, GE_STORE, false, false>()) ||
+        (e = set_attr1<FMT, SPLIT, 64, GE_STORE, false, false>()))
+        return e;
+    if constexpr (FMT == FMT_BF16) {
+        if ((e = set_attr1<FMT, SPLIT, 128, GE_SPLIT, false, true>()) ||
+            (e = set_attr1<FMT, SPLIT, 128, GE_SPLIT, true, true>()))
+            return e;
+    }
+    return cudaSuccess;
 }
 
-// One persistent launch over the gx * gy tiles of a stage (one CTA per SM).
-// O: the output operand (its tensor maps serve the epilogue's tensor stores), or
-// NULL for the stages that write plain FP32 or the FISTA state.
-template <int FMT, bool SPLIT, int EPI>
-sfista_status launch_one(const Operand &P, const Operand &Q, const Operand *O, const GemmArgs &a, int grid_x,
-                         int grid_y, int sms, cudaStream_t s) {
-    const int ntiles = grid_x * grid_y;
+// Launch with programmatic stream serialisation (the kernel's prologue may
+// overlap the previous kernel's tail; it waits with griddepcontrol.wait).
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kern)(KArgs...), int grid, int smem, cudaStream_t s, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(320);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
+// One persistent launch over the tiles of a stage (one CTA per SM): gy row
+// tiles (terms stacked) times ceil(a.N / BN) column tiles.  O: the output
+// operand (its tensor maps serve the epilogue's tensor stores), or NULL for
+// the stages that write plain FP32 or the FISTA state.
+template <int FMT, bool SPLIT, int EPI, int BN, bool RES>
+void launch_tiles(const Operand &P, const Operand &Q, const Operand *O, const GemmArgs &a, int gy, int sms,
+                  cudaStream_t s) {
+    const int gx = (a.N + BN - 1) / BN;
+    const int ntiles = gx * gy;
     const int grid = ntiles < sms ? ntiles : sms;
     const Operand &Ou = O ? *O : P;
-    umma_gemm_persistent<FMT, SPLIT, BN_TILE, EPI, false><<<grid, 320, PCfg<FMT, SPLIT, BN_TILE>::SMEM, s>>>(
-        P.map_hi, SPLIT ? P.map_lo : P.map_hi, Q.map_hi, SPLIT ? Q.map_lo : Q.map_hi, Ou.map_hi,
-        SPLIT ? Ou.map_lo : Ou.map_hi, a, grid_x, ntiles, nullptr, nullptr, nullptr, 0);
-    return SFISTA_OK;
+    const CUtensorMap &qh = BN == 256 ? Q.map256_hi : BN == 64 ? Q.map64_hi : Q.map_hi;
+    const CUtensorMap &ql = BN == 256 ? Q.map256_lo : BN == 64 ? Q.map64_lo : Q.map_lo;
+    launch_pdl(umma_gemm_persistent<FMT, SPLIT, BN, EPI, false, RES>, grid, PCfg<FMT, SPLIT, BN, RES>::SMEM, s,
+               P.map_hi, SPLIT ? P.map_lo : P.map_hi, qh, SPLIT ? ql : qh, Ou.map_hi, SPLIT ? Ou.map_lo : Ou.map_hi,
+               a, gx, ntiles, (const CUtensorMap *)nullptr, (const GemmArgs *)nullptr, (const WorkItem *)nullptr,
+               0);
+}
+
+// The instance for a stage's tile shape (bn, res); shapes without an
+// instance (the host never selects them) fall back to BN = 128, streamed.
+template <int FMT, bool SPLIT, int EPI>
+void launch_shape(const Operand &P, const Operand &Q, const Operand *O, const GemmArgs &a, int gy, int bn, bool res,
+                  int sms, cudaStream_t s) {
+    if constexpr (EPI == GE_SPLIT && FMT == FMT_BF16) {
+        if (res) return launch_tiles<FMT, SPLIT, EPI, 128, true>(P, Q, O, a, gy, sms, s);
+    }
+    if constexpr (EPI != GE_SPLIT) {
+        if (bn == 256) return launch_tiles<FMT, SPLIT, EPI, 256, false>(P, Q, O, a, gy, sms, s);
+        if (bn == 64) return launch_tiles<FMT, SPLIT, EPI, 64, false>(P, Q, O, a, gy, sms, s);
+    }
+    launch_tiles<FMT, SPLIT, EPI, 128, false>(P, Q, O, a, gy, sms, s);
 }
 
 template <int EPI>
 sfista_status dispatch(const GemmPath *g, const Operand &P, const Operand &Q, const Operand *O, const GemmArgs &a,
-                       int gx, int gy, cudaStream_t s) {
-    if (g->fmt == FMT_BF16)
-        return g->split ? launch_one<FMT_BF16, true, EPI>(P, Q, O, a, gx, gy, g->sms, s)
-                        : launch_one<FMT_BF16, false, EPI>(P, Q, O, a, gx, gy, g->sms, s);
-    return g->split ? launch_one<FMT_TF32, true, EPI>(P, Q, O, a, gx, gy, g->sms, s)
-                    : launch_one<FMT_TF32, false, EPI>(P, Q, O, a, gx, gy, g->sms, s);
+                       int gy, int bn, bool res, cudaStream_t s) {
+    if (g->fmt == FMT_BF16) {
+        if (g->split) launch_shape<FMT_BF16, true, EPI>(P, Q, O, a, gy, bn, res, g->sms, s);
+        else launch_shape<FMT_BF16, false, EPI>(P, Q, O, a, gy, bn, res, g->sms, s);
+    } else {
+        if (g->split) launch_shape<FMT_TF32, true, EPI>(P, Q, O, a, gy, bn, res, g->sms, s);
+        else launch_shape<FMT_TF32, false, EPI>(P, Q, O, a, gy, bn, res, g->sms, s);
+    }
+    return SFISTA_OK;
 }
 
 GemmArgs base_args(const GemmPath *g) {
@@ -703,7 +886,7 @@ GemmArgs base_args(const GemmPath *g) {
 }
 
 // Stage 0 / 2: out[term][row][col] = sum_k P_term[row][k] Q[col][k] (terms along M).
-GemmArgs stacked_args(const GemmPath *g, const Band &band, Operand &Out, int *gx, int *gy) {
+GemmArgs stacked_args(const GemmPath *g, const Band &band, Operand &Out, int *gy) {
     GemmArgs a = base_args(g);
     a.rows = g->n;
     a.m_tiles = (g->n + BM - 1) / BM;
@@ -715,13 +898,12 @@ GemmArgs stacked_args(const GemmPath *g, const Band &band, Operand &Out, int *gx
     a.type_b = 0;
     a.out_hi = Out.hi;
     a.out_lo = Out.lo;
-    *gx = (g->m + BN_TILE - 1) / BN_TILE;
     *gy = a.m_tiles * g->r;
     return a;
 }
 
 // Stage 1 / 3: out[row][col] = sum_{t, k} P_t[row][k] Q_t[col][k] (terms along K).
-void summed_args(const GemmPath *g, const Band &band, GemmArgs *a, int *gx, int *gy) {
+void summed_args(const GemmPath *g, const Band &band, GemmArgs *a, int *gy) {
     a->rows = g->m;
     a->m_tiles = (g->m + BM - 1) / BM;
     a->N = g->n;
@@ -730,23 +912,39 @@ void summed_args(const GemmPath *g, const Band &band, GemmArgs *a, int *gx, int 
     a->band_hi = band.lo + band.w - 1;
     a->segs = g->r;
     a->type_b = 1;
-    *gx = (g->n + BN_TILE - 1) / BN_TILE;
     *gy = a->m_tiles;
 }
 
-sfista_status run_stacked(const GemmPath *g, const Operand &P, const Band &band, const Operand &Q, Operand &Out,
-                          cudaStream_t s) {
-    int gx, gy;
-    GemmArgs a = stacked_args(g, band, Out, &gx, &gy);
-    return dispatch<GE_SPLIT>(g, P, Q, &Out, a, gx, gy, s);
+// The resident panel applies in band mode only (a dense K range is longer).
+bool stage_res(const GemmPath *g, int st) { return g->res[st] && g->res_ok[st] && !g->dense; }
+
+sfista_status run_stacked(const GemmPath *g, int st, const Operand &P, const Band &band, const Operand &Q,
+                          Operand &Out, cudaStream_t s) {
+    int gy;
+    GemmArgs a = stacked_args(g, band, Out, &gy);
+    return dispatch<GE_SPLIT>(g, P, Q, &Out, a, gy, 128, stage_res(g, st), s);
 }
 
 template <int EPI>
-sfista_status run_summed(const GemmPath *g, const Operand &P, const Band &band, const Operand &Q, const Operand *O,
-                         GemmArgs a, cudaStream_t s) {
-    int gx, gy;
-    summed_args(g, band, &a, &gx, &gy);
-    return dispatch<EPI>(g, P, Q, O, a, gx, gy, s);
+sfista_status run_summed(const GemmPath *g, int st, const Operand &P, const Band &band, const Operand &Q,
+                         const Operand *O, GemmArgs a, cudaStream_t s) {
+    int gy;
+    summed_args(g, band, &a, &gy);
+    return dispatch<EPI>(g, P, Q, O, a, gy, g->bn[st], false, s);
+}
+
+// Largest number of K blocks (of kb_elems, start aligned down to `align`)
+// that the band range of any row tile of a len x len factor spans; the same
+// arithmetic as tile_k_range.
+int band_kblocks_max(int len, const Band &band, int align, int kb_elems) {
+    int mx = 0;
+    for (int m0 = 0; m0 < len; m0 += BM) {
+        int lo = std::max(0, m0 + band.lo);
+        const int hi = std::min(len, m0 + BM + band.lo + band.w - 1);
+        lo = (lo / align) * align;
+        mx = std::max(mx, hi > lo ? (hi - lo + kb_elems - 1) / kb_elems : 0);
+    }
+    return mx;
 }
 
 cudaError_t alloc_operand(Operand *o, size_t elems, size_t es, bool split) {
@@ -844,6 +1042,27 @@ sfista_status gemm_create(GemmPath **out, const HostSetup &h, int prec, bool den
         if ((st = make_map(&mm.o->map_hi, mm.o->hi, g->fmt, mm.d0, mm.d1, mm.d2, mm.rows))) return bail(st);
         if ((st = make_map(&mm.o->map_lo, mm.o->lo, g->fmt, mm.d0, mm.d1, mm.d2, mm.rows))) return bail(st);
     }
+    // Q operands of the summed stages with BN = 256 / 64: boxes of 256 / 64 rows.
+    for (Operand *o : {&g->QT, &g->QU}) {
+        if ((st = make_map(&o->map256_hi, o->hi, g->fmt, (int)m, (int)n, (int)r, 256))) return bail(st);
+        if ((st = make_map(&o->map256_lo, o->lo, g->fmt, (int)m, (int)n, (int)r, 256))) return bail(st);
+        if ((st = make_map(&o->map64_hi, o->hi, g->fmt, (int)m, (int)n, (int)r, 64))) return bail(st);
+        if ((st = make_map(&o->map64_lo, o->lo, g->fmt, (int)m, (int)n, (int)r, 64))) return bail(st);
+    }
+    for (Operand *o : {&g->QY, &g->QR}) {
+        o->map256_hi = o->map64_hi = o->map_hi;
+        o->map256_lo = o->map64_lo = o->map_lo;
+    }
+    // Resident P panels for the stacked stages: BF16 band mode, every row
+    // tile's band within three K blocks of 64.  On by default where allowed.
+    if (g->fmt == FMT_BF16) {
+        using CB = Cfg<FMT_BF16, true, 128>;
+        constexpr int kres = PCfg<FMT_BF16, true, 128, true>::RES_KB;
+        g->res_ok[0] = band_kblocks_max((int)n, h.A, CB::ALIGN, CB::KB_ELEMS) <= kres;
+        g->res_ok[2] = band_kblocks_max((int)n, h.AT, CB::ALIGN, CB::KB_ELEMS) <= kres;
+        g->res[0] = g->res_ok[0];
+        g->res[2] = g->res_ok[2];
+    }
     *out = g;
     return SFISTA_OK;
 }
@@ -853,6 +1072,34 @@ void launch_wait_timeout_selftest(unsigned *status, cudaStream_t s) {
 }
 
 void gemm_set_dense(GemmPath *g, bool dense) { g->dense = dense; }
+
+int gemm_tile_options(const GemmPath *g, int st, int *bn, int *res) {
+    int n = 0;
+    if (st == 0 || st == 2) {
+        bn[n] = 128, res[n++] = 0;
+        if (g->res_ok[st] && !g->dense) bn[n] = 128, res[n++] = 1;
+    } else {
+        bn[n] = 64, res[n++] = 0;
+        bn[n] = 128, res[n++] = 0;
+        bn[n] = 256, res[n++] = 0;
+    }
+    return n;
+}
+
+void gemm_set_tile(GemmPath *g, int st, int bn, int res) {
+    if (st == 0 || st == 2) {
+        g->bn[st] = 128;
+        g->res[st] = res && g->res_ok[st];
+    } else {
+        g->bn[st] = bn == 256 || bn == 64 ? bn : 128;
+        g->res[st] = false;
+    }
+}
+
+void gemm_get_tile(const GemmPath *g, int st, int *bn, int *res) {
+    *bn = g->bn[st];
+    *res = stage_res(g, st) ? 1 : 0;
+}
 
 void gemm_destroy(GemmPath *g) {
     if (!g) return;
@@ -872,18 +1119,18 @@ void gemm_prepare_solve(GemmPath *g, const float *Bd, cudaStream_t) { g->Bd = Bd
 void gemm_stage(GemmPath *g, int st, const ProxArgs &pa_in, cudaStream_t s) {
     switch (st) {
         case 0:
-            run_stacked(g, g->PA, g->bandA, g->QY, g->QT, s);
+            run_stacked(g, 0, g->PA, g->bandA, g->QY, g->QT, s);
             break;
         case 1: {
             GemmArgs a = base_args(g);
             a.Bd = g->Bd;
             a.out_hi = g->QR.hi;
             a.out_lo = g->QR.lo;
-            run_summed<GE_RESID>(g, g->PB, g->bandB, g->QT, &g->QR, a, s);
+            run_summed<GE_RESID>(g, 1, g->PB, g->bandB, g->QT, &g->QR, a, s);
             break;
         }
         case 2:
-            run_stacked(g, g->PAT, g->bandAT, g->QR, g->QU, s);
+            run_stacked(g, 2, g->PAT, g->bandAT, g->QR, g->QU, s);
             break;
         default: {
             GemmArgs a = base_args(g);
@@ -893,7 +1140,7 @@ void gemm_stage(GemmPath *g, int st, const ProxArgs &pa_in, cudaStream_t s) {
             a.pa.Ylo = g->split ? g->QY.lo : nullptr;
             a.pa.split_kind = g->split_kind;
             a.status = pa_in.status;
-            run_summed<GE_PROX>(g, g->PBT, g->bandBT, g->QU, nullptr, a, s);
+            run_summed<GE_PROX>(g, 3, g->PBT, g->bandBT, g->QU, nullptr, a, s);
             break;
         }
     }
@@ -909,6 +1156,9 @@ struct GemmBatch {
     std::vector<GemmArgs> h_args[4];
     WorkItem *d_work[4] = {nullptr, nullptr, nullptr, nullptr};
     int nwork[4] = {0, 0, 0, 0};
+    // Stages 0 and 2 with resident P panels: allowed when every problem
+    // allows them (BF16 band mode, bands within three K blocks).
+    bool res = false, res_ok = false;
 };
 
 void gemm_batch_destroy(GemmBatch *b) {
@@ -951,26 +1201,26 @@ sfista_status gemm_batch_create(GemmBatch **out, GemmPath *const *paths, int npr
         for (int p = 0; p < nprob; ++p) {
             GemmPath *g = paths[p];
             const Operand *P = nullptr, *Q = nullptr;
-            int gx = 0, gy = 0;
+            int gy = 0;
             GemmArgs a{};
             if (st == 0) {
-                a = stacked_args(g, g->bandA, g->QT, &gx, &gy);
+                a = stacked_args(g, g->bandA, g->QT, &gy);
                 P = &g->PA;
                 Q = &g->QY;
             } else if (st == 1) {
                 a = base_args(g);
                 a.out_hi = g->QR.hi;
                 a.out_lo = g->QR.lo;
-                summed_args(g, g->bandB, &a, &gx, &gy);
+                summed_args(g, g->bandB, &a, &gy);
                 P = &g->PB;
                 Q = &g->QT;
             } else if (st == 2) {
-                a = stacked_args(g, g->bandAT, g->QU, &gx, &gy);
+                a = stacked_args(g, g->bandAT, g->QU, &gy);
                 P = &g->PAT;
                 Q = &g->QR;
             } else {
                 a = base_args(g);
-                summed_args(g, g->bandBT, &a, &gx, &gy);
+                summed_args(g, g->bandBT, &a, &gy);
                 P = &g->PBT;
                 Q = &g->QU;
             }
@@ -1012,9 +1262,21 @@ sfista_status gemm_batch_create(GemmBatch **out, GemmPath *const *paths, int npr
         gemm_batch_destroy(b);
         return fail(SFISTA_ENOMEM, std::string("batch tables: ") + cudaGetErrorString(e));
     }
+    // Resident panels when every problem allows them, and by default when
+    // every problem's own stages use them.
+    b->res_ok = b->fmt == FMT_BF16;
+    b->res = true;
+    for (const GemmPath *g : b->paths) {
+        b->res_ok = b->res_ok && g->res_ok[0] && g->res_ok[2] && !g->dense;
+        b->res = b->res && g->res[0] && g->res[2];
+    }
+    b->res = b->res && b->res_ok;
     *out = b;
     return SFISTA_OK;
 }
+
+bool gemm_batch_res_ok(const GemmBatch *b) { return b->res_ok; }
+void gemm_batch_set_res(GemmBatch *b, bool res) { b->res = res && b->res_ok; }
 
 // Per solve: observation pointers and the prox arguments of every problem
 // (pa.Xin / pa.Xout hold the problem's state buffers 0 / 1).
@@ -1040,21 +1302,28 @@ sfista_status gemm_batch_bind(GemmBatch *b, const float *const *Bds, const ProxA
 }
 
 namespace {
-template <int FMT, bool SPLIT, int EPI>
+template <int FMT, bool SPLIT, int EPI, bool RES>
 void launch_grouped(const GemmBatch *b, int st, int k, cudaStream_t s) {
     const int grid = b->nwork[st] < b->sms ? b->nwork[st] : b->sms;
     // The parameter-space maps are unused in grouped mode: pass the first problem's.
     const Operand &P0 = b->paths[0]->PA;
-    umma_gemm_persistent<FMT, SPLIT, BN_TILE, EPI, true><<<grid, 320, PCfg<FMT, SPLIT, BN_TILE>::SMEM, s>>>(
-        P0.map_hi, P0.map_hi, P0.map_hi, P0.map_hi, P0.map_hi, P0.map_hi, b->h_args[st][0], 1, b->nwork[st],
-        b->d_maps[st], b->d_args[st],
-        b->d_work[st], k);
+    launch_pdl(umma_gemm_persistent<FMT, SPLIT, BN_TILE, EPI, true, RES>, grid,
+               PCfg<FMT, SPLIT, BN_TILE, RES>::SMEM, s, P0.map_hi, P0.map_hi, P0.map_hi, P0.map_hi, P0.map_hi,
+               P0.map_hi, b->h_args[st][0], 1, b->nwork[st], (const CUtensorMap *)b->d_maps[st],
+               (const GemmArgs *)b->d_args[st], (const WorkItem *)b->d_work[st], k);
 }
 template <int FMT, bool SPLIT>
 void grouped_stage(const GemmBatch *b, int st, int k, cudaStream_t s) {
-    if (st == 0 || st == 2) launch_grouped<FMT, SPLIT, GE_SPLIT>(b, st, k, s);
-    else if (st == 1) launch_grouped<FMT, SPLIT, GE_RESID>(b, st, k, s);
-    else launch_grouped<FMT, SPLIT, GE_PROX>(b, st, k, s);
+    if (st == 0 || st == 2) {
+        if constexpr (FMT == FMT_BF16) {
+            if (b->res) return launch_grouped<FMT, SPLIT, GE_SPLIT, true>(b, st, k, s);
+        }
+        launch_grouped<FMT, SPLIT, GE_SPLIT, false>(b, st, k, s);
+    } else if (st == 1) {
+        launch_grouped<FMT, SPLIT, GE_RESID, false>(b, st, k, s);
+    } else {
+        launch_grouped<FMT, SPLIT, GE_PROX, false>(b, st, k, s);
+    }
 }
 }  // namespace
 
@@ -1077,11 +1346,11 @@ sfista_status gemm_apply(GemmPath *g, const float *x, float *y, int transpose, c
     a.out_f32 = y;
     sfista_status st;
     if (!transpose) {
-        if ((st = run_stacked(g, g->PA, g->bandA, g->QY, g->QT, s))) return st;
-        st = run_summed<GE_STORE>(g, g->PB, g->bandB, g->QT, nullptr, a, s);
+        if ((st = run_stacked(g, 0, g->PA, g->bandA, g->QY, g->QT, s))) return st;
+        st = run_summed<GE_STORE>(g, 1, g->PB, g->bandB, g->QT, nullptr, a, s);
     } else {
-        if ((st = run_stacked(g, g->PAT, g->bandAT, g->QR, g->QU, s))) return st;
-        st = run_summed<GE_STORE>(g, g->PBT, g->bandBT, g->QU, nullptr, a, s);
+        if ((st = run_stacked(g, 2, g->PAT, g->bandAT, g->QR, g->QU, s))) return st;
+        st = run_summed<GE_STORE>(g, 3, g->PBT, g->bandBT, g->QU, nullptr, a, s);
     }
     if (st) return st;
     cudaError_t e = cudaGetLastError();

@@ -17,6 +17,14 @@ sfista_status gemm_create(GemmPath **out, const HostSetup &h, int prec, bool den
 void gemm_destroy(GemmPath *g);
 // Switches between band-limited and full K ranges (the panels are the same).
 void gemm_set_dense(GemmPath *g, bool dense);
+// Tile shapes of stage st (0..3) that can be selected: the count returned,
+// entries of (N tile width, resident P panel) written to bn / res (at most
+// 3); the stacked stages 0 and 2 offer the resident panel in BF16 band mode
+// when the band fits it, the summed stages 1 and 3 the widths 64, 128, 256.
+int gemm_tile_options(const GemmPath *g, int st, int *bn, int *res);
+void gemm_set_tile(GemmPath *g, int st, int bn, int res);
+// The shape stage st runs with (res as it applies in the current K mode).
+void gemm_get_tile(const GemmPath *g, int st, int *bn, int *res);
 // Split-operand copies of Y that the prox epilogue must write.
 void gemm_state_operands(GemmPath *g, void **yhi, void **ylo, int *split_kind);
 // Called once per solve after B has been copied in (binds its pointer).
@@ -41,6 +49,10 @@ sfista_status gemm_batch_create(GemmBatch **out, GemmPath *const *paths, int npr
 // Per solve: B pointers and prox arguments (pa.Xin / pa.Xout = state buffers 0 / 1).
 sfista_status gemm_batch_bind(GemmBatch *b, const float *const *Bds, const ProxArgs *pas, cudaStream_t s);
 void gemm_batch_stage(GemmBatch *b, int st, int k, cudaStream_t s);
+// Resident P panels in the grouped stages 0 and 2 (allowed when every
+// problem allows them; on by default then).
+bool gemm_batch_res_ok(const GemmBatch *b);
+void gemm_batch_set_res(GemmBatch *b, bool res);
 void gemm_batch_destroy(GemmBatch *b);
 
 }  // namespace sfista
