@@ -1038,7 +1038,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--forms", default="fp32:auto+tune,fp32:banded_fused,fp32:banded,fp32:banded_persistent,bf16x3:gemm_band,tf32x3:gemm_band,bf16:gemm_band,tf32:gemm_band,bf16x3:gemm_band+ref1,bf16:gemm_band+ref1",
+    ap.add_argument("--forms", default="fp32:auto+tune,fp32:banded_fused,fp32:banded,fp32:banded_persistent,bf16x3:gemm_band,bf16x3:gemm_band+tune,tf32x3:gemm_band,bf16:gemm_band,tf32:gemm_band,bf16x3:gemm_band+ref1,bf16:gemm_band+ref1",
                     help="comma list of prec:op forms to measure")
     ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "cfg4", "cfg5", "ex2", "fft"])
     ap.add_argument("--check-iters", type=int, default=10)

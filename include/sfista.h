@@ -459,7 +459,11 @@ typedef struct {
  * sfista_tune -- autotuner for this context's problem shape.  The paper has no
  * counterpart (its operator runs in serial MATLAB).  Times `iters` repetitions
  * of each candidate on the context's own stream, on an all-zero observation
- * (timing does not depend on the data), and keeps the fastest:
+ * (timing does not depend on the data), and keeps the fastest.  Candidates for
+ * a single stage are launched directly; whole-iteration candidates run the
+ * iteration loop exactly as a solve does (a CUDA graph of the iterations when
+ * use_graph is set, or the one-launch solver), so forms with several launches
+ * per iteration carry the launch cost a solve has:
  *   - two-pass banded FP32 form: for each of the four stages, the number of
  *     terms staged per block (1 .. r, those that fit in shared memory); this
  *     sets shared memory per block and so the blocks resident per SM;

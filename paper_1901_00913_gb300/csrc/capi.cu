@@ -1612,13 +1612,21 @@ sfista_status time_stage_range(sfista_ctx *c, int s0, int s1, int reps, float *m
     return SFISTA_OK;
 }
 
-// Mean time per iteration of the one-launch solver over `iters` iterations
-// (one untimed launch of 2 iterations first).
-sfista_status time_persistent(sfista_ctx *c, int iters, float *ms) {
+// Mean time per iteration of the iteration loop exactly as a solve runs it
+// (run_loop: a CUDA graph of `iters` iterations when the context uses graphs,
+// or the one-launch solver), over `iters` iterations after one untimed run
+// of the same loop.  Forms with several launches per iteration are timed
+// with the launch cost a solve has, not with that of separate launches.
+sfista_status time_loop(sfista_ctx *c, int iters, float *ms) {
+    if (c->gexec) {   // a graph captured for another configuration
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+        c->g_k0 = c->g_iters = -1;
+    }
     cudaEvent_t e0, e1;
     SF_CUDA(cudaEventCreate(&e0));
     SF_CUDA(cudaEventCreate(&e1));
-    sfista_status st = run_loop(c, 0.0, 0, 2);
+    sfista_status st = run_loop(c, 0.0, 0, iters);
     cudaError_t e = cudaSuccess;
     if (!st) e = cudaEventRecord(e0, c->stream);
     if (!st && !e) st = run_loop(c, 0.0, 0, iters);
@@ -1644,7 +1652,7 @@ sfista_status sfista_tune(sfista_ctx *c, int iters, sfista_tune_entry *entries, 
     if (n_entries) *n_entries = 0;
     if (iters < 1 || max_entries < 0) return fail(SFISTA_EINVAL, "iters must be >= 1 and max_entries >= 0");
     DeviceGuard g(c->dev);
-    st = ensure_beta(c, iters + 3);
+    st = ensure_beta(c, std::max(iters, 40) + 3);   // the longest timed loop (one-launch solver: >= 40 its)
     if (st) return st;
     // All-zero observation and state (c->tmp is scratch).
     SF_CUDA(cudaMemsetAsync(c->tmp, 0, c->N * sizeof(float), c->stream));
@@ -1679,7 +1687,7 @@ sfista_status sfista_tune(sfista_ctx *c, int iters, sfista_tune_entry *entries, 
                 c->chunk[s4] = best_ch;
             }
             float t_two = 0.f;
-            st = time_stage_range(c, 0, 3, iters, &t_two);
+            st = time_loop(c, iters, &t_two);
             if (st) return st;
             log(SFISTA_OP_BANDED, -1, 0, t_two);
             c->op = SFISTA_OP_BANDED;
@@ -1687,7 +1695,7 @@ sfista_status sfista_tune(sfista_ctx *c, int iters, sfista_tune_entry *entries, 
             if (auto_op && band_op_fused_prepare(c->r, std::max(h.A.w, h.AT.w), std::max(h.B.w, h.BT.w))) {
                 float t_fused = 0.f;
                 c->op = SFISTA_OP_BANDED_FUSED;
-                st = time_stage_range(c, 0, 3, iters, &t_fused);
+                st = time_loop(c, iters, &t_fused);
                 if (st) return st;
                 log(SFISTA_OP_BANDED_FUSED, -1, 0, t_fused);
                 c->op = t_fused < t_two ? SFISTA_OP_BANDED_FUSED : SFISTA_OP_BANDED;
@@ -1713,7 +1721,7 @@ sfista_status sfista_tune(sfista_ctx *c, int iters, sfista_tune_entry *entries, 
                     c->psmem = smem;
                     c->pth = th;
                     float t_one = 0.f;
-                    st = time_persistent(c, std::max(iters, 40), &t_one);
+                    st = time_loop(c, std::max(iters, 40), &t_one);
                     if (st) return st;
                     log(SFISTA_OP_BANDED_PERSISTENT, -1, th, t_one);
                     if (t_one < t_best) {
@@ -1745,7 +1753,7 @@ sfista_status sfista_tune(sfista_ctx *c, int iters, sfista_tune_entry *entries, 
                 if (have) {
                     float t_fft = 0.f;
                     c->op = SFISTA_OP_FFT;
-                    st = time_stage_range(c, 0, 3, iters, &t_fft);
+                    st = time_loop(c, iters, &t_fft);
                     if (st) return st;
                     log(SFISTA_OP_FFT, -1, 0, t_fft);
                     if (!(t_fft < t_best)) c->op = best_op;
@@ -1758,12 +1766,12 @@ sfista_status sfista_tune(sfista_ctx *c, int iters, sfista_tune_entry *entries, 
         float t_band = 0.f, t_dense = 0.f;
         c->op = SFISTA_OP_GEMM_BAND;
         gemm_set_dense(c->gemm, false);
-        st = time_stage_range(c, 0, 3, iters, &t_band);
+        st = time_loop(c, iters, &t_band);
         if (st) return st;
         log(SFISTA_OP_GEMM_BAND, -1, 0, t_band);
         c->op = SFISTA_OP_GEMM_DENSE;
         gemm_set_dense(c->gemm, true);
-        st = time_stage_range(c, 0, 3, iters, &t_dense);
+        st = time_loop(c, iters, &t_dense);
         if (st) return st;
         log(SFISTA_OP_GEMM_DENSE, -1, 0, t_dense);
         const bool dense = t_dense < t_band;
