@@ -135,12 +135,13 @@ typedef struct {
                                SFISTA_EINVAL otherwise; ignored where the one-launch fused
                                solver is not used, and the two-pass persistent form is
                                used instead if those tiles do not all fit).             */
-    int gemm_bn;            /* tensor-core forms: N tile width of the summed stages 1 and
-                               3 (the left-factor products): 0 (default) = 128; 64, 128
-                               or 256 (SFISTA_EINVAL otherwise).  Wider tiles read each
-                               factor block once for more columns, narrower ones spread
-                               the tiles more evenly over the SMs; sfista_tune measures
-                               all three.                                               */
+    int gemm_bn;            /* tensor-core forms: N tile width of the GEMM stages: 0
+                               (default) = 128; 64 or 128 for all four stages, 256 for the
+                               summed stages 1 and 3 (the left-factor products; stages 0
+                               and 2 keep 128); SFISTA_EINVAL otherwise.  Wider tiles read
+                               each factor block once for more columns, narrower ones
+                               spread the tiles more evenly over the SMs; sfista_tune
+                               measures every width per stage.                          */
     int gemm_stream_panels; /* tensor-core forms, stacked stages 0 and 2 (the right-factor
                                products): 0 (default) keeps each row tile's factor panel
                                (all K blocks of its band, hi and lo) resident in shared
@@ -449,9 +450,9 @@ typedef struct {
     int chunk;         /* terms staged per block in that stage (two-pass banded form);
                           for SFISTA_OP_BANDED_PERSISTENT entries the one-launch
                           solver's tile height th; for tensor-core stage entries the
-                          N tile width (stages 1, 3) or 1 / 0 for a resident / streamed
-                          factor panel (stages 0, 2; batch entries: stage -1);
-                          0 where none applies                                         */
+                          N tile width (64, 128 or 256), plus 1 for a resident factor
+                          panel (stages 0 and 2: 65 / 129); batch entries (stage -1):
+                          1 / 0 for resident / streamed panels; 0 where none applies */
     float ms;          /* mean time per stage (or per iteration), ms                  */
 } sfista_tune_entry;
 
@@ -476,9 +477,9 @@ typedef struct {
  *     tensor-core contexts compare the band-limited and full (dense) K
  *     ranges;
  *   - tensor-core forms: for each stage, timed alone in the chosen K range,
- *     the tile shapes gemm_bn and gemm_stream_panels select between (N tile
- *     64, 128 or 256 for stages 1 and 3; resident or streamed factor panel
- *     for stages 0 and 2 where the panel fits).
+ *     its tile shapes: N tile 64, 128 or 256 for stages 1 and 3 (the choice
+ *     gemm_bn fixes); N tile 64 or 128 for stages 0 and 2, each with a
+ *     streamed or (where the panel fits) resident factor panel.
  * An explicitly chosen form is kept (only its stages are tuned).  The chosen
  * configuration applies to later solves, sfista_apply and batches created
  * afterwards (sfista_info reports the form).

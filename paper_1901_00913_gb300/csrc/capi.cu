@@ -794,11 +794,13 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int ce
     if (c->op == SFISTA_OP_GEMM_BAND || c->op == SFISTA_OP_GEMM_DENSE) {
         st = gemm_create(&c->gemm, h, c->prec, c->op == SFISTA_OP_GEMM_DENSE, c->status, c->stream);
         if (st) return bail(st);
-        const int bn = o.gemm_bn ? o.gemm_bn : 128;
+        // gemm_bn: every stage's N tile; 256 exists for the summed stages
+        // only (the stacked ones keep 128 then).
+        const int bn = o.gemm_bn ? o.gemm_bn : 128, bn_stacked = bn == 64 ? 64 : 128;
         gemm_set_tile(c->gemm, 1, bn, 0);
         gemm_set_tile(c->gemm, 3, bn, 0);
-        gemm_set_tile(c->gemm, 0, 128, !o.gemm_stream_panels);
-        gemm_set_tile(c->gemm, 2, 128, !o.gemm_stream_panels);
+        gemm_set_tile(c->gemm, 0, bn_stacked, !o.gemm_stream_panels);
+        gemm_set_tile(c->gemm, 2, bn_stacked, !o.gemm_stream_panels);
         // FP32 state for the forms whose products are far coarser than FP32
         // (BF16, BF16x3, TF32); TF32x3 keeps the double-float state, which its
         // products are accurate enough to use (1.9e-6 vs 1.7e-5 at 512^2).
@@ -1780,11 +1782,12 @@ sfista_status sfista_tune(sfista_ctx *c, int iters, sfista_tune_entry *entries, 
     }
     if (c->gemm) {
         // Tile shape of each tensor-core stage in the chosen K mode, timed
-        // alone: the N tile width of the summed stages 1 and 3 (64, 128 or
-        // 256; entries report it in `chunk`) and the resident P panel of the
-        // stacked stages 0 and 2 (chunk 1; 0 = streamed).
+        // alone: the N tile width (entries report it in `chunk`) of the
+        // summed stages 1 and 3 (64, 128 or 256) and of the stacked stages 0
+        // and 2 (64 or 128, each streamed or, chunk + 1, with the resident
+        // factor panel).
         for (int s4 = 0; s4 < 4; ++s4) {
-            int bn[3], res[3];
+            int bn[4], res[4];
             const int nopt = gemm_tile_options(c->gemm, s4, bn, res);
             if (nopt < 2) continue;
             float best = 0.f;
@@ -1794,7 +1797,7 @@ sfista_status sfista_tune(sfista_ctx *c, int iters, sfista_tune_entry *entries, 
                 float t = 0.f;
                 st = time_stage_range(c, s4, s4, iters, &t);
                 if (st) return st;
-                log(c->op, s4, s4 % 2 == 0 ? res[o] : bn[o], t);
+                log(c->op, s4, s4 % 2 == 0 ? bn[o] + res[o] : bn[o], t);
                 if (bi < 0 || t < best) best = t, bi = o;
             }
             gemm_set_tile(c->gemm, s4, bn[bi], res[bi]);

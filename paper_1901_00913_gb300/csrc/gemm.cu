@@ -785,13 +785,14 @@ cudaError_t set_attr1() {
 }
 
 // Every kernel instance the launchers below can select: GE_SPLIT with
-// BN = 128 (streamed or, BF16, resident panel), GE_RESID / GE_PROX / GE_STORE
-// with BN = 64, 128 or 256 (single problems), GE_RESID / GE_PROX with 128
-// (grouped).
+// BN = 64 or 128 (streamed or, BF16, resident panel; grouped: 128),
+// GE_RESID / GE_PROX / GE_STORE with BN = 64, 128 or 256 (single problems),
+// GE_RESID / GE_PROX with 128 (grouped).
 template <int FMT, bool SPLIT>
 cudaError_t set_attrs() {
     cudaError_t e;
     if ((e = set_attr1<FMT, SPLIT, 128, GE_SPLIT, false, false>()) ||
+        (e = set_attr1<FMT, SPLIT, 64, GE_SPLIT, false, false>()) ||
         (e = set_attr1<FMT, SPLIT, 128, GE_SPLIT, true, false>()) ||
         (e = set_attr1<FMT, SPLIT, 128, GE_RESID, false, false>()) ||
         (e = set_attr1<FMT, SPLIT, 256, GE_RESID, false, false>()) ||
@@ -807,6 +808,7 @@ cudaError_t set_attrs() {
         return e;
     if constexpr (FMT == FMT_BF16) {
         if ((e = set_attr1<FMT, SPLIT, 128, GE_SPLIT, false, true>()) ||
+            (e = set_attr1<FMT, SPLIT, 64, GE_SPLIT, false, true>()) ||
             (e = set_attr1<FMT, SPLIT, 128, GE_SPLIT, true, true>()))
             return e;
     }
@@ -855,7 +857,11 @@ template <int FMT, bool SPLIT, int EPI>
 void launch_shape(const Operand &P, const Operand &Q, const Operand *O, const GemmArgs &a, int gy, int bn, bool res,
                   int sms, cudaStream_t s) {
     if constexpr (EPI == GE_SPLIT && FMT == FMT_BF16) {
+        if (res && bn == 64) return launch_tiles<FMT, SPLIT, EPI, 64, true>(P, Q, O, a, gy, sms, s);
         if (res) return launch_tiles<FMT, SPLIT, EPI, 128, true>(P, Q, O, a, gy, sms, s);
+    }
+    if constexpr (EPI == GE_SPLIT) {
+        if (bn == 64) return launch_tiles<FMT, SPLIT, EPI, 64, false>(P, Q, O, a, gy, sms, s);
     }
     if constexpr (EPI != GE_SPLIT) {
         if (bn == 256) return launch_tiles<FMT, SPLIT, EPI, 256, false>(P, Q, O, a, gy, sms, s);
@@ -922,7 +928,7 @@ sfista_status run_stacked(const GemmPath *g, int st, const Operand &P, const Ban
                           Operand &Out, cudaStream_t s) {
     int gy;
     GemmArgs a = stacked_args(g, band, Out, &gy);
-    return dispatch<GE_SPLIT>(g, P, Q, &Out, a, gy, 128, stage_res(g, st), s);
+    return dispatch<GE_SPLIT>(g, P, Q, &Out, a, gy, g->bn[st], stage_res(g, st), s);
 }
 
 template <int EPI>
@@ -1042,16 +1048,20 @@ sfista_status gemm_create(GemmPath **out, const HostSetup &h, int prec, bool den
         if ((st = make_map(&mm.o->map_hi, mm.o->hi, g->fmt, mm.d0, mm.d1, mm.d2, mm.rows))) return bail(st);
         if ((st = make_map(&mm.o->map_lo, mm.o->lo, g->fmt, mm.d0, mm.d1, mm.d2, mm.rows))) return bail(st);
     }
-    // Q operands of the summed stages with BN = 256 / 64: boxes of 256 / 64 rows.
+    // Q operands with BN = 256 (summed stages) or 64 (all stages): boxes of 256 / 64 rows.
     for (Operand *o : {&g->QT, &g->QU}) {
         if ((st = make_map(&o->map256_hi, o->hi, g->fmt, (int)m, (int)n, (int)r, 256))) return bail(st);
         if ((st = make_map(&o->map256_lo, o->lo, g->fmt, (int)m, (int)n, (int)r, 256))) return bail(st);
-        if ((st = make_map(&o->map64_hi, o->hi, g->fmt, (int)m, (int)n, (int)r, 64))) return bail(st);
-        if ((st = make_map(&o->map64_lo, o->lo, g->fmt, (int)m, (int)n, (int)r, 64))) return bail(st);
+    }
+    for (Operand *o : {&g->QT, &g->QU, &g->QY, &g->QR}) {
+        const int d0 = (o == &g->QY || o == &g->QR) ? (int)n : (int)m, d1 = (o == &g->QY || o == &g->QR) ? (int)m : (int)n;
+        const int d2 = (o == &g->QY || o == &g->QR) ? 1 : (int)r;
+        if ((st = make_map(&o->map64_hi, o->hi, g->fmt, d0, d1, d2, 64))) return bail(st);
+        if ((st = make_map(&o->map64_lo, o->lo, g->fmt, d0, d1, d2, 64))) return bail(st);
     }
     for (Operand *o : {&g->QY, &g->QR}) {
-        o->map256_hi = o->map64_hi = o->map_hi;
-        o->map256_lo = o->map64_lo = o->map_lo;
+        o->map256_hi = o->map_hi;
+        o->map256_lo = o->map_lo;
     }
     // Resident P panels for the stacked stages: BF16 band mode, every row
     // tile's band within three K blocks of 64.  On by default where allowed.
@@ -1076,8 +1086,10 @@ void gemm_set_dense(GemmPath *g, bool dense) { g->dense = dense; }
 int gemm_tile_options(const GemmPath *g, int st, int *bn, int *res) {
     int n = 0;
     if (st == 0 || st == 2) {
-        bn[n] = 128, res[n++] = 0;
-        if (g->res_ok[st] && !g->dense) bn[n] = 128, res[n++] = 1;
+        for (int w : {128, 64}) {
+            bn[n] = w, res[n++] = 0;
+            if (g->res_ok[st] && !g->dense) bn[n] = w, res[n++] = 1;
+        }
     } else {
         bn[n] = 64, res[n++] = 0;
         bn[n] = 128, res[n++] = 0;
@@ -1088,7 +1100,7 @@ int gemm_tile_options(const GemmPath *g, int st, int *bn, int *res) {
 
 void gemm_set_tile(GemmPath *g, int st, int bn, int res) {
     if (st == 0 || st == 2) {
-        g->bn[st] = 128;
+        g->bn[st] = bn == 64 ? 64 : 128;
         g->res[st] = res && g->res_ok[st];
     } else {
         g->bn[st] = bn == 256 || bn == 64 ? bn : 128;

@@ -19,8 +19,9 @@ void gemm_destroy(GemmPath *g);
 void gemm_set_dense(GemmPath *g, bool dense);
 // Tile shapes of stage st (0..3) that can be selected: the count returned,
 // entries of (N tile width, resident P panel) written to bn / res (at most
-// 3); the stacked stages 0 and 2 offer the resident panel in BF16 band mode
-// when the band fits it, the summed stages 1 and 3 the widths 64, 128, 256.
+// 4); the stacked stages 0 and 2 offer the widths 128 and 64, each also with
+// the resident panel in BF16 band mode when the band fits it, the summed
+// stages 1 and 3 the widths 64, 128, 256.
 int gemm_tile_options(const GemmPath *g, int st, int *bn, int *res);
 void gemm_set_tile(GemmPath *g, int st, int bn, int res);
 // The shape stage st runs with (res as it applies in the current K mode).
