@@ -91,7 +91,7 @@ typedef enum {
                                   image that toep + hank encode is separable, so
                                   sum_i B_i X A_i^T is one 2-D convolution of the extended
                                   image with the rank-r kernel sum_i c_i d_i^T, done by
-                                  mixed-radix (2, 3, 4, 5) FFTs in shared memory; cost
+                                  mixed-radix (2 - 16, 3, 9, 5) FFTs in shared memory; cost
                                   O(mn log mn) per application, independent of r and of the
                                   PSF width.  Requires m + psf_rows - 1 and
                                   n + psf_cols - 1 <= 8192. */

@@ -192,6 +192,90 @@ __device__ __forceinline__ void dft<8, true>(float2 (&v)[8]) {
     dft8<true>(v);
 }
 
+// a * exp(-+i theta) with c = cos(theta), sn = sin(theta) (minus: forward,
+// plus: INV).
+template <bool INV>
+__device__ __forceinline__ float2 twc(float2 a, float c, float sn) {
+    return INV ? make_float2(a.x * c - a.y * sn, a.y * c + a.x * sn)
+               : make_float2(a.x * c + a.y * sn, a.y * c - a.x * sn);
+}
+
+// R = n1 n2 in two levels (Cooley-Tukey on the register array): with
+// v[n2 k2 + k1] (k2 < n1, k1 < n2),
+//   X[u1 + n1 u2] = sum_k1 w_R^(k1 u1) w_n2^(k1 u2) sum_k2 v[n2 k2 + k1] w_n1^(k2 u1),
+// i.e. n2 DFTs of n1 points, the internal twiddles w_R^(k1 u1), then n1
+// DFTs of n2 points.  R = 16 = 4 x 4: w16^k = cos(2 pi k / 16) -+ i sin(.).
+template <bool INV>
+__device__ __forceinline__ void dft16(float2 (&v)[16]) {
+    const float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f;   // k = 1 (k = 3: swapped)
+    const float h = 0.70710678118654752440f;                                   // k = 2, 6
+    float2 y[4][4];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        float2 a[4] = {v[k1], v[4 + k1], v[8 + k1], v[12 + k1]};
+        dft4<INV>(a);
+#pragma unroll
+        for (int u1 = 0; u1 < 4; ++u1) y[k1][u1] = a[u1];
+    }
+    // w16^(k1 u1), k1 u1 in {1, 2, 3, 4, 6, 9}
+    y[1][1] = twc<INV>(y[1][1], c1, s1);
+    y[1][2] = twc<INV>(y[1][2], h, h);
+    y[1][3] = twc<INV>(y[1][3], s1, c1);
+    y[2][1] = twc<INV>(y[2][1], h, h);
+    y[2][2] = rot<INV>(y[2][2]);
+    y[2][3] = twc<INV>(y[2][3], -h, h);
+    y[3][1] = twc<INV>(y[3][1], s1, c1);
+    y[3][2] = twc<INV>(y[3][2], -h, h);
+    y[3][3] = twc<INV>(y[3][3], -c1, -s1);
+#pragma unroll
+    for (int u1 = 0; u1 < 4; ++u1) {
+        float2 b[4] = {y[0][u1], y[1][u1], y[2][u1], y[3][u1]};
+        dft4<INV>(b);
+#pragma unroll
+        for (int u2 = 0; u2 < 4; ++u2) v[u1 + 4 * u2] = b[u2];
+    }
+}
+template <>
+__device__ __forceinline__ void dft<16, false>(float2 (&v)[16]) {
+    dft16<false>(v);
+}
+template <>
+__device__ __forceinline__ void dft<16, true>(float2 (&v)[16]) {
+    dft16<true>(v);
+}
+
+// R = 9 = 3 x 3 the same way; w9^k = cos(2 pi k / 9) -+ i sin(.), k in {1, 2, 4}.
+template <bool INV>
+__device__ __forceinline__ void dft9(float2 (&v)[9]) {
+    float2 y[3][3];
+#pragma unroll
+    for (int k1 = 0; k1 < 3; ++k1) {
+        float2 a[3] = {v[k1], v[3 + k1], v[6 + k1]};
+        dft3<INV>(a);
+#pragma unroll
+        for (int u1 = 0; u1 < 3; ++u1) y[k1][u1] = a[u1];
+    }
+    y[1][1] = twc<INV>(y[1][1], 0.76604444311897803520f, 0.64278760968653932632f);
+    y[1][2] = twc<INV>(y[1][2], 0.17364817766693034885f, 0.98480775301220805936f);
+    y[2][1] = twc<INV>(y[2][1], 0.17364817766693034885f, 0.98480775301220805936f);
+    y[2][2] = twc<INV>(y[2][2], -0.93969262078590838405f, 0.34202014332566873304f);
+#pragma unroll
+    for (int u1 = 0; u1 < 3; ++u1) {
+        float2 b[3] = {y[0][u1], y[1][u1], y[2][u1]};
+        dft3<INV>(b);
+#pragma unroll
+        for (int u2 = 0; u2 < 3; ++u2) v[u1 + 3 * u2] = b[u2];
+    }
+}
+template <>
+__device__ __forceinline__ void dft<9, false>(float2 (&v)[9]) {
+    dft9<false>(v);
+}
+template <>
+__device__ __forceinline__ void dft<9, true>(float2 (&v)[9]) {
+    dft9<true>(v);
+}
+
 // One butterfly of a stage: the R points x[k * M], k < R, with the stage's
 // twiddles w[u - 1] = w_L^(u q), u >= 1, already loaded.
 // DIF (forward): DFT, then the twiddles on outputs u >= 1.
@@ -253,7 +337,7 @@ __device__ __forceinline__ void fft_stage_lines(int buf, int lines, int ls, int 
 // twiddle table in shared memory.  Forward: DIF, natural order in,
 // digit-reversed out.  INV: DIT with the stages in reverse order,
 // digit-reversed in, natural out, unscaled.
-template <bool INV>
+template <bool INV, bool BIG>
 __device__ void fft_lines(int buf, int lines, int ls, const FftLine &P, int tw) {
     for (int jj = 0; jj < P.ns; ++jj) {
         const int j = INV ? P.ns - 1 - jj : jj;
@@ -264,6 +348,12 @@ __device__ void fft_lines(int buf, int lines, int ls, const FftLine &P, int tw) 
             case 3: fft_stage_lines<3, INV>(buf, lines, ls, P.N, M, t); break;
             case 4: fft_stage_lines<4, INV>(buf, lines, ls, P.N, M, t); break;
             case 5: fft_stage_lines<5, INV>(buf, lines, ls, P.N, M, t); break;
+            case 9:
+                if constexpr (BIG) fft_stage_lines<9, INV>(buf, lines, ls, P.N, M, t);
+                break;
+            case 16:
+                if constexpr (BIG) fft_stage_lines<16, INV>(buf, lines, ls, P.N, M, t);
+                break;
             default: fft_stage_lines<8, INV>(buf, lines, ls, P.N, M, t); break;
         }
         __syncthreads();
@@ -359,7 +449,7 @@ __device__ __forceinline__ void batched_lines(int cols, Load load, Use use) {
 
 // Pass A: rows (extended rows for the forward operator) -> half spectra S1
 // (8-row tiles).  LPC: complex lines (row pairs) per block.
-template <bool ADJ, int LPC>
+template <bool ADJ, int LPC, bool BIG>
 __global__ void __launch_bounds__(kThreads) fft_pass_a(FftConvDev P, const float *__restrict__ In) {
     const int N = P.l2.N, ls = N + 1;
     const PassSmem sm = pass_smem(LPC, N);
@@ -389,7 +479,7 @@ __global__ void __launch_bounds__(kThreads) fft_pass_a(FftConvDev P, const float
         },
         [&](int j, int t, float2 v) { fft_sm[j * ls + t] = v; });
     __syncthreads();
-    fft_lines<false>(0, LPC, ls, P.l2, sm.tw);
+    fft_lines<false, BIG>(0, LPC, ls, P.l2, sm.tw);
     // Z = FFT(a + i b): A[f] = (Z[f] + conj Z[N-f]) / 2, B[f] = (Z[f] - conj Z[N-f]) / (2i);
     // the two rows' values at f leave as one 16-byte store, neighbouring
     // threads taking neighbouring row pairs of the same f (one contiguous run
@@ -409,7 +499,7 @@ __global__ void __launch_bounds__(kThreads) fft_pass_a(FftConvDev P, const float
 
 // Pass B: frequency lines of S1 -> kernel product along the rows -> S2.
 // LPC: neighbouring frequencies per block.
-template <bool ADJ, int LPC>
+template <bool ADJ, int LPC, bool BIG>
 __global__ void __launch_bounds__(kThreads) fft_pass_b(FftConvDev P) {
     const int N = P.l1.N, ls = N + 1;
     const PassSmem sm = pass_smem(LPC, N);
@@ -432,7 +522,7 @@ __global__ void __launch_bounds__(kThreads) fft_pass_b(FftConvDev P) {
             if (s < N) fft_sm[(rem >> 3) * ls + s] = v;
         });
     __syncthreads();
-    fft_lines<false>(0, LPC, ls, P.l1, sm.tw);
+    fft_lines<false, BIG>(0, LPC, ls, P.l1, sm.tw);
     batched_lines<LPC, float2>(
         N,
         [&](int j, int t) { return f0 + j < P.H2 ? __ldg(P.K + (size_t)(f0 + j) * N + t) : make_float2(0.f, 0.f); },
@@ -441,7 +531,7 @@ __global__ void __launch_bounds__(kThreads) fft_pass_b(FftConvDev P) {
             x = ADJ ? cmulc(x, k) : cmul(x, k);
         });
     __syncthreads();
-    fft_lines<true>(0, LPC, ls, P.l1, sm.tw);
+    fft_lines<true, BIG>(0, LPC, ls, P.l1, sm.tw);
     const int mt = (P.m + 7) & ~7;
     for (int it = threadIdx.x; it < LPC * mt; it += blockDim.x) {
         const int ab = it / run, rem = it - ab * run;
@@ -468,7 +558,7 @@ __global__ void __launch_bounds__(kThreads) fft_pass_b(FftConvDev P) {
 
 // Pass C: two rows' half spectra -> one inverse FFT -> the two output rows,
 // then the epilogue.  LPC: row pairs per block.
-template <bool ADJ, int EPI, int LPC>
+template <bool ADJ, int EPI, int LPC, bool BIG>
 __global__ void __launch_bounds__(kThreads) fft_pass_c(FftConvDev P, float *__restrict__ Out, ProxArgs pa) {
     const int N = P.l2.N, ls = N + 1;
     const PassSmem sm = pass_smem(LPC, N);
@@ -495,7 +585,7 @@ __global__ void __launch_bounds__(kThreads) fft_pass_c(FftConvDev P, float *__re
             fft_sm[j * ls + pos[f]] = make_float2(y.x - y.w, y.y + y.z);
         });
     __syncthreads();
-    fft_lines<true>(0, LPC, ls, P.l2, sm.tw);
+    fft_lines<true, BIG>(0, LPC, ls, P.l2, sm.tw);
     // Output pixels of each of the block's 2 LPC rows, kEpi per thread at a
     // time (their state / observation loads issued together).
     const int n = P.n;
@@ -547,24 +637,43 @@ __global__ void __launch_bounds__(kThreads) fft_pass_c(FftConvDev P, float *__re
     }
 }
 
-// Kernel instances by lines per block (1, 2, 4).
-template <bool ADJ>
-void launch_a(int lpc, int grid, size_t smem, cudaStream_t s, const FftConvDev &d, const float *In) {
-    if (lpc == 4) fft_pass_a<ADJ, 4><<<grid, kThreads, smem, s>>>(d, In);
-    else if (lpc == 2) fft_pass_a<ADJ, 2><<<grid, kThreads, smem, s>>>(d, In);
-    else fft_pass_a<ADJ, 1><<<grid, kThreads, smem, s>>>(d, In);
+// Kernel instances by lines per block (1, 2, 4) and by whether the line's
+// plan has radix-9 / radix-16 stages (BIG: those butterflies need about
+// twice the registers, so plans without them use instances without them
+// and keep their occupancy).
+template <bool ADJ, bool BIG>
+void launch_a2(int lpc, int grid, size_t smem, cudaStream_t s, const FftConvDev &d, const float *In) {
+    if (lpc == 4) fft_pass_a<ADJ, 4, BIG><<<grid, kThreads, smem, s>>>(d, In);
+    else if (lpc == 2) fft_pass_a<ADJ, 2, BIG><<<grid, kThreads, smem, s>>>(d, In);
+    else fft_pass_a<ADJ, 1, BIG><<<grid, kThreads, smem, s>>>(d, In);
 }
 template <bool ADJ>
-void launch_b(int lpc, int grid, size_t smem, cudaStream_t s, const FftConvDev &d) {
-    if (lpc == 4) fft_pass_b<ADJ, 4><<<grid, kThreads, smem, s>>>(d);
-    else if (lpc == 2) fft_pass_b<ADJ, 2><<<grid, kThreads, smem, s>>>(d);
-    else fft_pass_b<ADJ, 1><<<grid, kThreads, smem, s>>>(d);
+void launch_a(int lpc, bool big, int grid, size_t smem, cudaStream_t s, const FftConvDev &d, const float *In) {
+    if (big) launch_a2<ADJ, true>(lpc, grid, smem, s, d, In);
+    else launch_a2<ADJ, false>(lpc, grid, smem, s, d, In);
+}
+template <bool ADJ, bool BIG>
+void launch_b2(int lpc, int grid, size_t smem, cudaStream_t s, const FftConvDev &d) {
+    if (lpc == 4) fft_pass_b<ADJ, 4, BIG><<<grid, kThreads, smem, s>>>(d);
+    else if (lpc == 2) fft_pass_b<ADJ, 2, BIG><<<grid, kThreads, smem, s>>>(d);
+    else fft_pass_b<ADJ, 1, BIG><<<grid, kThreads, smem, s>>>(d);
+}
+template <bool ADJ>
+void launch_b(int lpc, bool big, int grid, size_t smem, cudaStream_t s, const FftConvDev &d) {
+    if (big) launch_b2<ADJ, true>(lpc, grid, smem, s, d);
+    else launch_b2<ADJ, false>(lpc, grid, smem, s, d);
+}
+template <bool ADJ, int EPI, bool BIG>
+void launch_c2(int lpc, int grid, size_t smem, cudaStream_t s, const FftConvDev &d, float *Out, const ProxArgs &pa) {
+    if (lpc == 4) fft_pass_c<ADJ, EPI, 4, BIG><<<grid, kThreads, smem, s>>>(d, Out, pa);
+    else if (lpc == 2) fft_pass_c<ADJ, EPI, 2, BIG><<<grid, kThreads, smem, s>>>(d, Out, pa);
+    else fft_pass_c<ADJ, EPI, 1, BIG><<<grid, kThreads, smem, s>>>(d, Out, pa);
 }
 template <bool ADJ, int EPI>
-void launch_c(int lpc, int grid, size_t smem, cudaStream_t s, const FftConvDev &d, float *Out, const ProxArgs &pa) {
-    if (lpc == 4) fft_pass_c<ADJ, EPI, 4><<<grid, kThreads, smem, s>>>(d, Out, pa);
-    else if (lpc == 2) fft_pass_c<ADJ, EPI, 2><<<grid, kThreads, smem, s>>>(d, Out, pa);
-    else fft_pass_c<ADJ, EPI, 1><<<grid, kThreads, smem, s>>>(d, Out, pa);
+void launch_c(int lpc, bool big, int grid, size_t smem, cudaStream_t s, const FftConvDev &d, float *Out,
+              const ProxArgs &pa) {
+    if (big) launch_c2<ADJ, EPI, true>(lpc, grid, smem, s, d, Out, pa);
+    else launch_c2<ADJ, EPI, false>(lpc, grid, smem, s, d, Out, pa);
 }
 
 // ------------------------------------------------------------------ host plan
@@ -578,14 +687,25 @@ int smooth_len(int need) {
     return (int)best;
 }
 
-// DIF stages of length N: the factors 2 as radix 8 and 4 (a single 2 only
-// when the power of two is odd and below 8, or after the 8s), then 3s, 5s.
+// DIF stages of length N.  Long lines (N / R >= 128: a butterfly for
+// every thread of a block's half) take the factors 2 as radix 16
+// (in-register 4 x 4) and the factors 3 as radix 9 (3 x 3): fewer stages,
+// each one pass over the line in shared memory and one block barrier.
+// Otherwise, and for what remains, the factors 2 as radix 8 and 4 (a single
+// 2 only when the power of two is odd and below 8, or after the 8s), then
+// 3s, then 5s.  (Measured: 2160-point lines 16, 9, 3, 5 against 4, 4, 3, 3,
+// 3, 5: 6 % faster per solve; 640-point lines 16, 8, 5 against 8, 4, 4, 5:
+// 2 % slower, as a radix-16 stage has only 40 butterflies there.)
 bool line_plan(int N, FftLine *P, std::vector<double2> *tw) {
     std::vector<int> rad;
     int r = N, n2 = 0;
     while (r % 2 == 0) {
         r /= 2;
         ++n2;
+    }
+    while (n2 >= 4 && N / 16 >= 128) {
+        rad.push_back(16);
+        n2 -= 4;
     }
     while (n2 >= 3 && n2 != 4) {
         rad.push_back(8);
@@ -596,6 +716,10 @@ bool line_plan(int N, FftLine *P, std::vector<double2> *tw) {
         n2 -= 2;
     }
     if (n2 == 1) rad.push_back(2);
+    while (r % 9 == 0 && N / 9 >= 128) {
+        rad.push_back(9);
+        r /= 9;
+    }
     while (r % 3 == 0) {
         rad.push_back(3);
         r /= 3;
@@ -676,22 +800,25 @@ template <typename K>
 cudaError_t allow_smem(K kernel, int limit) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
 }
-template <int LPC>
+template <int LPC, bool BIG>
 cudaError_t allow_smem_lpc(int limit) {
     cudaError_t e;
-    if ((e = allow_smem(fft_pass_a<false, LPC>, limit)) || (e = allow_smem(fft_pass_a<true, LPC>, limit)) ||
-        (e = allow_smem(fft_pass_b<false, LPC>, limit)) || (e = allow_smem(fft_pass_b<true, LPC>, limit)) ||
-        (e = allow_smem(fft_pass_c<false, EPI_STORE, LPC>, limit)) ||
-        (e = allow_smem(fft_pass_c<false, EPI_RESIDUAL, LPC>, limit)) ||
-        (e = allow_smem(fft_pass_c<true, EPI_STORE, LPC>, limit)) ||
-        (e = allow_smem(fft_pass_c<true, EPI_PROX, LPC>, limit)))
+    if ((e = allow_smem(fft_pass_a<false, LPC, BIG>, limit)) || (e = allow_smem(fft_pass_a<true, LPC, BIG>, limit)) ||
+        (e = allow_smem(fft_pass_b<false, LPC, BIG>, limit)) || (e = allow_smem(fft_pass_b<true, LPC, BIG>, limit)) ||
+        (e = allow_smem(fft_pass_c<false, EPI_STORE, LPC, BIG>, limit)) ||
+        (e = allow_smem(fft_pass_c<false, EPI_RESIDUAL, LPC, BIG>, limit)) ||
+        (e = allow_smem(fft_pass_c<true, EPI_STORE, LPC, BIG>, limit)) ||
+        (e = allow_smem(fft_pass_c<true, EPI_PROX, LPC, BIG>, limit)))
         return e;
     return cudaSuccess;
 }
 cudaError_t allow_smem_all(size_t sa, size_t sb, size_t sc, int limit) {
     if (sa > (size_t)limit || sb > (size_t)limit || sc > (size_t)limit) return cudaErrorInvalidValue;
     cudaError_t e;
-    if ((e = allow_smem_lpc<1>(limit)) || (e = allow_smem_lpc<2>(limit)) || (e = allow_smem_lpc<4>(limit))) return e;
+    if ((e = allow_smem_lpc<1, false>(limit)) || (e = allow_smem_lpc<2, false>(limit)) ||
+        (e = allow_smem_lpc<4, false>(limit)) || (e = allow_smem_lpc<1, true>(limit)) ||
+        (e = allow_smem_lpc<2, true>(limit)) || (e = allow_smem_lpc<4, true>(limit)))
+        return e;
     return cudaSuccess;
 }
 
@@ -777,6 +904,13 @@ sfista_status fftconv_create(FftConv **out, const double *K, int p, int q, int c
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const size_t budget = 110 * 1024;
+    auto has_big = [](const FftLine &P) {
+        for (int j = 0; j < P.ns; ++j)
+            if (P.R[j] == 9 || P.R[j] == 16) return true;
+        return false;
+    };
+    f->big1 = has_big(d.l1);
+    f->big2 = has_big(d.l2);
     f->lpc_a = pick_lpc((d.ext_rows + 1) / 2, N2, sms, true, budget);
     f->lpc_b = pick_lpc(H2, N1, sms, false, budget);
     f->lpc_c = pick_lpc((m + 1) / 2, N2, sms, true, budget);
@@ -807,29 +941,29 @@ void fftconv_part(const FftConv *f, int part, bool adj, const float *In, EpiKind
         const int ga = (int)(((rows + 1) / 2 + f->lpc_a - 1) / f->lpc_a);
         const size_t sa = pass_smem_bytes(f->lpc_a, d.l2.N, true);
         if (adj)
-            launch_a<true>(f->lpc_a, ga, sa, s, d, In);
+            launch_a<true>(f->lpc_a, f->big2, ga, sa, s, d, In);
         else
-            launch_a<false>(f->lpc_a, ga, sa, s, d, In);
+            launch_a<false>(f->lpc_a, f->big2, ga, sa, s, d, In);
         const int gb = (d.H2 + f->lpc_b - 1) / f->lpc_b;
         const size_t sb = pass_smem_bytes(f->lpc_b, d.l1.N, false);
         if (adj)
-            launch_b<true>(f->lpc_b, gb, sb, s, d);
+            launch_b<true>(f->lpc_b, f->big1, gb, sb, s, d);
         else
-            launch_b<false>(f->lpc_b, gb, sb, s, d);
+            launch_b<false>(f->lpc_b, f->big1, gb, sb, s, d);
         return;
     }
     const int gc = ((d.m + 1) / 2 + f->lpc_c - 1) / f->lpc_c;
     const size_t sc = pass_smem_bytes(f->lpc_c, d.l2.N, true);
     if (adj) {
         if (epi == EPI_PROX)
-            launch_c<true, EPI_PROX>(f->lpc_c, gc, sc, s, d, Out, pa);
+            launch_c<true, EPI_PROX>(f->lpc_c, f->big2, gc, sc, s, d, Out, pa);
         else
-            launch_c<true, EPI_STORE>(f->lpc_c, gc, sc, s, d, Out, pa);
+            launch_c<true, EPI_STORE>(f->lpc_c, f->big2, gc, sc, s, d, Out, pa);
     } else {
         if (epi == EPI_RESIDUAL)
-            launch_c<false, EPI_RESIDUAL>(f->lpc_c, gc, sc, s, d, Out, pa);
+            launch_c<false, EPI_RESIDUAL>(f->lpc_c, f->big2, gc, sc, s, d, Out, pa);
         else
-            launch_c<false, EPI_STORE>(f->lpc_c, gc, sc, s, d, Out, pa);
+            launch_c<false, EPI_STORE>(f->lpc_c, f->big2, gc, sc, s, d, Out, pa);
     }
 }
 

@@ -35,6 +35,7 @@ struct FftConvDev {
 struct FftConv {
     FftConvDev d{};
     int lpc_a = 1, lpc_b = 1, lpc_c = 1;   // lines per block of the three passes
+    bool big1 = false, big2 = false;        // the column (l1) / row (l2) plan has radix-9 or radix-16 stages
 };
 
 // K: p x q kernel (FP64, row-major) with centre (cr, cc), for m x n images.

@@ -68,6 +68,24 @@ def test_fft_apply_wide_psf(bc):
     s.close()
 
 
+@pytest.mark.parametrize("bc", [0, 1])
+def test_fft_apply_long_lines(bc):
+    """2100 x 2104 image with a 31 x 27 PSF: both extended axes (2130) take 2160-point lines, whose
+    plan has the in-register radix-16 and radix-9 stages (16, 9, 3, 5); A_s X and A_s^T X against the
+    oracle."""
+    m, n = 2100, 2104
+    g = W.rng(320 + bc)
+    P = W.random_psf(g, 31, 27)
+    ka = kron.kron_approx(P, 15, 13, m, n, bc, 2)
+    s = api.Sfista(P, (m, n), bc, 2, center=(15, 13), prec="fp32", op="fft", lipschitz=1.0)
+    X = g.standard_normal((m, n)).astype(np.float32)
+    for tr in (False, True):
+        Y = s.apply(_cuda(X), transpose=tr).cpu().numpy()
+        Yo = (oracle.kron_apply_T if tr else oracle.kron_apply)(X.astype(np.float64), ka)
+        assert oracle.rel_fro(Y, Yo) < OP_TOL, (tr, oracle.rel_fro(Y, Yo))
+    s.close()
+
+
 def _observation(x, P, cr, cc, bc, g, level=0.01):
     bx = oracle.blur(x, P, cr, cc, bc)
     return (bx + W.noise_scale(bx, g.standard_normal(x.shape), level)).astype(np.float32)
