@@ -136,19 +136,21 @@ typedef struct {
                                solver is not used, and the two-pass persistent form is
                                used instead if those tiles do not all fit).             */
     int gemm_bn;            /* tensor-core forms: N tile width of the GEMM stages: 0
-                               (default) = 128; 64 or 128 for all four stages, 256 for the
-                               summed stages 1 and 3 (the left-factor products; stages 0
-                               and 2 keep 128); SFISTA_EINVAL otherwise.  Wider tiles read
-                               each factor block once for more columns, narrower ones
-                               spread the tiles more evenly over the SMs; sfista_tune
-                               measures every width per stage.                          */
-    int gemm_stream_panels; /* tensor-core forms, stacked stages 0 and 2 (the right-factor
-                               products): 0 (default) keeps each row tile's factor panel
-                               (all K blocks of its band, hi and lo) resident in shared
-                               memory while the tiles that share it run, where that is
-                               possible (BF16 and BF16x3 band mode, every band within
-                               three K blocks of 64); 1 streams the panel with every
-                               tile.  sfista_tune measures both.                        */
+                               (default): per stage, 64 where the stage has fewer tiles
+                               of 128 columns than the GPU has SMs, else 128; 64 or 128
+                               for all four stages; 256 for the summed stages 1 and 3
+                               (the left-factor products; stages 0 and 2 keep 128);
+                               SFISTA_EINVAL otherwise.  Wider tiles read each factor
+                               block once for more columns, narrower ones spread the
+                               tiles more evenly over the SMs; sfista_tune measures
+                               every width per stage.                                   */
+    int gemm_resident_panels; /* tensor-core forms, stacked stages 0 and 2 (the right-
+                               factor products): 0 (default) streams each tile's factor
+                               panel with the tile's other operand; 1 keeps the panel of
+                               a row tile (all K blocks of its band, hi and lo) resident
+                               in shared memory while the tiles that share it run, where
+                               that is possible (BF16 and BF16x3 band mode, every band
+                               within three K blocks of 64).  sfista_tune measures both. */
 } sfista_opts;
 
 /* Fill *opts with the defaults listed above. */

@@ -40,7 +40,7 @@ class Opts(ctypes.Structure):
                 ("lipschitz_tol", ctypes.c_double), ("lipschitz_maxit", ctypes.c_int),
                 ("device", ctypes.c_int), ("l1", ctypes.c_double), ("refine_every", ctypes.c_int),
                 ("tile_override", ctypes.c_int), ("gemm_bn", ctypes.c_int),
-                ("gemm_stream_panels", ctypes.c_int)]
+                ("gemm_resident_panels", ctypes.c_int)]
 
 
 def load(path=None):
@@ -463,7 +463,7 @@ class Sfista:
 
     def __init__(self, psf, shape, bc, r, center=(-1, -1), prec="fp32", op="auto", project=False,
                  use_graph=True, lipschitz=None, lipschitz_tol=1e-10, lipschitz_maxit=1000, device=-1, l1=0.0,
-                 refine_every=0, tile_override=0, exact=False, gemm_bn=0, gemm_stream_panels=False):
+                 refine_every=0, tile_override=0, exact=False, gemm_bn=0, gemm_resident_panels=False):
         """exact=True: the exact blur A instead of the rank-r approximation (sfista_setup_exact; r unused)."""
         o = default_opts()
         o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
@@ -478,7 +478,7 @@ class Sfista:
         o.refine_every = int(refine_every)
         o.tile_override = int(tile_override)
         o.gemm_bn = int(gemm_bn)
-        o.gemm_stream_panels = int(bool(gemm_stream_panels))
+        o.gemm_resident_panels = int(bool(gemm_resident_panels))
         bcv = BC[bc] if isinstance(bc, str) else int(bc)
         self.shape = (int(shape[0]), int(shape[1]))
         self.psf_shape = np.asarray(psf).shape

@@ -652,7 +652,7 @@ void sfista_default_opts(sfista_opts *o) {
     o->refine_every = 0;
     o->tile_override = 0;
     o->gemm_bn = 0;
-    o->gemm_stream_panels = 0;
+    o->gemm_resident_panels = 0;
 }
 
 sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int center_row,
@@ -673,8 +673,8 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int ce
         return fail(SFISTA_EINVAL, "tile_override must be 0 or a multiple of 4 from 16 to 64");
     if (o.gemm_bn != 0 && o.gemm_bn != 64 && o.gemm_bn != 128 && o.gemm_bn != 256)
         return fail(SFISTA_EINVAL, "gemm_bn must be 0, 64, 128 or 256");
-    if (o.gemm_stream_panels != 0 && o.gemm_stream_panels != 1)
-        return fail(SFISTA_EINVAL, "gemm_stream_panels must be 0 or 1");
+    if (o.gemm_resident_panels != 0 && o.gemm_resident_panels != 1)
+        return fail(SFISTA_EINVAL, "gemm_resident_panels must be 0 or 1");
     if (center_row == -1 && psf_rows > 0) center_row = (psf_rows - 1) / 2;
     if (center_col == -1 && psf_cols > 0) center_col = (psf_cols - 1) / 2;
     sfista_ctx *c = new (std::nothrow) sfista_ctx();
@@ -794,13 +794,14 @@ sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols, int ce
     if (c->op == SFISTA_OP_GEMM_BAND || c->op == SFISTA_OP_GEMM_DENSE) {
         st = gemm_create(&c->gemm, h, c->prec, c->op == SFISTA_OP_GEMM_DENSE, c->status, c->stream);
         if (st) return bail(st);
-        // gemm_bn: every stage's N tile; 256 exists for the summed stages
-        // only (the stacked ones keep 128 then).
-        const int bn = o.gemm_bn ? o.gemm_bn : 128, bn_stacked = bn == 64 ? 64 : 128;
-        gemm_set_tile(c->gemm, 1, bn, 0);
-        gemm_set_tile(c->gemm, 3, bn, 0);
-        gemm_set_tile(c->gemm, 0, bn_stacked, !o.gemm_stream_panels);
-        gemm_set_tile(c->gemm, 2, bn_stacked, !o.gemm_stream_panels);
+        // gemm_bn: every stage's N tile (256 exists for the summed stages
+        // only; the stacked ones keep 128 then); 0: per stage, 64 where the
+        // stage has fewer 128-column tiles than the GPU has SMs, else 128.
+        for (int s4 = 0; s4 < 4; ++s4) {
+            int bn = o.gemm_bn ? o.gemm_bn : gemm_default_bn(c->gemm, s4);
+            if (s4 % 2 == 0 && bn == 256) bn = 128;
+            gemm_set_tile(c->gemm, s4, bn, s4 % 2 == 0 ? o.gemm_resident_panels : 0);
+        }
         // FP32 state for the forms whose products are far coarser than FP32
         // (BF16, BF16x3, TF32); TF32x3 keeps the double-float state, which its
         // products are accurate enough to use (1.9e-6 vs 1.7e-5 at 512^2).

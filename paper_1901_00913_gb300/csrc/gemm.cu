@@ -1063,15 +1063,14 @@ sfista_status gemm_create(GemmPath **out, const HostSetup &h, int prec, bool den
         o->map256_hi = o->map_hi;
         o->map256_lo = o->map_lo;
     }
-    // Resident P panels for the stacked stages: BF16 band mode, every row
-    // tile's band within three K blocks of 64.  On by default where allowed.
+    // Resident P panels for the stacked stages: allowed in BF16 band mode when
+    // every row tile's band lies within three K blocks of 64 (off by default;
+    // the context's options or the tuner switch them on).
     if (g->fmt == FMT_BF16) {
         using CB = Cfg<FMT_BF16, true, 128>;
         constexpr int kres = PCfg<FMT_BF16, true, 128, true>::RES_KB;
         g->res_ok[0] = band_kblocks_max((int)n, h.A, CB::ALIGN, CB::KB_ELEMS) <= kres;
         g->res_ok[2] = band_kblocks_max((int)n, h.AT, CB::ALIGN, CB::KB_ELEMS) <= kres;
-        g->res[0] = g->res_ok[0];
-        g->res[2] = g->res_ok[2];
     }
     *out = g;
     return SFISTA_OK;
@@ -1106,6 +1105,12 @@ void gemm_set_tile(GemmPath *g, int st, int bn, int res) {
         g->bn[st] = bn == 256 || bn == 64 ? bn : 128;
         g->res[st] = false;
     }
+}
+
+int gemm_default_bn(const GemmPath *g, int st) {
+    const int mt = (st % 2 == 0) ? ((g->n + BM - 1) / BM) * g->r : (g->m + BM - 1) / BM;
+    const int N = (st % 2 == 0) ? g->m : g->n;
+    return (long)mt * ((N + 127) / 128) < g->sms ? 64 : 128;
 }
 
 void gemm_get_tile(const GemmPath *g, int st, int *bn, int *res) {

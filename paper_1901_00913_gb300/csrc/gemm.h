@@ -24,6 +24,9 @@ void gemm_set_dense(GemmPath *g, bool dense);
 // stages 1 and 3 the widths 64, 128, 256.
 int gemm_tile_options(const GemmPath *g, int st, int *bn, int *res);
 void gemm_set_tile(GemmPath *g, int st, int bn, int res);
+// The default N tile of stage st: 64 when the stage has fewer tiles of 128
+// columns than the GPU has SMs (most SMs would idle), else 128.
+int gemm_default_bn(const GemmPath *g, int st);
 // The shape stage st runs with (res as it applies in the current K mode).
 void gemm_get_tile(const GemmPath *g, int st, int *bn, int *res);
 // Split-operand copies of Y that the prox epilogue must write.

@@ -108,11 +108,11 @@ def test_default_opts(lib):
     assert o.prec == 0 and o.op == 0 and o.use_graph == 1 and o.device == -1
     assert o.lipschitz == 0.0 and o.lipschitz_maxit > 0
     assert o.l1 == 0.0 and o.refine_every == 0
-    assert o.tile_override == 0 and o.gemm_bn == 0 and o.gemm_stream_panels == 0
+    assert o.tile_override == 0 and o.gemm_bn == 0 and o.gemm_resident_panels == 0
 
 
 @pytest.mark.parametrize("field,value", [("refine_every", -1), ("l1", -0.5), ("prec", 9), ("tile_override", 30),
-                                         ("gemm_bn", 192), ("gemm_bn", 32), ("gemm_stream_panels", 2)])
+                                         ("gemm_bn", 192), ("gemm_bn", 32), ("gemm_resident_panels", 2)])
 def test_option_errors(lib, field, value):
     o = api.default_opts()
     setattr(o, field, value)

@@ -51,7 +51,7 @@ def test_tile_shapes_apply_match_oracle(prec, bc):
     out = {}
     for bn, stream in _shapes():
         s = api.Sfista(P, (M, N), bc, 3, center=(cr, cc), prec=prec, op="gemm_band", lipschitz=1.0, gemm_bn=bn,
-                       gemm_stream_panels=stream)
+                       gemm_resident_panels=not stream)
         for tr in (False, True):
             Y = s.apply(_cuda(X), transpose=tr)
             out[(bn, stream, tr)] = Y
@@ -94,7 +94,7 @@ def test_tile_shapes_solve_match_oracle(solved, prec):
     res = {}
     for bn, stream in _shapes():
         s = api.Sfista(P, (M, N), 1, 3, center=c, prec=prec, op="gemm_band", lipschitz=L, gemm_bn=bn,
-                       gemm_stream_panels=stream)
+                       gemm_resident_panels=not stream)
         X = s.solve_device(_cuda(b), lam, iters)
         res[(bn, stream)] = X
         Xn = X.cpu().numpy()
@@ -153,7 +153,7 @@ def test_batch_resident_panels_bit_exact():
     outs = {}
     for stream in (False, True):
         solvers = [api.Sfista(P, bb.shape, 1, ka.r, prec="bf16x3", op="gemm_band", lipschitz=L,
-                              gemm_stream_panels=stream) for P, bb, ka, L in probs]
+                              gemm_resident_panels=not stream) for P, bb, ka, L in probs]
         batch = api.Batch(solvers)
         outs[stream] = [X.clone() for X in batch.solve(d_bs, [lam] * len(probs), iters)]
         if not stream:
