@@ -128,6 +128,21 @@ __device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, uint32_t sr
                  "r"(src), "r"(x), "r"(y), "r"(z)
                  : "memory");
 }
+// The same with an L2 eviction-priority policy (from l2_evict_last).
+__device__ __forceinline__ void tma_store_3d_hint(const CUtensorMap *map, uint32_t src, int x, int y, int z,
+                                                  uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group.L2::cache_hint [%0, {%2, %3, %4}], [%1], %5;" ::"l"(
+            (uint64_t)map),
+        "r"(src), "r"(x), "r"(y), "r"(z), "l"(policy)
+        : "memory");
+}
+// An L2 policy that keeps the lines it covers over normal ones when L2 evicts.
+__device__ __forceinline__ uint64_t l2_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // The committed stores have finished reading shared memory (the buffer may be rewritten).
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
@@ -181,27 +196,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Store two neighbouring values (idx even) as split operand copies.
-__device__ __forceinline__ void store_split2(void *hi, void *lo, int kind, size_t idx, float v0, float v1) {
-    if (kind == 1) {
-        __nv_bfloat162 h, l;
-        h.x = __float2bfloat16_rn(v0);
-        h.y = __float2bfloat16_rn(v1);
-        *reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<__nv_bfloat16 *>(hi) + idx) = h;
-        if (lo) {
-            l.x = __float2bfloat16_rn(v0 - __bfloat162float(h.x));
-            l.y = __float2bfloat16_rn(v1 - __bfloat162float(h.y));
-            *reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<__nv_bfloat16 *>(lo) + idx) = l;
-        }
-    } else {
-        const float h0 = tf32_round(v0), h1 = tf32_round(v1);
-        *reinterpret_cast<float2 *>(reinterpret_cast<float *>(hi) + idx) = make_float2(h0, h1);
-        if (lo)
-            *reinterpret_cast<float2 *>(reinterpret_cast<float *>(lo) + idx) =
-                make_float2(tf32_round(v0 - h0), tf32_round(v1 - h1));
-    }
 }
 
 // Store four neighbouring values (idx a multiple of 4) as split operand
@@ -589,8 +583,16 @@ __global__ void __launch_bounds__(320, 1)
                         const CUtensorMap *oh = GROUPED ? m4 + 4 : &tOhi, *ol = GROUPED ? m4 + 5 : &tOlo;
                         const int x = nt * BN + h * CW;
                         if (x < ga->N) {   // boxes reaching past N or the last row are clipped by the unit
-                            tma_store_3d(oh, smem_u32(box_hi), x, m0, term);
-                            if (SPLIT) tma_store_3d(ol, smem_u32(box_lo), x, m0, term);
+                            if (EPI == GE_SPLIT) {
+                                // T / U are read back by the next stage: ask L2 to keep them
+                                // (84 MB at 2048^2, r = 5, within the 129 MB L2).
+                                const uint64_t pol = l2_evict_last();
+                                tma_store_3d_hint(oh, smem_u32(box_hi), x, m0, term, pol);
+                                if (SPLIT) tma_store_3d_hint(ol, smem_u32(box_lo), x, m0, term, pol);
+                            } else {
+                                tma_store_3d(oh, smem_u32(box_hi), x, m0, term);
+                                if (SPLIT) tma_store_3d(ol, smem_u32(box_lo), x, m0, term);
+                            }
                         }
                         bulk_commit();
                     }
