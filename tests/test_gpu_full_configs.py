@@ -74,8 +74,8 @@ def cfg3():
     return pr, _cuda(b), ref
 
 
-@pytest.mark.parametrize("prec,op", [("fp32", "auto"), ("bf16x3", "gemm_band"), ("tf32x3", "gemm_band"),
-                                     ("bf16x3", "gemm_dense")])
+@pytest.mark.parametrize("prec,op", [("fp32", "auto"), ("fp32", "fft"), ("bf16x3", "gemm_band"),
+                                     ("tf32x3", "gemm_band"), ("bf16x3", "gemm_dense")])
 def test_config3_300_iterations(cfg3, prec, op):
     """2048^2, r = 5, 63 x 63 mixture + Moffat PSF, reflective, lambda 0.002: all 300 iterations of Alg. 2."""
     pr, db, ref = cfg3
