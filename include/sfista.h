@@ -45,7 +45,7 @@ typedef enum {
     SFISTA_EINVAL = 1,    /* bad argument (size, centre, rank, NaN/Inf input, tied singular values) */
     SFISTA_ENOMEM = 2,    /* host or device allocation failed */
     SFISTA_ECUDA = 3,     /* a CUDA runtime/driver call failed */
-    SFISTA_ENOTSUP = 4,   /* valid request this build does not implement (e.g. periodic boundary) */
+    SFISTA_ENOTSUP = 4,   /* valid request this library does not implement (e.g. periodic boundary) */
     SFISTA_ENUMERIC = 5,  /* the iteration produced a non-finite value */
     SFISTA_ETIMEOUT = 6   /* a device-side wait exceeded its bound; the kernel returned early */
 } sfista_status;
@@ -180,7 +180,7 @@ void sfista_default_opts(sfista_opts *opts);
  * L = lambda_max(A_s^T A_s) by FP64 power iteration.
  * Errors: EINVAL for bad sizes/centre/rank, non-finite PSF, or
  * s_r == s_{r+1} > 0 (the truncation is not unique); ENOTSUP for periodic
- * boundary or a precision/operator pair this build lacks; ENOMEM; ECUDA.
+ * boundary or a precision/operator pair this library lacks; ENOMEM; ECUDA.
  */
 sfista_status sfista_setup(const double *psf, int psf_rows, int psf_cols,
                            int center_row, int center_col,
