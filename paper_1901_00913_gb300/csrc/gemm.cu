@@ -62,6 +62,7 @@ struct GemmArgs {
     float *out_f32;          // GE_STORE
     const float *Bd;         // GE_RESID
     int split_kind;          // 1 bf16, 2 tf32 (fp32 storage)
+    int keep_l2;             // GE_SPLIT, BF16: tensor-store the output with an L2 evict-last policy
     ProxArgs pa;             // GE_PROX
     unsigned *status;
 };
@@ -583,7 +584,7 @@ __global__ void __launch_bounds__(320, 1)
                         const CUtensorMap *oh = GROUPED ? m4 + 4 : &tOhi, *ol = GROUPED ? m4 + 5 : &tOlo;
                         const int x = nt * BN + h * CW;
                         if (x < ga->N) {   // boxes reaching past N or the last row are clipped by the unit
-                            if (EPI == GE_SPLIT) {
+                            if (EPI == GE_SPLIT && ga->keep_l2) {
                                 // T / U are read back by the next stage: ask L2 to keep them
                                 // (84 MB at 2048^2, r = 5, within the 129 MB L2).
                                 const uint64_t pol = l2_evict_last();
@@ -906,6 +907,10 @@ GemmArgs stacked_args(const GemmPath *g, const Band &band, Operand &Out, int *gy
     a.type_b = 0;
     a.out_hi = Out.hi;
     a.out_lo = Out.lo;
+    // Large intermediates (beyond a quarter of L2) are stored with the evict-last
+    // policy so that the next stage reads them from L2; small ones stay there anyway.
+    const size_t bytes = (size_t)g->r * g->m * g->n * (g->fmt == FMT_BF16 ? 2 : 4) * (g->split ? 2 : 1);
+    a.keep_l2 = bytes > ((size_t)32 << 20) ? 1 : 0;
     *gy = a.m_tiles * g->r;
     return a;
 }
