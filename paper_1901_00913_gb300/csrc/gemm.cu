@@ -20,10 +20,13 @@
 // Kernel roles (320 threads): warp 0 lane 0 issues TMA loads into a ring of
 // shared-memory stages; warp 1 owns the TMEM allocation and lane 0 issues the
 // MMAs, releasing each stage with tcgen05.commit; warps 2-9 wait for the
-// accumulator, read it with tcgen05.ld (two warps per 32-lane quarter, one
-// per column half) and run the epilogue.  Every mbarrier wait is bounded (about one second); on
-// expiry the kernel records DEV_TIMEOUT in the status word, drains what it
-// issued and returns, so the host sees SFISTA_ETIMEOUT instead of a hang.
+// accumulator, read it with tcgen05.ld in chunks of 64 columns (two warps per
+// 32-lane quarter, 32 columns each) and run the epilogue.  Tile shapes: N
+// tile 64, 128 or 256 (BN), and for the stacked stages optionally a resident
+// factor panel (RES); the four stages are chained by programmatic dependent
+// launch.  Every mbarrier wait is bounded (about one second); on expiry the
+// kernel records DEV_TIMEOUT in the status word, drains what it issued and
+// returns, so the host sees SFISTA_ETIMEOUT instead of a hang.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
