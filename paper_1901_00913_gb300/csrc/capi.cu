@@ -185,12 +185,13 @@ BandProb ctx_prob(const sfista_ctx *c) {
 void enqueue_stage(sfista_ctx *c, int st, const ProxArgs &pa) {
     const HostSetup &h = c->hs;
     if (is_fft(c->op)) {
-        // Stage 0: Passes A and B of A_s Y (or A Y); 1: Pass C + residual;
-        // 2, 3: the same for the adjoint, Pass C with Step 1 + Step 3.
+        // Stage 0: Passes A and B of A_s Y (or A Y); 1: Pass C with the
+        // residual fused with the adjoint's Pass A on it (R stays on chip);
+        // 2: the adjoint's Pass B; 3: its Pass C with Step 1 + Step 3.
         switch (st) {
             case 0: fftconv_part(c->fft, 0, false, c->Yop, EPI_STORE, nullptr, pa, c->stream); break;
-            case 1: fftconv_part(c->fft, 1, false, nullptr, EPI_RESIDUAL, c->R, pa, c->stream); break;
-            case 2: fftconv_part(c->fft, 0, true, c->R, EPI_STORE, nullptr, pa, c->stream); break;
+            case 1: fftconv_residual_adjoint(c->fft, pa, c->stream); break;
+            case 2: fftconv_adjoint_columns(c->fft, c->stream); break;
             default: fftconv_part(c->fft, 1, true, nullptr, EPI_PROX, nullptr, pa, c->stream); break;
         }
     } else if (fused_apply(c)) {

@@ -637,6 +637,80 @@ __global__ void __launch_bounds__(kThreads) fft_pass_c(FftConvDev P, float *__re
     }
 }
 
+// Pass C of the forward operator with the residual, fused with Pass A of
+// the adjoint: the inverse row transforms give (A Y)_a + i (A Y)_{a+1}, the
+// residual R = A Y - B of the two rows replaces them in the same line buffer
+// (columns n .. N - 1, and a row past the image, set to zero as Pass A's
+// zero padding would), and the forward row transform of R and the Hermitian
+// unpacking into the half spectra S1 follow without R leaving shared memory.
+// Pass B of the adjoint then reads S1.  Same row pairs, line plan, twiddles
+// and positions as the two passes it replaces.
+template <int LPC, bool BIG>
+__global__ void __launch_bounds__(kThreads) fft_pass_ca(FftConvDev P, ProxArgs pa) {
+    const int N = P.l2.N, ls = N + 1;
+    const PassSmem sm = pass_smem(LPC, N);
+    stage_tables(P.l2, P.tw2, P.pos2, sm);
+    __syncthreads();
+    const int a0 = 2 * blockIdx.x * LPC;
+    const int *pos = fft_pos() + sm.pos;
+    batched<float4>(
+        LPC * N,
+        [&](int it) {
+            const int f = it / LPC, j = it - f * LPC;
+            const int a = a0 + 2 * j;
+            const int g = f >= P.H2 ? N - f : f;
+            return a < P.m ? __ldcg(reinterpret_cast<const float4 *>(P.S2 + tile_index(a, g, P.H2)))
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+        },
+        [&](int it, float4 y) {
+            const int f = it / LPC, j = it - f * LPC;
+            if (f >= P.H2) {
+                y.y = -y.y;
+                y.w = -y.w;
+            }
+            fft_sm[j * ls + pos[f]] = make_float2(y.x - y.w, y.y + y.z);
+        });
+    __syncthreads();
+    fft_lines<true, BIG>(0, LPC, ls, P.l2, sm.tw);
+    // Residual of each row, in place: row 2j + 0 in the real part of line j,
+    // row 2j + 1 in the imaginary part.  Each thread reads and rewrites only
+    // its own elements, one component per row.
+    const int n = P.n;
+    constexpr int kEpi = 4;
+#pragma unroll 1
+    for (int rr = 0; rr < 2 * LPC; ++rr) {
+        const int a = a0 + rr;
+        float2 *ub = fft_sm + (rr >> 1) * ls;
+        for (int base = threadIdx.x; base < N; base += kEpi * blockDim.x) {
+            float bv[kEpi];
+#pragma unroll
+            for (int u = 0; u < kEpi; ++u) {
+                const int b = base + u * blockDim.x;
+                bv[u] = (a < P.m && b < n) ? __ldcg(pa.Bd + (size_t)a * n + b) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < kEpi; ++u) {
+                const int b = base + u * blockDim.x;
+                if (b >= N) continue;
+                float &c = (rr & 1) ? ub[b].y : ub[b].x;
+                c = (a < P.m && b < n) ? c - bv[u] : 0.f;   // zero padding past the row and past the image
+            }
+        }
+    }
+    __syncthreads();
+    fft_lines<false, BIG>(0, LPC, ls, P.l2, sm.tw);
+    for (int it = threadIdx.x; it < LPC * P.H2; it += blockDim.x) {
+        const int f = it / LPC, j = it - f * LPC;
+        const int s2 = a0 + 2 * j;
+        if (s2 >= P.m) continue;
+        const float2 z1 = fft_sm[j * ls + pos[f]];
+        const float2 z2 = fft_sm[j * ls + pos[f == 0 ? 0 : N - f]];
+        const float4 v = make_float4(0.5f * (z1.x + z2.x), 0.5f * (z1.y - z2.y), 0.5f * (z1.y + z2.y),
+                                     0.5f * (z2.x - z1.x));
+        *reinterpret_cast<float4 *>(P.S1 + tile_index(s2, f, P.H2)) = v;
+    }
+}
+
 // Kernel instances by lines per block (1, 2, 4) and by whether the line's
 // plan has radix-9 / radix-16 stages (BIG: those butterflies need about
 // twice the registers, so plans without them use instances without them
@@ -668,6 +742,12 @@ void launch_c2(int lpc, int grid, size_t smem, cudaStream_t s, const FftConvDev 
     if (lpc == 4) fft_pass_c<ADJ, EPI, 4, BIG><<<grid, kThreads, smem, s>>>(d, Out, pa);
     else if (lpc == 2) fft_pass_c<ADJ, EPI, 2, BIG><<<grid, kThreads, smem, s>>>(d, Out, pa);
     else fft_pass_c<ADJ, EPI, 1, BIG><<<grid, kThreads, smem, s>>>(d, Out, pa);
+}
+template <bool BIG>
+void launch_ca2(int lpc, int grid, size_t smem, cudaStream_t s, const FftConvDev &d, const ProxArgs &pa) {
+    if (lpc == 4) fft_pass_ca<4, BIG><<<grid, kThreads, smem, s>>>(d, pa);
+    else if (lpc == 2) fft_pass_ca<2, BIG><<<grid, kThreads, smem, s>>>(d, pa);
+    else fft_pass_ca<1, BIG><<<grid, kThreads, smem, s>>>(d, pa);
 }
 template <bool ADJ, int EPI>
 void launch_c(int lpc, bool big, int grid, size_t smem, cudaStream_t s, const FftConvDev &d, float *Out,
@@ -808,7 +888,8 @@ cudaError_t allow_smem_lpc(int limit) {
         (e = allow_smem(fft_pass_c<false, EPI_STORE, LPC, BIG>, limit)) ||
         (e = allow_smem(fft_pass_c<false, EPI_RESIDUAL, LPC, BIG>, limit)) ||
         (e = allow_smem(fft_pass_c<true, EPI_STORE, LPC, BIG>, limit)) ||
-        (e = allow_smem(fft_pass_c<true, EPI_PROX, LPC, BIG>, limit)))
+        (e = allow_smem(fft_pass_c<true, EPI_PROX, LPC, BIG>, limit)) ||
+        (e = allow_smem(fft_pass_ca<LPC, BIG>, limit)))
         return e;
     return cudaSuccess;
 }
@@ -965,6 +1046,21 @@ void fftconv_part(const FftConv *f, int part, bool adj, const float *In, EpiKind
         else
             launch_c<false, EPI_STORE>(f->lpc_c, f->big2, gc, sc, s, d, Out, pa);
     }
+}
+
+void fftconv_residual_adjoint(const FftConv *f, const ProxArgs &pa, cudaStream_t s) {
+    const FftConvDev &d = f->d;
+    const int gc = ((d.m + 1) / 2 + f->lpc_c - 1) / f->lpc_c;
+    const size_t sc = pass_smem_bytes(f->lpc_c, d.l2.N, true);
+    if (f->big2) launch_ca2<true>(f->lpc_c, gc, sc, s, d, pa);
+    else launch_ca2<false>(f->lpc_c, gc, sc, s, d, pa);
+}
+
+void fftconv_adjoint_columns(const FftConv *f, cudaStream_t s) {
+    const FftConvDev &d = f->d;
+    const int gb = (d.H2 + f->lpc_b - 1) / f->lpc_b;
+    const size_t sb = pass_smem_bytes(f->lpc_b, d.l1.N, false);
+    launch_b<true>(f->lpc_b, f->big1, gb, sb, s, d);
 }
 
 void fftconv_apply(const FftConv *f, bool adj, const float *In, EpiKind epi, float *Out, const ProxArgs &pa,

@@ -45,6 +45,13 @@ void fftconv_destroy(FftConv *f);
 // Passes A and B (In read), part 1 = Pass C with the epilogue (Out written).
 void fftconv_part(const FftConv *f, int part, bool adj, const float *In, EpiKind epi, float *Out, const ProxArgs &pa,
                   cudaStream_t s);
+// Pass C of the forward operator with the residual R = A Y - B, fused with
+// Pass A of the adjoint on R (R is not written to global memory): after it,
+// fftconv_adjoint_columns and fftconv_part(1, adj = true, ...) complete the
+// adjoint product.
+void fftconv_residual_adjoint(const FftConv *f, const ProxArgs &pa, cudaStream_t s);
+// Pass B of the adjoint (column transforms with the conjugate kernel spectrum).
+void fftconv_adjoint_columns(const FftConv *f, cudaStream_t s);
 void fftconv_apply(const FftConv *f, bool adj, const float *In, EpiKind epi, float *Out, const ProxArgs &pa,
                    cudaStream_t s);
 // Device bytes the engine holds (spectra and kernel spectrum).
